@@ -1,0 +1,420 @@
+"""Pins of the FP64 oracle against closed forms, invariants, brute force and the
+paper's printed numbers.  CPU only.
+
+Each test is chosen so that a plausible slip in the oracle (a dropped term, a
+wrong sign or index, a transposed operand, a wrong unit) fails at least one of
+them.  None of them compares the oracle with itself.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate, stats
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+ME = 0.51099895            # m_e c^2, MeV (CODATA 2018)
+RE = 2.8179403262e-13      # classical electron radius, cm
+SIGMA_T = 8.0 * math.pi * RE * RE / 3.0   # Thomson cross section
+
+
+def water(orc, **kw):
+    return orc.Materials(z_over_a=[0.5551], zeff=[7.42], **kw)
+
+
+# ---------------------------------------------------------------------------
+# Klein-Nishina
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("e", [0.011, 0.05, 0.2, 0.511])
+def test_kn_total_equals_integral_of_differential(orc, e):
+    # σ = 2π ∫ dσ/dΩ d(cosθ): the closed form and the angular form are separate
+    # formulas, so a dropped term in either breaks the equality.
+    val, err = integrate.quad(lambda c: orc.dsigma_kn(e, c), -1.0, 1.0, epsabs=0, epsrel=1e-13)
+    assert abs(2 * math.pi * val / orc.sigma_kn(e) - 1.0) < 1e-10
+
+
+def test_kn_thomson_limit(orc):
+    # Low-energy expansion σ/σ_T = 1 - 2k + 26/5 k^2 - 133/10 k^3 + O(k^4), and
+    # dσ/dΩ -> (r_e^2/2)(1 + cos^2θ) as k -> 0.
+    e = 0.511e-3
+    k = e / ME
+    assert abs(orc.sigma_kn(e) / (SIGMA_T * (1 - 2 * k + 5.2 * k * k - 13.3 * k ** 3)) - 1.0) < 1e-9
+    e = 1e-5
+    for c in (-1.0, -0.3, 0.0, 0.7, 1.0):
+        assert abs(orc.dsigma_kn(e, c) / (0.5 * RE * RE * (1 + c * c)) - 1.0) < 1e-4
+
+
+def test_kn_forward_and_backward_values(orc):
+    # Forward scattering: P = 1, dσ/dΩ = r_e^2 for any energy.
+    for e in (0.05, 0.511):
+        assert abs(orc.dsigma_kn(e, 1.0) / (RE * RE) - 1.0) < 1e-13
+    # Backscatter at 511 keV: P = 1/(1+2k); dσ/dΩ = (r_e^2/2) P^2 (P + 1/P).
+    k = 0.511 / ME
+    p = 1.0 / (1.0 + 2.0 * k)
+    assert abs(orc.dsigma_kn(0.511, -1.0) / (0.5 * RE * RE * p * p * (p + 1 / p)) - 1) < 1e-13
+    # Published value of σ_KN at 511 keV: 0.2865 barn per electron.
+    assert abs(orc.sigma_kn(0.511) / 0.2865e-24 - 1.0) < 2e-4
+
+
+def _kn_bin_probs(e, edges):
+    # Bin probabilities of cosθ from the textbook dσ/dΩ (written here on its own,
+    # Compton's formula for P) -- not from the oracle.
+    def f(c):
+        k = e / ME
+        p = 1.0 / (1.0 + k * (1.0 - c))
+        return p * p * (p + 1.0 / p - (1.0 - c * c))
+    z = integrate.quad(f, -1, 1, epsrel=1e-12)[0]
+    return np.array([integrate.quad(f, a, b, epsrel=1e-12)[0] for a, b in zip(edges[:-1], edges[1:])]) / z
+
+
+@pytest.mark.parametrize("e", [0.511, 0.2, 0.05])
+def test_kn_sampler_chi2(orc, e):
+    n = 1_000_000
+    s = orc.sample_kn_cos(e, n, seed=12345)
+    edges = np.linspace(-1, 1, 51)
+    p = _kn_bin_probs(e, edges)
+    h, _ = np.histogram(s, edges)
+    chi2 = ((h - n * p) ** 2 / (n * p)).sum()
+    assert stats.chi2.sf(chi2, len(p) - 1) > 1e-4, chi2
+
+
+# ---------------------------------------------------------------------------
+# Directions
+# ---------------------------------------------------------------------------
+def test_marsaglia_isotropic(orc):
+    n = 1_000_000
+    d = orc.sample_dirs(n, seed=7)
+    assert np.allclose(np.linalg.norm(d, axis=1), 1.0, atol=1e-12)
+    # mean 0, <w_i^2> = 1/3, <w_i w_j> = 0 (closed forms for the uniform sphere).
+    se = 1.0 / math.sqrt(3 * n)
+    assert np.all(np.abs(d.mean(axis=0)) < 5 * se)
+    m2 = (d ** 2).mean(axis=0)
+    se2 = math.sqrt(4.0 / 45.0 / n)      # var(w^2) = 1/5 - 1/9
+    assert np.all(np.abs(m2 - 1 / 3) < 5 * se2)
+    # cosθ uniform on [-1, 1] and azimuth uniform: chi-square.
+    h, _ = np.histogram(d[:, 2], np.linspace(-1, 1, 41))
+    assert stats.chisquare(h).pvalue > 1e-4
+    phi = np.arctan2(d[:, 1], d[:, 0])
+    h, _ = np.histogram(phi, np.linspace(-np.pi, np.pi, 41))
+    assert stats.chisquare(h).pvalue > 1e-4
+
+
+def test_rotation_keeps_angle_and_is_symmetric(orc):
+    rng = np.random.default_rng(3)
+    for _ in range(50):
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        c = rng.uniform(-1, 1)
+        phis = np.linspace(0, 2 * np.pi, 64, endpoint=False)
+        out = np.array([orc.rotate(d, c, ph) for ph in phis])
+        assert np.allclose(np.linalg.norm(out, axis=1), 1.0, atol=1e-12)
+        assert np.allclose(out @ d, c, atol=1e-12)
+        # Averaged over the azimuth the new direction is c * d.
+        assert np.allclose(out.mean(axis=0), c * d, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Voxel traversal and free flight
+# ---------------------------------------------------------------------------
+def _slab_exit(p, d, L):
+    # Distance from p (inside the box [0, L]) to the box boundary along d.
+    t = np.inf
+    for a in range(3):
+        if d[a] > 0:
+            t = min(t, (L[a] - p[a]) / d[a])
+        elif d[a] < 0:
+            t = min(t, -p[a] / d[a])
+    return t
+
+
+def _brute_lengths(shape_zyx, spacing, p, d, step):
+    nz, ny, nx = shape_zyx
+    L = np.array([nx * spacing[0], ny * spacing[1], nz * spacing[2]])
+    t_exit = _slab_exit(p, d, L)
+    t = (np.arange(int(t_exit / step) + 1) + 0.5) * step
+    t = t[t < t_exit]
+    pts = p[None, :] + t[:, None] * d[None, :]
+    idx = np.floor(pts / np.array(spacing)).astype(np.int64)
+    idx = np.clip(idx, 0, [nx - 1, ny - 1, nz - 1])
+    flat = (idx[:, 2] * ny + idx[:, 1]) * nx + idx[:, 0]
+    out = np.bincount(flat, minlength=nx * ny * nz).astype(np.float64) * step
+    # last partial step
+    out[flat[-1]] += t_exit - (t[-1] + 0.5 * step)
+    return out, t_exit
+
+
+def test_trace_matches_brute_force_stepping(orc):
+    rng = np.random.default_rng(11)
+    shape = (3, 4, 5)
+    spacing = (0.7, 0.5, 1.1)
+    L = np.array([5 * 0.7, 4 * 0.5, 3 * 1.1])
+    step = 1e-5
+    for _ in range(20):
+        p = rng.uniform(0, 1, 3) * L
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        vox, ln = orc.trace(shape, spacing, p, d)
+        got = np.zeros(60)
+        np.add.at(got, vox, ln)
+        ref, t_exit = _brute_lengths(shape, spacing, p, d, step)
+        assert abs(ln.sum() - t_exit) < 1e-12
+        assert np.all(np.abs(got - ref) < 2 * step), np.abs(got - ref).max()
+        # Consecutive voxels are face neighbours (one index changes by one).
+        v = np.stack([vox % 5, (vox // 5) % 4, vox // 20], axis=1)
+        assert np.all(np.abs(np.diff(v, axis=0)).sum(axis=1) == 1)
+
+
+def test_trace_axis_aligned_and_on_boundary(orc):
+    # A ray along +x from a point on a voxel corner: floor convention puts it in
+    # the upper voxel; it visits every voxel of its row with full length.
+    vox, ln = orc.trace((4, 4, 4), (0.5, 0.5, 0.5), [1.0, 1.0, 1.0], [1.0, 0.0, 0.0])
+    assert list(vox) == [2 * 16 + 2 * 4 + i for i in (2, 3)]
+    assert np.allclose(ln, 0.5)
+    vox, ln = orc.trace((4, 4, 4), (0.5, 0.5, 0.5), [1.0, 1.0, 1.0], [-1.0, 0.0, 0.0])
+    assert list(vox) == [2 * 16 + 2 * 4 + i for i in (2, 1, 0)]
+    assert np.allclose(ln, [0.0, 0.5, 0.5])
+
+
+def test_first_flight_follows_exp_of_optical_depth(orc):
+    rng = np.random.default_rng(5)
+    mu = rng.uniform(0.05, 0.6, size=(2, 3, 4))
+    spacing = (0.8, 0.6, 1.0)
+    p = np.array([0.1, 0.9, 0.3])
+    d = np.array([0.8, 0.3, 0.5])
+    d /= np.linalg.norm(d)
+    n = 400_000
+    dist = orc.first_flight(mu, spacing, p, d, n, seed=99)
+    lens, t_exit = _brute_lengths(mu.shape, spacing, p, d, 1e-5)
+    tau = float((lens * mu.ravel()).sum())
+    esc = np.mean(dist < 0)
+    se = math.sqrt(math.exp(-tau) * (1 - math.exp(-tau)) / n)
+    assert abs(esc - math.exp(-tau)) < 5 * se
+    # P(collision before t) = 1 - exp(-tau(t)) at a few depths along the ray.
+    for frac in (0.2, 0.5, 0.8):
+        t = frac * t_exit
+        l_t, _ = _brute_lengths(mu.shape, spacing, p, d, 1e-5)
+        # optical depth up to t by brute-force stepping
+        steps = np.arange(int(t / 1e-5)) * 1e-5 + 0.5e-5
+        pts = p[None] + steps[:, None] * d[None]
+        idx = np.floor(pts / np.array(spacing)).astype(int)
+        tau_t = mu[idx[:, 2], idx[:, 1], idx[:, 0]].sum() * 1e-5
+        pr = 1 - math.exp(-tau_t)
+        got = np.mean((dist >= 0) & (dist < t))
+        assert abs(got - pr) < 5 * math.sqrt(pr * (1 - pr) / n)
+
+
+# ---------------------------------------------------------------------------
+# HU -> density / material (§2.1)
+# ---------------------------------------------------------------------------
+def test_hu_curve_nodes_midpoints_and_clamps(orc):
+    nodes_hu = [-1000, -750, -100, 40, 1000]
+    nodes_rho = [0.0012, 0.26, 0.95, 1.03, 1.85]
+    den, mat = orc.hu_to_phantom(np.array(nodes_hu, np.int16))
+    assert np.allclose(den, nodes_rho, rtol=0, atol=1e-15)
+    assert list(mat) == [0, 1, 2, 3, 4]
+    mids = [(a + b) // 2 for a, b in zip(nodes_hu[:-1], nodes_hu[1:])]
+    den, _ = orc.hu_to_phantom(np.array(mids, np.int16))
+    exp = [nodes_rho[i] + (mids[i] - nodes_hu[i]) / (nodes_hu[i + 1] - nodes_hu[i]) * (nodes_rho[i + 1] - nodes_rho[i]) for i in range(4)]
+    assert np.allclose(den, exp, rtol=0, atol=1e-15)
+    den, mat = orc.hu_to_phantom(np.array([-1024, -3000, 1500, 3071], np.int16))
+    assert np.allclose(den, [0.0012, 0.0012, 1.85, 1.85])
+    assert list(mat) == [0, 0, 4, 4]
+    # Nearest-node material: boundaries halfway between nodes, ties to the lower node.
+    den, mat = orc.hu_to_phantom(np.array([-875, -874, -425, -424, -30, -29, 520, 521], np.int16))
+    assert list(mat) == [0, 1, 1, 2, 2, 3, 3, 4]
+    # Density is monotone in HU.
+    h = np.arange(-1024, 3072, dtype=np.int16)
+    den, _ = orc.hu_to_phantom(h)
+    assert np.all(np.diff(den) >= 0)
+
+
+# ---------------------------------------------------------------------------
+# Whole-simulation pins
+# ---------------------------------------------------------------------------
+def _ray_box_interval(d, lo, hi):
+    # Entry and exit distances of rays from the origin (direction d[n,3]) through
+    # the axis-aligned box [lo, hi] (slab method); empty intervals give t0 >= t1.
+    with np.errstate(divide="ignore", invalid="ignore"):
+        inv = 1.0 / d
+        t_a = (lo[None, :]) * inv
+        t_b = (hi[None, :]) * inv
+    tmin = np.minimum(t_a, t_b)
+    tmax = np.maximum(t_a, t_b)
+    tmin = np.where(np.isnan(tmin), -np.inf, tmin)
+    tmax = np.where(np.isnan(tmax), np.inf, tmax)
+    t0 = np.maximum(tmin.max(axis=1), 0.0)
+    t1 = tmax.min(axis=1)
+    return t0, t1
+
+
+def test_point_source_absorber_matches_first_collision_kernel(orc):
+    # Pure absorber (no electrons, so no Compton): every photon deposits all its
+    # energy at its first interaction, so the expected tally of voxel v is
+    #   N q(E) ∫_{4π} dΩ/4π [exp(-mu r_in) - exp(-mu r_out)]
+    # i.e. the uncollided kernel mu exp(-mu r)/(4 pi r^2) integrated over v.
+    n_side, vox = 8, 0.5
+    mu_target = 0.4                       # 1/cm at 0.511 MeV
+    zeff = 7.42
+    pe = mu_target * 0.511 ** 3 / zeff ** 3.8
+    mat = orc.Materials(z_over_a=[0.0], zeff=[zeff], pe_coeff=pe)
+    assert abs(orc.mu(mat, 0, 1.0, 0.511)[1] - mu_target) < 1e-12
+    den = np.ones((n_side,) * 3)
+    src = np.array([2.0, 2.0, 2.0])        # a voxel corner at the cube centre
+    N = 2_000_000
+    r = orc.run(den, np.zeros((n_side,) * 3, np.uint8), mat, spacing=(vox,) * 3, point=tuple(src),
+                n_hist=N, seed=4, batches=10)
+    q = round(0.511 * 64e6)
+    assert r.counters["compton"] == 0
+    # Quadrature over directions: a fine stratified grid in (cosθ, φ).
+    m = 1500
+    c = (np.arange(m) + 0.5) / m * 2 - 1
+    ph = (np.arange(2 * m) + 0.5) / (2 * m) * 2 * np.pi
+    C_, P_ = np.meshgrid(c, ph, indexing="ij")
+    s = np.sqrt(1 - C_ ** 2)
+    dirs = np.stack([s * np.cos(P_), s * np.sin(P_), C_], axis=-1).reshape(-1, 3)
+    # Check the voxels of a 4x4x4 block around the source and a far corner.
+    checks = [(i, j, k) for i in range(2, 6) for j in range(2, 6) for k in range(2, 6)] + [(7, 7, 7), (0, 3, 6)]
+    z = []
+    for (ix, iy, iz) in checks:
+        lo = np.array([ix, iy, iz]) * vox - src
+        hi = lo + vox
+        t0, t1 = _ray_box_interval(dirs, lo, hi)
+        ok = t1 > t0
+        prob = np.where(ok, np.exp(-mu_target * t0) - np.exp(-mu_target * np.where(ok, t1, t0)), 0).mean()
+        expect = N * prob * q
+        got = r.tally[iz, iy, ix]
+        sd = math.sqrt(N * prob * (1 - prob)) * q
+        z.append((got - expect) / sd)
+        assert abs(prob) > 0
+    z = np.array(z)
+    assert np.all(np.abs(z) < 5), z
+    assert abs(z.mean()) < 5 / math.sqrt(len(z))
+
+
+def test_energy_conservation_is_exact(orc):
+    from paper_2111_11687_gb300 import inputs
+    cube = inputs.water_cube(16, 1.0)
+    mat = water(orc)
+    r = orc.run(cube.density, cube.material, mat, spacing=cube.spacing, point=cube.point,
+                n_hist=20000, seed=2, batches=4)
+    c = r.counters
+    assert c["emitted"] == 20000 * round(0.511 * 64e6)
+    assert c["deposited"] + c["escaped"] == c["emitted"]
+    assert int(r.tally.sum()) == c["deposited"]
+    # Decay mode on a small phantom: positron energy plus two photons per decay.
+    ph = inputs.adult_phantom(shape=(30, 24, 24), spacing=(2.1, 2.1, 3.0), seed=3)
+    den, mt = orc.hu_to_phantom(ph.hu)
+    mat5 = orc.Materials(z_over_a=inputs.MATERIAL_Z_OVER_A, zeff=inputs.MATERIAL_ZEFF)
+    r = orc.run(den, mt, mat5, activity=ph.activity, labels=ph.labels, n_labels=27,
+                spacing=ph.spacing, n_hist=20000, seed=5, batches=4)
+    c = r.counters
+    per_decay = 2 * round(0.511 * 64e6) + round(0.25 * 64e6)
+    assert c["emitted"] == 20000 * per_decay
+    assert c["deposited"] + c["escaped"] == c["emitted"]
+    assert int(r.tally.sum()) == c["deposited"]
+    # No photon gains energy: nothing deposited per event above 0.511 MeV
+    # (pair production is absent below 1.02 MeV).
+    assert c["compton"] > 0 and c["photo"] > 0
+
+
+def test_infinite_medium_absorbs_everything(orc):
+    # A 10 m water block: escape probability ~exp(-48), so absorbed = emitted.
+    n = 5
+    den = np.ones((n, n, n))
+    r = orc.run(den, np.zeros((n, n, n), np.uint8), water(orc), spacing=(200.0,) * 3,
+                point=(500.0, 500.0, 500.0), n_hist=20000, seed=9, batches=4)
+    c = r.counters
+    assert c["escaped"] == 0 and c["escapes"] == 0
+    assert c["deposited"] == c["emitted"]
+
+
+def test_eq1_to_eq3_on_a_deterministic_case(orc):
+    # Opaque single voxel: mu huge, every photon is absorbed where it starts, so
+    # each batch's tally is exact and the batch variance is zero.
+    n = 3
+    mat = orc.Materials(z_over_a=[0.0], zeff=[7.42], pe_coeff=1e3)
+    den = np.full((n, n, n), 2.0)
+    act = np.zeros((n, n, n))
+    act[1, 1, 1] = 1.0
+    lab = np.zeros((n, n, n), np.uint8)
+    lab[1, 1, :] = 1          # organ 1: three voxels, one of them the source
+    N, A = 1001, 3.0e8
+    spacing = (0.4, 0.5, 0.6)
+    r = orc.run(den, np.zeros((n, n, n), np.uint8), mat, activity=act, labels=lab, n_labels=1,
+                spacing=spacing, n_hist=N, seed=1, batches=10, activity_bq=A)
+    q = 2 * round(0.511 * 64e6) + round(0.25 * 64e6)
+    assert r.tally[1, 1, 1] == N * q and r.tally.sum() == N * q
+    mass = 2.0 * 0.4 * 0.5 * 0.6 * 1e-3                      # kg
+    e_j = q / 64.0 * 1.602176634e-19                          # J per decay
+    dr = e_j / mass * A                                       # Eq. 1
+    assert abs(r.dose_rate[1, 1, 1] / dr - 1) < 1e-14
+    assert r.sigma[1, 1, 1] < 1e-12 * dr
+    # Eq. 2: unweighted mean over the organ's 3 voxels.
+    assert abs(r.organ_mean[1] / (dr / 3) - 1) < 1e-14
+    # Eq. 3: RMS of relative uncertainties: the source voxel 0, the two empty
+    # voxels 1 (100 %) each.
+    assert abs(r.organ_eps[1] - math.sqrt(2 / 3)) < 1e-14
+    assert r.organ_sigma[1] < 1e-12 * dr
+
+
+def test_batch_sigma_matches_spread_over_seeds(orc):
+    # The batch estimate of sigma of the mean must match the scatter of the mean
+    # over independent runs (consistency of the variance estimator).
+    n = 6
+    mat = orc.Materials(z_over_a=[0.5551], zeff=[7.42])
+    den = np.ones((n, n, n))
+    lab = np.zeros((n, n, n), np.uint8)
+    lab[:3] = 1
+    act = np.ones((n, n, n))
+    means, sig, om, osg = [], [], [], []
+    for s in range(40):
+        r = orc.run(den, np.zeros((n, n, n), np.uint8), mat, activity=act, labels=lab, n_labels=1,
+                    spacing=(1.0,) * 3, n_hist=4000, seed=100 + s, batches=8)
+        means.append(r.dose_rate[2, 2, 2]); sig.append(r.sigma[2, 2, 2])
+        om.append(r.organ_mean[1]); osg.append(r.organ_sigma[1])
+    for m, sg in ((means, sig), (om, osg)):
+        emp = np.std(m, ddof=1)
+        est = math.sqrt(np.mean(np.square(sg)))
+        # ratio of variances ~ F-distributed; 40 runs -> about +-25 % at 2 sigma
+        assert 0.6 < emp / est < 1.5, (emp, est)
+
+
+# ---------------------------------------------------------------------------
+# Eq. 4 against the paper's Table 1
+# ---------------------------------------------------------------------------
+def _table1():
+    rows = []
+    with open(os.path.join(GOLDEN, "table1_organ_dose_rates.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            name, g, gu, a, au, d = line.split()
+            rows.append((name, float(g), float(gu), float(a), float(au), float(d)))
+    return rows
+
+
+def test_eq4_reproduces_table1(orc):
+    rows = _table1()
+    assert len(rows) == 27
+    g = np.array([r[1] for r in rows])
+    a = np.array([r[3] for r in rows])
+    d = np.array([r[5] for r in rows])
+    got = orc.rel_diff_percent(a, g)
+    # Printed rates have 4 significant digits: the recomputed difference can be
+    # off by up to ~(0.5e-3/1.3)*100*2 percent from the printed one.
+    assert np.all(np.abs(got - d) < 0.08), np.abs(got - d).max()
+    summ = {}
+    with open(os.path.join(GOLDEN, "table1_summary.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            k, v = line.split()
+            summ[k] = float(v)
+    assert abs(d.min() - summ["diff_min"]) < 1e-9 and abs(d.max() - summ["diff_max"]) < 1e-9
+    assert abs(np.abs(d).mean() - summ["mean_abs_diff"]) < 0.005
+    assert abs(np.abs(got).mean() - summ["mean_abs_diff"]) < 0.01
+    gu = np.array([r[2] for r in rows]); au = np.array([r[4] for r in rows])
+    assert gu.min() == summ["gate_unc_min"] and gu.max() == summ["gate_unc_max"]
+    assert au.min() == summ["archer_unc_min"] and au.max() == summ["archer_unc_max"]
+    # Sign convention: test above reference -> positive.
+    assert orc.rel_diff_percent(2.0, 1.0) == 100.0
