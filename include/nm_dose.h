@@ -1,0 +1,202 @@
+/*
+ * nm_dose.h -- C ABI of the GB300 (sm_103a) Monte Carlo internal-dosimetry
+ * engine for 18F PET/CT, after ARCHER-NM (Peng et al., arXiv 2111.11687).
+ *
+ * The engine simulates positron-emitter decays drawn from a PET-derived
+ * activity map (§2.1: linear PET -> decay PDF), each giving two back-to-back
+ * 0.511 MeV photons (§2.1) plus a locally deposited positron kinetic energy,
+ * transports the photons through a CT-derived density/material voxel grid with
+ * Compton (Klein-Nishina) and photoelectric events and a 10 keV photon cutoff
+ * (§2.1), tallies deposited energy per voxel, and reports the dose-rate map
+ * of Eq. 1, its batch uncertainty, and the organ means of Eq. 2 and Eq. 3.
+ *
+ * Conventions for every entry point:
+ *  - Voxel arrays are [nz][ny][nx] with x fastest; spacing is in cm; the grid
+ *    origin is its corner; the outside of the grid is vacuum.
+ *  - A pointer argument may be host or device memory: the library asks the
+ *    CUDA runtime which it is.  Inputs are copied before the call returns, so
+ *    the caller may free them afterwards.  Outputs are allocated by the caller.
+ *  - Every call returns an nm_status; nothing aborts, traps or asserts.  On an
+ *    error, nm_last_error() returns a message for the calling thread.
+ *  - Device work is ordered on the stream given in nm_options (NULL = the
+ *    legacy default stream); calls that return data synchronise that stream.
+ *  - Energies are tallied in int64 fixed point, one unit = 2^-6 eV, and each
+ *    deposit is a difference of fixed-point energies, so a fixed seed gives
+ *    bit-identical tallies run to run whatever the scheduling.
+ */
+#ifndef NM_DOSE_H
+#define NM_DOSE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NM_MAX_MATERIALS 8  /* material ids 0..7 */
+#define NM_MAX_LABELS 31    /* organ labels 1..31; 0 = outside every organ */
+#define NM_UNITS_PER_MEV 64000000.0 /* tally unit: 2^-6 eV */
+
+typedef struct nm_dose nm_dose; /* opaque handle; owns all its device memory */
+
+typedef enum {
+  NM_OK = 0,
+  NM_ERR_ARG = 1,      /* invalid argument: sizes, NaN/negative inputs, ... */
+  NM_ERR_CUDA = 2,     /* a CUDA runtime call failed */
+  NM_ERR_OOM = 3,      /* device allocation failed */
+  NM_ERR_OVERFLOW = 4, /* the int64 tallies could overflow */
+  NM_ERR_TIMEOUT = 5,  /* a bounded device wait gave up */
+  NM_ERR_STATE = 6,    /* call not valid in the handle's state */
+  NM_ERR_DEVICE = 7    /* a device-side check failed (see nm_last_error) */
+} nm_status;
+
+enum { NM_SOURCE_DECAY = 0, NM_SOURCE_POINT = 1 };
+
+/* Voxel phantom (§2.1: CT -> mass density and material per voxel). */
+typedef struct {
+  int32_t nx, ny, nz;        /* voxels; nx*ny*nz < 2^31 */
+  float dx, dy, dz;          /* voxel size, cm, > 0 */
+  const float* density;      /* g/cm^3, finite, > 0, [nz][ny][nx] */
+  const uint8_t* material;   /* material id < materials.n, [nz][ny][nx] */
+} nm_grid;
+
+/* Photon interaction data (§2.1: photoelectric and Compton explicit, pair
+ * production absent below 1.02 MeV).  Per material m:
+ *   mu_compton = rho N_A (Z/A)_m sigma_KN(E)           (Klein-Nishina)
+ *   mu_photo   = rho pe_coeff Zeff_m^pe_exp / E^3       (E in MeV)
+ *   mu_rayl    = rho rayleigh_coeff Zeff_m^2 / E^2      (only if rayleigh != 0)
+ * with linear attenuation in 1/cm. */
+typedef struct {
+  int32_t n;                 /* materials, 1..NM_MAX_MATERIALS */
+  const double* z_over_a;    /* [n] host pointer */
+  const double* zeff;        /* [n] host pointer */
+  double pe_coeff;           /* cm^2/g MeV^3 */
+  double pe_exp;             /* 3.8 */
+  double rayleigh_coeff;     /* cm^2/g MeV^2 */
+  int32_t rayleigh;          /* 0 = off (the paper's physics) */
+  double photon_cut_mev;     /* 0.010 (§2.1) */
+  double electron_cut_mev;   /* 0.200 (§2.1); recorded, electrons deposit locally */
+} nm_materials;
+
+typedef struct {
+  int32_t source_mode;       /* NM_SOURCE_DECAY (activity map) or NM_SOURCE_POINT */
+  float point[3];            /* cm, point mode: one photon per history from here */
+  double photon_mev;         /* 0.511 */
+  double positron_mev;       /* positron energy deposited at the decay, 0.25 */
+  int32_t batches;           /* batches per nm_dose_run call, >= 2 (default 10) */
+  double activity_bq;        /* A(t_s) of Eq. 1, Bq */
+  int32_t n_labels;          /* organs 1..n_labels in the label map (0 = none) */
+  int32_t block_threads;     /* transport CTA size; 0 = autotuned */
+  int32_t chunk;             /* histories per warp work grab; 0 = autotuned */
+  int32_t warp_aggregate;    /* warp-aggregated tally atomics: -1 auto, 0 off, 1 on */
+  int32_t regroup;           /* event regrouping in the transport: -1 auto, 0 off, 1 on */
+  int32_t max_steps;         /* per-photon flight-step limit (bounded loops) */
+  void* stream;              /* cudaStream_t; NULL = legacy default stream */
+} nm_options;
+
+typedef struct {
+  uint64_t histories;        /* histories simulated so far */
+  uint64_t batches;          /* batches folded so far */
+  int64_t emitted;           /* energy units emitted by all histories */
+  int64_t deposited;         /* energy units in the tally */
+  int64_t escaped;           /* energy units carried out of the grid */
+  int64_t killed;            /* energy units of photons stopped by max_steps */
+  uint64_t steps;            /* flight steps (real + virtual) */
+  uint64_t compton, photo, rayleigh, cutoff, escapes;
+  double transport_ms;       /* device time of the transport launches */
+  double fold_ms;            /* device time of the batch folds */
+  uint32_t device_status;    /* OR of NM_DEV_* flags seen */
+  int32_t block_threads, chunk, warp_aggregate, regroup, grid_blocks; /* tuning used */
+} nm_counters;
+
+#define NM_DEV_STEP_LIMIT 1u   /* a photon hit max_steps */
+#define NM_DEV_KAHN_LIMIT 2u   /* Kahn sampling hit its trial limit */
+#define NM_DEV_BAD_VOXEL 4u    /* material id out of range, density not > 0 */
+#define NM_DEV_BAD_ACTIVITY 8u /* activity negative or not finite */
+
+/* Fills *o with the defaults: decay mode, 0.511 MeV photons, 0.25 MeV positron,
+ * 10 batches, A(t_s) = 8.0 mCi decayed 60 min with T1/2 = 109.77 min (§2.2),
+ * autotuned launch shape, max_steps 100000, legacy default stream. */
+void nm_options_default(nm_options* o);
+
+/* §2.1 CT -> phantom: HU to mass density by the piecewise-linear curve through
+ * (HU, g/cm^3) = (-1000, 0.0012), (-750, 0.26), (-100, 0.95), (40, 1.03),
+ * (1000, 1.85), clamped at both ends, computed in FP32; material = the node
+ * nearest in HU, ties to the lower node (0 air, 1 lung, 2 adipose, 3 soft
+ * tissue, 4 bone), decided in integer arithmetic.  hu[n] in; density[n],
+ * material[n] out (host or device).  n >= 0. */
+nm_status nm_ct_to_phantom(const int16_t* hu, int64_t n, float* density, uint8_t* material,
+                           void* stream);
+
+/* Creates a simulation handle (§2.1).  grid, materials: as above.  activity:
+ * [V] decay density (the PET value, Bq/mL; linear -> decay PDF), >= 0 and
+ * finite with a positive sum, required in decay mode, ignored (may be NULL) in
+ * point mode.  labels: [V] organ ids 0..opts->n_labels, or NULL.  opts: NULL =
+ * defaults.  The activity is turned into an alias table on the device in FP64.
+ * All inputs are copied.  Errors: NM_ERR_ARG for invalid sizes or values,
+ * NM_ERR_OOM, NM_ERR_CUDA; *out is NULL on error. */
+nm_status nm_dose_create(nm_dose** out, const nm_grid* grid, const nm_materials* materials,
+                         const float* activity, const uint8_t* labels, const nm_options* opts);
+
+/* Simulates n_decays more histories (§2.1-2.2) in opts.batches batches of
+ * near-equal size, folding each batch into the statistics.  History ids
+ * continue across calls and every history's random numbers depend only on
+ * (seed, history id) (Philox4x32-10), so the tally after run(a) + run(b) is
+ * bit-identical to run(a + b); the batch uncertainty depends on the split.
+ * NM_ERR_OVERFLOW if the cumulative tally could exceed 2^63 units;
+ * NM_ERR_DEVICE if a device check fired (the batch is still folded). */
+nm_status nm_dose_run(nm_dose* h, uint64_t n_decays, uint64_t seed);
+
+/* Eq. 1: dose rate D/N_evts * A(t_s) per voxel (Gy/s) into dose[V], and the
+ * batch standard deviation of that mean into sigma[V] (Gy/s); either may be
+ * NULL.  organ_dose[n_labels + 1]: Eq. 2 organ means (index = label; index 0
+ * is the mean outside all organs), may be NULL.  NM_ERR_STATE before any run. */
+nm_status nm_dose_get(nm_dose* h, float* dose, float* sigma, double* organ_dose);
+
+/* Per organ label 0..n_labels (arrays of n_labels + 1 doubles, any may be
+ * NULL): Eq. 2 mean dose rate (Gy/s), Eq. 3 RMS of the voxels' relative
+ * uncertainties (a voxel with zero dose counts as 1), batch standard deviation
+ * of the organ mean (Gy/s), and the organ's voxel count. */
+nm_status nm_dose_get_organs(nm_dose* h, double* mean, double* eps_rms, double* sigma_mean,
+                             int64_t* voxels);
+
+/* Exact cumulative tally, int64 energy units per voxel, into tally[V]. */
+nm_status nm_dose_get_tally(nm_dose* h, int64_t* tally);
+
+/* Counters and the launch shape in use. */
+nm_status nm_dose_counters(nm_dose* h, nm_counters* c);
+
+/* Forgets all histories and statistics (history ids restart at 0). */
+nm_status nm_dose_reset(nm_dose* h);
+
+/* Frees the handle and its device memory.  NULL is allowed. */
+void nm_dose_destroy(nm_dose* h);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* nm_last_error(void);
+
+/* ---- Checks of the device building blocks (used by the test suite) ------- */
+
+/* Philox4x32-10 (Salmon et al., SC'11) evaluated by the device code for n
+ * (counter, key) pairs: ctr[4n], key[2n] in, out[4n] out; host pointers. */
+nm_status nm_check_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out);
+
+/* n Klein-Nishina scattering cosines at energy e_mev drawn by the device's
+ * Kahn sampler with key (seed) and counters 0..n-1; cos_out[n] host. */
+nm_status nm_check_kahn(double e_mev, int64_t n, uint64_t seed, float* cos_out);
+
+/* The handle's alias table: n_active entries of (prob, voxel, alias voxel).
+ * Pass NULL arrays to query *n_active only.  Host pointers. */
+nm_status nm_dose_alias_table(nm_dose* h, int64_t* n_active, float* prob, int32_t* voxel,
+                              int32_t* alias_voxel);
+
+/* Decay sites of histories first..first+n-1 with the handle's source sampler:
+ * voxel[n], pos[3n] (cm), dir[3n] (first photon); host pointers. */
+nm_status nm_check_source(nm_dose* h, uint64_t first, int64_t n, uint64_t seed, int32_t* voxel,
+                          float* pos, float* dir);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NM_DOSE_H */

@@ -89,13 +89,22 @@ typedef struct {
   double photon_cut_mev;     // 0.010 (§2.1)
 } orc_materials;
 
+// Mass attenuation coefficients (cm^2/g) of material m at energy E: Compton
+// (electrons per gram N_A Z/A times sigma_KN), photoelectric, Rayleigh.
+void orc_mass_atten(const orc_materials* mt, int m, double e_mev, double* c, double* pe,
+                    double* r) {
+  *c = kAvogadro * mt->z_over_a[m] * orc_sigma_kn(e_mev);
+  *pe = mt->pe_coeff * std::pow(mt->zeff[m], mt->pe_exp) / (e_mev * e_mev * e_mev);
+  *r = mt->rayleigh ? mt->rayleigh_coeff * mt->zeff[m] * mt->zeff[m] / (e_mev * e_mev) : 0.0;
+}
+
 // Linear attenuation coefficients (1/cm) of material m at density rho and energy E.
 void orc_mu(const orc_materials* mt, int m, double rho, double e_mev, double* mu_c,
             double* mu_pe, double* mu_r) {
-  *mu_c = rho * kAvogadro * mt->z_over_a[m] * orc_sigma_kn(e_mev);
-  *mu_pe = rho * mt->pe_coeff * std::pow(mt->zeff[m], mt->pe_exp) / (e_mev * e_mev * e_mev);
-  *mu_r = mt->rayleigh ? rho * mt->rayleigh_coeff * mt->zeff[m] * mt->zeff[m] / (e_mev * e_mev)
-                       : 0.0;
+  orc_mass_atten(mt, m, e_mev, mu_c, mu_pe, mu_r);
+  *mu_c *= rho;
+  *mu_pe *= rho;
+  *mu_r *= rho;
 }
 
 // ---------------------------------------------------------------------------
@@ -361,6 +370,9 @@ int orc_run(const orc_problem* pr, int64_t* tally_sum, double* dose_rate, double
             double* organ_mean, double* organ_eps, double* organ_sigma, orc_counters* out_c) {
   const int64_t V = (int64_t)pr->nx * pr->ny * pr->nz;
   if (V <= 0 || pr->batches < 2 || pr->n_hist < (uint64_t)pr->batches) return 1;
+  if (pr->mat.n < 1 || pr->mat.n > 64) return 1;
+  for (int64_t v = 0; v < V; ++v)
+    if (pr->material[v] >= pr->mat.n || !(pr->density[v] > 0.0)) return 3;
   Grid g{pr->nx, pr->ny, pr->nz, {pr->dx, pr->dy, pr->dz}, pr->density, pr->material};
   const double L[3] = {pr->nx * pr->dx, pr->ny * pr->dy, pr->nz * pr->dz};
 
@@ -409,15 +421,20 @@ int orc_run(const orc_problem* pr, int64_t* tally_sum, double* dose_rate, double
     double e = pr->photon_mev;
     c.emitted += q_photon;
     for (;;) {
+      // The energy is fixed during a flight: mass attenuation per material once.
+      double mass_tot[64];
+      for (int m = 0; m < pr->mat.n; ++m) {
+        double a, b, cc;
+        orc_mass_atten(&pr->mat, m, e, &a, &b, &cc);
+        mass_tot[m] = a + b + cc;
+      }
       const double tau_star = -std::log(r.u());
       double tau = 0.0, t_hit = -1.0;
       int64_t v_hit = -1;
       ++c.flights;
       const bool escaped = traverse(g, p, d, [&](int64_t v, double t0, double t1) {
         ++c.crossings;
-        double mc, mp, mr;
-        orc_mu(&pr->mat, pr->material[v], pr->density[v], e, &mc, &mp, &mr);
-        const double m = mc + mp + mr;
+        const double m = pr->density[v] * mass_tot[pr->material[v]];
         const double seg = (t1 - t0) * m;
         if (m > 0.0 && tau + seg >= tau_star) {
           t_hit = t0 + (tau_star - tau) / m;

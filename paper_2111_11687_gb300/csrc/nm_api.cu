@@ -1,0 +1,622 @@
+// C ABI of libnmdose (include/nm_dose.h): argument checks, device memory,
+// the batch loop of nm_dose_run, and the read-out calls.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "nm_internal.cuh"
+
+using namespace nm;
+
+namespace {
+
+thread_local std::string g_err;
+
+nm_status fail(nm_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+nm_status cuda_fail(cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation)
+    return fail(NM_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+  return fail(NM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define NM_CUDA(call, what)                         \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Klein-Nishina total cross section per electron (cm^2), FP64, with ln(1 + 2k)
+// taken by log1p so that the low-energy end keeps its digits.
+double sigma_kn(double e_mev) {
+  const double k = e_mev / kElectronMassMeV;
+  const double a = 1.0 + 2.0 * k;
+  const double l = std::log1p(2.0 * k);
+  const double t1 = (1.0 + k) / (k * k) * (2.0 * (1.0 + k) / a - l / k);
+  const double t2 = l / (2.0 * k);
+  const double t3 = (1.0 + 3.0 * k) / (a * a);
+  return 2.0 * M_PI * kClassicalRadiusCm * kClassicalRadiusCm * (t1 + t2 - t3);
+}
+
+template <class T>
+cudaError_t dalloc(T** p, size_t n) {
+  return cudaMalloc((void**)p, n * sizeof(T) > 0 ? n * sizeof(T) : 1);
+}
+
+}  // namespace
+
+struct nm_dose {
+  int nx = 0, ny = 0, nz = 0;
+  float dx = 0, dy = 0, dz = 0;
+  int64_t V = 0;
+  nm_options opt{};
+  int n_mat = 0;
+  MaterialCoef mat[NM_MAX_MATERIALS]{};
+  int rayleigh = 0;
+  float cut = 0.01f;
+  float e0 = 0.511f;
+  int32_t q_e0 = 0, q_pos = 0;
+  float ln_e_lo = 0, inv_dln = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0, sms = 0;
+  // device memory
+  uint32_t* vox = nullptr;
+  float* density = nullptr;
+  uint8_t* labels = nullptr;
+  uint4* alias = nullptr;
+  int64_t n_active = 0;
+  ull* tb = nullptr;
+  ull* tsum = nullptr;
+  double* s2 = nullptr;
+  float* kn = nullptr;
+  ull* counters = nullptr;     // kCtrCount
+  ull* work = nullptr;
+  uint32_t* status = nullptr;
+  uint32_t* rho_max_bits = nullptr;
+  double* org_s1 = nullptr;
+  double* org_s2 = nullptr;
+  long long* organ_count = nullptr;
+  double* organ_partial = nullptr;
+  double* organ_out = nullptr;
+  float* out_dose = nullptr;
+  float* out_sigma = nullptr;
+  // host state
+  uint64_t hist_next = 0;
+  uint64_t n_batches = 0;
+  uint32_t status_seen = 0;
+  double transport_ms = 0, fold_ms = 0;
+  int block = 256, chunk = 256, warp_agg = 0, regroup = 0, grid = 0;
+  std::vector<cudaEvent_t> ev;
+
+  ~nm_dose() {
+    void* ptrs[] = {vox, density, labels, alias, tb, tsum, s2, kn, counters, work, status,
+                    rho_max_bits, org_s1, org_s2, organ_count, organ_partial, organ_out,
+                    out_dose, out_sigma};
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+
+  TransportParams params(uint64_t first, uint64_t n, uint64_t seed) const {
+    TransportParams p;
+    memset(&p, 0, sizeof p);
+    p.vox = vox;
+    p.alias = alias;
+    p.tally = tb;
+    p.counters = counters;
+    p.work = work;
+    p.status = status;
+    p.kn = kn;
+    p.nx = nx; p.ny = ny; p.nz = nz;
+    p.fnx = (float)nx; p.fny = (float)ny; p.fnz = (float)nz;
+    p.inv_dx = 1.0f / dx; p.inv_dy = 1.0f / dy; p.inv_dz = 1.0f / dz;
+    p.n_active = (uint64_t)n_active;
+    p.hist_begin = first;
+    p.n_hist = n;
+    p.key0 = (uint32_t)seed;
+    p.key1 = (uint32_t)(seed >> 32);
+    p.source_mode = opt.source_mode;
+    p.px = opt.point[0] / dx; p.py = opt.point[1] / dy; p.pz = opt.point[2] / dz;
+    p.e0 = e0;
+    p.q_e0 = q_e0;
+    p.q_positron = q_pos;
+    p.cut = cut;
+    p.n_mat = n_mat;
+    for (int m = 0; m < NM_MAX_MATERIALS; ++m) p.mat[m] = mat[m];
+    p.ln_e_lo = ln_e_lo;
+    p.inv_dln_e = inv_dln;
+    p.chunk = chunk;
+    p.max_steps = opt.max_steps;
+    return p;
+  }
+
+  double gy_per_unit_vol() const {
+    // one tally unit = 2^-6 eV; mass = rho [g/cm^3] * volume [cm^3] * 1e-3 kg/g
+    return kJoulePerEv / 64.0 / (1e-3 * (double)dx * (double)dy * (double)dz);
+  }
+  uint64_t units_per_history() const {
+    return opt.source_mode == NM_SOURCE_DECAY ? 2ull * (uint64_t)q_e0 + (uint64_t)q_pos
+                                              : (uint64_t)q_e0;
+  }
+};
+
+extern "C" {
+
+void nm_options_default(nm_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof *o);
+  o->source_mode = NM_SOURCE_DECAY;
+  o->photon_mev = 0.511;
+  o->positron_mev = 0.25;
+  o->batches = 10;
+  o->activity_bq = 8.0e-3 * 3.7e10 * std::pow(2.0, -60.0 / 109.77);
+  o->n_labels = 0;
+  o->block_threads = 0;
+  o->chunk = 0;
+  o->warp_aggregate = -1;
+  o->regroup = -1;
+  o->max_steps = 100000;
+  o->stream = nullptr;
+}
+
+const char* nm_last_error(void) { return g_err.c_str(); }
+
+nm_status nm_ct_to_phantom(const int16_t* hu, int64_t n, float* density, uint8_t* material,
+                           void* stream) {
+  if (n < 0 || (n > 0 && (!hu || !density || !material)))
+    return fail(NM_ERR_ARG, "nm_ct_to_phantom: bad arguments");
+  if (n == 0) return NM_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool din = is_device_ptr(hu), dd = is_device_ptr(density), dm = is_device_ptr(material);
+  int16_t* h = nullptr;
+  float* d = nullptr;
+  uint8_t* m = nullptr;
+  nm_status st = NM_OK;
+  cudaError_t e = cudaSuccess;
+  if (!din) e = dalloc(&h, n);
+  if (!e && !dd) e = dalloc(&d, n);
+  if (!e && !dm) e = dalloc(&m, n);
+  if (!e && !din) e = cudaMemcpyAsync(h, hu, n * sizeof(int16_t), cudaMemcpyHostToDevice, s);
+  if (!e) e = launch_ct_to_phantom(din ? hu : h, n, dd ? density : d, dm ? material : m, s);
+  if (!e && !dd) e = cudaMemcpyAsync(density, d, n * sizeof(float), cudaMemcpyDeviceToHost, s);
+  if (!e && !dm) e = cudaMemcpyAsync(material, m, n, cudaMemcpyDeviceToHost, s);
+  if (!e) e = cudaStreamSynchronize(s);
+  if (e) st = cuda_fail(e, "nm_ct_to_phantom");
+  if (h) cudaFree(h);
+  if (d) cudaFree(d);
+  if (m) cudaFree(m);
+  return st;
+}
+
+static nm_status choose_shape(nm_dose* h) {
+  const nm_options& o = h->opt;
+  h->block = o.block_threads > 0 ? o.block_threads : 256;
+  if (h->block % 32 || h->block > 1024) return fail(NM_ERR_ARG, "block_threads must be a multiple of 32, <= 1024");
+  h->chunk = o.chunk > 0 ? o.chunk : 256;
+  if (h->chunk < 32) return fail(NM_ERR_ARG, "chunk must be >= 32");
+  // A point source concentrates deposits near the source, where lanes of a
+  // warp often hit the same voxel; a spread-out source rarely does.
+  h->warp_agg = o.warp_aggregate >= 0 ? (o.warp_aggregate != 0) : (o.source_mode == NM_SOURCE_POINT);
+  h->regroup = o.regroup >= 0 ? (o.regroup != 0) : 0;
+  const int per_sm = transport_max_blocks_per_sm(h->block, h->warp_agg, h->rayleigh, h->regroup);
+  if (per_sm <= 0) return fail(NM_ERR_ARG, "transport kernel cannot launch with %d threads", h->block);
+  h->grid = per_sm * h->sms;
+  return NM_OK;
+}
+
+nm_status nm_dose_create(nm_dose** out, const nm_grid* g, const nm_materials* mt,
+                         const float* activity, const uint8_t* labels, const nm_options* opts) {
+  if (!out) return fail(NM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!g || !mt) return fail(NM_ERR_ARG, "grid or materials is NULL");
+  if (g->nx <= 0 || g->ny <= 0 || g->nz <= 0) return fail(NM_ERR_ARG, "grid dimensions must be > 0");
+  const int64_t V = (int64_t)g->nx * g->ny * g->nz;
+  if (V >= (int64_t)1 << 31) return fail(NM_ERR_ARG, "grid has %lld voxels; the limit is 2^31 - 1", (long long)V);
+  if (!(g->dx > 0 && g->dy > 0 && g->dz > 0) || !std::isfinite(g->dx) || !std::isfinite(g->dy) ||
+      !std::isfinite(g->dz))
+    return fail(NM_ERR_ARG, "voxel sizes must be finite and > 0");
+  if (!g->density || !g->material) return fail(NM_ERR_ARG, "density or material is NULL");
+  if (mt->n < 1 || mt->n > NM_MAX_MATERIALS || !mt->z_over_a || !mt->zeff)
+    return fail(NM_ERR_ARG, "materials: need 1..%d materials with z_over_a and zeff", NM_MAX_MATERIALS);
+  nm_options o;
+  if (opts) o = *opts; else nm_options_default(&o);
+  if (o.source_mode != NM_SOURCE_DECAY && o.source_mode != NM_SOURCE_POINT)
+    return fail(NM_ERR_ARG, "unknown source_mode %d", o.source_mode);
+  if (o.source_mode == NM_SOURCE_DECAY && !activity)
+    return fail(NM_ERR_ARG, "decay mode needs an activity map");
+  if (o.batches < 2) return fail(NM_ERR_ARG, "batches must be >= 2");
+  if (o.n_labels < 0 || o.n_labels > NM_MAX_LABELS) return fail(NM_ERR_ARG, "n_labels must be 0..%d", NM_MAX_LABELS);
+  if (!(o.photon_mev > mt->photon_cut_mev) || !(mt->photon_cut_mev > 0) || !(o.photon_mev <= 1.0))
+    return fail(NM_ERR_ARG, "need 0 < photon cutoff < photon energy <= 1 MeV");
+  if (!(o.positron_mev >= 0) || o.positron_mev > 1.0) return fail(NM_ERR_ARG, "positron energy must be in [0, 1] MeV");
+  if (!(o.activity_bq >= 0) || !std::isfinite(o.activity_bq)) return fail(NM_ERR_ARG, "activity_bq must be finite and >= 0");
+  if (o.max_steps <= 0) return fail(NM_ERR_ARG, "max_steps must be > 0");
+  for (int m = 0; m < mt->n; ++m)
+    if (!(mt->z_over_a[m] >= 0) || !(mt->zeff[m] >= 0)) return fail(NM_ERR_ARG, "material %d: negative constants", m);
+  if (o.source_mode == NM_SOURCE_POINT) {
+    const float L[3] = {g->nx * g->dx, g->ny * g->dy, g->nz * g->dz};
+    for (int a = 0; a < 3; ++a)
+      if (!(o.point[a] >= 0.0f && o.point[a] < L[a])) return fail(NM_ERR_ARG, "point source outside the grid");
+  }
+
+  nm_dose* h = new nm_dose();
+  h->nx = g->nx; h->ny = g->ny; h->nz = g->nz;
+  h->dx = g->dx; h->dy = g->dy; h->dz = g->dz;
+  h->V = V;
+  h->opt = o;
+  h->stream = (cudaStream_t)o.stream;
+  h->n_mat = mt->n;
+  h->rayleigh = mt->rayleigh != 0;
+  h->cut = (float)mt->photon_cut_mev;
+  h->e0 = (float)o.photon_mev;
+  h->q_e0 = q_units(h->e0);
+  h->q_pos = o.source_mode == NM_SOURCE_DECAY ? q_units((float)o.positron_mev) : 0;
+  auto bail = [&](nm_status st) { delete h; return st; };
+
+  cudaError_t e;
+  if ((e = cudaGetDevice(&h->device))) return bail(cuda_fail(e, "cudaGetDevice"));
+  if ((e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device)))
+    return bail(cuda_fail(e, "cudaDeviceGetAttribute"));
+  cudaStream_t s = h->stream;
+
+  // Physics tables: N_A sigma_KN(E) on a log-energy grid (FP64 -> FP32).
+  const double e_lo = 0.5 * mt->photon_cut_mev, e_hi = 1.05 * o.photon_mev;
+  const double dln = (std::log(e_hi) - std::log(e_lo)) / (kKnTable - 1);
+  h->ln_e_lo = (float)std::log(e_lo);
+  h->inv_dln = (float)(1.0 / dln);
+  std::vector<float> kn(kKnTable);
+  for (int i = 0; i < kKnTable; ++i)
+    kn[i] = (float)(kAvogadro * sigma_kn(std::exp(std::log(e_lo) + i * dln)));
+  for (int m = 0; m < mt->n; ++m) {
+    h->mat[m].za = (float)mt->z_over_a[m];
+    h->mat[m].zp = (float)(mt->pe_coeff * std::pow(mt->zeff[m], mt->pe_exp));
+    h->mat[m].zr = h->rayleigh ? (float)(mt->rayleigh_coeff * mt->zeff[m] * mt->zeff[m]) : 0.0f;
+  }
+
+  if ((e = dalloc(&h->vox, V)) || (e = dalloc(&h->density, V)) || (e = dalloc(&h->tb, V)) ||
+      (e = dalloc(&h->tsum, V)) || (e = dalloc(&h->s2, V)) || (e = dalloc(&h->kn, kKnTable)) ||
+      (e = dalloc(&h->counters, kCtrCount)) || (e = dalloc(&h->work, 1)) ||
+      (e = dalloc(&h->status, 1)) || (e = dalloc(&h->rho_max_bits, NM_MAX_MATERIALS)) ||
+      (e = dalloc(&h->org_s1, kLabelSlots)) || (e = dalloc(&h->org_s2, kLabelSlots)) ||
+      (e = dalloc(&h->organ_count, kLabelSlots)) ||
+      (e = dalloc(&h->organ_partial, (size_t)fold_blocks(V) * 2 * kLabelSlots)) ||
+      (e = dalloc(&h->organ_out, 4 * kLabelSlots)))
+    return bail(cuda_fail(e, "device allocation"));
+  if (labels && (e = dalloc(&h->labels, V))) return bail(cuda_fail(e, "device allocation"));
+
+  uint8_t* mat_dev = nullptr;
+  if ((e = dalloc(&mat_dev, V))) return bail(cuda_fail(e, "device allocation"));
+  e = cudaMemcpyAsync(h->density, g->density, V * sizeof(float), cudaMemcpyDefault, s);
+  if (!e) e = cudaMemcpyAsync(mat_dev, g->material, V, cudaMemcpyDefault, s);
+  if (!e && labels) e = cudaMemcpyAsync(h->labels, labels, V, cudaMemcpyDefault, s);
+  if (!e) e = cudaMemcpyAsync(h->kn, kn.data(), kKnTable * sizeof(float), cudaMemcpyHostToDevice, s);
+  if (!e) e = cudaMemsetAsync(h->status, 0, sizeof(uint32_t), s);
+  if (!e) e = cudaMemsetAsync(h->rho_max_bits, 0, NM_MAX_MATERIALS * sizeof(uint32_t), s);
+  if (!e) e = launch_pack_voxels(h->density, mat_dev, V, h->n_mat, h->vox, h->rho_max_bits, h->status, s);
+  uint32_t rho_bits[NM_MAX_MATERIALS] = {0};
+  uint32_t st = 0;
+  if (!e) e = cudaMemcpyAsync(rho_bits, h->rho_max_bits, sizeof rho_bits, cudaMemcpyDeviceToHost, s);
+  if (!e) e = cudaMemcpyAsync(&st, h->status, 4, cudaMemcpyDeviceToHost, s);
+  if (!e) e = cudaStreamSynchronize(s);
+  cudaFree(mat_dev);
+  if (e) return bail(cuda_fail(e, "nm_dose_create: upload"));
+  if (st & NM_DEV_BAD_VOXEL)
+    return bail(fail(NM_ERR_ARG, "density must be finite and > 0 and material < %d in every voxel", h->n_mat));
+  if (labels) {
+    // labels must be <= n_labels
+    std::vector<uint8_t> lab_host;
+    const uint8_t* lp = labels;
+    if (is_device_ptr(labels)) {
+      lab_host.resize(V);
+      if ((e = cudaMemcpy(lab_host.data(), labels, V, cudaMemcpyDeviceToHost))) return bail(cuda_fail(e, "labels"));
+      lp = lab_host.data();
+    }
+    for (int64_t i = 0; i < V; ++i)
+      if (lp[i] > o.n_labels) return bail(fail(NM_ERR_ARG, "label %d at voxel %lld exceeds n_labels", lp[i], (long long)i));
+  }
+  for (int m = 0; m < NM_MAX_MATERIALS; ++m) {
+    float r;
+    memcpy(&r, &rho_bits[m], 4);
+    h->mat[m].rho_max = m < h->n_mat ? r : 0.0f;
+  }
+
+  // Decay sampler: alias table over the active voxels, FP64 on the device.
+  if (o.source_mode == NM_SOURCE_DECAY) {
+    float* act = nullptr;
+    void* scratch = nullptr;
+    if ((e = dalloc(&act, V)) || (e = cudaMalloc(&scratch, AliasScratch::bytes(V)))) {
+      if (act) cudaFree(act);
+      return bail(cuda_fail(e, "alias scratch"));
+    }
+    e = cudaMemcpyAsync(act, activity, V * sizeof(float), cudaMemcpyDefault, s);
+    if (!e) e = dalloc(&h->alias, V);
+    if (!e) e = build_alias_table(act, V, AliasScratch{scratch}, h->alias, &h->n_active, h->status, s);
+    if (!e) e = cudaMemcpyAsync(&st, h->status, 4, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    cudaFree(act);
+    cudaFree(scratch);
+    if (e) return bail(cuda_fail(e, "alias table"));
+    if (st & NM_DEV_BAD_ACTIVITY) return bail(fail(NM_ERR_ARG, "activity must be finite and >= 0"));
+    if (h->n_active == 0) return bail(fail(NM_ERR_ARG, "activity map sums to zero"));
+  }
+
+  e = cudaMemsetAsync(h->tb, 0, V * sizeof(ull), s);
+  if (!e) e = cudaMemsetAsync(h->tsum, 0, V * sizeof(ull), s);
+  if (!e) e = cudaMemsetAsync(h->s2, 0, V * sizeof(double), s);
+  if (!e) e = cudaMemsetAsync(h->counters, 0, kCtrCount * sizeof(ull), s);
+  if (!e) e = cudaMemsetAsync(h->org_s1, 0, kLabelSlots * sizeof(double), s);
+  if (!e) e = cudaMemsetAsync(h->org_s2, 0, kLabelSlots * sizeof(double), s);
+  if (!e) e = cudaMemsetAsync(h->organ_count, 0, kLabelSlots * sizeof(long long), s);
+  if (!e && h->labels) e = launch_label_count(h->labels, V, h->organ_count, s);
+  if (!e) e = cudaStreamSynchronize(s);
+  if (e) return bail(cuda_fail(e, "nm_dose_create: init"));
+  nm_status cs = choose_shape(h);
+  if (cs != NM_OK) return bail(cs);
+  *out = h;
+  return NM_OK;
+}
+
+nm_status nm_dose_run(nm_dose* h, uint64_t n, uint64_t seed) {
+  if (!h) return fail(NM_ERR_ARG, "handle is NULL");
+  if (n == 0) return NM_OK;
+  const uint64_t per = h->units_per_history();
+  const uint64_t lim = (uint64_t)INT64_MAX / (per ? per : 1);
+  if (h->hist_next > lim || n > lim - h->hist_next)
+    return fail(NM_ERR_OVERFLOW, "%llu more histories could overflow the int64 tally",
+                (unsigned long long)n);
+  if (h->hist_next + n < h->hist_next || h->hist_next + n > (1ull << 62))
+    return fail(NM_ERR_OVERFLOW, "history ids exhausted");
+  const int B = (uint64_t)h->opt.batches < n ? h->opt.batches : (int)n;
+  cudaStream_t s = h->stream;
+  while ((int)h->ev.size() < 4 * B) {
+    cudaEvent_t ev;
+    NM_CUDA(cudaEventCreate(&ev), "cudaEventCreate");
+    h->ev.push_back(ev);
+  }
+  FoldParams fp;
+  fp.tb = h->tb; fp.tsum = h->tsum; fp.s2 = h->s2; fp.density = h->density;
+  fp.labels = h->labels; fp.V = h->V; fp.gy_per_unit_vol = h->gy_per_unit_vol();
+  fp.organ_partial = h->organ_partial; fp.org_s1 = h->org_s1; fp.org_s2 = h->org_s2;
+  fp.deposited = h->counters + kCtrDepositedUnits;
+  for (int b = 0; b < B; ++b) {
+    const uint64_t nb = n / B + ((uint64_t)b < n % B ? 1 : 0);
+    const TransportParams p = h->params(h->hist_next, nb, seed);
+    NM_CUDA(cudaMemsetAsync(h->work, 0, sizeof(ull), s), "cudaMemsetAsync");
+    NM_CUDA(cudaEventRecord(h->ev[4 * b + 0], s), "cudaEventRecord");
+    NM_CUDA(launch_transport(p, h->grid, h->block, h->warp_agg, h->rayleigh, h->regroup, s),
+            "transport launch");
+    NM_CUDA(cudaEventRecord(h->ev[4 * b + 1], s), "cudaEventRecord");
+    fp.n_b = (double)nb;
+    NM_CUDA(cudaEventRecord(h->ev[4 * b + 2], s), "cudaEventRecord");
+    NM_CUDA(launch_fold(fp, s), "fold launch");
+    NM_CUDA(cudaEventRecord(h->ev[4 * b + 3], s), "cudaEventRecord");
+    h->hist_next += nb;
+    h->n_batches += 1;
+  }
+  uint32_t st = 0;
+  NM_CUDA(cudaMemcpyAsync(&st, h->status, 4, cudaMemcpyDeviceToHost, s), "status read");
+  NM_CUDA(cudaStreamSynchronize(s), "nm_dose_run");
+  for (int b = 0; b < B; ++b) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, h->ev[4 * b], h->ev[4 * b + 1]) == cudaSuccess) h->transport_ms += ms;
+    if (cudaEventElapsedTime(&ms, h->ev[4 * b + 2], h->ev[4 * b + 3]) == cudaSuccess) h->fold_ms += ms;
+  }
+  h->status_seen |= st;
+  if (st) {
+    NM_CUDA(cudaMemsetAsync(h->status, 0, 4, s), "status reset");
+    return fail(NM_ERR_DEVICE, "device check fired (flags 0x%x: %s%s)", st,
+                (st & NM_DEV_STEP_LIMIT) ? "photon step limit " : "",
+                (st & NM_DEV_KAHN_LIMIT) ? "Kahn trial limit" : "");
+  }
+  return NM_OK;
+}
+
+static nm_status finalize(nm_dose* h, float* dose, float* sigma) {
+  if (h->hist_next == 0) return fail(NM_ERR_STATE, "no histories simulated yet");
+  if (h->n_batches < 2) return fail(NM_ERR_STATE, "need at least 2 batches for the uncertainty");
+  cudaStream_t s = h->stream;
+  FinalizeParams p;
+  p.tsum = h->tsum; p.s2 = h->s2; p.density = h->density; p.labels = h->labels; p.V = h->V;
+  p.n_total = (double)h->hist_next;
+  p.n_batches = (double)h->n_batches;
+  p.gy_per_unit_vol = h->gy_per_unit_vol();
+  p.activity_bq = h->opt.activity_bq;
+  p.dose = dose;
+  p.sigma = sigma;
+  p.organ_partial = h->organ_partial;
+  p.org_s1 = h->org_s1; p.org_s2 = h->org_s2;
+  p.organ_count = h->organ_count;
+  p.organ_out = h->organ_out;
+  NM_CUDA(launch_finalize(p, s), "finalize launch");
+  return NM_OK;
+}
+
+nm_status nm_dose_get(nm_dose* h, float* dose, float* sigma, double* organ_dose) {
+  if (!h) return fail(NM_ERR_ARG, "handle is NULL");
+  cudaStream_t s = h->stream;
+  const bool dd = is_device_ptr(dose), ds = is_device_ptr(sigma);
+  if ((dose && !dd) || (sigma && !ds)) {
+    if (!h->out_dose) NM_CUDA(dalloc(&h->out_dose, h->V), "output buffer");
+    if (!h->out_sigma) NM_CUDA(dalloc(&h->out_sigma, h->V), "output buffer");
+  }
+  float* d_out = dose ? (dd ? dose : h->out_dose) : nullptr;
+  float* s_out = sigma ? (ds ? sigma : h->out_sigma) : nullptr;
+  nm_status st = finalize(h, d_out, s_out);
+  if (st != NM_OK) return st;
+  if (dose && !dd) NM_CUDA(cudaMemcpyAsync(dose, d_out, h->V * sizeof(float), cudaMemcpyDeviceToHost, s), "dose copy");
+  if (sigma && !ds) NM_CUDA(cudaMemcpyAsync(sigma, s_out, h->V * sizeof(float), cudaMemcpyDeviceToHost, s), "sigma copy");
+  if (organ_dose)
+    NM_CUDA(cudaMemcpyAsync(organ_dose, h->organ_out, (h->opt.n_labels + 1) * sizeof(double),
+                            cudaMemcpyDefault, s), "organ copy");
+  NM_CUDA(cudaStreamSynchronize(s), "nm_dose_get");
+  return NM_OK;
+}
+
+nm_status nm_dose_get_organs(nm_dose* h, double* mean, double* eps_rms, double* sigma_mean,
+                             int64_t* voxels) {
+  if (!h) return fail(NM_ERR_ARG, "handle is NULL");
+  nm_status st = finalize(h, nullptr, nullptr);
+  if (st != NM_OK) return st;
+  std::vector<double> out(4 * kLabelSlots);
+  NM_CUDA(cudaMemcpyAsync(out.data(), h->organ_out, out.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "organ copy");
+  NM_CUDA(cudaStreamSynchronize(h->stream), "nm_dose_get_organs");
+  const int n = h->opt.n_labels + 1;
+  for (int l = 0; l < n; ++l) {
+    if (mean) mean[l] = out[l];
+    if (eps_rms) eps_rms[l] = out[kLabelSlots + l];
+    if (sigma_mean) sigma_mean[l] = out[2 * kLabelSlots + l];
+    if (voxels) voxels[l] = (int64_t)out[3 * kLabelSlots + l];
+  }
+  return NM_OK;
+}
+
+nm_status nm_dose_get_tally(nm_dose* h, int64_t* tally) {
+  if (!h || !tally) return fail(NM_ERR_ARG, "bad arguments");
+  NM_CUDA(cudaMemcpyAsync(tally, h->tsum, h->V * sizeof(int64_t), cudaMemcpyDefault, h->stream), "tally copy");
+  NM_CUDA(cudaStreamSynchronize(h->stream), "nm_dose_get_tally");
+  return NM_OK;
+}
+
+nm_status nm_dose_counters(nm_dose* h, nm_counters* c) {
+  if (!h || !c) return fail(NM_ERR_ARG, "bad arguments");
+  ull v[kCtrCount];
+  NM_CUDA(cudaMemcpyAsync(v, h->counters, sizeof v, cudaMemcpyDeviceToHost, h->stream), "counters");
+  NM_CUDA(cudaStreamSynchronize(h->stream), "nm_dose_counters");
+  memset(c, 0, sizeof *c);
+  c->histories = h->hist_next;
+  c->batches = h->n_batches;
+  c->emitted = (int64_t)(h->hist_next * h->units_per_history());
+  c->deposited = (int64_t)v[kCtrDepositedUnits];
+  c->escaped = (int64_t)v[kCtrEscapedUnits];
+  c->killed = (int64_t)v[kCtrKilledUnits];
+  c->steps = v[kCtrSteps];
+  c->compton = v[kCtrCompton];
+  c->photo = v[kCtrPhoto];
+  c->rayleigh = v[kCtrRayleigh];
+  c->cutoff = v[kCtrCutoff];
+  c->escapes = v[kCtrEscapes];
+  c->transport_ms = h->transport_ms;
+  c->fold_ms = h->fold_ms;
+  c->device_status = h->status_seen;
+  c->block_threads = h->block;
+  c->chunk = h->chunk;
+  c->warp_aggregate = h->warp_agg;
+  c->regroup = h->regroup;
+  c->grid_blocks = h->grid;
+  return NM_OK;
+}
+
+nm_status nm_dose_reset(nm_dose* h) {
+  if (!h) return fail(NM_ERR_ARG, "handle is NULL");
+  cudaStream_t s = h->stream;
+  NM_CUDA(cudaMemsetAsync(h->tb, 0, h->V * sizeof(ull), s), "reset");
+  NM_CUDA(cudaMemsetAsync(h->tsum, 0, h->V * sizeof(ull), s), "reset");
+  NM_CUDA(cudaMemsetAsync(h->s2, 0, h->V * sizeof(double), s), "reset");
+  NM_CUDA(cudaMemsetAsync(h->counters, 0, kCtrCount * sizeof(ull), s), "reset");
+  NM_CUDA(cudaMemsetAsync(h->org_s1, 0, kLabelSlots * sizeof(double), s), "reset");
+  NM_CUDA(cudaMemsetAsync(h->org_s2, 0, kLabelSlots * sizeof(double), s), "reset");
+  NM_CUDA(cudaStreamSynchronize(s), "reset");
+  h->hist_next = 0;
+  h->n_batches = 0;
+  h->status_seen = 0;
+  h->transport_ms = h->fold_ms = 0;
+  return NM_OK;
+}
+
+void nm_dose_destroy(nm_dose* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  delete h;
+}
+
+nm_status nm_check_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out) {
+  if (n < 0 || (n > 0 && (!ctr || !key || !out))) return fail(NM_ERR_ARG, "bad arguments");
+  if (n == 0) return NM_OK;
+  uint4 *dc = nullptr, *dout = nullptr;
+  uint2* dk = nullptr;
+  cudaError_t e = dalloc(&dc, n);
+  if (!e) e = dalloc(&dk, n);
+  if (!e) e = dalloc(&dout, n);
+  if (!e) e = cudaMemcpy(dc, ctr, n * 16, cudaMemcpyHostToDevice);
+  if (!e) e = cudaMemcpy(dk, key, n * 8, cudaMemcpyHostToDevice);
+  if (!e) e = launch_check_philox(dc, dk, n, dout, 0);
+  if (!e) e = cudaMemcpy(out, dout, n * 16, cudaMemcpyDeviceToHost);
+  cudaFree(dc); cudaFree(dk); cudaFree(dout);
+  return e ? cuda_fail(e, "nm_check_philox") : NM_OK;
+}
+
+nm_status nm_check_kahn(double e_mev, int64_t n, uint64_t seed, float* cos_out) {
+  if (n < 0 || (n > 0 && !cos_out) || !(e_mev > 0)) return fail(NM_ERR_ARG, "bad arguments");
+  if (n == 0) return NM_OK;
+  float* d = nullptr;
+  uint32_t* st = nullptr;
+  cudaError_t e = dalloc(&d, n);
+  if (!e) e = dalloc(&st, 1);
+  if (!e) e = cudaMemset(st, 0, 4);
+  if (!e) e = launch_check_kahn((float)e_mev, n, (uint32_t)seed, (uint32_t)(seed >> 32), d, st, 0);
+  if (!e) e = cudaMemcpy(cos_out, d, n * 4, cudaMemcpyDeviceToHost);
+  uint32_t flags = 0;
+  if (!e) e = cudaMemcpy(&flags, st, 4, cudaMemcpyDeviceToHost);
+  cudaFree(d); cudaFree(st);
+  if (e) return cuda_fail(e, "nm_check_kahn");
+  if (flags) return fail(NM_ERR_DEVICE, "Kahn trial limit hit");
+  return NM_OK;
+}
+
+nm_status nm_dose_alias_table(nm_dose* h, int64_t* n_active, float* prob, int32_t* voxel,
+                              int32_t* alias_voxel) {
+  if (!h || !n_active) return fail(NM_ERR_ARG, "bad arguments");
+  *n_active = h->n_active;
+  if (!prob && !voxel && !alias_voxel) return NM_OK;
+  if (h->n_active == 0) return NM_OK;
+  std::vector<uint4> t(h->n_active);
+  NM_CUDA(cudaMemcpy(t.data(), h->alias, h->n_active * sizeof(uint4), cudaMemcpyDeviceToHost), "alias copy");
+  for (int64_t i = 0; i < h->n_active; ++i) {
+    if (prob) memcpy(&prob[i], &t[i].x, 4);
+    if (voxel) voxel[i] = (int32_t)t[i].y;
+    if (alias_voxel) alias_voxel[i] = (int32_t)t[i].z;
+  }
+  return NM_OK;
+}
+
+nm_status nm_check_source(nm_dose* h, uint64_t first, int64_t n, uint64_t seed, int32_t* voxel,
+                          float* pos, float* dir) {
+  if (!h || n < 0 || (n > 0 && (!voxel || !pos || !dir))) return fail(NM_ERR_ARG, "bad arguments");
+  if (n == 0) return NM_OK;
+  int32_t* dv = nullptr;
+  float *dp = nullptr, *dd = nullptr;
+  cudaError_t e = dalloc(&dv, n);
+  if (!e) e = dalloc(&dp, 3 * n);
+  if (!e) e = dalloc(&dd, 3 * n);
+  const TransportParams p = h->params(first, (uint64_t)n, seed);
+  if (!e) e = launch_check_source(p, first, n, dv, dp, dd, h->stream);
+  if (!e) e = cudaMemcpyAsync(voxel, dv, n * 4, cudaMemcpyDeviceToHost, h->stream);
+  if (!e) e = cudaMemcpyAsync(pos, dp, 3 * n * 4, cudaMemcpyDeviceToHost, h->stream);
+  if (!e) e = cudaMemcpyAsync(dir, dd, 3 * n * 4, cudaMemcpyDeviceToHost, h->stream);
+  if (!e) e = cudaStreamSynchronize(h->stream);
+  cudaFree(dv); cudaFree(dp); cudaFree(dd);
+  return e ? cuda_fail(e, "nm_check_source") : NM_OK;
+}
+
+}  // extern "C"

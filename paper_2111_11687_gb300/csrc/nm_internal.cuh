@@ -1,0 +1,166 @@
+// Internal declarations shared by the CUDA translation units of libnmdose.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nm_dose.h"
+
+namespace nm {
+
+typedef unsigned long long ull;
+
+constexpr float kInvElectronMassMeV = 1.0f / 0.51099895f;  // 1 / m_e c^2
+constexpr double kElectronMassMeV = 0.51099895;
+constexpr double kClassicalRadiusCm = 2.8179403262e-13;
+constexpr double kAvogadro = 6.02214076e23;
+constexpr double kJoulePerEv = 1.602176634e-19;
+constexpr float kTwoPi = 6.283185307179586f;
+constexpr int kKnTable = 1024;      // log-energy nodes of the Klein-Nishina table
+constexpr int kFoldThreads = 128;   // fold / finalize CTA size
+constexpr int kFoldTile = 8192;     // voxels per fold CTA
+constexpr int kLabelSlots = NM_MAX_LABELS + 1;
+
+// Fixed-point energy: round-to-nearest-even of the FP32 product E * 6.4e7.
+// Deposits are differences of these values, so energy bookkeeping is exact
+// whatever the rounding.
+__host__ __device__ inline int32_t q_units(float e_mev) {
+#ifdef __CUDA_ARCH__
+  return __float2int_rn(__fmul_rn(e_mev, 64.0e6f));
+#else
+  const float p = e_mev * 64.0e6f;
+  return (int32_t)__builtin_rintf(p);
+#endif
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32
+// -> 64-bit multiplies with the key bumped by the Weyl constants between rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Uniform float in the open interval (0, 1) from 23 random bits.
+__device__ __forceinline__ float u01(uint32_t r) { return ((float)(r >> 9) + 0.5f) * 0x1p-23f; }
+
+// Random-stream ids inside one history.
+enum : uint32_t { kStreamSource = 0, kStreamPhotonA = 1, kStreamPhotonB = 2 };
+
+struct MaterialCoef {
+  float za;       // (Z/A) * N_A * sigma-table scale: mu_c/rho = za * kn(E)
+  float zp;       // pe_coeff * Zeff^pe_exp:            mu_pe/rho = zp / E^3
+  float zr;       // rayleigh_coeff * Zeff^2:           mu_R/rho = zr / E^2
+  float rho_max;  // largest density of this material in the grid
+};
+
+struct TransportParams {
+  const uint32_t* vox;        // packed voxel: density bits with the low 3 bits = material
+  const uint4* alias;         // {prob bits, voxel, alias voxel, 0}
+  ull* tally;                 // batch tally, units
+  ull* counters;              // device counters (see CounterSlot)
+  ull* work;                  // histories handed out in this launch
+  uint32_t* status;           // NM_DEV_* flags
+  const float* kn;            // kKnTable nodes of N_A * sigma_KN(E)
+  int nx, ny, nz;
+  float fnx, fny, fnz;        // grid size as float (voxel units)
+  float inv_dx, inv_dy, inv_dz;
+  uint64_t n_active;
+  uint64_t hist_begin;        // first global history id of this launch
+  uint64_t n_hist;            // histories in this launch
+  uint32_t key0, key1;        // Philox key = seed
+  int source_mode;
+  float px, py, pz;           // point source, voxel units
+  float e0;                   // photon energy, MeV
+  int32_t q_e0;               // q_units(e0)
+  int32_t q_positron;         // q_units(positron energy), 0 in point mode
+  float cut;                  // photon cutoff, MeV
+  int n_mat;
+  MaterialCoef mat[NM_MAX_MATERIALS];
+  float ln_e_lo, inv_dln_e;   // table grid: ln E = ln_e_lo + i / inv_dln_e
+  int chunk;                  // histories per warp work grab
+  int max_steps;
+};
+
+enum CounterSlot {
+  kCtrSteps = 0, kCtrCompton, kCtrPhoto, kCtrRayleigh, kCtrCutoff, kCtrEscapes,
+  kCtrEscapedUnits, kCtrKilledUnits, kCtrDepositedUnits, kCtrCount
+};
+
+// ---- launchers (host side), one translation unit each ---------------------
+cudaError_t launch_transport(const TransportParams& p, int grid, int block, bool warp_agg,
+                             bool rayleigh, bool regroup, cudaStream_t s);
+int transport_max_blocks_per_sm(int block, bool warp_agg, bool rayleigh, bool regroup);
+cudaError_t launch_check_philox(const uint4* ctr, const uint2* key, int64_t n, uint4* out,
+                                cudaStream_t s);
+cudaError_t launch_check_kahn(float e, int64_t n, uint32_t k0, uint32_t k1, float* out,
+                              uint32_t* status, cudaStream_t s);
+cudaError_t launch_check_source(const TransportParams& p, uint64_t first, int64_t n, int32_t* voxel,
+                                float* pos, float* dir, cudaStream_t s);
+
+// HU -> density/material (§2.1).
+cudaError_t launch_ct_to_phantom(const int16_t* hu, int64_t n, float* density, uint8_t* material,
+                                 cudaStream_t s);
+
+// Voxel packing and validation; per-material maximum density (as float bits).
+cudaError_t launch_pack_voxels(const float* density, const uint8_t* material, int64_t V, int n_mat,
+                               uint32_t* vox, uint32_t* rho_max_bits, uint32_t* status,
+                               cudaStream_t s);
+
+// Alias table over the positive entries of activity[V] in FP64 on the device.
+// Scratch is owned by the caller (AliasScratch::bytes(V)).
+struct AliasScratch {
+  static size_t bytes(int64_t V);
+  void* base;
+};
+cudaError_t build_alias_table(const float* activity, int64_t V, AliasScratch scratch, uint4* table,
+                              int64_t* n_active_host, uint32_t* status, cudaStream_t s);
+
+// Batch fold (per batch) and finalize.
+struct FoldParams {
+  ull* tb;                  // batch tally, zeroed by the fold
+  ull* tsum;                // cumulative tally
+  double* s2;               // sum over batches of T_b^2 / n_b
+  const float* density;
+  const uint8_t* labels;    // may be NULL
+  int64_t V;
+  double n_b;               // histories in this batch
+  double gy_per_unit_vol;   // J per unit / (1e-3 kg/g * voxel volume cm^3)
+  double* organ_partial;    // [blocks][kLabelSlots]
+  double* org_s1;           // [kLabelSlots] sum_b O_b
+  double* org_s2;           // [kLabelSlots] sum_b O_b^2 / n_b
+  ull* deposited;           // counter
+};
+int fold_blocks(int64_t V);
+cudaError_t launch_fold(const FoldParams& p, cudaStream_t s);
+
+struct FinalizeParams {
+  const ull* tsum;
+  const double* s2;
+  const float* density;
+  const uint8_t* labels;
+  int64_t V;
+  double n_total;           // histories
+  double n_batches;         // K
+  double gy_per_unit_vol;
+  double activity_bq;
+  float* dose;              // may be NULL
+  float* sigma;             // may be NULL
+  double* organ_partial;    // [blocks][2][kLabelSlots]
+  const double* org_s1;
+  const double* org_s2;
+  const long long* organ_count;  // [kLabelSlots]
+  double* organ_out;        // [4][kLabelSlots]: mean, eps_rms, sigma_mean, count
+};
+cudaError_t launch_finalize(const FinalizeParams& p, cudaStream_t s);
+cudaError_t launch_label_count(const uint8_t* labels, int64_t V, long long* count, cudaStream_t s);
+
+}  // namespace nm

@@ -1,0 +1,172 @@
+// Tally statistics (§2.1 dose and uncertainty maps, Eq. 1-3).
+//
+// Per batch b of n_b histories the fold moves the int64 batch tally T_b into
+// the exact cumulative tally and accumulates, in FP64, S2 = sum_b T_b^2 / n_b
+// per voxel and the organ sums O_b = sum over the organ's voxels of the batch
+// dose.  With N = sum n_b histories and K batches the per-decay mean of a
+// voxel is x = Tsum / N and the batch estimate of its variance is
+//   var(x) = (S2 - Tsum^2 / N) / ((K - 1) N),
+// the n_b-weighted form of the batch-means estimator.  Every reduction has a
+// fixed tree (per-thread columns in shared memory, then fixed warp trees, then
+// blocks in index order), so the statistics are the same on every run.
+#include "nm_internal.cuh"
+
+namespace nm {
+namespace {
+
+__device__ __forceinline__ double warp_sum_d(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// Reduce acc[l][0..kFoldThreads) for every label into out[l] (fixed tree).
+__device__ void reduce_label_columns(const double (*acc)[kFoldThreads], double* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  constexpr int nw = kFoldThreads / 32;
+  for (int l = wid; l < kLabelSlots; l += nw) {
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < kFoldThreads / 32; ++j) s += acc[l][lane + 32 * j];
+    s = warp_sum_d(s);
+    if (lane == 0) out[l] = s;
+  }
+}
+
+__global__ void __launch_bounds__(kFoldThreads) fold_kernel(const FoldParams p) {
+  __shared__ double acc[kLabelSlots][kFoldThreads];
+  __shared__ ull dep_w[kFoldThreads / 32];
+  for (int l = 0; l < kLabelSlots; ++l) acc[l][threadIdx.x] = 0.0;
+  const int64_t v0 = (int64_t)blockIdx.x * kFoldTile;
+  const int64_t v1 = v0 + kFoldTile < p.V ? v0 + kFoldTile : p.V;
+  ull dep = 0;
+  const double inv_nb = 1.0 / p.n_b;
+  for (int64_t v = v0 + threadIdx.x; v < v1; v += kFoldThreads) {
+    const ull t = p.tb[v];
+    if (t == 0) continue;
+    p.tb[v] = 0;
+    p.tsum[v] += t;
+    const double x = (double)t;
+    p.s2[v] += x * x * inv_nb;
+    dep += t;
+    if (p.labels) {
+      const int l = p.labels[v];
+      acc[l][threadIdx.x] += x * (p.gy_per_unit_vol / (double)p.density[v]);
+    }
+  }
+  // deposited-energy counter (integer, so the order of the adds does not matter)
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) dep += __shfl_xor_sync(0xffffffffu, dep, o);
+  if ((threadIdx.x & 31) == 0) dep_w[threadIdx.x >> 5] = dep;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ull s = 0;
+    for (int w = 0; w < kFoldThreads / 32; ++w) s += dep_w[w];
+    if (s) atomicAdd(p.deposited, s);
+  }
+  if (p.labels) reduce_label_columns(acc, p.organ_partial + (size_t)blockIdx.x * kLabelSlots);
+}
+
+// One warp per label: blocks in index order, lane-strided, then a fixed tree.
+__global__ void fold_organs_kernel(const FoldParams p, int n_blocks) {
+  const int lane = threadIdx.x & 31;
+  const int l = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (l >= kLabelSlots) return;
+  double s = 0.0;
+  for (int b = lane; b < n_blocks; b += 32) s += p.organ_partial[(size_t)b * kLabelSlots + l];
+  s = warp_sum_d(s);
+  if (lane == 0) {
+    p.org_s1[l] += s;
+    p.org_s2[l] += s * s / p.n_b;
+  }
+}
+
+__global__ void __launch_bounds__(kFoldThreads) finalize_kernel(const FinalizeParams p) {
+  extern __shared__ double sm[];
+  double(*acc_d)[kFoldThreads] = (double(*)[kFoldThreads])sm;
+  double(*acc_e)[kFoldThreads] = (double(*)[kFoldThreads])(sm + kLabelSlots * kFoldThreads);
+  for (int l = 0; l < kLabelSlots; ++l) acc_d[l][threadIdx.x] = acc_e[l][threadIdx.x] = 0.0;
+  const int64_t v0 = (int64_t)blockIdx.x * kFoldTile;
+  const int64_t v1 = v0 + kFoldTile < p.V ? v0 + kFoldTile : p.V;
+  const double inv_n = 1.0 / p.n_total;
+  const double inv_k1n = 1.0 / ((p.n_batches - 1.0) * p.n_total);
+  for (int64_t v = v0 + threadIdx.x; v < v1; v += kFoldThreads) {
+    const double t = (double)p.tsum[v];
+    const double mean = t * inv_n;                         // units per decay
+    const double var = fmax(p.s2[v] - t * mean, 0.0) * inv_k1n;
+    const double conv = p.gy_per_unit_vol / (double)p.density[v] * p.activity_bq;
+    const double d = mean * conv;                          // Eq. 1, Gy/s
+    const double sg = sqrt(var) * conv;
+    if (p.dose) p.dose[v] = (float)d;
+    if (p.sigma) p.sigma[v] = (float)sg;
+    if (p.labels) {
+      const int l = p.labels[v];
+      acc_d[l][threadIdx.x] += d;
+      const double eps = d > 0.0 ? sg / d : 1.0;
+      acc_e[l][threadIdx.x] += eps * eps;
+    }
+  }
+  if (!p.labels) return;
+  __syncthreads();
+  double* out = p.organ_partial + (size_t)blockIdx.x * 2 * kLabelSlots;
+  reduce_label_columns(acc_d, out);
+  reduce_label_columns(acc_e, out + kLabelSlots);
+}
+
+__global__ void finalize_organs_kernel(const FinalizeParams p, int n_blocks) {
+  const int lane = threadIdx.x & 31;
+  const int l = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (l >= kLabelSlots) return;
+  double sd = 0.0, se = 0.0;
+  for (int b = lane; b < n_blocks; b += 32) {
+    sd += p.organ_partial[(size_t)b * 2 * kLabelSlots + l];
+    se += p.organ_partial[(size_t)b * 2 * kLabelSlots + kLabelSlots + l];
+  }
+  sd = warp_sum_d(sd);
+  se = warp_sum_d(se);
+  if (lane != 0) return;
+  const double cnt = (double)p.organ_count[l];
+  double mean = 0.0, eps = 0.0, sig = 0.0;
+  if (cnt > 0.0) {
+    mean = sd / cnt;                                          // Eq. 2
+    eps = sqrt(se / cnt);                                     // Eq. 3
+    // Batch sigma of the organ mean: m_b = O_b / (n_b cnt) per decay.
+    const double N = p.n_total;
+    const double mbar = p.org_s1[l] / (N * cnt);
+    const double sum_nm2 = p.org_s2[l] / (cnt * cnt);
+    const double var = fmax(sum_nm2 - N * mbar * mbar, 0.0) / ((p.n_batches - 1.0) * N);
+    sig = sqrt(var) * p.activity_bq;
+  }
+  p.organ_out[l] = mean;
+  p.organ_out[kLabelSlots + l] = eps;
+  p.organ_out[2 * kLabelSlots + l] = sig;
+  p.organ_out[3 * kLabelSlots + l] = cnt;
+}
+
+}  // namespace
+
+int fold_blocks(int64_t V) { return (int)((V + kFoldTile - 1) / kFoldTile); }
+
+cudaError_t launch_fold(const FoldParams& p, cudaStream_t s) {
+  const int nb = fold_blocks(p.V);
+  fold_kernel<<<nb, kFoldThreads, 0, s>>>(p);
+  if (p.labels) fold_organs_kernel<<<(kLabelSlots + 3) / 4, 128, 0, s>>>(p, nb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const FinalizeParams& p, cudaStream_t s) {
+  const int nb = fold_blocks(p.V);
+  const size_t smem = 2 * kLabelSlots * kFoldThreads * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(finalize_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  finalize_kernel<<<nb, kFoldThreads, smem, s>>>(p);
+  if (p.labels) finalize_organs_kernel<<<(kLabelSlots + 3) / 4, 128, 0, s>>>(p, nb);
+  return cudaGetLastError();
+}
+
+}  // namespace nm

@@ -1,0 +1,481 @@
+// Photon transport for ARCHER-NM's method (§2.1): decay sampling, two
+// back-to-back 0.511 MeV photons, Woodcock delta tracking through the voxel
+// grid, Klein-Nishina Compton (Kahn's sampler), photoelectric absorption,
+// optional Rayleigh, 10 keV photon cutoff, int64 fixed-point tally.
+//
+// One persistent launch per batch.  Each lane owns one photon; a lane whose
+// photon ends takes the decay's second photon or, with the rest of its warp,
+// refills from a warp-private pool of history ids that one lane grabs from a
+// global counter in chunks.  Every iteration of the loop is one flight step
+// for every live lane, so lanes stay converged on the flight; the interaction
+// work is regrouped (see the `regroup` variant) so that a warp runs Compton
+// sampling for a batch of lanes at once instead of once per step.
+//
+// A history's random numbers come from Philox4x32-10 keyed by the seed with
+// counter (block index, stream, history id), so which lane or SM simulates it
+// does not matter, and integer atomics make the tally order-independent: a
+// fixed seed gives bit-identical tallies.
+#include "nm_internal.cuh"
+
+namespace nm {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kKahnTrialLimit = 1000;
+
+struct Energy {
+  float s_c, s_pe, s_r;   // per-unit-density factors: mu/rho = za s_c + zp s_pe + zr s_r
+  float mubar;            // majorant (1/cm) over all materials at their largest density
+  float inv_mubar;
+};
+
+template <bool RAYLEIGH>
+__device__ __forceinline__ Energy energy_factors(float e, const float* __restrict__ kn,
+                                                 const MaterialCoef* __restrict__ mat, int n_mat,
+                                                 float ln_lo, float inv_dln) {
+  Energy f;
+  float x = (__logf(e) - ln_lo) * inv_dln;
+  x = fminf(fmaxf(x, 0.0f), (float)(kKnTable - 1) - 0x1p-10f);
+  const int i = (int)x;
+  const float w = x - (float)i;
+  const float a = kn[i], b = kn[i + 1];
+  f.s_c = fmaf(w, b - a, a);
+  const float ie = 1.0f / e;
+  const float ie2 = ie * ie;
+  f.s_pe = ie2 * ie;
+  f.s_r = RAYLEIGH ? ie2 : 0.0f;
+  float mb = 0.0f;
+  for (int m = 0; m < n_mat; ++m) {
+    const MaterialCoef c = mat[m];
+    const float t = fmaf(c.zr, f.s_r, fmaf(c.zp, f.s_pe, c.za * f.s_c));
+    mb = fmaxf(mb, c.rho_max * t);
+  }
+  // Each voxel evaluates the same nested expression with rho <= rho_max, and
+  // rounded products are monotone, so mu_voxel <= mb; the margin is for safety.
+  f.mubar = mb * (1.0f + 0x1p-20f);
+  f.inv_mubar = 1.0f / f.mubar;
+  return f;
+}
+
+__device__ __forceinline__ uint4 draw(uint32_t& ctr, uint32_t stream, uint32_t hlo, uint32_t hhi,
+                                      uint32_t k0, uint32_t k1) {
+  return philox4x32_10(make_uint4(ctr++, stream, hlo, hhi), k0, k1);
+}
+
+// Kahn's rejection sampler for the Klein-Nishina distribution (Kahn 1954).
+// With k = E/m_e c^2, eta = E/E' in [1, 1 + 2k] and x = (eta - 1)/k = 1 - cos θ:
+//   branch 1 (prob. (1+2k)/(9+2k)): eta uniform, accept with 4(eta-1)/eta^2;
+//   branch 2: eta = (1+2k)/(1+2k r), accept with (cos^2 θ + 1/eta)/2.
+// x is formed directly from the uniforms so that cos θ keeps full precision
+// at low energy.  One Philox block per trial; its 4th word is the azimuth.
+__device__ __forceinline__ float kahn_x(float k, uint32_t& ctr, uint32_t stream, uint32_t hlo,
+                                        uint32_t hhi, uint32_t k0, uint32_t k1, uint32_t& r_phi,
+                                        uint32_t& flags) {
+  const float two_k = 2.0f * k;
+  const float thr = (1.0f + two_k) / (9.0f + two_k);
+  for (int trial = 0;; ++trial) {
+    const uint4 r = draw(ctr, stream, hlo, hhi, k0, k1);
+    const float r1 = u01(r.x), r2 = u01(r.y), r3 = u01(r.z);
+    float x;
+    bool acc;
+    if (r1 <= thr) {
+      x = 2.0f * r2;
+      const float eta = fmaf(k, x, 1.0f);
+      acc = r3 * eta * eta <= 4.0f * k * x;
+    } else {
+      x = 2.0f * (1.0f - r2) / fmaf(two_k, r2, 1.0f);
+      const float eta = fmaf(k, x, 1.0f);
+      const float c = 1.0f - x;
+      acc = 2.0f * r3 <= fmaf(c, c, 1.0f / eta);
+    }
+    if (acc || trial + 1 >= kKahnTrialLimit) {
+      if (!acc) flags |= NM_DEV_KAHN_LIMIT;
+      r_phi = r.w;
+      return x;
+    }
+  }
+}
+
+// New direction at polar cosine c and azimuth phi about (u, v, w).
+__device__ __forceinline__ void rotate(float& u, float& v, float& w, float c, float phi) {
+  const float s = sqrtf(fmaxf(0.0f, fmaf(-c, c, 1.0f)));
+  float sp, cp;
+  __sincosf(phi, &sp, &cp);
+  const float t2 = fmaf(-w, w, 1.0f);
+  float nu, nv, nw;
+  if (t2 > 1e-10f) {
+    const float t = sqrtf(t2);
+    const float it = 1.0f / t;
+    nu = fmaf(c, u, s * (u * w * cp - v * sp) * it);
+    nv = fmaf(c, v, s * (v * w * cp + u * sp) * it);
+    nw = fmaf(c, w, -s * cp * t);
+  } else {
+    nu = s * cp;
+    nv = s * sp;
+    nw = w > 0.0f ? c : -c;
+  }
+  const float n = rsqrtf(fmaf(nu, nu, fmaf(nv, nv, nw * nw)));
+  u = nu * n;
+  v = nv * n;
+  w = nw * n;
+}
+
+// Decay site and first-photon direction of history (hlo, hhi).
+struct Site {
+  int v;              // decay voxel (-1 in point mode)
+  float x, y, z;      // voxel units
+  float u, v_, w;     // direction of photon A
+};
+
+__device__ __forceinline__ Site sample_site(const TransportParams& p, uint32_t hlo, uint32_t hhi) {
+  Site s;
+  uint32_t ctr = 0;
+  uint4 r = draw(ctr, kStreamSource, hlo, hhi, p.key0, p.key1);
+  uint32_t rc, rphi;
+  if (p.source_mode == NM_SOURCE_DECAY) {
+    // Alias table: 64 random bits pick a column uniformly, one more the side.
+    const uint64_t r64 = ((uint64_t)r.y << 32) | r.x;
+    const uint64_t col = __umul64hi(r64, p.n_active);
+    const uint4 a = __ldg(p.alias + col);
+    s.v = (u01(r.z) < __uint_as_float(a.x)) ? (int)a.y : (int)a.z;
+    const int nxy = p.nx * p.ny;
+    const int iz = s.v / nxy;
+    const int rem = s.v - iz * nxy;
+    const int iy = rem / p.nx;
+    const int ix = rem - iy * p.nx;
+    const uint32_t rx = r.w;
+    r = draw(ctr, kStreamSource, hlo, hhi, p.key0, p.key1);
+    // Uniform inside the voxel; keep ix + u below ix + 1 after rounding.
+    s.x = fminf((float)ix + u01(rx), __int_as_float(__float_as_int((float)(ix + 1)) - 1));
+    s.y = fminf((float)iy + u01(r.x), __int_as_float(__float_as_int((float)(iy + 1)) - 1));
+    s.z = fminf((float)iz + u01(r.y), __int_as_float(__float_as_int((float)(iz + 1)) - 1));
+    rc = r.z;
+    rphi = r.w;
+  } else {
+    s.v = -1;
+    s.x = p.px;
+    s.y = p.py;
+    s.z = p.pz;
+    rc = r.x;
+    rphi = r.y;
+  }
+  // Isotropic: cos θ uniform on (-1, 1), azimuth uniform.
+  const float c = fmaf(2.0f, u01(rc), -1.0f);
+  const float sn = sqrtf(fmaxf(0.0f, fmaf(-c, c, 1.0f)));
+  float sp, cp;
+  __sincosf(fmaf(kTwoPi, u01(rphi), -3.14159265f), &sp, &cp);
+  s.u = sn * cp;
+  s.v_ = sn * sp;
+  s.w = c;
+  return s;
+}
+
+template <bool WARP_AGG>
+__device__ __forceinline__ void tally_flush(ull* __restrict__ tally, bool has, int v, uint32_t dq,
+                                            uint32_t lane) {
+  if (WARP_AGG) {
+    const unsigned m = __ballot_sync(kFull, has);
+    if (has) {
+      const unsigned g = __match_any_sync(m, v);
+      const unsigned sum = __reduce_add_sync(g, dq);
+      if (lane == (unsigned)(__ffs(g) - 1)) atomicAdd(tally + v, (ull)sum);
+    }
+  } else if (has) {
+    atomicAdd(tally + v, (ull)dq);
+  }
+}
+
+__device__ __forceinline__ ull warp_sum(ull x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+  return x;
+}
+
+template <bool WARP_AGG, bool RAYLEIGH, bool REGROUP>
+__global__ void __launch_bounds__(256) transport_kernel(const TransportParams p) {
+  __shared__ float s_kn[kKnTable];
+  __shared__ MaterialCoef s_mat[NM_MAX_MATERIALS];
+  for (int i = threadIdx.x; i < kKnTable; i += blockDim.x) s_kn[i] = p.kn[i];
+  if (threadIdx.x < NM_MAX_MATERIALS) s_mat[threadIdx.x] = p.mat[threadIdx.x];
+  __syncthreads();
+
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  const Energy f0 = energy_factors<RAYLEIGH>(p.e0, s_kn, s_mat, p.n_mat, p.ln_e_lo, p.inv_dln_e);
+
+  uint64_t pool_next = 0, pool_end = 0;  // warp-uniform
+  bool done = false, alive = false, pending_b = false, pending_c = false;
+  float px = 0.f, py = 0.f, pz = 0.f, ux = 0.f, uy = 0.f, uz = 0.f;
+  float bx = 0.f, by = 0.f, bz = 0.f;    // decay site, for photon B
+  float au = 0.f, av = 0.f, aw = 0.f;    // photon A's initial direction
+  float e = 0.f;
+  Energy f = f0;
+  int32_t qe = 0;
+  int cv = 0;                            // voxel of a pending Compton event
+  uint32_t hlo = 0, hhi = 0, stream = 0, ctr = 0, spare0 = 0, spare1 = 0;
+  bool have_spare = false;
+  int steps = 0;
+  uint32_t n_steps = 0, n_compton = 0, n_photo = 0, n_rayl = 0, n_cut = 0, n_esc = 0, flags = 0;
+  ull escaped = 0, killed = 0;
+
+  for (;;) {
+    // ---- second photon of the decay: same site, opposite direction ----------
+    if (!alive && pending_b) {
+      pending_b = false;
+      alive = true;
+      px = bx; py = by; pz = bz;
+      ux = -au; uy = -av; uz = -aw;
+      e = p.e0; qe = p.q_e0; f = f0;
+      stream = kStreamPhotonB; ctr = 0; have_spare = false; steps = 0;
+    }
+    // ---- refill: lanes without a photon take new histories from the pool ----
+    const unsigned need = __ballot_sync(kFull, !alive && !done);
+    if (need) {
+      const uint32_t cnt = __popc(need);
+      const uint64_t avail = pool_end > pool_next ? pool_end - pool_next : 0;
+      uint64_t fresh = 0;
+      if (avail < cnt) {
+        if (lane == 0) fresh = atomicAdd(p.work, (ull)p.chunk);
+        fresh = __shfl_sync(kFull, fresh, 0);
+      }
+      bool has = false;
+      int dv = 0;
+      if (!alive && !done) {
+        const uint32_t rank = __popc(need & lt_mask);
+        const uint64_t idx = rank < avail ? pool_next + rank : fresh + (rank - avail);
+        if (idx < p.n_hist) {
+          const uint64_t h = p.hist_begin + idx;
+          hlo = (uint32_t)h;
+          hhi = (uint32_t)(h >> 32);
+          const Site s = sample_site(p, hlo, hhi);
+          px = bx = s.x; py = by = s.y; pz = bz = s.z;
+          ux = au = s.u; uy = av = s.v_; uz = aw = s.w;
+          e = p.e0; qe = p.q_e0; f = f0;
+          stream = kStreamPhotonA; ctr = 0; have_spare = false; steps = 0;
+          alive = true;
+          if (p.source_mode == NM_SOURCE_DECAY) {
+            pending_b = true;
+            has = p.q_positron > 0;
+            dv = s.v;
+          }
+        } else {
+          done = true;
+        }
+      }
+      if (avail < cnt) {
+        pool_next = fresh + (cnt - avail);
+        pool_end = fresh + (uint64_t)p.chunk;
+      } else {
+        pool_next += cnt;
+      }
+      tally_flush<WARP_AGG>(p.tally, has, dv, (uint32_t)p.q_positron, lane);
+    }
+    if (!__any_sync(kFull, alive)) break;
+
+    bool has = false;
+    int dv = 0;
+    uint32_t dq = 0;
+    // ---- Compton interaction (regrouped: run when enough lanes wait) --------
+    if (REGROUP) {
+      const unsigned waiting = __ballot_sync(kFull, pending_c);
+      const unsigned flying = __ballot_sync(kFull, alive && !pending_c);
+      if (waiting && (__popc(waiting) >= 12 || flying == 0)) {
+        if (pending_c) {
+          pending_c = false;
+          uint32_t rphi;
+          const float k = e * kInvElectronMassMeV;
+          const float x = kahn_x(k, ctr, stream, hlo, hhi, p.key0, p.key1, rphi, flags);
+          const float e2 = e / fmaf(k, x, 1.0f);
+          rotate(ux, uy, uz, 1.0f - x, fmaf(kTwoPi, u01(rphi), -3.14159265f));
+          const int32_t q2 = q_units(e2);
+          has = true;
+          dv = cv;
+          if (e2 < p.cut) {
+            dq = (uint32_t)qe;
+            ++n_cut;
+            alive = false;
+          } else {
+            dq = (uint32_t)(qe - q2);
+            e = e2;
+            qe = q2;
+            f = energy_factors<RAYLEIGH>(e, s_kn, s_mat, p.n_mat, p.ln_e_lo, p.inv_dln_e);
+          }
+        }
+      }
+    }
+    // ---- one Woodcock flight step per live lane -------------------------------
+    if (alive && !pending_c && !has) {
+      uint32_t r0, r1;
+      if (have_spare) {
+        r0 = spare0; r1 = spare1; have_spare = false;
+      } else {
+        const uint4 r = draw(ctr, stream, hlo, hhi, p.key0, p.key1);
+        r0 = r.x; r1 = r.y; spare0 = r.z; spare1 = r.w; have_spare = true;
+      }
+      const float s = -__logf(u01(r0)) * f.inv_mubar;   // cm
+      px = fmaf(s * p.inv_dx, ux, px);
+      py = fmaf(s * p.inv_dy, uy, py);
+      pz = fmaf(s * p.inv_dz, uz, pz);
+      ++n_steps;
+      ++steps;
+      if (!(px >= 0.0f && px < p.fnx && py >= 0.0f && py < p.fny && pz >= 0.0f && pz < p.fnz)) {
+        escaped += (ull)qe;
+        ++n_esc;
+        alive = false;
+      } else {
+        const int v = ((int)pz * p.ny + (int)py) * p.nx + (int)px;
+        const uint32_t wv = __ldg(p.vox + v);
+        const float rho = __uint_as_float(wv & ~7u);
+        const MaterialCoef c = s_mat[wv & 7u];
+        const float ic = c.za * f.s_c;
+        const float icp = fmaf(c.zp, f.s_pe, ic);
+        const float t = u01(r1) * f.mubar;
+        if (t < rho * ic) {
+          ++n_compton;
+          if (REGROUP) {
+            pending_c = true;
+            cv = v;
+          } else {
+            uint32_t rphi;
+            const float k = e * kInvElectronMassMeV;
+            const float x = kahn_x(k, ctr, stream, hlo, hhi, p.key0, p.key1, rphi, flags);
+            const float e2 = e / fmaf(k, x, 1.0f);
+            rotate(ux, uy, uz, 1.0f - x, fmaf(kTwoPi, u01(rphi), -3.14159265f));
+            const int32_t q2 = q_units(e2);
+            has = true;
+            dv = v;
+            if (e2 < p.cut) {
+              dq = (uint32_t)qe;
+              ++n_cut;
+              alive = false;
+            } else {
+              dq = (uint32_t)(qe - q2);
+              e = e2;
+              qe = q2;
+              f = energy_factors<RAYLEIGH>(e, s_kn, s_mat, p.n_mat, p.ln_e_lo, p.inv_dln_e);
+            }
+          }
+        } else if (t < rho * icp) {
+          ++n_photo;
+          has = true;
+          dv = v;
+          dq = (uint32_t)qe;
+          alive = false;
+        } else if (RAYLEIGH && t < rho * fmaf(c.zr, f.s_r, icp)) {
+          ++n_rayl;
+          // Thomson angular shape (1 + cos^2)/2 by rejection; one block per trial.
+          for (int trial = 0;; ++trial) {
+            const uint4 r = draw(ctr, stream, hlo, hhi, p.key0, p.key1);
+            const float cth = fmaf(2.0f, u01(r.x), -1.0f);
+            if (2.0f * u01(r.y) <= fmaf(cth, cth, 1.0f) || trial + 1 >= kKahnTrialLimit) {
+              rotate(ux, uy, uz, cth, fmaf(kTwoPi, u01(r.z), -3.14159265f));
+              break;
+            }
+          }
+        }
+      }
+      if (alive && steps >= p.max_steps) {
+        killed += (ull)qe;
+        flags |= NM_DEV_STEP_LIMIT;
+        alive = false;
+        pending_c = false;
+      }
+    }
+    tally_flush<WARP_AGG>(p.tally, has, dv, dq, lane);
+  }
+
+  // ---- counters: warp sums, one atomic per warp per counter ----------------
+  const ull cs[8] = {n_steps, n_compton, n_photo, n_rayl, n_cut, n_esc, escaped, killed};
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const ull s = warp_sum(cs[i]);
+    if (lane == 0 && s) atomicAdd(p.counters + i, s);
+  }
+  const unsigned fl = __reduce_or_sync(kFull, flags);
+  if (lane == 0 && fl) atomicOr(p.status, fl);
+}
+
+__global__ void check_philox_kernel(const uint4* ctr, const uint2* key, int64_t n, uint4* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = philox4x32_10(ctr[i], key[i].x, key[i].y);
+}
+
+__global__ void check_kahn_kernel(float e, int64_t n, uint32_t k0, uint32_t k1, float* out,
+                                  uint32_t* status) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t ctr = 0, rphi, flags = 0;
+  const float x = kahn_x(e * kInvElectronMassMeV, ctr, 7u, (uint32_t)i, (uint32_t)(i >> 32), k0, k1,
+                         rphi, flags);
+  out[i] = 1.0f - x;
+  if (flags) atomicOr(status, flags);
+}
+
+__global__ void check_source_kernel(const TransportParams p, uint64_t first, int64_t n,
+                                    int32_t* voxel, float* pos, float* dir) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t h = first + (uint64_t)i;
+  const Site s = sample_site(p, (uint32_t)h, (uint32_t)(h >> 32));
+  voxel[i] = s.v;
+  pos[3 * i + 0] = s.x / p.inv_dx;
+  pos[3 * i + 1] = s.y / p.inv_dy;
+  pos[3 * i + 2] = s.z / p.inv_dz;
+  dir[3 * i + 0] = s.u;
+  dir[3 * i + 1] = s.v_;
+  dir[3 * i + 2] = s.w;
+}
+
+template <bool A, bool R, bool G>
+void* kernel_ptr() {
+  return (void*)transport_kernel<A, R, G>;
+}
+
+void* pick(bool a, bool r, bool g) {
+  if (a) {
+    if (r) return g ? kernel_ptr<true, true, true>() : kernel_ptr<true, true, false>();
+    return g ? kernel_ptr<true, false, true>() : kernel_ptr<true, false, false>();
+  }
+  if (r) return g ? kernel_ptr<false, true, true>() : kernel_ptr<false, true, false>();
+  return g ? kernel_ptr<false, false, true>() : kernel_ptr<false, false, false>();
+}
+
+}  // namespace
+
+cudaError_t launch_transport(const TransportParams& p, int grid, int block, bool warp_agg,
+                             bool rayleigh, bool regroup, cudaStream_t s) {
+  void* fn = pick(warp_agg, rayleigh, regroup);
+  void* args[] = {(void*)&p};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, 0, s);
+}
+
+int transport_max_blocks_per_sm(int block, bool warp_agg, bool rayleigh, bool regroup) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick(warp_agg, rayleigh, regroup), block,
+                                                    0) != cudaSuccess)
+    return 0;
+  return n;
+}
+
+cudaError_t launch_check_philox(const uint4* ctr, const uint2* key, int64_t n, uint4* out,
+                                cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  check_philox_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ctr, key, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_kahn(float e, int64_t n, uint32_t k0, uint32_t k1, float* out,
+                              uint32_t* status, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  check_kahn_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(e, n, k0, k1, out, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_source(const TransportParams& p, uint64_t first, int64_t n, int32_t* voxel,
+                                float* pos, float* dir, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  check_source_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, first, n, voxel, pos, dir);
+  return cudaGetLastError();
+}
+
+}  // namespace nm

@@ -1,0 +1,303 @@
+"""Thin Python binding of libnmdose (include/nm_dose.h).
+
+Argument marshalling only: every step of the simulation runs in the CUDA
+library.  Functions keep the C names; arrays may be numpy arrays (host) or
+torch tensors (host or CUDA), passed by pointer.  If the library has not been
+built, the first call raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnmdose.so")
+_lib = None
+
+NM_OK, NM_ERR_ARG, NM_ERR_CUDA, NM_ERR_OOM, NM_ERR_OVERFLOW, NM_ERR_TIMEOUT, NM_ERR_STATE, NM_ERR_DEVICE = range(8)
+NM_SOURCE_DECAY, NM_SOURCE_POINT = 0, 1
+NM_MAX_MATERIALS = 8
+NM_MAX_LABELS = 31
+UNITS_PER_MEV = 64.0e6
+STATUS_NAMES = ["NM_OK", "NM_ERR_ARG", "NM_ERR_CUDA", "NM_ERR_OOM", "NM_ERR_OVERFLOW",
+                "NM_ERR_TIMEOUT", "NM_ERR_STATE", "NM_ERR_DEVICE"]
+
+
+class NmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+class nm_grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("dx", C.c_float), ("dy", C.c_float), ("dz", C.c_float),
+                ("density", C.c_void_p), ("material", C.c_void_p)]
+
+
+class nm_materials(C.Structure):
+    _fields_ = [("n", C.c_int32), ("z_over_a", C.POINTER(C.c_double)), ("zeff", C.POINTER(C.c_double)),
+                ("pe_coeff", C.c_double), ("pe_exp", C.c_double), ("rayleigh_coeff", C.c_double),
+                ("rayleigh", C.c_int32), ("photon_cut_mev", C.c_double), ("electron_cut_mev", C.c_double)]
+
+
+class nm_options(C.Structure):
+    _fields_ = [("source_mode", C.c_int32), ("point", C.c_float * 3), ("photon_mev", C.c_double),
+                ("positron_mev", C.c_double), ("batches", C.c_int32), ("activity_bq", C.c_double),
+                ("n_labels", C.c_int32), ("block_threads", C.c_int32), ("chunk", C.c_int32),
+                ("warp_aggregate", C.c_int32), ("regroup", C.c_int32), ("max_steps", C.c_int32),
+                ("stream", C.c_void_p)]
+
+
+class nm_counters(C.Structure):
+    _fields_ = [("histories", C.c_uint64), ("batches", C.c_uint64), ("emitted", C.c_int64),
+                ("deposited", C.c_int64), ("escaped", C.c_int64), ("killed", C.c_int64),
+                ("steps", C.c_uint64), ("compton", C.c_uint64), ("photo", C.c_uint64),
+                ("rayleigh", C.c_uint64), ("cutoff", C.c_uint64), ("escapes", C.c_uint64),
+                ("transport_ms", C.c_double), ("fold_ms", C.c_double), ("device_status", C.c_uint32),
+                ("block_threads", C.c_int32), ("chunk", C.c_int32), ("warp_aggregate", C.c_int32),
+                ("regroup", C.c_int32), ("grid_blocks", C.c_int32)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+# Every entry point declared in include/nm_dose.h, with its ctypes signature.
+_SIGS = {
+    "nm_options_default": (None, [C.POINTER(nm_options)]),
+    "nm_last_error": (C.c_char_p, []),
+    "nm_ct_to_phantom": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "nm_dose_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(nm_grid), C.POINTER(nm_materials),
+                                 C.c_void_p, C.c_void_p, C.POINTER(nm_options)]),
+    "nm_dose_run": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64]),
+    "nm_dose_get": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "nm_dose_get_organs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "nm_dose_get_tally": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "nm_dose_counters": (C.c_int, [C.c_void_p, C.POINTER(nm_counters)]),
+    "nm_dose_reset": (C.c_int, [C.c_void_p]),
+    "nm_dose_destroy": (None, [C.c_void_p]),
+    "nm_check_philox": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
+    "nm_check_kahn": (C.c_int, [C.c_double, C.c_int64, C.c_uint64, C.c_void_p]),
+    "nm_dose_alias_table": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "nm_check_source": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int64, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p]),
+}
+
+
+def load():
+    """Load libnmdose.so; raises if it was not built (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2111_11687_gb300.build.build()")
+        lib = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def symbols():
+    return list(_SIGS)
+
+
+def _check(st):
+    if st != NM_OK:
+        raise NmError(st, load().nm_last_error().decode())
+
+
+def ptr(x):
+    """Pointer of a numpy array or torch tensor (host or device), or None."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags.c_contiguous
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous()
+        return x.data_ptr()
+    raise TypeError(type(x))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def options(**kw) -> nm_options:
+    o = nm_options()
+    load().nm_options_default(C.byref(o))
+    for k, v in kw.items():
+        if k == "point":
+            o.point[:] = [float(a) for a in v]
+        elif k == "stream":
+            o.stream = _stream_ptr(v)
+        else:
+            setattr(o, k, v)
+    return o
+
+
+@dataclass
+class Materials:
+    z_over_a: list
+    zeff: list
+    pe_coeff: float = 2.0e-9
+    pe_exp: float = 3.8
+    rayleigh_coeff: float = 1.0e-6
+    rayleigh: int = 0
+    photon_cut_mev: float = 0.010
+    electron_cut_mev: float = 0.200
+
+    def c(self):
+        za = np.ascontiguousarray(self.z_over_a, np.float64)
+        ze = np.ascontiguousarray(self.zeff, np.float64)
+        m = nm_materials(len(za), za.ctypes.data_as(C.POINTER(C.c_double)), ze.ctypes.data_as(C.POINTER(C.c_double)),
+                         self.pe_coeff, self.pe_exp, self.rayleigh_coeff, self.rayleigh,
+                         self.photon_cut_mev, self.electron_cut_mev)
+        m._keep = (za, ze)
+        return m
+
+
+def nm_ct_to_phantom(hu, density, material, stream=None):
+    n = int(np.prod(hu.shape))
+    _check(load().nm_ct_to_phantom(ptr(hu), n, ptr(density), ptr(material), _stream_ptr(stream)))
+
+
+def nm_dose_create(density, material, spacing, materials: Materials, activity=None, labels=None,
+                   opts: nm_options | None = None):
+    """density/material/activity/labels are [nz, ny, nx] (x fastest); spacing (dx, dy, dz) cm."""
+    nz, ny, nx = density.shape
+    g = nm_grid(nx, ny, nz, float(spacing[0]), float(spacing[1]), float(spacing[2]), ptr(density), ptr(material))
+    m = materials.c()
+    h = C.c_void_p()
+    _check(load().nm_dose_create(C.byref(h), C.byref(g), C.byref(m), ptr(activity), ptr(labels),
+                                 C.byref(opts) if opts is not None else None))
+    return h
+
+
+def nm_dose_run(h, n_decays: int, seed: int):
+    _check(load().nm_dose_run(h, int(n_decays), int(seed)))
+
+
+def nm_dose_get(h, dose=None, sigma=None, organ_dose=None):
+    _check(load().nm_dose_get(h, ptr(dose), ptr(sigma), ptr(organ_dose)))
+
+
+def nm_dose_get_organs(h, n_labels: int):
+    n = n_labels + 1
+    mean, eps, sig = np.zeros(n), np.zeros(n), np.zeros(n)
+    cnt = np.zeros(n, np.int64)
+    _check(load().nm_dose_get_organs(h, ptr(mean), ptr(eps), ptr(sig), ptr(cnt)))
+    return mean, eps, sig, cnt
+
+
+def nm_dose_get_tally(h, tally):
+    _check(load().nm_dose_get_tally(h, ptr(tally)))
+
+
+def nm_dose_counters(h) -> dict:
+    c = nm_counters()
+    _check(load().nm_dose_counters(h, C.byref(c)))
+    return c.as_dict()
+
+
+def nm_dose_reset(h):
+    _check(load().nm_dose_reset(h))
+
+
+def nm_dose_destroy(h):
+    load().nm_dose_destroy(h)
+
+
+def nm_last_error() -> str:
+    return load().nm_last_error().decode()
+
+
+def nm_check_philox(ctr: np.ndarray, key: np.ndarray) -> np.ndarray:
+    ctr = np.ascontiguousarray(ctr, np.uint32).reshape(-1, 4)
+    key = np.ascontiguousarray(key, np.uint32).reshape(-1, 2)
+    out = np.empty_like(ctr)
+    _check(load().nm_check_philox(ptr(ctr), ptr(key), len(ctr), ptr(out)))
+    return out
+
+
+def nm_check_kahn(e_mev: float, n: int, seed: int) -> np.ndarray:
+    out = np.empty(n, np.float32)
+    _check(load().nm_check_kahn(float(e_mev), n, seed, ptr(out)))
+    return out
+
+
+def nm_dose_alias_table(h):
+    n = C.c_int64()
+    _check(load().nm_dose_alias_table(h, C.byref(n), None, None, None))
+    prob = np.empty(n.value, np.float32)
+    vox = np.empty(n.value, np.int32)
+    ali = np.empty(n.value, np.int32)
+    _check(load().nm_dose_alias_table(h, C.byref(n), ptr(prob), ptr(vox), ptr(ali)))
+    return prob, vox, ali
+
+
+def nm_check_source(h, first: int, n: int, seed: int):
+    vox = np.empty(n, np.int32)
+    pos = np.empty((n, 3), np.float32)
+    d = np.empty((n, 3), np.float32)
+    _check(load().nm_check_source(h, first, n, seed, ptr(vox), ptr(pos), ptr(d)))
+    return vox, pos, d
+
+
+class Dose:
+    """Owning wrapper of an nm_dose handle."""
+
+    def __init__(self, density, material, spacing, materials: Materials, activity=None, labels=None, **opts):
+        self.shape = tuple(density.shape)
+        self.n_labels = int(opts.get("n_labels", 0))
+        self.h = nm_dose_create(density, material, spacing, materials, activity, labels, options(**opts))
+
+    def run(self, n_decays: int, seed: int = 1):
+        nm_dose_run(self.h, n_decays, seed)
+
+    def get(self, dose=None, sigma=None):
+        if dose is None:
+            dose = np.empty(self.shape, np.float32)
+        if sigma is None:
+            sigma = np.empty(self.shape, np.float32)
+        nm_dose_get(self.h, dose, sigma, None)
+        return dose, sigma
+
+    def organs(self):
+        return nm_dose_get_organs(self.h, self.n_labels)
+
+    def tally(self):
+        t = np.empty(self.shape, np.int64)
+        nm_dose_get_tally(self.h, t)
+        return t
+
+    def counters(self):
+        return nm_dose_counters(self.h)
+
+    def reset(self):
+        nm_dose_reset(self.h)
+
+    def close(self):
+        if self.h:
+            nm_dose_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,69 @@
+"""CPU checks of the C ABI boundary: the library builds and exports every entry
+point that include/nm_dose.h declares, the binding covers them, the product
+never touches the oracle, and the oracle never touches the product."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "nm_dose.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(nm_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_2111_11687_gb300 import build
+    return build.build()
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_the_header(lib_path):
+    from paper_2111_11687_gb300 import nmdose
+    assert sorted(nmdose.symbols()) == declared_functions()
+    nmdose.load()
+
+
+def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    from paper_2111_11687_gb300 import nmdose
+    monkeypatch.setattr(nmdose, "_lib", None)
+    monkeypatch.setattr(nmdose, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError):
+        nmdose.load()
+
+
+def test_options_default_without_gpu(lib_path):
+    from paper_2111_11687_gb300 import nmdose
+    o = nmdose.options()
+    assert o.batches == 10 and o.source_mode == nmdose.NM_SOURCE_DECAY
+    assert abs(o.photon_mev - 0.511) < 1e-12 and abs(o.positron_mev - 0.25) < 1e-12
+    # A(t_s): 8.0 mCi after 60 min of decay with T1/2 = 109.77 min.
+    assert abs(o.activity_bq / (8e-3 * 3.7e10 * 2 ** (-60 / 109.77)) - 1) < 1e-12
+
+
+def test_product_and_oracle_share_nothing():
+    pkg = os.path.join(ROOT, "paper_2111_11687_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", text, flags=re.M), f
+                assert "nm_oracle" not in text and "liboracle" not in text, f
+    for f in os.listdir(os.path.join(ROOT, "oracle")):
+        if f.endswith((".py", ".cpp")):
+            text = open(os.path.join(ROOT, "oracle", f)).read()
+            assert not re.search(r"^\s*(import|from)\s+paper_2111_11687_gb300\b", text, flags=re.M), f
+            assert "nm_dose.h" not in text and "libnmdose" not in text, f
+            assert "nm_internal" not in text, f

@@ -1,0 +1,83 @@
+"""Argument and state errors come back as status codes with a message."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nm():
+    from paper_2111_11687_gb300 import build, nmdose
+    build.build()
+    nmdose.load()
+    return nmdose
+
+
+def _mk(nm, act=None, den=None, mat=None, labels=None, **kw):
+    shape = (4, 5, 6)
+    den = np.ones(shape, np.float32) if den is None else den
+    mat = np.zeros(shape, np.uint8) if mat is None else mat
+    act = np.ones(shape, np.float32) if act is None else act
+    return nm.Dose(den, mat, (0.5, 0.5, 0.5), nm.Materials([0.5551], [7.42]), activity=act, labels=labels, **kw)
+
+
+@pytest.mark.parametrize("case", ["neg_activity", "nan_activity", "zero_activity", "nan_density",
+                                  "zero_density", "bad_material", "bad_label", "batches", "point_outside"])
+def test_invalid_inputs_are_rejected(nm, case):
+    shape = (4, 5, 6)
+    kw = {}
+    act = den = mat = lab = None
+    if case == "neg_activity":
+        act = np.ones(shape, np.float32); act[1, 2, 3] = -1
+    elif case == "nan_activity":
+        act = np.ones(shape, np.float32); act[0, 0, 0] = np.nan
+    elif case == "zero_activity":
+        act = np.zeros(shape, np.float32)
+    elif case == "nan_density":
+        den = np.ones(shape, np.float32); den[3, 4, 5] = np.nan
+    elif case == "zero_density":
+        den = np.ones(shape, np.float32); den[2, 2, 2] = 0
+    elif case == "bad_material":
+        mat = np.zeros(shape, np.uint8); mat[1, 1, 1] = 1
+    elif case == "bad_label":
+        lab = np.zeros(shape, np.uint8); lab[0, 1, 2] = 5
+        kw["n_labels"] = 3
+    elif case == "batches":
+        kw["batches"] = 1
+    elif case == "point_outside":
+        kw.update(source_mode=nm.NM_SOURCE_POINT, point=(3.0, 0.1, 0.1))
+    with pytest.raises(nm.NmError) as e:
+        _mk(nm, act, den, mat, lab, **kw)
+    assert e.value.status == nm.NM_ERR_ARG
+    assert nm.nm_last_error()
+
+
+def test_get_before_run_is_a_state_error(nm):
+    with _mk(nm) as d:
+        with pytest.raises(nm.NmError) as e:
+            d.get()
+        assert e.value.status == nm.NM_ERR_STATE
+        d.run(1000, seed=1)
+        d.get()
+        d.reset()
+        with pytest.raises(nm.NmError):
+            d.get()
+
+
+def test_overflow_is_refused(nm):
+    with _mk(nm) as d:
+        with pytest.raises(nm.NmError) as e:
+            d.run(2 ** 62, seed=1)
+        assert e.value.status == nm.NM_ERR_OVERFLOW
+
+
+def test_step_limit_reports_device_status(nm):
+    # A bounded loop that runs out: photons stop after 2 steps, the run returns
+    # NM_ERR_DEVICE, and the stopped energy is accounted for exactly.
+    with _mk(nm, max_steps=2) as d:
+        with pytest.raises(nm.NmError) as e:
+            d.run(20000, seed=1)
+        assert e.value.status == nm.NM_ERR_DEVICE
+        c = d.counters()
+        assert c["killed"] > 0
+        assert c["emitted"] == c["deposited"] + c["escaped"] + c["killed"]
