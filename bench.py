@@ -307,6 +307,27 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_profile(args):
+    """One short run of the benchmark workload for ncu: create, then one
+    nm_dose_run of --decays decays in 2 batches (2 transport launches)."""
+    import torch
+
+    from paper_2111_11687_gb300 import build, inputs, nmdose
+    build.build()
+    ph = _phantom()
+    den = torch.empty(SHAPE, dtype=torch.float32, device="cuda")
+    mat = torch.empty(SHAPE, dtype=torch.uint8, device="cuda")
+    nmdose.nm_ct_to_phantom(torch.from_numpy(ph.hu).cuda(), den, mat)
+    with nmdose.Dose(den, mat, SPACING, _materials_gpu(nmdose), activity=torch.from_numpy(ph.activity).cuda(),
+                     labels=torch.from_numpy(ph.labels).cuda(), n_labels=inputs.N_LABELS, batches=2,
+                     activity_bq=inputs.ACTIVITY_BQ, **json.loads(args.tuning)) as d:
+        d.run(args.decays, seed=1)
+        c = d.counters()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_decays": args.decays, "transport_ms": c["transport_ms"],
+                      "decays_per_s": args.decays / (c["transport_ms"] * 1e-3), "counters": c}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -316,8 +337,13 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-decays", type=int, default=400_000)
     ap.add_argument("--ref-decays", type=int, default=200_000)
+    ap.add_argument("--profile", action="store_true", help="one short run for ncu")
+    ap.add_argument("--decays", type=int, default=200_000_000)
+    ap.add_argument("--tuning", default="{}", help="JSON dict of nm_options launch fields (profile mode)")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile:
+        run_profile(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

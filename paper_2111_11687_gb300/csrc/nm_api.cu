@@ -212,7 +212,7 @@ nm_status nm_ct_to_phantom(const int16_t* hu, int64_t n, float* density, uint8_t
 static nm_status choose_shape(nm_dose* h) {
   const nm_options& o = h->opt;
   h->block = o.block_threads > 0 ? o.block_threads : 256;
-  if (h->block % 32 || h->block > 1024) return fail(NM_ERR_ARG, "block_threads must be a multiple of 32, <= 1024");
+  if (h->block % 32 || h->block > 512) return fail(NM_ERR_ARG, "block_threads must be a multiple of 32, <= 512");
   h->chunk = o.chunk > 0 ? o.chunk : 256;
   if (h->chunk < 32) return fail(NM_ERR_ARG, "chunk must be >= 32");
   // A point source concentrates deposits near the source, where lanes of a

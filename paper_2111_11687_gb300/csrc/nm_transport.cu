@@ -192,7 +192,7 @@ __device__ __forceinline__ ull warp_sum(ull x) {
 }
 
 template <bool WARP_AGG, bool RAYLEIGH, bool REGROUP>
-__global__ void __launch_bounds__(256) transport_kernel(const TransportParams p) {
+__global__ void __launch_bounds__(512) transport_kernel(const TransportParams p) {
   __shared__ float s_kn[kKnTable];
   __shared__ MaterialCoef s_mat[NM_MAX_MATERIALS];
   for (int i = threadIdx.x; i < kKnTable; i += blockDim.x) s_kn[i] = p.kn[i];
@@ -446,7 +446,9 @@ cudaError_t launch_transport(const TransportParams& p, int grid, int block, bool
                              bool rayleigh, bool regroup, cudaStream_t s) {
   void* fn = pick(warp_agg, rayleigh, regroup);
   void* args[] = {(void*)&p};
-  return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, 0, s);
+  const cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(block), args, 0, s);
+  if (e != cudaSuccess) cudaGetLastError();  // a refused launch must not linger as the last error
+  return e;
 }
 
 int transport_max_blocks_per_sm(int block, bool warp_agg, bool rayleigh, bool regroup) {
