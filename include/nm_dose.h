@@ -90,6 +90,8 @@ typedef struct {
   int32_t chunk;             /* histories per warp work grab; 0 = autotuned */
   int32_t warp_aggregate;    /* warp-aggregated tally atomics: -1 auto, 0 off, 1 on */
   int32_t regroup;           /* event regrouping in the transport: -1 auto, 0 off, 1 on */
+  int32_t regroup_lanes;     /* lanes of a warp that must wait for a Compton or a
+                                new-history pass before it runs (1..32); 0 = auto */
   int32_t max_steps;         /* per-photon flight-step limit (bounded loops) */
   void* stream;              /* cudaStream_t; NULL = legacy default stream */
 } nm_options;
@@ -106,7 +108,7 @@ typedef struct {
   double transport_ms;       /* device time of the transport launches */
   double fold_ms;            /* device time of the batch folds */
   uint32_t device_status;    /* OR of NM_DEV_* flags seen */
-  int32_t block_threads, chunk, warp_aggregate, regroup, grid_blocks; /* tuning used */
+  int32_t block_threads, chunk, warp_aggregate, regroup, regroup_lanes, grid_blocks; /* tuning used */
 } nm_counters;
 
 #define NM_DEV_STEP_LIMIT 1u   /* a photon hit max_steps */

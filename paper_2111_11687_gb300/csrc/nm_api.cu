@@ -106,7 +106,7 @@ struct nm_dose {
   uint64_t n_batches = 0;
   uint32_t status_seen = 0;
   double transport_ms = 0, fold_ms = 0;
-  int block = 256, chunk = 256, warp_agg = 0, regroup = 0, grid = 0;
+  int block = 256, chunk = 256, warp_agg = 0, regroup = 0, regroup_lanes = 12, grid = 0;
   std::vector<cudaEvent_t> ev;
 
   ~nm_dose() {
@@ -148,6 +148,8 @@ struct nm_dose {
     p.inv_dln_e = inv_dln;
     p.chunk = chunk;
     p.max_steps = opt.max_steps;
+    p.regroup_compton = regroup_lanes;
+    p.regroup_refill = regroup_lanes;
     return p;
   }
 
@@ -218,7 +220,9 @@ static nm_status choose_shape(nm_dose* h) {
   // A point source concentrates deposits near the source, where lanes of a
   // warp often hit the same voxel; a spread-out source rarely does.
   h->warp_agg = o.warp_aggregate >= 0 ? (o.warp_aggregate != 0) : (o.source_mode == NM_SOURCE_POINT);
-  h->regroup = o.regroup >= 0 ? (o.regroup != 0) : 0;
+  h->regroup = o.regroup >= 0 ? (o.regroup != 0) : 1;
+  h->regroup_lanes = o.regroup_lanes > 0 ? o.regroup_lanes : 12;
+  if (h->regroup_lanes > 32) return fail(NM_ERR_ARG, "regroup_lanes must be 1..32");
   const int per_sm = transport_max_blocks_per_sm(h->block, h->warp_agg, h->rayleigh, h->regroup);
   if (per_sm <= 0) return fail(NM_ERR_ARG, "transport kernel cannot launch with %d threads", h->block);
   h->grid = per_sm * h->sms;
@@ -523,6 +527,7 @@ nm_status nm_dose_counters(nm_dose* h, nm_counters* c) {
   c->chunk = h->chunk;
   c->warp_aggregate = h->warp_agg;
   c->regroup = h->regroup;
+  c->regroup_lanes = h->regroup_lanes;
   c->grid_blocks = h->grid;
   return NM_OK;
 }

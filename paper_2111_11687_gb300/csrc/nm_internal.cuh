@@ -88,6 +88,8 @@ struct TransportParams {
   float ln_e_lo, inv_dln_e;   // table grid: ln E = ln_e_lo + i / inv_dln_e
   int chunk;                  // histories per warp work grab
   int max_steps;
+  int regroup_compton;        // regrouped variant: lanes that must wait before a Compton pass
+  int regroup_refill;         // regrouped variant: lanes that must wait before a refill pass
 };
 
 enum CounterSlot {

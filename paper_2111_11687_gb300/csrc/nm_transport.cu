@@ -230,7 +230,14 @@ __global__ void __launch_bounds__(512) transport_kernel(const TransportParams p)
     }
     // ---- refill: lanes without a photon take new histories from the pool ----
     const unsigned need = __ballot_sync(kFull, !alive && !done);
-    if (need) {
+    // Regrouped: new histories are started for many lanes at once, once enough
+    // lanes wait or nothing else can fly.
+    bool refill = need != 0;
+    if (REGROUP && refill) {
+      const unsigned flying = __ballot_sync(kFull, alive && !pending_c);
+      refill = __popc(need) >= (unsigned)p.regroup_refill || flying == 0;
+    }
+    if (refill) {
       const uint32_t cnt = __popc(need);
       const uint64_t avail = pool_end > pool_next ? pool_end - pool_next : 0;
       uint64_t fresh = 0;
@@ -270,7 +277,7 @@ __global__ void __launch_bounds__(512) transport_kernel(const TransportParams p)
       }
       tally_flush<WARP_AGG>(p.tally, has, dv, (uint32_t)p.q_positron, lane);
     }
-    if (!__any_sync(kFull, alive)) break;
+    if (!__any_sync(kFull, alive || !done)) break;
 
     bool has = false;
     int dv = 0;
@@ -279,7 +286,7 @@ __global__ void __launch_bounds__(512) transport_kernel(const TransportParams p)
     if (REGROUP) {
       const unsigned waiting = __ballot_sync(kFull, pending_c);
       const unsigned flying = __ballot_sync(kFull, alive && !pending_c);
-      if (waiting && (__popc(waiting) >= 12 || flying == 0)) {
+      if (waiting && (__popc(waiting) >= (unsigned)p.regroup_compton || flying == 0)) {
         if (pending_c) {
           pending_c = false;
           uint32_t rphi;

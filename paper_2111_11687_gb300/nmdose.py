@@ -48,7 +48,8 @@ class nm_options(C.Structure):
     _fields_ = [("source_mode", C.c_int32), ("point", C.c_float * 3), ("photon_mev", C.c_double),
                 ("positron_mev", C.c_double), ("batches", C.c_int32), ("activity_bq", C.c_double),
                 ("n_labels", C.c_int32), ("block_threads", C.c_int32), ("chunk", C.c_int32),
-                ("warp_aggregate", C.c_int32), ("regroup", C.c_int32), ("max_steps", C.c_int32),
+                ("warp_aggregate", C.c_int32), ("regroup", C.c_int32), ("regroup_lanes", C.c_int32),
+                ("max_steps", C.c_int32),
                 ("stream", C.c_void_p)]
 
 
@@ -59,7 +60,7 @@ class nm_counters(C.Structure):
                 ("rayleigh", C.c_uint64), ("cutoff", C.c_uint64), ("escapes", C.c_uint64),
                 ("transport_ms", C.c_double), ("fold_ms", C.c_double), ("device_status", C.c_uint32),
                 ("block_threads", C.c_int32), ("chunk", C.c_int32), ("warp_aggregate", C.c_int32),
-                ("regroup", C.c_int32), ("grid_blocks", C.c_int32)]
+                ("regroup", C.c_int32), ("regroup_lanes", C.c_int32), ("grid_blocks", C.c_int32)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
