@@ -1,5 +1,6 @@
 // C ABI of libnmdose (include/nm_dose.h): argument checks, device memory,
 // the batch loop of nm_dose_run, and the read-out calls.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -90,8 +91,9 @@ struct nm_dose {
   ull* tsum = nullptr;
   double* s2 = nullptr;
   float* kn = nullptr;
+  float* minv = nullptr;
   ull* counters = nullptr;     // kCtrCount
-  ull* work = nullptr;
+  unsigned* work = nullptr;
   uint32_t* status = nullptr;
   uint32_t* rho_max_bits = nullptr;
   double* org_s1 = nullptr;
@@ -110,7 +112,7 @@ struct nm_dose {
   std::vector<cudaEvent_t> ev;
 
   ~nm_dose() {
-    void* ptrs[] = {vox, density, labels, alias, tb, tsum, s2, kn, counters, work, status,
+    void* ptrs[] = {vox, density, labels, alias, tb, tsum, s2, kn, minv, counters, work, status,
                     rho_max_bits, org_s1, org_s2, organ_count, organ_partial, organ_out,
                     out_dose, out_sigma};
     for (void* p : ptrs)
@@ -128,6 +130,7 @@ struct nm_dose {
     p.work = work;
     p.status = status;
     p.kn = kn;
+    p.minv = minv;
     p.nx = nx; p.ny = ny; p.nz = nz;
     p.fnx = (float)nx; p.fny = (float)ny; p.fnz = (float)nz;
     p.inv_dx = 1.0f / dx; p.inv_dy = 1.0f / dy; p.inv_dz = 1.0f / dz;
@@ -300,6 +303,7 @@ nm_status nm_dose_create(nm_dose** out, const nm_grid* g, const nm_materials* mt
 
   if ((e = dalloc(&h->vox, V)) || (e = dalloc(&h->density, V)) || (e = dalloc(&h->tb, V)) ||
       (e = dalloc(&h->tsum, V)) || (e = dalloc(&h->s2, V)) || (e = dalloc(&h->kn, kKnTable)) ||
+      (e = dalloc(&h->minv, kKnTable)) ||
       (e = dalloc(&h->counters, kCtrCount)) || (e = dalloc(&h->work, 1)) ||
       (e = dalloc(&h->status, 1)) || (e = dalloc(&h->rho_max_bits, NM_MAX_MATERIALS)) ||
       (e = dalloc(&h->org_s1, kLabelSlots)) || (e = dalloc(&h->org_s2, kLabelSlots)) ||
@@ -344,6 +348,26 @@ nm_status nm_dose_create(nm_dose** out, const nm_grid* g, const nm_materials* mt
     memcpy(&r, &rho_bits[m], 4);
     h->mat[m].rho_max = m < h->n_mat ? r : 0.0f;
   }
+  // Woodcock majorant per table bin [E_i, E_i+1): every mu/rho decreases with E,
+  // so the value at E_i over all materials at their largest density bounds mu
+  // on the whole bin.  Evaluated in FP64 from the FP32 coefficients the kernel
+  // uses, with a 1e-4 margin for the kernel's FP32 rounding and ln E error,
+  // and stored as a reciprocal rounded down.
+  std::vector<float> minv(kKnTable);
+  for (int i = 0; i < kKnTable; ++i) {
+    const double ei = std::exp(std::log(e_lo) + i * dln);
+    double maj = 0.0;
+    for (int m = 0; m < h->n_mat; ++m) {
+      const double mu = (double)h->mat[m].za * (double)kn[i] +
+                        (double)h->mat[m].zp / (ei * ei * ei) +
+                        (double)h->mat[m].zr / (ei * ei);
+      maj = std::max(maj, (double)h->mat[m].rho_max * mu);
+    }
+    maj *= 1.0 + 1e-4;
+    minv[i] = std::nextafter((float)(1.0 / maj), 0.0f);
+  }
+  if ((e = cudaMemcpy(h->minv, minv.data(), kKnTable * sizeof(float), cudaMemcpyHostToDevice)))
+    return bail(cuda_fail(e, "majorant table"));
 
   // Decay sampler: alias table over the active voxels, FP64 on the device.
   if (o.source_mode == NM_SOURCE_DECAY) {
@@ -405,11 +429,16 @@ nm_status nm_dose_run(nm_dose* h, uint64_t n, uint64_t seed) {
   fp.deposited = h->counters + kCtrDepositedUnits;
   for (int b = 0; b < B; ++b) {
     const uint64_t nb = n / B + ((uint64_t)b < n % B ? 1 : 0);
-    const TransportParams p = h->params(h->hist_next, nb, seed);
-    NM_CUDA(cudaMemsetAsync(h->work, 0, sizeof(ull), s), "cudaMemsetAsync");
     NM_CUDA(cudaEventRecord(h->ev[4 * b + 0], s), "cudaEventRecord");
-    NM_CUDA(launch_transport(p, h->grid, h->block, h->warp_agg, h->rayleigh, h->regroup, s),
-            "transport launch");
+    // A launch hands out at most 2^31 histories (32-bit work counter).
+    for (uint64_t done = 0; done < nb;) {
+      const uint64_t part = std::min<uint64_t>(nb - done, 1ull << 31);
+      const TransportParams p = h->params(h->hist_next + done, part, seed);
+      NM_CUDA(cudaMemsetAsync(h->work, 0, sizeof(unsigned), s), "cudaMemsetAsync");
+      NM_CUDA(launch_transport(p, h->grid, h->block, h->warp_agg, h->rayleigh, h->regroup, s),
+              "transport launch");
+      done += part;
+    }
     NM_CUDA(cudaEventRecord(h->ev[4 * b + 1], s), "cudaEventRecord");
     fp.n_b = (double)nb;
     NM_CUDA(cudaEventRecord(h->ev[4 * b + 2], s), "cudaEventRecord");

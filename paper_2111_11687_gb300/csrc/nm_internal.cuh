@@ -59,7 +59,7 @@ struct MaterialCoef {
   float za;       // (Z/A) * N_A * sigma-table scale: mu_c/rho = za * kn(E)
   float zp;       // pe_coeff * Zeff^pe_exp:            mu_pe/rho = zp / E^3
   float zr;       // rayleigh_coeff * Zeff^2:           mu_R/rho = zr / E^2
-  float rho_max;  // largest density of this material in the grid
+  float rho_max;  // largest density of this material in the grid (host side)
 };
 
 struct TransportParams {
@@ -67,9 +67,10 @@ struct TransportParams {
   const uint4* alias;         // {prob bits, voxel, alias voxel, 0}
   ull* tally;                 // batch tally, units
   ull* counters;              // device counters (see CounterSlot)
-  ull* work;                  // histories handed out in this launch
+  unsigned* work;             // histories handed out in this launch (< 2^32 per launch)
   uint32_t* status;           // NM_DEV_* flags
   const float* kn;            // kKnTable nodes of N_A * sigma_KN(E)
+  const float* minv;          // kKnTable bins: 1 / majorant (cm) on [E_i, E_i+1)
   int nx, ny, nz;
   float fnx, fny, fnz;        // grid size as float (voxel units)
   float inv_dx, inv_dy, inv_dz;

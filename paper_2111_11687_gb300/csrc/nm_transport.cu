@@ -25,14 +25,17 @@ constexpr int kKahnTrialLimit = 1000;
 
 struct Energy {
   float s_c, s_pe, s_r;   // per-unit-density factors: mu/rho = za s_c + zp s_pe + zr s_r
-  float mubar;            // majorant (1/cm) over all materials at their largest density
-  float inv_mubar;
+  float inv_mubar;        // 1 / majorant (cm) over all materials at their largest density
 };
 
+// Energy-dependent factors, computed once per energy change.  s_c is
+// interpolated in ln E from the Klein-Nishina table; the majorant is constant
+// over a table bin and taken at the bin's lower edge, which bounds every
+// material's mu on the whole bin because all three mu/rho decrease with E.
 template <bool RAYLEIGH>
 __device__ __forceinline__ Energy energy_factors(float e, const float* __restrict__ kn,
-                                                 const MaterialCoef* __restrict__ mat, int n_mat,
-                                                 float ln_lo, float inv_dln) {
+                                                 const float* __restrict__ minv, float ln_lo,
+                                                 float inv_dln) {
   Energy f;
   float x = (__logf(e) - ln_lo) * inv_dln;
   x = fminf(fmaxf(x, 0.0f), (float)(kKnTable - 1) - 0x1p-10f);
@@ -44,16 +47,7 @@ __device__ __forceinline__ Energy energy_factors(float e, const float* __restric
   const float ie2 = ie * ie;
   f.s_pe = ie2 * ie;
   f.s_r = RAYLEIGH ? ie2 : 0.0f;
-  float mb = 0.0f;
-  for (int m = 0; m < n_mat; ++m) {
-    const MaterialCoef c = mat[m];
-    const float t = fmaf(c.zr, f.s_r, fmaf(c.zp, f.s_pe, c.za * f.s_c));
-    mb = fmaxf(mb, c.rho_max * t);
-  }
-  // Each voxel evaluates the same nested expression with rho <= rho_max, and
-  // rounded products are monotone, so mu_voxel <= mb; the margin is for safety.
-  f.mubar = mb * (1.0f + 0x1p-20f);
-  f.inv_mubar = 1.0f / f.mubar;
+  f.inv_mubar = minv[i];
   return f;
 }
 
@@ -191,79 +185,116 @@ __device__ __forceinline__ ull warp_sum(ull x) {
   return x;
 }
 
+// Compton event at energy e: Kahn-sampled angle, new energy and direction, and
+// the local deposit (the electron's energy, or everything below the cutoff).
+template <bool RAYLEIGH>
+__device__ __forceinline__ void compton(const TransportParams& p, const float* s_kn,
+                                        const float* s_minv, float& e, int32_t& qe, Energy& f,
+                                        float& ux, float& uy, float& uz, uint32_t& ctr,
+                                        uint32_t stream, uint32_t hlo, uint32_t hhi,
+                                        bool& alive, uint32_t& dq, uint32_t& flags,
+                                        unsigned long long* s_cnt) {
+  uint32_t rphi;
+  const float k = e * kInvElectronMassMeV;
+  const float x = kahn_x(k, ctr, stream, hlo, hhi, p.key0, p.key1, rphi, flags);
+  const float e2 = e / fmaf(k, x, 1.0f);
+  rotate(ux, uy, uz, 1.0f - x, fmaf(kTwoPi, u01(rphi), -3.14159265f));
+  if (e2 < p.cut) {
+    dq = (uint32_t)qe;
+    alive = false;
+    atomicAdd(&s_cnt[1], 1ull);
+  } else {
+    const int32_t q2 = q_units(e2);
+    dq = (uint32_t)(qe - q2);
+    e = e2;
+    qe = q2;
+    f = energy_factors<RAYLEIGH>(e, s_kn, s_minv, p.ln_e_lo, p.inv_dln_e);
+  }
+}
+
 template <bool WARP_AGG, bool RAYLEIGH, bool REGROUP>
-__global__ void __launch_bounds__(512) transport_kernel(const TransportParams p) {
+__global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams p) {
   __shared__ float s_kn[kKnTable];
+  __shared__ float s_minv[kKnTable];
   __shared__ MaterialCoef s_mat[NM_MAX_MATERIALS];
-  for (int i = threadIdx.x; i < kKnTable; i += blockDim.x) s_kn[i] = p.kn[i];
+  __shared__ Energy s_f0;
+  __shared__ unsigned long long s_cnt[4];   // photo, cutoff, rayleigh, killed units
+  extern __shared__ float s_site[];         // [6][blockDim]: decay site and photon A direction
+  for (int i = threadIdx.x; i < kKnTable; i += blockDim.x) {
+    s_kn[i] = p.kn[i];
+    s_minv[i] = p.minv[i];
+  }
   if (threadIdx.x < NM_MAX_MATERIALS) s_mat[threadIdx.x] = p.mat[threadIdx.x];
+  if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0;
   __syncthreads();
+  if (threadIdx.x == 0) s_f0 = energy_factors<RAYLEIGH>(p.e0, s_kn, s_minv, p.ln_e_lo, p.inv_dln_e);
+  __syncthreads();
+  float* site = s_site + threadIdx.x;
+  const int nb = blockDim.x;
 
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t lt_mask = (1u << lane) - 1u;
-  const Energy f0 = energy_factors<RAYLEIGH>(p.e0, s_kn, s_mat, p.n_mat, p.ln_e_lo, p.inv_dln_e);
-
-  uint64_t pool_next = 0, pool_end = 0;  // warp-uniform
+  uint32_t pool_next = 0, pool_end = 0;  // warp-uniform, relative to hist_begin
   bool done = false, alive = false, pending_b = false, pending_c = false;
   float px = 0.f, py = 0.f, pz = 0.f, ux = 0.f, uy = 0.f, uz = 0.f;
-  float bx = 0.f, by = 0.f, bz = 0.f;    // decay site, for photon B
-  float au = 0.f, av = 0.f, aw = 0.f;    // photon A's initial direction
   float e = 0.f;
-  Energy f = f0;
+  Energy f = s_f0;
   int32_t qe = 0;
   int cv = 0;                            // voxel of a pending Compton event
   uint32_t hlo = 0, hhi = 0, stream = 0, ctr = 0, spare0 = 0, spare1 = 0;
   bool have_spare = false;
   int steps = 0;
-  uint32_t n_steps = 0, n_compton = 0, n_photo = 0, n_rayl = 0, n_cut = 0, n_esc = 0, flags = 0;
-  ull escaped = 0, killed = 0;
+  uint32_t n_steps = 0, n_compton = 0, n_esc = 0, flags = 0;
+  ull escaped = 0;
 
   for (;;) {
     // ---- second photon of the decay: same site, opposite direction ----------
     if (!alive && pending_b) {
       pending_b = false;
       alive = true;
-      px = bx; py = by; pz = bz;
-      ux = -au; uy = -av; uz = -aw;
-      e = p.e0; qe = p.q_e0; f = f0;
+      px = site[0]; py = site[nb]; pz = site[2 * nb];
+      ux = -site[3 * nb]; uy = -site[4 * nb]; uz = -site[5 * nb];
+      e = p.e0; qe = p.q_e0; f = s_f0;
       stream = kStreamPhotonB; ctr = 0; have_spare = false; steps = 0;
     }
     // ---- refill: lanes without a photon take new histories from the pool ----
     const unsigned need = __ballot_sync(kFull, !alive && !done);
-    // Regrouped: new histories are started for many lanes at once, once enough
-    // lanes wait or nothing else can fly.
     bool refill = need != 0;
     if (REGROUP && refill) {
+      // Start new histories for many lanes at once, once enough lanes wait or
+      // nothing else can fly.
       const unsigned flying = __ballot_sync(kFull, alive && !pending_c);
       refill = __popc(need) >= (unsigned)p.regroup_refill || flying == 0;
     }
     if (refill) {
       const uint32_t cnt = __popc(need);
-      const uint64_t avail = pool_end > pool_next ? pool_end - pool_next : 0;
-      uint64_t fresh = 0;
+      const uint32_t avail = pool_end > pool_next ? pool_end - pool_next : 0u;
+      uint32_t fresh = 0;
       if (avail < cnt) {
-        if (lane == 0) fresh = atomicAdd(p.work, (ull)p.chunk);
+        if (lane == 0) fresh = atomicAdd(p.work, (unsigned)p.chunk);
         fresh = __shfl_sync(kFull, fresh, 0);
       }
       bool has = false;
       int dv = 0;
       if (!alive && !done) {
         const uint32_t rank = __popc(need & lt_mask);
-        const uint64_t idx = rank < avail ? pool_next + rank : fresh + (rank - avail);
+        const uint64_t idx = rank < avail ? (uint64_t)pool_next + rank : (uint64_t)fresh + (rank - avail);
         if (idx < p.n_hist) {
           const uint64_t h = p.hist_begin + idx;
           hlo = (uint32_t)h;
           hhi = (uint32_t)(h >> 32);
-          const Site s = sample_site(p, hlo, hhi);
-          px = bx = s.x; py = by = s.y; pz = bz = s.z;
-          ux = au = s.u; uy = av = s.v_; uz = aw = s.w;
-          e = p.e0; qe = p.q_e0; f = f0;
+          const Site st = sample_site(p, hlo, hhi);
+          px = st.x; py = st.y; pz = st.z;
+          ux = st.u; uy = st.v_; uz = st.w;
+          e = p.e0; qe = p.q_e0; f = s_f0;
           stream = kStreamPhotonA; ctr = 0; have_spare = false; steps = 0;
           alive = true;
           if (p.source_mode == NM_SOURCE_DECAY) {
+            site[0] = st.x; site[nb] = st.y; site[2 * nb] = st.z;
+            site[3 * nb] = st.u; site[4 * nb] = st.v_; site[5 * nb] = st.w;
             pending_b = true;
             has = p.q_positron > 0;
-            dv = s.v;
+            dv = st.v;
           }
         } else {
           done = true;
@@ -271,7 +302,7 @@ __global__ void __launch_bounds__(512) transport_kernel(const TransportParams p)
       }
       if (avail < cnt) {
         pool_next = fresh + (cnt - avail);
-        pool_end = fresh + (uint64_t)p.chunk;
+        pool_end = fresh + (uint32_t)p.chunk;
       } else {
         pool_next += cnt;
       }
@@ -282,31 +313,17 @@ __global__ void __launch_bounds__(512) transport_kernel(const TransportParams p)
     bool has = false;
     int dv = 0;
     uint32_t dq = 0;
-    // ---- Compton interaction (regrouped: run when enough lanes wait) --------
+    // ---- Compton passes (regrouped: run when enough lanes wait) -------------
     if (REGROUP) {
       const unsigned waiting = __ballot_sync(kFull, pending_c);
       const unsigned flying = __ballot_sync(kFull, alive && !pending_c);
       if (waiting && (__popc(waiting) >= (unsigned)p.regroup_compton || flying == 0)) {
         if (pending_c) {
           pending_c = false;
-          uint32_t rphi;
-          const float k = e * kInvElectronMassMeV;
-          const float x = kahn_x(k, ctr, stream, hlo, hhi, p.key0, p.key1, rphi, flags);
-          const float e2 = e / fmaf(k, x, 1.0f);
-          rotate(ux, uy, uz, 1.0f - x, fmaf(kTwoPi, u01(rphi), -3.14159265f));
-          const int32_t q2 = q_units(e2);
+          compton<RAYLEIGH>(p, s_kn, s_minv, e, qe, f, ux, uy, uz, ctr, stream, hlo, hhi, alive, dq,
+                            flags, s_cnt);
           has = true;
           dv = cv;
-          if (e2 < p.cut) {
-            dq = (uint32_t)qe;
-            ++n_cut;
-            alive = false;
-          } else {
-            dq = (uint32_t)(qe - q2);
-            e = e2;
-            qe = q2;
-            f = energy_factors<RAYLEIGH>(e, s_kn, s_mat, p.n_mat, p.ln_e_lo, p.inv_dln_e);
-          }
         }
       }
     }
@@ -332,44 +349,31 @@ __global__ void __launch_bounds__(512) transport_kernel(const TransportParams p)
       } else {
         const int v = ((int)pz * p.ny + (int)py) * p.nx + (int)px;
         const uint32_t wv = __ldg(p.vox + v);
-        const float rho = __uint_as_float(wv & ~7u);
         const MaterialCoef c = s_mat[wv & 7u];
+        // real event with probability mu(voxel)/mubar; the same uniform picks the type
+        const float scale = __uint_as_float(wv & ~7u) * f.inv_mubar;
         const float ic = c.za * f.s_c;
         const float icp = fmaf(c.zp, f.s_pe, ic);
-        const float t = u01(r1) * f.mubar;
-        if (t < rho * ic) {
+        const float t = u01(r1);
+        if (t < scale * ic) {
           ++n_compton;
           if (REGROUP) {
             pending_c = true;
             cv = v;
           } else {
-            uint32_t rphi;
-            const float k = e * kInvElectronMassMeV;
-            const float x = kahn_x(k, ctr, stream, hlo, hhi, p.key0, p.key1, rphi, flags);
-            const float e2 = e / fmaf(k, x, 1.0f);
-            rotate(ux, uy, uz, 1.0f - x, fmaf(kTwoPi, u01(rphi), -3.14159265f));
-            const int32_t q2 = q_units(e2);
+            compton<RAYLEIGH>(p, s_kn, s_minv, e, qe, f, ux, uy, uz, ctr, stream, hlo, hhi, alive,
+                              dq, flags, s_cnt);
             has = true;
             dv = v;
-            if (e2 < p.cut) {
-              dq = (uint32_t)qe;
-              ++n_cut;
-              alive = false;
-            } else {
-              dq = (uint32_t)(qe - q2);
-              e = e2;
-              qe = q2;
-              f = energy_factors<RAYLEIGH>(e, s_kn, s_mat, p.n_mat, p.ln_e_lo, p.inv_dln_e);
-            }
           }
-        } else if (t < rho * icp) {
-          ++n_photo;
+        } else if (t < scale * icp) {
+          atomicAdd(&s_cnt[0], 1ull);
           has = true;
           dv = v;
           dq = (uint32_t)qe;
           alive = false;
-        } else if (RAYLEIGH && t < rho * fmaf(c.zr, f.s_r, icp)) {
-          ++n_rayl;
+        } else if (RAYLEIGH && t < scale * fmaf(c.zr, f.s_r, icp)) {
+          atomicAdd(&s_cnt[2], 1ull);
           // Thomson angular shape (1 + cos^2)/2 by rejection; one block per trial.
           for (int trial = 0;; ++trial) {
             const uint4 r = draw(ctr, stream, hlo, hhi, p.key0, p.key1);
@@ -381,25 +385,31 @@ __global__ void __launch_bounds__(512) transport_kernel(const TransportParams p)
           }
         }
       }
-      if (alive && steps >= p.max_steps) {
-        killed += (ull)qe;
+      if (alive && !pending_c && steps >= p.max_steps) {
+        atomicAdd(&s_cnt[3], (ull)qe);
         flags |= NM_DEV_STEP_LIMIT;
         alive = false;
-        pending_c = false;
       }
     }
     tally_flush<WARP_AGG>(p.tally, has, dv, dq, lane);
   }
 
   // ---- counters: warp sums, one atomic per warp per counter ----------------
-  const ull cs[8] = {n_steps, n_compton, n_photo, n_rayl, n_cut, n_esc, escaped, killed};
+  const ull cs[4] = {n_steps, n_compton, n_esc, escaped};
+  const int slot[4] = {kCtrSteps, kCtrCompton, kCtrEscapes, kCtrEscapedUnits};
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
+  for (int i = 0; i < 4; ++i) {
     const ull s = warp_sum(cs[i]);
-    if (lane == 0 && s) atomicAdd(p.counters + i, s);
+    if (lane == 0 && s) atomicAdd(p.counters + slot[i], s);
   }
   const unsigned fl = __reduce_or_sync(kFull, flags);
   if (lane == 0 && fl) atomicOr(p.status, fl);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int slot2[4] = {kCtrPhoto, kCtrCutoff, kCtrRayleigh, kCtrKilledUnits};
+    for (int i = 0; i < 4; ++i)
+      if (s_cnt[i]) atomicAdd(p.counters + slot2[i], s_cnt[i]);
+  }
 }
 
 __global__ void check_philox_kernel(const uint4* ctr, const uint2* key, int64_t n, uint4* out) {
@@ -433,6 +443,8 @@ __global__ void check_source_kernel(const TransportParams p, uint64_t first, int
   dir[3 * i + 2] = s.w;
 }
 
+size_t transport_smem(int block) { return (size_t)6 * block * sizeof(float); }
+
 template <bool A, bool R, bool G>
 void* kernel_ptr() {
   return (void*)transport_kernel<A, R, G>;
@@ -453,7 +465,7 @@ cudaError_t launch_transport(const TransportParams& p, int grid, int block, bool
                              bool rayleigh, bool regroup, cudaStream_t s) {
   void* fn = pick(warp_agg, rayleigh, regroup);
   void* args[] = {(void*)&p};
-  const cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(block), args, 0, s);
+  const cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(block), args, transport_smem(block), s);
   if (e != cudaSuccess) cudaGetLastError();  // a refused launch must not linger as the last error
   return e;
 }
@@ -461,7 +473,7 @@ cudaError_t launch_transport(const TransportParams& p, int grid, int block, bool
 int transport_max_blocks_per_sm(int block, bool warp_agg, bool rayleigh, bool regroup) {
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick(warp_agg, rayleigh, regroup), block,
-                                                    0) != cudaSuccess)
+                                                    transport_smem(block)) != cudaSuccess)
     return 0;
   return n;
 }
