@@ -385,10 +385,11 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
           }
         }
       }
-      if (alive && !pending_c && steps >= p.max_steps) {
+      if (alive && steps >= p.max_steps) {
         atomicAdd(&s_cnt[3], (ull)qe);
         flags |= NM_DEV_STEP_LIMIT;
         alive = false;
+        pending_c = false;
       }
     }
     tally_flush<WARP_AGG>(p.tally, has, dv, dq, lane);
