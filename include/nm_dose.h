@@ -197,6 +197,37 @@ nm_status nm_dose_alias_table(nm_dose* h, int64_t* n_active, float* prob, int32_
 nm_status nm_check_source(nm_dose* h, uint64_t first, int64_t n, uint64_t seed, int32_t* voxel,
                           float* pos, float* dir);
 
+/* ---- Tally without device allocation ---------------------------------------
+ *
+ * For callers that cannot call cudaMalloc -- code running inside another
+ * framework's memory pool or arena, real-time or safety-constrained services
+ * that forbid allocation after start-up, hosts that hand the library only
+ * pre-allocated buffers.  The paper has no counterpart: it is a deployment
+ * variant of nm_dose_create + nm_dose_run + nm_dose_get_tally.
+ *
+ * Computes the cumulative tally of histories 0..n_decays-1 (seed as in
+ * nm_dose_run; bit-identical to a handle's tally after nm_dose_run(n_decays,
+ * seed)) into tally[V] (int64 energy units, device memory, overwritten).
+ * grid->density, grid->material, activity (decay mode) and tally must be
+ * device pointers; materials and opts are host structs as for nm_dose_create;
+ * labels and batch statistics are not part of this call.  counters may be NULL;
+ * its deposited field is emitted - escaped - killed.
+ *
+ * All working memory (packed voxels, alias table and its FP64 scans, physics
+ * tables, counters) lives in one fixed device array of 24 MiB that every GPU
+ * which loads the library holds until the process exits; grids above 2^18
+ * voxels (64^3) are rejected with NM_ERR_ARG.  The call allocates no device
+ * memory.  Its first call on a device looks up that array's device address
+ * (with the device current) and keeps it; make that first call before any
+ * stream capture.  Every call uses the same array, so calls that overlap on
+ * the GPU (other streams or threads, the same device) race and must be
+ * serialised by the caller; nothing in the array needs clearing between
+ * calls.  The call synchronises opts->stream. */
+nm_status nm_dose_tally_noalloc(const nm_grid* grid, const nm_materials* materials,
+                                const float* activity, const nm_options* opts,
+                                uint64_t n_decays, uint64_t seed, int64_t* tally,
+                                nm_counters* counters);
+
 #ifdef __cplusplus
 }
 #endif

@@ -187,6 +187,12 @@ void nm_options_default(nm_options* o) {
 
 const char* nm_last_error(void) { return g_err.c_str(); }
 
+}  // extern "C"
+
+void nm::set_error_message(const char* msg) { g_err = msg; }
+
+extern "C" {
+
 nm_status nm_ct_to_phantom(const int16_t* hu, int64_t n, float* density, uint8_t* material,
                            void* stream) {
   if (n < 0 || (n > 0 && (!hu || !density || !material)))

@@ -98,6 +98,9 @@ enum CounterSlot {
   kCtrEscapedUnits, kCtrKilledUnits, kCtrDepositedUnits, kCtrCount
 };
 
+// Sets the message that nm_last_error() returns on the calling thread.
+void set_error_message(const char* msg);
+
 // ---- launchers (host side), one translation unit each ---------------------
 cudaError_t launch_transport(const TransportParams& p, int grid, int block, bool warp_agg,
                              bool rayleigh, bool regroup, cudaStream_t s);

@@ -84,6 +84,9 @@ _SIGS = {
     "nm_check_kahn": (C.c_int, [C.c_double, C.c_int64, C.c_uint64, C.c_void_p]),
     "nm_dose_alias_table": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.c_void_p, C.c_void_p, C.c_void_p]),
     "nm_check_source": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int64, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "nm_dose_tally_noalloc": (C.c_int, [C.POINTER(nm_grid), C.POINTER(nm_materials), C.c_void_p,
+                                        C.POINTER(nm_options), C.c_uint64, C.c_uint64, C.c_void_p,
+                                        C.POINTER(nm_counters)]),
 }
 
 
@@ -251,6 +254,20 @@ def nm_check_source(h, first: int, n: int, seed: int):
     d = np.empty((n, 3), np.float32)
     _check(load().nm_check_source(h, first, n, seed, ptr(vox), ptr(pos), ptr(d)))
     return vox, pos, d
+
+
+def nm_dose_tally_noalloc(density, material, spacing, materials: Materials, tally, n_decays: int, seed: int,
+                          activity=None, opts: nm_options | None = None) -> dict:
+    """Tally without device allocation; density, material, activity and tally must
+    be device tensors.  Returns the counters."""
+    nz, ny, nx = density.shape
+    g = nm_grid(nx, ny, nz, float(spacing[0]), float(spacing[1]), float(spacing[2]), ptr(density), ptr(material))
+    m = materials.c()
+    c = nm_counters()
+    _check(load().nm_dose_tally_noalloc(C.byref(g), C.byref(m), ptr(activity),
+                                        C.byref(opts) if opts is not None else None,
+                                        int(n_decays), int(seed), ptr(tally), C.byref(c)))
+    return c.as_dict()
 
 
 class Dose:
