@@ -149,6 +149,20 @@ nm_status nm_dose_create(nm_dose** out, const nm_grid* grid, const nm_materials*
  * NM_ERR_DEVICE if a device check fired (the batch is still folded). */
 nm_status nm_dose_run(nm_dose* h, uint64_t n_decays, uint64_t seed);
 
+/* Many patients in one launch (the paper runs one patient at a time; this is
+ * the batched form of nm_dose_run).  Runs n_decays[i] more histories on each
+ * handle hs[i] (i < n <= 64) with seed `seed`, in the handles' common number
+ * of batches: per batch one persistent transport launch whose warps drain
+ * per-patient work queues, moving to the next patient when one runs dry, then
+ * every patient's fold; all batches are captured into one CUDA graph and
+ * launched once on the first handle's stream.  Handles must be distinct and
+ * share materials, energies, batches, max_steps and device; grids may differ.
+ * Each handle's tally is bit-identical to nm_dose_run(hs[i], n_decays[i],
+ * seed).  The launch shape is the first handle's explicit options, else
+ * chosen by timed trials on the batch (cached per batch geometry).  Errors as
+ * for nm_dose_run; NM_ERR_ARG for mismatched handles. */
+nm_status nm_dose_run_batch(nm_dose* const* hs, int32_t n, const uint64_t* n_decays, uint64_t seed);
+
 /* Eq. 1: dose rate D/N_evts * A(t_s) per voxel (Gy/s) into dose[V], and the
  * batch standard deviation of that mean into sigma[V] (Gy/s); either may be
  * NULL.  organ_dose[n_labels + 1]: Eq. 2 organ means (index = label; index 0

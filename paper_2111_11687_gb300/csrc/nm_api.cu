@@ -5,7 +5,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "nm_internal.cuh"
@@ -110,6 +113,9 @@ struct nm_dose {
   double transport_ms = 0, fold_ms = 0;
   int block = 256, chunk = 256, warp_agg = 0, regroup = 0, regroup_lanes = 12, grid = 0;
   std::vector<cudaEvent_t> ev;
+  std::vector<float> minv_host;   // host copy of the majorant table
+  bool tuned = false;             // launch shape chosen by the autotuner
+  double batch_graph_ms = 0;      // device time of graphs launched by nm_dose_run_batch
 
   ~nm_dose() {
     void* ptrs[] = {vox, density, labels, alias, tb, tsum, s2, kn, minv, counters, work, status,
@@ -120,30 +126,37 @@ struct nm_dose {
     for (auto e : ev) cudaEventDestroy(e);
   }
 
+  PatientGeom geom(uint64_t first, uint64_t n) const {
+    PatientGeom g;
+    memset(&g, 0, sizeof g);
+    g.vox = vox;
+    g.alias = alias;
+    g.tally = tb;
+    g.counters = counters;
+    g.work = work;
+    g.n_active = (uint64_t)n_active;
+    g.hist_begin = first;
+    g.n_hist = n;
+    g.nx = nx; g.ny = ny; g.nz = nz;
+    g.fnx = (float)nx; g.fny = (float)ny; g.fnz = (float)nz;
+    g.inv_dx = 1.0f / dx; g.inv_dy = 1.0f / dy; g.inv_dz = 1.0f / dz;
+    g.source_mode = opt.source_mode;
+    g.px = opt.point[0] / dx; g.py = opt.point[1] / dy; g.pz = opt.point[2] / dz;
+    g.q_positron = q_pos;
+    return g;
+  }
+
   TransportParams params(uint64_t first, uint64_t n, uint64_t seed) const {
     TransportParams p;
     memset(&p, 0, sizeof p);
-    p.vox = vox;
-    p.alias = alias;
-    p.tally = tb;
-    p.counters = counters;
-    p.work = work;
+    p.g = geom(first, n);
     p.status = status;
     p.kn = kn;
     p.minv = minv;
-    p.nx = nx; p.ny = ny; p.nz = nz;
-    p.fnx = (float)nx; p.fny = (float)ny; p.fnz = (float)nz;
-    p.inv_dx = 1.0f / dx; p.inv_dy = 1.0f / dy; p.inv_dz = 1.0f / dz;
-    p.n_active = (uint64_t)n_active;
-    p.hist_begin = first;
-    p.n_hist = n;
     p.key0 = (uint32_t)seed;
     p.key1 = (uint32_t)(seed >> 32);
-    p.source_mode = opt.source_mode;
-    p.px = opt.point[0] / dx; p.py = opt.point[1] / dy; p.pz = opt.point[2] / dz;
     p.e0 = e0;
     p.q_e0 = q_e0;
-    p.q_positron = q_pos;
     p.cut = cut;
     p.n_mat = n_mat;
     for (int m = 0; m < NM_MAX_MATERIALS; ++m) p.mat[m] = mat[m];
@@ -220,21 +233,138 @@ nm_status nm_ct_to_phantom(const int16_t* hu, int64_t n, float* density, uint8_t
   return st;
 }
 
+// ---------------------------------------------------------------------------
+// Launch shape: explicit options win; every knob left on "auto" is chosen by
+// timed trial launches on the handle's own phantom (coordinate descent over
+// Compton/new-history regrouping, CTA size and work-chunk size, then warp
+// aggregation), cached per (device, grid, source mode, Rayleigh).  Trials use
+// history ids above 2^62, which runs never reach, and their tallies and
+// counters are cleared afterwards; any shape gives bit-identical results.
+// ---------------------------------------------------------------------------
+struct Shape {
+  int block, chunk, warp_agg, regroup, lanes;
+  bool operator<(const Shape& o) const {
+    return std::tie(block, chunk, warp_agg, regroup, lanes) <
+           std::tie(o.block, o.chunk, o.warp_agg, o.regroup, o.lanes);
+  }
+};
+
+typedef std::tuple<int, int, int, int, int, int, int> TuneKey;
+static std::mutex g_tune_mu;
+static std::map<TuneKey, Shape> g_tune_cache;
+
+static int grid_for_shape(const nm_dose* h, const Shape& sh, bool multi) {
+  const int per_sm = transport_max_blocks_per_sm(sh.block, sh.warp_agg, h->rayleigh, sh.regroup, multi);
+  return per_sm * h->sms;
+}
+
+static void apply_shape(nm_dose* h, const Shape& sh) {
+  h->block = sh.block;
+  h->chunk = sh.chunk;
+  h->warp_agg = sh.warp_agg;
+  h->regroup = sh.regroup;
+  h->regroup_lanes = sh.lanes;
+  h->grid = grid_for_shape(h, sh, false);
+}
+
+static nm_status autotune(nm_dose* h, Shape sh, bool free_block, bool free_chunk, bool free_agg,
+                          bool free_regroup, bool free_lanes) {
+  const TuneKey key{h->device, h->nx, h->ny, h->nz, h->opt.source_mode, h->rayleigh,
+                    (free_block ? 1 : 0) | (free_chunk ? 2 : 0) | (free_agg ? 4 : 0) |
+                        (free_regroup ? 8 : 0) | (free_lanes ? 16 : 0)};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      apply_shape(h, it->second);
+      h->tuned = true;
+      return NM_OK;
+    }
+  }
+  cudaStream_t s = h->stream;
+  cudaEvent_t e0, e1;
+  NM_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
+  NM_CUDA(cudaEventCreate(&e1), "cudaEventCreate");
+  const uint64_t n_trial = 1ull << 22;
+  const uint64_t first = 1ull << 62;
+  std::map<Shape, float> seen;
+  auto trial = [&](const Shape& t, float* ms) -> nm_status {
+    auto it = seen.find(t);
+    if (it != seen.end()) { *ms = it->second; return NM_OK; }
+    apply_shape(h, t);
+    if (h->grid <= 0) { *ms = 1e30f; return NM_OK; }
+    TransportParams p = h->params(first, n_trial, 0x7475u);
+    NM_CUDA(cudaMemsetAsync(h->work, 0, sizeof(unsigned), s), "autotune");
+    NM_CUDA(cudaEventRecord(e0, s), "autotune");
+    NM_CUDA(launch_transport(p, h->grid, h->block, h->warp_agg, h->rayleigh, h->regroup, s), "autotune");
+    NM_CUDA(cudaEventRecord(e1, s), "autotune");
+    NM_CUDA(cudaEventSynchronize(e1), "autotune");
+    NM_CUDA(cudaEventElapsedTime(ms, e0, e1), "autotune");
+    seen[t] = *ms;
+    return NM_OK;
+  };
+  float ms = 0;
+  nm_status st = trial(sh, &ms);  // warm-up (module load, caches)
+  seen.clear();
+  if (st == NM_OK) st = trial(sh, &ms);
+  float best = ms;
+  auto consider = [&](Shape t) -> nm_status {
+    float m = 0;
+    nm_status r = trial(t, &m);
+    if (r == NM_OK && m < best) { best = m; sh = t; }
+    return r;
+  };
+  for (int pass = 0; pass < 2 && st == NM_OK; ++pass) {
+    if (free_regroup || free_lanes) {
+      const int lanes[] = {8, 12, 16};
+      for (int l : lanes) {
+        if (!free_lanes && l != sh.lanes) continue;
+        Shape t = sh; t.regroup = 1; t.lanes = l;
+        if ((st = consider(t)) != NM_OK) break;
+      }
+      if (free_regroup && st == NM_OK) { Shape t = sh; t.regroup = 0; st = consider(t); }
+    }
+    if (free_block && st == NM_OK)
+      for (int b : {128, 256, 512}) { Shape t = sh; t.block = b; if ((st = consider(t)) != NM_OK) break; }
+    if (free_chunk && st == NM_OK)
+      for (int c : {64, 256, 1024}) { Shape t = sh; t.chunk = c; if ((st = consider(t)) != NM_OK) break; }
+    if (free_agg && st == NM_OK)
+      for (int a : {0, 1}) { Shape t = sh; t.warp_agg = a; if ((st = consider(t)) != NM_OK) break; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != NM_OK) return st;
+  apply_shape(h, sh);
+  h->tuned = true;
+  // Trials tallied into the batch tally and counters: clear them.
+  NM_CUDA(cudaMemsetAsync(h->tb, 0, h->V * sizeof(ull), s), "autotune");
+  NM_CUDA(cudaMemsetAsync(h->counters, 0, kCtrCount * sizeof(ull), s), "autotune");
+  NM_CUDA(cudaMemsetAsync(h->status, 0, sizeof(uint32_t), s), "autotune");
+  NM_CUDA(cudaStreamSynchronize(s), "autotune");
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_cache[key] = sh;
+  return NM_OK;
+}
+
 static nm_status choose_shape(nm_dose* h) {
   const nm_options& o = h->opt;
-  h->block = o.block_threads > 0 ? o.block_threads : 256;
-  if (h->block % 32 || h->block > 512) return fail(NM_ERR_ARG, "block_threads must be a multiple of 32, <= 512");
-  h->chunk = o.chunk > 0 ? o.chunk : 256;
-  if (h->chunk < 32) return fail(NM_ERR_ARG, "chunk must be >= 32");
+  if (o.block_threads > 0 && (o.block_threads % 32 || o.block_threads > 512))
+    return fail(NM_ERR_ARG, "block_threads must be a multiple of 32, <= 512");
+  if (o.chunk > 0 && o.chunk < 32) return fail(NM_ERR_ARG, "chunk must be >= 32");
+  if (o.regroup_lanes > 32) return fail(NM_ERR_ARG, "regroup_lanes must be 1..32");
+  Shape sh;
+  sh.block = o.block_threads > 0 ? o.block_threads : 256;
+  sh.chunk = o.chunk > 0 ? o.chunk : 256;
   // A point source concentrates deposits near the source, where lanes of a
   // warp often hit the same voxel; a spread-out source rarely does.
-  h->warp_agg = o.warp_aggregate >= 0 ? (o.warp_aggregate != 0) : (o.source_mode == NM_SOURCE_POINT);
-  h->regroup = o.regroup >= 0 ? (o.regroup != 0) : 1;
-  h->regroup_lanes = o.regroup_lanes > 0 ? o.regroup_lanes : 12;
-  if (h->regroup_lanes > 32) return fail(NM_ERR_ARG, "regroup_lanes must be 1..32");
-  const int per_sm = transport_max_blocks_per_sm(h->block, h->warp_agg, h->rayleigh, h->regroup);
-  if (per_sm <= 0) return fail(NM_ERR_ARG, "transport kernel cannot launch with %d threads", h->block);
-  h->grid = per_sm * h->sms;
+  sh.warp_agg = o.warp_aggregate >= 0 ? (o.warp_aggregate != 0) : (o.source_mode == NM_SOURCE_POINT);
+  sh.regroup = o.regroup >= 0 ? (o.regroup != 0) : 1;
+  sh.lanes = o.regroup_lanes > 0 ? o.regroup_lanes : 12;
+  apply_shape(h, sh);
+  if (h->grid <= 0) return fail(NM_ERR_ARG, "transport kernel cannot launch with %d threads", h->block);
+  const bool fb = o.block_threads <= 0, fc = o.chunk <= 0, fa = o.warp_aggregate < 0,
+             fr = o.regroup < 0, fl = o.regroup_lanes <= 0 && sh.regroup;
+  if (fb || fc || fa || fr || fl) return autotune(h, sh, fb, fc, fa, fr, fl);
   return NM_OK;
 }
 
@@ -374,6 +504,7 @@ nm_status nm_dose_create(nm_dose** out, const nm_grid* g, const nm_materials* mt
   }
   if ((e = cudaMemcpy(h->minv, minv.data(), kKnTable * sizeof(float), cudaMemcpyHostToDevice)))
     return bail(cuda_fail(e, "majorant table"));
+  h->minv_host = minv;
 
   // Decay sampler: alias table over the active voxels, FP64 on the device.
   if (o.source_mode == NM_SOURCE_DECAY) {
@@ -469,6 +600,216 @@ nm_status nm_dose_run(nm_dose* h, uint64_t n, uint64_t seed) {
                 (st & NM_DEV_KAHN_LIMIT) ? "Kahn trial limit" : "");
   }
   return NM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Many patients in one graph: per batch, one persistent multi-patient transport
+// launch in which every warp drains per-patient work queues (moving on to the
+// next patient when one runs dry), then each patient's fold.  The B batches
+// are captured into a CUDA graph once per call and launched as one graph.
+// ---------------------------------------------------------------------------
+static bool same_physics(const nm_dose* a, const nm_dose* b) {
+  if (a->n_mat != b->n_mat || a->rayleigh != b->rayleigh || a->e0 != b->e0 || a->cut != b->cut ||
+      a->ln_e_lo != b->ln_e_lo || a->inv_dln != b->inv_dln || a->device != b->device ||
+      a->opt.batches != b->opt.batches || a->opt.max_steps != b->opt.max_steps)
+    return false;
+  for (int m = 0; m < a->n_mat; ++m)
+    if (a->mat[m].za != b->mat[m].za || a->mat[m].zp != b->mat[m].zp || a->mat[m].zr != b->mat[m].zr)
+      return false;
+  return true;
+}
+
+typedef std::tuple<int, int, long long, long long> BatchKey;
+static std::map<BatchKey, Shape> g_batch_tune;
+
+extern "C" nm_status nm_dose_run_batch(nm_dose* const* hs, int32_t n, const uint64_t* n_decays,
+                                       uint64_t seed) {
+  if (!hs || !n_decays || n < 1 || n > kMaxBatchPatients)
+    return fail(NM_ERR_ARG, "need 1..%d handles and their decay counts", kMaxBatchPatients);
+  long long vox_sum = 0, vox_hash = 0;
+  for (int i = 0; i < n; ++i) {
+    if (!hs[i]) return fail(NM_ERR_ARG, "handle %d is NULL", i);
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return fail(NM_ERR_ARG, "handle %d appears twice", i);
+    if (!same_physics(hs[0], hs[i]))
+      return fail(NM_ERR_ARG, "handle %d: all patients of a batch need the same materials, energies, batches and device", i);
+    const uint64_t per = hs[i]->units_per_history();
+    const uint64_t lim = (uint64_t)INT64_MAX / (per ? per : 1);
+    if (hs[i]->hist_next > lim || n_decays[i] > lim - hs[i]->hist_next ||
+        hs[i]->hist_next + n_decays[i] > (1ull << 62))
+      return fail(NM_ERR_OVERFLOW, "handle %d: too many histories", i);
+    vox_sum += hs[i]->V;
+    vox_hash = vox_hash * 1000003 + hs[i]->V;
+  }
+  nm_dose* h0 = hs[0];
+  cudaStream_t s = h0->stream;
+  const int B = h0->opt.batches;
+  uint64_t total = 0;
+  for (int i = 0; i < n; ++i) total += n_decays[i];
+  if (total == 0) return NM_OK;
+
+  // Shared physics: the batch majorant is the largest of the patients'.
+  std::vector<float> minv(kKnTable);
+  for (int k = 0; k < kKnTable; ++k) {
+    float m = h0->minv_host[k];
+    for (int i = 1; i < n; ++i) m = std::min(m, hs[i]->minv_host[k]);
+    minv[k] = m;
+  }
+  // Temporary device memory: per-batch patient tables, majorant, status.
+  PatientGeom* d_pat = nullptr;
+  float* d_minv = nullptr;
+  uint32_t* d_status = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  nm_status st = NM_OK;
+  auto cleanup = [&]() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (d_pat) cudaFree(d_pat);
+    if (d_minv) cudaFree(d_minv);
+    if (d_status) cudaFree(d_status);
+  };
+  cudaError_t e;
+  std::vector<PatientGeom> pat((size_t)B * n);
+  std::vector<uint64_t> off(n, 0);
+  for (int b = 0; b < B; ++b)
+    for (int i = 0; i < n; ++i) {
+      const uint64_t nb = n_decays[i] / B + ((uint64_t)b < n_decays[i] % B ? 1 : 0);
+      pat[(size_t)b * n + i] = hs[i]->geom(hs[i]->hist_next + off[i], nb);
+      off[i] += nb;
+      if (nb >= (1ull << 31)) { cleanup(); return fail(NM_ERR_ARG, "handle %d: batches above 2^31 histories", i); }
+    }
+  if ((e = cudaMalloc(&d_pat, pat.size() * sizeof(PatientGeom))) ||
+      (e = cudaMalloc(&d_minv, kKnTable * sizeof(float))) || (e = cudaMalloc(&d_status, 4)) ||
+      (e = cudaMemcpyAsync(d_pat, pat.data(), pat.size() * sizeof(PatientGeom), cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemcpyAsync(d_minv, minv.data(), kKnTable * sizeof(float), cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemsetAsync(d_status, 0, 4, s)) || (e = cudaStreamSynchronize(s))) {
+    cleanup();
+    return cuda_fail(e, "nm_dose_run_batch: set-up");
+  }
+  TransportParams p = h0->params(0, 0, seed);
+  p.minv = d_minv;
+  p.status = d_status;
+  p.n_patients = n;
+
+  // Launch shape of the multi-patient kernel: the first handle's explicit
+  // options, else timed trials on this batch (cached per batch geometry).
+  Shape sh{h0->block, h0->chunk, h0->warp_agg, h0->regroup, h0->regroup_lanes};
+  const BatchKey key{h0->device, n, vox_sum, vox_hash};
+  bool have = false;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_batch_tune.find(key);
+    if (it != g_batch_tune.end()) { sh = it->second; have = true; }
+  }
+  const bool free_shape = h0->opt.block_threads <= 0 || h0->opt.chunk <= 0 || h0->opt.regroup < 0;
+  if (!have && free_shape) {
+    // Trials on history ids above 2^62 of every patient, then cleared.
+    if ((e = cudaEventCreate(&e0)) || (e = cudaEventCreate(&e1))) { cleanup(); return cuda_fail(e, "events"); }
+    std::vector<PatientGeom> tp(n);
+    for (int i = 0; i < n; ++i) tp[i] = hs[i]->geom(1ull << 62, (1ull << 22) / n + 1);
+    if ((e = cudaMemcpy(d_pat, tp.data(), n * sizeof(PatientGeom), cudaMemcpyHostToDevice))) {
+      cleanup();
+      return cuda_fail(e, "batch autotune");
+    }
+    // Trials add to the handles' counters: keep them to restore afterwards.
+    std::vector<ull> saved((size_t)n * kCtrCount);
+    for (int i = 0; i < n && !e; ++i)
+      e = cudaMemcpy(&saved[(size_t)i * kCtrCount], hs[i]->counters, kCtrCount * sizeof(ull), cudaMemcpyDeviceToHost);
+    if (e) { cleanup(); return cuda_fail(e, "batch autotune"); }
+    float best = 1e30f;
+    Shape cand[] = {{128, 256, sh.warp_agg, 1, 12}, {256, 256, sh.warp_agg, 1, 12},
+                    {512, 256, sh.warp_agg, 1, 12}, {256, 64, sh.warp_agg, 1, 12},
+                    {256, 1024, sh.warp_agg, 1, 12}, {256, 256, sh.warp_agg, 1, 8},
+                    {256, 256, sh.warp_agg, 1, 16}, {256, 256, sh.warp_agg, 0, 12}};
+    Shape pick = sh;
+    for (int rep = 0; rep < 2; ++rep)
+      for (const Shape& c : cand) {
+        const int grid = grid_for_shape(h0, c, true);
+        if (grid <= 0) continue;
+        p.patients = d_pat;
+        p.chunk = c.chunk;
+        p.regroup_compton = p.regroup_refill = c.lanes;
+        for (int i = 0; i < n; ++i) cudaMemsetAsync(hs[i]->work, 0, 4, s);
+        float ms = 0;
+        if ((e = cudaEventRecord(e0, s)) ||
+            (e = launch_transport(p, grid, c.block, c.warp_agg, h0->rayleigh, c.regroup, s, true)) ||
+            (e = cudaEventRecord(e1, s)) || (e = cudaEventSynchronize(e1)) ||
+            (e = cudaEventElapsedTime(&ms, e0, e1))) {
+          cleanup();
+          return cuda_fail(e, "batch autotune");
+        }
+        if (rep == 1 && ms < best) { best = ms; pick = c; }
+      }
+    sh = pick;
+    for (int i = 0; i < n && !e; ++i) {
+      e = cudaMemsetAsync(hs[i]->tb, 0, hs[i]->V * sizeof(ull), s);
+      if (!e) e = cudaMemcpyAsync(hs[i]->counters, &saved[(size_t)i * kCtrCount], kCtrCount * sizeof(ull),
+                                  cudaMemcpyHostToDevice, s);
+    }
+    if (!e) e = cudaMemsetAsync(d_status, 0, 4, s);
+    if (e) { cleanup(); return cuda_fail(e, "batch autotune"); }
+    if ((e = cudaMemcpyAsync(d_pat, pat.data(), pat.size() * sizeof(PatientGeom), cudaMemcpyHostToDevice, s)) ||
+        (e = cudaStreamSynchronize(s))) {
+      cleanup();
+      return cuda_fail(e, "batch autotune");
+    }
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_batch_tune[key] = sh;
+  }
+  const int grid = grid_for_shape(h0, sh, true);
+  if (grid <= 0) { cleanup(); return fail(NM_ERR_ARG, "multi-patient kernel cannot launch"); }
+  p.chunk = sh.chunk;
+  p.regroup_compton = p.regroup_refill = sh.lanes;
+
+  // Capture: B x (reset queues, one transport launch over all patients, folds).
+  if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal))) {
+    cleanup();
+    return cuda_fail(e, "stream capture");
+  }
+  for (int b = 0; b < B && !e; ++b) {
+    for (int i = 0; i < n && !e; ++i) e = cudaMemsetAsync(hs[i]->work, 0, sizeof(unsigned), s);
+    p.patients = d_pat + (size_t)b * n;
+    if (!e) e = launch_transport(p, grid, sh.block, sh.warp_agg, h0->rayleigh, sh.regroup, s, true);
+    for (int i = 0; i < n && !e; ++i) {
+      const uint64_t nb = pat[(size_t)b * n + i].n_hist;
+      if (nb == 0) continue;
+      nm_dose* h = hs[i];
+      FoldParams fp;
+      fp.tb = h->tb; fp.tsum = h->tsum; fp.s2 = h->s2; fp.density = h->density;
+      fp.labels = h->labels; fp.V = h->V; fp.gy_per_unit_vol = h->gy_per_unit_vol();
+      fp.organ_partial = h->organ_partial; fp.org_s1 = h->org_s1; fp.org_s2 = h->org_s2;
+      fp.deposited = h->counters + kCtrDepositedUnits;
+      fp.n_b = (double)nb;
+      e = launch_fold(fp, s);
+    }
+  }
+  cudaError_t ec = cudaStreamEndCapture(s, &graph);
+  if (e || ec) { cleanup(); return cuda_fail(e ? e : ec, "stream capture"); }
+  if ((e = cudaGraphInstantiate(&exec, graph, 0))) { cleanup(); return cuda_fail(e, "graph instantiate"); }
+  if (!e0 && ((e = cudaEventCreate(&e0)) || (e = cudaEventCreate(&e1)))) { cleanup(); return cuda_fail(e, "events"); }
+  float ms = 0;
+  uint32_t flags = 0;
+  if ((e = cudaEventRecord(e0, s)) || (e = cudaGraphLaunch(exec, s)) || (e = cudaEventRecord(e1, s)) ||
+      (e = cudaMemcpyAsync(&flags, d_status, 4, cudaMemcpyDeviceToHost, s)) ||
+      (e = cudaStreamSynchronize(s)) || (e = cudaEventElapsedTime(&ms, e0, e1))) {
+    cleanup();
+    return cuda_fail(e, "graph launch");
+  }
+  for (int i = 0; i < n; ++i) {
+    if (n_decays[i] == 0) continue;
+    hs[i]->hist_next += n_decays[i];
+    hs[i]->n_batches += (uint64_t)std::min<uint64_t>(B, n_decays[i]);
+    hs[i]->transport_ms += ms * (double)n_decays[i] / (double)total;  // graph time, shared by decays
+    hs[i]->status_seen |= flags;
+  }
+  h0->batch_graph_ms += ms;
+  cleanup();
+  if (flags) return fail(NM_ERR_DEVICE, "device check fired (flags 0x%x)", flags);
+  return st;
 }
 
 static nm_status finalize(nm_dose* h, float* dose, float* sigma) {

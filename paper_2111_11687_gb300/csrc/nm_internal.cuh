@@ -62,27 +62,34 @@ struct MaterialCoef {
   float rho_max;  // largest density of this material in the grid (host side)
 };
 
-struct TransportParams {
+// Per-patient (per-grid) part of a transport launch.
+struct PatientGeom {
   const uint32_t* vox;        // packed voxel: density bits with the low 3 bits = material
   const uint4* alias;         // {prob bits, voxel, alias voxel, 0}
   ull* tally;                 // batch tally, units
   ull* counters;              // device counters (see CounterSlot)
   unsigned* work;             // histories handed out in this launch (< 2^32 per launch)
-  uint32_t* status;           // NM_DEV_* flags
-  const float* kn;            // kKnTable nodes of N_A * sigma_KN(E)
-  const float* minv;          // kKnTable bins: 1 / majorant (cm) on [E_i, E_i+1)
-  int nx, ny, nz;
-  float fnx, fny, fnz;        // grid size as float (voxel units)
-  float inv_dx, inv_dy, inv_dz;
   uint64_t n_active;
   uint64_t hist_begin;        // first global history id of this launch
   uint64_t n_hist;            // histories in this launch
-  uint32_t key0, key1;        // Philox key = seed
+  int nx, ny, nz;
+  float fnx, fny, fnz;        // grid size as float (voxel units)
+  float inv_dx, inv_dy, inv_dz;
   int source_mode;
   float px, py, pz;           // point source, voxel units
+  int32_t q_positron;         // q_units(positron energy), 0 in point mode
+};
+
+struct TransportParams {
+  PatientGeom g;              // the patient of a single-patient launch
+  const PatientGeom* patients;  // multi-patient launch: n_patients entries (device memory)
+  int n_patients;
+  uint32_t* status;           // NM_DEV_* flags
+  const float* kn;            // kKnTable nodes of N_A * sigma_KN(E)
+  const float* minv;          // kKnTable bins: 1 / majorant (cm) on [E_i, E_i+1)
+  uint32_t key0, key1;        // Philox key = seed
   float e0;                   // photon energy, MeV
   int32_t q_e0;               // q_units(e0)
-  int32_t q_positron;         // q_units(positron energy), 0 in point mode
   float cut;                  // photon cutoff, MeV
   int n_mat;
   MaterialCoef mat[NM_MAX_MATERIALS];
@@ -92,6 +99,8 @@ struct TransportParams {
   int regroup_compton;        // regrouped variant: lanes that must wait before a Compton pass
   int regroup_refill;         // regrouped variant: lanes that must wait before a refill pass
 };
+
+constexpr int kMaxBatchPatients = 64;
 
 enum CounterSlot {
   kCtrSteps = 0, kCtrCompton, kCtrPhoto, kCtrRayleigh, kCtrCutoff, kCtrEscapes,
@@ -103,8 +112,9 @@ void set_error_message(const char* msg);
 
 // ---- launchers (host side), one translation unit each ---------------------
 cudaError_t launch_transport(const TransportParams& p, int grid, int block, bool warp_agg,
-                             bool rayleigh, bool regroup, cudaStream_t s);
-int transport_max_blocks_per_sm(int block, bool warp_agg, bool rayleigh, bool regroup);
+                             bool rayleigh, bool regroup, cudaStream_t s, bool multi = false);
+int transport_max_blocks_per_sm(int block, bool warp_agg, bool rayleigh, bool regroup,
+                                bool multi = false);
 cudaError_t launch_check_philox(const uint4* ctr, const uint2* key, int64_t n, uint4* out,
                                 cudaStream_t s);
 cudaError_t launch_check_kahn(float e, int64_t n, uint32_t k0, uint32_t k1, float* out,

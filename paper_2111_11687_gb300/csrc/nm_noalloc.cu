@@ -192,25 +192,25 @@ extern "C" nm_status nm_dose_tally_noalloc(const nm_grid* g, const nm_materials*
     if (n_active == 0) return fail(NM_ERR_ARG, "activity map sums to zero");
   }
 
-  p.vox = vox;
-  p.alias = alias;
-  p.tally = (ull*)tally;
-  p.counters = ctr_d;
-  p.work = work;
+  p.g.vox = vox;
+  p.g.alias = alias;
+  p.g.tally = (ull*)tally;
+  p.g.counters = ctr_d;
+  p.g.work = work;
+  p.g.n_active = (uint64_t)n_active;
+  p.g.nx = g->nx; p.g.ny = g->ny; p.g.nz = g->nz;
+  p.g.fnx = (float)g->nx; p.g.fny = (float)g->ny; p.g.fnz = (float)g->nz;
+  p.g.inv_dx = 1.0f / g->dx; p.g.inv_dy = 1.0f / g->dy; p.g.inv_dz = 1.0f / g->dz;
+  p.g.source_mode = o.source_mode;
+  p.g.px = o.point[0] / g->dx; p.g.py = o.point[1] / g->dy; p.g.pz = o.point[2] / g->dz;
+  p.g.q_positron = q_pos;
   p.status = status;
   p.kn = kn_d;
   p.minv = minv_d;
-  p.nx = g->nx; p.ny = g->ny; p.nz = g->nz;
-  p.fnx = (float)g->nx; p.fny = (float)g->ny; p.fnz = (float)g->nz;
-  p.inv_dx = 1.0f / g->dx; p.inv_dy = 1.0f / g->dy; p.inv_dz = 1.0f / g->dz;
-  p.n_active = (uint64_t)n_active;
   p.key0 = (uint32_t)seed;
   p.key1 = (uint32_t)(seed >> 32);
-  p.source_mode = o.source_mode;
-  p.px = o.point[0] / g->dx; p.py = o.point[1] / g->dy; p.pz = o.point[2] / g->dz;
   p.e0 = (float)o.photon_mev;
   p.q_e0 = q_e0;
-  p.q_positron = q_pos;
   p.cut = (float)mt->photon_cut_mev;
   p.n_mat = mt->n;
   p.ln_e_lo = (float)std::log(e_lo);
@@ -229,8 +229,8 @@ extern "C" nm_status nm_dose_tally_noalloc(const nm_grid* g, const nm_materials*
   if ((e = cudaMemsetAsync(tally, 0, 8 * V, s))) return cuda_fail(e, "tally clear");
   for (uint64_t done = 0; done < n_decays;) {
     const uint64_t part = std::min<uint64_t>(n_decays - done, 1ull << 31);
-    p.hist_begin = done;
-    p.n_hist = part;
+    p.g.hist_begin = done;
+    p.g.n_hist = part;
     if ((e = cudaMemsetAsync(work, 0, sizeof(unsigned), s)) ||
         (e = launch_transport(p, per_sm * sms, block, warp_agg, rayleigh, regroup, s)))
       return cuda_fail(e, "transport");

@@ -121,24 +121,25 @@ struct Site {
   float u, v_, w;     // direction of photon A
 };
 
-__device__ __forceinline__ Site sample_site(const TransportParams& p, uint32_t hlo, uint32_t hhi) {
+__device__ __forceinline__ Site sample_site(const PatientGeom& G, uint32_t k0, uint32_t k1,
+                                           uint32_t hlo, uint32_t hhi) {
   Site s;
   uint32_t ctr = 0;
-  uint4 r = draw(ctr, kStreamSource, hlo, hhi, p.key0, p.key1);
+  uint4 r = draw(ctr, kStreamSource, hlo, hhi, k0, k1);
   uint32_t rc, rphi;
-  if (p.source_mode == NM_SOURCE_DECAY) {
+  if (G.source_mode == NM_SOURCE_DECAY) {
     // Alias table: 64 random bits pick a column uniformly, one more the side.
     const uint64_t r64 = ((uint64_t)r.y << 32) | r.x;
-    const uint64_t col = __umul64hi(r64, p.n_active);
-    const uint4 a = __ldg(p.alias + col);
+    const uint64_t col = __umul64hi(r64, G.n_active);
+    const uint4 a = __ldg(G.alias + col);
     s.v = (u01(r.z) < __uint_as_float(a.x)) ? (int)a.y : (int)a.z;
-    const int nxy = p.nx * p.ny;
+    const int nxy = G.nx * G.ny;
     const int iz = s.v / nxy;
     const int rem = s.v - iz * nxy;
-    const int iy = rem / p.nx;
-    const int ix = rem - iy * p.nx;
+    const int iy = rem / G.nx;
+    const int ix = rem - iy * G.nx;
     const uint32_t rx = r.w;
-    r = draw(ctr, kStreamSource, hlo, hhi, p.key0, p.key1);
+    r = draw(ctr, kStreamSource, hlo, hhi, k0, k1);
     // Uniform inside the voxel; keep ix + u below ix + 1 after rounding.
     s.x = fminf((float)ix + u01(rx), __int_as_float(__float_as_int((float)(ix + 1)) - 1));
     s.y = fminf((float)iy + u01(r.x), __int_as_float(__float_as_int((float)(iy + 1)) - 1));
@@ -147,9 +148,9 @@ __device__ __forceinline__ Site sample_site(const TransportParams& p, uint32_t h
     rphi = r.w;
   } else {
     s.v = -1;
-    s.x = p.px;
-    s.y = p.py;
-    s.z = p.pz;
+    s.x = G.px;
+    s.y = G.py;
+    s.z = G.pz;
     rc = r.x;
     rphi = r.y;
   }
@@ -164,18 +165,20 @@ __device__ __forceinline__ Site sample_site(const TransportParams& p, uint32_t h
   return s;
 }
 
+// Adds dq units to *cell.  With WARP_AGG the lanes that hit the same cell
+// (same address, so lanes of different patients never merge) add their
+// deposits with one warp reduction and one atomic.
 template <bool WARP_AGG>
-__device__ __forceinline__ void tally_flush(ull* __restrict__ tally, bool has, int v, uint32_t dq,
-                                            uint32_t lane) {
+__device__ __forceinline__ void tally_flush(ull* cell, bool has, uint32_t dq, uint32_t lane) {
   if (WARP_AGG) {
     const unsigned m = __ballot_sync(kFull, has);
     if (has) {
-      const unsigned g = __match_any_sync(m, v);
+      const unsigned g = __match_any_sync(m, (unsigned long long)cell);
       const unsigned sum = __reduce_add_sync(g, dq);
-      if (lane == (unsigned)(__ffs(g) - 1)) atomicAdd(tally + v, (ull)sum);
+      if (lane == (unsigned)(__ffs(g) - 1)) atomicAdd(cell, (ull)sum);
     }
   } else if (has) {
-    atomicAdd(tally + v, (ull)dq);
+    atomicAdd(cell, (ull)dq);
   }
 }
 
@@ -202,7 +205,7 @@ __device__ __forceinline__ void compton(const TransportParams& p, const float* s
   if (e2 < p.cut) {
     dq = (uint32_t)qe;
     alive = false;
-    atomicAdd(&s_cnt[1], 1ull);
+    atomicAdd(&s_cnt[kCtrCutoff], 1ull);
   } else {
     const int32_t q2 = q_units(e2);
     dq = (uint32_t)(qe - q2);
@@ -212,20 +215,27 @@ __device__ __forceinline__ void compton(const TransportParams& p, const float* s
   }
 }
 
-template <bool WARP_AGG, bool RAYLEIGH, bool REGROUP>
+template <bool WARP_AGG, bool RAYLEIGH, bool REGROUP, bool MULTI>
 __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams p) {
   __shared__ float s_kn[kKnTable];
   __shared__ float s_minv[kKnTable];
   __shared__ MaterialCoef s_mat[NM_MAX_MATERIALS];
   __shared__ Energy s_f0;
-  __shared__ unsigned long long s_cnt[4];   // photo, cutoff, rayleigh, killed units
+  // Per patient, indexed by CounterSlot: the rare events (photo, cutoff,
+  // rayleigh, killed units) counted here directly, and (multi) the lanes'
+  // register counters handed over when a lane changes patient.
+  __shared__ unsigned long long s_cnt[MULTI ? kMaxBatchPatients : 1][8];
+  __shared__ PatientGeom s_geom[MULTI ? kMaxBatchPatients : 1];
   extern __shared__ float s_site[];         // [6][blockDim]: decay site and photon A direction
+  const int n_pat = MULTI ? p.n_patients : 1;
   for (int i = threadIdx.x; i < kKnTable; i += blockDim.x) {
     s_kn[i] = p.kn[i];
     s_minv[i] = p.minv[i];
   }
   if (threadIdx.x < NM_MAX_MATERIALS) s_mat[threadIdx.x] = p.mat[threadIdx.x];
-  if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0;
+  for (int i = threadIdx.x; i < n_pat * 8; i += blockDim.x) s_cnt[i / 8][i % 8] = 0;
+  if (MULTI)
+    for (int i = threadIdx.x; i < n_pat; i += blockDim.x) s_geom[i] = p.patients[i];
   __syncthreads();
   if (threadIdx.x == 0) s_f0 = energy_factors<RAYLEIGH>(p.e0, s_kn, s_minv, p.ln_e_lo, p.inv_dln_e);
   __syncthreads();
@@ -234,7 +244,12 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
 
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t lt_mask = (1u << lane) - 1u;
-  uint32_t pool_next = 0, pool_end = 0;  // warp-uniform, relative to hist_begin
+  // Warp-uniform work pool [pool_next, pool_end) of patient wp; the warps start
+  // spread over the patients.
+  uint32_t pool_next = 0, pool_end = 0;
+  int wp = MULTI ? (int)((blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) % n_pat) : 0;
+  int pi = 0;                            // this lane's patient
+  int cpi = 0;                           // patient the lane's counters belong to
   bool done = false, alive = false, pending_b = false, pending_c = false;
   float px = 0.f, py = 0.f, pz = 0.f, ux = 0.f, uy = 0.f, uz = 0.f;
   float e = 0.f;
@@ -268,48 +283,87 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
     }
     if (refill) {
       const uint32_t cnt = __popc(need);
-      const uint32_t avail = pool_end > pool_next ? pool_end - pool_next : 0u;
-      uint32_t fresh = 0;
+      const uint32_t avail = pool_end - pool_next;
+      uint32_t fresh = 0, fresh_end = 0;
+      int nwp = wp;
       if (avail < cnt) {
-        if (lane == 0) fresh = atomicAdd(p.work, (unsigned)p.chunk);
+        // Grab a chunk from the current patient's queue; a drained queue moves
+        // the warp on to the next patient.
+        if (lane == 0) {
+          for (int t = 0; t < n_pat; ++t) {
+            const PatientGeom& Q = MULTI ? s_geom[nwp] : p.g;
+            const unsigned f0 = atomicAdd(Q.work, (unsigned)p.chunk);
+            if ((uint64_t)f0 < Q.n_hist) {
+              fresh = f0;
+              fresh_end = (uint32_t)min((uint64_t)f0 + (uint64_t)p.chunk, Q.n_hist);
+              break;
+            }
+            if (MULTI) nwp = nwp + 1 < n_pat ? nwp + 1 : 0;
+          }
+        }
         fresh = __shfl_sync(kFull, fresh, 0);
+        fresh_end = __shfl_sync(kFull, fresh_end, 0);
+        nwp = __shfl_sync(kFull, nwp, 0);
       }
       bool has = false;
-      int dv = 0;
+      ull* cell = nullptr;
       if (!alive && !done) {
         const uint32_t rank = __popc(need & lt_mask);
-        const uint64_t idx = rank < avail ? (uint64_t)pool_next + rank : (uint64_t)fresh + (rank - avail);
-        if (idx < p.n_hist) {
-          const uint64_t h = p.hist_begin + idx;
+        uint32_t idx = 0;
+        bool got = true;
+        int npi = wp;
+        if (rank < avail) {
+          idx = pool_next + rank;
+        } else if (fresh + (rank - avail) < fresh_end) {
+          idx = fresh + (rank - avail);
+          npi = nwp;
+        } else {
+          got = false;
+          if (fresh_end == 0) done = true;   // every queue is drained
+        }
+        if (got) {
+          if (MULTI && npi != cpi) {
+            // counters belong to one patient: hand them over before switching
+            atomicAdd(&s_cnt[cpi][kCtrSteps], (ull)n_steps);
+            atomicAdd(&s_cnt[cpi][kCtrCompton], (ull)n_compton);
+            atomicAdd(&s_cnt[cpi][kCtrEscapes], (ull)n_esc);
+            atomicAdd(&s_cnt[cpi][kCtrEscapedUnits], escaped);
+            n_steps = n_compton = n_esc = 0;
+            escaped = 0;
+            cpi = npi;
+          }
+          pi = npi;
+          const PatientGeom& G = MULTI ? s_geom[pi] : p.g;
+          const uint64_t h = G.hist_begin + idx;
           hlo = (uint32_t)h;
           hhi = (uint32_t)(h >> 32);
-          const Site st = sample_site(p, hlo, hhi);
+          const Site st = sample_site(G, p.key0, p.key1, hlo, hhi);
           px = st.x; py = st.y; pz = st.z;
           ux = st.u; uy = st.v_; uz = st.w;
           e = p.e0; qe = p.q_e0; f = s_f0;
           stream = kStreamPhotonA; ctr = 0; have_spare = false; steps = 0;
           alive = true;
-          if (p.source_mode == NM_SOURCE_DECAY) {
+          if (G.source_mode == NM_SOURCE_DECAY) {
             site[0] = st.x; site[nb] = st.y; site[2 * nb] = st.z;
             site[3 * nb] = st.u; site[4 * nb] = st.v_; site[5 * nb] = st.w;
             pending_b = true;
-            has = p.q_positron > 0;
-            dv = st.v;
+            has = G.q_positron > 0;
+            cell = G.tally + st.v;
           }
-        } else {
-          done = true;
         }
       }
       if (avail < cnt) {
-        pool_next = fresh + (cnt - avail);
-        pool_end = fresh + (uint32_t)p.chunk;
+        pool_next = min(fresh + (cnt - avail), fresh_end);
+        pool_end = fresh_end;
+        wp = nwp;
       } else {
         pool_next += cnt;
       }
-      tally_flush<WARP_AGG>(p.tally, has, dv, (uint32_t)p.q_positron, lane);
+      tally_flush<WARP_AGG>(cell, has, (uint32_t)(MULTI ? s_geom[pi].q_positron : p.g.q_positron), lane);
     }
     if (!__any_sync(kFull, alive || !done)) break;
 
+    const PatientGeom& G = MULTI ? s_geom[pi] : p.g;
     bool has = false;
     int dv = 0;
     uint32_t dq = 0;
@@ -321,7 +375,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
         if (pending_c) {
           pending_c = false;
           compton<RAYLEIGH>(p, s_kn, s_minv, e, qe, f, ux, uy, uz, ctr, stream, hlo, hhi, alive, dq,
-                            flags, s_cnt);
+                            flags, s_cnt[MULTI ? pi : 0]);
           has = true;
           dv = cv;
         }
@@ -337,18 +391,18 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
         r0 = r.x; r1 = r.y; spare0 = r.z; spare1 = r.w; have_spare = true;
       }
       const float s = -__logf(u01(r0)) * f.inv_mubar;   // cm
-      px = fmaf(s * p.inv_dx, ux, px);
-      py = fmaf(s * p.inv_dy, uy, py);
-      pz = fmaf(s * p.inv_dz, uz, pz);
+      px = fmaf(s * G.inv_dx, ux, px);
+      py = fmaf(s * G.inv_dy, uy, py);
+      pz = fmaf(s * G.inv_dz, uz, pz);
       ++n_steps;
       ++steps;
-      if (!(px >= 0.0f && px < p.fnx && py >= 0.0f && py < p.fny && pz >= 0.0f && pz < p.fnz)) {
+      if (!(px >= 0.0f && px < G.fnx && py >= 0.0f && py < G.fny && pz >= 0.0f && pz < G.fnz)) {
         escaped += (ull)qe;
         ++n_esc;
         alive = false;
       } else {
-        const int v = ((int)pz * p.ny + (int)py) * p.nx + (int)px;
-        const uint32_t wv = __ldg(p.vox + v);
+        const int v = ((int)pz * G.ny + (int)py) * G.nx + (int)px;
+        const uint32_t wv = __ldg(G.vox + v);
         const MaterialCoef c = s_mat[wv & 7u];
         // real event with probability mu(voxel)/mubar; the same uniform picks the type
         const float scale = __uint_as_float(wv & ~7u) * f.inv_mubar;
@@ -362,18 +416,18 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
             cv = v;
           } else {
             compton<RAYLEIGH>(p, s_kn, s_minv, e, qe, f, ux, uy, uz, ctr, stream, hlo, hhi, alive,
-                              dq, flags, s_cnt);
+                              dq, flags, s_cnt[MULTI ? pi : 0]);
             has = true;
             dv = v;
           }
         } else if (t < scale * icp) {
-          atomicAdd(&s_cnt[0], 1ull);
+          atomicAdd(&s_cnt[MULTI ? pi : 0][kCtrPhoto], 1ull);
           has = true;
           dv = v;
           dq = (uint32_t)qe;
           alive = false;
         } else if (RAYLEIGH && t < scale * fmaf(c.zr, f.s_r, icp)) {
-          atomicAdd(&s_cnt[2], 1ull);
+          atomicAdd(&s_cnt[MULTI ? pi : 0][kCtrRayleigh], 1ull);
           // Thomson angular shape (1 + cos^2)/2 by rejection; one block per trial.
           for (int trial = 0;; ++trial) {
             const uint4 r = draw(ctr, stream, hlo, hhi, p.key0, p.key1);
@@ -386,30 +440,38 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
         }
       }
       if (alive && steps >= p.max_steps) {
-        atomicAdd(&s_cnt[3], (ull)qe);
+        atomicAdd(&s_cnt[MULTI ? pi : 0][kCtrKilledUnits], (ull)qe);
         flags |= NM_DEV_STEP_LIMIT;
         alive = false;
         pending_c = false;
       }
     }
-    tally_flush<WARP_AGG>(p.tally, has, dv, dq, lane);
+    tally_flush<WARP_AGG>(G.tally + dv, has, dq, lane);
   }
 
-  // ---- counters: warp sums, one atomic per warp per counter ----------------
-  const ull cs[4] = {n_steps, n_compton, n_esc, escaped};
-  const int slot[4] = {kCtrSteps, kCtrCompton, kCtrEscapes, kCtrEscapedUnits};
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const ull s = warp_sum(cs[i]);
-    if (lane == 0 && s) atomicAdd(p.counters + slot[i], s);
+  // ---- counters ---------------------------------------------------------------
+  if (MULTI) {
+    atomicAdd(&s_cnt[cpi][kCtrSteps], (ull)n_steps);
+    atomicAdd(&s_cnt[cpi][kCtrCompton], (ull)n_compton);
+    atomicAdd(&s_cnt[cpi][kCtrEscapes], (ull)n_esc);
+    atomicAdd(&s_cnt[cpi][kCtrEscapedUnits], escaped);
+  } else {
+    // warp sums, one atomic per warp per counter
+    ull sm = warp_sum((ull)n_steps);
+    if (lane == 0 && sm) atomicAdd(p.g.counters + kCtrSteps, sm);
+    sm = warp_sum((ull)n_compton);
+    if (lane == 0 && sm) atomicAdd(p.g.counters + kCtrCompton, sm);
+    sm = warp_sum((ull)n_esc);
+    if (lane == 0 && sm) atomicAdd(p.g.counters + kCtrEscapes, sm);
+    sm = warp_sum(escaped);
+    if (lane == 0 && sm) atomicAdd(p.g.counters + kCtrEscapedUnits, sm);
   }
   const unsigned fl = __reduce_or_sync(kFull, flags);
   if (lane == 0 && fl) atomicOr(p.status, fl);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    const int slot2[4] = {kCtrPhoto, kCtrCutoff, kCtrRayleigh, kCtrKilledUnits};
-    for (int i = 0; i < 4; ++i)
-      if (s_cnt[i]) atomicAdd(p.counters + slot2[i], s_cnt[i]);
+  for (int i = threadIdx.x; i < n_pat * 8; i += blockDim.x) {
+    const int q = i / 8, k = i % 8;   // k is the CounterSlot
+    if (s_cnt[q][k]) atomicAdd((MULTI ? s_geom[q].counters : p.g.counters) + k, s_cnt[q][k]);
   }
 }
 
@@ -434,11 +496,11 @@ __global__ void check_source_kernel(const TransportParams p, uint64_t first, int
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const uint64_t h = first + (uint64_t)i;
-  const Site s = sample_site(p, (uint32_t)h, (uint32_t)(h >> 32));
+  const Site s = sample_site(p.g, p.key0, p.key1, (uint32_t)h, (uint32_t)(h >> 32));
   voxel[i] = s.v;
-  pos[3 * i + 0] = s.x / p.inv_dx;
-  pos[3 * i + 1] = s.y / p.inv_dy;
-  pos[3 * i + 2] = s.z / p.inv_dz;
+  pos[3 * i + 0] = s.x / p.g.inv_dx;
+  pos[3 * i + 1] = s.y / p.g.inv_dy;
+  pos[3 * i + 2] = s.z / p.g.inv_dz;
   dir[3 * i + 0] = s.u;
   dir[3 * i + 1] = s.v_;
   dir[3 * i + 2] = s.w;
@@ -446,34 +508,37 @@ __global__ void check_source_kernel(const TransportParams p, uint64_t first, int
 
 size_t transport_smem(int block) { return (size_t)6 * block * sizeof(float); }
 
-template <bool A, bool R, bool G>
+template <bool A, bool R, bool G, bool M>
 void* kernel_ptr() {
-  return (void*)transport_kernel<A, R, G>;
+  return (void*)transport_kernel<A, R, G, M>;
 }
 
-void* pick(bool a, bool r, bool g) {
+template <bool M>
+void* pick_m(bool a, bool r, bool g) {
   if (a) {
-    if (r) return g ? kernel_ptr<true, true, true>() : kernel_ptr<true, true, false>();
-    return g ? kernel_ptr<true, false, true>() : kernel_ptr<true, false, false>();
+    if (r) return g ? kernel_ptr<true, true, true, M>() : kernel_ptr<true, true, false, M>();
+    return g ? kernel_ptr<true, false, true, M>() : kernel_ptr<true, false, false, M>();
   }
-  if (r) return g ? kernel_ptr<false, true, true>() : kernel_ptr<false, true, false>();
-  return g ? kernel_ptr<false, false, true>() : kernel_ptr<false, false, false>();
+  if (r) return g ? kernel_ptr<false, true, true, M>() : kernel_ptr<false, true, false, M>();
+  return g ? kernel_ptr<false, false, true, M>() : kernel_ptr<false, false, false, M>();
 }
+
+void* pick(bool a, bool r, bool g, bool m) { return m ? pick_m<true>(a, r, g) : pick_m<false>(a, r, g); }
 
 }  // namespace
 
 cudaError_t launch_transport(const TransportParams& p, int grid, int block, bool warp_agg,
-                             bool rayleigh, bool regroup, cudaStream_t s) {
-  void* fn = pick(warp_agg, rayleigh, regroup);
+                             bool rayleigh, bool regroup, cudaStream_t s, bool multi) {
+  void* fn = pick(warp_agg, rayleigh, regroup, multi);
   void* args[] = {(void*)&p};
   const cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(block), args, transport_smem(block), s);
   if (e != cudaSuccess) cudaGetLastError();  // a refused launch must not linger as the last error
   return e;
 }
 
-int transport_max_blocks_per_sm(int block, bool warp_agg, bool rayleigh, bool regroup) {
+int transport_max_blocks_per_sm(int block, bool warp_agg, bool rayleigh, bool regroup, bool multi) {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick(warp_agg, rayleigh, regroup), block,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick(warp_agg, rayleigh, regroup, multi), block,
                                                     transport_smem(block)) != cudaSuccess)
     return 0;
   return n;

@@ -74,6 +74,7 @@ _SIGS = {
     "nm_dose_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(nm_grid), C.POINTER(nm_materials),
                                  C.c_void_p, C.c_void_p, C.POINTER(nm_options)]),
     "nm_dose_run": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64]),
+    "nm_dose_run_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_uint64), C.c_uint64]),
     "nm_dose_get": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "nm_dose_get_organs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "nm_dose_get_tally": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -188,6 +189,14 @@ def nm_dose_create(density, material, spacing, materials: Materials, activity=No
 
 def nm_dose_run(h, n_decays: int, seed: int):
     _check(load().nm_dose_run(h, int(n_decays), int(seed)))
+
+
+def nm_dose_run_batch(handles, n_decays, seed: int):
+    """handles: list of handles (or Dose objects); n_decays: one count per handle."""
+    hs = [h.h if isinstance(h, Dose) else h for h in handles]
+    arr = (C.c_void_p * len(hs))(*[h.value if isinstance(h, C.c_void_p) else h for h in hs])
+    nd = (C.c_uint64 * len(hs))(*[int(x) for x in n_decays])
+    _check(load().nm_dose_run_batch(arr, len(hs), nd, int(seed)))
 
 
 def nm_dose_get(h, dose=None, sigma=None, organ_dose=None):
