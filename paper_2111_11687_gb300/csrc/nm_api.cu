@@ -765,15 +765,24 @@ extern "C" nm_status nm_dose_run_batch(nm_dose* const* hs, int32_t n, const uint
   p.chunk = sh.chunk;
   p.regroup_compton = p.regroup_refill = sh.lanes;
 
-  // Capture: B x (reset queues, one transport launch over all patients, folds).
-  if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal))) {
+  // Capture: B x (reset queues, one transport launch over all patients, folds),
+  // on a private stream (the legacy default stream cannot be captured), after
+  // the handles' stream has drained.
+  cudaStream_t cs = nullptr;
+  if ((e = cudaStreamSynchronize(s)) || (e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking))) {
+    cleanup();
+    return cuda_fail(e, "capture stream");
+  }
+  auto cleanup_stream = [&]() { if (cs) cudaStreamDestroy(cs); cs = nullptr; };
+  if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal))) {
+    cleanup_stream();
     cleanup();
     return cuda_fail(e, "stream capture");
   }
   for (int b = 0; b < B && !e; ++b) {
-    for (int i = 0; i < n && !e; ++i) e = cudaMemsetAsync(hs[i]->work, 0, sizeof(unsigned), s);
+    for (int i = 0; i < n && !e; ++i) e = cudaMemsetAsync(hs[i]->work, 0, sizeof(unsigned), cs);
     p.patients = d_pat + (size_t)b * n;
-    if (!e) e = launch_transport(p, grid, sh.block, sh.warp_agg, h0->rayleigh, sh.regroup, s, true);
+    if (!e) e = launch_transport(p, grid, sh.block, sh.warp_agg, h0->rayleigh, sh.regroup, cs, true);
     for (int i = 0; i < n && !e; ++i) {
       const uint64_t nb = pat[(size_t)b * n + i].n_hist;
       if (nb == 0) continue;
@@ -784,21 +793,23 @@ extern "C" nm_status nm_dose_run_batch(nm_dose* const* hs, int32_t n, const uint
       fp.organ_partial = h->organ_partial; fp.org_s1 = h->org_s1; fp.org_s2 = h->org_s2;
       fp.deposited = h->counters + kCtrDepositedUnits;
       fp.n_b = (double)nb;
-      e = launch_fold(fp, s);
+      e = launch_fold(fp, cs);
     }
   }
-  cudaError_t ec = cudaStreamEndCapture(s, &graph);
-  if (e || ec) { cleanup(); return cuda_fail(e ? e : ec, "stream capture"); }
-  if ((e = cudaGraphInstantiate(&exec, graph, 0))) { cleanup(); return cuda_fail(e, "graph instantiate"); }
-  if (!e0 && ((e = cudaEventCreate(&e0)) || (e = cudaEventCreate(&e1)))) { cleanup(); return cuda_fail(e, "events"); }
+  cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+  if (e || ec) { cleanup_stream(); cleanup(); return cuda_fail(e ? e : ec, "stream capture"); }
+  if ((e = cudaGraphInstantiate(&exec, graph, 0))) { cleanup_stream(); cleanup(); return cuda_fail(e, "graph instantiate"); }
+  if (!e0 && ((e = cudaEventCreate(&e0)) || (e = cudaEventCreate(&e1)))) { cleanup_stream(); cleanup(); return cuda_fail(e, "events"); }
   float ms = 0;
   uint32_t flags = 0;
-  if ((e = cudaEventRecord(e0, s)) || (e = cudaGraphLaunch(exec, s)) || (e = cudaEventRecord(e1, s)) ||
-      (e = cudaMemcpyAsync(&flags, d_status, 4, cudaMemcpyDeviceToHost, s)) ||
-      (e = cudaStreamSynchronize(s)) || (e = cudaEventElapsedTime(&ms, e0, e1))) {
+  if ((e = cudaEventRecord(e0, cs)) || (e = cudaGraphLaunch(exec, cs)) || (e = cudaEventRecord(e1, cs)) ||
+      (e = cudaMemcpyAsync(&flags, d_status, 4, cudaMemcpyDeviceToHost, cs)) ||
+      (e = cudaStreamSynchronize(cs)) || (e = cudaEventElapsedTime(&ms, e0, e1))) {
+    cleanup_stream();
     cleanup();
     return cuda_fail(e, "graph launch");
   }
+  cleanup_stream();
   for (int i = 0; i < n; ++i) {
     if (n_decays[i] == 0) continue;
     hs[i]->hist_next += n_decays[i];
