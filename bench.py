@@ -335,8 +335,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--cpu-decays", type=int, default=400_000)
-    ap.add_argument("--ref-decays", type=int, default=200_000)
+    ap.add_argument("--cpu-decays", type=int, default=4_000_000)
+    ap.add_argument("--ref-decays", type=int, default=2_000_000)
     ap.add_argument("--profile", action="store_true", help="one short run for ncu")
     ap.add_argument("--decays", type=int, default=200_000_000)
     ap.add_argument("--tuning", default="{}", help="JSON dict of nm_options launch fields (profile mode)")
