@@ -191,15 +191,18 @@ def run_gpu(args):
     achieved = bytes_per_decay * decays_per_launch / (launch_ms * 1e-3) / 1e9
     peaks = _peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
+    # DRAM bytes per decay from the committed ncu summary, valid only while the
+    # kernel source is the one that was profiled.
     traffic = None
-    tp = os.path.join(ROOT, "profiles", "transport_traffic.json")
+    tp = os.path.join(ROOT, "profiles", "transport_kernel_adult_phantom.md")
     if os.path.exists(tp):
-        try:
-            tj = json.load(open(tp))
-            if tj.get("kernel_source_hash") == _kernel_hash():
-                traffic = tj["dram_bytes_per_decay"] * decays_per_launch
-        except Exception:
-            traffic = None
+        kv = {}
+        for line in open(tp):
+            if ":" in line and not line.startswith(("|", " ", "#")):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("kernel_source_hash") == _kernel_hash() and "dram_bytes_per_decay" in kv:
+            traffic = float(kv["dram_bytes_per_decay"]) * decays_per_launch
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "peak_source": "measured" if peaks else "fallback",
