@@ -115,6 +115,7 @@ typedef struct {
 #define NM_DEV_KAHN_LIMIT 2u   /* Kahn sampling hit its trial limit */
 #define NM_DEV_BAD_VOXEL 4u    /* material id out of range, density not > 0 */
 #define NM_DEV_BAD_ACTIVITY 8u /* activity negative or not finite */
+#define NM_DEV_TIMEOUT 16u     /* a bounded wait on the tensor cores gave up */
 
 /* Fills *o with the defaults: decay mode, 0.511 MeV photons, 0.25 MeV positron,
  * 10 batches, A(t_s) = 8.0 mCi decayed 60 min with T1/2 = 109.77 min (§2.2),
@@ -210,6 +211,49 @@ nm_status nm_dose_alias_table(nm_dose* h, int64_t* n_active, float* prob, int32_
  * voxel[n], pos[3n] (cm), dir[3n] (first photon); host pointers. */
 nm_status nm_check_source(nm_dose* h, uint64_t first, int64_t n, uint64_t seed, int32_t* voxel,
                           float* pos, float* dir);
+
+/* ---- 3x3x3 convolutions of the dose denoiser (tensor cores, BF16 in, FP32 accumulate)
+ *
+ * The denoiser (a 3D U-Net) is not in the paper; these are its building blocks.
+ * Volumes are channels-last BF16 (raw 16-bit patterns), [n][d][h][w][c].  The
+ * input of a convolution is the channel concatenation of source 0 (c0
+ * channels; at half resolution, read with nearest upsampling, when
+ * src0_coarse != 0) and source 1 (c1 channels, full resolution, may be
+ * absent with c1 = 0).  Stride 1, zero padding 1.  Weights are BF16
+ * [cout][nm_conv3d_kpad(c0 + c1)] with column k = tap * (c0 + c1) + ci,
+ * tap = (dz+1)*9 + (dy+1)*3 + (dx+1), and zeros past 27 taps.  All pointers are
+ * device memory and 16-byte aligned; c0, c1 multiples of 8; cout one of
+ * 16, 32, 48, 64, 96, 128, 192 (weight gradients: 16, 32, 64, 128).  The
+ * calls run on `stream` and synchronise it; NM_ERR_DEVICE on a tensor-core
+ * wait time-out. */
+typedef struct {
+  int32_t n, d, h, w;   /* output grid: batch and (fine) spatial size */
+  int32_t c0, c1;       /* input channels from source 0 and source 1 */
+  int32_t src0_coarse;  /* source 0 is at half resolution */
+  int32_t cout;         /* output channels */
+} nm_conv3d_desc;
+
+/* Padded GEMM depth of a convolution with cin input channels (27 cin rounded
+ * up to a multiple of 128). */
+int32_t nm_conv3d_kpad(int32_t cin);
+
+/* y = act(conv(x) + bias): act = ReLU if relu != 0; bias [cout] FP32 or NULL. */
+nm_status nm_conv3d_fwd(const nm_conv3d_desc* desc, const uint16_t* x0, const uint16_t* x1,
+                        const uint16_t* w, const float* bias, uint16_t* y, int32_t relu,
+                        void* stream);
+
+/* Input gradient: dx[n][d][h][w][c0 + c1] (BF16, before any mask) of the
+ * convolution `desc` for the output gradient dy[n][d][h][w][cout]; dx is at
+ * full resolution for both sources (the caller sums source 0 back to half
+ * resolution).  c0 + c1 must be one of the output channel counts above. */
+nm_status nm_conv3d_dgrad(const nm_conv3d_desc* desc, const uint16_t* dy, const uint16_t* w,
+                          uint16_t* dx, void* stream);
+
+/* Weight and bias gradients: dw[cout][kpad] (FP32) = sum over voxels of the
+ * im2col rows of the input times dy; db[cout] (FP32, may be NULL) = sum of
+ * dy.  Deterministic: split over voxel ranges, summed in a fixed order. */
+nm_status nm_conv3d_wgrad(const nm_conv3d_desc* desc, const uint16_t* x0, const uint16_t* x1,
+                          const uint16_t* dy, float* dw, float* db, void* stream);
 
 /* ---- Tally without device allocation ---------------------------------------
  *

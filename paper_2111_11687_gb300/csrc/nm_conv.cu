@@ -1,0 +1,470 @@
+// 3x3x3 convolution (stride 1, zero padding 1) of channels-last BF16 volumes
+// on the 5th-generation tensor cores, for the dose denoiser.
+//
+// Forward and input-gradient passes are one implicit GEMM,
+//   Y[p, co] = sum_k A[p, k] W[co, k],  A[p, k] = X[p + offset(tap), ci],  k = tap * Cin + ci,
+// with M = voxels (128 per CTA tile), N = Cout, K = 27 Cin padded to 64.  The
+// weight gradient is the GEMM dW[co, k] = sum_p A[p, k] dY[p, co] with the
+// voxels as reduction dimension, split over CTAs and summed in a fixed order.
+//
+// Operands are gathered by all threads into shared memory in the tensor
+// cores' canonical no-swizzle layout (8x16-byte core matrices), one thread
+// issues tcgen05.mma into a tensor-memory accumulator and commits to an
+// mbarrier; two stage buffers let the gather of stage s+1 overlap the MMAs of
+// stage s.  Every wait is bounded: on time-out the CTA records NM_DEV_TIMEOUT,
+// drains what it issued (bounded again), frees its tensor memory and returns.
+#include <cuda_bf16.h>
+
+#include "nm_internal.cuh"
+#include "nm_tc.cuh"
+
+namespace nm {
+namespace {
+
+constexpr int kBM = 128;        // GEMM rows per CTA
+constexpr int kKS = 64;         // K elements per stage (4 MMAs of K = 16)
+constexpr int kThreads = 128;
+constexpr long long kWaitCycles = 4ll << 30;  // about 2 s at 2 GHz
+
+struct ConvGeom {
+  int n, d, h, w;               // output grid (fine)
+  int c0, c1, cin, cout, kpad;  // channels; kpad = K padded to a multiple of 64
+  int coarse;                   // source 0 is at half resolution (nearest upsampling)
+  long long m;                  // voxels = n*d*h*w
+};
+
+// 8 consecutive channels (16 bytes) of the im2col row of voxel (b, z, y, x)
+// at GEMM column k, or zeros outside the volume / past 27 taps.
+__device__ __forceinline__ uint4 gather8(const ConvGeom& g, const __nv_bfloat16* __restrict__ x0,
+                                         const __nv_bfloat16* __restrict__ x1, int b, int z, int y,
+                                         int x, int k) {
+  const int tap = k / g.cin;
+  if (tap >= 27) return make_uint4(0, 0, 0, 0);
+  const int ci = k - tap * g.cin;
+  const int zz = z + tap / 9 - 1, yy = y + (tap / 3) % 3 - 1, xx = x + tap % 3 - 1;
+  if ((unsigned)zz >= (unsigned)g.d || (unsigned)yy >= (unsigned)g.h || (unsigned)xx >= (unsigned)g.w)
+    return make_uint4(0, 0, 0, 0);
+  if (ci < g.c0) {
+    long long off;
+    if (g.coarse) {
+      const int dd = g.d >> 1, hh = g.h >> 1, ww = g.w >> 1;
+      off = ((((long long)b * dd + (zz >> 1)) * hh + (yy >> 1)) * ww + (xx >> 1)) * g.c0 + ci;
+    } else {
+      off = ((((long long)b * g.d + zz) * g.h + yy) * g.w + xx) * g.c0 + ci;
+    }
+    return __ldg(reinterpret_cast<const uint4*>(x0 + off));
+  }
+  const long long off = ((((long long)b * g.d + zz) * g.h + yy) * g.w + xx) * g.c1 + (ci - g.c0);
+  return __ldg(reinterpret_cast<const uint4*>(x1 + off));
+}
+
+__device__ __forceinline__ void voxel_coords(const ConvGeom& g, long long m, int& b, int& z, int& y, int& x) {
+  x = (int)(m % g.w);
+  long long t = m / g.w;
+  y = (int)(t % g.h);
+  t /= g.h;
+  z = (int)(t % g.d);
+  b = (int)(t / g.d);
+}
+
+// ---------------------------------------------------------------------------
+// Forward / input-gradient: Y = act(A W^T + bias), K-major A and B.
+// ---------------------------------------------------------------------------
+template <int COUT>
+__global__ void __launch_bounds__(kThreads) conv_fwd_kernel(ConvGeom g, const __nv_bfloat16* __restrict__ x0,
+                                                            const __nv_bfloat16* __restrict__ x1,
+                                                            const __nv_bfloat16* __restrict__ wt,
+                                                            const float* __restrict__ bias,
+                                                            __nv_bfloat16* __restrict__ y, int relu,
+                                                            uint32_t* status) {
+  constexpr int kNcols = COUT <= 32 ? 32 : COUT <= 64 ? 64 : COUT <= 128 ? 128 : 256;
+  constexpr uint32_t kABytes = kBM * kKS * 2;       // 16 KB
+  constexpr uint32_t kBBytes = COUT * kKS * 2;
+  constexpr uint32_t kSbo = (kKS / 8) * 128;        // 8-row groups are 1 KB apart
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* sa = smem;                                // [2][kABytes]
+  uint8_t* sb = smem + 2 * kABytes;                  // [2][kBBytes]
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ uint32_t s_tmem;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) tc::tmem_alloc(&s_tmem, kNcols);
+  if (tid == 0) {
+    tc::mbar_init(&bar[0], 1);
+    tc::mbar_init(&bar[1], 1);
+    tc::mbar_fence_init();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = s_tmem;
+
+  const long long m_row = (long long)blockIdx.x * kBM + tid;  // this thread gathers GEMM row tid
+  const bool row_ok = m_row < g.m;
+  int b = 0, z = 0, yv = 0, xv = 0;
+  if (row_ok) voxel_coords(g, m_row, b, z, yv, xv);
+  const int nstages = g.kpad / kKS;
+  constexpr uint32_t idesc = tc::idesc_bf16_f32(kBM, COUT, false, false);
+  bool timeout = false;
+  int issued = 0;  // stages whose MMAs were issued
+
+  for (int s = 0; s < nstages; ++s) {
+    const int buf = s & 1;
+    if (s >= 2 && !tc::mbar_wait_bounded(&bar[buf], ((s >> 1) - 1) & 1, kWaitCycles)) timeout = true;
+    if (__syncthreads_or(timeout)) { timeout = true; break; }
+    uint8_t* a = sa + buf * kABytes;
+    uint8_t* bm = sb + buf * kBBytes;
+    // A: this thread's row, 8 chunks of 8 channels.
+#pragma unroll
+    for (int kc = 0; kc < 8; ++kc) {
+      const uint4 v = row_ok ? gather8(g, x0, x1, b, z, yv, xv, s * kKS + kc * 8) : make_uint4(0, 0, 0, 0);
+      *reinterpret_cast<uint4*>(a + (tid >> 3) * kSbo + kc * 128 + (tid & 7) * 16) = v;
+    }
+    // B: COUT rows x 8 chunks of the weight matrix [Cout][kpad].
+#pragma unroll
+    for (int i = 0; i < COUT / 16; ++i) {
+      const int q = tid + kThreads * i;
+      const int r = q >> 3, kc = q & 7;
+      const uint4 v = __ldg(reinterpret_cast<const uint4*>(wt + (long long)r * g.kpad + s * kKS + kc * 8));
+      *reinterpret_cast<uint4*>(bm + (r >> 3) * kSbo + kc * 128 + (r & 7) * 16) = v;
+    }
+    tc::fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint32_t a0 = tc::smem_u32(a), b0 = tc::smem_u32(bm);
+#pragma unroll
+      for (int kk = 0; kk < kKS / 16; ++kk)
+        tc::mma_bf16(tmem, tc::smem_desc(a0 + kk * 256, 128, kSbo), tc::smem_desc(b0 + kk * 256, 128, kSbo),
+                     idesc, (s | kk) != 0);
+      tc::mma_commit(&bar[buf]);
+    }
+    issued = s + 1;
+  }
+  if (!timeout && issued > 0) {
+    const int last = issued - 1;
+    if (!tc::mbar_wait_bounded(&bar[last & 1], (last >> 1) & 1, kWaitCycles)) timeout = true;
+  }
+  timeout = __syncthreads_or(timeout);
+  if (timeout) {
+    if (tid == 0) atomicOr(status, NM_DEV_TIMEOUT);
+    // drain: the last issued commit covers every MMA this CTA issued
+    if (issued > 0) tc::mbar_wait_bounded(&bar[(issued - 1) & 1], ((issued - 1) >> 1) & 1, kWaitCycles);
+  } else {
+    tc::fence_after_sync();
+    const int row = warp * 32 + lane;
+    const long long m = (long long)blockIdx.x * kBM + row;
+#pragma unroll
+    for (int c = 0; c < COUT / 16; ++c) {
+      float v[16];
+      tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c * 16, v);
+      if (m < g.m) {
+        __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          float t = v[j] + (bias ? __ldg(bias + c * 16 + j) : 0.0f);
+          if (relu) t = fmaxf(t, 0.0f);
+          o[j] = __float2bfloat16_rn(t);
+        }
+        uint4* dst = reinterpret_cast<uint4*>(y + m * COUT + c * 16);
+        dst[0] = reinterpret_cast<uint4*>(o)[0];
+        dst[1] = reinterpret_cast<uint4*>(o)[1];
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, kNcols);
+}
+
+// ---------------------------------------------------------------------------
+// Weight gradient: D[k, co] = sum_p A[p, k] dY[p, co] over this CTA's voxel
+// range; rows k are MN-contiguous in the gathered data, so both operands are
+// staged MN-major.  Partial results go to part[split][kpad][Cout].
+// ---------------------------------------------------------------------------
+template <int COUT>
+__global__ void __launch_bounds__(kThreads) conv_wgrad_kernel(ConvGeom g, const __nv_bfloat16* __restrict__ x0,
+                                                              const __nv_bfloat16* __restrict__ x1,
+                                                              const __nv_bfloat16* __restrict__ dy,
+                                                              float* __restrict__ part, long long vox_per_split,
+                                                              uint32_t* status) {
+  constexpr int kNcols = COUT < 32 ? 32 : COUT;
+  constexpr uint32_t kABytes = kBM * kKS * 2;
+  constexpr uint32_t kBBytes = COUT * kKS * 2;
+  constexpr uint32_t kSboA = (kBM / 8) * 128;       // K-adjacent core matrices of A
+  constexpr uint32_t kSboB = (COUT / 8) * 128;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* sa = smem;
+  uint8_t* sb = smem + 2 * kABytes;
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ uint32_t s_tmem;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) tc::tmem_alloc(&s_tmem, kNcols);
+  if (tid == 0) {
+    tc::mbar_init(&bar[0], 1);
+    tc::mbar_init(&bar[1], 1);
+    tc::mbar_fence_init();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = s_tmem;
+
+  const int k0 = blockIdx.x * kBM;                 // GEMM row block (im2col columns)
+  const long long p_begin = (long long)blockIdx.y * vox_per_split;
+  long long p_end = p_begin + vox_per_split;
+  if (p_end > g.m) p_end = g.m;
+  const int nstages = p_begin < p_end ? (int)((p_end - p_begin + kKS - 1) / kKS) : 0;
+  constexpr uint32_t idesc = tc::idesc_bf16_f32(kBM, COUT, true, true);
+  bool timeout = false;
+  int issued = 0;
+
+  for (int s = 0; s < nstages; ++s) {
+    const int buf = s & 1;
+    if (s >= 2 && !tc::mbar_wait_bounded(&bar[buf], ((s >> 1) - 1) & 1, kWaitCycles)) timeout = true;
+    if (__syncthreads_or(timeout)) { timeout = true; break; }
+    uint8_t* a = sa + buf * kABytes;
+    uint8_t* bm = sb + buf * kBBytes;
+    // A: 64 voxels x 16 chunks (8 GEMM rows each); thread -> (voxel, chunk).
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int q = tid + kThreads * i;
+      const int pl = q >> 4, rc = q & 15;
+      const long long p = p_begin + s * kKS + pl;
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (p < p_end) {
+        int b, z, yv, xv;
+        voxel_coords(g, p, b, z, yv, xv);
+        v = gather8(g, x0, x1, b, z, yv, xv, k0 + rc * 8);
+      }
+      *reinterpret_cast<uint4*>(a + rc * 128 + (pl >> 3) * kSboA + (pl & 7) * 16) = v;
+    }
+    // B: 64 voxels x COUT/8 chunks of dY.
+    for (int q = tid; q < kKS * (COUT / 8); q += kThreads) {
+      const int pl = q / (COUT / 8), rc = q % (COUT / 8);
+      const long long p = p_begin + s * kKS + pl;
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (p < p_end) v = __ldg(reinterpret_cast<const uint4*>(dy + p * COUT + rc * 8));
+      *reinterpret_cast<uint4*>(bm + rc * 128 + (pl >> 3) * kSboB + (pl & 7) * 16) = v;
+    }
+    tc::fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint32_t a0 = tc::smem_u32(a), b0 = tc::smem_u32(bm);
+#pragma unroll
+      for (int kk = 0; kk < kKS / 16; ++kk)
+        tc::mma_bf16(tmem, tc::smem_desc(a0 + kk * 2 * kSboA, 128, kSboA),
+                     tc::smem_desc(b0 + kk * 2 * kSboB, 128, kSboB), idesc, (s | kk) != 0);
+      tc::mma_commit(&bar[buf]);
+    }
+    issued = s + 1;
+  }
+  if (!timeout && issued > 0) {
+    const int last = issued - 1;
+    if (!tc::mbar_wait_bounded(&bar[last & 1], (last >> 1) & 1, kWaitCycles)) timeout = true;
+  }
+  timeout = __syncthreads_or(timeout);
+  const int row = warp * 32 + lane;
+  float* dst = part + ((long long)blockIdx.y * g.kpad + k0 + row) * COUT;
+  if (timeout) {
+    if (tid == 0) atomicOr(status, NM_DEV_TIMEOUT);
+    if (issued > 0) tc::mbar_wait_bounded(&bar[(issued - 1) & 1], ((issued - 1) >> 1) & 1, kWaitCycles);
+  } else if (issued == 0) {
+    for (int c = 0; c < COUT; ++c) dst[c] = 0.0f;
+  } else {
+    tc::fence_after_sync();
+#pragma unroll
+    for (int c = 0; c < COUT / 16; ++c) {
+      float v[16];
+      tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c * 16, v);
+#pragma unroll
+      for (int j = 0; j < 16; j += 4)
+        *reinterpret_cast<float4*>(dst + c * 16 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, kNcols);
+}
+
+// dW[co][k] = sum over splits (in order) of part[split][k][co].
+__global__ void wgrad_reduce_kernel(const float* __restrict__ part, int splits, int kpad, int cout,
+                                    float* __restrict__ dw) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)kpad * cout) return;
+  const int k = (int)(i / cout), co = (int)(i % cout);
+  float s = 0.0f;
+  for (int t = 0; t < splits; ++t) s += part[((long long)t * kpad + k) * cout + co];
+  dw[(long long)co * kpad + k] = s;
+}
+
+// db[co] = sum_p dY[p, co], per-CTA partial sums then a fixed-order total.
+__global__ void bias_grad_partial_kernel(const __nv_bfloat16* __restrict__ dy, long long m, int cout,
+                                         long long per_block, float* __restrict__ part) {
+  const int co = threadIdx.x;
+  if (co >= cout) return;
+  const long long p0 = (long long)blockIdx.x * per_block;
+  long long p1 = p0 + per_block;
+  if (p1 > m) p1 = m;
+  float s = 0.0f;
+  for (long long p = p0; p < p1; ++p) s += __bfloat162float(dy[p * cout + co]);
+  part[(long long)blockIdx.x * cout + co] = s;
+}
+
+__global__ void bias_grad_reduce_kernel(const float* __restrict__ part, int blocks, int cout,
+                                        float* __restrict__ db) {
+  const int co = threadIdx.x;
+  if (co >= cout) return;
+  float s = 0.0f;
+  for (int b = 0; b < blocks; ++b) s += part[(long long)b * cout + co];
+  db[co] = s;
+}
+
+// Weights of the input-gradient convolution: the forward weights [Cout][kpad(Cin)]
+// with the taps reversed and the channel roles swapped, [Cin][kpad(Cout)].
+__global__ void flip_weights_kernel(const __nv_bfloat16* __restrict__ w, int cin, int cout, int kpad_f,
+                                    int kpad_b, __nv_bfloat16* __restrict__ wb) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)cin * kpad_b) return;
+  const int ci = (int)(i / kpad_b), k = (int)(i % kpad_b);
+  const int tap = k / cout, co = k % cout;
+  __nv_bfloat16 v = __float2bfloat16_rn(0.0f);
+  if (tap < 27) v = w[(long long)co * kpad_f + (26 - tap) * cin + ci];
+  wb[i] = v;
+}
+
+template <int COUT>
+size_t fwd_smem() { return 2 * (size_t)kBM * kKS * 2 + 2 * (size_t)COUT * kKS * 2; }
+
+template <int COUT>
+cudaError_t launch_fwd_t(const ConvGeom& g, const __nv_bfloat16* x0, const __nv_bfloat16* x1,
+                         const __nv_bfloat16* w, const float* bias, __nv_bfloat16* y, int relu,
+                         uint32_t* status, cudaStream_t s) {
+  const size_t smem = fwd_smem<COUT>();
+  cudaError_t e = cudaFuncSetAttribute(conv_fwd_kernel<COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const long long grid = (g.m + kBM - 1) / kBM;
+  conv_fwd_kernel<COUT><<<(unsigned)grid, kThreads, smem, s>>>(g, x0, x1, w, bias, y, relu, status);
+  return cudaGetLastError();
+}
+
+// The weight-gradient buffers are over-allocated to 96 KB: every read the
+// MMAs can make from the stage buffers stays inside the CTA's allocation.
+template <int COUT>
+size_t wgrad_smem() {
+  const size_t need = fwd_smem<COUT>();
+  return need > 96 * 1024 ? need : 96 * 1024;
+}
+
+template <int COUT>
+cudaError_t launch_wgrad_t(const ConvGeom& g, const __nv_bfloat16* x0, const __nv_bfloat16* x1,
+                           const __nv_bfloat16* dy, float* part, int splits, uint32_t* status,
+                           cudaStream_t s) {
+  const size_t smem = wgrad_smem<COUT>();
+  cudaError_t e = cudaFuncSetAttribute(conv_wgrad_kernel<COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const long long per = ((g.m + splits - 1) / splits + kKS - 1) / kKS * kKS;
+  dim3 grid(g.kpad / kBM, splits);
+  conv_wgrad_kernel<COUT><<<grid, kThreads, smem, s>>>(g, x0, x1, dy, part, per, status);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int conv_kpad(int cin) {
+  const int k = 27 * cin;
+  // the weight-gradient GEMM tiles K in rows of 128
+  return (k + 127) / 128 * 128;
+}
+
+bool conv_geom_ok(const nm_conv3d_desc& d) {
+  const int cin = d.c0 + d.c1;
+  if (d.n <= 0 || d.d <= 0 || d.h <= 0 || d.w <= 0) return false;
+  if (d.c0 <= 0 || d.c0 % 8 || d.c1 < 0 || d.c1 % 8 || cin > 512) return false;
+  if (!(d.cout == 16 || d.cout == 32 || d.cout == 48 || d.cout == 64 || d.cout == 96 || d.cout == 128 ||
+        d.cout == 192))
+    return false;
+  if (d.src0_coarse && (d.d % 2 || d.h % 2 || d.w % 2)) return false;
+  return true;
+}
+
+static ConvGeom make_geom(const nm_conv3d_desc& d) {
+  ConvGeom g;
+  g.n = d.n; g.d = d.d; g.h = d.h; g.w = d.w;
+  g.c0 = d.c0; g.c1 = d.c1; g.cin = d.c0 + d.c1; g.cout = d.cout;
+  g.kpad = conv_kpad(g.cin);
+  g.coarse = d.src0_coarse;
+  g.m = (long long)d.n * d.d * d.h * d.w;
+  return g;
+}
+
+cudaError_t conv3d_fwd(const nm_conv3d_desc& d, const void* x0, const void* x1, const void* w,
+                       const float* bias, void* y, int relu, uint32_t* status, cudaStream_t s) {
+  const ConvGeom g = make_geom(d);
+  auto X0 = (const __nv_bfloat16*)x0, X1 = (const __nv_bfloat16*)x1, W = (const __nv_bfloat16*)w;
+  auto Y = (__nv_bfloat16*)y;
+  switch (d.cout) {
+    case 16: return launch_fwd_t<16>(g, X0, X1, W, bias, Y, relu, status, s);
+    case 32: return launch_fwd_t<32>(g, X0, X1, W, bias, Y, relu, status, s);
+    case 48: return launch_fwd_t<48>(g, X0, X1, W, bias, Y, relu, status, s);
+    case 64: return launch_fwd_t<64>(g, X0, X1, W, bias, Y, relu, status, s);
+    case 96: return launch_fwd_t<96>(g, X0, X1, W, bias, Y, relu, status, s);
+    case 128: return launch_fwd_t<128>(g, X0, X1, W, bias, Y, relu, status, s);
+    case 192: return launch_fwd_t<192>(g, X0, X1, W, bias, Y, relu, status, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int conv_wgrad_splits(const nm_conv3d_desc& d) {
+  const long long m = (long long)d.n * d.d * d.h * d.w;
+  const int mtiles = conv_kpad(d.c0 + d.c1) / kBM;
+  // about four CTAs per SM of 152 in total, at least 64 voxels each
+  long long splits = (4 * 152 + mtiles - 1) / mtiles;
+  if (splits * 64 > m) splits = (m + 63) / 64;
+  return (int)(splits < 1 ? 1 : splits);
+}
+
+size_t conv_wgrad_workspace(const nm_conv3d_desc& d) {
+  return (size_t)conv_wgrad_splits(d) * conv_kpad(d.c0 + d.c1) * d.cout * sizeof(float) +
+         (size_t)1024 * d.cout * sizeof(float);
+}
+
+cudaError_t conv3d_flip_weights(const nm_conv3d_desc& d, const void* w, void* wb, cudaStream_t s) {
+  const int cin = d.c0 + d.c1;
+  const int kf = conv_kpad(cin), kb = conv_kpad(d.cout);
+  const long long n = (long long)cin * kb;
+  flip_weights_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const __nv_bfloat16*)w, cin, d.cout, kf, kb,
+                                                                   (__nv_bfloat16*)wb);
+  return cudaGetLastError();
+}
+
+cudaError_t conv3d_wgrad(const nm_conv3d_desc& d, const void* x0, const void* x1, const void* dy,
+                         float* dw, float* db, void* workspace, uint32_t* status, cudaStream_t s) {
+  const ConvGeom g = make_geom(d);
+  const int splits = conv_wgrad_splits(d);
+  float* part = (float*)workspace;
+  auto X0 = (const __nv_bfloat16*)x0, X1 = (const __nv_bfloat16*)x1, DY = (const __nv_bfloat16*)dy;
+  cudaError_t e;
+  switch (d.cout) {
+    case 16: e = launch_wgrad_t<16>(g, X0, X1, DY, part, splits, status, s); break;
+    case 32: e = launch_wgrad_t<32>(g, X0, X1, DY, part, splits, status, s); break;
+    case 64: e = launch_wgrad_t<64>(g, X0, X1, DY, part, splits, status, s); break;
+    case 128: e = launch_wgrad_t<128>(g, X0, X1, DY, part, splits, status, s); break;
+    default: return cudaErrorInvalidValue;  // weight gradients exist for the U-Net's outputs only
+  }
+  if (e != cudaSuccess) return e;
+  const long long n = (long long)g.kpad * g.cout;
+  wgrad_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(part, splits, g.kpad, g.cout, dw);
+  if (db) {
+    float* bpart = part + (size_t)splits * g.kpad * g.cout;
+    const int blocks = 1024;
+    const long long per = (g.m + blocks - 1) / blocks;
+    bias_grad_partial_kernel<<<blocks, 128, 0, s>>>(DY, g.m, g.cout, per, bpart);
+    bias_grad_reduce_kernel<<<1, 128, 0, s>>>(bpart, blocks, g.cout, db);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace nm

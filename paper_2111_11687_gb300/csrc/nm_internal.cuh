@@ -179,4 +179,15 @@ struct FinalizeParams {
 cudaError_t launch_finalize(const FinalizeParams& p, cudaStream_t s);
 cudaError_t launch_label_count(const uint8_t* labels, int64_t V, long long* count, cudaStream_t s);
 
+// ---- 3x3x3 convolution on the tensor cores (nm_conv.cu) -------------------
+int conv_kpad(int cin);
+bool conv_geom_ok(const nm_conv3d_desc& d);
+int conv_wgrad_splits(const nm_conv3d_desc& d);
+size_t conv_wgrad_workspace(const nm_conv3d_desc& d);
+cudaError_t conv3d_fwd(const nm_conv3d_desc& d, const void* x0, const void* x1, const void* w,
+                       const float* bias, void* y, int relu, uint32_t* status, cudaStream_t s);
+cudaError_t conv3d_flip_weights(const nm_conv3d_desc& d, const void* w, void* wb, cudaStream_t s);
+cudaError_t conv3d_wgrad(const nm_conv3d_desc& d, const void* x0, const void* x1, const void* dy,
+                         float* dw, float* db, void* workspace, uint32_t* status, cudaStream_t s);
+
 }  // namespace nm

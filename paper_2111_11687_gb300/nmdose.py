@@ -66,6 +66,10 @@ class nm_counters(C.Structure):
         return {n: getattr(self, n) for n, _ in self._fields_}
 
 
+class nm_conv3d_desc(C.Structure):
+    _fields_ = [(k, C.c_int32) for k in ("n", "d", "h", "w", "c0", "c1", "src0_coarse", "cout")]
+
+
 # Every entry point declared in include/nm_dose.h, with its ctypes signature.
 _SIGS = {
     "nm_options_default": (None, [C.POINTER(nm_options)]),
@@ -85,6 +89,12 @@ _SIGS = {
     "nm_check_kahn": (C.c_int, [C.c_double, C.c_int64, C.c_uint64, C.c_void_p]),
     "nm_dose_alias_table": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.c_void_p, C.c_void_p, C.c_void_p]),
     "nm_check_source": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int64, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "nm_conv3d_kpad": (C.c_int32, [C.c_int32]),
+    "nm_conv3d_fwd": (C.c_int, [C.POINTER(nm_conv3d_desc), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                C.c_void_p, C.c_int32, C.c_void_p]),
+    "nm_conv3d_dgrad": (C.c_int, [C.POINTER(nm_conv3d_desc), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "nm_conv3d_wgrad": (C.c_int, [C.POINTER(nm_conv3d_desc), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_void_p]),
     "nm_dose_tally_noalloc": (C.c_int, [C.POINTER(nm_grid), C.POINTER(nm_materials), C.c_void_p,
                                         C.POINTER(nm_options), C.c_uint64, C.c_uint64, C.c_void_p,
                                         C.POINTER(nm_counters)]),
@@ -277,6 +287,27 @@ def nm_dose_tally_noalloc(density, material, spacing, materials: Materials, tall
                                         C.byref(opts) if opts is not None else None,
                                         int(n_decays), int(seed), ptr(tally), C.byref(c)))
     return c.as_dict()
+
+
+def nm_conv3d_kpad(cin: int) -> int:
+    return int(load().nm_conv3d_kpad(int(cin)))
+
+
+def _desc(n, d, h, w, c0, c1=0, coarse=0, cout=16):
+    return nm_conv3d_desc(n, d, h, w, c0, c1, coarse, cout)
+
+
+def nm_conv3d_fwd(desc, x0, x1, w, bias, y, relu: bool, stream=None):
+    _check(load().nm_conv3d_fwd(C.byref(desc), ptr(x0), ptr(x1), ptr(w), ptr(bias), ptr(y), int(relu),
+                                _stream_ptr(stream)))
+
+
+def nm_conv3d_dgrad(desc, dy, w, dx, stream=None):
+    _check(load().nm_conv3d_dgrad(C.byref(desc), ptr(dy), ptr(w), ptr(dx), _stream_ptr(stream)))
+
+
+def nm_conv3d_wgrad(desc, x0, x1, dy, dw, db=None, stream=None):
+    _check(load().nm_conv3d_wgrad(C.byref(desc), ptr(x0), ptr(x1), ptr(dy), ptr(dw), ptr(db), _stream_ptr(stream)))
 
 
 class Dose:

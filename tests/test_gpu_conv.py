@@ -1,0 +1,132 @@
+"""The denoiser's tensor-core convolutions against the FP64 oracle on the same
+BF16-rounded operands.
+
+Tolerances follow the arithmetic: products of two BF16 numbers are exact in
+FP32, the FP32 accumulation over K terms errs by at most about K 2^-24 of the
+sum of |terms|, and a BF16 output adds a rounding of 2^-9 relative."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    from oracle import denoise
+    from paper_2111_11687_gb300 import build, nmdose
+    build.build()
+    nmdose.load()
+    return torch, nmdose, denoise
+
+
+def bf16(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(torch.bfloat16)
+
+
+def as64(t):
+    return t.float().cpu().numpy().astype(np.float64)
+
+
+def conv_desc(nm, n, d, h, w, c0, c1, coarse, cout):
+    return nm.nm_conv3d_desc(n, d, h, w, c0, c1, coarse, cout)
+
+
+def weights_padded(torch, w3, kpad):
+    # w3 [cout, 27, cin] -> [cout, kpad] with k = tap * cin + ci
+    cout, _, cin = w3.shape
+    wp = np.zeros((cout, kpad), np.float32)
+    wp[:, :27 * cin] = w3.reshape(cout, 27 * cin)
+    return bf16(torch, wp)
+
+
+CASES = [
+    # n, d, h, w, c0, c1, coarse, cout
+    (1, 8, 8, 8, 8, 0, 0, 16),        # first layer (3 channels padded to 8)
+    (2, 6, 7, 9, 16, 0, 0, 32),       # ragged voxel count (756, not a multiple of 128)
+    (1, 8, 8, 8, 32, 16, 1, 16),      # decoder: upsampled 32 channels + 16 skip
+    (1, 4, 4, 4, 64, 0, 0, 128),
+    (1, 4, 6, 4, 128, 64, 1, 64),     # deepest decoder input, 192 channels
+    (1, 16, 16, 16, 16, 0, 0, 16),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_conv_forward_dgrad_wgrad(env, case):
+    torch, nm, dn = env
+    n, d, h, w, c0, c1, coarse, cout = case
+    cin = c0 + c1
+    rng = np.random.default_rng(hash(case) % 2 ** 32)
+    s0 = (n, d // 2, h // 2, w // 2, c0) if coarse else (n, d, h, w, c0)
+    x0 = bf16(torch, rng.normal(size=s0))
+    x1 = bf16(torch, rng.normal(size=(n, d, h, w, c1))) if c1 else None
+    w3 = bf16(torch, rng.normal(0, 1 / np.sqrt(27 * cin), size=(cout, 27, cin)))
+    bias = torch.from_numpy(rng.normal(0, 0.1, cout).astype(np.float32))
+    kpad = nm.load().nm_conv3d_kpad(cin)
+    assert kpad % 128 == 0 and kpad >= 27 * cin
+    wg = weights_padded(torch, w3.float().numpy(), kpad).cuda()
+    desc = conv_desc(nm, n, d, h, w, c0, c1, coarse, cout)
+    x0g = x0.cuda()
+    x1g = x1.cuda() if x1 is not None else None
+    # reference input: concatenation at full resolution
+    X0 = as64(x0)
+    if coarse:
+        X0 = dn.upsample2(X0)
+    X = np.concatenate([X0, as64(x1)], axis=4) if x1 is not None else X0
+    W = as64(w3)
+
+    # forward with bias and ReLU
+    y = torch.empty((n, d, h, w, cout), dtype=torch.bfloat16, device="cuda")
+    nm.nm_conv3d_fwd(desc, x0g, x1g, wg, bias.cuda(), y, True)
+    pre = dn.conv3d(X, W, as64(bias))
+    ref = np.maximum(pre, 0)
+    absum = dn.conv3d(np.abs(X), np.abs(W)) + np.abs(as64(bias))
+    got = as64(y.cpu())
+    tol = 2.0 ** -8 * np.abs(ref) + 27 * cin * 2.0 ** -23 * absum + 1e-30
+    assert np.all(np.abs(got - ref) <= tol), np.max(np.abs(got - ref) / tol)
+
+    # input gradient
+    if cin in (16, 32, 48, 64, 96, 128, 192):
+        g = bf16(torch, rng.normal(size=(n, d, h, w, cout)))
+        dx = torch.empty((n, d, h, w, cin), dtype=torch.bfloat16, device="cuda")
+        nm.nm_conv3d_dgrad(desc, g.cuda(), wg, dx)
+        G = as64(g)
+        ref = dn.conv3d_dgrad(G, W)
+        absum = dn.conv3d_dgrad(np.abs(G), np.abs(W))
+        tol = 2.0 ** -8 * np.abs(ref) + 27 * cout * 2.0 ** -23 * absum + 1e-30
+        got = as64(dx.cpu())
+        assert np.all(np.abs(got - ref) <= tol), np.max(np.abs(got - ref) / tol)
+
+    # weight and bias gradients
+    if cout in (16, 32, 64, 128):
+        g = bf16(torch, rng.normal(size=(n, d, h, w, cout)))
+        dw = torch.full((cout, kpad), 7.0, dtype=torch.float32, device="cuda")
+        db = torch.zeros(cout, dtype=torch.float32, device="cuda")
+        nm.nm_conv3d_wgrad(desc, x0g, x1g, g.cuda(), dw, db)
+        G = as64(g)
+        rdw, rdb = dn.conv3d_wgrad(X, G)
+        adw, _ = dn.conv3d_wgrad(np.abs(X), np.abs(G))
+        got = dw.cpu().numpy().astype(np.float64)
+        m = n * d * h * w
+        assert np.all(got[:, 27 * cin:] == 0.0)               # padding columns stay exactly zero
+        got3 = got[:, :27 * cin].reshape(cout, 27, cin)
+        tol = m * 2.0 ** -22 * adw + 1e-30
+        assert np.all(np.abs(got3 - rdw) <= tol), np.max(np.abs(got3 - rdw) / tol)
+        assert np.allclose(db.cpu().numpy(), rdb, rtol=1e-5, atol=1e-4)
+
+
+def test_conv_is_deterministic(env):
+    torch, nm, dn = env
+    n, d, h, w, c0, cout = 1, 16, 16, 16, 16, 32
+    rng = np.random.default_rng(9)
+    x = bf16(torch, rng.normal(size=(n, d, h, w, c0))).cuda()
+    g = bf16(torch, rng.normal(size=(n, d, h, w, cout))).cuda()
+    desc = conv_desc(nm, n, d, h, w, c0, 0, 0, cout)
+    kpad = nm.load().nm_conv3d_kpad(c0)
+    outs = []
+    for _ in range(2):
+        dw = torch.empty((cout, kpad), dtype=torch.float32, device="cuda")
+        nm.nm_conv3d_wgrad(desc, x, None, g, dw)
+        outs.append(dw.cpu())
+    assert torch.equal(outs[0], outs[1])
