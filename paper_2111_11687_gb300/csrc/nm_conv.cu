@@ -191,8 +191,8 @@ __global__ void __launch_bounds__(kThreads) conv_wgrad_kernel(ConvGeom g, const 
   constexpr int kNcols = COUT < 32 ? 32 : COUT;
   constexpr uint32_t kABytes = kBM * kKS * 2;
   constexpr uint32_t kBBytes = COUT * kKS * 2;
-  constexpr uint32_t kSboA = (kBM / 8) * 128;       // K-adjacent core matrices of A
-  constexpr uint32_t kSboB = (COUT / 8) * 128;
+  constexpr uint32_t kSboA = (kBM / 8) * 128;       // distance of K-adjacent core matrices of A
+  constexpr uint32_t kSboB = (COUT / 8) * 128;      // ... and of B
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sa = smem;
   uint8_t* sb = smem + 2 * kABytes;
@@ -255,8 +255,10 @@ __global__ void __launch_bounds__(kThreads) conv_wgrad_kernel(ConvGeom g, const 
       const uint32_t a0 = tc::smem_u32(a), b0 = tc::smem_u32(bm);
 #pragma unroll
       for (int kk = 0; kk < kKS / 16; ++kk)
-        tc::mma_bf16(tmem, tc::smem_desc(a0 + kk * 2 * kSboA, 128, kSboA),
-                     tc::smem_desc(b0 + kk * 2 * kSboB, 128, kSboB), idesc, (s | kk) != 0);
+        // MN-major, no swizzle: the leading byte offset steps along K (8 voxels),
+        // the stride byte offset along MN (8 rows).
+        tc::mma_bf16(tmem, tc::smem_desc(a0 + kk * 2 * kSboA, kSboA, 128),
+                     tc::smem_desc(b0 + kk * 2 * kSboB, kSboB, 128), idesc, (s | kk) != 0);
       tc::mma_commit(&bar[buf]);
     }
     issued = s + 1;
