@@ -255,6 +255,75 @@ nm_status nm_conv3d_dgrad(const nm_conv3d_desc* desc, const uint16_t* dy, const 
 nm_status nm_conv3d_wgrad(const nm_conv3d_desc* desc, const uint16_t* x0, const uint16_t* x1,
                           const uint16_t* dy, float* dw, float* db, void* stream);
 
+/* ---- Dose denoiser: 3D U-Net trained and applied on the GPU ------------------
+ *
+ * Not in the paper.  A U-Net of `levels` levels with widths base_width * 2^i
+ * (default 4 levels, 16..128), two 3x3x3 convolutions with ReLU per level,
+ * 2x2x2 average pooling down, nearest upsampling concatenated with the skip
+ * up, and a 1x1x1 head added to input channel 0.  Inputs are BF16 [batch][P]
+ * [P][P][8]: channel 0 = log1p(low-count dose / s), 1 = density, 2 =
+ * log1p(activity / a), 3..7 = 0, where s and a are the body means (density >=
+ * 0.1) of the low-count dose and of the activity; the output and training
+ * target are log1p(dose / s).  Weights: FP32 master copy updated by Adam,
+ * BF16 copy for the convolutions; all convolutions on the tensor cores. */
+typedef struct {
+  int32_t patch;       /* P, a multiple of 2^(levels-1) (default 64) */
+  int32_t batch;       /* patches per step (default 2) */
+  int32_t levels;      /* 2..4 (default 4) */
+  int32_t base_width;  /* 16 or 32 (default 16) */
+  float lr, beta1, beta2, eps;  /* Adam (defaults 1e-3, 0.9, 0.999, 1e-8) */
+  uint64_t seed;       /* weight initialisation */
+  void* stream;        /* cudaStream_t; NULL = legacy default stream */
+} nm_denoise_options;
+
+typedef struct nm_denoiser nm_denoiser;
+
+void nm_denoise_options_default(nm_denoise_options* o);
+nm_status nm_denoise_create(nm_denoiser** out, const nm_denoise_options* opts);
+void nm_denoise_destroy(nm_denoiser* h);
+
+/* Number of FP32 parameters in the flat parameter vector, and the layout of
+ * layer i (0 .. 2*(2*levels-1)-1 in forward order e0a e0b e1a ... d0a d0b; i =
+ * that count is the head): weights at w_offset as [cout][kpad] with column
+ * k = tap * cin + ci, biases at b_offset. */
+int64_t nm_denoise_param_count(const nm_denoiser* h);
+nm_status nm_denoise_layer(const nm_denoiser* h, int32_t i, int32_t* cin, int32_t* cout, int32_t* kpad,
+                           int64_t* w_offset, int64_t* b_offset);
+
+/* Copies the parameters out (get), in (set, also refreshes the BF16 copy)
+ * and/or the last step's gradients out (grads); any may be NULL; host or
+ * device pointers of nm_denoise_param_count floats. */
+nm_status nm_denoise_params(nm_denoiser* h, float* get, const float* set, float* grads);
+
+/* One training step on device tensors: x [batch][P]^3[8] BF16, target
+ * [batch][P]^3 FP32, weight [batch][P]^3 FP32 or NULL (= 1); loss = mean of
+ * weight * (y - target)^2 over all voxels (written to *loss, host).  Forward,
+ * backward (tensor-core input and weight gradients) and, if lr > 0, an Adam
+ * update with learning rate lr. */
+nm_status nm_denoise_train_step(nm_denoiser* h, const uint16_t* x, const float* target, const float* weight,
+                                float lr, float* loss);
+
+/* Forward only: y [batch][P]^3 FP32 (device). */
+nm_status nm_denoise_forward(nm_denoiser* h, const uint16_t* x, float* y);
+
+/* Network inputs (and optionally targets and body weights) for n_patches
+ * patches at corners[3*i..] (x, y, z; may lie partly outside the volume,
+ * which reads as zero) of whole volumes [nz][ny][nx] (device FP32). */
+nm_status nm_denoise_make_patches(const float* dose, const float* density, const float* activity,
+                                  const float* dose_high, int32_t nx, int32_t ny, int32_t nz, float dose_scale,
+                                  float act_scale, const int32_t* corners, int32_t n_patches, int32_t patch,
+                                  uint16_t* x, float* target, float* weight, void* stream);
+
+/* Body means (density >= 0.1) of a dose map and an activity map (device). */
+nm_status nm_denoise_scales(const float* dose, const float* activity, const float* density, int64_t n,
+                            float* dose_scale, float* act_scale, void* stream);
+
+/* Denoises a whole low-count dose-rate map (device FP32 [nz][ny][nx]) with
+ * overlapping patches whose cores tile the volume; dose_out in the input's
+ * units. */
+nm_status nm_denoise_apply(nm_denoiser* h, const float* dose, const float* density, const float* activity,
+                           int32_t nx, int32_t ny, int32_t nz, float* dose_out);
+
 /* ---- Tally without device allocation ---------------------------------------
  *
  * For callers that cannot call cudaMalloc -- code running inside another

@@ -1,0 +1,778 @@
+// The dose denoiser: a 3D U-Net on BF16 channels-last volumes whose 3x3x3
+// convolutions run on the tensor cores (nm_conv.cu), trained with Adam on FP32
+// master weights.  Not part of the paper; it maps a low-count dose map plus
+// density and activity to a high-count one.
+//
+// Architecture (levels L, widths w_i = base * 2^i): per level two 3x3x3
+// convolutions with ReLU; 2x2x2 average pooling down; on the way up nearest
+// upsampling of the coarser output concatenated with the level's skip
+// (read directly by the convolution, never materialised), two convolutions
+// with ReLU; a 1x1x1 head whose output is added to input channel 0.
+//
+// Input channels (8, of which 3 used): 0 = log1p(low-count dose / s), 1 =
+// density, 2 = log1p(activity / a); the target is log1p(high-count dose / s).
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <random>
+#include <string>
+#include <vector>
+
+#include "nm_internal.cuh"
+
+using namespace nm;
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+// ---------------------------------------------------------------------------
+// Elementwise and reduction kernels.
+// ---------------------------------------------------------------------------
+__global__ void avgpool_kernel(const bf16* __restrict__ x, int n, int s, int c, bf16* __restrict__ y) {
+  // x [n][s][s][s][c] -> y [n][s/2]^3[c]
+  const int h = s >> 1;
+  const long long total = (long long)n * h * h * h * c;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int ch = (int)(i % c);
+    long long v = i / c;
+    const int xx = (int)(v % h); v /= h;
+    const int yy = (int)(v % h); v /= h;
+    const int zz = (int)(v % h);
+    const int b = (int)(v / h);
+    float sum = 0.0f;
+    for (int dz = 0; dz < 2; ++dz)
+      for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx)
+          sum += __bfloat162float(x[((((long long)b * s + 2 * zz + dz) * s + 2 * yy + dy) * s + 2 * xx + dx) * c + ch]);
+    y[i] = __float2bfloat16_rn(sum * 0.125f);
+  }
+}
+
+// g *= (act > 0)
+__global__ void relu_mask_kernel(bf16* __restrict__ g, const bf16* __restrict__ act, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    if (!(__bfloat162float(act[i]) > 0.0f)) g[i] = __float2bfloat16_rn(0.0f);
+}
+
+// Gradient of a decoder input [n][s]^3[c0 + c1] split into the coarse source
+// (summed over its 8 children, times the coarse activation's ReLU mask) and
+// the skip source (copied).
+__global__ void split_concat_grad_kernel(const bf16* __restrict__ dx, int n, int s, int c0, int c1,
+                                         const bf16* __restrict__ coarse_act, bf16* __restrict__ g_coarse,
+                                         bf16* __restrict__ g_skip) {
+  const int h = s >> 1, c = c0 + c1;
+  const long long nc = (long long)n * h * h * h * c0;
+  const long long ns = (long long)n * s * s * s * c1;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nc + ns;
+       i += (long long)gridDim.x * blockDim.x) {
+    if (i < nc) {
+      const int ch = (int)(i % c0);
+      long long v = i / c0;
+      const int xx = (int)(v % h); v /= h;
+      const int yy = (int)(v % h); v /= h;
+      const int zz = (int)(v % h);
+      const int b = (int)(v / h);
+      float sum = 0.0f;
+      for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+          for (int dx2 = 0; dx2 < 2; ++dx2)
+            sum += __bfloat162float(dx[((((long long)b * s + 2 * zz + dz) * s + 2 * yy + dy) * s + 2 * xx + dx2) * c + ch]);
+      g_coarse[i] = __float2bfloat16_rn(__bfloat162float(coarse_act[i]) > 0.0f ? sum : 0.0f);
+    } else {
+      const long long j = i - nc;
+      const long long vox = j / c1;
+      const int ch = (int)(j % c1);
+      g_skip[j] = dx[vox * c + c0 + ch];
+    }
+  }
+}
+
+// Encoder output gradient: (pool adjoint of the coarser gradient + skip gradient) * ReLU mask.
+__global__ void encoder_grad_kernel(const bf16* __restrict__ g_coarse, const bf16* __restrict__ g_skip,
+                                    const bf16* __restrict__ act, int n, int s, int c, bf16* __restrict__ g) {
+  const int h = s >> 1;
+  const long long total = (long long)n * s * s * s * c;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int ch = (int)(i % c);
+    long long v = i / c;
+    const int xx = (int)(v % s); v /= s;
+    const int yy = (int)(v % s); v /= s;
+    const int zz = (int)(v % s);
+    const int b = (int)(v / s);
+    float t = __bfloat162float(g_skip[i]);
+    t += 0.125f * __bfloat162float(g_coarse[((((long long)b * h + (zz >> 1)) * h + (yy >> 1)) * h + (xx >> 1)) * c + ch]);
+    g[i] = __float2bfloat16_rn(__bfloat162float(act[i]) > 0.0f ? t : 0.0f);
+  }
+}
+
+// Head: y = sum_c top[v][c] hw[c] + hb + x[v][0] (FP32).  With a target, also
+// the weighted squared-error loss partials, dL/dy, d top (BF16) and the head's
+// gradient partials.  One thread per voxel; per-CTA partials summed later in
+// a fixed order.
+__global__ void head_kernel(const bf16* __restrict__ top, int c, const bf16* __restrict__ x, int cx,
+                            const float* __restrict__ hw, const float* __restrict__ target,
+                            const float* __restrict__ weight, long long m, float inv_norm,
+                            float* __restrict__ y, bf16* __restrict__ dtop, float* __restrict__ part) {
+  // part per CTA: [loss, dhb, dhw[0..c-1]]
+  extern __shared__ float red[];  // [blockDim][c + 2]
+  const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int stride = c + 2;
+  float* mine = red + threadIdx.x * stride;
+  for (int j = 0; j < stride; ++j) mine[j] = 0.0f;
+  if (v < m) {
+    float t[64];
+    float out = hw[c] + __bfloat162float(x[v * cx]);
+    for (int j = 0; j < c; ++j) {
+      t[j] = __bfloat162float(top[v * c + j]);
+      out = fmaf(t[j], hw[j], out);
+    }
+    y[v] = out;
+    if (target) {
+      const float wv = weight ? weight[v] : 1.0f;
+      const float diff = out - target[v];
+      const float gy = 2.0f * wv * diff * inv_norm;
+      mine[0] = wv * diff * diff * inv_norm;
+      mine[1] = gy;
+      for (int j = 0; j < c; ++j) {
+        mine[2 + j] = gy * t[j];
+        dtop[v * c + j] = __float2bfloat16_rn(gy * hw[j]);
+      }
+    }
+  }
+  if (!target) return;
+  __syncthreads();
+  for (int j = threadIdx.x; j < stride; j += blockDim.x) {
+    float s = 0.0f;
+    for (int t2 = 0; t2 < (int)blockDim.x; ++t2) s += red[t2 * stride + j];
+    part[(long long)blockIdx.x * stride + j] = s;
+  }
+}
+
+__global__ void sum_parts_kernel(const float* __restrict__ part, int blocks, int stride, float* __restrict__ out) {
+  const int j = threadIdx.x;
+  if (j >= stride) return;
+  float s = 0.0f;
+  for (int b = 0; b < blocks; ++b) s += part[(long long)b * stride + j];
+  out[j] = s;
+}
+
+// Adam on FP32 master weights; writes the BF16 copy the convolutions read.
+__global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m1,
+                            float* __restrict__ m2, long long n, float lr, float b1, float b2, float eps,
+                            float c1, float c2, bf16* __restrict__ wb) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float a = b1 * m1[i] + (1.0f - b1) * gi;
+    const float b = b2 * m2[i] + (1.0f - b2) * gi * gi;
+    m1[i] = a;
+    m2[i] = b;
+    const float wi = w[i] - lr * (a / c1) / (sqrtf(b / c2) + eps);
+    w[i] = wi;
+    if (wb) wb[i] = __float2bfloat16_rn(wi);
+  }
+}
+
+__global__ void to_bf16_kernel(const float* __restrict__ a, long long n, bf16* __restrict__ b) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = __float2bfloat16_rn(a[i]);
+}
+
+// Network input channels from whole volumes, for patches at the given corners:
+// out [np][P][P][P][8] BF16 = (log1p(dose/s), density, log1p(act/a), 0...);
+// target [np][P]^3 = log1p(dose_high/s) (if dose_high), weight = (density >= 0.1).
+__global__ void make_patches_kernel(const float* __restrict__ dose, const float* __restrict__ density,
+                                    const float* __restrict__ act, const float* __restrict__ dose_high,
+                                    int nx, int ny, int nz, float inv_s, float inv_a,
+                                    const int* __restrict__ corners, int np, int P,
+                                    bf16* __restrict__ out, float* __restrict__ target,
+                                    float* __restrict__ weight) {
+  const long long per = (long long)P * P * P;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < per * np;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int p = (int)(i / per);
+    long long r = i % per;
+    const int x = (int)(r % P); r /= P;
+    const int y = (int)(r % P);
+    const int z = (int)(r / P);
+    const int gx = corners[3 * p] + x, gy = corners[3 * p + 1] + y, gz = corners[3 * p + 2] + z;
+    float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f, t = 0.0f, wv = 0.0f;
+    if (gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz) {
+      const long long v = ((long long)gz * ny + gy) * nx + gx;
+      c0 = log1pf(fmaxf(dose[v], 0.0f) * inv_s);
+      c1 = density[v];
+      c2 = log1pf(fmaxf(act[v], 0.0f) * inv_a);
+      if (dose_high) t = log1pf(fmaxf(dose_high[v], 0.0f) * inv_s);
+      wv = density[v] >= 0.1f ? 1.0f : 0.0f;
+    }
+    bf16* o = out + i * 8;
+    o[0] = __float2bfloat16_rn(c0);
+    o[1] = __float2bfloat16_rn(c1);
+    o[2] = __float2bfloat16_rn(c2);
+    for (int k = 3; k < 8; ++k) o[k] = __float2bfloat16_rn(0.0f);
+    if (target) target[i] = t;
+    if (weight) weight[i] = wv;
+  }
+}
+
+// Writes the central region of predicted patches back into the volume:
+// dose_out = s * expm1(y) for voxels of the patch's core box.
+__global__ void scatter_patches_kernel(const float* __restrict__ y, const int* __restrict__ corners,
+                                       const int* __restrict__ lo, const int* __restrict__ hi, int np, int P,
+                                       int nx, int ny, int nz, float s, float* __restrict__ dose_out) {
+  const long long per = (long long)P * P * P;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < per * np;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int p = (int)(i / per);
+    long long r = i % per;
+    const int x = (int)(r % P); r /= P;
+    const int yy = (int)(r % P);
+    const int z = (int)(r / P);
+    if (x < lo[3 * p] || x >= hi[3 * p] || yy < lo[3 * p + 1] || yy >= hi[3 * p + 1] || z < lo[3 * p + 2] ||
+        z >= hi[3 * p + 2])
+      continue;
+    const int gx = corners[3 * p] + x, gy = corners[3 * p + 1] + yy, gz = corners[3 * p + 2] + z;
+    if (gx < 0 || gx >= nx || gy < 0 || gy >= ny || gz < 0 || gz >= nz) continue;
+    dose_out[((long long)gz * ny + gy) * nx + gx] = s * expm1f(y[i]);
+  }
+}
+
+// Masked mean of a volume: partial sums per CTA (fixed tree), then one CTA.
+__global__ void masked_mean_partial(const float* __restrict__ a, const float* __restrict__ density, long long n,
+                                    double* __restrict__ part) {
+  __shared__ double sv[256], sc[256];
+  double v = 0.0, c = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    if (density[i] >= 0.1f) { v += a[i]; c += 1.0; }
+  sv[threadIdx.x] = v;
+  sc[threadIdx.x] = c;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) { sv[threadIdx.x] += sv[threadIdx.x + o]; sc[threadIdx.x] += sc[threadIdx.x + o]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { part[2 * blockIdx.x] = sv[0]; part[2 * blockIdx.x + 1] = sc[0]; }
+}
+
+int grid1d(long long n) { return (int)std::min<long long>((n + 255) / 256, 8192); }
+
+struct Layer {
+  std::string name;
+  int cin, c0, c1, coarse, cout, kpad, size, level;
+  long long w_off, b_off;  // offsets into the flat parameter vector (floats)
+};
+
+}  // namespace
+
+struct nm_denoiser {
+  nm_denoise_options opt{};
+  cudaStream_t s = nullptr;
+  int P = 64, B = 1, L = 4, base = 16, cx = 8;
+  std::vector<int> widths;
+  std::vector<Layer> layers;
+  long long n_params = 0;
+  long long head_off = 0;
+  // parameters
+  float* w = nullptr;     // FP32 master, flat
+  float* g = nullptr;     // gradients, flat
+  float* m1 = nullptr;
+  float* m2 = nullptr;
+  bf16* wb = nullptr;     // BF16 copy, flat (same offsets)
+  bf16* wflip = nullptr;  // flipped weights of the layer being back-propagated
+  long long wflip_elems = 0;
+  // activations [level tensors]
+  std::vector<bf16*> ea, eb, pool, da, db;
+  bf16 *gA = nullptr, *gB = nullptr, *gC = nullptr, *gD = nullptr;  // gradient scratch (largest size)
+  std::vector<bf16*> gskip;
+  bf16* x_in = nullptr;
+  float* y = nullptr;
+  float* target = nullptr;
+  float* weight = nullptr;
+  bf16* dtop = nullptr;
+  float* head_part = nullptr;
+  float* head_sum = nullptr;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  uint32_t* status = nullptr;
+  long long step = 0;
+  int head_blocks = 0;
+
+  ~nm_denoiser() {
+    auto f = [](void* p) { if (p) cudaFree(p); };
+    f(w); f(g); f(m1); f(m2); f(wb); f(wflip);
+    for (auto p : ea) f(p);
+    for (auto p : eb) f(p);
+    for (auto p : pool) f(p);
+    for (auto p : da) f(p);
+    for (auto p : db) f(p);
+    for (auto p : gskip) f(p);
+    f(gA); f(gB); f(gC); f(gD); f(x_in); f(y); f(target); f(weight); f(dtop); f(head_part); f(head_sum);
+    f(ws); f(status);
+  }
+
+  long long vox(int level) const {
+    const long long s = P >> level;
+    return (long long)B * s * s * s;
+  }
+  nm_conv3d_desc desc(const Layer& l) const {
+    nm_conv3d_desc d;
+    d.n = B; d.d = d.h = d.w = l.size;
+    d.c0 = l.c0; d.c1 = l.c1; d.src0_coarse = l.coarse; d.cout = l.cout;
+    return d;
+  }
+};
+
+namespace {
+
+nm_status fail(nm_status st, const char* msg) {
+  set_error_message(msg);
+  return st;
+}
+nm_status cfail(cudaError_t e, const char* what) {
+  char buf[256];
+  snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+  set_error_message(buf);
+  return e == cudaErrorMemoryAllocation ? NM_ERR_OOM : NM_ERR_CUDA;
+}
+#define CK(call, what)                              \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return cfail(e_, what);  \
+  } while (0)
+
+template <class T>
+cudaError_t dmalloc(T** p, long long n) {
+  return cudaMalloc((void**)p, (size_t)std::max<long long>(n, 1) * sizeof(T));
+}
+
+bool dev_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+nm_status check_status(nm_denoiser* h) {
+  uint32_t flags = 0;
+  CK(cudaMemcpyAsync(&flags, h->status, 4, cudaMemcpyDeviceToHost, h->s), "status");
+  CK(cudaStreamSynchronize(h->s), "denoiser");
+  if (flags) {
+    cudaMemsetAsync(h->status, 0, 4, h->s);
+    return fail(NM_ERR_DEVICE, "tensor-core wait timed out");
+  }
+  return NM_OK;
+}
+
+nm_status forward(nm_denoiser* h) {
+  cudaStream_t s = h->s;
+  const int L = h->L;
+  const bf16* in = h->x_in;
+  int li = 0;
+  for (int i = 0; i < L; ++i) {
+    const Layer& la = h->layers[li++];
+    const Layer& lb = h->layers[li++];
+    CK(conv3d_fwd(h->desc(la), in, nullptr, h->wb + la.w_off, h->w + la.b_off, h->ea[i], 1, h->status, s), "conv");
+    CK(conv3d_fwd(h->desc(lb), h->ea[i], nullptr, h->wb + lb.w_off, h->w + lb.b_off, h->eb[i], 1, h->status, s), "conv");
+    if (i < L - 1) {
+      const long long n = h->vox(i + 1) * h->widths[i];
+      avgpool_kernel<<<grid1d(n), 256, 0, s>>>(h->eb[i], h->B, h->P >> i, h->widths[i], h->pool[i]);
+      in = h->pool[i];
+    }
+  }
+  const bf16* coarse = h->eb[L - 1];
+  for (int i = L - 2; i >= 0; --i) {
+    const Layer& la = h->layers[li++];
+    const Layer& lb = h->layers[li++];
+    CK(conv3d_fwd(h->desc(la), coarse, h->eb[i], h->wb + la.w_off, h->w + la.b_off, h->da[i], 1, h->status, s), "conv");
+    CK(conv3d_fwd(h->desc(lb), h->da[i], nullptr, h->wb + lb.w_off, h->w + lb.b_off, h->db[i], 1, h->status, s), "conv");
+    coarse = h->db[i];
+  }
+  return NM_OK;
+}
+
+nm_status head(nm_denoiser* h, bool train) {
+  cudaStream_t s = h->s;
+  const long long m = h->vox(0);
+  const int c = h->widths[0];
+  const int threads = 128;
+  const size_t smem = (size_t)threads * (c + 2) * sizeof(float);
+  // loss normalisation: mean over all voxels of the batch
+  head_kernel<<<h->head_blocks, threads, smem, s>>>(h->db[0], c, h->x_in, h->cx, h->w + h->head_off,
+                                                    train ? h->target : nullptr, train ? h->weight : nullptr, m,
+                                                    1.0f / (float)m, h->y, h->dtop, h->head_part);
+  CK(cudaGetLastError(), "head");
+  if (train) {
+    sum_parts_kernel<<<1, 128, 0, s>>>(h->head_part, h->head_blocks, c + 2, h->head_sum);
+    CK(cudaGetLastError(), "head");
+  }
+  return NM_OK;
+}
+
+nm_status backward(nm_denoiser* h) {
+  cudaStream_t s = h->s;
+  const int L = h->L;
+  // head gradients: head_sum = [loss, dhb, dhw...] -> g[head_off + j] = dhw[j], g[head_off + c] = dhb
+  const int c0w = h->widths[0];
+  CK(cudaMemcpyAsync(h->g + h->head_off, h->head_sum + 2, c0w * sizeof(float), cudaMemcpyDeviceToDevice, s), "head grad");
+  CK(cudaMemcpyAsync(h->g + h->head_off + c0w, h->head_sum + 1, sizeof(float), cudaMemcpyDeviceToDevice, s), "head grad");
+  auto lay = [&](const std::string& n) -> const Layer& {
+    for (auto& l : h->layers) if (l.name == n) return l;
+    return h->layers[0];
+  };
+  auto conv_back = [&](const Layer& l, const bf16* x0, const bf16* x1, const bf16* gout, bf16* gin) -> nm_status {
+    // weight/bias gradients, then (if gin) the input gradient through flipped weights
+    CK(conv3d_wgrad(h->desc(l), x0, x1, gout, h->g + l.w_off, h->g + l.b_off, h->ws, h->status, s), "wgrad");
+    if (gin) {
+      nm_conv3d_desc fd = h->desc(l);
+      CK(conv3d_flip_weights(fd, h->wb + l.w_off, h->wflip, s), "flip");
+      nm_conv3d_desc bd;
+      memset(&bd, 0, sizeof bd);
+      bd.n = fd.n; bd.d = bd.h = bd.w = l.size;
+      bd.c0 = l.cout; bd.cout = l.c0 + l.c1;
+      CK(conv3d_fwd(bd, gout, nullptr, h->wflip, nullptr, gin, 0, h->status, s), "dgrad");
+    }
+    return NM_OK;
+  };
+  nm_status st;
+  // gradient wrt the top decoder output
+  bf16* g = h->dtop;
+  for (int i = 0; i < L - 1; ++i) {
+    const Layer& lb = lay("d" + std::to_string(i) + "b");
+    const Layer& la = lay("d" + std::to_string(i) + "a");
+    const long long nb = h->vox(i) * h->widths[i];
+    relu_mask_kernel<<<grid1d(nb), 256, 0, s>>>(g, h->db[i], nb);
+    if ((st = conv_back(lb, h->da[i], nullptr, g, h->gA)) != NM_OK) return st;
+    relu_mask_kernel<<<grid1d(nb), 256, 0, s>>>(h->gA, h->da[i], nb);
+    const bf16* coarse = i + 1 <= L - 2 ? h->db[i + 1] : h->eb[L - 1];
+    if ((st = conv_back(la, coarse, h->eb[i], h->gA, h->gB)) != NM_OK) return st;
+    const long long total = h->vox(i + 1) * h->widths[i + 1] + nb;
+    split_concat_grad_kernel<<<grid1d(total), 256, 0, s>>>(h->gB, h->B, h->P >> i, h->widths[i + 1], h->widths[i],
+                                                           coarse, h->gC, h->gskip[i]);
+    // gC now holds the (masked) gradient wrt the coarser output; move it to gD
+    std::swap(h->gC, h->gD);
+    g = h->gD;
+  }
+  // encoder, deepest first; g = gradient wrt e_{L-1} output (already masked by its ReLU)
+  for (int i = L - 1; i >= 0; --i) {
+    const Layer& lb = lay("e" + std::to_string(i) + "b");
+    const Layer& la = lay("e" + std::to_string(i) + "a");
+    const long long nb = h->vox(i) * h->widths[i];
+    if (i < L - 1) {
+      encoder_grad_kernel<<<grid1d(nb), 256, 0, s>>>(g, h->gskip[i], h->eb[i], h->B, h->P >> i, h->widths[i], h->gC);
+      g = h->gC;
+    }
+    if ((st = conv_back(lb, h->ea[i], nullptr, g, h->gA)) != NM_OK) return st;
+    relu_mask_kernel<<<grid1d(nb), 256, 0, s>>>(h->gA, h->ea[i], nb);
+    const bf16* in = i == 0 ? h->x_in : h->pool[i - 1];
+    if ((st = conv_back(la, in, nullptr, h->gA, i > 0 ? h->gB : nullptr)) != NM_OK) return st;
+    if (i > 0) {
+      std::swap(h->gB, h->gD);
+      g = h->gD;  // gradient wrt pool[i-1] = pooled e_{i-1} output
+    }
+  }
+  CK(cudaGetLastError(), "backward");
+  return NM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void nm_denoise_options_default(nm_denoise_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof *o);
+  o->patch = 64;
+  o->batch = 2;
+  o->levels = 4;
+  o->base_width = 16;
+  o->lr = 1e-3f;
+  o->beta1 = 0.9f;
+  o->beta2 = 0.999f;
+  o->eps = 1e-8f;
+  o->seed = 1;
+}
+
+nm_status nm_denoise_create(nm_denoiser** out, const nm_denoise_options* opts) {
+  if (!out) return fail(NM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  nm_denoise_options o;
+  if (opts) o = *opts; else nm_denoise_options_default(&o);
+  if (o.levels < 2 || o.levels > 4 || o.patch % (1 << (o.levels - 1)) || o.patch < 8 || o.batch < 1 ||
+      !(o.base_width == 16 || o.base_width == 32) || (o.base_width << (o.levels - 1)) > 128)
+    return fail(NM_ERR_ARG, "denoiser: levels 2..4, patch a multiple of 2^(levels-1), base width 16 or 32, widths <= 128");
+  nm_denoiser* h = new nm_denoiser();
+  auto bail = [&](nm_status st) { delete h; return st; };
+  h->opt = o;
+  h->s = (cudaStream_t)o.stream;
+  h->P = o.patch; h->B = o.batch; h->L = o.levels; h->base = o.base_width;
+  for (int i = 0; i < h->L; ++i) h->widths.push_back(h->base << i);
+  // layers in forward order
+  long long off = 0;
+  int c = h->cx;
+  auto add = [&](const std::string& n, int c0, int c1, int coarse, int cout, int level) {
+    Layer l;
+    l.name = n; l.c0 = c0; l.c1 = c1; l.cin = c0 + c1; l.coarse = coarse; l.cout = cout;
+    l.kpad = conv_kpad(l.cin); l.size = h->P >> level; l.level = level;
+    l.w_off = off; off += (long long)cout * l.kpad;
+    l.b_off = off; off += cout;
+    off = (off + 7) / 8 * 8;  // 16-byte aligned BF16 weights
+    h->layers.push_back(l);
+  };
+  for (int i = 0; i < h->L; ++i) {
+    add("e" + std::to_string(i) + "a", c, 0, 0, h->widths[i], i);
+    add("e" + std::to_string(i) + "b", h->widths[i], 0, 0, h->widths[i], i);
+    c = h->widths[i];
+  }
+  for (int i = h->L - 2; i >= 0; --i) {
+    add("d" + std::to_string(i) + "a", c, h->widths[i], 1, h->widths[i], i);
+    add("d" + std::to_string(i) + "b", h->widths[i], 0, 0, h->widths[i], i);
+    c = h->widths[i];
+  }
+  h->head_off = off;
+  off += h->widths[0] + 1;
+  h->n_params = (off + 7) / 8 * 8;
+
+  cudaError_t e;
+  if ((e = dmalloc(&h->w, h->n_params)) || (e = dmalloc(&h->g, h->n_params)) || (e = dmalloc(&h->m1, h->n_params)) ||
+      (e = dmalloc(&h->m2, h->n_params)) || (e = dmalloc(&h->wb, h->n_params)) || (e = dmalloc(&h->status, 1)))
+    return bail(cfail(e, "denoiser parameters"));
+  long long flip = 0;
+  size_t ws = 0;
+  for (auto& l : h->layers) {
+    flip = std::max<long long>(flip, (long long)l.cin * conv_kpad(l.cout));
+    ws = std::max(ws, conv_wgrad_workspace(h->desc(l)));
+  }
+  h->wflip_elems = flip;
+  h->ws_bytes = ws;
+  if ((e = dmalloc(&h->wflip, flip)) || (e = cudaMalloc(&h->ws, ws))) return bail(cfail(e, "denoiser workspace"));
+  h->ea.resize(h->L); h->eb.resize(h->L); h->pool.resize(h->L); h->da.resize(h->L); h->db.resize(h->L);
+  h->gskip.resize(h->L);
+  long long gmax = 0;
+  for (int i = 0; i < h->L; ++i) {
+    const long long n = h->vox(i) * h->widths[i];
+    if ((e = dmalloc(&h->ea[i], n)) || (e = dmalloc(&h->eb[i], n))) return bail(cfail(e, "activations"));
+    if (i < h->L - 1) {
+      if ((e = dmalloc(&h->pool[i], h->vox(i + 1) * h->widths[i])) || (e = dmalloc(&h->da[i], n)) ||
+          (e = dmalloc(&h->db[i], n)) || (e = dmalloc(&h->gskip[i], n)))
+        return bail(cfail(e, "activations"));
+      gmax = std::max(gmax, h->vox(i) * (long long)(h->widths[i] + h->widths[i + 1]));
+    }
+    gmax = std::max(gmax, n);
+  }
+  const long long m = h->vox(0);
+  h->head_blocks = (int)((m + 127) / 128);
+  if ((e = dmalloc(&h->gA, gmax)) || (e = dmalloc(&h->gB, gmax)) || (e = dmalloc(&h->gC, gmax)) ||
+      (e = dmalloc(&h->gD, gmax)) || (e = dmalloc(&h->x_in, m * h->cx)) || (e = dmalloc(&h->y, m)) ||
+      (e = dmalloc(&h->target, m)) || (e = dmalloc(&h->weight, m)) || (e = dmalloc(&h->dtop, m * h->widths[0])) ||
+      (e = dmalloc(&h->head_part, (long long)h->head_blocks * (h->widths[0] + 2))) ||
+      (e = dmalloc(&h->head_sum, h->widths[0] + 2)))
+    return bail(cfail(e, "denoiser buffers"));
+  // He-normal initialisation on the host (seeded), zero padding columns.
+  std::vector<float> w(h->n_params, 0.0f);
+  std::mt19937_64 rng(o.seed);
+  std::normal_distribution<double> nd(0.0, 1.0);
+  for (auto& l : h->layers) {
+    const double std_ = std::sqrt(2.0 / (27.0 * l.cin));
+    for (int co = 0; co < l.cout; ++co)
+      for (int k = 0; k < 27 * l.cin; ++k) w[l.w_off + (long long)co * l.kpad + k] = (float)(std_ * nd(rng));
+  }
+  // the head starts at zero: the initial network is the identity on channel 0
+  if ((e = cudaMemcpy(h->w, w.data(), h->n_params * sizeof(float), cudaMemcpyHostToDevice)) ||
+      (e = cudaMemset(h->g, 0, h->n_params * sizeof(float))) || (e = cudaMemset(h->m1, 0, h->n_params * sizeof(float))) ||
+      (e = cudaMemset(h->m2, 0, h->n_params * sizeof(float))) || (e = cudaMemset(h->status, 0, 4)))
+    return bail(cfail(e, "denoiser init"));
+  to_bf16_kernel<<<grid1d(h->n_params), 256, 0, h->s>>>(h->w, h->n_params, h->wb);
+  if ((e = cudaStreamSynchronize(h->s))) return bail(cfail(e, "denoiser init"));
+  *out = h;
+  return NM_OK;
+}
+
+void nm_denoise_destroy(nm_denoiser* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->s);
+  delete h;
+}
+
+int64_t nm_denoise_param_count(const nm_denoiser* h) { return h ? h->n_params : 0; }
+
+nm_status nm_denoise_layer(const nm_denoiser* h, int32_t i, int32_t* cin, int32_t* cout, int32_t* kpad,
+                           int64_t* w_offset, int64_t* b_offset) {
+  if (!h || i < 0 || i > (int)h->layers.size()) return fail(NM_ERR_ARG, "layer index out of range");
+  if (i == (int)h->layers.size()) {  // the head
+    if (cin) *cin = h->widths[0];
+    if (cout) *cout = 1;
+    if (kpad) *kpad = h->widths[0];
+    if (w_offset) *w_offset = h->head_off;
+    if (b_offset) *b_offset = h->head_off + h->widths[0];
+    return NM_OK;
+  }
+  const Layer& l = h->layers[i];
+  if (cin) *cin = l.cin;
+  if (cout) *cout = l.cout;
+  if (kpad) *kpad = l.kpad;
+  if (w_offset) *w_offset = l.w_off;
+  if (b_offset) *b_offset = l.b_off;
+  return NM_OK;
+}
+
+nm_status nm_denoise_params(nm_denoiser* h, float* get, const float* set, float* grads) {
+  if (!h) return fail(NM_ERR_ARG, "handle is NULL");
+  const size_t bytes = h->n_params * sizeof(float);
+  if (set) {
+    CK(cudaMemcpyAsync(h->w, set, bytes, cudaMemcpyDefault, h->s), "params");
+    to_bf16_kernel<<<grid1d(h->n_params), 256, 0, h->s>>>(h->w, h->n_params, h->wb);
+  }
+  if (get) CK(cudaMemcpyAsync(get, h->w, bytes, cudaMemcpyDefault, h->s), "params");
+  if (grads) CK(cudaMemcpyAsync(grads, h->g, bytes, cudaMemcpyDefault, h->s), "params");
+  CK(cudaStreamSynchronize(h->s), "params");
+  return NM_OK;
+}
+
+nm_status nm_denoise_train_step(nm_denoiser* h, const uint16_t* x, const float* target, const float* weight,
+                                float lr, float* loss) {
+  if (!h || !x || !target) return fail(NM_ERR_ARG, "bad arguments");
+  if (!dev_ptr(x) || !dev_ptr(target) || (weight && !dev_ptr(weight)))
+    return fail(NM_ERR_ARG, "x, target and weight must be device pointers");
+  cudaStream_t s = h->s;
+  const long long m = h->vox(0);
+  CK(cudaMemcpyAsync(h->x_in, x, m * h->cx * 2, cudaMemcpyDeviceToDevice, s), "input");
+  CK(cudaMemcpyAsync(h->target, target, m * 4, cudaMemcpyDeviceToDevice, s), "input");
+  if (weight) CK(cudaMemcpyAsync(h->weight, weight, m * 4, cudaMemcpyDeviceToDevice, s), "input");
+  else {
+    std::vector<float> ones(m, 1.0f);
+    CK(cudaMemcpyAsync(h->weight, ones.data(), m * 4, cudaMemcpyHostToDevice, s), "input");
+    CK(cudaStreamSynchronize(s), "input");
+  }
+  nm_status st;
+  if ((st = forward(h)) != NM_OK) return st;
+  if ((st = head(h, true)) != NM_OK) return st;
+  if ((st = backward(h)) != NM_OK) return st;
+  if (lr > 0.0f) {
+    h->step += 1;
+    const float c1 = 1.0f - std::pow(h->opt.beta1, (float)h->step);
+    const float c2 = 1.0f - std::pow(h->opt.beta2, (float)h->step);
+    adam_kernel<<<grid1d(h->n_params), 256, 0, s>>>(h->w, h->g, h->m1, h->m2, h->n_params, lr, h->opt.beta1,
+                                                   h->opt.beta2, h->opt.eps, c1, c2, h->wb);
+    CK(cudaGetLastError(), "adam");
+  }
+  if (loss) CK(cudaMemcpyAsync(loss, h->head_sum, sizeof(float), cudaMemcpyDeviceToHost, s), "loss");
+  return check_status(h);
+}
+
+nm_status nm_denoise_forward(nm_denoiser* h, const uint16_t* x, float* y) {
+  if (!h || !x || !y || !dev_ptr(x) || !dev_ptr(y)) return fail(NM_ERR_ARG, "x and y must be device pointers");
+  cudaStream_t s = h->s;
+  const long long m = h->vox(0);
+  CK(cudaMemcpyAsync(h->x_in, x, m * h->cx * 2, cudaMemcpyDeviceToDevice, s), "input");
+  nm_status st;
+  if ((st = forward(h)) != NM_OK) return st;
+  if ((st = head(h, false)) != NM_OK) return st;
+  CK(cudaMemcpyAsync(y, h->y, m * 4, cudaMemcpyDeviceToDevice, s), "output");
+  return check_status(h);
+}
+
+nm_status nm_denoise_make_patches(const float* dose, const float* density, const float* activity,
+                                  const float* dose_high, int32_t nx, int32_t ny, int32_t nz, float dose_scale,
+                                  float act_scale, const int32_t* corners, int32_t n_patches, int32_t patch,
+                                  uint16_t* x, float* target, float* weight, void* stream) {
+  if (!dose || !density || !activity || !corners || !x || nx <= 0 || ny <= 0 || nz <= 0 || n_patches <= 0 ||
+      patch <= 0 || !(dose_scale > 0) || !(act_scale > 0))
+    return fail(NM_ERR_ARG, "bad arguments");
+  if (!dev_ptr(dose) || !dev_ptr(density) || !dev_ptr(activity) || !dev_ptr(corners) || !dev_ptr(x) ||
+      (dose_high && !dev_ptr(dose_high)) || (target && !dev_ptr(target)) || (weight && !dev_ptr(weight)))
+    return fail(NM_ERR_ARG, "all arrays must be device pointers");
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long n = (long long)patch * patch * patch * n_patches;
+  make_patches_kernel<<<grid1d(n), 256, 0, s>>>(dose, density, activity, dose_high, nx, ny, nz, 1.0f / dose_scale,
+                                                1.0f / act_scale, corners, n_patches, patch, (bf16*)x, target, weight);
+  CK(cudaGetLastError(), "make_patches");
+  CK(cudaStreamSynchronize(s), "make_patches");
+  return NM_OK;
+}
+
+nm_status nm_denoise_scales(const float* dose, const float* activity, const float* density, int64_t n,
+                            float* dose_scale, float* act_scale, void* stream) {
+  if (!dose || !activity || !density || n <= 0 || !dose_scale || !act_scale) return fail(NM_ERR_ARG, "bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  double* part = nullptr;
+  const int blocks = 1024;
+  CK(cudaMallocAsync((void**)&part, blocks * 2 * sizeof(double), s), "scales");
+  double r[2][2 * 1024];
+  for (int k = 0; k < 2; ++k) {
+    masked_mean_partial<<<blocks, 256, 0, s>>>(k == 0 ? dose : activity, density, n, part);
+    cudaMemcpyAsync(r[k], part, blocks * 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  }
+  cudaFreeAsync(part, s);
+  CK(cudaStreamSynchronize(s), "scales");
+  double v[2] = {0, 0}, c = 0;
+  for (int k = 0; k < 2; ++k)
+    for (int b = 0; b < blocks; ++b) {
+      v[k] += r[k][2 * b];
+      if (k == 0) c += r[k][2 * b + 1];
+    }
+  *dose_scale = c > 0 && v[0] > 0 ? (float)(v[0] / c) : 1.0f;
+  *act_scale = c > 0 && v[1] > 0 ? (float)(v[1] / c) : 1.0f;
+  return NM_OK;
+}
+
+// Whole-volume inference with overlapping patches: each patch keeps its core
+// (a margin of patch/8 voxels is dropped on interior faces).
+nm_status nm_denoise_apply(nm_denoiser* h, const float* dose, const float* density, const float* activity,
+                           int32_t nx, int32_t ny, int32_t nz, float* dose_out) {
+  if (!h || !dose || !density || !activity || !dose_out || nx <= 0 || ny <= 0 || nz <= 0)
+    return fail(NM_ERR_ARG, "bad arguments");
+  if (!dev_ptr(dose) || !dev_ptr(density) || !dev_ptr(activity) || !dev_ptr(dose_out))
+    return fail(NM_ERR_ARG, "volumes must be device pointers");
+  cudaStream_t s = h->s;
+  const int P = h->P, mg = P / 8, core = P - 2 * mg;
+  float ds = 1, as = 1;
+  nm_status st = nm_denoise_scales(dose, activity, density, (int64_t)nx * ny * nz, &ds, &as, s);
+  if (st != NM_OK) return st;
+  // patch corners: cores tile the volume
+  std::vector<int> corners, lo, hi;
+  auto starts = [&](int n) {
+    std::vector<int> v;
+    for (int c = 0; c < n; c += core) v.push_back(c - mg);
+    return v;
+  };
+  for (int z : starts(nz))
+    for (int y : starts(ny))
+      for (int x : starts(nx)) {
+        corners.insert(corners.end(), {x, y, z});
+        lo.insert(lo.end(), {mg, mg, mg});
+        hi.insert(hi.end(), {mg + core, mg + core, mg + core});
+      }
+  const int np = (int)(corners.size() / 3);
+  int* dcorn = nullptr;
+  CK(cudaMallocAsync((void**)&dcorn, corners.size() * 3 * sizeof(int), s), "apply");
+  CK(cudaMemcpyAsync(dcorn, corners.data(), corners.size() * sizeof(int), cudaMemcpyHostToDevice, s), "apply");
+  CK(cudaMemcpyAsync(dcorn + corners.size(), lo.data(), lo.size() * sizeof(int), cudaMemcpyHostToDevice, s), "apply");
+  CK(cudaMemcpyAsync(dcorn + 2 * corners.size(), hi.data(), hi.size() * sizeof(int), cudaMemcpyHostToDevice, s), "apply");
+  const long long per = (long long)P * P * P;
+  for (int p0 = 0; p0 < np && st == NM_OK; p0 += h->B) {
+    const int cnt = std::min(h->B, np - p0);
+    const long long n = per * cnt;
+    make_patches_kernel<<<grid1d(n), 256, 0, s>>>(dose, density, activity, nullptr, nx, ny, nz, 1.0f / ds, 1.0f / as,
+                                                  dcorn + 3 * p0, cnt, P, h->x_in, nullptr, nullptr);
+    if (cnt < h->B) cudaMemsetAsync(h->x_in + n * h->cx, 0, (per * h->B - n) * h->cx * 2, s);
+    if ((st = forward(h)) != NM_OK) break;
+    if ((st = head(h, false)) != NM_OK) break;
+    scatter_patches_kernel<<<grid1d(n), 256, 0, s>>>(h->y, dcorn + 3 * p0, dcorn + corners.size() + 3 * p0,
+                                                     dcorn + 2 * corners.size() + 3 * p0, cnt, P, nx, ny, nz, ds,
+                                                     dose_out);
+  }
+  cudaFreeAsync(dcorn, s);
+  if (st != NM_OK) return st;
+  CK(cudaGetLastError(), "apply");
+  return check_status(h);
+}
+
+}  // extern "C"

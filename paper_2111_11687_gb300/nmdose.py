@@ -70,6 +70,12 @@ class nm_conv3d_desc(C.Structure):
     _fields_ = [(k, C.c_int32) for k in ("n", "d", "h", "w", "c0", "c1", "src0_coarse", "cout")]
 
 
+class nm_denoise_options(C.Structure):
+    _fields_ = [("patch", C.c_int32), ("batch", C.c_int32), ("levels", C.c_int32), ("base_width", C.c_int32),
+                ("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("seed", C.c_uint64), ("stream", C.c_void_p)]
+
+
 # Every entry point declared in include/nm_dose.h, with its ctypes signature.
 _SIGS = {
     "nm_options_default": (None, [C.POINTER(nm_options)]),
@@ -95,6 +101,23 @@ _SIGS = {
     "nm_conv3d_dgrad": (C.c_int, [C.POINTER(nm_conv3d_desc), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "nm_conv3d_wgrad": (C.c_int, [C.POINTER(nm_conv3d_desc), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_void_p]),
+    "nm_denoise_options_default": (None, [C.POINTER(nm_denoise_options)]),
+    "nm_denoise_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(nm_denoise_options)]),
+    "nm_denoise_destroy": (None, [C.c_void_p]),
+    "nm_denoise_param_count": (C.c_int64, [C.c_void_p]),
+    "nm_denoise_layer": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                   C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "nm_denoise_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "nm_denoise_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_float,
+                                        C.POINTER(C.c_float)]),
+    "nm_denoise_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "nm_denoise_make_patches": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
+                                          C.c_int32, C.c_float, C.c_float, C.c_void_p, C.c_int32, C.c_int32,
+                                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "nm_denoise_scales": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_float),
+                                    C.POINTER(C.c_float), C.c_void_p]),
+    "nm_denoise_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
+                                   C.c_int32, C.c_void_p]),
     "nm_dose_tally_noalloc": (C.c_int, [C.POINTER(nm_grid), C.POINTER(nm_materials), C.c_void_p,
                                         C.POINTER(nm_options), C.c_uint64, C.c_uint64, C.c_void_p,
                                         C.POINTER(nm_counters)]),
@@ -308,6 +331,74 @@ def nm_conv3d_dgrad(desc, dy, w, dx, stream=None):
 
 def nm_conv3d_wgrad(desc, x0, x1, dy, dw, db=None, stream=None):
     _check(load().nm_conv3d_wgrad(C.byref(desc), ptr(x0), ptr(x1), ptr(dy), ptr(dw), ptr(db), _stream_ptr(stream)))
+
+
+class Denoiser:
+    """Owning wrapper of an nm_denoiser handle (all arrays are device tensors)."""
+
+    def __init__(self, **kw):
+        o = nm_denoise_options()
+        load().nm_denoise_options_default(C.byref(o))
+        for k, v in kw.items():
+            setattr(o, k, _stream_ptr(v) if k == "stream" else v)
+        self.opts = o
+        self.h = C.c_void_p()
+        _check(load().nm_denoise_create(C.byref(self.h), C.byref(o)))
+        self.n_params = int(load().nm_denoise_param_count(self.h))
+
+    def layers(self):
+        out = []
+        i = 0
+        while True:
+            ci, co, kp = C.c_int32(), C.c_int32(), C.c_int32()
+            wo, bo = C.c_int64(), C.c_int64()
+            if load().nm_denoise_layer(self.h, i, C.byref(ci), C.byref(co), C.byref(kp), C.byref(wo), C.byref(bo)) != NM_OK:
+                break
+            out.append(dict(cin=ci.value, cout=co.value, kpad=kp.value, w_off=wo.value, b_off=bo.value))
+            i += 1
+        return out
+
+    def params(self, get=None, set=None, grads=None):
+        _check(load().nm_denoise_params(self.h, ptr(get), ptr(set), ptr(grads)))
+
+    def train_step(self, x, target, weight=None, lr=None) -> float:
+        loss = C.c_float()
+        _check(load().nm_denoise_train_step(self.h, ptr(x), ptr(target), ptr(weight),
+                                            float(self.opts.lr if lr is None else lr), C.byref(loss)))
+        return loss.value
+
+    def forward(self, x, y):
+        _check(load().nm_denoise_forward(self.h, ptr(x), ptr(y)))
+
+    def apply(self, dose, density, activity, out):
+        nz, ny, nx = dose.shape
+        _check(load().nm_denoise_apply(self.h, ptr(dose), ptr(density), ptr(activity), nx, ny, nz, ptr(out)))
+
+    def close(self):
+        if self.h:
+            load().nm_denoise_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def nm_denoise_make_patches(dose, density, activity, dose_high, dose_scale, act_scale, corners, patch, x,
+                            target=None, weight=None, stream=None):
+    nz, ny, nx = dose.shape
+    _check(load().nm_denoise_make_patches(ptr(dose), ptr(density), ptr(activity), ptr(dose_high), nx, ny, nz,
+                                          float(dose_scale), float(act_scale), ptr(corners), int(corners.shape[0]),
+                                          int(patch), ptr(x), ptr(target), ptr(weight), _stream_ptr(stream)))
+
+
+def nm_denoise_scales(dose, activity, density, stream=None):
+    ds, as_ = C.c_float(), C.c_float()
+    _check(load().nm_denoise_scales(ptr(dose), ptr(activity), ptr(density), int(dose.numel()), C.byref(ds),
+                                    C.byref(as_), _stream_ptr(stream)))
+    return ds.value, as_.value
 
 
 class Dose:
