@@ -177,6 +177,11 @@ nm_status nm_dose_get(nm_dose* h, float* dose, float* sigma, double* organ_dose)
 nm_status nm_dose_get_organs(nm_dose* h, double* mean, double* eps_rms, double* sigma_mean,
                              int64_t* voxels);
 
+/* Eq. 2 over any dose map of the handle's grid (e.g. a denoised one): the
+ * unweighted mean of dose[V] (host or device FP32) over each label's voxels,
+ * into mean[n_labels + 1] (host or device).  NM_ERR_STATE without labels. */
+nm_status nm_dose_map_organs(nm_dose* h, const float* dose, double* mean);
+
 /* Exact cumulative tally, int64 energy units per voxel, into tally[V]. */
 nm_status nm_dose_get_tally(nm_dose* h, int64_t* tally);
 

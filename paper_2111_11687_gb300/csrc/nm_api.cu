@@ -882,6 +882,24 @@ nm_status nm_dose_get_organs(nm_dose* h, double* mean, double* eps_rms, double* 
   return NM_OK;
 }
 
+nm_status nm_dose_map_organs(nm_dose* h, const float* dose, double* mean) {
+  if (!h || !dose || !mean) return fail(NM_ERR_ARG, "bad arguments");
+  if (!h->labels) return fail(NM_ERR_STATE, "the handle has no label map");
+  cudaStream_t s = h->stream;
+  const float* d = dose;
+  if (!is_device_ptr(dose)) {
+    if (!h->out_dose) NM_CUDA(dalloc(&h->out_dose, h->V), "output buffer");
+    NM_CUDA(cudaMemcpyAsync(h->out_dose, dose, h->V * sizeof(float), cudaMemcpyHostToDevice, s), "map copy");
+    d = h->out_dose;
+  }
+  NM_CUDA(launch_map_organ_means(d, h->labels, h->V, h->organ_partial, h->organ_count, h->organ_out, s),
+          "organ means");
+  NM_CUDA(cudaMemcpyAsync(mean, h->organ_out, (h->opt.n_labels + 1) * sizeof(double), cudaMemcpyDefault, s),
+          "organ copy");
+  NM_CUDA(cudaStreamSynchronize(s), "nm_dose_map_organs");
+  return NM_OK;
+}
+
 nm_status nm_dose_get_tally(nm_dose* h, int64_t* tally) {
   if (!h || !tally) return fail(NM_ERR_ARG, "bad arguments");
   NM_CUDA(cudaMemcpyAsync(tally, h->tsum, h->V * sizeof(int64_t), cudaMemcpyDefault, h->stream), "tally copy");

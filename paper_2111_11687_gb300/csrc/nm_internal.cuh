@@ -178,6 +178,8 @@ struct FinalizeParams {
 };
 cudaError_t launch_finalize(const FinalizeParams& p, cudaStream_t s);
 cudaError_t launch_label_count(const uint8_t* labels, int64_t V, long long* count, cudaStream_t s);
+cudaError_t launch_map_organ_means(const float* dose, const uint8_t* labels, int64_t V, double* part,
+                                   const long long* count, double* out, cudaStream_t s);
 
 // ---- 3x3x3 convolution on the tensor cores (nm_conv.cu) -------------------
 int conv_kpad(int cin);

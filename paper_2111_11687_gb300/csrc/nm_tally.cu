@@ -143,7 +143,42 @@ __global__ void finalize_organs_kernel(const FinalizeParams p, int n_blocks) {
   p.organ_out[3 * kLabelSlots + l] = cnt;
 }
 
+// Eq. 2 over an arbitrary dose map: per-CTA per-label partial sums (fixed tree).
+__global__ void __launch_bounds__(kFoldThreads) map_organ_kernel(const float* __restrict__ dose,
+                                                                 const uint8_t* __restrict__ labels, int64_t V,
+                                                                 double* __restrict__ part) {
+  __shared__ double acc[kLabelSlots][kFoldThreads];
+  for (int l = 0; l < kLabelSlots; ++l) acc[l][threadIdx.x] = 0.0;
+  const int64_t v0 = (int64_t)blockIdx.x * kFoldTile;
+  const int64_t v1 = v0 + kFoldTile < V ? v0 + kFoldTile : V;
+  for (int64_t v = v0 + threadIdx.x; v < v1; v += kFoldThreads) {
+    const int l = labels[v];
+    if (l < kLabelSlots) acc[l][threadIdx.x] += (double)dose[v];
+  }
+  __syncthreads();
+  reduce_label_columns(acc, part + (size_t)blockIdx.x * kLabelSlots);
+}
+
+__global__ void map_organ_final_kernel(const double* __restrict__ part, int n_blocks,
+                                       const long long* __restrict__ count, double* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int l = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (l >= kLabelSlots) return;
+  double s = 0.0;
+  for (int b = lane; b < n_blocks; b += 32) s += part[(size_t)b * kLabelSlots + l];
+  s = warp_sum_d(s);
+  if (lane == 0) out[l] = count[l] > 0 ? s / (double)count[l] : 0.0;
+}
+
 }  // namespace
+
+cudaError_t launch_map_organ_means(const float* dose, const uint8_t* labels, int64_t V, double* part,
+                                   const long long* count, double* out, cudaStream_t s) {
+  const int nb = fold_blocks(V);
+  map_organ_kernel<<<nb, kFoldThreads, 0, s>>>(dose, labels, V, part);
+  map_organ_final_kernel<<<(kLabelSlots + 3) / 4, 128, 0, s>>>(part, nb, count, out);
+  return cudaGetLastError();
+}
 
 int fold_blocks(int64_t V) { return (int)((V + kFoldTile - 1) / kFoldTile); }
 

@@ -1,0 +1,222 @@
+"""Denoiser experiment: train the U-Net on pairs the engine generates on
+synthetic phantoms, then compare, on held-out phantoms, the wall time plain
+Monte Carlo needs to bring every organ dose within 2 % of a high-count
+reference with the time of low-count Monte Carlo plus the denoiser.
+
+Everything numerical runs through the C ABI (nm_dose_* for the transport,
+nm_denoise_* for the network); this module only orchestrates: phantom
+generation on the host (a spawn process pool, started before any GPU work),
+device buffers, patch sampling, the training loop and the timing.
+
+    python -m paper_2111_11687_gb300.experiment --train 200 --test 20
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def _gen(args):
+    from paper_2111_11687_gb300 import inputs
+    shape, spacing, seed = args
+    ph = inputs.adult_phantom(shape=shape, spacing=spacing, seed=seed)
+    return ph.hu, ph.activity, ph.labels, ph.spacing
+
+
+def make_phantoms(seeds, shape, spacing, workers=None):
+    """Adult phantoms for the given seeds, generated in a spawn pool."""
+    jobs = [(shape, spacing, s) for s in seeds]
+    if workers == 1 or len(jobs) == 1:
+        return [_gen(j) for j in jobs]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers or min(len(jobs), os.cpu_count() or 1)) as pool:
+        return list(pool.imap(_gen, jobs, chunksize=1))
+
+
+class Case:
+    """One phantom on the device: density, material, activity, labels."""
+
+    def __init__(self, nm, torch, ph, materials, n_labels, activity_bq):
+        hu, act, lab, spacing = ph
+        self.shape = hu.shape
+        self.spacing = spacing
+        self.density = torch.empty(self.shape, dtype=torch.float32, device="cuda")
+        self.material = torch.empty(self.shape, dtype=torch.uint8, device="cuda")
+        nm.nm_ct_to_phantom(torch.from_numpy(hu).cuda(), self.density, self.material)
+        self.activity = torch.from_numpy(act).cuda()
+        self.labels = torch.from_numpy(lab).cuda()
+        self.nm, self.torch = nm, torch
+        self.materials = materials
+        self.n_labels = n_labels
+        self.activity_bq = activity_bq
+
+    def handle(self, **kw):
+        return self.nm.Dose(self.density, self.material, self.spacing, self.materials, activity=self.activity,
+                            labels=self.labels, n_labels=self.n_labels, activity_bq=self.activity_bq, **kw)
+
+    def dose(self, n_decays, seed):
+        """Dose-rate map (device FP32) after n_decays decays; returns (map, seconds)."""
+        out = self.torch.empty(self.shape, dtype=self.torch.float32, device="cuda")
+        with self.handle() as d:
+            self.torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            d.run(n_decays, seed)
+            self.nm.nm_dose_get(d.h, out, None, None)
+            self.torch.cuda.synchronize()
+            return out, time.perf_counter() - t0
+
+
+def body_box(density, margin):
+    """Voxel bounding box (z0, z1, y0, y1, x0, x1) of density >= 0.1."""
+    idx = (density >= 0.1).nonzero()
+    lo = idx.min(0).values.tolist()
+    hi = idx.max(0).values.tolist()
+    return lo, hi
+
+
+def train(nm, torch, net, cases, lows, highs, steps, patch, batch, lr, seed, log_every=0):
+    rng = np.random.default_rng(seed)
+    x = torch.empty((batch, patch, patch, patch, 8), dtype=torch.bfloat16, device="cuda")
+    tgt = torch.empty((batch, patch, patch, patch), dtype=torch.float32, device="cuda")
+    wgt = torch.empty_like(tgt)
+    scales = [nm.nm_denoise_scales(lo, c.activity, c.density) for c, lo in zip(cases, lows)]
+    boxes = [body_box(c.density, patch // 2) for c in cases]
+    losses = []
+    for step in range(steps):
+        # one phantom per step, `batch` patch centres drawn inside its body box
+        i = int(rng.integers(len(cases)))
+        (z0, y0, x0), (z1, y1, x1) = boxes[i]
+        corners = np.stack([rng.integers(x0, x1 + 1, batch), rng.integers(y0, y1 + 1, batch),
+                            rng.integers(z0, z1 + 1, batch)], 1) - patch // 2
+        cd = torch.from_numpy(corners.astype(np.int32)).cuda()
+        ds, as_ = scales[i]
+        nm.nm_denoise_make_patches(lows[i], cases[i].density, cases[i].activity, highs[i], ds, as_, cd, patch, x,
+                                   tgt, wgt)
+        lr_t = lr * 0.5 * (1 + np.cos(np.pi * step / steps))
+        losses.append(net.train_step(x, tgt, wgt, lr=lr_t))
+        if log_every and step % log_every == 0:
+            print(f"step {step} loss {losses[-1]:.5f}", flush=True)
+    return losses
+
+
+def organ_error(means, ref, counts, min_voxels=1):
+    sel = (counts[1:] >= min_voxels) & (ref[1:] > 0)
+    return np.abs(means[1:][sel] / ref[1:][sel] - 1.0)
+
+
+def time_to_target(case, ref, step_decays, max_decays, target, seed):
+    """Plain MC: wall time and decays until every organ is within target of ref."""
+    torch = case.torch
+    with case.handle(batches=2) as d:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n = 0
+        while n < max_decays:
+            d.run(step_decays, seed)
+            n += step_decays
+            mean, _, _, cnt = d.organs()
+            err = organ_error(mean, ref, cnt)
+            if err.max() <= target:
+                torch.cuda.synchronize()
+                return time.perf_counter() - t0, n, float(err.max())
+        torch.cuda.synchronize()
+        return None, n, float(err.max())
+
+
+def run(train_n=200, test_n=20, shape=(300, 256, 256), spacing=(0.2, 0.2, 0.3), low=int(1e7), high=int(1e9),
+        ref=int(1e10), denoise_low=int(1e7), steps=3000, patch=64, batch=4, lr=1e-3, workers=None,
+        step_decays=int(5e6), max_decays=int(2e9), seed0=1000, log_every=0):
+    phantoms = make_phantoms(list(range(seed0, seed0 + train_n + test_n)), shape, spacing, workers)
+    import torch
+
+    from paper_2111_11687_gb300 import build, inputs, nmdose as nm
+    build.build()
+    mats = nm.Materials(inputs.MATERIAL_Z_OVER_A, inputs.MATERIAL_ZEFF, inputs.PE_COEFF, inputs.PE_EXP)
+    cases = [Case(nm, torch, ph, mats, inputs.N_LABELS, inputs.ACTIVITY_BQ) for ph in phantoms]
+    del phantoms
+    tr, te = cases[:train_n], cases[train_n:]
+    t0 = time.perf_counter()
+    lows = [c.dose(low, 7)[0] for c in tr]
+    highs = [c.dose(high, 8)[0] for c in tr]
+    t_data = time.perf_counter() - t0
+    net = nm.Denoiser(patch=patch, batch=batch, levels=4, base_width=16, seed=1, lr=lr)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = train(nm, torch, net, tr, lows, highs, steps, patch, batch, lr, seed=5, log_every=log_every)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del lows, highs
+    results = []
+    for j, c in enumerate(te):
+        refmap, _ = c.dose(ref, 100 + j)
+        with c.handle() as h:
+            ref_org = h.map_organs(refmap)
+        # plain MC
+        t_mc, n_mc, e_mc = time_to_target(c, ref_org, step_decays, max_decays, 0.02, 200 + j)
+        # MC at the low count + denoiser
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lowmap, _ = c.dose(denoise_low, 300 + j)
+        den = torch.empty_like(lowmap)
+        net.apply(lowmap, c.density, c.activity, den)
+        torch.cuda.synchronize()
+        t_dn = time.perf_counter() - t0
+        with c.handle() as h:
+            m_dn = h.map_organs(den)
+            m_lo = h.map_organs(lowmap)
+        cnts = np.bincount(c.labels.flatten().cpu().numpy(), minlength=inputs.N_LABELS + 1)
+        e_dn = organ_error(m_dn, ref_org, cnts)
+        e_lo = organ_error(m_lo, ref_org, cnts)
+        results.append(dict(case=j, plain_mc_s=t_mc, plain_mc_decays=n_mc, plain_mc_err=e_mc,
+                            mc_denoiser_s=t_dn, denoiser_max_err=float(e_dn.max()),
+                            denoiser_mean_err=float(e_dn.mean()), low_mc_max_err=float(e_lo.max()),
+                            low_mc_mean_err=float(e_lo.mean())))
+    net.close()
+    ok_dn = [r for r in results if r["denoiser_max_err"] <= 0.02]
+    summary = dict(train=train_n, test=test_n, grid=list(shape[::-1]), low=low, high=high, ref=ref,
+                   denoise_low=denoise_low, steps=steps, patch=patch, batch=batch, data_s=t_data,
+                   train_s=t_train, final_loss=float(np.mean(losses[-50:])), first_loss=float(np.mean(losses[:10])),
+                   plain_mc_s_median=float(np.median([r["plain_mc_s"] for r in results if r["plain_mc_s"]] or [np.nan])),
+                   mc_denoiser_s_median=float(np.median([r["mc_denoiser_s"] for r in results])),
+                   denoiser_reaches_2pct=len(ok_dn), denoiser_max_err_median=float(np.median([r["denoiser_max_err"] for r in results])),
+                   low_mc_max_err_median=float(np.median([r["low_mc_max_err"] for r in results])),
+                   cases=results)
+    return summary
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train", type=int, default=200)
+    ap.add_argument("--test", type=int, default=20)
+    ap.add_argument("--grid", default="256,256,300")
+    ap.add_argument("--voxel-mm", default="2,2,3")
+    ap.add_argument("--low", type=float, default=1e7)
+    ap.add_argument("--high", type=float, default=1e9)
+    ap.add_argument("--ref", type=float, default=1e10)
+    ap.add_argument("--denoise-low", type=float, default=1e7)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--patch", type=int, default=64)
+    ap.add_argument("--batch", type=int, default=4)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--workers", type=int, default=0)
+    ap.add_argument("--log-every", type=int, default=0)
+    a = ap.parse_args()
+    nx, ny, nz = (int(v) for v in a.grid.split(","))
+    sp = tuple(float(v) / 10 for v in a.voxel_mm.split(","))
+    out = run(a.train, a.test, (nz, ny, nx), sp, int(a.low), int(a.high), int(a.ref), int(a.denoise_low), a.steps,
+              a.patch, a.batch, a.lr, a.workers or None, log_every=a.log_every)
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

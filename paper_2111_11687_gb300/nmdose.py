@@ -88,6 +88,7 @@ _SIGS = {
     "nm_dose_get": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "nm_dose_get_organs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "nm_dose_get_tally": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "nm_dose_map_organs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "nm_dose_counters": (C.c_int, [C.c_void_p, C.POINTER(nm_counters)]),
     "nm_dose_reset": (C.c_int, [C.c_void_p]),
     "nm_dose_destroy": (None, [C.c_void_p]),
@@ -422,6 +423,11 @@ class Dose:
 
     def organs(self):
         return nm_dose_get_organs(self.h, self.n_labels)
+
+    def map_organs(self, dose):
+        out = np.zeros(self.n_labels + 1)
+        _check(load().nm_dose_map_organs(self.h, ptr(dose), ptr(out)))
+        return out
 
     def tally(self):
         t = np.empty(self.shape, np.int64)
