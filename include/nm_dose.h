@@ -266,10 +266,11 @@ nm_status nm_conv3d_wgrad(const nm_conv3d_desc* desc, const uint16_t* x0, const 
  * (default 4 levels, 16..128), two 3x3x3 convolutions with ReLU per level,
  * 2x2x2 average pooling down, nearest upsampling concatenated with the skip
  * up, and a 1x1x1 head added to input channel 0.  Inputs are BF16 [batch][P]
- * [P][P][8]: channel 0 = log1p(low-count dose / s), 1 = density, 2 =
- * log1p(activity / a), 3..7 = 0, where s and a are the body means (density >=
- * 0.1) of the low-count dose and of the activity; the output and training
- * target are log1p(dose / s).  Weights: FP32 master copy updated by Adam,
+ * [P][P][8]: channel 0 = low-count dose / s, 1 = density, 2 = activity / a,
+ * 3 = activity / (a max(density, 0.1)), 4..7 = 0, where s and a are the body
+ * means (density >= 0.1) of the low-count dose and of the activity; the output
+ * and training target are dose / s (linear, so that the squared-error optimum
+ * is the conditional mean and organ means are not biased).  Weights: FP32 master copy updated by Adam,
  * BF16 copy for the convolutions; all convolutions on the tensor cores. */
 typedef struct {
   int32_t patch;       /* P, a multiple of 2^(levels-1) (default 64) */

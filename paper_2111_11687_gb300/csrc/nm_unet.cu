@@ -9,8 +9,9 @@
 // (read directly by the convolution, never materialised), two convolutions
 // with ReLU; a 1x1x1 head whose output is added to input channel 0.
 //
-// Input channels (8, of which 3 used): 0 = log1p(low-count dose / s), 1 =
-// density, 2 = log1p(activity / a); the target is log1p(high-count dose / s).
+// Input channels (8, of which 4 used): 0 = low-count dose / s, 1 = density,
+// 2 = activity / a, 3 = activity / (a max(density, 0.1)); the target is the
+// high-count dose / s (s, a: body means of the low-count dose and activity).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -184,8 +185,10 @@ __global__ void to_bf16_kernel(const float* __restrict__ a, long long n, bf16* _
 }
 
 // Network input channels from whole volumes, for patches at the given corners:
-// out [np][P][P][P][8] BF16 = (log1p(dose/s), density, log1p(act/a), 0...);
-// target [np][P]^3 = log1p(dose_high/s) (if dose_high), weight = (density >= 0.1).
+// out [np][P][P][P][8] BF16 = (dose/s, density, act/a, act/(a max(density, 0.1)), 0...);
+// target [np][P]^3 = dose_high/s (if dose_high), weight = (density >= 0.1).
+// Linear units keep the squared-error optimum at the conditional mean, so the
+// network does not bias organ means.
 __global__ void make_patches_kernel(const float* __restrict__ dose, const float* __restrict__ density,
                                     const float* __restrict__ act, const float* __restrict__ dose_high,
                                     int nx, int ny, int nz, float inv_s, float inv_a,
@@ -201,27 +204,30 @@ __global__ void make_patches_kernel(const float* __restrict__ dose, const float*
     const int y = (int)(r % P);
     const int z = (int)(r / P);
     const int gx = corners[3 * p] + x, gy = corners[3 * p + 1] + y, gz = corners[3 * p + 2] + z;
-    float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f, t = 0.0f, wv = 0.0f;
+    float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f, c3 = 0.0f, t = 0.0f, wv = 0.0f;
     if (gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz) {
       const long long v = ((long long)gz * ny + gy) * nx + gx;
-      c0 = log1pf(fmaxf(dose[v], 0.0f) * inv_s);
-      c1 = density[v];
-      c2 = log1pf(fmaxf(act[v], 0.0f) * inv_a);
-      if (dose_high) t = log1pf(fmaxf(dose_high[v], 0.0f) * inv_s);
-      wv = density[v] >= 0.1f ? 1.0f : 0.0f;
+      const float rho = density[v];
+      c0 = fmaxf(dose[v], 0.0f) * inv_s;
+      c1 = rho;
+      c2 = fmaxf(act[v], 0.0f) * inv_a;
+      c3 = c2 / fmaxf(rho, 0.1f);  // local (positron) deposit per unit mass
+      if (dose_high) t = fmaxf(dose_high[v], 0.0f) * inv_s;
+      wv = rho >= 0.1f ? 1.0f : 0.0f;
     }
     bf16* o = out + i * 8;
     o[0] = __float2bfloat16_rn(c0);
     o[1] = __float2bfloat16_rn(c1);
     o[2] = __float2bfloat16_rn(c2);
-    for (int k = 3; k < 8; ++k) o[k] = __float2bfloat16_rn(0.0f);
+    o[3] = __float2bfloat16_rn(c3);
+    for (int k = 4; k < 8; ++k) o[k] = __float2bfloat16_rn(0.0f);
     if (target) target[i] = t;
     if (weight) weight[i] = wv;
   }
 }
 
 // Writes the central region of predicted patches back into the volume:
-// dose_out = s * expm1(y) for voxels of the patch's core box.
+// dose_out = s * y for voxels of the patch's core box.
 __global__ void scatter_patches_kernel(const float* __restrict__ y, const int* __restrict__ corners,
                                        const int* __restrict__ lo, const int* __restrict__ hi, int np, int P,
                                        int nx, int ny, int nz, float s, float* __restrict__ dose_out) {
@@ -238,7 +244,7 @@ __global__ void scatter_patches_kernel(const float* __restrict__ y, const int* _
       continue;
     const int gx = corners[3 * p] + x, gy = corners[3 * p + 1] + yy, gz = corners[3 * p + 2] + z;
     if (gx < 0 || gx >= nx || gy < 0 || gy >= ny || gz < 0 || gz >= nz) continue;
-    dose_out[((long long)gz * ny + gy) * nx + gx] = s * expm1f(y[i]);
+    dose_out[((long long)gz * ny + gy) * nx + gx] = s * y[i];
   }
 }
 

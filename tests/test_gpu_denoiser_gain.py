@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 def test_denoiser_reduces_low_count_organ_error():
     from paper_2111_11687_gb300 import experiment
     out = experiment.run(train_n=10, test_n=3, shape=(75, 64, 64), spacing=(0.8, 0.8, 1.2), low=int(2e5),
-                         high=int(2e7), ref=int(2e8), denoise_low=int(2e5), steps=500, patch=32, batch=4, lr=2e-3,
+                         high=int(2e7), ref=int(2e8), denoise_low=int(2e5), steps=1200, patch=32, batch=4, lr=2e-3,
                          workers=1, step_decays=int(2e5), max_decays=int(2e8))
     assert out["final_loss"] < out["first_loss"]
     dn = np.array([c["denoiser_mean_err"] for c in out["cases"]])
