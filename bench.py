@@ -241,6 +241,8 @@ def run_gpu(args):
         e2e = {"value": e2e_val, "unit": METRIC, "h2d_bytes_per_step": int(V * (2 + 4 + 1)),
                "d2h_bytes_per_step": int(V * 8 + 8 * (inputs.N_LABELS + 1)), "steps": args.e2e_steps}
 
+    den = denoiser_perf(torch, nmdose, args.denoiser_steps, peaks) if args.denoiser_steps > 0 else None
+
     cpu = None
     if rank == 0 and ws == 1 and args.cpu_decays > 0:
         cpu = cpu_baseline(args.cpu_decays)
@@ -255,11 +257,63 @@ def run_gpu(args):
                            "l2": "working set (tallies 2x157 MB + grid 79 MB + alias 41 MB) exceeds the 129 MB L2",
                            "parallelism": f"histories sharded over {ws} GPU(s)"},
                 "gpu_launches": launches, "roofline": roofline, "clocks": clocks, "e2e": e2e,
-                "cpu_baseline": cpu}
+                "cpu_baseline": cpu, "denoiser": den}
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def unet_flops(layers, patch, batch, levels=4):
+    """Dense FLOPs of the U-Net's 3x3x3 convolutions for one batch (2 per MAC,
+    the 27*cin real K, not the padded one)."""
+    f = 0
+    names = []
+    for i in range(levels):
+        names += [i, i]
+    for i in range(levels - 2, -1, -1):
+        names += [i, i]
+    for l, lev in zip(layers[:-1], names):
+        vox = batch * (patch >> lev) ** 3
+        f += 2 * vox * l["cout"] * 27 * l["cin"]
+    return f
+
+
+def denoiser_perf(torch, nm, steps, peaks):
+    """Forward and training-step throughput of the U-Net (64^3 patches, batch 4)
+    on the tensor cores, timed with CUDA events on the launching stream."""
+    P, B = 64, 4
+    stream = torch.cuda.current_stream()
+    net = nm.Denoiser(patch=P, batch=B, levels=4, base_width=16, seed=1, stream=stream)
+    rng = np.random.default_rng(0)
+    x = torch.from_numpy(rng.normal(0, 1, (B, P, P, P, 8)).astype(np.float32)).to(torch.bfloat16).cuda()
+    t = torch.from_numpy(rng.normal(0, 1, (B, P, P, P)).astype(np.float32)).cuda()
+    y = torch.empty((B, P, P, P), dtype=torch.float32, device="cuda")
+    fl = unet_flops(net.layers(), P, B)
+    for _ in range(3):
+        net.forward(x, y)
+        net.train_step(x, t, lr=1e-4)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize()
+    e[0].record(stream)
+    for _ in range(steps):
+        net.forward(x, y)
+    e[1].record(stream)
+    for _ in range(steps):
+        net.train_step(x, t, lr=1e-4)
+    e[2].record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = e[0].elapsed_time(e[1]) / steps
+    trn_ms = e[1].elapsed_time(e[2]) / steps
+    net.close()
+    peak = peaks["bf16_tflops"] if peaks else 1900.0
+    fwd_tf = fl / (fwd_ms * 1e-3) / 1e12
+    trn_tf = 3 * fl / (trn_ms * 1e-3) / 1e12      # forward + input and weight gradients
+    return {"patch": P, "batch": B, "widths": [16, 32, 64, 128], "forward_ms": fwd_ms, "train_step_ms": trn_ms,
+            "forward_gflop": fl / 1e9, "patches_per_s_forward": B / (fwd_ms * 1e-3),
+            "roofline": {"bound": "tensor", "achieved": fwd_tf, "peak": peak, "unit": "TFLOP/s",
+                         "frac": fwd_tf / peak, "train_achieved": trn_tf, "train_frac": trn_tf / peak,
+                         "peak_source": "measured" if peaks else "fallback"}}
 
 
 def _kernel_hash():
@@ -340,6 +394,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-decays", type=int, default=4_000_000)
     ap.add_argument("--ref-decays", type=int, default=2_000_000)
+    ap.add_argument("--denoiser-steps", type=int, default=10)
     ap.add_argument("--profile", action="store_true", help="one short run for ncu")
     ap.add_argument("--decays", type=int, default=200_000_000)
     ap.add_argument("--tuning", default="{}", help="JSON dict of nm_options launch fields (profile mode)")

@@ -33,38 +33,94 @@ struct ConvGeom {
   long long m;                  // voxels = n*d*h*w
 };
 
-// 8 consecutive channels (16 bytes) of the im2col row of voxel (b, z, y, x)
-// at GEMM column k, or zeros outside the volume / past 27 taps.
-__device__ __forceinline__ uint4 gather8(const ConvGeom& g, const __nv_bfloat16* __restrict__ x0,
-                                         const __nv_bfloat16* __restrict__ x1, int b, int z, int y,
-                                         int x, int k) {
-  const int tap = k / g.cin;
-  if (tap >= 27) return make_uint4(0, 0, 0, 0);
-  const int ci = k - tap * g.cin;
-  const int zz = z + tap / 9 - 1, yy = y + (tap / 3) % 3 - 1, xx = x + tap % 3 - 1;
-  if ((unsigned)zz >= (unsigned)g.d || (unsigned)yy >= (unsigned)g.h || (unsigned)xx >= (unsigned)g.w)
-    return make_uint4(0, 0, 0, 0);
-  if (ci < g.c0) {
-    long long off;
-    if (g.coarse) {
-      const int dd = g.d >> 1, hh = g.h >> 1, ww = g.w >> 1;
-      off = ((((long long)b * dd + (zz >> 1)) * hh + (yy >> 1)) * ww + (xx >> 1)) * g.c0 + ci;
-    } else {
-      off = ((((long long)b * g.d + zz) * g.h + yy) * g.w + xx) * g.c0 + ci;
-    }
-    return __ldg(reinterpret_cast<const uint4*>(x0 + off));
+// Per-voxel part of the im2col gather, computed once per GEMM row: element
+// offsets of the voxel in both sources, which of its 27 neighbours lie inside
+// the volume, and (half-resolution source) its parities.
+struct Row {
+  long long off0, off1;
+  uint32_t vmask;     // bit t: the neighbour at tap t is inside the volume
+  int pz, py, px;     // parities of z, y, x (nearest-upsampled source)
+};
+
+__device__ __forceinline__ Row make_row(const ConvGeom& g, long long m) {
+  Row r;
+  const int x = (int)(m % g.w);
+  long long t = m / g.w;
+  const int y = (int)(t % g.h);
+  t /= g.h;
+  const int z = (int)(t % g.d);
+  const int b = (int)(t / g.d);
+  if (g.coarse) {
+    const int dd = g.d >> 1, hh = g.h >> 1, ww = g.w >> 1;
+    r.off0 = ((((long long)b * dd + (z >> 1)) * hh + (y >> 1)) * ww + (x >> 1)) * g.c0;
+  } else {
+    r.off0 = m * g.c0;
   }
-  const long long off = ((((long long)b * g.d + zz) * g.h + yy) * g.w + xx) * g.c1 + (ci - g.c0);
-  return __ldg(reinterpret_cast<const uint4*>(x1 + off));
+  r.off1 = m * g.c1;
+  r.pz = z & 1; r.py = y & 1; r.px = x & 1;
+  // neighbours inside the volume: axis masks over d in {-1, 0, +1}
+  const uint32_t mz = (z > 0 ? 1u : 0u) | 2u | (z < g.d - 1 ? 4u : 0u);
+  const uint32_t my = (y > 0 ? 1u : 0u) | 2u | (y < g.h - 1 ? 4u : 0u);
+  const uint32_t mx = (x > 0 ? 1u : 0u) | 2u | (x < g.w - 1 ? 4u : 0u);
+  uint32_t vm = 0;
+#pragma unroll
+  for (int t2 = 0; t2 < 27; ++t2)
+    if (((mz >> (t2 / 9)) & 1u) && ((my >> ((t2 / 3) % 3)) & 1u) && ((mx >> (t2 % 3)) & 1u)) vm |= 1u << t2;
+  r.vmask = vm;
+  return r;
 }
 
-__device__ __forceinline__ void voxel_coords(const ConvGeom& g, long long m, int& b, int& z, int& y, int& x) {
-  x = (int)(m % g.w);
-  long long t = m / g.w;
-  y = (int)(t % g.h);
-  t /= g.h;
-  z = (int)(t % g.d);
-  b = (int)(t / g.d);
+// Column table entry for each 8-wide chunk of K: tap (bits 0-4, 31 = past the
+// taps), the tap's axis indices dz+1, dy+1, dx+1 (2 bits each from bit 5) and
+// the channel (bits 16-31).
+__device__ __forceinline__ uint32_t kchunk_entry(const ConvGeom& g, int k) {
+  const int tap = k / g.cin;
+  if (tap >= 27) return 31u;
+  const int ci = k - tap * g.cin;
+  return (uint32_t)tap | ((uint32_t)(tap / 9) << 5) | ((uint32_t)((tap / 3) % 3) << 7) |
+         ((uint32_t)(tap % 3) << 9) | ((uint32_t)ci << 16);
+}
+
+// Element offset of tap t relative to the voxel, per source (full resolution).
+__device__ __forceinline__ int tap_delta(const ConvGeom& g, int t, int c) {
+  const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+  return ((dz * g.h + dy) * g.w + dx) * c;
+}
+
+// 8 consecutive channels (16 bytes) of the im2col row r at the chunk with
+// table entry e, or zeros outside the volume / past 27 taps.
+__device__ __forceinline__ uint4 gather8(const ConvGeom& g, const __nv_bfloat16* __restrict__ x0,
+                                         const __nv_bfloat16* __restrict__ x1, const Row& r, uint32_t e,
+                                         const int* __restrict__ s_d0, const int* __restrict__ s_d1) {
+  const int tap = e & 31u;
+  if (tap >= 27 || !((r.vmask >> tap) & 1u)) return make_uint4(0, 0, 0, 0);
+  const int ci = (int)(e >> 16);
+  if (ci < g.c0) {
+    if (!g.coarse) return __ldg(reinterpret_cast<const uint4*>(x0 + r.off0 + s_d0[tap] + ci));
+    // nearest upsampling: a step of -1 moves to the previous coarse voxel only
+    // from an even coordinate, a step of +1 to the next one only from an odd one
+    const int az = (int)((e >> 5) & 3u), ay = (int)((e >> 7) & 3u), ax = (int)((e >> 9) & 3u);
+    const int cz = az == 0 ? -(r.pz ^ 1) : (az == 2 ? r.pz : 0);
+    const int cy = ay == 0 ? -(r.py ^ 1) : (ay == 2 ? r.py : 0);
+    const int cx = ax == 0 ? -(r.px ^ 1) : (ax == 2 ? r.px : 0);
+    const long long off = r.off0 + ((long long)(cz * (g.h >> 1) + cy) * (g.w >> 1) + cx) * g.c0 + ci;
+    return __ldg(reinterpret_cast<const uint4*>(x0 + off));
+  }
+  return __ldg(reinterpret_cast<const uint4*>(x1 + r.off1 + s_d1[tap] + (ci - g.c0)));
+}
+
+// Tables shared by a CTA: chunk entries for all of K, tap deltas per source.
+struct GatherTables {
+  uint32_t* ktab;  // [kpad / 8]
+  int d0[27], d1[27];
+};
+
+__device__ __forceinline__ void fill_tables(const ConvGeom& g, uint32_t* ktab, int* d0, int* d1) {
+  for (int i = threadIdx.x; i < g.kpad / 8; i += blockDim.x) ktab[i] = kchunk_entry(g, i * 8);
+  for (int t = threadIdx.x; t < 27; t += blockDim.x) {
+    d0[t] = tap_delta(g, t, g.c0);
+    d1[t] = tap_delta(g, t, g.c1);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -84,10 +140,13 @@ __global__ void __launch_bounds__(kThreads) conv_fwd_kernel(ConvGeom g, const __
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sa = smem;                                // [2][kABytes]
   uint8_t* sb = smem + 2 * kABytes;                  // [2][kBBytes]
+  uint32_t* ktab = reinterpret_cast<uint32_t*>(smem + 2 * kABytes + 2 * kBBytes);  // [kpad / 8]
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ uint32_t s_tmem;
+  __shared__ int s_d0[27], s_d1[27];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  fill_tables(g, ktab, s_d0, s_d1);
   if (warp == 0) tc::tmem_alloc(&s_tmem, kNcols);
   if (tid == 0) {
     tc::mbar_init(&bar[0], 1);
@@ -101,8 +160,9 @@ __global__ void __launch_bounds__(kThreads) conv_fwd_kernel(ConvGeom g, const __
 
   const long long m_row = (long long)blockIdx.x * kBM + tid;  // this thread gathers GEMM row tid
   const bool row_ok = m_row < g.m;
-  int b = 0, z = 0, yv = 0, xv = 0;
-  if (row_ok) voxel_coords(g, m_row, b, z, yv, xv);
+  Row row;
+  if (row_ok) row = make_row(g, m_row);
+  else row.vmask = 0u;
   const int nstages = g.kpad / kKS;
   constexpr uint32_t idesc = tc::idesc_bf16_f32(kBM, COUT, false, false);
   bool timeout = false;
@@ -117,7 +177,7 @@ __global__ void __launch_bounds__(kThreads) conv_fwd_kernel(ConvGeom g, const __
     // A: this thread's row, 8 chunks of 8 channels.
 #pragma unroll
     for (int kc = 0; kc < 8; ++kc) {
-      const uint4 v = row_ok ? gather8(g, x0, x1, b, z, yv, xv, s * kKS + kc * 8) : make_uint4(0, 0, 0, 0);
+      const uint4 v = gather8(g, x0, x1, row, ktab[s * (kKS / 8) + kc], s_d0, s_d1);
       *reinterpret_cast<uint4*>(a + (tid >> 3) * kSbo + kc * 128 + (tid & 7) * 16) = v;
     }
     // B: COUT rows x 8 chunks of the weight matrix [Cout][kpad].
@@ -196,10 +256,13 @@ __global__ void __launch_bounds__(kThreads) conv_wgrad_kernel(ConvGeom g, const 
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sa = smem;
   uint8_t* sb = smem + 2 * kABytes;
+  uint32_t* ktab = reinterpret_cast<uint32_t*>(smem + 2 * kABytes + 2 * kBBytes);  // [kpad / 8]
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ uint32_t s_tmem;
+  __shared__ int s_d0[27], s_d1[27];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  fill_tables(g, ktab, s_d0, s_d1);
   if (warp == 0) tc::tmem_alloc(&s_tmem, kNcols);
   if (tid == 0) {
     tc::mbar_init(&bar[0], 1);
@@ -226,19 +289,20 @@ __global__ void __launch_bounds__(kThreads) conv_wgrad_kernel(ConvGeom g, const 
     if (__syncthreads_or(timeout)) { timeout = true; break; }
     uint8_t* a = sa + buf * kABytes;
     uint8_t* bm = sb + buf * kBBytes;
-    // A: 64 voxels x 16 chunks (8 GEMM rows each); thread -> (voxel, chunk).
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int q = tid + kThreads * i;
-      const int pl = q >> 4, rc = q & 15;
+    // A: 64 voxels x 16 chunks (8 GEMM rows each); a thread owns one voxel
+    // (tid % 64) and every other chunk.
+    {
+      const int pl = tid & 63;
       const long long p = p_begin + s * kKS + pl;
-      uint4 v = make_uint4(0, 0, 0, 0);
-      if (p < p_end) {
-        int b, z, yv, xv;
-        voxel_coords(g, p, b, z, yv, xv);
-        v = gather8(g, x0, x1, b, z, yv, xv, k0 + rc * 8);
+      Row row;
+      if (p < p_end) row = make_row(g, p);
+      else row.vmask = 0u;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int rc = 2 * i + (tid >> 6);
+        const uint4 v = gather8(g, x0, x1, row, ktab[(k0 >> 3) + rc], s_d0, s_d1);
+        *reinterpret_cast<uint4*>(a + rc * 128 + (pl >> 3) * kSboA + (pl & 7) * 16) = v;
       }
-      *reinterpret_cast<uint4*>(a + rc * 128 + (pl >> 3) * kSboA + (pl & 7) * 16) = v;
     }
     // B: 64 voxels x COUT/8 chunks of dY.
     for (int q = tid; q < kKS * (COUT / 8); q += kThreads) {
@@ -338,13 +402,17 @@ __global__ void flip_weights_kernel(const __nv_bfloat16* __restrict__ w, int cin
 }
 
 template <int COUT>
-size_t fwd_smem() { return 2 * (size_t)kBM * kKS * 2 + 2 * (size_t)COUT * kKS * 2; }
+size_t fwd_smem_base() { return 2 * (size_t)kBM * kKS * 2 + 2 * (size_t)COUT * kKS * 2; }
+
+// stage buffers plus the K-chunk table
+template <int COUT>
+size_t fwd_smem(int kpad) { return fwd_smem_base<COUT>() + (size_t)(kpad / 8) * 4; }
 
 template <int COUT>
 cudaError_t launch_fwd_t(const ConvGeom& g, const __nv_bfloat16* x0, const __nv_bfloat16* x1,
                          const __nv_bfloat16* w, const float* bias, __nv_bfloat16* y, int relu,
                          uint32_t* status, cudaStream_t s) {
-  const size_t smem = fwd_smem<COUT>();
+  const size_t smem = fwd_smem<COUT>(g.kpad);
   cudaError_t e = cudaFuncSetAttribute(conv_fwd_kernel<COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const long long grid = (g.m + kBM - 1) / kBM;
@@ -355,16 +423,16 @@ cudaError_t launch_fwd_t(const ConvGeom& g, const __nv_bfloat16* x0, const __nv_
 // The weight-gradient buffers are over-allocated to 96 KB: every read the
 // MMAs can make from the stage buffers stays inside the CTA's allocation.
 template <int COUT>
-size_t wgrad_smem() {
-  const size_t need = fwd_smem<COUT>();
-  return need > 96 * 1024 ? need : 96 * 1024;
+size_t wgrad_smem(int kpad) {
+  const size_t need = fwd_smem_base<COUT>() > 96 * 1024 ? fwd_smem_base<COUT>() : 96 * 1024;
+  return need + (size_t)(kpad / 8) * 4;
 }
 
 template <int COUT>
 cudaError_t launch_wgrad_t(const ConvGeom& g, const __nv_bfloat16* x0, const __nv_bfloat16* x1,
                            const __nv_bfloat16* dy, float* part, int splits, uint32_t* status,
                            cudaStream_t s) {
-  const size_t smem = wgrad_smem<COUT>();
+  const size_t smem = wgrad_smem<COUT>(g.kpad);
   cudaError_t e = cudaFuncSetAttribute(conv_wgrad_kernel<COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const long long per = ((g.m + splits - 1) / splits + kKS - 1) / kKS * kKS;
