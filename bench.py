@@ -395,11 +395,18 @@ def main():
     ap.add_argument("--cpu-decays", type=int, default=4_000_000)
     ap.add_argument("--ref-decays", type=int, default=2_000_000)
     ap.add_argument("--denoiser-steps", type=int, default=10)
+    ap.add_argument("--denoiser-only", action="store_true", help="only the U-Net throughput (for ncu)")
     ap.add_argument("--profile", action="store_true", help="one short run for ncu")
     ap.add_argument("--decays", type=int, default=200_000_000)
     ap.add_argument("--tuning", default="{}", help="JSON dict of nm_options launch fields (profile mode)")
     args = ap.parse_args()
-    if args.profile:
+    if args.denoiser_only:
+        import torch
+
+        from paper_2111_11687_gb300 import build, nmdose
+        build.build()
+        print(json.dumps(denoiser_perf(torch, nmdose, args.denoiser_steps, _peaks())))
+    elif args.profile:
         run_profile(args)
     elif args.impl == "reference":
         run_reference(args)
