@@ -117,7 +117,52 @@ def _peaks():
         return None
 
 
+def _batch_phantom(i):
+    from paper_2111_11687_gb300 import inputs
+    ph = inputs.batch_phantoms(1, seed0=1 + i)[0]
+    return ph.hu, ph.activity, ph.labels, ph.spacing
+
+
+def batch_phantoms(n):
+    """The batched-patients workload, generated in a spawn pool before any GPU work."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(min(n, os.cpu_count() or 1)) as pool:
+        return pool.map(_batch_phantom, range(n))
+
+
+def batched_perf(torch, nm, phs, decays, steps, warmup):
+    """nm_dose_run_batch over the uneven patients: every patient gets `decays`
+    decays per step in one CUDA graph of persistent multi-patient launches."""
+    from paper_2111_11687_gb300 import inputs
+    gm = _materials_gpu(nm)
+    hs = []
+    for hu, act, lab, sp in phs:
+        den = torch.empty(hu.shape, dtype=torch.float32, device="cuda")
+        mat = torch.empty(hu.shape, dtype=torch.uint8, device="cuda")
+        nm.nm_ct_to_phantom(torch.from_numpy(hu).cuda(), den, mat)
+        hs.append(nm.Dose(den, mat, sp, gm, activity=torch.from_numpy(act).cuda(), labels=torch.from_numpy(lab).cuda(),
+                          n_labels=inputs.N_LABELS, activity_bq=inputs.ACTIVITY_BQ))
+    for _ in range(warmup):
+        nm.nm_dose_run_batch(hs, [decays] * len(hs), 1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        nm.nm_dose_run_batch(hs, [decays] * len(hs), 1)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    vox = [int(np.prod(p[0].shape)) for p in phs]
+    c = hs[0].counters()
+    out = {"patients": len(hs), "decays_per_patient_per_step": decays, "steps": steps,
+           "value": decays * len(hs) * steps / dt, "unit": METRIC, "ms_per_step": 1e3 * dt / steps,
+           "voxels_min_max": [min(vox), max(vox)],
+           "launch_shape": {k: c[k] for k in ("block_threads", "chunk", "regroup", "regroup_lanes")}}
+    for h in hs:
+        h.close()
+    return out
+
+
 def run_gpu(args):
+    phs = batch_phantoms(args.batch_patients) if args.batch_patients > 0 else None
     import torch
 
     from paper_2111_11687_gb300 import build, inputs, nmdose
@@ -242,6 +287,7 @@ def run_gpu(args):
                "d2h_bytes_per_step": int(V * 8 + 8 * (inputs.N_LABELS + 1)), "steps": args.e2e_steps}
 
     den = denoiser_perf(torch, nmdose, args.denoiser_steps, peaks) if args.denoiser_steps > 0 else None
+    batched = batched_perf(torch, nmdose, phs, args.batch_decays, 3, 1) if phs else None
 
     cpu = None
     if rank == 0 and ws == 1 and args.cpu_decays > 0:
@@ -257,7 +303,7 @@ def run_gpu(args):
                            "l2": "working set (tallies 2x157 MB + grid 79 MB + alias 41 MB) exceeds the 129 MB L2",
                            "parallelism": f"histories sharded over {ws} GPU(s)"},
                 "gpu_launches": launches, "roofline": roofline, "clocks": clocks, "e2e": e2e,
-                "cpu_baseline": cpu, "denoiser": den}
+                "cpu_baseline": cpu, "denoiser": den, "batched": batched}
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
@@ -395,6 +441,8 @@ def main():
     ap.add_argument("--cpu-decays", type=int, default=4_000_000)
     ap.add_argument("--ref-decays", type=int, default=2_000_000)
     ap.add_argument("--denoiser-steps", type=int, default=10)
+    ap.add_argument("--batch-patients", type=int, default=16)
+    ap.add_argument("--batch-decays", type=int, default=100_000_000)
     ap.add_argument("--denoiser-only", action="store_true", help="only the U-Net throughput (for ncu)")
     ap.add_argument("--profile", action="store_true", help="one short run for ncu")
     ap.add_argument("--decays", type=int, default=200_000_000)

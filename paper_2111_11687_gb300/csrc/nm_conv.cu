@@ -62,7 +62,7 @@ __device__ __forceinline__ Row make_row(const ConvGeom& g, long long m) {
   const uint32_t mz = (z > 0 ? 1u : 0u) | 2u | (z < g.d - 1 ? 4u : 0u);
   const uint32_t my = (y > 0 ? 1u : 0u) | 2u | (y < g.h - 1 ? 4u : 0u);
   const uint32_t mx = (x > 0 ? 1u : 0u) | 2u | (x < g.w - 1 ? 4u : 0u);
-  uint32_t vm = 0;
+  uint32_t vm = 1u << 30;  // the row is a voxel of the volume
 #pragma unroll
   for (int t2 = 0; t2 < 27; ++t2)
     if (((mz >> (t2 / 9)) & 1u) && ((my >> ((t2 / 3) % 3)) & 1u) && ((mx >> (t2 % 3)) & 1u)) vm |= 1u << t2;
@@ -73,8 +73,9 @@ __device__ __forceinline__ Row make_row(const ConvGeom& g, long long m) {
 // Column table entry for each 8-wide chunk of K: tap (bits 0-4, 31 = past the
 // taps), the tap's axis indices dz+1, dy+1, dx+1 (2 bits each from bit 5) and
 // the channel (bits 16-31).
-__device__ __forceinline__ uint32_t kchunk_entry(const ConvGeom& g, int k) {
+__device__ __forceinline__ uint32_t kchunk_entry(const ConvGeom& g, int k, bool bias_row) {
   const int tap = k / g.cin;
+  if (bias_row && k == 27 * g.cin) return 30u;  // (1, 0, ..., 0): the bias-gradient row
   if (tap >= 27) return 31u;
   const int ci = k - tap * g.cin;
   return (uint32_t)tap | ((uint32_t)(tap / 9) << 5) | ((uint32_t)((tap / 3) % 3) << 7) |
@@ -93,6 +94,7 @@ __device__ __forceinline__ uint4 gather8(const ConvGeom& g, const __nv_bfloat16*
                                          const __nv_bfloat16* __restrict__ x1, const Row& r, uint32_t e,
                                          const int* __restrict__ s_d0, const int* __restrict__ s_d1) {
   const int tap = e & 31u;
+  if (tap == 30) return make_uint4((r.vmask >> 30) & 1u ? 0x3F80u : 0u, 0, 0, 0);  // BF16 1.0 in a valid row
   if (tap >= 27 || !((r.vmask >> tap) & 1u)) return make_uint4(0, 0, 0, 0);
   const int ci = (int)(e >> 16);
   if (ci < g.c0) {
@@ -115,8 +117,8 @@ struct GatherTables {
   int d0[27], d1[27];
 };
 
-__device__ __forceinline__ void fill_tables(const ConvGeom& g, uint32_t* ktab, int* d0, int* d1) {
-  for (int i = threadIdx.x; i < g.kpad / 8; i += blockDim.x) ktab[i] = kchunk_entry(g, i * 8);
+__device__ __forceinline__ void fill_tables(const ConvGeom& g, uint32_t* ktab, int* d0, int* d1, bool bias_row) {
+  for (int i = threadIdx.x; i < g.kpad / 8; i += blockDim.x) ktab[i] = kchunk_entry(g, i * 8, bias_row);
   for (int t = threadIdx.x; t < 27; t += blockDim.x) {
     d0[t] = tap_delta(g, t, g.c0);
     d1[t] = tap_delta(g, t, g.c1);
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(kThreads) conv_fwd_kernel(ConvGeom g, const __
   __shared__ int s_d0[27], s_d1[27];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  fill_tables(g, ktab, s_d0, s_d1);
+  fill_tables(g, ktab, s_d0, s_d1, false);
   if (warp == 0) tc::tmem_alloc(&s_tmem, kNcols);
   if (tid == 0) {
     tc::mbar_init(&bar[0], 1);
@@ -262,7 +264,7 @@ __global__ void __launch_bounds__(kThreads) conv_wgrad_kernel(ConvGeom g, const 
   __shared__ int s_d0[27], s_d1[27];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  fill_tables(g, ktab, s_d0, s_d1);
+  fill_tables(g, ktab, s_d0, s_d1, true);
   if (warp == 0) tc::tmem_alloc(&s_tmem, kNcols);
   if (tid == 0) {
     tc::mbar_init(&bar[0], 1);
@@ -355,37 +357,17 @@ __global__ void __launch_bounds__(kThreads) conv_wgrad_kernel(ConvGeom g, const 
   if (warp == 0) tc::tmem_dealloc(tmem, kNcols);
 }
 
-// dW[co][k] = sum over splits (in order) of part[split][k][co].
-__global__ void wgrad_reduce_kernel(const float* __restrict__ part, int splits, int kpad, int cout,
-                                    float* __restrict__ dw) {
+// dW[co][k] = sum over splits (in order) of part[split][k][co]; row 27*cin
+// carries the bias gradient (its A row is all ones), the padding stays zero.
+__global__ void wgrad_reduce_kernel(const float* __restrict__ part, int splits, int kpad, int kreal,
+                                    int cout, float* __restrict__ dw, float* __restrict__ db) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (long long)kpad * cout) return;
   const int k = (int)(i / cout), co = (int)(i % cout);
   float s = 0.0f;
   for (int t = 0; t < splits; ++t) s += part[((long long)t * kpad + k) * cout + co];
-  dw[(long long)co * kpad + k] = s;
-}
-
-// db[co] = sum_p dY[p, co], per-CTA partial sums then a fixed-order total.
-__global__ void bias_grad_partial_kernel(const __nv_bfloat16* __restrict__ dy, long long m, int cout,
-                                         long long per_block, float* __restrict__ part) {
-  const int co = threadIdx.x;
-  if (co >= cout) return;
-  const long long p0 = (long long)blockIdx.x * per_block;
-  long long p1 = p0 + per_block;
-  if (p1 > m) p1 = m;
-  float s = 0.0f;
-  for (long long p = p0; p < p1; ++p) s += __bfloat162float(dy[p * cout + co]);
-  part[(long long)blockIdx.x * cout + co] = s;
-}
-
-__global__ void bias_grad_reduce_kernel(const float* __restrict__ part, int blocks, int cout,
-                                        float* __restrict__ db) {
-  const int co = threadIdx.x;
-  if (co >= cout) return;
-  float s = 0.0f;
-  for (int b = 0; b < blocks; ++b) s += part[(long long)b * cout + co];
-  db[co] = s;
+  if (k == kreal && db) db[co] = s;
+  dw[(long long)co * kpad + k] = k < kreal ? s : 0.0f;
 }
 
 // Weights of the input-gradient convolution: the forward weights [Cout][kpad(Cin)]
@@ -444,8 +426,9 @@ cudaError_t launch_wgrad_t(const ConvGeom& g, const __nv_bfloat16* x0, const __n
 }  // namespace
 
 int conv_kpad(int cin) {
-  const int k = 27 * cin;
-  // the weight-gradient GEMM tiles K in rows of 128
+  // the weight-gradient GEMM tiles K in rows of 128 and uses row 27*cin (a
+  // padding row, so there is always one) for the bias gradient
+  const int k = 27 * cin + 1;
   return (k + 127) / 128 * 128;
 }
 
@@ -497,8 +480,7 @@ int conv_wgrad_splits(const nm_conv3d_desc& d) {
 }
 
 size_t conv_wgrad_workspace(const nm_conv3d_desc& d) {
-  return (size_t)conv_wgrad_splits(d) * conv_kpad(d.c0 + d.c1) * d.cout * sizeof(float) +
-         (size_t)1024 * d.cout * sizeof(float);
+  return (size_t)conv_wgrad_splits(d) * conv_kpad(d.c0 + d.c1) * d.cout * sizeof(float);
 }
 
 cudaError_t conv3d_flip_weights(const nm_conv3d_desc& d, const void* w, void* wb, cudaStream_t s) {
@@ -526,14 +508,7 @@ cudaError_t conv3d_wgrad(const nm_conv3d_desc& d, const void* x0, const void* x1
   }
   if (e != cudaSuccess) return e;
   const long long n = (long long)g.kpad * g.cout;
-  wgrad_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(part, splits, g.kpad, g.cout, dw);
-  if (db) {
-    float* bpart = part + (size_t)splits * g.kpad * g.cout;
-    const int blocks = 1024;
-    const long long per = (g.m + blocks - 1) / blocks;
-    bias_grad_partial_kernel<<<blocks, 128, 0, s>>>(DY, g.m, g.cout, per, bpart);
-    bias_grad_reduce_kernel<<<1, 128, 0, s>>>(bpart, blocks, g.cout, db);
-  }
+  wgrad_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(part, splits, g.kpad, 27 * g.cin, g.cout, dw, db);
   return cudaGetLastError();
 }
 

@@ -155,12 +155,17 @@ __global__ void head_kernel(const bf16* __restrict__ top, int c, const bf16* __r
   }
 }
 
+// out[j] = sum over blocks of part[b][j]: one warp per entry, lanes strided
+// over the blocks, then a fixed shuffle tree.
 __global__ void sum_parts_kernel(const float* __restrict__ part, int blocks, int stride, float* __restrict__ out) {
-  const int j = threadIdx.x;
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
   if (j >= stride) return;
   float s = 0.0f;
-  for (int b = 0; b < blocks; ++b) s += part[(long long)b * stride + j];
-  out[j] = s;
+  for (int b = lane; b < blocks; b += 32) s += part[(long long)b * stride + j];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[j] = s;
 }
 
 // Adam on FP32 master weights; writes the BF16 copy the convolutions read.
@@ -416,7 +421,7 @@ nm_status head(nm_denoiser* h, bool train) {
                                                     1.0f / (float)m, h->y, h->dtop, h->head_part);
   CK(cudaGetLastError(), "head");
   if (train) {
-    sum_parts_kernel<<<1, 128, 0, s>>>(h->head_part, h->head_blocks, c + 2, h->head_sum);
+    sum_parts_kernel<<<(c + 2 + 3) / 4, 128, 0, s>>>(h->head_part, h->head_blocks, c + 2, h->head_sum);
     CK(cudaGetLastError(), "head");
   }
   return NM_OK;
