@@ -34,13 +34,18 @@ def _gen(args):
 
 
 def make_phantoms(seeds, shape, spacing, workers=None):
-    """Adult phantoms for the given seeds, generated in a spawn pool."""
+    """Adult phantoms for the given seeds, generated in a spawn pool and
+    yielded in order (so that the caller can move each to the device and drop
+    the host copy)."""
     jobs = [(shape, spacing, s) for s in seeds]
     if workers == 1 or len(jobs) == 1:
-        return [_gen(j) for j in jobs]
+        for j in jobs:
+            yield _gen(j)
+        return
     ctx = mp.get_context("spawn")
     with ctx.Pool(workers or min(len(jobs), os.cpu_count() or 1)) as pool:
-        return list(pool.imap(_gen, jobs, chunksize=1))
+        for ph in pool.imap(_gen, jobs, chunksize=1):
+            yield ph
 
 
 class Case:
@@ -136,14 +141,19 @@ def time_to_target(case, ref, step_decays, max_decays, target, seed):
 def run(train_n=200, test_n=20, shape=(300, 256, 256), spacing=(0.2, 0.2, 0.3), low=int(1e7), high=int(1e9),
         ref=int(1e10), denoise_low=int(1e7), steps=3000, patch=64, batch=4, lr=1e-3, workers=None,
         step_decays=int(5e6), max_decays=int(2e9), seed0=1000, log_every=0):
+    # the pool is started (first next()) before any GPU work
     phantoms = make_phantoms(list(range(seed0, seed0 + train_n + test_n)), shape, spacing, workers)
+    first = next(phantoms)
     import torch
 
     from paper_2111_11687_gb300 import build, inputs, nmdose as nm
     build.build()
     mats = nm.Materials(inputs.MATERIAL_Z_OVER_A, inputs.MATERIAL_ZEFF, inputs.PE_COEFF, inputs.PE_EXP)
-    cases = [Case(nm, torch, ph, mats, inputs.N_LABELS, inputs.ACTIVITY_BQ) for ph in phantoms]
-    del phantoms
+    cases = [Case(nm, torch, first, mats, inputs.N_LABELS, inputs.ACTIVITY_BQ)]
+    del first
+    for ph in phantoms:
+        cases.append(Case(nm, torch, ph, mats, inputs.N_LABELS, inputs.ACTIVITY_BQ))
+        del ph
     tr, te = cases[:train_n], cases[train_n:]
     t0 = time.perf_counter()
     lows = [c.dose(low, 7)[0] for c in tr]
