@@ -15,6 +15,8 @@
 // drains what it issued (bounded again), frees its tensor memory and returns.
 #include <cuda_bf16.h>
 
+#include <cstdlib>
+
 #include "nm_internal.cuh"
 #include "nm_tc.cuh"
 
@@ -455,6 +457,10 @@ static ConvGeom make_geom(const nm_conv3d_desc& d) {
 
 cudaError_t conv3d_fwd(const nm_conv3d_desc& d, const void* x0, const void* x1, const void* w,
                        const float* bias, void* y, int relu, uint32_t* status, cudaStream_t s) {
+  // Single-source convolutions with few output channels take the shifted-window
+  // kernel (no im2col gather); NM_CONV_GATHER=1 forces the gather kernel.
+  const char* force = getenv("NM_CONV_GATHER");
+  if (conv_tile_ok(d) && !(force && force[0] == '1')) return conv3d_fwd_tile(d, x0, w, bias, y, relu, status, s);
   const ConvGeom g = make_geom(d);
   auto X0 = (const __nv_bfloat16*)x0, X1 = (const __nv_bfloat16*)x1, W = (const __nv_bfloat16*)w;
   auto Y = (__nv_bfloat16*)y;

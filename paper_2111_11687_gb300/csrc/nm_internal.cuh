@@ -188,6 +188,9 @@ int conv_wgrad_splits(const nm_conv3d_desc& d);
 size_t conv_wgrad_workspace(const nm_conv3d_desc& d);
 cudaError_t conv3d_fwd(const nm_conv3d_desc& d, const void* x0, const void* x1, const void* w,
                        const float* bias, void* y, int relu, uint32_t* status, cudaStream_t s);
+bool conv_tile_ok(const nm_conv3d_desc& d);
+cudaError_t conv3d_fwd_tile(const nm_conv3d_desc& d, const void* x, const void* w, const float* bias, void* y,
+                            int relu, uint32_t* status, cudaStream_t s);
 cudaError_t conv3d_flip_weights(const nm_conv3d_desc& d, const void* w, void* wb, cudaStream_t s);
 cudaError_t conv3d_wgrad(const nm_conv3d_desc& d, const void* x0, const void* x1, const void* dy,
                          float* dw, float* db, void* workspace, uint32_t* status, cudaStream_t s);

@@ -44,6 +44,8 @@ def weights_padded(torch, w3, kpad):
 CASES = [
     # n, d, h, w, c0, c1, coarse, cout
     (1, 8, 8, 8, 8, 0, 0, 16),        # first layer (3 channels padded to 8)
+    (2, 5, 19, 17, 24, 0, 0, 16),     # ragged shifted-window tiles, 24 channels (a half 16-chunk)
+    (1, 9, 33, 35, 48, 0, 0, 32),
     (2, 6, 7, 9, 16, 0, 0, 32),       # ragged voxel count (756, not a multiple of 128)
     (1, 8, 8, 8, 32, 16, 1, 16),      # decoder: upsampled 32 channels + 16 skip
     (1, 4, 4, 4, 64, 0, 0, 128),
@@ -52,8 +54,19 @@ CASES = [
 ]
 
 
+@pytest.fixture(params=["default", "gather"])
+def conv_path(request, monkeypatch):
+    # "default": single-source convolutions with 16 or 32 outputs take the
+    # shifted-window kernel; "gather": the im2col-gather kernel for everything.
+    if request.param == "gather":
+        monkeypatch.setenv("NM_CONV_GATHER", "1")
+    else:
+        monkeypatch.delenv("NM_CONV_GATHER", raising=False)
+    return request.param
+
+
 @pytest.mark.parametrize("case", CASES)
-def test_conv_forward_dgrad_wgrad(env, case):
+def test_conv_forward_dgrad_wgrad(env, case, conv_path):
     torch, nm, dn = env
     n, d, h, w, c0, c1, coarse, cout = case
     cin = c0 + c1
