@@ -136,6 +136,7 @@ __global__ void __launch_bounds__(kThreads) conv_fwd_kernel(ConvGeom g, const __
                                                             const __nv_bfloat16* __restrict__ wt,
                                                             const float* __restrict__ bias,
                                                             __nv_bfloat16* __restrict__ y, int relu,
+                                                            float* __restrict__ part, int stages_per_split,
                                                             uint32_t* status) {
   constexpr int kNcols = COUT <= 32 ? 32 : COUT <= 64 ? 64 : COUT <= 128 ? 128 : 256;
   constexpr uint32_t kABytes = kBM * kKS * 2;       // 16 KB
@@ -167,13 +168,17 @@ __global__ void __launch_bounds__(kThreads) conv_fwd_kernel(ConvGeom g, const __
   Row row;
   if (row_ok) row = make_row(g, m_row);
   else row.vmask = 0u;
-  const int nstages = g.kpad / kKS;
+  // split K: this CTA takes stages [s0, s0 + nstages) of the GEMM depth
+  const int s0 = blockIdx.y * stages_per_split;
+  int nstages = g.kpad / kKS - s0;
+  if (nstages > stages_per_split) nstages = stages_per_split;
   constexpr uint32_t idesc = tc::idesc_bf16_f32(kBM, COUT, false, false);
   bool timeout = false;
   int issued = 0;  // stages whose MMAs were issued
 
   for (int s = 0; s < nstages; ++s) {
     const int buf = s & 1;
+    const int sg = s0 + s;
     if (s >= 2 && !tc::mbar_wait_bounded(&bar[buf], ((s >> 1) - 1) & 1, kWaitCycles)) timeout = true;
     if (__syncthreads_or(timeout)) { timeout = true; break; }
     uint8_t* a = sa + buf * kABytes;
@@ -181,7 +186,7 @@ __global__ void __launch_bounds__(kThreads) conv_fwd_kernel(ConvGeom g, const __
     // A: this thread's row, 8 chunks of 8 channels.
 #pragma unroll
     for (int kc = 0; kc < 8; ++kc) {
-      const uint4 v = gather8(g, x0, x1, row, ktab[s * (kKS / 8) + kc], s_d0, s_d1);
+      const uint4 v = gather8(g, x0, x1, row, ktab[sg * (kKS / 8) + kc], s_d0, s_d1);
       *reinterpret_cast<uint4*>(a + (tid >> 3) * kSbo + kc * 128 + (tid & 7) * 16) = v;
     }
     // B: COUT rows x 8 chunks of the weight matrix [Cout][kpad].
@@ -189,7 +194,7 @@ __global__ void __launch_bounds__(kThreads) conv_fwd_kernel(ConvGeom g, const __
     for (int i = 0; i < COUT / 16; ++i) {
       const int q = tid + kThreads * i;
       const int r = q >> 3, kc = q & 7;
-      const uint4 v = __ldg(reinterpret_cast<const uint4*>(wt + (long long)r * g.kpad + s * kKS + kc * 8));
+      const uint4 v = __ldg(reinterpret_cast<const uint4*>(wt + (long long)r * g.kpad + sg * kKS + kc * 8));
       *reinterpret_cast<uint4*>(bm + (r >> 3) * kSbo + kc * 128 + (r & 7) * 16) = v;
     }
     tc::fence_async_smem();
@@ -222,7 +227,11 @@ __global__ void __launch_bounds__(kThreads) conv_fwd_kernel(ConvGeom g, const __
     for (int c = 0; c < COUT / 16; ++c) {
       float v[16];
       tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c * 16, v);
-      if (m < g.m) {
+      if (m < g.m && part) {
+        float* dst = part + ((long long)blockIdx.y * g.m + m) * COUT + c * 16;
+#pragma unroll
+        for (int j = 0; j < 16; j += 4) *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+      } else if (m < g.m) {
         __align__(16) __nv_bfloat16 o[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
@@ -385,6 +394,18 @@ __global__ void flip_weights_kernel(const __nv_bfloat16* __restrict__ w, int cin
   wb[i] = v;
 }
 
+// y = act(sum over splits of part + bias) for split-K forward convolutions.
+__global__ void split_finish_kernel(const float* __restrict__ part, int splits, long long m, int cout,
+                                    const float* __restrict__ bias, int relu, __nv_bfloat16* __restrict__ y) {
+  const long long n = m * cout;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    float t = bias ? bias[i % cout] : 0.0f;
+    for (int k = 0; k < splits; ++k) t += part[(long long)k * n + i];
+    if (relu) t = fmaxf(t, 0.0f);
+    y[i] = __float2bfloat16_rn(t);
+  }
+}
+
 template <int COUT>
 size_t fwd_smem_base() { return 2 * (size_t)kBM * kKS * 2 + 2 * (size_t)COUT * kKS * 2; }
 
@@ -400,8 +421,29 @@ cudaError_t launch_fwd_t(const ConvGeom& g, const __nv_bfloat16* x0, const __nv_
   cudaError_t e = cudaFuncSetAttribute(conv_fwd_kernel<COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const long long grid = (g.m + kBM - 1) / kBM;
-  conv_fwd_kernel<COUT><<<(unsigned)grid, kThreads, smem, s>>>(g, x0, x1, w, bias, y, relu, status);
-  return cudaGetLastError();
+  // Few row tiles and a deep K: split K over CTAs so that every SM has work.
+  const int nst = g.kpad / kKS;
+  int splits = 1;
+  if (grid < 2 * 152) {
+    splits = (int)((2 * 152 + grid - 1) / grid);
+    if (splits > nst / 4) splits = nst / 4 > 1 ? nst / 4 : 1;
+  }
+  const int per = (nst + splits - 1) / splits;
+  splits = (nst + per - 1) / per;
+  if (splits == 1) {
+    conv_fwd_kernel<COUT><<<(unsigned)grid, kThreads, smem, s>>>(g, x0, x1, w, bias, y, relu, nullptr, per, status);
+    return cudaGetLastError();
+  }
+  float* part = nullptr;
+  if ((e = cudaMallocAsync((void**)&part, (size_t)splits * g.m * COUT * sizeof(float), s))) return e;
+  conv_fwd_kernel<COUT><<<dim3((unsigned)grid, splits), kThreads, smem, s>>>(g, x0, x1, w, bias, y, relu, part, per,
+                                                                           status);
+  const long long n = g.m * COUT;
+  split_finish_kernel<<<(unsigned)((n + 255) / 256 < 8192 ? (n + 255) / 256 : 8192), 256, 0, s>>>(
+      part, splits, g.m, COUT, bias, relu, y);
+  e = cudaGetLastError();
+  cudaFreeAsync(part, s);
+  return e;
 }
 
 // The weight-gradient buffers are over-allocated to 96 KB: every read the

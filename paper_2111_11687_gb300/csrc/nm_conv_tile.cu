@@ -197,7 +197,7 @@ cudaError_t launch_tile(const nm_conv3d_desc& g, const void* x, const void* w, c
 }  // namespace
 
 bool conv_tile_ok(const nm_conv3d_desc& d) {
-  return d.c1 == 0 && !d.src0_coarse && d.c0 % 8 == 0 && d.c0 <= 64 && (d.cout == 16 || d.cout == 32);
+  return d.c1 == 0 && !d.src0_coarse && d.c0 % 8 == 0 && (d.cout == 16 || d.cout == 32);
 }
 
 cudaError_t conv3d_fwd_tile(const nm_conv3d_desc& d, const void* x, const void* w, const float* bias, void* y,

@@ -54,6 +54,31 @@ __global__ void avgpool_kernel(const bf16* __restrict__ x, int n, int s, int c, 
   }
 }
 
+// cat[v] = [coarse[parent(v)] (c0 channels) | skip[v] (c1 channels)], 16 bytes at a time.
+__global__ void upsample_concat_kernel(const bf16* __restrict__ coarse, const bf16* __restrict__ skip, int n, int s,
+                                       int c0, int c1, bf16* __restrict__ cat) {
+  const int h = s >> 1, c = c0 + c1, q = c / 8;
+  const long long total = (long long)n * s * s * s * q;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(i % q);
+    long long v = i / q;
+    uint4 val;
+    if (j * 8 < c0) {
+      long long t = v;
+      const int xx = (int)(t % s); t /= s;
+      const int yy = (int)(t % s); t /= s;
+      const int zz = (int)(t % s);
+      const int b = (int)(t / s);
+      const long long pv = (((long long)b * h + (zz >> 1)) * h + (yy >> 1)) * h + (xx >> 1);
+      val = *reinterpret_cast<const uint4*>(coarse + pv * c0 + j * 8);
+    } else {
+      val = *reinterpret_cast<const uint4*>(skip + v * c1 + (j * 8 - c0));
+    }
+    *reinterpret_cast<uint4*>(cat + v * c + j * 8) = val;
+  }
+}
+
 // g *= (act > 0)
 __global__ void relu_mask_kernel(bf16* __restrict__ g, const bf16* __restrict__ act, long long n) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -300,6 +325,7 @@ struct nm_denoiser {
   std::vector<bf16*> ea, eb, pool, da, db;
   bf16 *gA = nullptr, *gB = nullptr, *gC = nullptr, *gD = nullptr;  // gradient scratch (largest size)
   std::vector<bf16*> gskip;
+  std::vector<bf16*> cat;          // materialised decoder inputs (shifted-window path)
   bf16* x_in = nullptr;
   float* y = nullptr;
   float* target = nullptr;
@@ -322,6 +348,7 @@ struct nm_denoiser {
     for (auto p : da) f(p);
     for (auto p : db) f(p);
     for (auto p : gskip) f(p);
+    for (auto p : cat) f(p);
     f(gA); f(gB); f(gC); f(gD); f(x_in); f(y); f(target); f(weight); f(dtop); f(head_part); f(head_sum);
     f(ws); f(status);
   }
@@ -382,6 +409,17 @@ nm_status check_status(nm_denoiser* h) {
   return NM_OK;
 }
 
+// Decoder input convolution as one materialised source (upsampled coarse |
+// skip) when the shifted-window kernel can take it.
+nm_conv3d_desc single_source(const nm_denoiser* h, const Layer& l) {
+  nm_conv3d_desc d = h->desc(l);
+  d.c0 = l.c0 + l.c1;
+  d.c1 = 0;
+  d.src0_coarse = 0;
+  return d;
+}
+bool use_cat(const nm_denoiser* h, const Layer& l) { return l.c1 > 0 && conv_tile_ok(single_source(h, l)); }
+
 nm_status forward(nm_denoiser* h) {
   cudaStream_t s = h->s;
   const int L = h->L;
@@ -402,7 +440,15 @@ nm_status forward(nm_denoiser* h) {
   for (int i = L - 2; i >= 0; --i) {
     const Layer& la = h->layers[li++];
     const Layer& lb = h->layers[li++];
-    CK(conv3d_fwd(h->desc(la), coarse, h->eb[i], h->wb + la.w_off, h->w + la.b_off, h->da[i], 1, h->status, s), "conv");
+    if (use_cat(h, la)) {
+      const long long n = h->vox(i) * (la.cin / 8);
+      upsample_concat_kernel<<<grid1d(n), 256, 0, s>>>(coarse, h->eb[i], h->B, h->P >> i, la.c0, la.c1, h->cat[i]);
+      CK(conv3d_fwd(single_source(h, la), h->cat[i], nullptr, h->wb + la.w_off, h->w + la.b_off, h->da[i], 1,
+                    h->status, s), "conv");
+    } else {
+      CK(conv3d_fwd(h->desc(la), coarse, h->eb[i], h->wb + la.w_off, h->w + la.b_off, h->da[i], 1, h->status, s),
+         "conv");
+    }
     CK(conv3d_fwd(h->desc(lb), h->da[i], nullptr, h->wb + lb.w_off, h->w + lb.b_off, h->db[i], 1, h->status, s), "conv");
     coarse = h->db[i];
   }
@@ -438,6 +484,16 @@ nm_status backward(nm_denoiser* h) {
     for (auto& l : h->layers) if (l.name == n) return l;
     return h->layers[0];
   };
+  auto conv_back_input = [&](const Layer& l, const bf16* gout, bf16* gin) -> nm_status {
+    nm_conv3d_desc fd = h->desc(l);
+    CK(conv3d_flip_weights(fd, h->wb + l.w_off, h->wflip, s), "flip");
+    nm_conv3d_desc bd;
+    memset(&bd, 0, sizeof bd);
+    bd.n = fd.n; bd.d = bd.h = bd.w = l.size;
+    bd.c0 = l.cout; bd.cout = l.c0 + l.c1;
+    CK(conv3d_fwd(bd, gout, nullptr, h->wflip, nullptr, gin, 0, h->status, s), "dgrad");
+    return NM_OK;
+  };
   auto conv_back = [&](const Layer& l, const bf16* x0, const bf16* x1, const bf16* gout, bf16* gin) -> nm_status {
     // weight/bias gradients, then (if gin) the input gradient through flipped weights
     CK(conv3d_wgrad(h->desc(l), x0, x1, gout, h->g + l.w_off, h->g + l.b_off, h->ws, h->status, s), "wgrad");
@@ -463,7 +519,14 @@ nm_status backward(nm_denoiser* h) {
     if ((st = conv_back(lb, h->da[i], nullptr, g, h->gA)) != NM_OK) return st;
     relu_mask_kernel<<<grid1d(nb), 256, 0, s>>>(h->gA, h->da[i], nb);
     const bf16* coarse = i + 1 <= L - 2 ? h->db[i + 1] : h->eb[L - 1];
-    if ((st = conv_back(la, coarse, h->eb[i], h->gA, h->gB)) != NM_OK) return st;
+    if (use_cat(h, la)) {
+      // same im2col rows, read from the materialised input
+      CK(conv3d_wgrad(single_source(h, la), h->cat[i], nullptr, h->gA, h->g + la.w_off, h->g + la.b_off, h->ws,
+                      h->status, s), "wgrad");
+      if ((st = conv_back_input(la, h->gA, h->gB)) != NM_OK) return st;
+    } else if ((st = conv_back(la, coarse, h->eb[i], h->gA, h->gB)) != NM_OK) {
+      return st;
+    }
     const long long total = h->vox(i + 1) * h->widths[i + 1] + nb;
     split_concat_grad_kernel<<<grid1d(total), 256, 0, s>>>(h->gB, h->B, h->P >> i, h->widths[i + 1], h->widths[i],
                                                            coarse, h->gC, h->gskip[i]);
@@ -566,6 +629,9 @@ nm_status nm_denoise_create(nm_denoiser** out, const nm_denoise_options* opts) {
   if ((e = dmalloc(&h->wflip, flip)) || (e = cudaMalloc(&h->ws, ws))) return bail(cfail(e, "denoiser workspace"));
   h->ea.resize(h->L); h->eb.resize(h->L); h->pool.resize(h->L); h->da.resize(h->L); h->db.resize(h->L);
   h->gskip.resize(h->L);
+  h->cat.assign(h->L, nullptr);
+  for (int i = 0; i + 1 < h->L; ++i)
+    if ((e = dmalloc(&h->cat[i], h->vox(i) * (h->widths[i] + h->widths[i + 1])))) return bail(cfail(e, "activations"));
   long long gmax = 0;
   for (int i = 0; i < h->L; ++i) {
     const long long n = h->vox(i) * h->widths[i];
