@@ -95,6 +95,7 @@ struct nm_dose {
   double* s2 = nullptr;
   float* kn = nullptr;
   float* minv = nullptr;
+  float* minv_out = nullptr;
   ull* counters = nullptr;     // kCtrCount
   unsigned* work = nullptr;
   uint32_t* status = nullptr;
@@ -114,11 +115,13 @@ struct nm_dose {
   int block = 256, chunk = 256, warp_agg = 0, regroup = 0, regroup_lanes = 12, grid = 0;
   std::vector<cudaEvent_t> ev;
   std::vector<float> minv_host;   // host copy of the majorant table
+  std::vector<float> minv_out_host;  // ... and of the one outside the tracking box
+  float blo[3] = {0, 0, 0}, bhi[3] = {0, 0, 0};  // tracking box, voxel units
   bool tuned = false;             // launch shape chosen by the autotuner
   double batch_graph_ms = 0;      // device time of graphs launched by nm_dose_run_batch
 
   ~nm_dose() {
-    void* ptrs[] = {vox, density, labels, alias, tb, tsum, s2, kn, minv, counters, work, status,
+    void* ptrs[] = {vox, density, labels, alias, tb, tsum, s2, kn, minv, minv_out, counters, work, status,
                     rho_max_bits, org_s1, org_s2, organ_count, organ_partial, organ_out,
                     out_dose, out_sigma};
     for (void* p : ptrs)
@@ -143,6 +146,10 @@ struct nm_dose {
     g.source_mode = opt.source_mode;
     g.px = opt.point[0] / dx; g.py = opt.point[1] / dy; g.pz = opt.point[2] / dz;
     g.q_positron = q_pos;
+    for (int a = 0; a < 3; ++a) {
+      g.blo[a] = blo[a];
+      g.bhi[a] = bhi[a];
+    }
     return g;
   }
 
@@ -153,6 +160,7 @@ struct nm_dose {
     p.status = status;
     p.kn = kn;
     p.minv = minv;
+    p.minv_out = minv_out;
     p.key0 = (uint32_t)seed;
     p.key1 = (uint32_t)(seed >> 32);
     p.e0 = e0;
@@ -439,7 +447,7 @@ nm_status nm_dose_create(nm_dose** out, const nm_grid* g, const nm_materials* mt
 
   if ((e = dalloc(&h->vox, V)) || (e = dalloc(&h->density, V)) || (e = dalloc(&h->tb, V)) ||
       (e = dalloc(&h->tsum, V)) || (e = dalloc(&h->s2, V)) || (e = dalloc(&h->kn, kKnTable)) ||
-      (e = dalloc(&h->minv, kKnTable)) ||
+      (e = dalloc(&h->minv, kKnTable)) || (e = dalloc(&h->minv_out, kKnTable)) ||
       (e = dalloc(&h->counters, kCtrCount)) || (e = dalloc(&h->work, 1)) ||
       (e = dalloc(&h->status, 1)) || (e = dalloc(&h->rho_max_bits, NM_MAX_MATERIALS)) ||
       (e = dalloc(&h->org_s1, kLabelSlots)) || (e = dalloc(&h->org_s2, kLabelSlots)) ||
@@ -484,27 +492,25 @@ nm_status nm_dose_create(nm_dose** out, const nm_grid* g, const nm_materials* mt
     memcpy(&r, &rho_bits[m], 4);
     h->mat[m].rho_max = m < h->n_mat ? r : 0.0f;
   }
-  // Woodcock majorant per table bin [E_i, E_i+1): every mu/rho decreases with E,
-  // so the value at E_i over all materials at their largest density bounds mu
-  // on the whole bin.  Evaluated in FP64 from the FP32 coefficients the kernel
-  // uses, with a 1e-4 margin for the kernel's FP32 rounding and ln E error,
-  // and stored as a reciprocal rounded down.
-  std::vector<float> minv(kKnTable);
-  for (int i = 0; i < kKnTable; ++i) {
-    const double ei = std::exp(std::log(e_lo) + i * dln);
-    double maj = 0.0;
-    for (int m = 0; m < h->n_mat; ++m) {
-      const double mu = (double)h->mat[m].za * (double)kn[i] +
-                        (double)h->mat[m].zp / (ei * ei * ei) +
-                        (double)h->mat[m].zr / (ei * ei);
-      maj = std::max(maj, (double)h->mat[m].rho_max * mu);
-    }
-    maj *= 1.0 + 1e-4;
-    minv[i] = std::nextafter((float)(1.0 / maj), 0.0f);
+  // Woodcock majorants per table bin: over the whole grid, and outside the
+  // tracking box around the body.
+  float rho_max[NM_MAX_MATERIALS], rho_out[NM_MAX_MATERIALS];
+  for (int m = 0; m < NM_MAX_MATERIALS; ++m) rho_max[m] = h->mat[m].rho_max;
+  {
+    int* box_dev = nullptr;
+    if ((e = dalloc(&box_dev, 16))) return bail(cuda_fail(e, "device allocation"));
+    e = woodcock_regions(h->vox, h->nx, h->ny, h->nz, box_dev, (uint32_t*)(box_dev + 8), h->blo, h->bhi, rho_out, s);
+    cudaFree(box_dev);
+    if (e) return bail(cuda_fail(e, "tracking regions"));
   }
-  if ((e = cudaMemcpy(h->minv, minv.data(), kKnTable * sizeof(float), cudaMemcpyHostToDevice)))
+  std::vector<float> minv(kKnTable), minv_out(kKnTable);
+  majorant_table(h->mat, h->n_mat, rho_max, kn.data(), e_lo, dln, minv.data());
+  majorant_table(h->mat, h->n_mat, rho_out, kn.data(), e_lo, dln, minv_out.data());
+  if ((e = cudaMemcpy(h->minv, minv.data(), kKnTable * sizeof(float), cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(h->minv_out, minv_out.data(), kKnTable * sizeof(float), cudaMemcpyHostToDevice)))
     return bail(cuda_fail(e, "majorant table"));
   h->minv_host = minv;
+  h->minv_out_host = minv_out;
 
   // Decay sampler: alias table over the active voxels, FP64 on the device.
   if (o.source_mode == NM_SOURCE_DECAY) {
@@ -649,11 +655,15 @@ extern "C" nm_status nm_dose_run_batch(nm_dose* const* hs, int32_t n, const uint
   if (total == 0) return NM_OK;
 
   // Shared physics: the batch majorant is the largest of the patients'.
-  std::vector<float> minv(kKnTable);
+  std::vector<float> minv(2 * kKnTable);   // inside the tracking boxes, then outside
   for (int k = 0; k < kKnTable; ++k) {
-    float m = h0->minv_host[k];
-    for (int i = 1; i < n; ++i) m = std::min(m, hs[i]->minv_host[k]);
+    float m = h0->minv_host[k], mo = h0->minv_out_host[k];
+    for (int i = 1; i < n; ++i) {
+      m = std::min(m, hs[i]->minv_host[k]);
+      mo = std::min(mo, hs[i]->minv_out_host[k]);
+    }
     minv[k] = m;
+    minv[kKnTable + k] = mo;
   }
   // Temporary device memory: per-batch patient tables, majorant, status.
   PatientGeom* d_pat = nullptr;
@@ -683,15 +693,16 @@ extern "C" nm_status nm_dose_run_batch(nm_dose* const* hs, int32_t n, const uint
       if (nb >= (1ull << 31)) { cleanup(); return fail(NM_ERR_ARG, "handle %d: batches above 2^31 histories", i); }
     }
   if ((e = cudaMalloc(&d_pat, pat.size() * sizeof(PatientGeom))) ||
-      (e = cudaMalloc(&d_minv, kKnTable * sizeof(float))) || (e = cudaMalloc(&d_status, 4)) ||
+      (e = cudaMalloc(&d_minv, 2 * kKnTable * sizeof(float))) || (e = cudaMalloc(&d_status, 4)) ||
       (e = cudaMemcpyAsync(d_pat, pat.data(), pat.size() * sizeof(PatientGeom), cudaMemcpyHostToDevice, s)) ||
-      (e = cudaMemcpyAsync(d_minv, minv.data(), kKnTable * sizeof(float), cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemcpyAsync(d_minv, minv.data(), 2 * kKnTable * sizeof(float), cudaMemcpyHostToDevice, s)) ||
       (e = cudaMemsetAsync(d_status, 0, 4, s)) || (e = cudaStreamSynchronize(s))) {
     cleanup();
     return cuda_fail(e, "nm_dose_run_batch: set-up");
   }
   TransportParams p = h0->params(0, 0, seed);
   p.minv = d_minv;
+  p.minv_out = d_minv + kKnTable;
   p.status = d_status;
   p.n_patients = n;
 

@@ -78,6 +78,10 @@ struct PatientGeom {
   int source_mode;
   float px, py, pz;           // point source, voxel units
   int32_t q_positron;         // q_units(positron energy), 0 in point mode
+  // Two-region Woodcock tracking: the box [blo, bhi) (voxel units) holds every
+  // voxel denser than kRegionDensity plus a one-voxel margin; outside it the
+  // majorant is TransportParams::minv_out.
+  float blo[3], bhi[3];
 };
 
 struct TransportParams {
@@ -87,6 +91,7 @@ struct TransportParams {
   uint32_t* status;           // NM_DEV_* flags
   const float* kn;            // kKnTable nodes of N_A * sigma_KN(E)
   const float* minv;          // kKnTable bins: 1 / majorant (cm) on [E_i, E_i+1)
+  const float* minv_out;      // the same outside the tracking box (much larger)
   uint32_t key0, key1;        // Philox key = seed
   float e0;                   // photon energy, MeV
   int32_t q_e0;               // q_units(e0)
@@ -125,6 +130,22 @@ cudaError_t launch_check_source(const TransportParams& p, uint64_t first, int64_
 // HU -> density/material (§2.1).
 cudaError_t launch_ct_to_phantom(const int16_t* hu, int64_t n, float* density, uint8_t* material,
                                  cudaStream_t s);
+
+// Woodcock regions of a packed grid: the tracking box [blo, bhi) in voxel
+// units (the voxels denser than kRegionDensity, one voxel of margin, clamped to
+// the grid; empty when there are none) and the per-material largest density
+// outside the unpadded box.  box_dev (6 ints) and rho_dev (NM_MAX_MATERIALS
+// words) are device scratch; synchronises the stream.
+constexpr float kRegionDensity = 0.05f;   // g/cm^3: denser than any air, lighter than lung
+cudaError_t woodcock_regions(const uint32_t* vox, int nx, int ny, int nz, int* box_dev, uint32_t* rho_dev,
+                             float blo[3], float bhi[3], float rho_out[NM_MAX_MATERIALS], cudaStream_t s);
+// Per-bin inverse majorant (cm) for the materials at densities rho[m]: every
+// mu/rho decreases with E, so the value at a bin's lower edge bounds the bin.
+// FP64 from the FP32 coefficients the kernel uses, 1e-4 margin for the
+// kernel's FP32 rounding, reciprocal rounded down; an empty region gets a
+// finite 1e12 cm.
+void majorant_table(const MaterialCoef* mat, int n_mat, const float* rho, const float* kn, double e_lo, double dln,
+                    float* minv);
 
 // Voxel packing and validation; per-material maximum density (as float bits).
 cudaError_t launch_pack_voxels(const float* density, const uint8_t* material, int64_t V, int n_mat,

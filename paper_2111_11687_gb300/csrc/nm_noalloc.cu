@@ -130,7 +130,8 @@ extern "C" nm_status nm_dose_tally_noalloc(const nm_grid* g, const nm_materials*
   uint32_t* vox = (uint32_t*)take(4 * V);
   uint4* alias = (uint4*)take(16 * V);
   float* kn_d = (float*)take(4 * kKnTable);
-  float* minv_d = (float*)take(4 * kKnTable);
+  float* minv_d = (float*)take(8 * kKnTable);     // whole grid, then outside the tracking box
+  int* box_d = (int*)take(64);
   ull* ctr_d = (ull*)take(sizeof(ull) * kCtrCount);
   unsigned* work = (unsigned*)take(sizeof(unsigned));
   uint32_t* status = (uint32_t*)take(sizeof(uint32_t));
@@ -160,7 +161,7 @@ extern "C" nm_status nm_dose_tally_noalloc(const nm_grid* g, const nm_materials*
   memset(&p, 0, sizeof p);
   const double e_lo = 0.5 * mt->photon_cut_mev, e_hi = 1.05 * o.photon_mev;
   const double dln = (std::log(e_hi) - std::log(e_lo)) / (kKnTable - 1);
-  float kn[kKnTable], minv[kKnTable];
+  float kn[kKnTable], minv[2 * kKnTable];
   for (int i = 0; i < kKnTable; ++i) kn[i] = (float)(kAvogadro * kn_sigma(std::exp(std::log(e_lo) + i * dln)));
   for (int m = 0; m < mt->n; ++m) {
     p.mat[m].za = (float)mt->z_over_a[m];
@@ -168,15 +169,12 @@ extern "C" nm_status nm_dose_tally_noalloc(const nm_grid* g, const nm_materials*
     p.mat[m].zr = mt->rayleigh ? (float)(mt->rayleigh_coeff * mt->zeff[m] * mt->zeff[m]) : 0.0f;
     memcpy(&p.mat[m].rho_max, &rho_bits[m], 4);
   }
-  for (int i = 0; i < kKnTable; ++i) {
-    const double ei = std::exp(std::log(e_lo) + i * dln);
-    double maj = 0.0;
-    for (int m = 0; m < mt->n; ++m)
-      maj = std::max(maj, (double)p.mat[m].rho_max *
-                              ((double)p.mat[m].za * kn[i] + (double)p.mat[m].zp / (ei * ei * ei) +
-                               (double)p.mat[m].zr / (ei * ei)));
-    minv[i] = std::nextafter((float)(1.0 / (maj * (1.0 + 1e-4))), 0.0f);
-  }
+  float rho_max[NM_MAX_MATERIALS], rho_out[NM_MAX_MATERIALS];
+  for (int m = 0; m < NM_MAX_MATERIALS; ++m) rho_max[m] = p.mat[m].rho_max;
+  if ((e = woodcock_regions(vox, g->nx, g->ny, g->nz, box_d, (uint32_t*)(box_d + 8), p.g.blo, p.g.bhi, rho_out, s)))
+    return cuda_fail(e, "tracking regions");
+  majorant_table(p.mat, mt->n, rho_max, kn, e_lo, dln, minv);
+  majorant_table(p.mat, mt->n, rho_out, kn, e_lo, dln, minv + kKnTable);
   if ((e = cudaMemcpyAsync(kn_d, kn, sizeof kn, cudaMemcpyHostToDevice, s)) ||
       (e = cudaMemcpyAsync(minv_d, minv, sizeof minv, cudaMemcpyHostToDevice, s)) ||
       (e = cudaStreamSynchronize(s)))
@@ -207,6 +205,7 @@ extern "C" nm_status nm_dose_tally_noalloc(const nm_grid* g, const nm_materials*
   p.status = status;
   p.kn = kn_d;
   p.minv = minv_d;
+  p.minv_out = minv_d + kKnTable;
   p.key0 = (uint32_t)seed;
   p.key1 = (uint32_t)(seed >> 32);
   p.e0 = (float)o.photon_mev;

@@ -13,6 +13,10 @@
 //             alias = heavy m+1 (prob 1 if no such k, or for the last heavy).
 // Each item's probability mass then sums to its weight exactly.  The scans
 // use a fixed reduction tree, so the table is the same on every run.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
 #include "nm_internal.cuh"
 
 namespace nm {
@@ -289,6 +293,45 @@ __global__ void heavy_columns_kernel(const double* D, int64_t a, const int32_t* 
   }
 }
 
+__global__ void region_box_kernel(const uint32_t* __restrict__ vox, int nx, int ny, int nz, float thresh,
+                                  int* box) {
+  // box: [xmin, ymin, zmin, xmax, ymax, zmax]
+  int lo[3] = {nx, ny, nz}, hi[3] = {-1, -1, -1};
+  const long long V = (long long)nx * ny * nz;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x) {
+    if (__uint_as_float(vox[i] & ~7u) > thresh) {
+      const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long long)nx * ny));
+      lo[0] = min(lo[0], x); lo[1] = min(lo[1], y); lo[2] = min(lo[2], z);
+      hi[0] = max(hi[0], x); hi[1] = max(hi[1], y); hi[2] = max(hi[2], z);
+    }
+  }
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = __reduce_min_sync(0xffffffffu, lo[a]);
+    hi[a] = __reduce_max_sync(0xffffffffu, hi[a]);
+  }
+  if ((threadIdx.x & 31) == 0)
+    for (int a = 0; a < 3; ++a) {
+      atomicMin(box + a, lo[a]);
+      atomicMax(box + 3 + a, hi[a]);
+    }
+}
+
+__global__ void region_rho_out_kernel(const uint32_t* __restrict__ vox, int nx, int ny, int nz, int x0, int y0,
+                                      int z0, int x1, int y1, int z1, uint32_t* rho_max_bits) {
+  __shared__ uint32_t s_max[NM_MAX_MATERIALS];
+  if (threadIdx.x < NM_MAX_MATERIALS) s_max[threadIdx.x] = 0;
+  __syncthreads();
+  const long long V = (long long)nx * ny * nz;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long long)nx * ny));
+    if (x >= x0 && x <= x1 && y >= y0 && y <= y1 && z >= z0 && z <= z1) continue;
+    const uint32_t w = vox[i];
+    atomicMax(&s_max[w & 7u], w & ~7u);
+  }
+  __syncthreads();
+  if (threadIdx.x < NM_MAX_MATERIALS && s_max[threadIdx.x]) atomicMax(rho_max_bits + threadIdx.x, s_max[threadIdx.x]);
+}
+
 __global__ void label_count_kernel(const uint8_t* labels, int64_t V, long long* count) {
   __shared__ long long s[kLabelSlots];
   if (threadIdx.x < kLabelSlots) s[threadIdx.x] = 0;
@@ -362,6 +405,48 @@ cudaError_t launch_pack_voxels(const float* density, const uint8_t* material, in
   pack_voxels_kernel<<<grid_for(V), 256, 0, s>>>(density, material, V, n_mat, vox, rho_max_bits,
                                                  status);
   return cudaGetLastError();
+}
+
+cudaError_t woodcock_regions(const uint32_t* vox, int nx, int ny, int nz, int* box_dev, uint32_t* rho_dev,
+                             float blo[3], float bhi[3], float rho_out[NM_MAX_MATERIALS], cudaStream_t s) {
+  const long long V = (long long)nx * ny * nz;
+  const int init[6] = {nx, ny, nz, -1, -1, -1};
+  int b[6];
+  uint32_t bits[NM_MAX_MATERIALS];
+  cudaError_t e = cudaMemcpyAsync(box_dev, init, sizeof init, cudaMemcpyHostToDevice, s);
+  if (!e) e = cudaMemsetAsync(rho_dev, 0, sizeof bits, s);
+  if (e) return e;
+  region_box_kernel<<<grid_for(V), 256, 0, s>>>(vox, nx, ny, nz, kRegionDensity, box_dev);
+  if ((e = cudaGetLastError()) || (e = cudaMemcpyAsync(b, box_dev, sizeof b, cudaMemcpyDeviceToHost, s)) ||
+      (e = cudaStreamSynchronize(s)))
+    return e;
+  const int n[3] = {nx, ny, nz};
+  const bool empty = b[3] < b[0];
+  for (int a = 0; a < 3; ++a) {
+    blo[a] = empty ? 0.0f : (float)std::max(b[a] - 1, 0);
+    bhi[a] = empty ? 0.0f : (float)std::min(b[3 + a] + 2, n[a]);
+  }
+  region_rho_out_kernel<<<grid_for(V), 256, 0, s>>>(vox, nx, ny, nz, b[0], b[1], b[2], b[3], b[4], b[5], rho_dev);
+  if ((e = cudaGetLastError()) || (e = cudaMemcpyAsync(bits, rho_dev, sizeof bits, cudaMemcpyDeviceToHost, s)) ||
+      (e = cudaStreamSynchronize(s)))
+    return e;
+  for (int m = 0; m < NM_MAX_MATERIALS; ++m) memcpy(&rho_out[m], &bits[m], 4);
+  return cudaSuccess;
+}
+
+void majorant_table(const MaterialCoef* mat, int n_mat, const float* rho, const float* kn, double e_lo, double dln,
+                    float* minv) {
+  for (int i = 0; i < kKnTable; ++i) {
+    const double ei = std::exp(std::log(e_lo) + i * dln);
+    double maj = 0.0;
+    for (int m = 0; m < n_mat; ++m) {
+      const double mu = (double)mat[m].za * (double)kn[i] + (double)mat[m].zp / (ei * ei * ei) +
+                        (double)mat[m].zr / (ei * ei);
+      maj = std::max(maj, (double)rho[m] * mu);
+    }
+    maj = std::max(maj * (1.0 + 1e-4), 1e-12);
+    minv[i] = std::nextafter((float)(1.0 / maj), 0.0f);
+  }
 }
 
 cudaError_t launch_label_count(const uint8_t* labels, int64_t V, long long* count, cudaStream_t s) {

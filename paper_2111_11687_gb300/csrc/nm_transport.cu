@@ -114,6 +114,42 @@ __device__ __forceinline__ void rotate(float& u, float& v, float& w, float c, fl
   w = nw * n;
 }
 
+// Two-region Woodcock tracking.  Inside the tracking box the majorant is the
+// grid's; outside it only air-like voxels remain and the majorant is far
+// smaller, so a photon leaving the body crosses the surrounding air in one
+// step instead of several.  A flight is cut at the box boundary: by the
+// memorylessness of the exponential, restarting the flight there with the
+// other region's majorant leaves the free-path distribution unchanged.
+//
+// Distance (cm) from (x, y, z) along (u, v, w) to the boundary of the lane's
+// region: from inside, to the box's far side; from outside, to its near side,
+// or +inf when the ray misses the box (a ray that has left the convex box
+// never meets it again).
+__device__ __forceinline__ float region_distance(const PatientGeom& G, bool out, float x, float y, float z,
+                                                 float u, float v, float w) {
+  const float iu = 1.0f / (u * G.inv_dx), iv = 1.0f / (v * G.inv_dy), iw = 1.0f / (w * G.inv_dz);
+  const float ax = (G.blo[0] - x) * iu, bx = (G.bhi[0] - x) * iu;
+  const float ay = (G.blo[1] - y) * iv, by = (G.bhi[1] - y) * iv;
+  const float az = (G.blo[2] - z) * iw, bz = (G.bhi[2] - z) * iw;
+  // fminf/fmaxf drop the NaN of 0 * inf (a ray in a box face, parallel to it)
+  const float tf = fminf(fmaxf(ax, bx), fminf(fmaxf(ay, by), fmaxf(az, bz)));
+  if (!out) return tf;
+  const float tn = fmaxf(fminf(ax, bx), fmaxf(fminf(ay, by), fminf(az, bz)));
+  return tn <= tf && tf > 0.0f ? fmaxf(tn, 0.0f) : __int_as_float(0x7f800000);
+}
+
+__device__ __forceinline__ bool outside_box(const PatientGeom& G, float x, float y, float z) {
+  return !(x >= G.blo[0] && x < G.bhi[0] && y >= G.blo[1] && y < G.bhi[1] && z >= G.blo[2] && z < G.bhi[2]);
+}
+
+// 1 / majorant outside the box at energy e (same bin as energy_factors).
+__device__ __forceinline__ float inv_majorant_out(float e, const float* __restrict__ minv_out, float ln_lo,
+                                                  float inv_dln) {
+  float x = (__logf(e) - ln_lo) * inv_dln;
+  x = fminf(fmaxf(x, 0.0f), (float)(kKnTable - 1) - 0x1p-10f);
+  return minv_out[(int)x];
+}
+
 // Decay site and first-photon direction of history (hlo, hhi).
 struct Site {
   int v;              // decay voxel (-1 in point mode)
@@ -219,6 +255,7 @@ template <bool WARP_AGG, bool RAYLEIGH, bool REGROUP, bool MULTI>
 __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams p) {
   __shared__ float s_kn[kKnTable];
   __shared__ float s_minv[kKnTable];
+  __shared__ float s_minv_out[kKnTable];
   __shared__ MaterialCoef s_mat[NM_MAX_MATERIALS];
   __shared__ Energy s_f0;
   // Per patient, indexed by CounterSlot: the rare events (photo, cutoff,
@@ -231,6 +268,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
   for (int i = threadIdx.x; i < kKnTable; i += blockDim.x) {
     s_kn[i] = p.kn[i];
     s_minv[i] = p.minv[i];
+    s_minv_out[i] = p.minv_out[i];
   }
   if (threadIdx.x < NM_MAX_MATERIALS) s_mat[threadIdx.x] = p.mat[threadIdx.x];
   for (int i = threadIdx.x; i < n_pat * 8; i += blockDim.x) s_cnt[i / 8][i % 8] = 0;
@@ -258,6 +296,8 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
   int cv = 0;                            // voxel of a pending Compton event
   uint32_t hlo = 0, hhi = 0, stream = 0, ctr = 0, spare0 = 0, spare1 = 0;
   bool have_spare = false;
+  bool out = false;                      // outside the tracking box
+  float rem = 0.f;                       // cm to the region boundary along (ux, uy, uz)
   int steps = 0;
   uint32_t n_steps = 0, n_compton = 0, n_esc = 0, flags = 0;
   ull escaped = 0;
@@ -271,6 +311,9 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
       ux = -site[3 * nb]; uy = -site[4 * nb]; uz = -site[5 * nb];
       e = p.e0; qe = p.q_e0; f = s_f0;
       stream = kStreamPhotonB; ctr = 0; have_spare = false; steps = 0;
+      const PatientGeom& GB = MULTI ? s_geom[pi] : p.g;
+      out = outside_box(GB, px, py, pz);
+      rem = region_distance(GB, out, px, py, pz, ux, uy, uz);
     }
     // ---- refill: lanes without a photon take new histories from the pool ----
     const unsigned need = __ballot_sync(kFull, !alive && !done);
@@ -343,6 +386,8 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
           e = p.e0; qe = p.q_e0; f = s_f0;
           stream = kStreamPhotonA; ctr = 0; have_spare = false; steps = 0;
           alive = true;
+          out = outside_box(G, px, py, pz);
+          rem = region_distance(G, out, px, py, pz, ux, uy, uz);
           if (G.source_mode == NM_SOURCE_DECAY) {
             site[0] = st.x; site[nb] = st.y; site[2 * nb] = st.z;
             site[3 * nb] = st.u; site[4 * nb] = st.v_; site[5 * nb] = st.w;
@@ -376,6 +421,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
           pending_c = false;
           compton<RAYLEIGH>(p, s_kn, s_minv, e, qe, f, ux, uy, uz, ctr, stream, hlo, hhi, alive, dq,
                             flags, s_cnt[MULTI ? pi : 0]);
+          rem = region_distance(G, out, px, py, pz, ux, uy, uz);
           has = true;
           dv = cv;
         }
@@ -390,7 +436,11 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
         const uint4 r = draw(ctr, stream, hlo, hhi, p.key0, p.key1);
         r0 = r.x; r1 = r.y; spare0 = r.z; spare1 = r.w; have_spare = true;
       }
-      const float s = -__logf(u01(r0)) * f.inv_mubar;   // cm
+      const float imaj = out ? inv_majorant_out(e, s_minv_out, p.ln_e_lo, p.inv_dln_e) : f.inv_mubar;
+      float s = -__logf(u01(r0)) * imaj;   // cm
+      const bool cross = s >= rem;         // flight cut at the region boundary
+      if (cross) s = rem;
+      rem -= s;
       px = fmaf(s * G.inv_dx, ux, px);
       py = fmaf(s * G.inv_dy, uy, py);
       pz = fmaf(s * G.inv_dz, uz, pz);
@@ -400,12 +450,15 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
         escaped += (ull)qe;
         ++n_esc;
         alive = false;
+      } else if (cross) {
+        out = !out;
+        rem = out ? __int_as_float(0x7f800000) : region_distance(G, false, px, py, pz, ux, uy, uz);
       } else {
         const int v = ((int)pz * G.ny + (int)py) * G.nx + (int)px;
         const uint32_t wv = __ldg(G.vox + v);
         const MaterialCoef c = s_mat[wv & 7u];
         // real event with probability mu(voxel)/mubar; the same uniform picks the type
-        const float scale = __uint_as_float(wv & ~7u) * f.inv_mubar;
+        const float scale = __uint_as_float(wv & ~7u) * imaj;
         const float ic = c.za * f.s_c;
         const float icp = fmaf(c.zp, f.s_pe, ic);
         const float t = u01(r1);
@@ -417,6 +470,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
           } else {
             compton<RAYLEIGH>(p, s_kn, s_minv, e, qe, f, ux, uy, uz, ctr, stream, hlo, hhi, alive,
                               dq, flags, s_cnt[MULTI ? pi : 0]);
+            rem = region_distance(G, out, px, py, pz, ux, uy, uz);
             has = true;
             dv = v;
           }
@@ -434,6 +488,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
             const float cth = fmaf(2.0f, u01(r.x), -1.0f);
             if (2.0f * u01(r.y) <= fmaf(cth, cth, 1.0f) || trial + 1 >= kKahnTrialLimit) {
               rotate(ux, uy, uz, cth, fmaf(kTwoPi, u01(r.z), -3.14159265f));
+              rem = region_distance(G, out, px, py, pz, ux, uy, uz);
               break;
             }
           }
