@@ -253,6 +253,8 @@ def run_gpu(args):
                 "peak_source": "measured" if peaks else "fallback",
                 "kernel": "transport_kernel", "launch_ms": launch_ms,
                 "bytes_per_decay": bytes_per_decay, "per_decay": per_decay}
+    dose_map = torch.empty(SHAPE, dtype=torch.float32, device="cuda")
+    nmdose.nm_dose_get(d.h, dose_map, None, None)
     d.close()
 
     # ---- end to end through the C ABI from pinned host buffers ---------------
@@ -286,7 +288,8 @@ def run_gpu(args):
         e2e = {"value": e2e_val, "unit": METRIC, "h2d_bytes_per_step": int(V * (2 + 4 + 1)),
                "d2h_bytes_per_step": int(V * 8 + 8 * (inputs.N_LABELS + 1)), "steps": args.e2e_steps}
 
-    den = denoiser_perf(torch, nmdose, args.denoiser_steps, peaks) if args.denoiser_steps > 0 else None
+    den = (denoiser_perf(torch, nmdose, args.denoiser_steps, peaks, (dose_map, den_d, act_d))
+           if args.denoiser_steps > 0 else None)
     batched = batched_perf(torch, nmdose, phs, args.batch_decays, 3, 1) if phs else None
 
     cpu = None
@@ -325,9 +328,19 @@ def unet_flops(layers, patch, batch, levels=4):
     return f
 
 
-def denoiser_perf(torch, nm, steps, peaks):
+def infer_box(density, margin=8, align=8):
+    """Voxels of the volume that whole-volume inference runs: the body's
+    bounding box (density >= 0.1) plus the context margin, each side rounded
+    up to the network's alignment."""
+    idx = (density >= 0.1).nonzero()
+    ext = (idx.max(0).values - idx.min(0).values + 1 + 2 * margin).tolist()
+    return [(e + align - 1) // align * align for e in ext]
+
+
+def denoiser_perf(torch, nm, steps, peaks, vol=None):
     """Forward and training-step throughput of the U-Net (64^3 patches, batch 4)
-    on the tensor cores, timed with CUDA events on the launching stream."""
+    on the tensor cores, timed with CUDA events on the launching stream; with
+    vol = (dose, density, activity), also whole-volume inference on it."""
     P, B = 64, 4
     stream = torch.cuda.current_stream()
     net = nm.Denoiser(patch=P, batch=B, levels=4, base_width=16, seed=1, stream=stream)
@@ -351,15 +364,31 @@ def denoiser_perf(torch, nm, steps, peaks):
     torch.cuda.synchronize()
     fwd_ms = e[0].elapsed_time(e[1]) / steps
     trn_ms = e[1].elapsed_time(e[2]) / steps
-    net.close()
     peak = peaks["bf16_tflops"] if peaks else 1900.0
     fwd_tf = fl / (fwd_ms * 1e-3) / 1e12
     trn_tf = 3 * fl / (trn_ms * 1e-3) / 1e12      # forward + input and weight gradients
-    return {"patch": P, "batch": B, "widths": [16, 32, 64, 128], "forward_ms": fwd_ms, "train_step_ms": trn_ms,
-            "forward_gflop": fl / 1e9, "patches_per_s_forward": B / (fwd_ms * 1e-3),
-            "roofline": {"bound": "tensor", "achieved": fwd_tf, "peak": peak, "unit": "TFLOP/s",
-                         "frac": fwd_tf / peak, "train_achieved": trn_tf, "train_frac": trn_tf / peak,
-                         "peak_source": "measured" if peaks else "fallback"}}
+    out = {"patch": P, "batch": B, "widths": [16, 32, 64, 128], "forward_ms": fwd_ms, "train_step_ms": trn_ms,
+           "forward_gflop": fl / 1e9, "patches_per_s_forward": B / (fwd_ms * 1e-3),
+           "roofline": {"bound": "tensor", "achieved": fwd_tf, "peak": peak, "unit": "TFLOP/s",
+                        "frac": fwd_tf / peak, "train_achieved": trn_tf, "train_frac": trn_tf / peak,
+                        "peak_source": "measured" if peaks else "fallback"}}
+    if vol is not None:
+        dose, density, act = vol
+        res = torch.empty_like(dose)
+        net.apply(dose, density, act, res)   # allocates the inference buffers
+        torch.cuda.synchronize()
+        e[0].record(stream)
+        for _ in range(steps):
+            net.apply(dose, density, act, res)
+        e[1].record(stream)
+        torch.cuda.synchronize()
+        ap_ms = e[0].elapsed_time(e[1]) / steps
+        box = infer_box(density)
+        fl_box = unet_flops(net.layers(), P, 1) * (box[0] * box[1] * box[2]) / P ** 3
+        out["apply"] = {"volume": list(dose.shape[::-1]), "network_box_zyx": box, "ms": ap_ms,
+                        "tflops": fl_box / (ap_ms * 1e-3) / 1e12}
+    net.close()
+    return out
 
 
 def _kernel_hash():

@@ -280,6 +280,7 @@ typedef struct {
   float lr, beta1, beta2, eps;  /* Adam (defaults 1e-3, 0.9, 0.999, 1e-8) */
   uint64_t seed;       /* weight initialisation */
   void* stream;        /* cudaStream_t; NULL = legacy default stream */
+  int64_t infer_voxels;  /* voxels of one whole-volume inference pass (default 2^25, >= 4096) */
 } nm_denoise_options;
 
 typedef struct nm_denoiser nm_denoiser;
@@ -324,9 +325,12 @@ nm_status nm_denoise_make_patches(const float* dose, const float* density, const
 nm_status nm_denoise_scales(const float* dose, const float* activity, const float* density, int64_t n,
                             float* dose_scale, float* act_scale, void* stream);
 
-/* Denoises a whole low-count dose-rate map (device FP32 [nz][ny][nx]) with
- * overlapping patches whose cores tile the volume; dose_out in the input's
- * units. */
+/* Denoises a whole low-count dose-rate map (device FP32 [nz][ny][nx]) into
+ * dose_out (device, same units; may equal dose).  The bounding box of the body
+ * (density >= 0.1) plus 8 voxels of context on every side runs through the
+ * network as one volume (in slabs along z, each with its own context, when it
+ * exceeds infer_voxels); voxels outside the body box keep the input value.  Allocates
+ * the forward buffers of that volume once and keeps them with the handle. */
 nm_status nm_denoise_apply(nm_denoiser* h, const float* dose, const float* density, const float* activity,
                            int32_t nx, int32_t ny, int32_t nz, float* dose_out);
 

@@ -33,32 +33,33 @@ typedef __nv_bfloat16 bf16;
 // ---------------------------------------------------------------------------
 // Elementwise and reduction kernels.
 // ---------------------------------------------------------------------------
-__global__ void avgpool_kernel(const bf16* __restrict__ x, int n, int s, int c, bf16* __restrict__ y) {
-  // x [n][s][s][s][c] -> y [n][s/2]^3[c]
-  const int h = s >> 1;
-  const long long total = (long long)n * h * h * h * c;
+// Volumes are [n][d][h][w][c] with d, h, w even; the coarse level is half of each.
+__global__ void avgpool_kernel(const bf16* __restrict__ x, int n, int d, int h, int w, int c,
+                               bf16* __restrict__ y) {
+  const int d2 = d >> 1, h2 = h >> 1, w2 = w >> 1;
+  const long long total = (long long)n * d2 * h2 * w2 * c;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     const int ch = (int)(i % c);
     long long v = i / c;
-    const int xx = (int)(v % h); v /= h;
-    const int yy = (int)(v % h); v /= h;
-    const int zz = (int)(v % h);
-    const int b = (int)(v / h);
+    const int xx = (int)(v % w2); v /= w2;
+    const int yy = (int)(v % h2); v /= h2;
+    const int zz = (int)(v % d2);
+    const int b = (int)(v / d2);
     float sum = 0.0f;
     for (int dz = 0; dz < 2; ++dz)
       for (int dy = 0; dy < 2; ++dy)
         for (int dx = 0; dx < 2; ++dx)
-          sum += __bfloat162float(x[((((long long)b * s + 2 * zz + dz) * s + 2 * yy + dy) * s + 2 * xx + dx) * c + ch]);
+          sum += __bfloat162float(x[((((long long)b * d + 2 * zz + dz) * h + 2 * yy + dy) * w + 2 * xx + dx) * c + ch]);
     y[i] = __float2bfloat16_rn(sum * 0.125f);
   }
 }
 
 // cat[v] = [coarse[parent(v)] (c0 channels) | skip[v] (c1 channels)], 16 bytes at a time.
-__global__ void upsample_concat_kernel(const bf16* __restrict__ coarse, const bf16* __restrict__ skip, int n, int s,
-                                       int c0, int c1, bf16* __restrict__ cat) {
-  const int h = s >> 1, c = c0 + c1, q = c / 8;
-  const long long total = (long long)n * s * s * s * q;
+__global__ void upsample_concat_kernel(const bf16* __restrict__ coarse, const bf16* __restrict__ skip, int n, int d,
+                                       int h, int w, int c0, int c1, bf16* __restrict__ cat) {
+  const int h2 = h >> 1, w2 = w >> 1, c = c0 + c1, q = c / 8;
+  const long long total = (long long)n * d * h * w * q;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(i % q);
@@ -66,11 +67,11 @@ __global__ void upsample_concat_kernel(const bf16* __restrict__ coarse, const bf
     uint4 val;
     if (j * 8 < c0) {
       long long t = v;
-      const int xx = (int)(t % s); t /= s;
-      const int yy = (int)(t % s); t /= s;
-      const int zz = (int)(t % s);
-      const int b = (int)(t / s);
-      const long long pv = (((long long)b * h + (zz >> 1)) * h + (yy >> 1)) * h + (xx >> 1);
+      const int xx = (int)(t % w); t /= w;
+      const int yy = (int)(t % h); t /= h;
+      const int zz = (int)(t % d);
+      const int b = (int)(t / d);
+      const long long pv = (((long long)b * (d >> 1) + (zz >> 1)) * h2 + (yy >> 1)) * w2 + (xx >> 1);
       val = *reinterpret_cast<const uint4*>(coarse + pv * c0 + j * 8);
     } else {
       val = *reinterpret_cast<const uint4*>(skip + v * c1 + (j * 8 - c0));
@@ -88,26 +89,26 @@ __global__ void relu_mask_kernel(bf16* __restrict__ g, const bf16* __restrict__ 
 // Gradient of a decoder input [n][s]^3[c0 + c1] split into the coarse source
 // (summed over its 8 children, times the coarse activation's ReLU mask) and
 // the skip source (copied).
-__global__ void split_concat_grad_kernel(const bf16* __restrict__ dx, int n, int s, int c0, int c1,
+__global__ void split_concat_grad_kernel(const bf16* __restrict__ dx, int n, int d, int h, int w, int c0, int c1,
                                          const bf16* __restrict__ coarse_act, bf16* __restrict__ g_coarse,
                                          bf16* __restrict__ g_skip) {
-  const int h = s >> 1, c = c0 + c1;
-  const long long nc = (long long)n * h * h * h * c0;
-  const long long ns = (long long)n * s * s * s * c1;
+  const int d2 = d >> 1, h2 = h >> 1, w2 = w >> 1, c = c0 + c1;
+  const long long nc = (long long)n * d2 * h2 * w2 * c0;
+  const long long ns = (long long)n * d * h * w * c1;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nc + ns;
        i += (long long)gridDim.x * blockDim.x) {
     if (i < nc) {
       const int ch = (int)(i % c0);
       long long v = i / c0;
-      const int xx = (int)(v % h); v /= h;
-      const int yy = (int)(v % h); v /= h;
-      const int zz = (int)(v % h);
-      const int b = (int)(v / h);
+      const int xx = (int)(v % w2); v /= w2;
+      const int yy = (int)(v % h2); v /= h2;
+      const int zz = (int)(v % d2);
+      const int b = (int)(v / d2);
       float sum = 0.0f;
       for (int dz = 0; dz < 2; ++dz)
         for (int dy = 0; dy < 2; ++dy)
           for (int dx2 = 0; dx2 < 2; ++dx2)
-            sum += __bfloat162float(dx[((((long long)b * s + 2 * zz + dz) * s + 2 * yy + dy) * s + 2 * xx + dx2) * c + ch]);
+            sum += __bfloat162float(dx[((((long long)b * d + 2 * zz + dz) * h + 2 * yy + dy) * w + 2 * xx + dx2) * c + ch]);
       g_coarse[i] = __float2bfloat16_rn(__bfloat162float(coarse_act[i]) > 0.0f ? sum : 0.0f);
     } else {
       const long long j = i - nc;
@@ -120,19 +121,21 @@ __global__ void split_concat_grad_kernel(const bf16* __restrict__ dx, int n, int
 
 // Encoder output gradient: (pool adjoint of the coarser gradient + skip gradient) * ReLU mask.
 __global__ void encoder_grad_kernel(const bf16* __restrict__ g_coarse, const bf16* __restrict__ g_skip,
-                                    const bf16* __restrict__ act, int n, int s, int c, bf16* __restrict__ g) {
-  const int h = s >> 1;
-  const long long total = (long long)n * s * s * s * c;
+                                    const bf16* __restrict__ act, int n, int d, int h, int w, int c,
+                                    bf16* __restrict__ g) {
+  const int h2 = h >> 1, w2 = w >> 1;
+  const long long total = (long long)n * d * h * w * c;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     const int ch = (int)(i % c);
     long long v = i / c;
-    const int xx = (int)(v % s); v /= s;
-    const int yy = (int)(v % s); v /= s;
-    const int zz = (int)(v % s);
-    const int b = (int)(v / s);
+    const int xx = (int)(v % w); v /= w;
+    const int yy = (int)(v % h); v /= h;
+    const int zz = (int)(v % d);
+    const int b = (int)(v / d);
     float t = __bfloat162float(g_skip[i]);
-    t += 0.125f * __bfloat162float(g_coarse[((((long long)b * h + (zz >> 1)) * h + (yy >> 1)) * h + (xx >> 1)) * c + ch]);
+    t += 0.125f * __bfloat162float(
+                      g_coarse[((((long long)b * (d >> 1) + (zz >> 1)) * h2 + (yy >> 1)) * w2 + (xx >> 1)) * c + ch]);
     g[i] = __float2bfloat16_rn(__bfloat162float(act[i]) > 0.0f ? t : 0.0f);
   }
 }
@@ -214,25 +217,26 @@ __global__ void to_bf16_kernel(const float* __restrict__ a, long long n, bf16* _
     b[i] = __float2bfloat16_rn(a[i]);
 }
 
-// Network input channels from whole volumes, for patches at the given corners:
-// out [np][P][P][P][8] BF16 = (dose/s, density, act/a, act/(a max(density, 0.1)), 0...);
-// target [np][P]^3 = dose_high/s (if dose_high), weight = (density >= 0.1).
+// Network input channels from whole volumes, for boxes of px x py x pz voxels
+// at the given corners: out [np][pz][py][px][8] BF16 = (dose/s, density, act/a,
+// act/(a max(density, 0.1)), 0...); target [np][pz][py][px] = dose_high/s (if
+// dose_high), weight = (density >= 0.1).  Voxels outside the volume read as 0.
 // Linear units keep the squared-error optimum at the conditional mean, so the
 // network does not bias organ means.
 __global__ void make_patches_kernel(const float* __restrict__ dose, const float* __restrict__ density,
                                     const float* __restrict__ act, const float* __restrict__ dose_high,
                                     int nx, int ny, int nz, float inv_s, float inv_a,
-                                    const int* __restrict__ corners, int np, int P,
+                                    const int* __restrict__ corners, int np, int px, int py, int pz,
                                     bf16* __restrict__ out, float* __restrict__ target,
                                     float* __restrict__ weight) {
-  const long long per = (long long)P * P * P;
+  const long long per = (long long)px * py * pz;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < per * np;
        i += (long long)gridDim.x * blockDim.x) {
     const int p = (int)(i / per);
     long long r = i % per;
-    const int x = (int)(r % P); r /= P;
-    const int y = (int)(r % P);
-    const int z = (int)(r / P);
+    const int x = (int)(r % px); r /= px;
+    const int y = (int)(r % py);
+    const int z = (int)(r / py);
     const int gx = corners[3 * p] + x, gy = corners[3 * p + 1] + y, gz = corners[3 * p + 2] + z;
     float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f, c3 = 0.0f, t = 0.0f, wv = 0.0f;
     if (gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz) {
@@ -245,37 +249,56 @@ __global__ void make_patches_kernel(const float* __restrict__ dose, const float*
       if (dose_high) t = fmaxf(dose_high[v], 0.0f) * inv_s;
       wv = rho >= 0.1f ? 1.0f : 0.0f;
     }
-    bf16* o = out + i * 8;
+    __align__(16) bf16 o[8];
     o[0] = __float2bfloat16_rn(c0);
     o[1] = __float2bfloat16_rn(c1);
     o[2] = __float2bfloat16_rn(c2);
     o[3] = __float2bfloat16_rn(c3);
     for (int k = 4; k < 8; ++k) o[k] = __float2bfloat16_rn(0.0f);
+    *reinterpret_cast<uint4*>(out + i * 8) = *reinterpret_cast<const uint4*>(o);
     if (target) target[i] = t;
     if (weight) weight[i] = wv;
   }
 }
 
-// Writes the central region of predicted patches back into the volume:
-// dose_out = s * y for voxels of the patch's core box.
-__global__ void scatter_patches_kernel(const float* __restrict__ y, const int* __restrict__ corners,
-                                       const int* __restrict__ lo, const int* __restrict__ hi, int np, int P,
-                                       int nx, int ny, int nz, float s, float* __restrict__ dose_out) {
-  const long long per = (long long)P * P * P;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < per * np;
+// Writes the core [lo, hi) (box coordinates) of one predicted box of
+// px x py x pz voxels at `corner` back into the volume: dose_out = s * y.
+__global__ void scatter_box_kernel(const float* __restrict__ y, int cx, int cy, int cz, int px, int py, int pz,
+                                   int lox, int loy, int loz, int hix, int hiy, int hiz, int nx, int ny, int nz,
+                                   float s, float* __restrict__ dose_out) {
+  const long long per = (long long)px * py * pz;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < per;
        i += (long long)gridDim.x * blockDim.x) {
-    const int p = (int)(i / per);
-    long long r = i % per;
-    const int x = (int)(r % P); r /= P;
-    const int yy = (int)(r % P);
-    const int z = (int)(r / P);
-    if (x < lo[3 * p] || x >= hi[3 * p] || yy < lo[3 * p + 1] || yy >= hi[3 * p + 1] || z < lo[3 * p + 2] ||
-        z >= hi[3 * p + 2])
-      continue;
-    const int gx = corners[3 * p] + x, gy = corners[3 * p + 1] + yy, gz = corners[3 * p + 2] + z;
+    long long r = i;
+    const int x = (int)(r % px); r /= px;
+    const int yy = (int)(r % py);
+    const int z = (int)(r / py);
+    if (x < lox || x >= hix || yy < loy || yy >= hiy || z < loz || z >= hiz) continue;
+    const int gx = cx + x, gy = cy + yy, gz = cz + z;
     if (gx < 0 || gx >= nx || gy < 0 || gy >= ny || gz < 0 || gz >= nz) continue;
     dose_out[((long long)gz * ny + gy) * nx + gx] = s * y[i];
   }
+}
+
+// Bounding box [xmin, ymin, zmin, xmax, ymax, zmax] of the body (density >= 0.1).
+__global__ void body_box_kernel(const float* __restrict__ density, int nx, int ny, int nz, int* box) {
+  int lo[3] = {nx, ny, nz}, hi[3] = {-1, -1, -1};
+  const long long V = (long long)nx * ny * nz;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x)
+    if (density[i] >= 0.1f) {
+      const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long long)nx * ny));
+      lo[0] = min(lo[0], x); lo[1] = min(lo[1], y); lo[2] = min(lo[2], z);
+      hi[0] = max(hi[0], x); hi[1] = max(hi[1], y); hi[2] = max(hi[2], z);
+    }
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = __reduce_min_sync(0xffffffffu, lo[a]);
+    hi[a] = __reduce_max_sync(0xffffffffu, hi[a]);
+  }
+  if ((threadIdx.x & 31) == 0)
+    for (int a = 0; a < 3; ++a) {
+      atomicMin(box + a, lo[a]);
+      atomicMax(box + 3 + a, hi[a]);
+    }
 }
 
 // Masked mean of a volume: partial sums per CTA (fixed tree), then one CTA.
@@ -295,11 +318,15 @@ __global__ void masked_mean_partial(const float* __restrict__ a, const float* __
   if (threadIdx.x == 0) { part[2 * blockIdx.x] = sv[0]; part[2 * blockIdx.x + 1] = sc[0]; }
 }
 
+// Default voxel budget of one inference pass: about 330 bytes of activations
+// per voxel over all levels, so about 11 GB.
+constexpr long long kInferVoxels = 1ll << 25;
+
 int grid1d(long long n) { return (int)std::min<long long>((n + 255) / 256, 8192); }
 
 struct Layer {
   std::string name;
-  int cin, c0, c1, coarse, cout, kpad, size, level;
+  int cin, c0, c1, coarse, cout, kpad, level;
   long long w_off, b_off;  // offsets into the flat parameter vector (floats)
 };
 
@@ -309,6 +336,11 @@ struct nm_denoiser {
   nm_denoise_options opt{};
   cudaStream_t s = nullptr;
   int P = 64, B = 1, L = 4, base = 16, cx = 8;
+  int PD = 64, PH = 64, PW = 64;   // volume of one batch item (P^3 for training)
+  // Inference instance for whole-volume apply: forward buffers of its own
+  // size, parameters and status shared with (owned by) this handle.
+  nm_denoiser* inf = nullptr;
+  bool owns_params = true;
   std::vector<int> widths;
   std::vector<Layer> layers;
   long long n_params = 0;
@@ -341,7 +373,11 @@ struct nm_denoiser {
 
   ~nm_denoiser() {
     auto f = [](void* p) { if (p) cudaFree(p); };
-    f(w); f(g); f(m1); f(m2); f(wb); f(wflip);
+    delete inf;
+    if (owns_params) {
+      f(w); f(g); f(m1); f(m2); f(wb); f(status);
+    }
+    f(wflip);
     for (auto p : ea) f(p);
     for (auto p : eb) f(p);
     for (auto p : pool) f(p);
@@ -350,16 +386,13 @@ struct nm_denoiser {
     for (auto p : gskip) f(p);
     for (auto p : cat) f(p);
     f(gA); f(gB); f(gC); f(gD); f(x_in); f(y); f(target); f(weight); f(dtop); f(head_part); f(head_sum);
-    f(ws); f(status);
+    f(ws);
   }
 
-  long long vox(int level) const {
-    const long long s = P >> level;
-    return (long long)B * s * s * s;
-  }
+  long long vox(int level) const { return (long long)B * (PD >> level) * (PH >> level) * (PW >> level); }
   nm_conv3d_desc desc(const Layer& l) const {
     nm_conv3d_desc d;
-    d.n = B; d.d = d.h = d.w = l.size;
+    d.n = B; d.d = PD >> l.level; d.h = PH >> l.level; d.w = PW >> l.level;
     d.c0 = l.c0; d.c1 = l.c1; d.src0_coarse = l.coarse; d.cout = l.cout;
     return d;
   }
@@ -432,7 +465,8 @@ nm_status forward(nm_denoiser* h) {
     CK(conv3d_fwd(h->desc(lb), h->ea[i], nullptr, h->wb + lb.w_off, h->w + lb.b_off, h->eb[i], 1, h->status, s), "conv");
     if (i < L - 1) {
       const long long n = h->vox(i + 1) * h->widths[i];
-      avgpool_kernel<<<grid1d(n), 256, 0, s>>>(h->eb[i], h->B, h->P >> i, h->widths[i], h->pool[i]);
+      avgpool_kernel<<<grid1d(n), 256, 0, s>>>(h->eb[i], h->B, h->PD >> i, h->PH >> i, h->PW >> i, h->widths[i],
+                                               h->pool[i]);
       in = h->pool[i];
     }
   }
@@ -442,7 +476,8 @@ nm_status forward(nm_denoiser* h) {
     const Layer& lb = h->layers[li++];
     if (use_cat(h, la)) {
       const long long n = h->vox(i) * (la.cin / 8);
-      upsample_concat_kernel<<<grid1d(n), 256, 0, s>>>(coarse, h->eb[i], h->B, h->P >> i, la.c0, la.c1, h->cat[i]);
+      upsample_concat_kernel<<<grid1d(n), 256, 0, s>>>(coarse, h->eb[i], h->B, h->PD >> i, h->PH >> i, h->PW >> i,
+                                                       la.c0, la.c1, h->cat[i]);
       CK(conv3d_fwd(single_source(h, la), h->cat[i], nullptr, h->wb + la.w_off, h->w + la.b_off, h->da[i], 1,
                     h->status, s), "conv");
     } else {
@@ -473,6 +508,44 @@ nm_status head(nm_denoiser* h, bool train) {
   return NM_OK;
 }
 
+// Forward-only instance of h for one D x H x W volume (multiples of 2^(L-1)),
+// sharing h's parameters; kept in h->inf and reused while it is large enough.
+nm_status inference_instance(nm_denoiser* h, int D, int H, int W, nm_denoiser** out) {
+  const long long need = (long long)D * H * W;
+  nm_denoiser* c = h->inf;
+  if (!c || (long long)c->PD * c->PH * c->PW < need) {
+    delete h->inf;
+    h->inf = nullptr;
+    c = new nm_denoiser();
+    c->owns_params = false;
+    c->opt = h->opt; c->s = h->s; c->P = 0; c->B = 1; c->L = h->L; c->base = h->base; c->cx = h->cx;
+    c->widths = h->widths; c->layers = h->layers; c->n_params = h->n_params; c->head_off = h->head_off;
+    c->w = h->w; c->wb = h->wb; c->status = h->status;
+    c->PD = D; c->PH = H; c->PW = W;
+    h->inf = c;
+    const int L = c->L;
+    c->ea.assign(L, nullptr); c->eb.assign(L, nullptr); c->pool.assign(L, nullptr);
+    c->da.assign(L, nullptr); c->db.assign(L, nullptr); c->cat.assign(L, nullptr);
+    cudaError_t e;
+    for (int i = 0; i < L; ++i) {
+      const long long n = c->vox(i) * c->widths[i];
+      if ((e = dmalloc(&c->ea[i], n)) || (e = dmalloc(&c->eb[i], n))) return cfail(e, "inference activations");
+      if (i < L - 1) {
+        if ((e = dmalloc(&c->pool[i], c->vox(i + 1) * c->widths[i])) || (e = dmalloc(&c->da[i], n)) ||
+            (e = dmalloc(&c->db[i], n)) || (e = dmalloc(&c->cat[i], c->vox(i) * (c->widths[i] + c->widths[i + 1]))))
+          return cfail(e, "inference activations");
+      }
+    }
+    if ((e = dmalloc(&c->x_in, c->vox(0) * c->cx)) || (e = dmalloc(&c->y, c->vox(0))))
+      return cfail(e, "inference activations");
+  }
+  // every buffer scales with D H W / 8^level, so a larger allocation serves
+  c->PD = D; c->PH = H; c->PW = W;
+  c->head_blocks = (int)((c->vox(0) + 127) / 128);
+  *out = c;
+  return NM_OK;
+}
+
 nm_status backward(nm_denoiser* h) {
   cudaStream_t s = h->s;
   const int L = h->L;
@@ -489,7 +562,7 @@ nm_status backward(nm_denoiser* h) {
     CK(conv3d_flip_weights(fd, h->wb + l.w_off, h->wflip, s), "flip");
     nm_conv3d_desc bd;
     memset(&bd, 0, sizeof bd);
-    bd.n = fd.n; bd.d = bd.h = bd.w = l.size;
+    bd.n = fd.n; bd.d = fd.d; bd.h = fd.h; bd.w = fd.w;
     bd.c0 = l.cout; bd.cout = l.c0 + l.c1;
     CK(conv3d_fwd(bd, gout, nullptr, h->wflip, nullptr, gin, 0, h->status, s), "dgrad");
     return NM_OK;
@@ -502,7 +575,7 @@ nm_status backward(nm_denoiser* h) {
       CK(conv3d_flip_weights(fd, h->wb + l.w_off, h->wflip, s), "flip");
       nm_conv3d_desc bd;
       memset(&bd, 0, sizeof bd);
-      bd.n = fd.n; bd.d = bd.h = bd.w = l.size;
+      bd.n = fd.n; bd.d = fd.d; bd.h = fd.h; bd.w = fd.w;
       bd.c0 = l.cout; bd.cout = l.c0 + l.c1;
       CK(conv3d_fwd(bd, gout, nullptr, h->wflip, nullptr, gin, 0, h->status, s), "dgrad");
     }
@@ -528,7 +601,8 @@ nm_status backward(nm_denoiser* h) {
       return st;
     }
     const long long total = h->vox(i + 1) * h->widths[i + 1] + nb;
-    split_concat_grad_kernel<<<grid1d(total), 256, 0, s>>>(h->gB, h->B, h->P >> i, h->widths[i + 1], h->widths[i],
+    split_concat_grad_kernel<<<grid1d(total), 256, 0, s>>>(h->gB, h->B, h->PD >> i, h->PH >> i, h->PW >> i,
+                                                           h->widths[i + 1], h->widths[i],
                                                            coarse, h->gC, h->gskip[i]);
     // gC now holds the (masked) gradient wrt the coarser output; move it to gD
     std::swap(h->gC, h->gD);
@@ -540,7 +614,8 @@ nm_status backward(nm_denoiser* h) {
     const Layer& la = lay("e" + std::to_string(i) + "a");
     const long long nb = h->vox(i) * h->widths[i];
     if (i < L - 1) {
-      encoder_grad_kernel<<<grid1d(nb), 256, 0, s>>>(g, h->gskip[i], h->eb[i], h->B, h->P >> i, h->widths[i], h->gC);
+      encoder_grad_kernel<<<grid1d(nb), 256, 0, s>>>(g, h->gskip[i], h->eb[i], h->B, h->PD >> i, h->PH >> i,
+                                                     h->PW >> i, h->widths[i], h->gC);
       g = h->gC;
     }
     if ((st = conv_back(lb, h->ea[i], nullptr, g, h->gA)) != NM_OK) return st;
@@ -572,6 +647,7 @@ void nm_denoise_options_default(nm_denoise_options* o) {
   o->beta2 = 0.999f;
   o->eps = 1e-8f;
   o->seed = 1;
+  o->infer_voxels = kInferVoxels;
 }
 
 nm_status nm_denoise_create(nm_denoiser** out, const nm_denoise_options* opts) {
@@ -582,11 +658,14 @@ nm_status nm_denoise_create(nm_denoiser** out, const nm_denoise_options* opts) {
   if (o.levels < 2 || o.levels > 4 || o.patch % (1 << (o.levels - 1)) || o.patch < 8 || o.batch < 1 ||
       !(o.base_width == 16 || o.base_width == 32) || (o.base_width << (o.levels - 1)) > 128)
     return fail(NM_ERR_ARG, "denoiser: levels 2..4, patch a multiple of 2^(levels-1), base width 16 or 32, widths <= 128");
+  if (o.infer_voxels == 0) o.infer_voxels = kInferVoxels;
+  if (o.infer_voxels < 4096) return fail(NM_ERR_ARG, "denoiser: infer_voxels must be >= 4096");
   nm_denoiser* h = new nm_denoiser();
   auto bail = [&](nm_status st) { delete h; return st; };
   h->opt = o;
   h->s = (cudaStream_t)o.stream;
   h->P = o.patch; h->B = o.batch; h->L = o.levels; h->base = o.base_width;
+  h->PD = h->PH = h->PW = o.patch;
   for (int i = 0; i < h->L; ++i) h->widths.push_back(h->base << i);
   // layers in forward order
   long long off = 0;
@@ -594,7 +673,7 @@ nm_status nm_denoise_create(nm_denoiser** out, const nm_denoise_options* opts) {
   auto add = [&](const std::string& n, int c0, int c1, int coarse, int cout, int level) {
     Layer l;
     l.name = n; l.c0 = c0; l.c1 = c1; l.cin = c0 + c1; l.coarse = coarse; l.cout = cout;
-    l.kpad = conv_kpad(l.cin); l.size = h->P >> level; l.level = level;
+    l.kpad = conv_kpad(l.cin); l.level = level;
     l.w_off = off; off += (long long)cout * l.kpad;
     l.b_off = off; off += cout;
     off = (off + 7) / 8 * 8;  // 16-byte aligned BF16 weights
@@ -769,7 +848,8 @@ nm_status nm_denoise_make_patches(const float* dose, const float* density, const
   cudaStream_t s = (cudaStream_t)stream;
   const long long n = (long long)patch * patch * patch * n_patches;
   make_patches_kernel<<<grid1d(n), 256, 0, s>>>(dose, density, activity, dose_high, nx, ny, nz, 1.0f / dose_scale,
-                                                1.0f / act_scale, corners, n_patches, patch, (bf16*)x, target, weight);
+                                                1.0f / act_scale, corners, n_patches, patch, patch, patch, (bf16*)x,
+                                                target, weight);
   CK(cudaGetLastError(), "make_patches");
   CK(cudaStreamSynchronize(s), "make_patches");
   return NM_OK;
@@ -800,8 +880,11 @@ nm_status nm_denoise_scales(const float* dose, const float* activity, const floa
   return NM_OK;
 }
 
-// Whole-volume inference with overlapping patches: each patch keeps its core
-// (a margin of patch/8 voxels is dropped on interior faces).
+// Whole-volume inference.  The body's bounding box (density >= 0.1) plus a
+// context margin of 8 voxels runs through the network as one volume; above the
+// handle's infer_voxels it runs in slabs along z, each with the margin on both
+// sides and only its core written back.  Voxels outside the body box keep the
+// input.
 nm_status nm_denoise_apply(nm_denoiser* h, const float* dose, const float* density, const float* activity,
                            int32_t nx, int32_t ny, int32_t nz, float* dose_out) {
   if (!h || !dose || !density || !activity || !dose_out || nx <= 0 || ny <= 0 || nz <= 0)
@@ -809,42 +892,51 @@ nm_status nm_denoise_apply(nm_denoiser* h, const float* dose, const float* densi
   if (!dev_ptr(dose) || !dev_ptr(density) || !dev_ptr(activity) || !dev_ptr(dose_out))
     return fail(NM_ERR_ARG, "volumes must be device pointers");
   cudaStream_t s = h->s;
-  const int P = h->P, mg = P / 8, core = P - 2 * mg;
+  const long long V = (long long)nx * ny * nz;
   float ds = 1, as = 1;
-  nm_status st = nm_denoise_scales(dose, activity, density, (int64_t)nx * ny * nz, &ds, &as, s);
+  nm_status st = nm_denoise_scales(dose, activity, density, V, &ds, &as, s);
   if (st != NM_OK) return st;
-  // patch corners: cores tile the volume
-  std::vector<int> corners, lo, hi;
-  auto starts = [&](int n) {
-    std::vector<int> v;
-    for (int c = 0; c < n; c += core) v.push_back(c - mg);
-    return v;
-  };
-  for (int z : starts(nz))
-    for (int y : starts(ny))
-      for (int x : starts(nx)) {
-        corners.insert(corners.end(), {x, y, z});
-        lo.insert(lo.end(), {mg, mg, mg});
-        hi.insert(hi.end(), {mg + core, mg + core, mg + core});
-      }
-  const int np = (int)(corners.size() / 3);
+  int* dbox = nullptr;
+  int box[6] = {nx, ny, nz, -1, -1, -1};
+  CK(cudaMallocAsync((void**)&dbox, sizeof box, s), "apply");
+  CK(cudaMemcpyAsync(dbox, box, sizeof box, cudaMemcpyHostToDevice, s), "apply");
+  body_box_kernel<<<grid1d(V), 256, 0, s>>>(density, nx, ny, nz, dbox);
+  CK(cudaMemcpyAsync(box, dbox, sizeof box, cudaMemcpyDeviceToHost, s), "apply");
+  cudaFreeAsync(dbox, s);
+  if (dose_out != dose) CK(cudaMemcpyAsync(dose_out, dose, V * sizeof(float), cudaMemcpyDeviceToDevice, s), "apply");
+  CK(cudaStreamSynchronize(s), "apply");
+  if (box[3] < box[0]) return NM_OK;  // no body: nothing to denoise
+  const int A = 1 << (h->L - 1), mg = 8;
+  auto up = [&](int n) { return (n + A - 1) / A * A; };
+  const int ex = box[3] + 1 - box[0], ey = box[4] + 1 - box[1], ez = box[5] + 1 - box[2];
+  const int W = up(ex + 2 * mg), H = up(ey + 2 * mg);
+  // z slabs: core depth tc, network depth D = up(tc + 2 mg) <= the voxel budget
+  const long long plane = (long long)W * H;
+  int tc = ez;
+  const long long budget = h->opt.infer_voxels;
+  if (plane * up(ez + 2 * mg) > budget) {
+    const int dmax = (int)std::min<long long>(budget / plane, 1 << 30) / A * A;
+    if (dmax < 2 * mg + A) return fail(NM_ERR_ARG, "volume cross-section too large for whole-volume inference");
+    tc = dmax - 2 * mg;
+  }
+  const int D = up(tc + 2 * mg);
+  nm_denoiser* c = nullptr;
+  if ((st = inference_instance(h, D, H, W, &c)) != NM_OK) return st;
   int* dcorn = nullptr;
-  CK(cudaMallocAsync((void**)&dcorn, corners.size() * 3 * sizeof(int), s), "apply");
-  CK(cudaMemcpyAsync(dcorn, corners.data(), corners.size() * sizeof(int), cudaMemcpyHostToDevice, s), "apply");
-  CK(cudaMemcpyAsync(dcorn + corners.size(), lo.data(), lo.size() * sizeof(int), cudaMemcpyHostToDevice, s), "apply");
-  CK(cudaMemcpyAsync(dcorn + 2 * corners.size(), hi.data(), hi.size() * sizeof(int), cudaMemcpyHostToDevice, s), "apply");
-  const long long per = (long long)P * P * P;
-  for (int p0 = 0; p0 < np && st == NM_OK; p0 += h->B) {
-    const int cnt = std::min(h->B, np - p0);
-    const long long n = per * cnt;
+  CK(cudaMallocAsync((void**)&dcorn, 3 * sizeof(int), s), "apply");
+  for (int z0 = box[2]; z0 <= box[5] && st == NM_OK; z0 += tc) {
+    const int core = std::min(tc, box[5] + 1 - z0);
+    const int corner[3] = {box[0] - mg, box[1] - mg, z0 - mg};
+    CK(cudaMemcpyAsync(dcorn, corner, sizeof corner, cudaMemcpyHostToDevice, s), "apply");
+    const long long n = (long long)W * H * D;
     make_patches_kernel<<<grid1d(n), 256, 0, s>>>(dose, density, activity, nullptr, nx, ny, nz, 1.0f / ds, 1.0f / as,
-                                                  dcorn + 3 * p0, cnt, P, h->x_in, nullptr, nullptr);
-    if (cnt < h->B) cudaMemsetAsync(h->x_in + n * h->cx, 0, (per * h->B - n) * h->cx * 2, s);
-    if ((st = forward(h)) != NM_OK) break;
-    if ((st = head(h, false)) != NM_OK) break;
-    scatter_patches_kernel<<<grid1d(n), 256, 0, s>>>(h->y, dcorn + 3 * p0, dcorn + corners.size() + 3 * p0,
-                                                     dcorn + 2 * corners.size() + 3 * p0, cnt, P, nx, ny, nz, ds,
-                                                     dose_out);
+                                                  dcorn, 1, W, H, D, c->x_in, nullptr, nullptr);
+    if ((st = forward(c)) != NM_OK) break;
+    if ((st = head(c, false)) != NM_OK) break;
+    scatter_box_kernel<<<grid1d(n), 256, 0, s>>>(c->y, corner[0], corner[1], corner[2], W, H, D, mg, mg, mg,
+                                                 mg + ex, mg + ey, mg + core, nx, ny, nz, ds, dose_out);
+    // the corner buffer is reused by the next slab
+    CK(cudaStreamSynchronize(s), "apply");
   }
   cudaFreeAsync(dcorn, s);
   if (st != NM_OK) return st;

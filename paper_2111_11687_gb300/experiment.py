@@ -1,7 +1,8 @@
 """Denoiser experiment: train the U-Net on pairs the engine generates on
 synthetic phantoms, then compare, on held-out phantoms, the wall time plain
 Monte Carlo needs to bring every organ dose within 2 % of a high-count
-reference with the time of low-count Monte Carlo plus the denoiser.
+reference with the time Monte Carlo plus the denoiser needs (checkpoints of
+low-count decays, each denoised whole-volume).
 
 Everything numerical runs through the C ABI (nm_dose_* for the transport,
 nm_denoise_* for the network); this module only orchestrates: phantom
@@ -138,6 +139,38 @@ def time_to_target(case, ref, step_decays, max_decays, target, seed):
         return None, n, float(err.max())
 
 
+def time_to_target_denoised(case, net, ref, counts, step_decays, max_decays, target, seed):
+    """MC + denoiser: wall time and decays until the denoised map puts every
+    organ within target of ref.  Each checkpoint adds step_decays decays to the
+    same run, denoises the whole accumulated map and checks it, so a case the
+    network cannot bring within target at the first checkpoint falls back to
+    more Monte Carlo.  Also returns the errors at the first checkpoint."""
+    torch, nm = case.torch, case.nm
+    raw = torch.empty(case.shape, dtype=torch.float32, device="cuda")
+    den = torch.empty_like(raw)
+    first = None
+    with case.handle(batches=2) as d:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n = 0
+        while n < max_decays:
+            d.run(step_decays, seed)
+            n += step_decays
+            nm.nm_dose_get(d.h, raw, None, None)
+            net.apply(raw, case.density, case.activity, den)
+            err = organ_error(d.map_organs(den), ref, counts)
+            if first is None:
+                # the undenoised error is for the record only: its time is not counted
+                ta = time.perf_counter()
+                first = (err, organ_error(d.map_organs(raw), ref, counts), ta - t0)
+                t0 += time.perf_counter() - ta
+            if err.max() <= target:
+                torch.cuda.synchronize()
+                return time.perf_counter() - t0, n, float(err.max()), first
+        torch.cuda.synchronize()
+        return None, n, float(err.max()), first
+
+
 def run(train_n=200, test_n=20, shape=(300, 256, 256), spacing=(0.2, 0.2, 0.3), low=int(1e7), high=int(1e9),
         ref=int(1e10), denoise_low=int(1e7), steps=3000, patch=64, batch=4, lr=1e-3, workers=None,
         step_decays=int(5e6), max_decays=int(2e9), seed0=1000, log_every=0):
@@ -171,34 +204,28 @@ def run(train_n=200, test_n=20, shape=(300, 256, 256), spacing=(0.2, 0.2, 0.3), 
         refmap, _ = c.dose(ref, 100 + j)
         with c.handle() as h:
             ref_org = h.map_organs(refmap)
+        cnts = np.bincount(c.labels.flatten().cpu().numpy(), minlength=inputs.N_LABELS + 1)
         # plain MC
         t_mc, n_mc, e_mc = time_to_target(c, ref_org, step_decays, max_decays, 0.02, 200 + j)
-        # MC at the low count + denoiser
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        lowmap, _ = c.dose(denoise_low, 300 + j)
-        den = torch.empty_like(lowmap)
-        net.apply(lowmap, c.density, c.activity, den)
-        torch.cuda.synchronize()
-        t_dn = time.perf_counter() - t0
-        with c.handle() as h:
-            m_dn = h.map_organs(den)
-            m_lo = h.map_organs(lowmap)
-        cnts = np.bincount(c.labels.flatten().cpu().numpy(), minlength=inputs.N_LABELS + 1)
-        e_dn = organ_error(m_dn, ref_org, cnts)
-        e_lo = organ_error(m_lo, ref_org, cnts)
+        # MC + denoiser, checkpoints of denoise_low decays
+        t_dn, n_dn, e_dn, (e1_dn, e1_lo, t1) = time_to_target_denoised(c, net, ref_org, cnts, denoise_low,
+                                                                       max_decays, 0.02, 300 + j)
         results.append(dict(case=j, plain_mc_s=t_mc, plain_mc_decays=n_mc, plain_mc_err=e_mc,
-                            mc_denoiser_s=t_dn, denoiser_max_err=float(e_dn.max()),
-                            denoiser_mean_err=float(e_dn.mean()), low_mc_max_err=float(e_lo.max()),
-                            low_mc_mean_err=float(e_lo.mean())))
+                            mc_denoiser_s=t_dn, mc_denoiser_decays=n_dn, mc_denoiser_err=e_dn,
+                            first_checkpoint_s=t1, denoiser_max_err=float(e1_dn.max()),
+                            denoiser_mean_err=float(e1_dn.mean()), low_mc_max_err=float(e1_lo.max()),
+                            low_mc_mean_err=float(e1_lo.mean())))
     net.close()
     ok_dn = [r for r in results if r["denoiser_max_err"] <= 0.02]
+    med = lambda k: float(np.median([r[k] for r in results if r[k] is not None] or [np.nan]))
     summary = dict(train=train_n, test=test_n, grid=list(shape[::-1]), low=low, high=high, ref=ref,
                    denoise_low=denoise_low, steps=steps, patch=patch, batch=batch, data_s=t_data,
                    train_s=t_train, final_loss=float(np.mean(losses[-50:])), first_loss=float(np.mean(losses[:10])),
-                   plain_mc_s_median=float(np.median([r["plain_mc_s"] for r in results if r["plain_mc_s"]] or [np.nan])),
-                   mc_denoiser_s_median=float(np.median([r["mc_denoiser_s"] for r in results])),
-                   denoiser_reaches_2pct=len(ok_dn), denoiser_max_err_median=float(np.median([r["denoiser_max_err"] for r in results])),
+                   plain_mc_s_median=med("plain_mc_s"), mc_denoiser_s_median=med("mc_denoiser_s"),
+                   plain_mc_decays_median=med("plain_mc_decays"), mc_denoiser_decays_median=med("mc_denoiser_decays"),
+                   denoiser_faster=sum(1 for r in results if r["mc_denoiser_s"] is not None and
+                                       (r["plain_mc_s"] is None or r["mc_denoiser_s"] < r["plain_mc_s"])),
+                   denoiser_reaches_2pct_first_checkpoint=len(ok_dn), denoiser_max_err_median=float(np.median([r["denoiser_max_err"] for r in results])),
                    low_mc_max_err_median=float(np.median([r["low_mc_max_err"] for r in results])),
                    cases=results)
     return summary

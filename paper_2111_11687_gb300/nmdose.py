@@ -73,7 +73,7 @@ class nm_conv3d_desc(C.Structure):
 class nm_denoise_options(C.Structure):
     _fields_ = [("patch", C.c_int32), ("batch", C.c_int32), ("levels", C.c_int32), ("base_width", C.c_int32),
                 ("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
-                ("seed", C.c_uint64), ("stream", C.c_void_p)]
+                ("seed", C.c_uint64), ("stream", C.c_void_p), ("infer_voxels", C.c_int64)]
 
 
 # Every entry point declared in include/nm_dose.h, with its ctypes signature.

@@ -135,3 +135,92 @@ def test_apply_covers_the_volume(env):
     assert np.all(o > 0)
     assert np.allclose(o, dose, rtol=1e-2)
     net.close()
+
+
+def _random_net(torch, nm, seed, **kw):
+    """A network with BF16-exact weights, random biases and a non-zero head."""
+    net = nm.Denoiser(patch=16, batch=1, levels=4, base_width=16, seed=seed, **kw)
+    layers = net.layers()
+    rng = np.random.default_rng(seed)
+    flat = np.zeros(net.n_params, np.float32)
+    net.params(get=flat)
+    for l in layers[:-1]:
+        flat[l["b_off"]:l["b_off"] + l["cout"]] = rng.normal(0, 0.05, l["cout"])
+        w = flat[l["w_off"]:l["w_off"] + l["cout"] * l["kpad"]].reshape(l["cout"], l["kpad"])
+        w[:, :27 * l["cin"]] = bf16_round(torch, w[:, :27 * l["cin"]])
+    h = layers[-1]
+    flat[h["w_off"]:h["w_off"] + 16] = rng.normal(0, 0.3, 16)
+    flat[h["b_off"]] = 0.1
+    net.params(set=flat)
+    return net, flat, layers
+
+
+def _volume(rng, shape, body):
+    (z0, z1), (y0, y1), (x0, x1) = body
+    den = np.full(shape, 0.0012, np.float32)
+    den[z0:z1, y0:y1, x0:x1] = rng.uniform(0.9, 1.1, (z1 - z0, y1 - y0, x1 - x0))
+    den[z0 + 2:z0 + 5, y0 + 3:y0 + 7, x0 + 4:x0 + 9] = 0.26   # a lung-like pocket
+    dose = rng.lognormal(-16, 1.0, shape).astype(np.float32)
+    act = np.zeros(shape, np.float32)
+    act[z0:z1, y0:y1, x0:x1] = rng.lognormal(0, 0.3, (z1 - z0, y1 - y0, x1 - x0))
+    return dose, den, act
+
+
+def _oracle_box(torch, dn, params, dose, den, act, s, a, corner, dims):
+    """Oracle forward of the network input box at corner (x, y, z) of dims (w, h, d)."""
+    nz, ny, nx = dose.shape
+    w, h, d = dims
+    x = np.zeros((1, d, h, w, 8), np.float32)
+    inv_s, inv_a = np.float32(1) / np.float32(s), np.float32(1) / np.float32(a)
+    zs, ys, xs = [np.arange(c, c + n) for c, n in zip(corner[::-1], (d, h, w))]
+    iz, iy, ix = [(v >= 0) & (v < n) for v, n in zip((zs, ys, xs), (nz, ny, nx))]
+    sub = np.ix_(zs[iz], ys[iy], xs[ix])
+    box = np.ix_(np.nonzero(iz)[0], np.nonzero(iy)[0], np.nonzero(ix)[0])
+    rho = den[sub]
+    c2 = np.maximum(act[sub], 0) * inv_a
+    x[0][box + (0,)] = np.maximum(dose[sub], 0) * inv_s
+    x[0][box + (1,)] = rho
+    x[0][box + (2,)] = c2
+    x[0][box + (3,)] = c2 / np.maximum(rho, np.float32(0.1))
+    xb = bf16_round(torch, x).astype(np.float64)
+    y, _ = dn.unet_forward(xb, params, (16, 32, 64, 128))
+    return y[0]
+
+
+@pytest.mark.parametrize("budget", [0, 48 * 32 * 24])
+def test_apply_whole_volume_matches_oracle(env, budget):
+    """Whole-volume inference on a non-cubic body box (one pass, and in z slabs
+    under a small voxel budget) against the FP64 oracle U-Net run on the same
+    boxes; outside the body box the input is returned unchanged."""
+    torch, nm, dn = env
+    rng = np.random.default_rng(11)
+    shape = (20, 28, 36)
+    body = ((4, 16), (6, 22), (5, 31))
+    dose, den, act = _volume(rng, shape, body)
+    kw = {"infer_voxels": budget} if budget else {}
+    net, flat, layers = _random_net(torch, nm, 4, **kw)
+    names = [n for n, _, _ in dn.unet_layers(8, (16, 32, 64, 128))]
+    params = to_oracle(flat, layers, (16, 32, 64, 128), names)
+    out = torch.empty(shape, dtype=torch.float32, device="cuda")
+    net.apply(torch.from_numpy(dose).cuda(), torch.from_numpy(den).cuda(), torch.from_numpy(act).cuda(), out)
+    o = out.cpu().numpy()
+    net.close()
+    m = den >= 0.1
+    s = np.float32(dose[m].astype(np.float64).mean())
+    a = np.float32(act[m].astype(np.float64).mean())
+    # network boxes: body box + 8 voxels of context, sides rounded up to 8
+    (z0, z1), (y0, y1), (x0, x1) = body
+    W, H = 48, 32
+    tc = 12 if not budget else 8                    # z core per pass
+    exp = np.zeros(shape)
+    for zc in range(z0, z1, tc):
+        core = min(tc, z1 - zc)
+        D = (core + 16 + 7) // 8 * 8 if not budget else 24
+        y = _oracle_box(torch, dn, params, dose, den, act, s, a, (x0 - 8, y0 - 8, zc - 8), (W, H, D))
+        exp[zc:zc + core, y0:y1, x0:x1] = s * y[8:8 + core, 8:8 + (y1 - y0), 8:8 + (x1 - x0)]
+    inside = np.zeros(shape, bool)
+    inside[z0:z1, y0:y1, x0:x1] = True
+    # BF16 activations through ~10 convolutions: 2 % in norm, as for the patch forward
+    rel = np.linalg.norm(o[inside] - exp[inside]) / np.linalg.norm(exp[inside])
+    assert rel < 2e-2, rel
+    assert np.array_equal(o[~inside], dose[~inside])
