@@ -25,7 +25,7 @@ constexpr int kKahnTrialLimit = 1000;
 
 struct Energy {
   float s_c, s_pe, s_r;   // per-unit-density factors: mu/rho = za s_c + zp s_pe + zr s_r
-  float inv_mubar;        // 1 / majorant (cm) over all materials at their largest density
+  float inv_mubar;        // 1 / majorant (cm) of the lane's tracking region
 };
 
 // Energy-dependent factors, computed once per energy change.  s_c is
@@ -43,7 +43,7 @@ __device__ __forceinline__ Energy energy_factors(float e, const float* __restric
   const float w = x - (float)i;
   const float a = kn[i], b = kn[i + 1];
   f.s_c = fmaf(w, b - a, a);
-  const float ie = 1.0f / e;
+  const float ie = __fdividef(1.0f, e);
   const float ie2 = ie * ie;
   f.s_pe = ie2 * ie;
   f.s_r = RAYLEIGH ? ie2 : 0.0f;
@@ -66,7 +66,7 @@ __device__ __forceinline__ float kahn_x(float k, uint32_t& ctr, uint32_t stream,
                                         uint32_t hhi, uint32_t k0, uint32_t k1, uint32_t& r_phi,
                                         uint32_t& flags) {
   const float two_k = 2.0f * k;
-  const float thr = (1.0f + two_k) / (9.0f + two_k);
+  const float thr = __fdividef(1.0f + two_k, 9.0f + two_k);
   for (int trial = 0;; ++trial) {
     const uint4 r = draw(ctr, stream, hlo, hhi, k0, k1);
     const float r1 = u01(r.x), r2 = u01(r.y), r3 = u01(r.z);
@@ -77,10 +77,10 @@ __device__ __forceinline__ float kahn_x(float k, uint32_t& ctr, uint32_t stream,
       const float eta = fmaf(k, x, 1.0f);
       acc = r3 * eta * eta <= 4.0f * k * x;
     } else {
-      x = 2.0f * (1.0f - r2) / fmaf(two_k, r2, 1.0f);
+      x = __fdividef(2.0f * (1.0f - r2), fmaf(two_k, r2, 1.0f));
       const float eta = fmaf(k, x, 1.0f);
       const float c = 1.0f - x;
-      acc = 2.0f * r3 <= fmaf(c, c, 1.0f / eta);
+      acc = 2.0f * r3 <= fmaf(c, c, __fdividef(1.0f, eta));
     }
     if (acc || trial + 1 >= kKahnTrialLimit) {
       if (!acc) flags |= NM_DEV_KAHN_LIMIT;
@@ -92,14 +92,15 @@ __device__ __forceinline__ float kahn_x(float k, uint32_t& ctr, uint32_t stream,
 
 // New direction at polar cosine c and azimuth phi about (u, v, w).
 __device__ __forceinline__ void rotate(float& u, float& v, float& w, float c, float phi) {
-  const float s = sqrtf(fmaxf(0.0f, fmaf(-c, c, 1.0f)));
+  const float s2 = fmaf(-c, c, 1.0f);
+  const float s = s2 > 0.0f ? s2 * rsqrtf(s2) : 0.0f;
   float sp, cp;
   __sincosf(phi, &sp, &cp);
   const float t2 = fmaf(-w, w, 1.0f);
   float nu, nv, nw;
   if (t2 > 1e-10f) {
-    const float t = sqrtf(t2);
-    const float it = 1.0f / t;
+    const float it = rsqrtf(t2);
+    const float t = t2 * it;
     nu = fmaf(c, u, s * (u * w * cp - v * sp) * it);
     nv = fmaf(c, v, s * (v * w * cp + u * sp) * it);
     nw = fmaf(c, w, -s * cp * t);
@@ -121,33 +122,61 @@ __device__ __forceinline__ void rotate(float& u, float& v, float& w, float c, fl
 // memorylessness of the exponential, restarting the flight there with the
 // other region's majorant leaves the free-path distribution unchanged.
 //
+// Slab parameters of the ray (x, y, z) + t (u, v, w), t in cm, against the
+// box: it is inside the box for tn < t < tf.
+__device__ __forceinline__ void region_slabs(const PatientGeom& G, float x, float y, float z, float u, float v,
+                                             float w, float& tn, float& tf) {
+  // approximate reciprocals: the box has a one-voxel margin, so a distance
+  // off by a few ulp cannot reach a voxel the region's majorant does not cover
+  const float iu = __fdividef(1.0f, u * G.inv_dx), iv = __fdividef(1.0f, v * G.inv_dy),
+              iw = __fdividef(1.0f, w * G.inv_dz);
+  const float ax = (G.blo[0] - x) * iu, bx = (G.bhi[0] - x) * iu;
+  const float ay = (G.blo[1] - y) * iv, by = (G.bhi[1] - y) * iv;
+  const float az = (G.blo[2] - z) * iw, bz = (G.bhi[2] - z) * iw;
+  // fminf/fmaxf drop the NaN of 0 * inf (a ray in a box face, parallel to it)
+  tf = fminf(fmaxf(ax, bx), fminf(fmaxf(ay, by), fmaxf(az, bz)));
+  tn = fmaxf(fminf(ax, bx), fmaxf(fminf(ay, by), fminf(az, bz)));
+}
+
+constexpr float kInf = __builtin_huge_valf();
+
 // Distance (cm) from (x, y, z) along (u, v, w) to the boundary of the lane's
 // region: from inside, to the box's far side; from outside, to its near side,
 // or +inf when the ray misses the box (a ray that has left the convex box
 // never meets it again).
 __device__ __forceinline__ float region_distance(const PatientGeom& G, bool out, float x, float y, float z,
                                                  float u, float v, float w) {
-  const float iu = 1.0f / (u * G.inv_dx), iv = 1.0f / (v * G.inv_dy), iw = 1.0f / (w * G.inv_dz);
-  const float ax = (G.blo[0] - x) * iu, bx = (G.bhi[0] - x) * iu;
-  const float ay = (G.blo[1] - y) * iv, by = (G.bhi[1] - y) * iv;
-  const float az = (G.blo[2] - z) * iw, bz = (G.bhi[2] - z) * iw;
-  // fminf/fmaxf drop the NaN of 0 * inf (a ray in a box face, parallel to it)
-  const float tf = fminf(fmaxf(ax, bx), fminf(fmaxf(ay, by), fmaxf(az, bz)));
+  float tn, tf;
+  region_slabs(G, x, y, z, u, v, w, tn, tf);
   if (!out) return tf;
-  const float tn = fmaxf(fminf(ax, bx), fmaxf(fminf(ay, by), fminf(az, bz)));
-  return tn <= tf && tf > 0.0f ? fmaxf(tn, 0.0f) : __int_as_float(0x7f800000);
+  return tn <= tf && tf > 0.0f ? fmaxf(tn, 0.0f) : kInf;
+}
+
+// The same for the ray and for its reverse (photon B leaves the decay site
+// opposite to photon A): reversing the ray maps (tn, tf) to (-tf, -tn).
+__device__ __forceinline__ void region_distance_pair(const PatientGeom& G, bool out, float x, float y, float z,
+                                                     float u, float v, float w, float& fwd, float& rev) {
+  float tn, tf;
+  region_slabs(G, x, y, z, u, v, w, tn, tf);
+  if (!out) {
+    fwd = tf;
+    rev = -tn;
+  } else {
+    fwd = tn <= tf && tf > 0.0f ? fmaxf(tn, 0.0f) : kInf;
+    rev = tn <= tf && tn < 0.0f ? fmaxf(-tf, 0.0f) : kInf;
+  }
 }
 
 __device__ __forceinline__ bool outside_box(const PatientGeom& G, float x, float y, float z) {
   return !(x >= G.blo[0] && x < G.bhi[0] && y >= G.blo[1] && y < G.bhi[1] && z >= G.blo[2] && z < G.bhi[2]);
 }
 
-// 1 / majorant outside the box at energy e (same bin as energy_factors).
-__device__ __forceinline__ float inv_majorant_out(float e, const float* __restrict__ minv_out, float ln_lo,
-                                                  float inv_dln) {
+// 1 / majorant at energy e from a region's table (same bin as energy_factors).
+__device__ __forceinline__ float inv_majorant_at(float e, const float* __restrict__ minv, float ln_lo,
+                                                 float inv_dln) {
   float x = (__logf(e) - ln_lo) * inv_dln;
   x = fminf(fmaxf(x, 0.0f), (float)(kKnTable - 1) - 0x1p-10f);
-  return minv_out[(int)x];
+  return minv[(int)x];
 }
 
 // Decay site and first-photon direction of history (hlo, hhi).
@@ -236,7 +265,7 @@ __device__ __forceinline__ void compton(const TransportParams& p, const float* s
   uint32_t rphi;
   const float k = e * kInvElectronMassMeV;
   const float x = kahn_x(k, ctr, stream, hlo, hhi, p.key0, p.key1, rphi, flags);
-  const float e2 = e / fmaf(k, x, 1.0f);
+  const float e2 = __fdividef(e, fmaf(k, x, 1.0f));
   rotate(ux, uy, uz, 1.0f - x, fmaf(kTwoPi, u01(rphi), -3.14159265f));
   if (e2 < p.cut) {
     dq = (uint32_t)qe;
@@ -258,12 +287,14 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
   __shared__ float s_minv_out[kKnTable];
   __shared__ MaterialCoef s_mat[NM_MAX_MATERIALS];
   __shared__ Energy s_f0;
+  __shared__ float s_inv0_out;              // 1 / majorant outside the box at e0
   // Per patient, indexed by CounterSlot: the rare events (photo, cutoff,
   // rayleigh, killed units) counted here directly, and (multi) the lanes'
   // register counters handed over when a lane changes patient.
   __shared__ unsigned long long s_cnt[MULTI ? kMaxBatchPatients : 1][8];
   __shared__ PatientGeom s_geom[MULTI ? kMaxBatchPatients : 1];
-  extern __shared__ float s_site[];         // [6][blockDim]: decay site and photon A direction
+  extern __shared__ float s_site[];         // [7][blockDim]: decay site, photon A direction, photon B's
+                                            // distance to its region boundary
   const int n_pat = MULTI ? p.n_patients : 1;
   for (int i = threadIdx.x; i < kKnTable; i += blockDim.x) {
     s_kn[i] = p.kn[i];
@@ -275,7 +306,10 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
   if (MULTI)
     for (int i = threadIdx.x; i < n_pat; i += blockDim.x) s_geom[i] = p.patients[i];
   __syncthreads();
-  if (threadIdx.x == 0) s_f0 = energy_factors<RAYLEIGH>(p.e0, s_kn, s_minv, p.ln_e_lo, p.inv_dln_e);
+  if (threadIdx.x == 0) {
+    s_f0 = energy_factors<RAYLEIGH>(p.e0, s_kn, s_minv, p.ln_e_lo, p.inv_dln_e);
+    s_inv0_out = inv_majorant_at(p.e0, s_minv_out, p.ln_e_lo, p.inv_dln_e);
+  }
   __syncthreads();
   float* site = s_site + threadIdx.x;
   const int nb = blockDim.x;
@@ -313,7 +347,8 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
       stream = kStreamPhotonB; ctr = 0; have_spare = false; steps = 0;
       const PatientGeom& GB = MULTI ? s_geom[pi] : p.g;
       out = outside_box(GB, px, py, pz);
-      rem = region_distance(GB, out, px, py, pz, ux, uy, uz);
+      rem = site[6 * nb];
+      if (out) f.inv_mubar = s_inv0_out;
     }
     // ---- refill: lanes without a photon take new histories from the pool ----
     const unsigned need = __ballot_sync(kFull, !alive && !done);
@@ -387,10 +422,13 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
           stream = kStreamPhotonA; ctr = 0; have_spare = false; steps = 0;
           alive = true;
           out = outside_box(G, px, py, pz);
-          rem = region_distance(G, out, px, py, pz, ux, uy, uz);
+          if (out) f.inv_mubar = s_inv0_out;
+          float rem_b;
+          region_distance_pair(G, out, px, py, pz, ux, uy, uz, rem, rem_b);
           if (G.source_mode == NM_SOURCE_DECAY) {
             site[0] = st.x; site[nb] = st.y; site[2 * nb] = st.z;
             site[3 * nb] = st.u; site[4 * nb] = st.v_; site[5 * nb] = st.w;
+            site[6 * nb] = rem_b;
             pending_b = true;
             has = G.q_positron > 0;
             cell = G.tally + st.v;
@@ -419,8 +457,8 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
       if (waiting && (__popc(waiting) >= (unsigned)p.regroup_compton || flying == 0)) {
         if (pending_c) {
           pending_c = false;
-          compton<RAYLEIGH>(p, s_kn, s_minv, e, qe, f, ux, uy, uz, ctr, stream, hlo, hhi, alive, dq,
-                            flags, s_cnt[MULTI ? pi : 0]);
+          compton<RAYLEIGH>(p, s_kn, out ? s_minv_out : s_minv, e, qe, f, ux, uy, uz, ctr, stream, hlo, hhi,
+                            alive, dq, flags, s_cnt[MULTI ? pi : 0]);
           rem = region_distance(G, out, px, py, pz, ux, uy, uz);
           has = true;
           dv = cv;
@@ -436,7 +474,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
         const uint4 r = draw(ctr, stream, hlo, hhi, p.key0, p.key1);
         r0 = r.x; r1 = r.y; spare0 = r.z; spare1 = r.w; have_spare = true;
       }
-      const float imaj = out ? inv_majorant_out(e, s_minv_out, p.ln_e_lo, p.inv_dln_e) : f.inv_mubar;
+      const float imaj = f.inv_mubar;
       float s = -__logf(u01(r0)) * imaj;   // cm
       const bool cross = s >= rem;         // flight cut at the region boundary
       if (cross) s = rem;
@@ -452,7 +490,8 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
         alive = false;
       } else if (cross) {
         out = !out;
-        rem = out ? __int_as_float(0x7f800000) : region_distance(G, false, px, py, pz, ux, uy, uz);
+        rem = out ? kInf : region_distance(G, false, px, py, pz, ux, uy, uz);
+        f.inv_mubar = inv_majorant_at(e, out ? s_minv_out : s_minv, p.ln_e_lo, p.inv_dln_e);
       } else {
         const int v = ((int)pz * G.ny + (int)py) * G.nx + (int)px;
         const uint32_t wv = __ldg(G.vox + v);
@@ -468,8 +507,8 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
             pending_c = true;
             cv = v;
           } else {
-            compton<RAYLEIGH>(p, s_kn, s_minv, e, qe, f, ux, uy, uz, ctr, stream, hlo, hhi, alive,
-                              dq, flags, s_cnt[MULTI ? pi : 0]);
+            compton<RAYLEIGH>(p, s_kn, out ? s_minv_out : s_minv, e, qe, f, ux, uy, uz, ctr, stream, hlo,
+                              hhi, alive, dq, flags, s_cnt[MULTI ? pi : 0]);
             rem = region_distance(G, out, px, py, pz, ux, uy, uz);
             has = true;
             dv = v;
@@ -561,7 +600,7 @@ __global__ void check_source_kernel(const TransportParams p, uint64_t first, int
   dir[3 * i + 2] = s.w;
 }
 
-size_t transport_smem(int block) { return (size_t)6 * block * sizeof(float); }
+size_t transport_smem(int block) { return (size_t)7 * block * sizeof(float); }
 
 template <bool A, bool R, bool G, bool M>
 void* kernel_ptr() {
