@@ -328,8 +328,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
   Energy f = s_f0;
   int32_t qe = 0;
   int cv = 0;                            // voxel of a pending Compton event
-  uint32_t hlo = 0, hhi = 0, stream = 0, ctr = 0, spare0 = 0, spare1 = 0;
-  bool have_spare = false;
+  uint32_t hlo = 0, hhi = 0, stream = 0, ctr = 0;
   bool out = false;                      // outside the tracking box
   float rem = 0.f;                       // cm to the region boundary along (ux, uy, uz)
   int steps = 0;
@@ -344,7 +343,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
       px = site[0]; py = site[nb]; pz = site[2 * nb];
       ux = -site[3 * nb]; uy = -site[4 * nb]; uz = -site[5 * nb];
       e = p.e0; qe = p.q_e0; f = s_f0;
-      stream = kStreamPhotonB; ctr = 0; have_spare = false; steps = 0;
+      stream = kStreamPhotonB; ctr = 0; steps = 0;
       const PatientGeom& GB = MULTI ? s_geom[pi] : p.g;
       out = outside_box(GB, px, py, pz);
       rem = site[6 * nb];
@@ -419,7 +418,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
           px = st.x; py = st.y; pz = st.z;
           ux = st.u; uy = st.v_; uz = st.w;
           e = p.e0; qe = p.q_e0; f = s_f0;
-          stream = kStreamPhotonA; ctr = 0; have_spare = false; steps = 0;
+          stream = kStreamPhotonA; ctr = 0; steps = 0;
           alive = true;
           out = outside_box(G, px, py, pz);
           if (out) f.inv_mubar = s_inv0_out;
@@ -467,13 +466,11 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
     }
     // ---- one Woodcock flight step per live lane -------------------------------
     if (alive && !pending_c && !has) {
-      uint32_t r0, r1;
-      if (have_spare) {
-        r0 = spare0; r1 = spare1; have_spare = false;
-      } else {
-        const uint4 r = draw(ctr, stream, hlo, hhi, p.key0, p.key1);
-        r0 = r.x; r1 = r.y; spare0 = r.z; spare1 = r.w; have_spare = true;
-      }
+      // A fresh Philox block every step (words x and y): keeping the other two
+      // for the next step saves draws per lane but not per warp, where lanes
+      // are out of phase, and costs registers.
+      const uint4 rr = draw(ctr, stream, hlo, hhi, p.key0, p.key1);
+      const uint32_t r0 = rr.x, r1 = rr.y;
       const float imaj = f.inv_mubar;
       float s = -__logf(u01(r0)) * imaj;   // cm
       const bool cross = s >= rem;         // flight cut at the region boundary
