@@ -1,22 +1,36 @@
 // 3x3x3 convolution by shifted windows: the tensor cores read the 27 taps
 // straight out of one shared-memory halo tile, with no im2col gather.
 //
-// A CTA computes an output tile of TZ x TY x TX voxels.  Its input tile, with
-// a one-voxel halo, is stored as "channel planes": plane j holds channels
-// 8j..8j+7 of every padded voxel, 16 bytes per voxel, voxels in x-fastest
-// order.  In the no-swizzle K-major operand layout with a stride byte offset of
-// 128 (eight 16-byte rows) consecutive voxels are consecutive GEMM rows, so the
-// A operand of tap (dz, dy, dx) is the same tile shifted by
-// (dz*PY + dy)*PX + dx rows: a different start address in the descriptor.
-// GEMM rows run over the padded tile's centre indices; rows whose centre is a
-// halo voxel are computed and dropped (20 % for the 16 x 16 x 2 tile).
+// An output tile is TZ x TY x TX voxels.  Its input tile, with a one-voxel
+// halo, is stored as "channel planes": plane j holds channels 8j..8j+7 of
+// every padded voxel, 16 bytes per voxel, voxels in x-fastest order.  In the
+// no-swizzle K-major operand layout with a stride byte offset of 128 (eight
+// 16-byte rows) consecutive voxels are consecutive GEMM rows, so the A operand
+// of tap (dz, dy, dx) is the same tile shifted by (dz*PY + dy)*PX + dx rows: a
+// different start address in the descriptor.  GEMM rows run over the padded
+// tile's centre indices; rows whose centre is a halo voxel are computed and
+// dropped (20 % for a 16 x 16 x 2 tile, 27 % for 16 x 16 x 4).
 //
-// Channels are consumed 16 at a time (two planes = one MMA K-step): for each
-// 16-channel chunk the tile and the chunk's weights are copied with cp.async
-// (zero-filled outside the volume) into one of two stage buffers, then one
-// thread issues 27 taps x (tile rows / 128) MMAs and commits them to the
-// stage's mbarrier.  Waits are bounded as in nm_conv.cu.
+// The kernel is persistent and warp-specialised (one CTA per SM):
+//   warp 0    one thread issues TMA loads: per 16-channel chunk two 5-D tiled
+//             tensor loads (the two channel planes of the halo box; the TMA
+//             unit zero-fills outside the volume) and one bulk copy of the
+//             chunk's weights, pre-arranged in the operand layout;
+//   warp 1    one thread issues 27 taps x (tile rows / 128) MMAs per chunk
+//             into a TMEM accumulator and commits them to the stage's "empty"
+//             barrier, then the tile to the accumulator's "full" barrier;
+//   warps 2-5 the epilogue: tcgen05.ld of their TMEM lane quarter, bias, ReLU,
+//             BF16, 16-byte stores; then they release the accumulator.
+// A ring of shared-memory stages and two TMEM accumulators (one when they do
+// not fit) let loads, MMAs and the epilogue of consecutive tiles overlap.
+// Every wait is bounded; a time-out sets NM_DEV_TIMEOUT, drains the copies
+// and MMAs in flight and frees the tensor memory.
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
 
 #include "nm_internal.cuh"
 #include "nm_tc.cuh"
@@ -24,63 +38,83 @@
 namespace nm {
 namespace {
 
-constexpr int TX = 16, TY = 16, TZ = 2;
-constexpr int PX = TX + 2, PY = TY + 2, PZ = TZ + 2;
-constexpr int kRows = PX * PY * PZ;                         // padded tile voxels
-constexpr int kCmin = (1 * PY + 1) * PX + 1;                // first centre
-constexpr int kCmax = (TZ * PY + TY) * PX + TX;             // last centre
-constexpr int kMt = (kCmax - kCmin + 1 + 127) / 128;        // 128-row MMA tiles
-constexpr int kDelta = PY * PX + PX + 1;                    // largest tap shift
-constexpr int kRowsAlloc = kCmin + kMt * 128 + kDelta;      // rows any MMA may read
-constexpr int kThreads = 128;
+typedef __nv_bfloat16 bf16;
+
+constexpr int TX = 16, TY = 16;
+constexpr uint32_t kSboB = 27 * 16 / 8 * 128;               // 8 weight rows of 27 x 16 channels
+constexpr int kThreads = 192;
 constexpr long long kWaitCycles = 4ll << 30;
 
-static_assert(kRowsAlloc >= kRows, "tile rows");
-
-template <int COUT>
+// Tile geometry and resources for COUT outputs and tiles TZ voxels deep.
+// Every 128-row M-tile accumulates its 27 taps in order, so the M-tiles are
+// the independent MMA chains in flight: 16-output layers, whose small MMAs
+// are bound by that chain latency, take deeper tiles (more M-tiles).
+template <int COUT, int TZ, bool SWZ>
 struct TileLayout {
-  static constexpr uint32_t kPlane = kRowsAlloc * 16;       // one 8-channel plane
-  static constexpr uint32_t kA = 2 * kPlane;                // 16 channels
-  static constexpr uint32_t kSboB = 27 * 16 / 8 * 128;      // 8 weight rows of 27 x 16 channels
-  static constexpr uint32_t kB = COUT / 8 * kSboB;
-  static constexpr uint32_t kStage = (kA + kB + 1023) / 1024 * 1024;
-  static constexpr int kNcols = kMt * COUT <= 32 ? 32 : kMt * COUT <= 64 ? 64 : kMt * COUT <= 128 ? 128
-                                : kMt * COUT <= 256 ? 256 : 512;
+  static constexpr int PX = TX + 2, PY = TY + 2, PZ = TZ + 2;
+  static constexpr int kRows = PX * PY * PZ;                // padded tile voxels
+  static constexpr int kCmin = (1 * PY + 1) * PX + 1;       // first centre
+  static constexpr int kCmax = (TZ * PY + TY) * PX + TX;    // last centre
+  static constexpr int kMt = (kCmax - kCmin + 1 + 127) / 128;  // 128-row MMA tiles
+  static constexpr int kDelta = PY * PX + PX + 1;           // largest tap shift
+  static constexpr int kRowsAlloc = (kCmin + kMt * 128 + kDelta + 15) / 16 * 16;  // rows any MMA may read
+  // SWZ: one 16-channel plane of 32-byte swizzled rows; else two 8-channel
+  // planes of 16-byte rows
+  static constexpr int kPlanes = SWZ ? 1 : 2;
+  static constexpr uint32_t kRowBytes = SWZ ? 32 : 16;
+  static constexpr uint32_t kPlane = kRowsAlloc * kRowBytes; // one plane (256-byte multiple)
+  static constexpr uint32_t kBoxBytes = kRows * kRowBytes;  // what one plane's TMA load writes
+  static constexpr uint32_t kB = COUT / 8 * kSboB;          // one chunk's weights
+  static constexpr uint32_t kStage = (kPlanes * kPlane + kB + 1023) / 1024 * 1024;
+  static constexpr int kStages = (3 * kStage <= 220 * 1024) ? 3 : 2;
+  static constexpr int kAccCols = kMt * COUT;
+  static constexpr int kNacc = 2 * kAccCols <= 512 ? 2 : 1;
+  static constexpr int kNcols = kNacc * kAccCols <= 32 ? 32 : kNacc * kAccCols <= 64 ? 64
+                                : kNacc * kAccCols <= 128 ? 128 : kNacc * kAccCols <= 256 ? 256 : 512;
+  static constexpr size_t kSmem = (size_t)kStages * kStage;
+  static_assert(kRowsAlloc >= kRows, "tile rows");
+  static_assert(kPlane % 256 == 0, "planes keep 256-byte (swizzle atom) alignment");
+  static_assert(kAccCols <= 512, "accumulator fits the tensor memory");
+  static_assert(kSmem <= 227 * 1024, "shared memory");
 };
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-}
+struct TileGrid {
+  int n, d, h, w, tz, tiles_x, tiles_y, tiles_z;
+  long long tiles;
+  __device__ void coords(long long t, int& b, int& x0, int& y0, int& z0) const {
+    x0 = (int)(t % tiles_x) * TX; t /= tiles_x;
+    y0 = (int)(t % tiles_y) * TY; t /= tiles_y;
+    z0 = (int)(t % tiles_z) * tz;
+    b = (int)(t / tiles_z);
+  }
+};
 
-template <int COUT>
-__global__ void __launch_bounds__(kThreads) conv_tile_kernel(int n, int d, int h, int w, int cin, int kpad,
-                                                             const __nv_bfloat16* __restrict__ x,
-                                                             const __nv_bfloat16* __restrict__ wt,
-                                                             const float* __restrict__ bias,
-                                                             __nv_bfloat16* __restrict__ y, int relu,
-                                                             uint32_t* status) {
-  typedef TileLayout<COUT> L;
+template <int COUT, int TZ, bool SWZ>
+__global__ void __launch_bounds__(kThreads, 1) conv_tile_kernel(const __grid_constant__ CUtensorMap tmx,
+                                                                const TileGrid g, int nchunks,
+                                                                const bf16* __restrict__ wt,
+                                                                const float* __restrict__ bias,
+                                                                bf16* __restrict__ y, int relu,
+                                                                uint32_t* status) {
+  typedef TileLayout<COUT, TZ, SWZ> L;
+  constexpr int S = L::kStages, NA = L::kNacc;
+  constexpr int PX = L::PX, PY = L::PY, kMt = L::kMt, kCmin = L::kCmin, kCmax = L::kCmax;
+  constexpr uint32_t kPlane = L::kPlane;
   extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ __align__(8) uint64_t full[S], empty[S], tfull[NA], tempty[NA];
   __shared__ uint32_t s_tmem;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // tile origin
-  const int tiles_x = (w + TX - 1) / TX, tiles_y = (h + TY - 1) / TY, tiles_z = (d + TZ - 1) / TZ;
-  int t = blockIdx.x;
-  const int tx = t % tiles_x; t /= tiles_x;
-  const int ty = t % tiles_y; t /= tiles_y;
-  const int tz = t % tiles_z;
-  const int b = t / tiles_z;
-  const int x0 = tx * TX, y0 = ty * TY, z0 = tz * TZ;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (warp == 0) tc::tmem_alloc(&s_tmem, L::kNcols);
-  if (tid == 0) {
-    tc::mbar_init(&bar[0], 1);
-    tc::mbar_init(&bar[1], 1);
+  if (threadIdx.x == 32) {
+    for (int i = 0; i < S; ++i) {
+      tc::mbar_init(&full[i], 1);
+      tc::mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < NA; ++i) {
+      tc::mbar_init(&tfull[i], 1);
+      tc::mbar_init(&tempty[i], 128);
+    }
     tc::mbar_fence_init();
   }
   tc::fence_before_sync();
@@ -88,122 +122,247 @@ __global__ void __launch_bounds__(kThreads) conv_tile_kernel(int n, int d, int h
   tc::fence_after_sync();
   const uint32_t tmem = s_tmem;
   const uint32_t base = tc::smem_u32(smem);
-  const int nchunks = (cin + 15) / 16;
-  constexpr uint32_t idesc = tc::idesc_bf16_f32(128, COUT, false, false);
+  const long long my_tiles = g.tiles > blockIdx.x ? (g.tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   bool timeout = false;
-  int issued = 0;
 
-  for (int cc = 0; cc < nchunks; ++cc) {
-    const int buf = cc & 1;
-    if (cc >= 2 && !tc::mbar_wait_bounded(&bar[buf], ((cc >> 1) - 1) & 1, kWaitCycles)) timeout = true;
-    if (__syncthreads_or(timeout)) { timeout = true; break; }
-    const uint32_t sa = base + buf * L::kStage;
-    const uint32_t sb = sa + L::kA;
-    // input planes 2cc, 2cc+1 of every padded voxel (zero outside the volume)
-    for (int i = tid; i < 2 * kRowsAlloc; i += kThreads) {
-      const int p = i / kRowsAlloc, r = i - p * kRowsAlloc;
-      const int ch = cc * 16 + p * 8;
-      const int pz = r / (PY * PX), py = (r / PX) % PY, px = r % PX;
-      const int gz = z0 + pz - 1, gy = y0 + py - 1, gx = x0 + px - 1;
-      const bool ok = r < kRows && ch < cin && (unsigned)gz < (unsigned)d && (unsigned)gy < (unsigned)h &&
-                      (unsigned)gx < (unsigned)w;
-      const __nv_bfloat16* src = ok ? x + ((((long long)b * d + gz) * h + gy) * w + gx) * cin + ch : x;
-      cp_async16(sa + p * L::kPlane + r * 16, src, ok);
-    }
-    // weights of this chunk: row co, K index tap*16 + c
-    for (int i = tid; i < COUT * 27 * 2; i += kThreads) {
-      const int co = i / 54, rest = i - co * 54;
-      const int tap = rest >> 1, j = rest & 1;
-      const int ch = cc * 16 + j * 8;
-      const bool ok = ch < cin;
-      const __nv_bfloat16* src = ok ? wt + (long long)co * kpad + tap * cin + ch : wt;
-      const int kchunk = tap * 2 + j;
-      cp_async16(sb + (co >> 3) * L::kSboB + kchunk * 128 + (co & 7) * 16, src, ok);
-    }
-    cp_async_wait_all();
-    tc::fence_async_smem();
-    __syncthreads();
-    if (tid == 0) {
-      tc::fence_after_sync();
-      for (int tap = 0; tap < 27; ++tap) {
-        const int delta = ((tap / 9 - 1) * PY + ((tap / 3) % 3 - 1)) * PX + (tap % 3 - 1);
-        const uint64_t bdesc = tc::smem_desc(sb + tap * 256, 128, L::kSboB);
-#pragma unroll
-        for (int mt = 0; mt < kMt; ++mt) {
-          const uint32_t a0 = sa + (uint32_t)(kCmin + mt * 128 + delta) * 16;
-          tc::mma_bf16(tmem + mt * COUT, tc::smem_desc(a0, L::kPlane, 128), bdesc, idesc,
-                       (cc | tap) != 0);
-        }
-      }
-      tc::mma_commit(&bar[buf]);
-    }
-    issued = cc + 1;
-  }
-  if (!timeout && issued > 0) {
-    const int last = issued - 1;
-    if (!tc::mbar_wait_bounded(&bar[last & 1], (last >> 1) & 1, kWaitCycles)) timeout = true;
-  }
-  timeout = __syncthreads_or(timeout);
-  if (timeout) {
-    if (tid == 0) atomicOr(status, NM_DEV_TIMEOUT);
-    if (issued > 0) tc::mbar_wait_bounded(&bar[(issued - 1) & 1], ((issued - 1) >> 1) & 1, kWaitCycles);
-  } else {
-    tc::fence_after_sync();
-    for (int mt = 0; mt < kMt; ++mt) {
-      const int c = kCmin + mt * 128 + warp * 32 + lane;  // this lane's centre
-      const int pz = c / (PY * PX), py = (c / PX) % PY, px = c % PX;
-      const int gz = z0 + pz - 1, gy = y0 + py - 1, gx = x0 + px - 1;
-      const bool ok = c <= kCmax && px >= 1 && px <= TX && py >= 1 && py <= TY && pz >= 1 && pz <= TZ &&
-                      gz < d && gy < h && gx < w;
-#pragma unroll
-      for (int cq = 0; cq < COUT / 16; ++cq) {
-        float v[16];
-        tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + mt * COUT + cq * 16, v);
-        if (ok) {
-          __align__(16) __nv_bfloat16 o[16];
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            float tv = v[j] + (bias ? __ldg(bias + cq * 16 + j) : 0.0f);
-            if (relu) tv = fmaxf(tv, 0.0f);
-            o[j] = __float2bfloat16_rn(tv);
+  if (warp == 0) {
+    // ---- producer ----------------------------------------------------------------
+    if (lane == 0) {
+      long long it = 0;
+      for (long long k = 0; k < my_tiles && !timeout; ++k) {
+        int b, x0, y0, z0;
+        g.coords(blockIdx.x + k * gridDim.x, b, x0, y0, z0);
+        for (int cc = 0; cc < nchunks; ++cc) {
+          const int s = (int)(it % S);
+          const long long u = it / S;
+          if (it >= S && !tc::mbar_wait_bounded(&empty[s], (uint32_t)((u - 1) & 1), kWaitCycles)) {
+            timeout = true;
+            break;
           }
-          uint4* dst = reinterpret_cast<uint4*>(y + ((((long long)b * d + gz) * h + gy) * w + gx) * COUT + cq * 16);
-          dst[0] = reinterpret_cast<uint4*>(o)[0];
-          dst[1] = reinterpret_cast<uint4*>(o)[1];
+          const uint32_t sa = base + s * L::kStage;
+          tc::mbar_arrive_expect_tx(&full[s], L::kPlanes * L::kBoxBytes + L::kB);
+          tc::tma_load_5d(sa, &tmx, &full[s], cc * 16, x0 - 1, y0 - 1, z0 - 1, b);
+          if (!SWZ) tc::tma_load_5d(sa + kPlane, &tmx, &full[s], cc * 16 + 8, x0 - 1, y0 - 1, z0 - 1, b);
+          tc::bulk_load(sa + L::kPlanes * kPlane, wt + (size_t)cc * COUT * 432, L::kB, &full[s]);
+          ++it;
         }
       }
+      // every copy issued has landed before the CTA can finish
+      for (long long j = it > S ? it - S : 0; j < it; ++j)
+        if (!tc::mbar_wait_bounded(&full[j % S], (uint32_t)((j / S) & 1), kWaitCycles)) timeout = true;
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer --------------------------------------------------------------
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc::idesc_bf16_f32(128, COUT, false, false);
+      long long it = 0;
+      for (long long k = 0; k < my_tiles && !timeout; ++k) {
+        const int a = (int)(k % NA);
+        if (k >= NA && !tc::mbar_wait_bounded(&tempty[a], (uint32_t)(((k / NA) - 1) & 1), kWaitCycles)) {
+          timeout = true;
+          break;
+        }
+        tc::fence_after_sync();
+        const uint32_t acc = tmem + a * L::kAccCols;
+        for (int cc = 0; cc < nchunks; ++cc) {
+          const int s = (int)(it % S);
+          if (!tc::mbar_wait_bounded(&full[s], (uint32_t)((it / S) & 1), kWaitCycles)) {
+            timeout = true;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t sa = base + s * L::kStage;
+          const uint32_t sb = sa + L::kPlanes * kPlane;
+          // Descriptors differ only in the start-address field (bits 0-13, in
+          // 16-byte units, no carry out for shared-memory addresses): build
+          // two once and offset them by compile-time constants, so that the
+          // issuing thread spends a few instructions per MMA.
+          const uint64_t a_base = SWZ ? tc::smem_desc_sw32(sa, 256) : tc::smem_desc(sa, kPlane, 128);
+          const uint64_t b_base = SWZ ? tc::smem_desc_sw32(sb, 256) : tc::smem_desc(sb, 128, kSboB);
+          const uint32_t first = cc != 0;
+#pragma unroll
+          for (int tap = 0; tap < 27; ++tap) {
+            const int delta = ((tap / 9 - 1) * PY + ((tap / 3) % 3 - 1)) * PX + (tap % 3 - 1);
+            const uint64_t bdesc = b_base + (uint64_t)((SWZ ? tap * COUT * 32 : tap * 256) >> 4);
+#pragma unroll
+            for (int mt = 0; mt < kMt; ++mt) {
+              const uint64_t adesc = a_base + (uint64_t)(((kCmin + mt * 128 + delta) * (int)L::kRowBytes) >> 4);
+              tc::mma_bf16(acc + mt * COUT, adesc, bdesc, idesc, tap == 0 ? first : 1u);
+            }
+          }
+          tc::mma_commit(&empty[s]);
+          ++it;
+        }
+        if (timeout) break;
+        tc::mma_commit(&tfull[a]);
+      }
+      // the MMAs issued last have completed before the tensor memory is freed
+      if (it > 0 && !tc::mbar_wait_bounded(&empty[(it - 1) % S], (uint32_t)(((it - 1) / S) & 1), kWaitCycles))
+        timeout = true;
+    }
+  } else {
+    // ---- epilogue ----------------------------------------------------------------
+    const int q = warp & 3;                  // TMEM lane quarter of this warp
+    for (long long k = 0; k < my_tiles; ++k) {
+      const int a = (int)(k % NA);
+      // the warp leaves together (tcgen05.ld below is warp-collective)
+      const bool got = tc::mbar_wait_bounded(&tfull[a], (uint32_t)((k / NA) & 1), kWaitCycles);
+      if (!__all_sync(0xffffffffu, got)) {
+        timeout = true;
+        break;
+      }
+      tc::fence_after_sync();
+      int b, x0, y0, z0;
+      g.coords(blockIdx.x + k * gridDim.x, b, x0, y0, z0);
+      for (int mt = 0; mt < kMt; ++mt) {
+        const int c = kCmin + mt * 128 + q * 32 + lane;   // this lane's centre
+        const int pz = c / (PY * PX), py = (c / PX) % PY, px = c % PX;
+        const int gz = z0 + pz - 1, gy = y0 + py - 1, gx = x0 + px - 1;
+        const bool ok = c <= kCmax && px >= 1 && px <= TX && py >= 1 && py <= TY && pz >= 1 && pz <= TZ &&
+                        gz < g.d && gy < g.h && gx < g.w;
+#pragma unroll
+        for (int cq = 0; cq < COUT / 16; ++cq) {
+          float v[16];
+          tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + a * L::kAccCols + mt * COUT + cq * 16, v);
+          if (ok) {
+            __align__(16) bf16 o[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              float tv = v[j] + (bias ? __ldg(bias + cq * 16 + j) : 0.0f);
+              if (relu) tv = fmaxf(tv, 0.0f);
+              o[j] = __float2bfloat16_rn(tv);
+            }
+            uint4* dst = reinterpret_cast<uint4*>(
+                y + ((((long long)b * g.d + gz) * g.h + gy) * g.w + gx) * COUT + cq * 16);
+            dst[0] = reinterpret_cast<uint4*>(o)[0];
+            dst[1] = reinterpret_cast<uint4*>(o)[1];
+          }
+        }
+      }
+      tc::fence_before_sync();
+      tc::mbar_arrive(&tempty[a]);
     }
   }
+  if (timeout) atomicOr(status, NM_DEV_TIMEOUT);
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, L::kNcols);
 }
 
-template <int COUT>
-cudaError_t launch_tile(const nm_conv3d_desc& g, const void* x, const void* w, const float* bias, void* y,
+// Weights [cout][kpad] (K index tap * cin + c) -> per 16-channel chunk the
+// shared-memory image of the B operand, zero for channels >= cin:
+//   swz:  [chunk][27 taps][cout rows][2 halves of 8 channels], the halves of
+//         row co exchanged when bit 2 of co is set (32-byte swizzle);
+//   else: [chunk][cout / 8][27 taps x 2 halves][8 rows][8 channels].
+__global__ void tile_weights_kernel(const bf16* __restrict__ w, int cin, int kpad, int cout, int nchunks, int swz,
+                                    bf16* __restrict__ out) {
+  const long long total = (long long)nchunks * cout * 432;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int e = (int)(i % 8);
+    long long t = i / 8;
+    int co, tap, half, cc;
+    if (swz) {
+      const int pos = (int)(t % 2); t /= 2;
+      co = (int)(t % cout); t /= cout;
+      tap = (int)(t % 27);
+      cc = (int)(t / 27);
+      half = pos ^ ((co >> 2) & 1);
+    } else {
+      const int r = (int)(t % 8); t /= 8;
+      const int kc = (int)(t % 54); t /= 54;
+      const int grp = (int)(t % (cout / 8));
+      cc = (int)(t / (cout / 8));
+      co = grp * 8 + r;
+      tap = kc >> 1;
+      half = kc & 1;
+    }
+    const int ch = cc * 16 + half * 8 + e;
+    out[i] = ch < cin ? w[(long long)co * kpad + tap * cin + ch] : __float2bfloat16_rn(0.0f);
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 1;
+  return n;
+}
+
+template <int COUT, int TZ, bool SWZ>
+cudaError_t launch_tile(const nm_conv3d_desc& d, const void* x, const void* w, const float* bias, void* y,
                         int relu, uint32_t* status, cudaStream_t s) {
-  typedef TileLayout<COUT> L;
-  const size_t smem = 2 * (size_t)L::kStage;
-  cudaError_t e = cudaFuncSetAttribute(conv_tile_kernel<COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  typedef TileLayout<COUT, TZ, SWZ> L;
+  const int cin = d.c0;
+  const int nchunks = (cin + 15) / 16;
+  // the input as a 5-D tensor (c, x, y, z, n); boxes of 8 channels x the padded tile
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  CUtensorMap map;
+  const cuuint64_t dims[5] = {(cuuint64_t)cin, (cuuint64_t)d.w, (cuuint64_t)d.h, (cuuint64_t)d.d, (cuuint64_t)d.n};
+  const cuuint64_t strides[4] = {(cuuint64_t)cin * 2, (cuuint64_t)d.w * cin * 2, (cuuint64_t)d.h * d.w * cin * 2,
+                                 (cuuint64_t)d.d * d.h * d.w * cin * 2};
+  const cuuint32_t box[5] = {SWZ ? 16u : 8u, (cuuint32_t)L::PX, (cuuint32_t)L::PY, (cuuint32_t)L::PZ, 1};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(x), dims, strides, box, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, SWZ ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  bf16* wt = nullptr;
+  const size_t welems = (size_t)nchunks * COUT * 432;
+  cudaError_t e = cudaMallocAsync((void**)&wt, welems * sizeof(bf16), s);
   if (e != cudaSuccess) return e;
-  const long long tiles = (long long)((g.w + TX - 1) / TX) * ((g.h + TY - 1) / TY) * ((g.d + TZ - 1) / TZ) * g.n;
-  const int cin = g.c0;
-  conv_tile_kernel<COUT><<<(unsigned)tiles, kThreads, smem, s>>>(g.n, g.d, g.h, g.w, cin, conv_kpad(cin),
-                                                                 (const __nv_bfloat16*)x, (const __nv_bfloat16*)w,
-                                                                 bias, (__nv_bfloat16*)y, relu, status);
-  return cudaGetLastError();
+  tile_weights_kernel<<<(unsigned)std::min<size_t>((welems + 255) / 256, 4096), 256, 0, s>>>(
+      (const bf16*)w, cin, conv_kpad(cin), COUT, nchunks, SWZ ? 1 : 0, wt);
+  TileGrid g;
+  g.n = d.n; g.d = d.d; g.h = d.h; g.w = d.w;
+  g.tiles_x = (d.w + TX - 1) / TX;
+  g.tiles_y = (d.h + TY - 1) / TY;
+  g.tz = TZ;
+  g.tiles_z = (d.d + TZ - 1) / TZ;
+  g.tiles = (long long)g.tiles_x * g.tiles_y * g.tiles_z * g.n;
+  e = cudaFuncSetAttribute(conv_tile_kernel<COUT, TZ, SWZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)L::kSmem);
+  if (e == cudaSuccess) {
+    const long long grid = std::min<long long>(g.tiles, sm_count());
+    conv_tile_kernel<COUT, TZ, SWZ><<<(unsigned)grid, kThreads, L::kSmem, s>>>(map, g, nchunks, wt, bias,
+                                                                                (bf16*)y, relu, status);
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(wt, s);
+  return e;
 }
 
 }  // namespace
 
 bool conv_tile_ok(const nm_conv3d_desc& d) {
-  return d.c1 == 0 && !d.src0_coarse && d.c0 % 8 == 0 && (d.cout == 16 || d.cout == 32);
+  return d.c1 == 0 && !d.src0_coarse && d.c0 % 8 == 0 && (d.cout == 16 || d.cout == 32 || d.cout == 64);
 }
 
 cudaError_t conv3d_fwd_tile(const nm_conv3d_desc& d, const void* x, const void* w, const float* bias, void* y,
                             int relu, uint32_t* status, cudaStream_t s) {
-  if (d.cout == 16) return launch_tile<16>(d, x, w, bias, y, relu, status, s);
-  return launch_tile<32>(d, x, w, bias, y, relu, status, s);
+  constexpr bool kSwz = true;
+  if (d.cout == 16) return launch_tile<16, 4, kSwz>(d, x, w, bias, y, relu, status, s);
+  if (d.cout == 32) return launch_tile<32, 2, kSwz>(d, x, w, bias, y, relu, status, s);
+  return launch_tile<64, 2, kSwz>(d, x, w, bias, y, relu, status, s);
 }
 
 }  // namespace nm

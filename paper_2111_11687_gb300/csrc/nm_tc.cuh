@@ -44,6 +44,35 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return true;
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// One arrival that also expects `bytes` of asynchronous copies to land.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// ---- bulk copies (TMA) ------------------------------------------------------------
+// 5-D tiled tensor load of the tensor map's box at coordinates c0..c4 (c0
+// innermost) into shared memory; completes `bytes` on the mbarrier.
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const void* tmap, uint64_t* bar, int c0, int c1, int c2,
+                                            int c3, int c4) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, "
+      "%6, %7}], [%2];" ::"r"(dst),
+      "l"(tmap), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+      : "memory");
+}
+
+// Contiguous copy of `bytes` (multiple of 16; both addresses 16-byte aligned).
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
 // ---- fences ---------------------------------------------------------------------
 // Generic-proxy shared-memory writes become visible to the tensor cores' async proxy.
 __device__ __forceinline__ void fence_async_smem() {
@@ -79,6 +108,18 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
   d |= (uint64_t)((lbo & 0x3FFFFu) >> 4) << 16;
   d |= (uint64_t)((sbo & 0x3FFFFu) >> 4) << 32;
   d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// K-major operand with 32-byte swizzling: rows of 32 bytes (16 BF16 of K),
+// atoms of 8 rows (stride byte offset between atoms), the 16-byte halves of
+// a row exchanged where the absolute shared-memory address has bit 7 set.
+// The pattern follows the absolute address, so a start address may sit at any
+// 32-byte row inside an atom with the base-offset field left at 0 (checked on
+// the device for shifts of 0-13 rows).
+__device__ __forceinline__ uint64_t smem_desc_sw32(uint32_t saddr, uint32_t sbo) {
+  uint64_t d = smem_desc(saddr, 16, sbo);
+  d |= (uint64_t)6 << 61;
   return d;
 }
 

@@ -15,6 +15,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -280,43 +281,72 @@ __global__ void scatter_box_kernel(const float* __restrict__ y, int cx, int cy, 
   }
 }
 
-// Bounding box [xmin, ymin, zmin, xmax, ymax, zmax] of the body (density >= 0.1).
-__global__ void body_box_kernel(const float* __restrict__ density, int nx, int ny, int nz, int* box) {
-  int lo[3] = {nx, ny, nz}, hi[3] = {-1, -1, -1};
-  const long long V = (long long)nx * ny * nz;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x)
-    if (density[i] >= 0.1f) {
-      const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long long)nx * ny));
-      lo[0] = min(lo[0], x); lo[1] = min(lo[1], y); lo[2] = min(lo[2], z);
-      hi[0] = max(hi[0], x); hi[1] = max(hi[1], y); hi[2] = max(hi[2], z);
-    }
-  for (int a = 0; a < 3; ++a) {
-    lo[a] = __reduce_min_sync(0xffffffffu, lo[a]);
-    hi[a] = __reduce_max_sync(0xffffffffu, hi[a]);
-  }
-  if ((threadIdx.x & 31) == 0)
-    for (int a = 0; a < 3; ++a) {
-      atomicMin(box + a, lo[a]);
-      atomicMax(box + 3 + a, hi[a]);
-    }
-}
-
-// Masked mean of a volume: partial sums per CTA (fixed tree), then one CTA.
-__global__ void masked_mean_partial(const float* __restrict__ a, const float* __restrict__ density, long long n,
-                                    double* __restrict__ part) {
-  __shared__ double sv[256], sc[256];
-  double v = 0.0, c = 0.0;
+// Body statistics in one pass over the volume: per CTA (fixed tree) the sums
+// of dose and activity and the voxel count over the body (density >= 0.1),
+// and (if box) its bounding box [xmin, ymin, zmin, xmax, ymax, zmax], merged
+// with one atomic per CTA and coordinate.
+constexpr int kStatBlocks = 1024;
+__global__ void __launch_bounds__(256) body_stats_kernel(const float* __restrict__ dose, const float* __restrict__ act,
+                                                         const float* __restrict__ density, int nx, int ny, long long n,
+                                                         double* __restrict__ part, int* __restrict__ box) {
+  __shared__ double sd[256], sa[256], sc[256];
+  __shared__ int sb[8][6];
+  double vd = 0.0, va = 0.0, c = 0.0;
+  int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {-1, -1, -1};
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    if (density[i] >= 0.1f) { v += a[i]; c += 1.0; }
-  sv[threadIdx.x] = v;
+    if (density[i] >= 0.1f) {
+      vd += dose[i];
+      va += act[i];
+      c += 1.0;
+      if (box) {
+        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long long)nx * ny));
+        lo[0] = min(lo[0], x); lo[1] = min(lo[1], y); lo[2] = min(lo[2], z);
+        hi[0] = max(hi[0], x); hi[1] = max(hi[1], y); hi[2] = max(hi[2], z);
+      }
+    }
+  sd[threadIdx.x] = vd;
+  sa[threadIdx.x] = va;
   sc[threadIdx.x] = c;
+  if (box) {
+    const int w = threadIdx.x >> 5;
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = __reduce_min_sync(0xffffffffu, lo[a]);
+      hi[a] = __reduce_max_sync(0xffffffffu, hi[a]);
+    }
+    if ((threadIdx.x & 31) == 0)
+      for (int a = 0; a < 3; ++a) {
+        sb[w][a] = lo[a];
+        sb[w][3 + a] = hi[a];
+      }
+  }
   __syncthreads();
   for (int o = 128; o > 0; o >>= 1) {
-    if ((int)threadIdx.x < o) { sv[threadIdx.x] += sv[threadIdx.x + o]; sc[threadIdx.x] += sc[threadIdx.x + o]; }
+    if ((int)threadIdx.x < o) {
+      sd[threadIdx.x] += sd[threadIdx.x + o];
+      sa[threadIdx.x] += sa[threadIdx.x + o];
+      sc[threadIdx.x] += sc[threadIdx.x + o];
+    }
     __syncthreads();
   }
-  if (threadIdx.x == 0) { part[2 * blockIdx.x] = sv[0]; part[2 * blockIdx.x + 1] = sc[0]; }
+  if (threadIdx.x == 0) {
+    part[3 * blockIdx.x] = sd[0];
+    part[3 * blockIdx.x + 1] = sa[0];
+    part[3 * blockIdx.x + 2] = sc[0];
+  }
+  if (box && threadIdx.x < 6) {
+    int v = sb[0][threadIdx.x];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+      v = threadIdx.x < 3 ? min(v, sb[w][threadIdx.x]) : max(v, sb[w][threadIdx.x]);
+    if (threadIdx.x < 3) atomicMin(box + threadIdx.x, v);
+    else atomicMax(box + threadIdx.x, v);
+  }
 }
+
+// Body means of dose and activity (1 where the body is empty or the sum is
+// not positive) and, if box_out, the body's bounding box (xmax < xmin when
+// there is no body).  Synchronises the stream.
+nm_status body_stats(const float* dose, const float* activity, const float* density, int nx, int ny, long long n,
+                     float* dose_scale, float* act_scale, int* box_out, cudaStream_t s);
 
 // Default voxel budget of one inference pass: about 330 bytes of activations
 // per voxel over all levels, so about 11 GB.
@@ -439,6 +469,35 @@ nm_status check_status(nm_denoiser* h) {
     cudaMemsetAsync(h->status, 0, 4, h->s);
     return fail(NM_ERR_DEVICE, "tensor-core wait timed out");
   }
+  return NM_OK;
+}
+
+nm_status body_stats(const float* dose, const float* activity, const float* density, int nx, int ny, long long n,
+                     float* dose_scale, float* act_scale, int* box_out, cudaStream_t s) {
+  double* part = nullptr;
+  int* dbox = nullptr;
+  const size_t pbytes = kStatBlocks * 3 * sizeof(double);
+  CK(cudaMallocAsync((void**)&part, pbytes + 8 * sizeof(int), s), "body statistics");
+  if (box_out) {
+    dbox = (int*)((char*)part + pbytes);
+    const int init[6] = {INT_MAX, INT_MAX, INT_MAX, -1, -1, -1};
+    CK(cudaMemcpyAsync(dbox, init, sizeof init, cudaMemcpyHostToDevice, s), "body statistics");
+  }
+  std::vector<double> r(kStatBlocks * 3);
+  body_stats_kernel<<<kStatBlocks, 256, 0, s>>>(dose, activity, density, nx, ny, n, part, dbox);
+  cudaError_t e = cudaMemcpyAsync(r.data(), part, pbytes, cudaMemcpyDeviceToHost, s);
+  if (!e && box_out) e = cudaMemcpyAsync(box_out, dbox, 6 * sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(part, s);
+  if (!e) e = cudaStreamSynchronize(s);
+  if (e) return cfail(e, "body statistics");
+  double v[2] = {0, 0}, c = 0;
+  for (int b = 0; b < kStatBlocks; ++b) {
+    v[0] += r[3 * b];
+    v[1] += r[3 * b + 1];
+    c += r[3 * b + 2];
+  }
+  *dose_scale = c > 0 && v[0] > 0 ? (float)(v[0] / c) : 1.0f;
+  *act_scale = c > 0 && v[1] > 0 ? (float)(v[1] / c) : 1.0f;
   return NM_OK;
 }
 
@@ -858,26 +917,7 @@ nm_status nm_denoise_make_patches(const float* dose, const float* density, const
 nm_status nm_denoise_scales(const float* dose, const float* activity, const float* density, int64_t n,
                             float* dose_scale, float* act_scale, void* stream) {
   if (!dose || !activity || !density || n <= 0 || !dose_scale || !act_scale) return fail(NM_ERR_ARG, "bad arguments");
-  cudaStream_t s = (cudaStream_t)stream;
-  double* part = nullptr;
-  const int blocks = 1024;
-  CK(cudaMallocAsync((void**)&part, blocks * 2 * sizeof(double), s), "scales");
-  double r[2][2 * 1024];
-  for (int k = 0; k < 2; ++k) {
-    masked_mean_partial<<<blocks, 256, 0, s>>>(k == 0 ? dose : activity, density, n, part);
-    cudaMemcpyAsync(r[k], part, blocks * 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
-  }
-  cudaFreeAsync(part, s);
-  CK(cudaStreamSynchronize(s), "scales");
-  double v[2] = {0, 0}, c = 0;
-  for (int k = 0; k < 2; ++k)
-    for (int b = 0; b < blocks; ++b) {
-      v[k] += r[k][2 * b];
-      if (k == 0) c += r[k][2 * b + 1];
-    }
-  *dose_scale = c > 0 && v[0] > 0 ? (float)(v[0] / c) : 1.0f;
-  *act_scale = c > 0 && v[1] > 0 ? (float)(v[1] / c) : 1.0f;
-  return NM_OK;
+  return body_stats(dose, activity, density, 1, 1, n, dose_scale, act_scale, nullptr, (cudaStream_t)stream);
 }
 
 // Whole-volume inference.  The body's bounding box (density >= 0.1) plus a
@@ -894,18 +934,14 @@ nm_status nm_denoise_apply(nm_denoiser* h, const float* dose, const float* densi
   cudaStream_t s = h->s;
   const long long V = (long long)nx * ny * nz;
   float ds = 1, as = 1;
-  nm_status st = nm_denoise_scales(dose, activity, density, V, &ds, &as, s);
+  int box[6];
+  nm_status st = body_stats(dose, activity, density, nx, ny, V, &ds, &as, box, s);
   if (st != NM_OK) return st;
-  int* dbox = nullptr;
-  int box[6] = {nx, ny, nz, -1, -1, -1};
-  CK(cudaMallocAsync((void**)&dbox, sizeof box, s), "apply");
-  CK(cudaMemcpyAsync(dbox, box, sizeof box, cudaMemcpyHostToDevice, s), "apply");
-  body_box_kernel<<<grid1d(V), 256, 0, s>>>(density, nx, ny, nz, dbox);
-  CK(cudaMemcpyAsync(box, dbox, sizeof box, cudaMemcpyDeviceToHost, s), "apply");
-  cudaFreeAsync(dbox, s);
   if (dose_out != dose) CK(cudaMemcpyAsync(dose_out, dose, V * sizeof(float), cudaMemcpyDeviceToDevice, s), "apply");
-  CK(cudaStreamSynchronize(s), "apply");
-  if (box[3] < box[0]) return NM_OK;  // no body: nothing to denoise
+  if (box[3] < box[0]) {  // no body: nothing to denoise
+    CK(cudaStreamSynchronize(s), "apply");
+    return NM_OK;
+  }
   const int A = 1 << (h->L - 1), mg = 8;
   auto up = [&](int n) { return (n + A - 1) / A * A; };
   const int ex = box[3] + 1 - box[0], ey = box[4] + 1 - box[1], ez = box[5] + 1 - box[2];
