@@ -385,8 +385,9 @@ def denoiser_perf(torch, nm, steps, peaks, vol=None):
         ap_ms = e[0].elapsed_time(e[1]) / steps
         box = infer_box(density)
         fl_box = unet_flops(net.layers(), P, 1) * (box[0] * box[1] * box[2]) / P ** 3
-        out["apply"] = {"volume": list(dose.shape[::-1]), "network_box_zyx": box, "ms": ap_ms,
-                        "tflops": fl_box / (ap_ms * 1e-3) / 1e12}
+        ap_tf = fl_box / (ap_ms * 1e-3) / 1e12
+        out["apply"] = {"volume": list(dose.shape[::-1]), "network_box_zyx": box, "ms": ap_ms, "tflops": ap_tf,
+                        "frac": ap_tf / peak}
     net.close()
     return out
 
@@ -460,6 +461,37 @@ def run_profile(args):
                       "decays_per_s": args.decays / (c["transport_ms"] * 1e-3), "counters": c}))
 
 
+def run_apply(args):
+    """Whole-volume denoiser inference on the benchmark phantom, for ncu: a
+    dose map of --decays decays, then --apply-reps applies of a fresh network
+    (the time does not depend on the weights)."""
+    import torch
+
+    from paper_2111_11687_gb300 import build, inputs, nmdose
+    build.build()
+    ph = _phantom()
+    den = torch.empty(SHAPE, dtype=torch.float32, device="cuda")
+    mat = torch.empty(SHAPE, dtype=torch.uint8, device="cuda")
+    nmdose.nm_ct_to_phantom(torch.from_numpy(ph.hu).cuda(), den, mat)
+    act = torch.from_numpy(ph.activity).cuda()
+    dose = torch.empty(SHAPE, dtype=torch.float32, device="cuda")
+    with nmdose.Dose(den, mat, SPACING, _materials_gpu(nmdose), activity=act, labels=torch.from_numpy(ph.labels).cuda(),
+                     n_labels=inputs.N_LABELS, activity_bq=inputs.ACTIVITY_BQ, **json.loads(args.tuning)) as d:
+        d.run(args.decays, seed=1)
+        nmdose.nm_dose_get(d.h, dose, None, None)
+    net = nmdose.Denoiser(patch=64, batch=4, levels=4, base_width=16, seed=1)
+    out = torch.empty_like(dose)
+    t = []
+    for _ in range(args.apply_reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        net.apply(dose, den, act, out)
+        torch.cuda.synchronize()
+        t.append((time.perf_counter() - t0) * 1e3)
+    net.close()
+    print(json.dumps({"apply_decays": args.decays, "apply_ms": t, "network_box_zyx": infer_box(den)}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -476,6 +508,8 @@ def main():
     ap.add_argument("--profile", action="store_true", help="one short run for ncu")
     ap.add_argument("--decays", type=int, default=200_000_000)
     ap.add_argument("--tuning", default="{}", help="JSON dict of nm_options launch fields (profile mode)")
+    ap.add_argument("--apply-only", action="store_true", help="only whole-volume denoiser inference (for ncu)")
+    ap.add_argument("--apply-reps", type=int, default=1)
     args = ap.parse_args()
     if args.denoiser_only:
         import torch
@@ -485,6 +519,8 @@ def main():
         print(json.dumps(denoiser_perf(torch, nmdose, args.denoiser_steps, _peaks())))
     elif args.profile:
         run_profile(args)
+    elif args.apply_only:
+        run_apply(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
