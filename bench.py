@@ -239,6 +239,7 @@ def run_gpu(args):
     # DRAM bytes per decay from the committed ncu summary, valid only while the
     # kernel source is the one that was profiled.
     traffic = None
+    issue = None
     tp = os.path.join(ROOT, "profiles", "transport_kernel_adult_phantom.md")
     if os.path.exists(tp):
         kv = {}
@@ -248,11 +249,14 @@ def run_gpu(args):
                 kv[k.strip()] = v.strip()
         if kv.get("kernel_source_hash") == _kernel_hash() and "dram_bytes_per_decay" in kv:
             traffic = float(kv["dram_bytes_per_decay"]) * decays_per_launch
+            # what bounds the kernel in that capture: instruction issue, not bytes
+            issue = {k: float(kv[k]) for k in ("issue_active_pct", "lane_efficiency_pct", "warp_inst_per_decay",
+                                               "dram_busy_pct") if k in kv}
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "peak_source": "measured" if peaks else "fallback",
                 "kernel": "transport_kernel", "launch_ms": launch_ms,
-                "bytes_per_decay": bytes_per_decay, "per_decay": per_decay}
+                "bytes_per_decay": bytes_per_decay, "per_decay": per_decay, "ncu_issue": issue}
     dose_map = torch.empty(SHAPE, dtype=torch.float32, device="cuda")
     nmdose.nm_dose_get(d.h, dose_map, None, None)
     d.close()

@@ -78,6 +78,16 @@ struct TileLayout {
   static_assert(kSmem <= 227 * 1024, "shared memory");
 };
 
+// Optional fused 1x1x1 head (16-output layers): instead of the activations,
+// write yh[v] = hb + x[v][0] + sum_c hw[c] * bf16(act[v][c]) (FP32), the same
+// arithmetic, in the same order, as the separate head.
+struct TileHead {
+  const float* hw;        // [16] weights then the bias; NULL = no head
+  const bf16* x;          // network input, cx channels per voxel (channel 0 is added)
+  int cx;
+  float* yh;
+};
+
 struct TileGrid {
   int n, d, h, w, tz, tiles_x, tiles_y, tiles_z;
   long long tiles;
@@ -95,7 +105,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tile_kernel(const __grid_con
                                                                 const bf16* __restrict__ wt,
                                                                 const float* __restrict__ bias,
                                                                 bf16* __restrict__ y, int relu,
-                                                                uint32_t* status) {
+                                                                const TileHead hd, uint32_t* status) {
   typedef TileLayout<COUT, TZ, SWZ> L;
   constexpr int S = L::kStages, NA = L::kNacc;
   constexpr int PX = L::PX, PY = L::PY, kMt = L::kMt, kCmin = L::kCmin, kCmax = L::kCmax;
@@ -220,6 +230,22 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tile_kernel(const __grid_con
         const int gz = z0 + pz - 1, gy = y0 + py - 1, gx = x0 + px - 1;
         const bool ok = c <= kCmax && px >= 1 && px <= TX && py >= 1 && py <= TY && pz >= 1 && pz <= TZ &&
                         gz < g.d && gy < g.h && gx < g.w;
+        const long long vox = (((long long)b * g.d + gz) * g.h + gy) * g.w + gx;
+        if (COUT == 16 && hd.hw) {
+          float v[16];
+          tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + a * L::kAccCols + mt * COUT, v);
+          if (ok) {
+            float out = __ldg(hd.hw + 16) + __bfloat162float(hd.x[vox * hd.cx]);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              float tv = v[j] + (bias ? __ldg(bias + j) : 0.0f);
+              if (relu) tv = fmaxf(tv, 0.0f);
+              out = fmaf(__bfloat162float(__float2bfloat16_rn(tv)), __ldg(hd.hw + j), out);
+            }
+            hd.yh[vox] = out;
+          }
+          continue;
+        }
 #pragma unroll
         for (int cq = 0; cq < COUT / 16; ++cq) {
           float v[16];
@@ -232,8 +258,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tile_kernel(const __grid_con
               if (relu) tv = fmaxf(tv, 0.0f);
               o[j] = __float2bfloat16_rn(tv);
             }
-            uint4* dst = reinterpret_cast<uint4*>(
-                y + ((((long long)b * g.d + gz) * g.h + gy) * g.w + gx) * COUT + cq * 16);
+            uint4* dst = reinterpret_cast<uint4*>(y + vox * COUT + cq * 16);
             dst[0] = reinterpret_cast<uint4*>(o)[0];
             dst[1] = reinterpret_cast<uint4*>(o)[1];
           }
@@ -308,7 +333,7 @@ int sm_count() {
 
 template <int COUT, int TZ, bool SWZ>
 cudaError_t launch_tile(const nm_conv3d_desc& d, const void* x, const void* w, const float* bias, void* y,
-                        int relu, uint32_t* status, cudaStream_t s) {
+                        int relu, const TileHead& hd, uint32_t* status, cudaStream_t s) {
   typedef TileLayout<COUT, TZ, SWZ> L;
   const int cin = d.c0;
   const int nchunks = (cin + 15) / 16;
@@ -344,7 +369,7 @@ cudaError_t launch_tile(const nm_conv3d_desc& d, const void* x, const void* w, c
   if (e == cudaSuccess) {
     const long long grid = std::min<long long>(g.tiles, sm_count());
     conv_tile_kernel<COUT, TZ, SWZ><<<(unsigned)grid, kThreads, L::kSmem, s>>>(map, g, nchunks, wt, bias,
-                                                                                (bf16*)y, relu, status);
+                                                                                (bf16*)y, relu, hd, status);
     e = cudaGetLastError();
   }
   cudaFreeAsync(wt, s);
@@ -360,9 +385,18 @@ bool conv_tile_ok(const nm_conv3d_desc& d) {
 cudaError_t conv3d_fwd_tile(const nm_conv3d_desc& d, const void* x, const void* w, const float* bias, void* y,
                             int relu, uint32_t* status, cudaStream_t s) {
   constexpr bool kSwz = true;
-  if (d.cout == 16) return launch_tile<16, 4, kSwz>(d, x, w, bias, y, relu, status, s);
-  if (d.cout == 32) return launch_tile<32, 2, kSwz>(d, x, w, bias, y, relu, status, s);
-  return launch_tile<64, 2, kSwz>(d, x, w, bias, y, relu, status, s);
+  const TileHead none{nullptr, nullptr, 0, nullptr};
+  if (d.cout == 16) return launch_tile<16, 4, kSwz>(d, x, w, bias, y, relu, none, status, s);
+  if (d.cout == 32) return launch_tile<32, 2, kSwz>(d, x, w, bias, y, relu, none, status, s);
+  return launch_tile<64, 2, kSwz>(d, x, w, bias, y, relu, none, status, s);
+}
+
+cudaError_t conv3d_fwd_tile_head(const nm_conv3d_desc& d, const void* x, const void* w, const float* bias,
+                                 const float* head_w, const void* xin, int cx, float* yh, uint32_t* status,
+                                 cudaStream_t s) {
+  if (d.cout != 16 || !conv_tile_ok(d)) return cudaErrorInvalidValue;
+  const TileHead hd{head_w, (const bf16*)xin, cx, yh};
+  return launch_tile<16, 4, true>(d, x, w, bias, nullptr, 1, hd, status, s);
 }
 
 }  // namespace nm

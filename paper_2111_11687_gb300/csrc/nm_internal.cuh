@@ -212,6 +212,11 @@ cudaError_t conv3d_fwd(const nm_conv3d_desc& d, const void* x0, const void* x1, 
 bool conv_tile_ok(const nm_conv3d_desc& d);
 cudaError_t conv3d_fwd_tile(const nm_conv3d_desc& d, const void* x, const void* w, const float* bias, void* y,
                             int relu, uint32_t* status, cudaStream_t s);
+// The same with the denoiser's 1x1x1 head fused into the epilogue (16
+// outputs, ReLU): yh[v] = head_w[16] + xin[v][0] + sum_c head_w[c] act[v][c].
+cudaError_t conv3d_fwd_tile_head(const nm_conv3d_desc& d, const void* x, const void* w, const float* bias,
+                                 const float* head_w, const void* xin, int cx, float* yh, uint32_t* status,
+                                 cudaStream_t s);
 cudaError_t conv3d_flip_weights(const nm_conv3d_desc& d, const void* w, void* wb, cudaStream_t s);
 cudaError_t conv3d_wgrad(const nm_conv3d_desc& d, const void* x0, const void* x1, const void* dy,
                          float* dw, float* db, void* workspace, uint32_t* status, cudaStream_t s);

@@ -481,7 +481,10 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
       pz = fmaf(s * G.inv_dz, uz, pz);
       ++n_steps;
       ++steps;
-      if (!(px >= 0.0f && px < G.fnx && py >= 0.0f && py < G.fny && pz >= 0.0f && pz < G.fnz)) {
+      // floor once: the same integers test the grid bounds (negative or past
+      // the end, as unsigned) and index the voxel (positions are finite)
+      const int ix = __float2int_rd(px), iy = __float2int_rd(py), iz = __float2int_rd(pz);
+      if ((unsigned)ix >= (unsigned)G.nx || (unsigned)iy >= (unsigned)G.ny || (unsigned)iz >= (unsigned)G.nz) {
         escaped += (ull)qe;
         ++n_esc;
         alive = false;
@@ -490,7 +493,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
         rem = out ? kInf : region_distance(G, false, px, py, pz, ux, uy, uz);
         f.inv_mubar = inv_majorant_at(e, out ? s_minv_out : s_minv, p.ln_e_lo, p.inv_dln_e);
       } else {
-        const int v = ((int)pz * G.ny + (int)py) * G.nx + (int)px;
+        const int v = (iz * G.ny + iy) * G.nx + ix;
         const uint32_t wv = __ldg(G.vox + v);
         const MaterialCoef c = s_mat[wv & 7u];
         // real event with probability mu(voxel)/mubar; the same uniform picks the type

@@ -512,7 +512,11 @@ nm_conv3d_desc single_source(const nm_denoiser* h, const Layer& l) {
 }
 bool use_cat(const nm_denoiser* h, const Layer& l) { return l.c1 > 0 && conv_tile_ok(single_source(h, l)); }
 
-nm_status forward(nm_denoiser* h) {
+// Forward pass.  With fuse_head (inference) the last convolution writes the
+// head's output h->y directly when the shifted-window kernel takes it, and
+// *fused says so (the caller then skips head()).
+nm_status forward(nm_denoiser* h, bool fuse_head = false, bool* fused = nullptr) {
+  if (fused) *fused = false;
   cudaStream_t s = h->s;
   const int L = h->L;
   const bf16* in = h->x_in;
@@ -542,6 +546,13 @@ nm_status forward(nm_denoiser* h) {
     } else {
       CK(conv3d_fwd(h->desc(la), coarse, h->eb[i], h->wb + la.w_off, h->w + la.b_off, h->da[i], 1, h->status, s),
          "conv");
+    }
+    if (i == 0 && fuse_head && lb.cout == 16 && conv_tile_ok(h->desc(lb))) {
+      CK(conv3d_fwd_tile_head(h->desc(lb), h->da[0], h->wb + lb.w_off, h->w + lb.b_off, h->w + h->head_off, h->x_in,
+                              h->cx, h->y, h->status, s),
+         "conv");
+      if (fused) *fused = true;
+      return NM_OK;
     }
     CK(conv3d_fwd(h->desc(lb), h->da[i], nullptr, h->wb + lb.w_off, h->w + lb.b_off, h->db[i], 1, h->status, s), "conv");
     coarse = h->db[i];
@@ -967,8 +978,9 @@ nm_status nm_denoise_apply(nm_denoiser* h, const float* dose, const float* densi
     const long long n = (long long)W * H * D;
     make_patches_kernel<<<grid1d(n), 256, 0, s>>>(dose, density, activity, nullptr, nx, ny, nz, 1.0f / ds, 1.0f / as,
                                                   dcorn, 1, W, H, D, c->x_in, nullptr, nullptr);
-    if ((st = forward(c)) != NM_OK) break;
-    if ((st = head(c, false)) != NM_OK) break;
+    bool fused = false;
+    if ((st = forward(c, true, &fused)) != NM_OK) break;
+    if (!fused && (st = head(c, false)) != NM_OK) break;
     scatter_box_kernel<<<grid1d(n), 256, 0, s>>>(c->y, corner[0], corner[1], corner[2], W, H, D, mg, mg, mg,
                                                  mg + ex, mg + ey, mg + core, nx, ny, nz, ds, dose_out);
     // the corner buffer is reused by the next slab
