@@ -74,6 +74,17 @@ def water_cube(n: int = 64, voxel_cm: float = 0.5) -> WaterCube:
     return WaterCube(den, mat, (voxel_cm,) * 3, (c, c, c))
 
 
+def paper_point_source(n: int = 101, voxel_cm: float = 0.05) -> "Phantom":
+    """The paper's point-source check (§2.2): CT of n^3 voxels all at 0 HU
+    (water), PET zero except the central voxel (default 101^3 voxels of
+    0.5 mm); every decay starts in that voxel."""
+    hu = np.zeros((n, n, n), np.int16)
+    act = np.zeros((n, n, n), np.float32)
+    act[n // 2, n // 2, n // 2] = 1.0
+    lab = np.zeros((n, n, n), np.uint8)
+    return Phantom(hu, act, lab, (voxel_cm,) * 3)
+
+
 @dataclass
 class Phantom:
     hu: np.ndarray          # int16 [nz,ny,nx]
