@@ -334,6 +334,13 @@ nm_status nm_denoise_scales(const float* dose, const float* activity, const floa
 nm_status nm_denoise_apply(nm_denoiser* h, const float* dose, const float* density, const float* activity,
                            int32_t nx, int32_t ny, int32_t nz, float* dose_out);
 
+/* The same over the bounding box of the non-zero voxels of roi (device
+ * uint8 [nz][ny][nx], e.g. the organ label map; NULL = the body) plus the 8
+ * voxels of context; the scales are still the body means.  Outside that box
+ * dose_out keeps the input. */
+nm_status nm_denoise_apply_roi(nm_denoiser* h, const float* dose, const float* density, const float* activity,
+                               const uint8_t* roi, int32_t nx, int32_t ny, int32_t nz, float* dose_out);
+
 /* ---- Tally without device allocation ---------------------------------------
  *
  * For callers that cannot call cudaMalloc -- code running inside another

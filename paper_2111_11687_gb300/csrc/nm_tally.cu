@@ -51,7 +51,8 @@ __global__ void __launch_bounds__(kFoldThreads) fold_kernel(const FoldParams p) 
     dep += t;
     if (p.labels) {
       const int l = p.labels[v];
-      acc[l][threadIdx.x] += x * (p.gy_per_unit_vol / (double)p.density[v]);
+      // Gy per unit in FP32 (GB300's FP64 divide is slow); the sum stays FP64
+      acc[l][threadIdx.x] += x * (double)__fdiv_rn((float)p.gy_per_unit_vol, p.density[v]);
     }
   }
   // deposited-energy counter (integer, so the order of the adds does not matter)
@@ -88,22 +89,30 @@ __global__ void __launch_bounds__(kFoldThreads) finalize_kernel(const FinalizePa
   for (int l = 0; l < kLabelSlots; ++l) acc_d[l][threadIdx.x] = acc_e[l][threadIdx.x] = 0.0;
   const int64_t v0 = (int64_t)blockIdx.x * kFoldTile;
   const int64_t v1 = v0 + kFoldTile < p.V ? v0 + kFoldTile : p.V;
+  // FP64 where cancellation needs it (the variance: S2 - Tsum^2/N) and in the
+  // organ sums; the rest in FP32, whose precision the FP32 outputs have anyway
+  // (GB300's FP64 rate is a small fraction of its FP32 rate).
   const double inv_n = 1.0 / p.n_total;
   const double inv_k1n = 1.0 / ((p.n_batches - 1.0) * p.n_total);
+  const float gy_a = (float)(p.gy_per_unit_vol * p.activity_bq);
   for (int64_t v = v0 + threadIdx.x; v < v1; v += kFoldThreads) {
-    const double t = (double)p.tsum[v];
-    const double mean = t * inv_n;                         // units per decay
-    const double var = fmax(p.s2[v] - t * mean, 0.0) * inv_k1n;
-    const double conv = p.gy_per_unit_vol / (double)p.density[v] * p.activity_bq;
-    const double d = mean * conv;                          // Eq. 1, Gy/s
-    const double sg = sqrt(var) * conv;
-    if (p.dose) p.dose[v] = (float)d;
-    if (p.sigma) p.sigma[v] = (float)sg;
+    const ull ti = p.tsum[v];
+    float d = 0.0f, sg = 0.0f;
+    if (ti) {
+      const double t = (double)ti;
+      const double mean = t * inv_n;                       // units per decay
+      const double var = fmax(fma(-t, mean, p.s2[v]), 0.0) * inv_k1n;
+      const float conv = __fdiv_rn(gy_a, p.density[v]);
+      d = (float)mean * conv;                              // Eq. 1, Gy/s
+      sg = sqrtf((float)var) * conv;
+    }
+    if (p.dose) p.dose[v] = d;
+    if (p.sigma) p.sigma[v] = sg;
     if (p.labels) {
       const int l = p.labels[v];
-      acc_d[l][threadIdx.x] += d;
-      const double eps = d > 0.0 ? sg / d : 1.0;
-      acc_e[l][threadIdx.x] += eps * eps;
+      acc_d[l][threadIdx.x] += (double)d;
+      const float eps = d > 0.0f ? __fdiv_rn(sg, d) : 1.0f;
+      acc_e[l][threadIdx.x] += (double)(eps * eps);
     }
   }
   if (!p.labels) return;

@@ -287,23 +287,26 @@ __global__ void scatter_box_kernel(const float* __restrict__ y, int cx, int cy, 
 // with one atomic per CTA and coordinate.
 constexpr int kStatBlocks = 1024;
 __global__ void __launch_bounds__(256) body_stats_kernel(const float* __restrict__ dose, const float* __restrict__ act,
-                                                         const float* __restrict__ density, int nx, int ny, long long n,
+                                                         const float* __restrict__ density,
+                                                         const uint8_t* __restrict__ roi, int nx, int ny, long long n,
                                                          double* __restrict__ part, int* __restrict__ box) {
   __shared__ double sd[256], sa[256], sc[256];
   __shared__ int sb[8][6];
   double vd = 0.0, va = 0.0, c = 0.0;
   int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {-1, -1, -1};
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    if (density[i] >= 0.1f) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const bool body = density[i] >= 0.1f;
+    if (body) {
       vd += dose[i];
       va += act[i];
       c += 1.0;
-      if (box) {
-        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long long)nx * ny));
-        lo[0] = min(lo[0], x); lo[1] = min(lo[1], y); lo[2] = min(lo[2], z);
-        hi[0] = max(hi[0], x); hi[1] = max(hi[1], y); hi[2] = max(hi[2], z);
-      }
     }
+    if (box && (roi ? roi[i] != 0 : body)) {
+      const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long long)nx * ny));
+      lo[0] = min(lo[0], x); lo[1] = min(lo[1], y); lo[2] = min(lo[2], z);
+      hi[0] = max(hi[0], x); hi[1] = max(hi[1], y); hi[2] = max(hi[2], z);
+    }
+  }
   sd[threadIdx.x] = vd;
   sa[threadIdx.x] = va;
   sc[threadIdx.x] = c;
@@ -343,10 +346,11 @@ __global__ void __launch_bounds__(256) body_stats_kernel(const float* __restrict
 }
 
 // Body means of dose and activity (1 where the body is empty or the sum is
-// not positive) and, if box_out, the body's bounding box (xmax < xmin when
-// there is no body).  Synchronises the stream.
-nm_status body_stats(const float* dose, const float* activity, const float* density, int nx, int ny, long long n,
-                     float* dose_scale, float* act_scale, int* box_out, cudaStream_t s);
+// not positive) and, if box_out, the bounding box of the body, or of the
+// non-zero voxels of roi when given (xmax < xmin when empty).  Synchronises
+// the stream.
+nm_status body_stats(const float* dose, const float* activity, const float* density, const uint8_t* roi, int nx,
+                     int ny, long long n, float* dose_scale, float* act_scale, int* box_out, cudaStream_t s);
 
 // Default voxel budget of one inference pass: about 330 bytes of activations
 // per voxel over all levels, so about 11 GB.
@@ -472,8 +476,8 @@ nm_status check_status(nm_denoiser* h) {
   return NM_OK;
 }
 
-nm_status body_stats(const float* dose, const float* activity, const float* density, int nx, int ny, long long n,
-                     float* dose_scale, float* act_scale, int* box_out, cudaStream_t s) {
+nm_status body_stats(const float* dose, const float* activity, const float* density, const uint8_t* roi, int nx,
+                     int ny, long long n, float* dose_scale, float* act_scale, int* box_out, cudaStream_t s) {
   double* part = nullptr;
   int* dbox = nullptr;
   const size_t pbytes = kStatBlocks * 3 * sizeof(double);
@@ -484,7 +488,7 @@ nm_status body_stats(const float* dose, const float* activity, const float* dens
     CK(cudaMemcpyAsync(dbox, init, sizeof init, cudaMemcpyHostToDevice, s), "body statistics");
   }
   std::vector<double> r(kStatBlocks * 3);
-  body_stats_kernel<<<kStatBlocks, 256, 0, s>>>(dose, activity, density, nx, ny, n, part, dbox);
+  body_stats_kernel<<<kStatBlocks, 256, 0, s>>>(dose, activity, density, roi, nx, ny, n, part, dbox);
   cudaError_t e = cudaMemcpyAsync(r.data(), part, pbytes, cudaMemcpyDeviceToHost, s);
   if (!e && box_out) e = cudaMemcpyAsync(box_out, dbox, 6 * sizeof(int), cudaMemcpyDeviceToHost, s);
   cudaFreeAsync(part, s);
@@ -928,7 +932,7 @@ nm_status nm_denoise_make_patches(const float* dose, const float* density, const
 nm_status nm_denoise_scales(const float* dose, const float* activity, const float* density, int64_t n,
                             float* dose_scale, float* act_scale, void* stream) {
   if (!dose || !activity || !density || n <= 0 || !dose_scale || !act_scale) return fail(NM_ERR_ARG, "bad arguments");
-  return body_stats(dose, activity, density, 1, 1, n, dose_scale, act_scale, nullptr, (cudaStream_t)stream);
+  return body_stats(dose, activity, density, nullptr, 1, 1, n, dose_scale, act_scale, nullptr, (cudaStream_t)stream);
 }
 
 // Whole-volume inference.  The body's bounding box (density >= 0.1) plus a
@@ -938,18 +942,23 @@ nm_status nm_denoise_scales(const float* dose, const float* activity, const floa
 // input.
 nm_status nm_denoise_apply(nm_denoiser* h, const float* dose, const float* density, const float* activity,
                            int32_t nx, int32_t ny, int32_t nz, float* dose_out) {
+  return nm_denoise_apply_roi(h, dose, density, activity, nullptr, nx, ny, nz, dose_out);
+}
+
+nm_status nm_denoise_apply_roi(nm_denoiser* h, const float* dose, const float* density, const float* activity,
+                               const uint8_t* roi, int32_t nx, int32_t ny, int32_t nz, float* dose_out) {
   if (!h || !dose || !density || !activity || !dose_out || nx <= 0 || ny <= 0 || nz <= 0)
     return fail(NM_ERR_ARG, "bad arguments");
-  if (!dev_ptr(dose) || !dev_ptr(density) || !dev_ptr(activity) || !dev_ptr(dose_out))
+  if (!dev_ptr(dose) || !dev_ptr(density) || !dev_ptr(activity) || !dev_ptr(dose_out) || (roi && !dev_ptr(roi)))
     return fail(NM_ERR_ARG, "volumes must be device pointers");
   cudaStream_t s = h->s;
   const long long V = (long long)nx * ny * nz;
   float ds = 1, as = 1;
   int box[6];
-  nm_status st = body_stats(dose, activity, density, nx, ny, V, &ds, &as, box, s);
+  nm_status st = body_stats(dose, activity, density, roi, nx, ny, V, &ds, &as, box, s);
   if (st != NM_OK) return st;
   if (dose_out != dose) CK(cudaMemcpyAsync(dose_out, dose, V * sizeof(float), cudaMemcpyDeviceToDevice, s), "apply");
-  if (box[3] < box[0]) {  // no body: nothing to denoise
+  if (box[3] < box[0]) {  // no body (or empty region): nothing to denoise
     CK(cudaStreamSynchronize(s), "apply");
     return NM_OK;
   }

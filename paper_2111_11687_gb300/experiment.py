@@ -139,12 +139,14 @@ def time_to_target(case, ref, step_decays, max_decays, target, seed):
         return None, n, float(err.max())
 
 
-def time_to_target_denoised(case, net, ref, counts, step_decays, max_decays, target, seed):
+def time_to_target_denoised(case, net, ref, counts, step_decays, max_decays, target, seed, organ_roi=True):
     """MC + denoiser: wall time and decays until the denoised map puts every
     organ within target of ref.  Each checkpoint adds step_decays decays to the
     same run, denoises the whole accumulated map and checks it, so a case the
     network cannot bring within target at the first checkpoint falls back to
-    more Monte Carlo.  Also returns the errors at the first checkpoint."""
+    more Monte Carlo.  With organ_roi the network runs on the organs' bounding
+    box (the label map) instead of the whole body: only organ doses are
+    judged.  Also returns the errors at the first checkpoint."""
     torch, nm = case.torch, case.nm
     raw = torch.empty(case.shape, dtype=torch.float32, device="cuda")
     den = torch.empty_like(raw)
@@ -157,7 +159,7 @@ def time_to_target_denoised(case, net, ref, counts, step_decays, max_decays, tar
             d.run(step_decays, seed)
             n += step_decays
             nm.nm_dose_get(d.h, raw, None, None)
-            net.apply(raw, case.density, case.activity, den)
+            net.apply(raw, case.density, case.activity, den, roi=case.labels if organ_roi else None)
             err = organ_error(d.map_organs(den), ref, counts)
             if first is None:
                 # the undenoised error is for the record only: its time is not counted
@@ -172,7 +174,7 @@ def time_to_target_denoised(case, net, ref, counts, step_decays, max_decays, tar
 
 
 def run(train_n=200, test_n=20, shape=(300, 256, 256), spacing=(0.2, 0.2, 0.3), low=int(1e7), high=int(1e9),
-        ref=int(1e10), denoise_low=int(1e7), steps=3000, patch=64, batch=4, lr=1e-3, workers=None,
+        ref=int(1e10), denoise_low=int(1e7), steps=10000, patch=64, batch=4, lr=1e-3, workers=None,
         step_decays=int(5e6), max_decays=int(2e9), seed0=1000, log_every=0):
     # the pool is started (first next()) before any GPU work
     phantoms = make_phantoms(list(range(seed0, seed0 + train_n + test_n)), shape, spacing, workers)
@@ -241,7 +243,7 @@ def main():
     ap.add_argument("--high", type=float, default=1e9)
     ap.add_argument("--ref", type=float, default=1e10)
     ap.add_argument("--denoise-low", type=float, default=1e7)
-    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--steps", type=int, default=10000)
     ap.add_argument("--patch", type=int, default=64)
     ap.add_argument("--batch", type=int, default=4)
     ap.add_argument("--lr", type=float, default=1e-3)

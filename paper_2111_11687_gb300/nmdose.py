@@ -119,6 +119,8 @@ _SIGS = {
                                     C.POINTER(C.c_float), C.c_void_p]),
     "nm_denoise_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
                                    C.c_int32, C.c_void_p]),
+    "nm_denoise_apply_roi": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
+                                       C.c_int32, C.c_int32, C.c_void_p]),
     "nm_dose_tally_noalloc": (C.c_int, [C.POINTER(nm_grid), C.POINTER(nm_materials), C.c_void_p,
                                         C.POINTER(nm_options), C.c_uint64, C.c_uint64, C.c_void_p,
                                         C.POINTER(nm_counters)]),
@@ -371,9 +373,13 @@ class Denoiser:
     def forward(self, x, y):
         _check(load().nm_denoise_forward(self.h, ptr(x), ptr(y)))
 
-    def apply(self, dose, density, activity, out):
+    def apply(self, dose, density, activity, out, roi=None):
         nz, ny, nx = dose.shape
-        _check(load().nm_denoise_apply(self.h, ptr(dose), ptr(density), ptr(activity), nx, ny, nz, ptr(out)))
+        if roi is None:
+            _check(load().nm_denoise_apply(self.h, ptr(dose), ptr(density), ptr(activity), nx, ny, nz, ptr(out)))
+        else:
+            _check(load().nm_denoise_apply_roi(self.h, ptr(dose), ptr(density), ptr(activity), ptr(roi), nx, ny, nz,
+                                               ptr(out)))
 
     def close(self):
         if self.h:

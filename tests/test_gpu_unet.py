@@ -224,3 +224,37 @@ def test_apply_whole_volume_matches_oracle(env, budget):
     rel = np.linalg.norm(o[inside] - exp[inside]) / np.linalg.norm(exp[inside])
     assert rel < 2e-2, rel
     assert np.array_equal(o[~inside], dose[~inside])
+
+
+def test_apply_roi_matches_oracle(env):
+    """Inference over a region of interest (an organ-like label block inside
+    the body): the network box is that region's bounding box plus 8 voxels of
+    context, the scales stay the body means; outside the box the input stays."""
+    torch, nm, dn = env
+    rng = np.random.default_rng(12)
+    shape = (20, 28, 36)
+    body = ((2, 18), (3, 25), (4, 33))
+    dose, den, act = _volume(rng, shape, body)
+    roi = np.zeros(shape, np.uint8)
+    (rz0, rz1), (ry0, ry1), (rx0, rx1) = (6, 11), (9, 17), (12, 20)
+    roi[rz0:rz1, ry0:ry1, rx0:rx1] = 3
+    net, flat, layers = _random_net(torch, nm, 6)
+    names = [n for n, _, _ in dn.unet_layers(8, (16, 32, 64, 128))]
+    params = to_oracle(flat, layers, (16, 32, 64, 128), names)
+    out = torch.empty(shape, dtype=torch.float32, device="cuda")
+    net.apply(torch.from_numpy(dose).cuda(), torch.from_numpy(den).cuda(), torch.from_numpy(act).cuda(), out,
+              roi=torch.from_numpy(roi).cuda())
+    o = out.cpu().numpy()
+    net.close()
+    m = den >= 0.1
+    s = np.float32(dose[m].astype(np.float64).mean())
+    a = np.float32(act[m].astype(np.float64).mean())
+    up = lambda n: (n + 7) // 8 * 8
+    W, H, D = up(rx1 - rx0 + 16), up(ry1 - ry0 + 16), up(rz1 - rz0 + 16)
+    y = _oracle_box(torch, dn, params, dose, den, act, s, a, (rx0 - 8, ry0 - 8, rz0 - 8), (W, H, D))
+    inside = np.zeros(shape, bool)
+    inside[rz0:rz1, ry0:ry1, rx0:rx1] = True
+    exp = s * y[8:8 + rz1 - rz0, 8:8 + ry1 - ry0, 8:8 + rx1 - rx0]
+    rel = np.linalg.norm(o[inside] - exp.ravel()) / np.linalg.norm(exp)
+    assert rel < 2e-2, rel
+    assert np.array_equal(o[~inside], dose[~inside])
