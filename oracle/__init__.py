@@ -100,7 +100,7 @@ def _load():
         lib.orc_rotate.restype = None
         lib.orc_rotate.argtypes = [p(d), d, d]
         lib.orc_run.restype = C.c_int
-        lib.orc_run.argtypes = [p(_Problem), p(C.c_int64), p(d), p(d), p(d), p(d), p(d), p(_Counters)]
+        lib.orc_run.argtypes = [p(_Problem), p(C.c_int64), p(d), p(d), p(d), p(d), p(d), p(_Counters), p(d)]
         _lib = lib
     return _lib
 
@@ -211,16 +211,19 @@ class Result:
     organ_eps: np.ndarray    # [n_labels+1] relative, Eq. 3
     organ_sigma: np.ndarray  # [n_labels+1] Gy/s, batch sigma of the organ mean
     counters: dict
+    sigma_history: np.ndarray = None  # Gy/s, history-by-history sigma of the mean (if asked for)
 
 
 def run(density, material, mat: Materials, *, activity=None, labels=None, n_labels: int = 0,
         spacing=(1.0, 1.0, 1.0), point=None, photon_mev: float = 0.511, positron_mev: float = 0.25,
         n_hist: int, seed: int = 1, batches: int = 10, threads: int = 0, first_history: int = 0,
-        activity_bq: float = 1.0) -> Result:
+        activity_bq: float = 1.0, history_sigma: bool = False) -> Result:
     """Run the oracle MC.  Arrays are [nz, ny, nx] (x fastest); spacing (dx, dy, dz) in cm.
 
     ``point`` (cm, xyz) selects point-photon mode (one photon per history);
-    otherwise decays are drawn from ``activity``.
+    otherwise decays are drawn from ``activity``.  ``history_sigma`` also
+    returns the history-by-history sigma of the mean dose rate (Walters et al.
+    2002: the spread of each history's total deposit per voxel).
     """
     lib = _load()
     density = np.ascontiguousarray(density, np.float64)
@@ -255,12 +258,13 @@ def run(density, material, mat: Materials, *, activity=None, labels=None, n_labe
     nl = n_labels + 1
     om, oe, os_ = (np.zeros(nl), np.zeros(nl), np.zeros(nl))
     cnt = _Counters()
+    sh = np.empty(density.shape, np.float64) if history_sigma else None
     rc = lib.orc_run(C.byref(pr), tally.ctypes.data_as(C.POINTER(C.c_int64)), _dp(dr), _dp(sg),
-                     _dp(om), _dp(oe), _dp(os_), C.byref(cnt))
+                     _dp(om), _dp(oe), _dp(os_), C.byref(cnt), _dp(sh) if sh is not None else None)
     if rc != 0:
         raise ValueError(f"orc_run failed with code {rc}")
     counters = {n: getattr(cnt, n) for n, _ in _Counters._fields_}
-    return Result(tally, dr, sg, om, oe, os_, counters)
+    return Result(tally, dr, sg, om, oe, os_, counters, sh)
 
 
 def rel_diff_percent(test, ref):

@@ -23,7 +23,9 @@
 //   * tallies: int64 fixed point, one unit = 2^-6 eV, every deposit a difference
 //     q(E_before) - q(E_after) so that energy conservation is exact;
 //   * statistics: batch means over B batches, Eq. 1 dose rate, Eq. 2 organ means,
-//     Eq. 3 organ RMS relative uncertainty, batch sigma of the organ means.
+//     Eq. 3 organ RMS relative uncertainty, batch sigma of the organ means; and,
+//     on request, the history-by-history sigma (§2.1's method, Walters et al.
+//     2002): each history's total deposit per voxel is squared and summed.
 //
 // Functions that no closed form or invariant pins are marked "parity unpinned"
 // at their definition (none at present).
@@ -367,7 +369,8 @@ typedef struct {
 } orc_counters;
 
 int orc_run(const orc_problem* pr, int64_t* tally_sum, double* dose_rate, double* sigma,
-            double* organ_mean, double* organ_eps, double* organ_sigma, orc_counters* out_c) {
+            double* organ_mean, double* organ_eps, double* organ_sigma, orc_counters* out_c,
+            double* sigma_history) {
   const int64_t V = (int64_t)pr->nx * pr->ny * pr->nz;
   if (V <= 0 || pr->batches < 2 || pr->n_hist < (uint64_t)pr->batches) return 1;
   if (pr->mat.n < 1 || pr->mat.n > 64) return 1;
@@ -406,12 +409,35 @@ int orc_run(const orc_problem* pr, int64_t* tally_sum, double* dose_rate, double
   struct Counters {
     int64_t emitted = 0, deposited = 0, escaped = 0, crossings = 0, flights = 0, compton = 0,
             photo = 0, rayleigh = 0, cutoff = 0, escapes = 0;
+    std::vector<std::pair<int64_t, int64_t>> hist;   // this history's (voxel, units) so far
   };
   std::vector<Counters> tc(nthreads);
+  // History-by-history statistics (Walters et al. 2002): per voxel the sum over
+  // histories of the square of each history's total deposit.
+  std::vector<double> s2h(sigma_history ? V : 0, 0.0);
 
   auto deposit = [&](int64_t v, int64_t dq, Counters& c) {
     __atomic_fetch_add(&tb[v], dq, __ATOMIC_RELAXED);
     c.deposited += dq;
+    if (sigma_history) {
+      bool found = false;
+      for (auto& e : c.hist)
+        if (e.first == v) { e.second += dq; found = true; break; }
+      if (!found) c.hist.emplace_back(v, dq);
+    }
+  };
+  // End of a history: its per-voxel totals enter the sums of squares.
+  auto end_history = [&](Counters& c) {
+    for (const auto& e : c.hist) {
+      const double t2 = (double)e.second * (double)e.second;
+      double* slot = &s2h[e.first];
+      double old, upd;
+      __atomic_load(slot, &old, __ATOMIC_RELAXED);
+      do {
+        upd = old + t2;
+      } while (!__atomic_compare_exchange(slot, &old, &upd, true, __ATOMIC_RELAXED, __ATOMIC_RELAXED));
+    }
+    c.hist.clear();
   };
 
   // Transport of one photon from p along dir with energy e (§2.1).
@@ -529,6 +555,7 @@ int orc_run(const orc_problem* pr, int64_t* tally_sum, double* dose_rate, double
             const double d2[3] = {-d[0], -d[1], -d[2]};
             transport(r, p, d2, c);
           }
+          if (sigma_history) end_history(c);
         }
       }
     };
@@ -565,6 +592,11 @@ int orc_run(const orc_problem* pr, int64_t* tally_sum, double* dose_rate, double
     const double sg = std::sqrt(var) * to_gy * pr->activity_bq;
     if (dose_rate) dose_rate[v] = dr;
     if (sigma) sigma[v] = sg;
+    if (sigma_history) {
+      // sample variance of the per-history totals, then sigma of their mean
+      const double var_h = std::max(0.0, s2h[v] / N - mean * mean) * N / (N - 1.0);
+      sigma_history[v] = std::sqrt(var_h / N) * to_gy * pr->activity_bq;
+    }
     if (pr->labels) {
       const int l = pr->labels[v];
       organ_count[l] += 1;

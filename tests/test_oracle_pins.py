@@ -418,3 +418,39 @@ def test_eq4_reproduces_table1(orc):
     assert au.min() == summ["archer_unc_min"] and au.max() == summ["archer_unc_max"]
     # Sign convention: test above reference -> positive.
     assert orc.rel_diff_percent(2.0, 1.0) == 100.0
+
+
+@pytest.mark.parametrize("absorb", [False, True])
+def test_history_sigma_bernoulli_closed_form(orc, absorb):
+    # Every history deposits a fixed amount T in its decay voxel and nothing
+    # elsewhere, so voxel v's per-history total is T with probability p_v and 0
+    # otherwise: the sample variance of the history totals is exactly
+    # T^2 p(1 - p) N / (N - 1) with p the observed fraction, and the
+    # history-by-history sigma of the mean over the mean is
+    # sqrt((1 - p) / ((N - 1) p)).
+    #   absorb=False: a near-vacuum (photons escape), T = the positron energy;
+    #   absorb=True: a dense photoelectric absorber, T = positron + two photons,
+    #   deposited in three pieces: squaring the pieces instead of their sum
+    #   would give a different answer.
+    rng = np.random.default_rng(4)
+    shape = (4, 4, 4)
+    act = rng.uniform(0.2, 1.0, shape)
+    if absorb:
+        den = np.full(shape, 10.0)
+        mat = orc.Materials(z_over_a=[0.0], zeff=[7.42], pe_coeff=1e3)
+    else:
+        den = np.full(shape, 1e-9)
+        mat = orc.Materials(z_over_a=[0.5551], zeff=[7.42])
+    N = 400_000
+    r = orc.run(den, np.zeros(shape, np.uint8), mat, activity=act, spacing=(1.0, 1.0, 1.0), n_hist=N, seed=9,
+                batches=10, history_sigma=True)
+    q_pos = round(0.25 * 6.4e7)
+    T = q_pos + (2 * round(0.511 * 6.4e7) if absorb else 0)
+    assert r.counters["deposited"] == N * T          # every history deposits T, and only in one voxel
+    p = r.tally / (T * N)
+    assert np.allclose(p * T * N, r.tally)
+    expect = np.sqrt((1 - p) / ((N - 1) * p))
+    assert np.allclose(r.sigma_history / r.dose_rate, expect, rtol=1e-9, atol=0)
+    # the batch sigma estimates the same quantity, with ~25 % scatter at 10 batches
+    ratio = r.sigma / r.sigma_history
+    assert 0.85 < np.median(ratio) < 1.15
