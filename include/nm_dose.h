@@ -94,6 +94,9 @@ typedef struct {
                                 new-history pass before it runs (1..32); 0 = auto */
   int32_t max_steps;         /* per-photon flight-step limit (bounded loops) */
   void* stream;              /* cudaStream_t; NULL = legacy default stream */
+  int32_t history_sigma;     /* 1: also keep history-by-history statistics (the paper's
+                                uncertainty method, §2.1; +16 B per voxel, no warp
+                                aggregation); read with nm_dose_get_history_sigma */
 } nm_options;
 
 typedef struct {
@@ -109,6 +112,8 @@ typedef struct {
   double fold_ms;            /* device time of the batch folds */
   uint32_t device_status;    /* OR of NM_DEV_* flags seen */
   int32_t block_threads, chunk, warp_aggregate, regroup, regroup_lanes, grid_blocks; /* tuning used */
+  uint64_t history_splits;   /* history_sigma: histories whose deposits touched more voxels
+                                than a lane keeps (their totals were squared in parts) */
 } nm_counters;
 
 #define NM_DEV_STEP_LIMIT 1u   /* a photon hit max_steps */
@@ -184,6 +189,15 @@ nm_status nm_dose_map_organs(nm_dose* h, const float* dose, double* mean);
 
 /* Exact cumulative tally, int64 energy units per voxel, into tally[V]. */
 nm_status nm_dose_get_tally(nm_dose* h, int64_t* tally);
+
+/* History-by-history sigma of the mean dose rate (Gy/s, [V], host or device),
+ * §2.1's method (Walters et al. 2002): every history's total deposit per voxel
+ * is squared into an exact 128-bit integer sum, and
+ *   sigma = sqrt((S2/N - (T/N)^2) / (N - 1)) in dose-rate units.
+ * Needs a handle created with history_sigma = 1 (else NM_ERR_STATE).  A
+ * history that deposits in more than 16 voxels has its totals squared in
+ * parts (counted in nm_counters.history_splits). */
+nm_status nm_dose_get_history_sigma(nm_dose* h, float* sigma);
 
 /* Counters and the launch shape in use. */
 nm_status nm_dose_counters(nm_dose* h, nm_counters* c);

@@ -96,6 +96,8 @@ struct nm_dose {
   float* kn = nullptr;
   float* minv = nullptr;
   float* minv_out = nullptr;
+  ull* s2h_lo = nullptr;       // history statistics (history_sigma): 128-bit sums of squares
+  ull* s2h_hi = nullptr;
   ull* counters = nullptr;     // kCtrCount
   unsigned* work = nullptr;
   uint32_t* status = nullptr;
@@ -121,7 +123,7 @@ struct nm_dose {
   double batch_graph_ms = 0;      // device time of graphs launched by nm_dose_run_batch
 
   ~nm_dose() {
-    void* ptrs[] = {vox, density, labels, alias, tb, tsum, s2, kn, minv, minv_out, counters, work, status,
+    void* ptrs[] = {vox, density, labels, alias, tb, tsum, s2, kn, minv, minv_out, s2h_lo, s2h_hi, counters, work, status,
                     rho_max_bits, org_s1, org_s2, organ_count, organ_partial, organ_out,
                     out_dose, out_sigma};
     for (void* p : ptrs)
@@ -161,6 +163,8 @@ struct nm_dose {
     p.kn = kn;
     p.minv = minv;
     p.minv_out = minv_out;
+    p.s2h_lo = s2h_lo;
+    p.s2h_hi = s2h_hi;
     p.key0 = (uint32_t)seed;
     p.key1 = (uint32_t)(seed >> 32);
     p.e0 = e0;
@@ -262,7 +266,8 @@ static std::mutex g_tune_mu;
 static std::map<TuneKey, Shape> g_tune_cache;
 
 static int grid_for_shape(const nm_dose* h, const Shape& sh, bool multi) {
-  const int per_sm = transport_max_blocks_per_sm(sh.block, sh.warp_agg, h->rayleigh, sh.regroup, multi);
+  const int per_sm = transport_max_blocks_per_sm(sh.block, sh.warp_agg, h->rayleigh, sh.regroup, multi,
+                                                 !multi && h->opt.history_sigma != 0);
   return per_sm * h->sms;
 }
 
@@ -304,7 +309,9 @@ static nm_status autotune(nm_dose* h, Shape sh, bool free_block, bool free_chunk
     TransportParams p = h->params(first, n_trial, 0x7475u);
     NM_CUDA(cudaMemsetAsync(h->work, 0, sizeof(unsigned), s), "autotune");
     NM_CUDA(cudaEventRecord(e0, s), "autotune");
-    NM_CUDA(launch_transport(p, h->grid, h->block, h->warp_agg, h->rayleigh, h->regroup, s), "autotune");
+    NM_CUDA(launch_transport(p, h->grid, h->block, h->warp_agg, h->rayleigh, h->regroup, s, false,
+                             h->opt.history_sigma != 0),
+            "autotune");
     NM_CUDA(cudaEventRecord(e1, s), "autotune");
     NM_CUDA(cudaEventSynchronize(e1), "autotune");
     NM_CUDA(cudaEventElapsedTime(ms, e0, e1), "autotune");
@@ -348,6 +355,10 @@ static nm_status autotune(nm_dose* h, Shape sh, bool free_block, bool free_chunk
   NM_CUDA(cudaMemsetAsync(h->tb, 0, h->V * sizeof(ull), s), "autotune");
   NM_CUDA(cudaMemsetAsync(h->counters, 0, kCtrCount * sizeof(ull), s), "autotune");
   NM_CUDA(cudaMemsetAsync(h->status, 0, sizeof(uint32_t), s), "autotune");
+  if (h->s2h_lo) {
+    NM_CUDA(cudaMemsetAsync(h->s2h_lo, 0, h->V * sizeof(ull), s), "autotune");
+    NM_CUDA(cudaMemsetAsync(h->s2h_hi, 0, h->V * sizeof(ull), s), "autotune");
+  }
   NM_CUDA(cudaStreamSynchronize(s), "autotune");
   std::lock_guard<std::mutex> lock(g_tune_mu);
   g_tune_cache[key] = sh;
@@ -366,11 +377,16 @@ static nm_status choose_shape(nm_dose* h) {
   // A point source concentrates deposits near the source, where lanes of a
   // warp often hit the same voxel; a spread-out source rarely does.
   sh.warp_agg = o.warp_aggregate >= 0 ? (o.warp_aggregate != 0) : (o.source_mode == NM_SOURCE_POINT);
+  if (o.history_sigma) {
+    // per-history totals need lane-wise deposits
+    if (o.warp_aggregate > 0) return fail(NM_ERR_ARG, "history_sigma needs warp_aggregate = 0");
+    sh.warp_agg = 0;
+  }
   sh.regroup = o.regroup >= 0 ? (o.regroup != 0) : 1;
   sh.lanes = o.regroup_lanes > 0 ? o.regroup_lanes : 12;
   apply_shape(h, sh);
   if (h->grid <= 0) return fail(NM_ERR_ARG, "transport kernel cannot launch with %d threads", h->block);
-  const bool fb = o.block_threads <= 0, fc = o.chunk <= 0, fa = o.warp_aggregate < 0,
+  const bool fb = o.block_threads <= 0, fc = o.chunk <= 0, fa = o.warp_aggregate < 0 && !o.history_sigma,
              fr = o.regroup < 0, fl = o.regroup_lanes <= 0 && sh.regroup;
   if (fb || fc || fa || fr || fl) return autotune(h, sh, fb, fc, fa, fr, fl);
   return NM_OK;
@@ -456,6 +472,11 @@ nm_status nm_dose_create(nm_dose** out, const nm_grid* g, const nm_materials* mt
       (e = dalloc(&h->organ_out, 4 * kLabelSlots)))
     return bail(cuda_fail(e, "device allocation"));
   if (labels && (e = dalloc(&h->labels, V))) return bail(cuda_fail(e, "device allocation"));
+  if (o.history_sigma) {
+    if ((e = dalloc(&h->s2h_lo, V)) || (e = dalloc(&h->s2h_hi, V)) ||
+        (e = cudaMemsetAsync(h->s2h_lo, 0, V * sizeof(ull), s)) || (e = cudaMemsetAsync(h->s2h_hi, 0, V * sizeof(ull), s)))
+      return bail(cuda_fail(e, "device allocation"));
+  }
 
   uint8_t* mat_dev = nullptr;
   if ((e = dalloc(&mat_dev, V))) return bail(cuda_fail(e, "device allocation"));
@@ -578,7 +599,8 @@ nm_status nm_dose_run(nm_dose* h, uint64_t n, uint64_t seed) {
       const uint64_t part = std::min<uint64_t>(nb - done, 1ull << 31);
       const TransportParams p = h->params(h->hist_next + done, part, seed);
       NM_CUDA(cudaMemsetAsync(h->work, 0, sizeof(unsigned), s), "cudaMemsetAsync");
-      NM_CUDA(launch_transport(p, h->grid, h->block, h->warp_agg, h->rayleigh, h->regroup, s),
+      NM_CUDA(launch_transport(p, h->grid, h->block, h->warp_agg, h->rayleigh, h->regroup, s, false,
+                               h->opt.history_sigma != 0),
               "transport launch");
       done += part;
     }
@@ -637,6 +659,8 @@ extern "C" nm_status nm_dose_run_batch(nm_dose* const* hs, int32_t n, const uint
     if (!hs[i]) return fail(NM_ERR_ARG, "handle %d is NULL", i);
     for (int j = 0; j < i; ++j)
       if (hs[j] == hs[i]) return fail(NM_ERR_ARG, "handle %d appears twice", i);
+    if (hs[i]->opt.history_sigma)
+      return fail(NM_ERR_ARG, "handle %d: history_sigma handles run with nm_dose_run, not in batches", i);
     if (!same_physics(hs[0], hs[i]))
       return fail(NM_ERR_ARG, "handle %d: all patients of a batch need the same materials, energies, batches and device", i);
     const uint64_t per = hs[i]->units_per_history();
@@ -893,6 +917,22 @@ nm_status nm_dose_get_organs(nm_dose* h, double* mean, double* eps_rms, double* 
   return NM_OK;
 }
 
+nm_status nm_dose_get_history_sigma(nm_dose* h, float* sigma) {
+  if (!h || !sigma) return fail(NM_ERR_ARG, "bad arguments");
+  if (!h->s2h_lo) return fail(NM_ERR_STATE, "the handle was created without history_sigma");
+  if (h->hist_next < 2) return fail(NM_ERR_STATE, "need at least 2 histories");
+  cudaStream_t s = h->stream;
+  const bool dev = is_device_ptr(sigma);
+  if (!dev && !h->out_sigma) NM_CUDA(dalloc(&h->out_sigma, h->V), "output buffer");
+  float* out = dev ? sigma : h->out_sigma;
+  NM_CUDA(launch_history_sigma(h->tsum, h->s2h_lo, h->s2h_hi, h->density, h->V, (double)h->hist_next,
+                               h->gy_per_unit_vol() * h->opt.activity_bq, out, s),
+          "history sigma");
+  if (!dev) NM_CUDA(cudaMemcpyAsync(sigma, out, h->V * sizeof(float), cudaMemcpyDeviceToHost, s), "sigma copy");
+  NM_CUDA(cudaStreamSynchronize(s), "nm_dose_get_history_sigma");
+  return NM_OK;
+}
+
 nm_status nm_dose_map_organs(nm_dose* h, const float* dose, double* mean) {
   if (!h || !dose || !mean) return fail(NM_ERR_ARG, "bad arguments");
   if (!h->labels) return fail(NM_ERR_STATE, "the handle has no label map");
@@ -945,6 +985,7 @@ nm_status nm_dose_counters(nm_dose* h, nm_counters* c) {
   c->regroup = h->regroup;
   c->regroup_lanes = h->regroup_lanes;
   c->grid_blocks = h->grid;
+  c->history_splits = v[kCtrHistSplits];
   return NM_OK;
 }
 
@@ -957,6 +998,10 @@ nm_status nm_dose_reset(nm_dose* h) {
   NM_CUDA(cudaMemsetAsync(h->counters, 0, kCtrCount * sizeof(ull), s), "reset");
   NM_CUDA(cudaMemsetAsync(h->org_s1, 0, kLabelSlots * sizeof(double), s), "reset");
   NM_CUDA(cudaMemsetAsync(h->org_s2, 0, kLabelSlots * sizeof(double), s), "reset");
+  if (h->s2h_lo) {
+    NM_CUDA(cudaMemsetAsync(h->s2h_lo, 0, h->V * sizeof(ull), s), "reset");
+    NM_CUDA(cudaMemsetAsync(h->s2h_hi, 0, h->V * sizeof(ull), s), "reset");
+  }
   NM_CUDA(cudaStreamSynchronize(s), "reset");
   h->hist_next = 0;
   h->n_batches = 0;

@@ -103,23 +103,31 @@ struct TransportParams {
   int max_steps;
   int regroup_compton;        // regrouped variant: lanes that must wait before a Compton pass
   int regroup_refill;         // regrouped variant: lanes that must wait before a refill pass
+  // History-by-history statistics (single-patient launches): per voxel the
+  // 128-bit sum over histories of each history's squared total deposit.
+  ull* s2h_lo;
+  ull* s2h_hi;
 };
+
+constexpr int kHistVoxels = 16;     // voxels a lane keeps per history (history statistics)
 
 constexpr int kMaxBatchPatients = 64;
 
 enum CounterSlot {
   kCtrSteps = 0, kCtrCompton, kCtrPhoto, kCtrRayleigh, kCtrCutoff, kCtrEscapes,
-  kCtrEscapedUnits, kCtrKilledUnits, kCtrDepositedUnits, kCtrCount
+  kCtrEscapedUnits, kCtrKilledUnits, kCtrDepositedUnits, kCtrHistSplits, kCtrCount
 };
 
 // Sets the message that nm_last_error() returns on the calling thread.
 void set_error_message(const char* msg);
 
 // ---- launchers (host side), one translation unit each ---------------------
+// history: history-by-history statistics (needs !warp_agg and !multi).
 cudaError_t launch_transport(const TransportParams& p, int grid, int block, bool warp_agg,
-                             bool rayleigh, bool regroup, cudaStream_t s, bool multi = false);
+                             bool rayleigh, bool regroup, cudaStream_t s, bool multi = false,
+                             bool history = false);
 int transport_max_blocks_per_sm(int block, bool warp_agg, bool rayleigh, bool regroup,
-                                bool multi = false);
+                                bool multi = false, bool history = false);
 cudaError_t launch_check_philox(const uint4* ctr, const uint2* key, int64_t n, uint4* out,
                                 cudaStream_t s);
 cudaError_t launch_check_kahn(float e, int64_t n, uint32_t k0, uint32_t k1, float* out,
@@ -199,6 +207,10 @@ struct FinalizeParams {
 };
 cudaError_t launch_finalize(const FinalizeParams& p, cudaStream_t s);
 cudaError_t launch_label_count(const uint8_t* labels, int64_t V, long long* count, cudaStream_t s);
+// History-by-history sigma of the mean dose rate: sigma[v] = sqrt((S2/N -
+// (T/N)^2) / (N - 1)) * gy_a / density[v], S2 = hi * 2^64 + lo.
+cudaError_t launch_history_sigma(const ull* tsum, const ull* s2h_lo, const ull* s2h_hi, const float* density,
+                                 int64_t V, double n_total, double gy_a, float* sigma, cudaStream_t s);
 cudaError_t launch_map_organ_means(const float* dose, const uint8_t* labels, int64_t V, double* part,
                                    const long long* count, double* out, cudaStream_t s);
 

@@ -179,7 +179,31 @@ __global__ void map_organ_final_kernel(const double* __restrict__ part, int n_bl
   if (lane == 0) out[l] = count[l] > 0 ? s / (double)count[l] : 0.0;
 }
 
+__global__ void history_sigma_kernel(const ull* __restrict__ tsum, const ull* __restrict__ lo,
+                                     const ull* __restrict__ hi, const float* __restrict__ density, int64_t V,
+                                     double n, float gy_a, float* __restrict__ sigma) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
+    const ull t = tsum[v];
+    float sg = 0.0f;
+    if (t) {
+      const double s2 = (double)hi[v] * 18446744073709551616.0 + (double)lo[v];
+      const double mean = (double)t / n;                   // units per history
+      const double var = fmax(s2 / n - mean * mean, 0.0) / (n - 1.0);   // of the mean
+      sg = sqrtf((float)var) * __fdiv_rn(gy_a, density[v]);
+    }
+    sigma[v] = sg;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_history_sigma(const ull* tsum, const ull* s2h_lo, const ull* s2h_hi, const float* density,
+                                 int64_t V, double n_total, double gy_a, float* sigma, cudaStream_t s) {
+  const int64_t g = (V + 255) / 256;
+  history_sigma_kernel<<<(unsigned)(g < 8192 ? g : 8192), 256, 0, s>>>(tsum, s2h_lo, s2h_hi, density, V, n_total,
+                                                                       (float)gy_a, sigma);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_map_organ_means(const float* dose, const uint8_t* labels, int64_t V, double* part,
                                    const long long* count, double* out, cudaStream_t s) {

@@ -280,8 +280,47 @@ __device__ __forceinline__ void compton(const TransportParams& p, const float* s
   }
 }
 
-template <bool WARP_AGG, bool RAYLEIGH, bool REGROUP, bool MULTI>
+// History statistics: a lane lists its current history's deposits per voxel
+// (kHistVoxels entries in shared memory, structure of arrays over the CTA) and
+// adds them to the tally, with their squares to the 128-bit sums, when the
+// history ends (the lane takes its next history, or the kernel ends).
+struct HistList {
+  uint32_t* v;   // voxel of entry i at v[i * stride]
+  uint32_t* q;   // units
+  int stride;
+};
+
+__device__ __forceinline__ void hist_flush(const HistList& L, int& n, ull* tally, ull* lo, ull* hi) {
+  for (int i = 0; i < n; ++i) {
+    const uint32_t v = L.v[i * L.stride], t = L.q[i * L.stride];
+    atomicAdd(tally + v, (ull)t);
+    const ull t2 = (ull)t * t;
+    const ull old = atomicAdd(lo + v, t2);
+    if (old + t2 < old) atomicAdd(hi + v, 1ull);   // carry into the high word
+  }
+  n = 0;
+}
+
+__device__ __forceinline__ void hist_add(const HistList& L, int& n, uint32_t v, uint32_t dq, ull* tally, ull* lo,
+                                         ull* hi, ull* splits) {
+  for (int i = 0; i < n; ++i)
+    if (L.v[i * L.stride] == v) {
+      L.q[i * L.stride] += dq;
+      return;
+    }
+  if (n == kHistVoxels) {
+    // more voxels than a lane keeps: the totals so far are squared now
+    hist_flush(L, n, tally, lo, hi);
+    atomicAdd(splits, 1ull);
+  }
+  L.v[n * L.stride] = v;
+  L.q[n * L.stride] = dq;
+  ++n;
+}
+
+template <bool WARP_AGG, bool RAYLEIGH, bool REGROUP, bool MULTI, bool HIST>
 __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams p) {
+  static_assert(!HIST || (!WARP_AGG && !MULTI), "history statistics: one patient, lane-wise deposits");
   __shared__ float s_kn[kKnTable];
   __shared__ float s_minv[kKnTable];
   __shared__ float s_minv_out[kKnTable];
@@ -313,6 +352,9 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
   __syncthreads();
   float* site = s_site + threadIdx.x;
   const int nb = blockDim.x;
+  const HistList hl{reinterpret_cast<uint32_t*>(s_site + 7 * nb) + threadIdx.x,
+                    reinterpret_cast<uint32_t*>(s_site + (7 + kHistVoxels) * nb) + threadIdx.x, nb};
+  int hn = 0;                            // entries in this lane's history list
 
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t lt_mask = (1u << lane) - 1u;
@@ -410,6 +452,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
             cpi = npi;
           }
           pi = npi;
+          if (HIST && hn) hist_flush(hl, hn, p.g.tally, p.s2h_lo, p.s2h_hi);   // the previous history ends
           const PatientGeom& G = MULTI ? s_geom[pi] : p.g;
           const uint64_t h = G.hist_begin + idx;
           hlo = (uint32_t)h;
@@ -429,8 +472,14 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
             site[3 * nb] = st.u; site[4 * nb] = st.v_; site[5 * nb] = st.w;
             site[6 * nb] = rem_b;
             pending_b = true;
-            has = G.q_positron > 0;
-            cell = G.tally + st.v;
+            if (HIST) {
+              if (G.q_positron > 0)
+                hist_add(hl, hn, (uint32_t)st.v, (uint32_t)G.q_positron, p.g.tally, p.s2h_lo, p.s2h_hi,
+                         p.g.counters + kCtrHistSplits);
+            } else {
+              has = G.q_positron > 0;
+              cell = G.tally + st.v;
+            }
           }
         }
       }
@@ -540,8 +589,13 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
         pending_c = false;
       }
     }
-    tally_flush<WARP_AGG>(G.tally + dv, has, dq, lane);
+    if (HIST) {
+      if (has) hist_add(hl, hn, (uint32_t)dv, dq, p.g.tally, p.s2h_lo, p.s2h_hi, p.g.counters + kCtrHistSplits);
+    } else {
+      tally_flush<WARP_AGG>(G.tally + dv, has, dq, lane);
+    }
   }
+  if (HIST && hn) hist_flush(hl, hn, p.g.tally, p.s2h_lo, p.s2h_hi);
 
   // ---- counters ---------------------------------------------------------------
   if (MULTI) {
@@ -600,41 +654,61 @@ __global__ void check_source_kernel(const TransportParams p, uint64_t first, int
   dir[3 * i + 2] = s.w;
 }
 
-size_t transport_smem(int block) { return (size_t)7 * block * sizeof(float); }
+// Dynamic shared memory: the site stash, and the history lists when kept.
+size_t transport_smem(int block, bool history) {
+  return ((size_t)7 + (history ? 2 * kHistVoxels : 0)) * block * sizeof(float);
+}
 
-template <bool A, bool R, bool G, bool M>
+template <bool A, bool R, bool G, bool M, bool H>
 void* kernel_ptr() {
-  return (void*)transport_kernel<A, R, G, M>;
+  return (void*)transport_kernel<A, R, G, M, H>;
 }
 
 template <bool M>
 void* pick_m(bool a, bool r, bool g) {
   if (a) {
-    if (r) return g ? kernel_ptr<true, true, true, M>() : kernel_ptr<true, true, false, M>();
-    return g ? kernel_ptr<true, false, true, M>() : kernel_ptr<true, false, false, M>();
+    if (r) return g ? kernel_ptr<true, true, true, M, false>() : kernel_ptr<true, true, false, M, false>();
+    return g ? kernel_ptr<true, false, true, M, false>() : kernel_ptr<true, false, false, M, false>();
   }
-  if (r) return g ? kernel_ptr<false, true, true, M>() : kernel_ptr<false, true, false, M>();
-  return g ? kernel_ptr<false, false, true, M>() : kernel_ptr<false, false, false, M>();
+  if (r) return g ? kernel_ptr<false, true, true, M, false>() : kernel_ptr<false, true, false, M, false>();
+  return g ? kernel_ptr<false, false, true, M, false>() : kernel_ptr<false, false, false, M, false>();
 }
 
-void* pick(bool a, bool r, bool g, bool m) { return m ? pick_m<true>(a, r, g) : pick_m<false>(a, r, g); }
+// History statistics exist only without warp aggregation and for one patient.
+void* pick(bool a, bool r, bool g, bool m, bool h) {
+  if (h) {
+    if (a || m) return nullptr;
+    if (r) return g ? kernel_ptr<false, true, true, false, true>() : kernel_ptr<false, true, false, false, true>();
+    return g ? kernel_ptr<false, false, true, false, true>() : kernel_ptr<false, false, false, false, true>();
+  }
+  return m ? pick_m<true>(a, r, g) : pick_m<false>(a, r, g);
+}
 
 }  // namespace
 
 cudaError_t launch_transport(const TransportParams& p, int grid, int block, bool warp_agg,
-                             bool rayleigh, bool regroup, cudaStream_t s, bool multi) {
-  void* fn = pick(warp_agg, rayleigh, regroup, multi);
+                             bool rayleigh, bool regroup, cudaStream_t s, bool multi, bool history) {
+  void* fn = pick(warp_agg, rayleigh, regroup, multi, history);
+  if (!fn) return cudaErrorInvalidValue;
   void* args[] = {(void*)&p};
-  const cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(block), args, transport_smem(block), s);
+  // the history lists take the static + dynamic total past the 48 KB default
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)transport_smem(block, history));
+  if (e == cudaSuccess) e = cudaLaunchKernel(fn, dim3(grid), dim3(block), args, transport_smem(block, history), s);
   if (e != cudaSuccess) cudaGetLastError();  // a refused launch must not linger as the last error
   return e;
 }
 
-int transport_max_blocks_per_sm(int block, bool warp_agg, bool rayleigh, bool regroup, bool multi) {
+int transport_max_blocks_per_sm(int block, bool warp_agg, bool rayleigh, bool regroup, bool multi, bool history) {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick(warp_agg, rayleigh, regroup, multi), block,
-                                                    transport_smem(block)) != cudaSuccess)
+  void* fn = pick(warp_agg, rayleigh, regroup, multi, history);
+  if (!fn ||
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)transport_smem(block, history)) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, transport_smem(block, history)) != cudaSuccess) {
+    cudaGetLastError();
     return 0;
+  }
   return n;
 }
 

@@ -50,7 +50,7 @@ class nm_options(C.Structure):
                 ("n_labels", C.c_int32), ("block_threads", C.c_int32), ("chunk", C.c_int32),
                 ("warp_aggregate", C.c_int32), ("regroup", C.c_int32), ("regroup_lanes", C.c_int32),
                 ("max_steps", C.c_int32),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("history_sigma", C.c_int32)]
 
 
 class nm_counters(C.Structure):
@@ -60,7 +60,7 @@ class nm_counters(C.Structure):
                 ("rayleigh", C.c_uint64), ("cutoff", C.c_uint64), ("escapes", C.c_uint64),
                 ("transport_ms", C.c_double), ("fold_ms", C.c_double), ("device_status", C.c_uint32),
                 ("block_threads", C.c_int32), ("chunk", C.c_int32), ("warp_aggregate", C.c_int32),
-                ("regroup", C.c_int32), ("regroup_lanes", C.c_int32), ("grid_blocks", C.c_int32)]
+                ("regroup", C.c_int32), ("regroup_lanes", C.c_int32), ("grid_blocks", C.c_int32), ("history_splits", C.c_uint64)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -88,6 +88,7 @@ _SIGS = {
     "nm_dose_get": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "nm_dose_get_organs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "nm_dose_get_tally": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "nm_dose_get_history_sigma": (C.c_int, [C.c_void_p, C.c_void_p]),
     "nm_dose_map_organs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "nm_dose_counters": (C.c_int, [C.c_void_p, C.POINTER(nm_counters)]),
     "nm_dose_reset": (C.c_int, [C.c_void_p]),
@@ -442,6 +443,13 @@ class Dose:
 
     def counters(self):
         return nm_dose_counters(self.h)
+
+    def history_sigma(self, out=None):
+        """History-by-history sigma of the mean dose rate (Gy/s)."""
+        if out is None:
+            out = np.empty(self.shape, np.float32)
+        _check(load().nm_dose_get_history_sigma(self.h, ptr(out)))
+        return out
 
     def reset(self):
         nm_dose_reset(self.h)
