@@ -192,3 +192,32 @@ def test_full_size_phantom_organs_match_oracle(nm, orc):
     assert npow >= 3 and worst < 0.01, (npow, worst)
     # GPU organ sigma at 1e9 decays: the well-sampled organs are below 1 %.
     assert np.all(gs[sel] / gm[sel] < 0.05)
+
+
+def test_whole_body_phantom_organs_match_oracle(nm, orc):
+    # The whole-body workload: 512x512x600 voxels of 1x1x3 mm with high-uptake
+    # lesions (157 M voxels, 1.26 GB of int64 tallies).  1e9 GPU decays against
+    # 2e6 oracle decays: organ means within 4 combined sigma, exact energy
+    # bookkeeping; then a whole-volume denoiser pass (z slabs at this size) of a
+    # fresh network, whose zero head returns its input.
+    from paper_2111_11687_gb300 import inputs
+    import torch
+    ph = inputs.whole_body_phantom()
+    N = 1_000_000_000
+    den, mat, g, sg, (gm, ge, gs, cnt), c, t = _gpu_phantom_run(nm, ph, N, seed=1)
+    assert c["emitted"] == c["deposited"] + c["escaped"] and c["killed"] == 0
+    assert int(t.sum()) == c["deposited"]
+    r = _oracle_phantom_run(orc, ph, 2_000_000, seed=2)
+    zmax, npow, worst, z, sel = organ_check(gm, gs, r.organ_mean, r.organ_sigma, cnt)
+    assert sel.sum() >= 20 and zmax < 4.0, z[sel]
+    assert npow == 0 or worst < 0.01, (npow, worst)
+    del t, r
+    net = nm.Denoiser(patch=32, batch=1, levels=4, base_width=16, seed=1)
+    dose = torch.from_numpy(g).cuda()
+    out = torch.empty_like(dose)
+    net.apply(dose, torch.from_numpy(den).cuda(), torch.from_numpy(ph.activity).cuda(), out)
+    o = out.cpu().numpy()
+    net.close()
+    assert np.all(np.isfinite(o))
+    body = den >= 0.1
+    assert np.allclose(o[body], g[body], rtol=1e-2, atol=1e-3 * g[body].max())
