@@ -17,6 +17,8 @@
 
 #include <cstdlib>
 
+#include <algorithm>
+
 #include "nm_internal.cuh"
 #include "nm_tc.cuh"
 
@@ -528,7 +530,8 @@ int conv_wgrad_splits(const nm_conv3d_desc& d) {
 }
 
 size_t conv_wgrad_workspace(const nm_conv3d_desc& d) {
-  return (size_t)conv_wgrad_splits(d) * conv_kpad(d.c0 + d.c1) * d.cout * sizeof(float);
+  const size_t gather = (size_t)conv_wgrad_splits(d) * conv_kpad(d.c0 + d.c1) * d.cout * sizeof(float);
+  return conv_wgrad_tile_ok(d) ? std::max(gather, conv_wgrad_tile_workspace(d)) : gather;
 }
 
 cudaError_t conv3d_flip_weights(const nm_conv3d_desc& d, const void* w, void* wb, cudaStream_t s) {
@@ -542,6 +545,11 @@ cudaError_t conv3d_flip_weights(const nm_conv3d_desc& d, const void* w, void* wb
 
 cudaError_t conv3d_wgrad(const nm_conv3d_desc& d, const void* x0, const void* x1, const void* dy,
                          float* dw, float* db, void* workspace, uint32_t* status, cudaStream_t s) {
+  // Single-source layers with 16 or 32 outputs take the shifted-window kernel;
+  // NM_CONV_GATHER=1 forces the gather kernel.
+  const char* force = getenv("NM_CONV_GATHER");
+  if (conv_wgrad_tile_ok(d) && !(force && force[0] == '1'))
+    return conv3d_wgrad_tile(d, x0, dy, dw, db, workspace, status, s);
   const ConvGeom g = make_geom(d);
   const int splits = conv_wgrad_splits(d);
   float* part = (float*)workspace;

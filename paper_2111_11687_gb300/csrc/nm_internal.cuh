@@ -230,6 +230,11 @@ cudaError_t conv3d_fwd_tile_head(const nm_conv3d_desc& d, const void* x, const v
                                  const float* head_w, const void* xin, int cx, float* yh, uint32_t* status,
                                  cudaStream_t s);
 cudaError_t conv3d_flip_weights(const nm_conv3d_desc& d, const void* w, void* wb, cudaStream_t s);
+// Shifted-window weight gradient (nm_wgrad_tile.cu): single source, 16 or 32 outputs.
+bool conv_wgrad_tile_ok(const nm_conv3d_desc& d);
+size_t conv_wgrad_tile_workspace(const nm_conv3d_desc& d);
+cudaError_t conv3d_wgrad_tile(const nm_conv3d_desc& d, const void* x, const void* dy, float* dw, float* db,
+                              void* workspace, uint32_t* status, cudaStream_t s);
 cudaError_t conv3d_wgrad(const nm_conv3d_desc& d, const void* x0, const void* x1, const void* dy,
                          float* dw, float* db, void* workspace, uint32_t* status, cudaStream_t s);
 

@@ -1,0 +1,410 @@
+// Weight gradient of a 3x3x3 convolution by shifted windows:
+//   dW[co][tap][ci] = sum over voxels v of dY[v][co] * X[v + off_tap][ci].
+//
+// Per tap this is a GEMM over voxels (K) with M = output channels and N = one
+// 16-channel chunk of input channels.  Both operands come from halo tiles in
+// shared memory in the 32-byte-swizzled MN-major layout (a voxel row of 16
+// channels, 32 bytes), loaded by TMA: dY over the tile's z-planes, X with its
+// one-voxel halo.  The K rows run over the padded tile's centre indices as in
+// the forward kernel; dY is zeroed at the halo positions (they belong to other
+// tiles), so those rows add nothing, and tap (dz, dy, dx) reads X from the
+// same rows shifted by (dz*PY + dy)*PX + dx: a different start address.  The
+// MMA shape is M = 64 (the 16 or 32 real output channels; the rest of D is
+// never read), N = 16, 32 or 48 input channels, K = 16; a pass's taps keep
+// their accumulators in TMEM across all of a CTA's tiles.
+//
+// Persistent, warp-specialised (one CTA per SM), passes over groups of input
+// chunks and of taps:
+//   warp 0    TMA producer (dY atoms + the pass's X chunks per tile) into a stage ring;
+//   warp 1    MMA issuer: per tile the pass's taps x 40 K-steps, commits to "empty";
+//   warps 2-5 zero dY's halo rows of each landed stage (then "ready"), and at
+//             the end of a pass warps 4 and 5 (the TMEM lane quarters that
+//             hold D's rows 0-15 and 16-31) write the CTA's partial dW for
+//             that chunk.
+// Partials are summed over CTAs in a fixed order by the caller (deterministic);
+// the bias gradient is a separate fixed-order reduction.  Every wait is
+// bounded; a time-out sets NM_DEV_TIMEOUT and drains what is in flight.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "nm_internal.cuh"
+#include "nm_tc.cuh"
+
+namespace nm {
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int TX = 16, TY = 16, TZ = 2;
+constexpr int PX = TX + 2, PY = TY + 2, PZ = TZ + 2;
+constexpr int kRows = PX * PY * PZ;                          // X box rows
+constexpr int kCmin = (1 * PY + 1) * PX + 1;                 // first centre
+constexpr int kCmax = (TZ * PY + TY) * PX + TX;              // last centre
+constexpr int kKRows = ((kCmax - kCmin + 1 + 127) / 128) * 128;  // K rows per tile (640)
+constexpr int kKSteps = kKRows / 16;
+constexpr int kDelta = PY * PX + PX + 1;                     // largest tap shift
+constexpr int kXRows = (kCmin + kKRows + kDelta + 15) / 16 * 16;  // rows any MMA may read from X
+constexpr int kYOff = PY * PX;                               // dY box starts one z-plane in
+constexpr int kYBox = PX * PY * TZ;                          // dY box rows
+constexpr int kYRows = (kCmin - kYOff + kKRows + 15) / 16 * 16;   // rows read from dY (>= kYBox)
+constexpr uint32_t kXBytes = kXRows * 32;
+constexpr uint32_t kYBytes = kYRows * 32;
+constexpr int kThreads = 192;
+constexpr long long kWaitCycles = 4ll << 30;
+constexpr int kBiasBlocks = 256;
+
+static_assert(kXRows >= kRows && kYRows >= kYBox, "tile rows");
+
+// G = input-channel atoms (16 channels each) per MMA: N = 16 G.  With more
+// atoms one MMA covers more of the input channels, so fewer instructions are
+// issued (their rate, not the tensor math, bounds these small GEMMs); the
+// taps of a pass are limited by TMEM (T taps x 16 G columns <= 512).
+template <int COUT, int G>
+struct WLayout {
+  static constexpr int kYAtoms = COUT / 16;
+  static constexpr int kTaps = 512 / (16 * G) < 27 ? 512 / (16 * G) : 27;
+  // the M = 64 operand reads four 16-channel atoms at the LBO stride: with 32
+  // outputs the two spare atoms must fall inside the stage, so it spans at
+  // least 4 x kYBytes
+  static constexpr uint32_t kUsed = kYAtoms * kYBytes + G * kXBytes;
+  static constexpr uint32_t kSpan = COUT == 16 ? kUsed : (4 * kYBytes > kUsed ? 4 * kYBytes : kUsed);
+  static constexpr uint32_t kStage = (kSpan + 1023) / 1024 * 1024;
+  static constexpr int kStages = 3 * kStage <= 220 * 1024 ? 3 : 2 * kStage <= 220 * 1024 ? 2 : 1;
+  static constexpr size_t kSmem = (size_t)kStages * kStage;
+  static_assert(kSmem <= 227 * 1024, "shared memory");
+};
+
+struct WGrid {
+  int n, d, h, w, tiles_x, tiles_y, tiles_z, cin, kpad;
+  long long tiles;
+  __device__ void coords(long long t, int& b, int& x0, int& y0, int& z0) const {
+    x0 = (int)(t % tiles_x) * TX; t /= tiles_x;
+    y0 = (int)(t % tiles_y) * TY; t /= tiles_y;
+    z0 = (int)(t % tiles_z) * TZ;
+    b = (int)(t / tiles_z);
+  }
+};
+
+__device__ __forceinline__ uint64_t desc_mn_sw32(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  // MN-major, 32-byte swizzle: LBO = stride between 16-element atoms along
+  // M/N, SBO = stride between groups of 8 K rows (checked on the device)
+  return tc::smem_desc(saddr, lbo, sbo) | ((uint64_t)6 << 61);
+}
+
+template <int COUT, int G>
+__global__ void __launch_bounds__(kThreads, 1) wgrad_tile_kernel(const __grid_constant__ CUtensorMap tmx,
+                                                                 const __grid_constant__ CUtensorMap tmy,
+                                                                 const WGrid g, float* __restrict__ part,
+                                                                 uint32_t* status) {
+  typedef WLayout<COUT, G> L;
+  constexpr int S = L::kStages, T = L::kTaps;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ __align__(8) uint64_t full[S], ready[S], empty[S], acc_full, acc_empty;
+  __shared__ uint32_t s_tmem;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nchunks = (g.cin + 15) / 16;
+  const long long my_tiles = g.tiles > blockIdx.x ? (g.tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  // passes: groups of G input chunks x groups of T taps
+  const int n_tg = (27 + T - 1) / T;
+  const int passes = (nchunks + G - 1) / G * n_tg;
+
+  if (warp == 0) tc::tmem_alloc(&s_tmem, 512);
+  // rows past the TMA boxes are read by the last K-steps but never loaded:
+  // zero them once per stage (dY there must be 0; X must at least be finite)
+  for (int i = threadIdx.x; i < S * L::kYAtoms * (kYRows - kYBox) * 2; i += blockDim.x) {
+    const int half = i & 1, r = kYBox + (i >> 1) % (kYRows - kYBox);
+    const int rest = (i >> 1) / (kYRows - kYBox);
+    const int atom = rest % L::kYAtoms, s = rest / L::kYAtoms;
+    *reinterpret_cast<uint4*>(smem + s * L::kStage + atom * kYBytes + r * 32 + half * 16) = make_uint4(0, 0, 0, 0);
+  }
+  for (int i = threadIdx.x; i < S * G * (kXRows - kRows) * 2; i += blockDim.x) {
+    const int half = i & 1, r = kRows + (i >> 1) % (kXRows - kRows);
+    const int rest = (i >> 1) / (kXRows - kRows), a = rest % G, s = rest / G;
+    *reinterpret_cast<uint4*>(smem + s * L::kStage + L::kYAtoms * kYBytes + a * kXBytes + r * 32 + half * 16) =
+        make_uint4(0, 0, 0, 0);
+  }
+  if (threadIdx.x == 32) {
+    for (int i = 0; i < S; ++i) {
+      tc::mbar_init(&full[i], 1);
+      tc::mbar_init(&ready[i], 128);
+      tc::mbar_init(&empty[i], 1);
+    }
+    tc::mbar_init(&acc_full, 1);
+    tc::mbar_init(&acc_empty, 64);
+    tc::mbar_fence_init();
+  }
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = s_tmem;
+  const uint32_t base = tc::smem_u32(smem);
+  bool timeout = false;
+
+  if (warp == 0) {
+    // ---- producer: for every pass (input chunk), every tile ------------------
+    if (lane == 0) {
+      long long it = 0;
+      for (int ps = 0; ps < passes && !timeout; ++ps) {
+        const int c0 = ps / n_tg * G, na = min(G, nchunks - c0);
+        for (long long k = 0; k < my_tiles; ++k, ++it) {
+          const int s = (int)(it % S);
+          if (it >= S && !tc::mbar_wait_bounded(&empty[s], (uint32_t)(((it / S) - 1) & 1), kWaitCycles)) {
+            timeout = true;
+            break;
+          }
+          int b, x0, y0, z0;
+          g.coords(blockIdx.x + k * gridDim.x, b, x0, y0, z0);
+          const uint32_t sa = base + s * L::kStage;
+          tc::mbar_arrive_expect_tx(&full[s], (L::kYAtoms * kYBox + na * kRows) * 32);
+          for (int q = 0; q < L::kYAtoms; ++q)
+            tc::tma_load_5d(sa + q * kYBytes, &tmy, &full[s], q * 16, x0 - 1, y0 - 1, z0, b);
+          for (int a = 0; a < na; ++a)
+            tc::tma_load_5d(sa + L::kYAtoms * kYBytes + a * kXBytes, &tmx, &full[s], (c0 + a) * 16, x0 - 1,
+                            y0 - 1, z0 - 1, b);
+        }
+      }
+      for (long long j = it > S ? it - S : 0; j < it; ++j)
+        if (!tc::mbar_wait_bounded(&full[j % S], (uint32_t)((j / S) & 1), kWaitCycles)) timeout = true;
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer -------------------------------------------------------------------
+    if (lane == 0) {
+      long long it = 0;
+      for (int ps = 0; ps < passes && !timeout; ++ps) {
+        const int c0 = ps / n_tg * G, na = min(G, nchunks - c0);
+        const int t0 = ps % n_tg * T, t1 = min(27, t0 + T);
+        const uint32_t idesc = tc::idesc_bf16_f32(64, 16 * na, true, true);
+        // the previous pass's accumulators have been read out
+        if (ps > 0 && !tc::mbar_wait_bounded(&acc_empty, (uint32_t)((ps - 1) & 1), kWaitCycles)) {
+          timeout = true;
+          break;
+        }
+        tc::fence_after_sync();
+        for (long long k = 0; k < my_tiles; ++k, ++it) {
+          const int s = (int)(it % S);
+          if (!tc::mbar_wait_bounded(&ready[s], (uint32_t)((it / S) & 1), kWaitCycles)) {
+            timeout = true;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t sy = base + s * L::kStage;
+          const uint32_t sx = sy + L::kYAtoms * kYBytes;
+          const uint64_t a_base = desc_mn_sw32(sy + (kCmin - kYOff) * 32, COUT == 16 ? 0 : kYBytes, 256);
+          const uint64_t b_base = desc_mn_sw32(sx + kCmin * 32, kXBytes, 256);
+          const uint32_t first = k == 0 ? 0u : 1u;
+          for (int ks = 0; ks < kKSteps; ++ks) {
+            const uint64_t adesc = a_base + (uint64_t)(ks * 16 * 32 >> 4);
+            for (int tap = t0; tap < t1; ++tap) {
+              const int delta = ((tap / 9 - 1) * PY + ((tap / 3) % 3 - 1)) * PX + (tap % 3 - 1);
+              const uint64_t bdesc = b_base + (uint64_t)((ks * 16 + delta) * 32 >> 4);
+              tc::mma_bf16(tmem + (tap - t0) * 16 * G, adesc, bdesc, idesc, ks == 0 ? first : 1u);
+            }
+          }
+          tc::mma_commit(&empty[s]);
+        }
+        if (timeout) break;
+        tc::mma_commit(&acc_full);
+      }
+      if (it > 0 && !tc::mbar_wait_bounded(&empty[(it - 1) % S], (uint32_t)(((it - 1) / S) & 1), kWaitCycles))
+        timeout = true;
+    }
+  } else {
+    // ---- halo zeroing, and the partial dW at the end of each pass -----------------
+    const int t = threadIdx.x - 64;                  // 0..127
+    long long it = 0;
+    for (int ps = 0; ps < passes && !timeout; ++ps) {
+      const int c0 = ps / n_tg * G, na = min(G, nchunks - c0);
+      const int t0 = ps % n_tg * T, t1 = min(27, t0 + T);
+      for (long long k = 0; k < my_tiles; ++k, ++it) {
+        const int s = (int)(it % S);
+        const bool got = tc::mbar_wait_bounded(&full[s], (uint32_t)((it / S) & 1), kWaitCycles);
+        if (!__all_sync(0xffffffffu, got)) {
+          timeout = true;
+          break;
+        }
+        // dY rows of x or y halo positions (2 z-planes x 68): zero both 16-byte halves
+        uint8_t* sy = smem + s * L::kStage;
+        for (int i = t; i < L::kYAtoms * TZ * 68 * 2; i += 128) {
+          const int half = i & 1, j = (i >> 1) % (TZ * 68), atom = (i >> 1) / (TZ * 68);
+          const int zp = j / 68, h = j % 68;
+          int xp, yp;
+          if (h < 18) { yp = 0; xp = h; }
+          else if (h < 36) { yp = PY - 1; xp = h - 18; }
+          else { yp = 1 + (h - 36) / 2; xp = (h & 1) ? PX - 1 : 0; }
+          const int r = (zp * PY + yp) * PX + xp;
+          *reinterpret_cast<uint4*>(sy + atom * kYBytes + r * 32 + half * 16) = make_uint4(0, 0, 0, 0);
+        }
+        tc::fence_async_smem();
+        tc::mbar_arrive(&ready[s]);
+      }
+      if (timeout) break;
+      // end of the pass: with M = 64, D row i sits in TMEM lane (i % 16) +
+      // 32 (i / 16), so output channels 0-15 are lanes 0-15 (warp 4's quarter)
+      // and 16-31 lanes 32-47 (warp 5's quarter)
+      if (warp == 4 || warp == 5) {
+        const bool got = tc::mbar_wait_bounded(&acc_full, (uint32_t)(ps & 1), kWaitCycles);
+        if (!__all_sync(0xffffffffu, got)) {
+          timeout = true;
+          break;
+        }
+        tc::fence_after_sync();
+        float* dst = part + (size_t)blockIdx.x * g.kpad * COUT;
+        const int q = warp & 3, co = q * 16 + lane;
+        for (int tap = t0; tap < t1; ++tap)
+          for (int a = 0; a < na; ++a) {
+            float v[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (tap - t0) * 16 * G + a * 16, v);
+            if (lane < 16 && co < COUT)
+#pragma unroll
+              for (int j = 0; j < 16; ++j) {
+                const int ci = (c0 + a) * 16 + j;
+                if (ci < g.cin) dst[(size_t)(tap * g.cin + ci) * COUT + co] = v[j];
+              }
+          }
+        tc::fence_before_sync();
+        tc::mbar_arrive(&acc_empty);
+      }
+    }
+  }
+  if (timeout) atomicOr(status, NM_DEV_TIMEOUT);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+// Bias gradient db[co] = sum over voxels of dY[v][co]: per-CTA partial sums
+// in a fixed order, then CTAs in index order.
+__global__ void bias_grad_partial(const bf16* __restrict__ dy, long long m, int cout, float* __restrict__ part) {
+  extern __shared__ float red[];                    // [blockDim][cout]
+  float acc[32];
+  for (int c = 0; c < cout; ++c) acc[c] = 0.0f;
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < m; v += (long long)gridDim.x * blockDim.x)
+    for (int c = 0; c < cout; ++c) acc[c] += __bfloat162float(dy[v * cout + c]);
+  for (int c = 0; c < cout; ++c) red[threadIdx.x * cout + c] = acc[c];
+  __syncthreads();
+  for (int c = threadIdx.x; c < cout; c += blockDim.x) {
+    float s = 0.0f;
+    for (int t = 0; t < (int)blockDim.x; ++t) s += red[t * cout + c];
+    part[(size_t)blockIdx.x * cout + c] = s;
+  }
+}
+
+__global__ void bias_grad_final(const float* __restrict__ part, int blocks, int cout, float* __restrict__ db) {
+  const int c = threadIdx.x;
+  if (c >= cout) return;
+  float s = 0.0f;
+  for (int b = 0; b < blocks; ++b) s += part[(size_t)b * cout + c];
+  db[c] = s;
+}
+
+__global__ void wgrad_tile_reduce(const float* __restrict__ part, int splits, int kpad, int kreal, int cout,
+                                  float* __restrict__ dw) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)kpad * cout) return;
+  const int co = (int)(i / kpad), k = (int)(i % kpad);
+  float s = 0.0f;
+  if (k < kreal)
+    for (int t = 0; t < splits; ++t) s += part[((long long)t * kpad + k) * cout + co];
+  dw[(long long)co * kpad + k] = s;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 1;
+  return n;
+}
+
+bool encode(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap* map, const void* t, int c, const nm_conv3d_desc& d,
+            int box_z) {
+  const cuuint64_t dims[5] = {(cuuint64_t)c, (cuuint64_t)d.w, (cuuint64_t)d.h, (cuuint64_t)d.d, (cuuint64_t)d.n};
+  const cuuint64_t strides[4] = {(cuuint64_t)c * 2, (cuuint64_t)d.w * c * 2, (cuuint64_t)d.h * d.w * c * 2,
+                                 (cuuint64_t)d.d * d.h * d.w * c * 2};
+  const cuuint32_t box[5] = {16, PX, PY, (cuuint32_t)box_z, 1};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(t), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int COUT, int G>
+cudaError_t launch_wgrad_tile(const nm_conv3d_desc& d, const void* x, const void* dy, float* dw, float* db,
+                              void* workspace, uint32_t* status, cudaStream_t s) {
+  typedef WLayout<COUT, G> L;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  CUtensorMap mx, my;
+  if (!encode(enc, &mx, x, d.c0, d, PZ) || !encode(enc, &my, dy, COUT, d, TZ)) return cudaErrorInvalidValue;
+  WGrid g;
+  g.n = d.n; g.d = d.d; g.h = d.h; g.w = d.w;
+  g.tiles_x = (d.w + TX - 1) / TX;
+  g.tiles_y = (d.h + TY - 1) / TY;
+  g.tiles_z = (d.d + TZ - 1) / TZ;
+  g.tiles = (long long)g.tiles_x * g.tiles_y * g.tiles_z * g.n;
+  g.cin = d.c0;
+  g.kpad = conv_kpad(d.c0);
+  // every CTA gets at least one tile (its pass-end read-out waits for MMAs)
+  const int grid = (int)std::min<long long>(g.tiles, sm_count());
+  float* part = (float*)workspace;
+  float* bpart = part + (size_t)grid * g.kpad * COUT;
+  cudaError_t e = cudaFuncSetAttribute(wgrad_tile_kernel<COUT, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)L::kSmem);
+  if (e != cudaSuccess) return e;
+  wgrad_tile_kernel<COUT, G><<<grid, kThreads, L::kSmem, s>>>(mx, my, g, part, status);
+  const long long n = (long long)g.kpad * COUT;
+  wgrad_tile_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(part, grid, g.kpad, 27 * d.c0, COUT, dw);
+  if (db) {
+    const long long m = (long long)d.n * d.d * d.h * d.w;
+    bias_grad_partial<<<kBiasBlocks, 128, 128 * COUT * sizeof(float), s>>>((const bf16*)dy, m, COUT, bpart);
+    bias_grad_final<<<1, 32, 0, s>>>(bpart, kBiasBlocks, COUT, db);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool conv_wgrad_tile_ok(const nm_conv3d_desc& d) {
+  return d.c1 == 0 && !d.src0_coarse && d.c0 % 8 == 0 && (d.cout == 16 || d.cout == 32);
+}
+
+size_t conv_wgrad_tile_workspace(const nm_conv3d_desc& d) {
+  return ((size_t)sm_count() * conv_kpad(d.c0) * d.cout + (size_t)kBiasBlocks * d.cout) * sizeof(float);
+}
+
+cudaError_t conv3d_wgrad_tile(const nm_conv3d_desc& d, const void* x, const void* dy, float* dw, float* db,
+                              void* workspace, uint32_t* status, cudaStream_t s) {
+  // input-channel atoms per MMA: as many as the input has, up to three
+  const int nchunks = (d.c0 + 15) / 16;
+  if (d.cout == 16) {
+    if (nchunks == 1) return launch_wgrad_tile<16, 1>(d, x, dy, dw, db, workspace, status, s);
+    if (nchunks == 2) return launch_wgrad_tile<16, 2>(d, x, dy, dw, db, workspace, status, s);
+    return launch_wgrad_tile<16, 3>(d, x, dy, dw, db, workspace, status, s);
+  }
+  if (nchunks == 1) return launch_wgrad_tile<32, 1>(d, x, dy, dw, db, workspace, status, s);
+  if (nchunks == 2) return launch_wgrad_tile<32, 2>(d, x, dy, dw, db, workspace, status, s);
+  return launch_wgrad_tile<32, 3>(d, x, dy, dw, db, workspace, status, s);
+}
+
+}  // namespace nm
