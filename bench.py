@@ -195,6 +195,11 @@ def run_gpu(args):
             torch.cuda.synchronize()
 
     seed = 1
+    # Ranks take disjoint contiguous history-id ranges (no exchange while they
+    # run); each rank's warm-up and timed steps continue through its range.
+    from paper_2111_11687_gb300 import shard
+    first, _ = shard.history_range(ws * (args.warmup + args.steps) * DECAYS_PER_STEP, ws, rank)
+    d.seek(first)
     for _ in range(args.warmup):
         d.run(DECAYS_PER_STEP, seed=seed)
     c0 = d.counters()

@@ -199,6 +199,40 @@ nm_status nm_dose_get_tally(nm_dose* h, int64_t* tally);
  * parts (counted in nm_counters.history_splits). */
 nm_status nm_dose_get_history_sigma(nm_dose* h, float* sigma);
 
+/* Sets the id of the next history (default 0; nm_dose_run and
+ * nm_dose_run_batch continue from it).  A history's random numbers depend
+ * only on (seed, id), so shards of one run on several devices or processes
+ * take disjoint id ranges [first, first + n) and their merged statistics
+ * (nm_dose_merge) equal those of one handle that ran the ranges in turn: the
+ * tally and counters bit for bit.  Ids above 2^62 are reserved
+ * (NM_ERR_ARG).  Nothing checks that ranges do not overlap. */
+nm_status nm_dose_seek(nm_dose* h, uint64_t next_history_id);
+
+/* Checkpoints of a handle's statistics (the exact cumulative tally of Eq. 1,
+ * the batch sums behind the uncertainty, the organ sums, counters, the
+ * history count, the next history id and, with history_sigma, the 128-bit
+ * sums of squared history totals) as one flat byte image that the caller
+ * owns, in host or device memory (found with pointer attributes).
+ * nm_dose_checkpoint_size gives its size for h; nm_dose_checkpoint writes it
+ * (NM_ERR_ARG if `bytes` is smaller).  The image holds no pointers: it can be
+ * written to a file or sent to another process. */
+nm_status nm_dose_checkpoint_size(const nm_dose* h, uint64_t* bytes);
+nm_status nm_dose_checkpoint(nm_dose* h, void* buf, uint64_t bytes);
+
+/* Replaces h's statistics by an image from a handle with the same grid,
+ * label slots and history_sigma option (else NM_ERR_ARG; nothing changes);
+ * runs then continue exactly as on the handle that wrote it. */
+nm_status nm_dose_restore(nm_dose* h, const void* buf, uint64_t bytes);
+
+/* Adds another shard's image (same grid and options, disjoint history ids)
+ * to h: tallies, counters and 128-bit sums add exactly, the FP64 batch and
+ * organ sums add (the shards' batches are batches of the combined run),
+ * history and batch counts add, the next id becomes the larger of the two.
+ * A host image is staged through a temporary device buffer.  NM_ERR_ARG on a
+ * mismatched image, NM_ERR_OVERFLOW if the merged tally could exceed 2^63
+ * units. */
+nm_status nm_dose_merge(nm_dose* h, const void* buf, uint64_t bytes);
+
 /* Counters and the launch shape in use. */
 nm_status nm_dose_counters(nm_dose* h, nm_counters* c);
 

@@ -110,7 +110,8 @@ struct nm_dose {
   float* out_dose = nullptr;
   float* out_sigma = nullptr;
   // host state
-  uint64_t hist_next = 0;
+  uint64_t hist_next = 0;         // histories simulated (the N of Eq. 1)
+  uint64_t id_next = 0;           // id of the next history (RNG key with the seed)
   uint64_t n_batches = 0;
   uint32_t status_seen = 0;
   double transport_ms = 0, fold_ms = 0;
@@ -577,7 +578,7 @@ nm_status nm_dose_run(nm_dose* h, uint64_t n, uint64_t seed) {
   if (h->hist_next > lim || n > lim - h->hist_next)
     return fail(NM_ERR_OVERFLOW, "%llu more histories could overflow the int64 tally",
                 (unsigned long long)n);
-  if (h->hist_next + n < h->hist_next || h->hist_next + n > (1ull << 62))
+  if (h->id_next + n < h->id_next || h->id_next + n > (1ull << 62))
     return fail(NM_ERR_OVERFLOW, "history ids exhausted");
   const int B = (uint64_t)h->opt.batches < n ? h->opt.batches : (int)n;
   cudaStream_t s = h->stream;
@@ -597,7 +598,7 @@ nm_status nm_dose_run(nm_dose* h, uint64_t n, uint64_t seed) {
     // A launch hands out at most 2^31 histories (32-bit work counter).
     for (uint64_t done = 0; done < nb;) {
       const uint64_t part = std::min<uint64_t>(nb - done, 1ull << 31);
-      const TransportParams p = h->params(h->hist_next + done, part, seed);
+      const TransportParams p = h->params(h->id_next + done, part, seed);
       NM_CUDA(cudaMemsetAsync(h->work, 0, sizeof(unsigned), s), "cudaMemsetAsync");
       NM_CUDA(launch_transport(p, h->grid, h->block, h->warp_agg, h->rayleigh, h->regroup, s, false,
                                h->opt.history_sigma != 0),
@@ -610,6 +611,7 @@ nm_status nm_dose_run(nm_dose* h, uint64_t n, uint64_t seed) {
     NM_CUDA(launch_fold(fp, s), "fold launch");
     NM_CUDA(cudaEventRecord(h->ev[4 * b + 3], s), "cudaEventRecord");
     h->hist_next += nb;
+    h->id_next += nb;
     h->n_batches += 1;
   }
   uint32_t st = 0;
@@ -666,7 +668,7 @@ extern "C" nm_status nm_dose_run_batch(nm_dose* const* hs, int32_t n, const uint
     const uint64_t per = hs[i]->units_per_history();
     const uint64_t lim = (uint64_t)INT64_MAX / (per ? per : 1);
     if (hs[i]->hist_next > lim || n_decays[i] > lim - hs[i]->hist_next ||
-        hs[i]->hist_next + n_decays[i] > (1ull << 62))
+        hs[i]->id_next + n_decays[i] > (1ull << 62))
       return fail(NM_ERR_OVERFLOW, "handle %d: too many histories", i);
     vox_sum += hs[i]->V;
     vox_hash = vox_hash * 1000003 + hs[i]->V;
@@ -712,7 +714,7 @@ extern "C" nm_status nm_dose_run_batch(nm_dose* const* hs, int32_t n, const uint
   for (int b = 0; b < B; ++b)
     for (int i = 0; i < n; ++i) {
       const uint64_t nb = n_decays[i] / B + ((uint64_t)b < n_decays[i] % B ? 1 : 0);
-      pat[(size_t)b * n + i] = hs[i]->geom(hs[i]->hist_next + off[i], nb);
+      pat[(size_t)b * n + i] = hs[i]->geom(hs[i]->id_next + off[i], nb);
       off[i] += nb;
       if (nb >= (1ull << 31)) { cleanup(); return fail(NM_ERR_ARG, "handle %d: batches above 2^31 histories", i); }
     }
@@ -848,6 +850,7 @@ extern "C" nm_status nm_dose_run_batch(nm_dose* const* hs, int32_t n, const uint
   for (int i = 0; i < n; ++i) {
     if (n_decays[i] == 0) continue;
     hs[i]->hist_next += n_decays[i];
+    hs[i]->id_next += n_decays[i];
     hs[i]->n_batches += (uint64_t)std::min<uint64_t>(B, n_decays[i]);
     hs[i]->transport_ms += ms * (double)n_decays[i] / (double)total;  // graph time, shared by decays
     hs[i]->status_seen |= flags;
@@ -958,6 +961,174 @@ nm_status nm_dose_get_tally(nm_dose* h, int64_t* tally) {
   return NM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Checkpoints: a flat byte image of a handle's statistics, host or device.
+//   header (kCkptHeader bytes, below), then tsum[V] (int64), s2[V] (FP64),
+//   org_s1, org_s2 [kLabelSlots] (FP64), counters [kCtrCount] (uint64) and,
+//   with history statistics, s2h_lo[V], s2h_hi[V] (uint64).
+// ---------------------------------------------------------------------------
+namespace {
+
+struct CkptHeader {
+  char magic[8];
+  int64_t nx, ny, nz, V, label_slots, ctr_count, history;
+  uint64_t hist_next, id_next, n_batches, status_seen;
+};
+constexpr char kCkptMagic[8] = {'N', 'M', 'D', 'O', 'S', 'E', '1', 0};
+static_assert(sizeof(CkptHeader) % 16 == 0, "checkpoint arrays stay 16-byte aligned");
+
+uint64_t ckpt_bytes(const nm_dose* h) {
+  const uint64_t V = (uint64_t)h->V;
+  return sizeof(CkptHeader) + 16 * V + 16 * (uint64_t)kLabelSlots + 8 * (uint64_t)kCtrCount +
+         (h->s2h_lo ? 16 * V : 0);
+}
+
+// Offsets of the arrays within the image.
+struct CkptOffsets {
+  uint64_t tsum, s2, org_s1, org_s2, counters, lo, hi;
+};
+CkptOffsets ckpt_offsets(int64_t V) {
+  CkptOffsets o;
+  o.tsum = sizeof(CkptHeader);
+  o.s2 = o.tsum + 8 * (uint64_t)V;
+  o.org_s1 = o.s2 + 8 * (uint64_t)V;
+  o.org_s2 = o.org_s1 + 8 * (uint64_t)kLabelSlots;
+  o.counters = o.org_s2 + 8 * (uint64_t)kLabelSlots;
+  o.lo = o.counters + 8 * (uint64_t)kCtrCount;
+  o.hi = o.lo + 8 * (uint64_t)V;
+  return o;
+}
+
+// Reads and checks the header of an image meant for handle h.
+nm_status ckpt_read_header(nm_dose* h, const void* buf, uint64_t bytes, CkptHeader* hd) {
+  if (!buf) return fail(NM_ERR_ARG, "checkpoint buffer is NULL");
+  if (bytes < sizeof(CkptHeader)) return fail(NM_ERR_ARG, "checkpoint buffer too small");
+  NM_CUDA(cudaMemcpyAsync(hd, buf, sizeof *hd, cudaMemcpyDefault, h->stream), "checkpoint header");
+  NM_CUDA(cudaStreamSynchronize(h->stream), "checkpoint header");
+  if (memcmp(hd->magic, kCkptMagic, 8) != 0) return fail(NM_ERR_ARG, "not a dose checkpoint");
+  if (hd->nx != h->nx || hd->ny != h->ny || hd->nz != h->nz || hd->V != h->V ||
+      hd->label_slots != kLabelSlots || hd->ctr_count != kCtrCount ||
+      hd->history != (h->s2h_lo ? 1 : 0))
+    return fail(NM_ERR_ARG, "checkpoint of a different grid or options");
+  if (bytes < ckpt_bytes(h)) return fail(NM_ERR_ARG, "checkpoint buffer too small");
+  return NM_OK;
+}
+
+}  // namespace
+
+nm_status nm_dose_seek(nm_dose* h, uint64_t next_history_id) {
+  if (!h) return fail(NM_ERR_ARG, "handle is NULL");
+  if (next_history_id > (1ull << 62)) return fail(NM_ERR_ARG, "history id above 2^62");
+  h->id_next = next_history_id;
+  return NM_OK;
+}
+
+nm_status nm_dose_checkpoint_size(const nm_dose* h, uint64_t* bytes) {
+  if (!h || !bytes) return fail(NM_ERR_ARG, "bad arguments");
+  *bytes = ckpt_bytes(h);
+  return NM_OK;
+}
+
+nm_status nm_dose_checkpoint(nm_dose* h, void* buf, uint64_t bytes) {
+  if (!h || !buf) return fail(NM_ERR_ARG, "bad arguments");
+  if (bytes < ckpt_bytes(h)) return fail(NM_ERR_ARG, "checkpoint buffer too small");
+  CkptHeader hd;
+  memset(&hd, 0, sizeof hd);
+  memcpy(hd.magic, kCkptMagic, 8);
+  hd.nx = h->nx; hd.ny = h->ny; hd.nz = h->nz; hd.V = h->V;
+  hd.label_slots = kLabelSlots; hd.ctr_count = kCtrCount; hd.history = h->s2h_lo ? 1 : 0;
+  hd.hist_next = h->hist_next; hd.id_next = h->id_next; hd.n_batches = h->n_batches;
+  hd.status_seen = h->status_seen;
+  const CkptOffsets o = ckpt_offsets(h->V);
+  uint8_t* b = static_cast<uint8_t*>(buf);
+  cudaStream_t s = h->stream;
+  const size_t V8 = 8 * (size_t)h->V;
+  NM_CUDA(cudaMemcpyAsync(b, &hd, sizeof hd, cudaMemcpyDefault, s), "checkpoint");
+  NM_CUDA(cudaMemcpyAsync(b + o.tsum, h->tsum, V8, cudaMemcpyDefault, s), "checkpoint");
+  NM_CUDA(cudaMemcpyAsync(b + o.s2, h->s2, V8, cudaMemcpyDefault, s), "checkpoint");
+  NM_CUDA(cudaMemcpyAsync(b + o.org_s1, h->org_s1, 8 * kLabelSlots, cudaMemcpyDefault, s), "checkpoint");
+  NM_CUDA(cudaMemcpyAsync(b + o.org_s2, h->org_s2, 8 * kLabelSlots, cudaMemcpyDefault, s), "checkpoint");
+  NM_CUDA(cudaMemcpyAsync(b + o.counters, h->counters, 8 * kCtrCount, cudaMemcpyDefault, s), "checkpoint");
+  if (h->s2h_lo) {
+    NM_CUDA(cudaMemcpyAsync(b + o.lo, h->s2h_lo, V8, cudaMemcpyDefault, s), "checkpoint");
+    NM_CUDA(cudaMemcpyAsync(b + o.hi, h->s2h_hi, V8, cudaMemcpyDefault, s), "checkpoint");
+  }
+  NM_CUDA(cudaStreamSynchronize(s), "nm_dose_checkpoint");
+  return NM_OK;
+}
+
+nm_status nm_dose_restore(nm_dose* h, const void* buf, uint64_t bytes) {
+  if (!h) return fail(NM_ERR_ARG, "handle is NULL");
+  CkptHeader hd;
+  nm_status st = ckpt_read_header(h, buf, bytes, &hd);
+  if (st != NM_OK) return st;
+  const CkptOffsets o = ckpt_offsets(h->V);
+  const uint8_t* b = static_cast<const uint8_t*>(buf);
+  cudaStream_t s = h->stream;
+  const size_t V8 = 8 * (size_t)h->V;
+  NM_CUDA(cudaMemcpyAsync(h->tsum, b + o.tsum, V8, cudaMemcpyDefault, s), "restore");
+  NM_CUDA(cudaMemcpyAsync(h->s2, b + o.s2, V8, cudaMemcpyDefault, s), "restore");
+  NM_CUDA(cudaMemcpyAsync(h->org_s1, b + o.org_s1, 8 * kLabelSlots, cudaMemcpyDefault, s), "restore");
+  NM_CUDA(cudaMemcpyAsync(h->org_s2, b + o.org_s2, 8 * kLabelSlots, cudaMemcpyDefault, s), "restore");
+  NM_CUDA(cudaMemcpyAsync(h->counters, b + o.counters, 8 * kCtrCount, cudaMemcpyDefault, s), "restore");
+  if (h->s2h_lo) {
+    NM_CUDA(cudaMemcpyAsync(h->s2h_lo, b + o.lo, V8, cudaMemcpyDefault, s), "restore");
+    NM_CUDA(cudaMemcpyAsync(h->s2h_hi, b + o.hi, V8, cudaMemcpyDefault, s), "restore");
+  }
+  NM_CUDA(cudaMemsetAsync(h->tb, 0, V8, s), "restore");
+  NM_CUDA(cudaStreamSynchronize(s), "nm_dose_restore");
+  h->hist_next = hd.hist_next;
+  h->id_next = hd.id_next;
+  h->n_batches = hd.n_batches;
+  h->status_seen = (uint32_t)hd.status_seen;
+  return NM_OK;
+}
+
+nm_status nm_dose_merge(nm_dose* h, const void* buf, uint64_t bytes) {
+  if (!h) return fail(NM_ERR_ARG, "handle is NULL");
+  CkptHeader hd;
+  nm_status st = ckpt_read_header(h, buf, bytes, &hd);
+  if (st != NM_OK) return st;
+  const uint64_t per = h->units_per_history();
+  const uint64_t lim = (uint64_t)INT64_MAX / (per ? per : 1);
+  if (h->hist_next > lim || hd.hist_next > lim - h->hist_next)
+    return fail(NM_ERR_OVERFLOW, "the merged tally could overflow int64");
+  cudaStream_t s = h->stream;
+  const uint64_t total = ckpt_bytes(h);
+  const uint8_t* b = static_cast<const uint8_t*>(buf);
+  uint8_t* tmp = nullptr;
+  if (!is_device_ptr(buf)) {
+    NM_CUDA(cudaMalloc(&tmp, total), "merge staging");
+    cudaError_t e = cudaMemcpyAsync(tmp, buf, total, cudaMemcpyDefault, s);
+    if (e != cudaSuccess) {
+      cudaFree(tmp);
+      return cuda_fail(e, "merge staging copy");
+    }
+    b = tmp;
+  }
+  const CkptOffsets o = ckpt_offsets(h->V);
+  MergeParams m;
+  m.tsum = h->tsum; m.s2 = h->s2; m.s2h_lo = h->s2h_lo; m.s2h_hi = h->s2h_hi;
+  m.org_s1 = h->org_s1; m.org_s2 = h->org_s2; m.counters = h->counters;
+  m.o_tsum = reinterpret_cast<const ull*>(b + o.tsum);
+  m.o_s2 = reinterpret_cast<const double*>(b + o.s2);
+  m.o_lo = h->s2h_lo ? reinterpret_cast<const ull*>(b + o.lo) : nullptr;
+  m.o_hi = h->s2h_lo ? reinterpret_cast<const ull*>(b + o.hi) : nullptr;
+  m.o_org_s1 = reinterpret_cast<const double*>(b + o.org_s1);
+  m.o_org_s2 = reinterpret_cast<const double*>(b + o.org_s2);
+  m.o_counters = reinterpret_cast<const ull*>(b + o.counters);
+  m.V = h->V;
+  cudaError_t e = launch_merge_stats(m, h->sms, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (tmp) cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_fail(e, "nm_dose_merge");
+  h->hist_next += hd.hist_next;
+  h->n_batches += hd.n_batches;
+  h->id_next = h->id_next > hd.id_next ? h->id_next : hd.id_next;
+  h->status_seen |= (uint32_t)hd.status_seen;
+  return NM_OK;
+}
+
 nm_status nm_dose_counters(nm_dose* h, nm_counters* c) {
   if (!h || !c) return fail(NM_ERR_ARG, "bad arguments");
   ull v[kCtrCount];
@@ -1004,6 +1175,7 @@ nm_status nm_dose_reset(nm_dose* h) {
   }
   NM_CUDA(cudaStreamSynchronize(s), "reset");
   h->hist_next = 0;
+  h->id_next = 0;
   h->n_batches = 0;
   h->status_seen = 0;
   h->transport_ms = h->fold_ms = 0;

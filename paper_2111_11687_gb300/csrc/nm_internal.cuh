@@ -187,6 +187,16 @@ struct FoldParams {
 int fold_blocks(int64_t V);
 cudaError_t launch_fold(const FoldParams& p, cudaStream_t s);
 
+// Adds another shard's statistics (o_*) into a handle's (all device arrays;
+// s2h_lo/hi and o_lo/hi NULL without history statistics).
+struct MergeParams {
+  ull* tsum; double* s2; ull* s2h_lo; ull* s2h_hi; double* org_s1; double* org_s2; ull* counters;
+  const ull* o_tsum; const double* o_s2; const ull* o_lo; const ull* o_hi;
+  const double* o_org_s1; const double* o_org_s2; const ull* o_counters;
+  int64_t V;
+};
+cudaError_t launch_merge_stats(const MergeParams& m, int sms, cudaStream_t s);
+
 struct FinalizeParams {
   const ull* tsum;
   const double* s2;

@@ -213,6 +213,41 @@ cudaError_t launch_map_organ_means(const float* dose, const uint8_t* labels, int
   return cudaGetLastError();
 }
 
+namespace {
+
+// Statistics of two shards of one run (disjoint history ids): the exact
+// tallies and counters add as integers, the 128-bit sums of squared history
+// totals add with a carry, and the FP64 batch sums add because the batches of
+// both shards are batches of the combined run.
+__global__ void merge_stats_kernel(const MergeParams m) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < m.V; v += stride) {
+    m.tsum[v] += m.o_tsum[v];
+    m.s2[v] += m.o_s2[v];
+    if (m.s2h_lo) {
+      const ull lo = m.s2h_lo[v] + m.o_lo[v];
+      m.s2h_hi[v] += m.o_hi[v] + (lo < m.o_lo[v] ? 1ull : 0ull);
+      m.s2h_lo[v] = lo;
+    }
+  }
+  if (blockIdx.x == 0) {
+    for (int i = threadIdx.x; i < kLabelSlots; i += blockDim.x) {
+      m.org_s1[i] += m.o_org_s1[i];
+      m.org_s2[i] += m.o_org_s2[i];
+    }
+    for (int i = threadIdx.x; i < kCtrCount; i += blockDim.x) m.counters[i] += m.o_counters[i];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_merge_stats(const MergeParams& m, int sms, cudaStream_t s) {
+  const int64_t want = (m.V + 255) / 256;
+  const int grid = (int)(want < 8LL * sms ? (want > 0 ? want : 1) : 8LL * sms);
+  merge_stats_kernel<<<grid, 256, 0, s>>>(m);
+  return cudaGetLastError();
+}
+
 int fold_blocks(int64_t V) { return (int)((V + kFoldTile - 1) / kFoldTile); }
 
 cudaError_t launch_fold(const FoldParams& p, cudaStream_t s) {

@@ -92,6 +92,11 @@ _SIGS = {
     "nm_dose_map_organs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "nm_dose_counters": (C.c_int, [C.c_void_p, C.POINTER(nm_counters)]),
     "nm_dose_reset": (C.c_int, [C.c_void_p]),
+    "nm_dose_seek": (C.c_int, [C.c_void_p, C.c_uint64]),
+    "nm_dose_checkpoint_size": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64)]),
+    "nm_dose_checkpoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64]),
+    "nm_dose_restore": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64]),
+    "nm_dose_merge": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64]),
     "nm_dose_destroy": (None, [C.c_void_p]),
     "nm_check_philox": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "nm_check_kahn": (C.c_int, [C.c_double, C.c_int64, C.c_uint64, C.c_void_p]),
@@ -409,6 +414,12 @@ def nm_denoise_scales(dose, activity, density, stream=None):
     return ds.value, as_.value
 
 
+def _nbytes(buf) -> int:
+    if isinstance(buf, np.ndarray):
+        return int(buf.nbytes)
+    return int(buf.numel() * buf.element_size())
+
+
 class Dose:
     """Owning wrapper of an nm_dose handle."""
 
@@ -453,6 +464,30 @@ class Dose:
 
     def reset(self):
         nm_dose_reset(self.h)
+
+    def seek(self, next_history_id: int):
+        """Id of the next history (shards of one run take disjoint ranges)."""
+        _check(load().nm_dose_seek(self.h, int(next_history_id)))
+
+    def checkpoint_size(self) -> int:
+        n = C.c_uint64()
+        _check(load().nm_dose_checkpoint_size(self.h, C.byref(n)))
+        return n.value
+
+    def checkpoint(self, out=None):
+        """The statistics as a byte image (numpy uint8 by default, or into
+        ``out``: any host or device buffer of at least checkpoint_size() bytes)."""
+        if out is None:
+            out = np.empty(self.checkpoint_size(), np.uint8)
+        _check(load().nm_dose_checkpoint(self.h, ptr(out), _nbytes(out)))
+        return out
+
+    def restore(self, image):
+        _check(load().nm_dose_restore(self.h, ptr(image), _nbytes(image)))
+
+    def merge(self, image):
+        """Adds another shard's image (disjoint history ids) to these statistics."""
+        _check(load().nm_dose_merge(self.h, ptr(image), _nbytes(image)))
 
     def close(self):
         if self.h:
