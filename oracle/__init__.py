@@ -66,6 +66,8 @@ class _Problem(C.Structure):
         ("batches", C.c_int32),
         ("threads", C.c_int32),
         ("activity_bq", C.c_double),
+        ("beta_max_mev", C.c_double),
+        ("beta_z", C.c_int32),
     ]
 
 
@@ -99,6 +101,14 @@ def _load():
         lib.orc_sample_dirs.argtypes = [C.c_int64, C.c_uint64, p(d)]
         lib.orc_rotate.restype = None
         lib.orc_rotate.argtypes = [p(d), d, d]
+        lib.orc_beta_density.restype = d
+        lib.orc_beta_density.argtypes = [d, d, C.c_int32]
+        lib.orc_sample_beta.restype = None
+        lib.orc_sample_beta.argtypes = [d, C.c_int32, C.c_int64, C.c_uint64, p(d)]
+        lib.orc_range_kp.restype = d
+        lib.orc_range_kp.argtypes = [d]
+        lib.orc_energy_at_range.restype = d
+        lib.orc_energy_at_range.argtypes = [d]
         lib.orc_run.restype = C.c_int
         lib.orc_run.argtypes = [p(_Problem), p(C.c_int64), p(d), p(d), p(d), p(d), p(d), p(_Counters), p(d)]
         _lib = lib
@@ -214,14 +224,40 @@ class Result:
     sigma_history: np.ndarray = None  # Gy/s, history-by-history sigma of the mean (if asked for)
 
 
+def beta_density(t: float, t_max: float, z: int) -> float:
+    """Unnormalised allowed beta+ spectrum N(T) with the Fermi function (daughter Z)."""
+    return _load().orc_beta_density(float(t), float(t_max), int(z))
+
+
+def sample_beta(t_max: float, z: int, n: int, seed: int) -> np.ndarray:
+    """Positron kinetic energies (MeV) drawn from N(T) by rejection."""
+    out = np.empty(n)
+    _load().orc_sample_beta(float(t_max), int(z), n, seed, _dp(out))
+    return out
+
+
+def range_kp(t_mev: float) -> float:
+    """Katz-Penfold range (g/cm^2) of an electron or positron of kinetic energy T."""
+    return _load().orc_range_kp(float(t_mev))
+
+
+def energy_at_range(r_gcm2: float) -> float:
+    """Inverse of range_kp: the kinetic energy whose range is R."""
+    return _load().orc_energy_at_range(float(r_gcm2))
+
+
 def run(density, material, mat: Materials, *, activity=None, labels=None, n_labels: int = 0,
         spacing=(1.0, 1.0, 1.0), point=None, photon_mev: float = 0.511, positron_mev: float = 0.25,
         n_hist: int, seed: int = 1, batches: int = 10, threads: int = 0, first_history: int = 0,
-        activity_bq: float = 1.0, history_sigma: bool = False) -> Result:
+        activity_bq: float = 1.0, history_sigma: bool = False, beta_max_mev: float = 0.0,
+        beta_z: int = 8) -> Result:
     """Run the oracle MC.  Arrays are [nz, ny, nx] (x fastest); spacing (dx, dy, dz) in cm.
 
     ``point`` (cm, xyz) selects point-photon mode (one photon per history);
-    otherwise decays are drawn from ``activity``.  ``history_sigma`` also
+    otherwise decays are drawn from ``activity``.  ``beta_max_mev`` > 0 draws
+    each positron's energy from the allowed beta+ spectrum with that endpoint
+    (daughter atomic number ``beta_z``) and follows it along a straight track
+    of Katz-Penfold range; else ``positron_mev`` is deposited at the decay.  ``history_sigma`` also
     returns the history-by-history sigma of the mean dose rate (Walters et al.
     2002: the spread of each history's total deposit per voxel).
     """
@@ -252,6 +288,8 @@ def run(density, material, mat: Materials, *, activity=None, labels=None, n_labe
     pr.batches = batches
     pr.threads = threads
     pr.activity_bq = activity_bq
+    pr.beta_max_mev = beta_max_mev
+    pr.beta_z = beta_z
     tally = np.empty(density.shape, np.int64)
     dr = np.empty(density.shape, np.float64)
     sg = np.empty(density.shape, np.float64)

@@ -22,6 +22,9 @@
 //   * RNG: std::mt19937_64, seeded per chunk of histories;
 //   * tallies: int64 fixed point, one unit = 2^-6 eV, every deposit a difference
 //     q(E_before) - q(E_after) so that energy conservation is exact;
+//   * positron (optional): kinetic energy by rejection from the allowed beta+
+//     spectrum with the Fermi function, a straight track that uses up the Katz-
+//     Penfold mass range voxel by voxel, annihilation at its end;
 //   * statistics: batch means over B batches, Eq. 1 dose rate, Eq. 2 organ means,
 //     Eq. 3 organ RMS relative uncertainty, batch sigma of the organ means; and,
 //     on request, the history-by-history sigma (§2.1's method, Walters et al.
@@ -47,6 +50,7 @@ constexpr double kClassicalRadiusCm = 2.8179403262e-13;  // r_e
 constexpr double kAvogadro = 6.02214076e23;
 constexpr double kJoulePerEv = 1.602176634e-19;
 constexpr double kPi = 3.14159265358979323846;
+constexpr double kFineStructure = 7.2973525693e-3;     // alpha
 // Tally unit: 2^-6 eV, so 1 MeV = 6.4e7 units.
 constexpr double kUnitsPerMeV = 64.0e6;
 
@@ -272,9 +276,78 @@ bool traverse(const Grid& g, const double p[3], const double dir[3], F&& visit) 
   }
 }
 
+// ---- beta+ spectrum and positron range --------------------------------------
+// Allowed beta+ spectrum (Fermi's theory of beta decay): with T the positron's
+// kinetic energy, E = T + m c^2 its total energy and p c = sqrt(T (T + 2 m c^2)),
+//   N(T) dT  proportional to  F(Z, E) p E (T_max - T)^2 dT,   0 < T < T_max,
+// where F is the non-relativistic Fermi function of a positron leaving a
+// daughter of atomic number Z: F = 2 pi eta / (1 - exp(-2 pi eta)) with
+// eta = -Z alpha E / (p c) (repulsion: F < 1, vanishing at low T).
+double beta_density(double t, double t_max, int z) {
+  if (!(t > 0.0) || !(t < t_max)) return 0.0;
+  const double e = t + kElectronMassMeV;
+  const double pc = std::sqrt(t * (t + 2.0 * kElectronMassMeV));
+  double f = 1.0;
+  if (z != 0) {
+    const double x = 2.0 * kPi * (-(double)z * kFineStructure * e / pc);
+    f = x / (-std::expm1(-x));
+  }
+  return f * pc * e * (t_max - t) * (t_max - t);
+}
+
+// Rejection sampling of N(T): T uniform on (0, T_max), accepted with
+// probability N(T) / envelope; the envelope is the density's maximum over a
+// fine scan, raised by 2 % (N is smooth, so the scan is within far less).
+struct BetaSampler {
+  double t_max = 0.0, env = 0.0;
+  int z = 0;
+  BetaSampler(double tm, int zz) : t_max(tm), z(zz) {
+    constexpr int kScan = 1 << 16;
+    for (int i = 1; i < kScan; ++i) env = std::max(env, beta_density(t_max * i / kScan, t_max, z));
+    env *= 1.02;
+  }
+  double operator()(Rng& r) const {
+    for (;;) {
+      const double t = r.u() * t_max;
+      if (r.u() * env < beta_density(t, t_max, z)) return t;
+    }
+  }
+};
+
+// Positron range, Katz and Penfold (1952), electrons in low-Z matter:
+//   R(T) = 0.412 T^(1.265 - 0.0954 ln T)  g/cm^2,  T in MeV,
+// and its inverse: with L = ln T, 0.0954 L^2 - 1.265 L + ln(R / 0.412) = 0,
+// the root below L = 1.265 / (2 x 0.0954) (where R increases with T).
+double range_kp(double t) {
+  if (!(t > 0.0)) return 0.0;
+  const double l = std::log(t);
+  return 0.412 * std::exp((1.265 - 0.0954 * l) * l);
+}
+
+double energy_at_range(double r) {
+  if (!(r > 0.0)) return 0.0;
+  const double c = std::log(r / 0.412);
+  const double disc = 1.265 * 1.265 - 4.0 * 0.0954 * c;
+  return std::exp((1.265 - std::sqrt(std::max(disc, 0.0))) / (2.0 * 0.0954));
+}
+
 }  // namespace
 
 extern "C" {
+
+// Unnormalised beta+ spectrum N(T) (pinned by the tests through its mean and
+// its statistical-shape limit).
+double orc_beta_density(double t, double t_max, int32_t z) { return beta_density(t, t_max, z); }
+
+void orc_sample_beta(double t_max, int32_t z, int64_t n, uint64_t seed, double* out) {
+  Rng r;
+  r.g.seed(seed);
+  const BetaSampler s(t_max, z);
+  for (int64_t i = 0; i < n; ++i) out[i] = s(r);
+}
+
+double orc_range_kp(double t) { return range_kp(t); }
+double orc_energy_at_range(double r) { return energy_at_range(r); }
 
 // Path lengths of a ray through the grid (pins the traversal against brute
 // force): writes up to cap (voxel, length) pairs, returns the count.
@@ -356,6 +429,8 @@ typedef struct {
   int32_t batches;              // >= 2
   int32_t threads;              // 0 = all hardware threads
   double activity_bq;           // A(t_s) of Eq. 1
+  double beta_max_mev;          // > 0: positron energy from the beta+ spectrum, positron range
+  int32_t beta_z;               // daughter's atomic number (Fermi function)
 } orc_problem;
 
 typedef struct {
@@ -396,6 +471,9 @@ int orc_run(const orc_problem* pr, int64_t* tally_sum, double* dose_rate, double
       pr->threads > 0 ? pr->threads : std::max(1u, std::thread::hardware_concurrency());
   const int64_t q_photon = q_units(pr->photon_mev);
   const int64_t q_positron = pr->point_mode ? 0 : q_units(pr->positron_mev);
+  const bool beta = !pr->point_mode && pr->beta_max_mev > 0.0;
+  if (beta && !(pr->beta_max_mev < 20.0)) return 1;
+  const BetaSampler beta_sampler(beta ? pr->beta_max_mev : 1.0, pr->beta_z);
   const double cut = pr->mat.photon_cut_mev;
 
   std::vector<int64_t> tb(V);
@@ -544,9 +622,43 @@ int orc_run(const orc_problem* pr, int64_t* tally_sum, double* dose_rate, double
             p[0] = (ix + r.u()) * pr->dx;
             p[1] = (iy + r.u()) * pr->dy;
             p[2] = (iz + r.u()) * pr->dz;
-            // Positron kinetic energy deposited in the decay voxel.
-            c.emitted += q_positron;
-            deposit(v0, q_positron, c);
+            if (!beta) {
+              // Positron kinetic energy deposited in the decay voxel.
+              c.emitted += q_positron;
+              deposit(v0, q_positron, c);
+            } else {
+              // Positron energy from the spectrum; a straight track in an
+              // isotropic direction uses up the mass range R(T) voxel by voxel
+              // (the continuous-slowing-down energy at the remaining range
+              // gives each voxel's deposit); the pair annihilates at its end.
+              const double t0 = beta_sampler(r);
+              double dp[3];
+              marsaglia(r, dp);
+              c.emitted += q_units(t0);
+              double t_cur = t0, r_rem = range_kp(t0), s_end = 0.0;
+              const bool left = traverse(g, p, dp, [&](int64_t v, double a, double b) {
+                const double rho = pr->density[v];
+                const double m = rho * (b - a);
+                if (m >= r_rem) {
+                  deposit(v, q_units(t_cur), c);
+                  s_end = a + r_rem / rho;
+                  return false;
+                }
+                r_rem -= m;
+                const double t_new = energy_at_range(r_rem);
+                deposit(v, q_units(t_cur) - q_units(t_new), c);
+                t_cur = t_new;
+                return true;
+              });
+              if (left) {
+                // annihilation outside the grid (vacuum): both photons escape
+                c.emitted += 2 * q_photon;
+                c.escaped += q_units(t_cur) + 2 * q_photon;
+                if (sigma_history) end_history(c);
+                continue;
+              }
+              for (int a = 0; a < 3; ++a) p[a] += s_end * dp[a];
+            }
           }
           marsaglia(r, d);
           transport(r, p, d, c);

@@ -454,3 +454,115 @@ def test_history_sigma_bernoulli_closed_form(orc, absorb):
     # the batch sigma estimates the same quantity, with ~25 % scatter at 10 batches
     ratio = r.sigma / r.sigma_history
     assert 0.85 < np.median(ratio) < 1.15
+
+
+# ---------------------------------------------------------------------------
+# Positron: beta+ spectrum and range (the beta-spectrum variant of the decay)
+# ---------------------------------------------------------------------------
+F18_T_MAX = 0.6335     # MeV, 18F beta+ endpoint (nuclear data tables)
+F18_T_MEAN = 0.2498    # MeV, 18F mean beta+ energy (nuclear data tables)
+
+
+def test_beta_spectrum_mean_of_18f(orc):
+    # The published mean of 18F's positrons, which is also the 0.25 MeV the
+    # constant-deposit model uses.  Without the Fermi function the mean would
+    # be 0.2404 MeV and with the electron's (attractive) one lower still, so a
+    # missing or sign-flipped Coulomb factor fails here.
+    t = orc.sample_beta(F18_T_MAX, 8, 2_000_000, 3)
+    assert 0.0 < t.min() and t.max() < F18_T_MAX
+    assert abs(t.mean() / F18_T_MEAN - 1.0) < 0.005
+    assert abs(t.mean() / 0.25 - 1.0) < 0.005
+    t0 = orc.sample_beta(F18_T_MAX, 0, 1_000_000, 4)
+    assert t0.mean() < 0.243
+
+
+def test_beta_spectrum_statistical_shape_limit(orc):
+    # Z = 0 and an endpoint far below m c^2: p E (T_max - T)^2 tends to
+    # sqrt(T) (T_max - T)^2, the Beta(3/2, 3) law on [0, T_max] (corrections
+    # O(T_max / m c^2) = 0.2 %, far below the test's resolution).
+    t_max = 1e-3
+    t = orc.sample_beta(t_max, 0, 200_000, 5)
+    ks = stats.kstest(t, stats.beta(1.5, 3.0, scale=t_max).cdf)
+    assert ks.pvalue > 1e-3
+    assert abs(t.mean() / (t_max / 3.0) - 1.0) < 0.01
+
+
+# NIST ESTAR, electrons in liquid water: CSDA range (g/cm^2).  The Katz-Penfold
+# relation is an empirical fit of practical ranges, within ~10 % of these.
+ESTAR_WATER_CSDA = {0.1: 1.431e-2, 0.2: 4.488e-2, 0.5: 1.766e-1, 1.0: 4.367e-1}
+
+
+def test_positron_range_against_estar(orc):
+    for t, r in ESTAR_WATER_CSDA.items():
+        assert abs(orc.range_kp(t) / r - 1.0) < 0.10, t
+    for t in np.geomspace(1e-3, 2.0, 23):
+        assert abs(orc.energy_at_range(orc.range_kp(t)) / t - 1.0) < 1e-12
+    assert orc.range_kp(0.0) == 0.0 and orc.energy_at_range(0.0) == 0.0
+
+
+def _cube_positron_expectation(rho, n_side, vox, t, rng):
+    """Per decay, brute force: straight tracks from a uniform point of the
+    central voxel in isotropic directions; the energy left when a track
+    reaches the cube's surface escapes, the energy lost before it leaves the
+    central voxel stays there."""
+    L = n_side * vox
+    c0 = (n_side // 2) * vox
+    n = t.size
+    x = c0 + vox * rng.random((n, 3))
+    u = rng.normal(size=(n, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+
+    def exit_dist(lo, hi):
+        with np.errstate(divide="ignore"):
+            d = np.where(u > 0, (hi - x) / u, np.where(u < 0, (lo - x) / u, np.inf))
+        return d.min(axis=1)
+
+    def kp(tt):
+        lt = np.log(tt)
+        return 0.412 * np.exp((1.265 - 0.0954 * lt) * lt)
+
+    def kp_inv(r):
+        c = np.log(r / 0.412)
+        return np.exp((1.265 - np.sqrt(1.265 ** 2 - 4 * 0.0954 * c)) / (2 * 0.0954))
+
+    r = kp(t)
+
+    def residual(d):
+        left = r - rho * d
+        out = np.zeros_like(t)
+        m = left > 0
+        out[m] = kp_inv(left[m])
+        return out
+
+    esc = residual(exit_dist(0.0, L))
+    centre = t - residual(exit_dist(c0, c0 + vox))
+    return esc, centre
+
+
+@pytest.mark.parametrize("rho", [1.0, 0.5])
+def test_positron_track_escape_and_local_deposit(orc, rho):
+    # Photons that never interact (mu = 0) leave the 5^3 cube; what stays is
+    # the positrons' energy.  The oracle's escaped positron energy and its
+    # central-voxel deposit per decay must match the brute-force expectation
+    # over the same spectrum (halving the density doubles every range).
+    n_side, vox, N = 5, 0.05, 200_000
+    den = np.full((n_side,) * 3, rho)
+    act = np.zeros((n_side,) * 3)
+    act[2, 2, 2] = 1.0
+    mat = orc.Materials(z_over_a=[0.0], zeff=[7.42], pe_coeff=0.0)
+    r = orc.run(den, np.zeros((n_side,) * 3, np.uint8), mat, activity=act, spacing=(vox,) * 3, n_hist=N,
+                seed=8, batches=2, beta_max_mev=F18_T_MAX, beta_z=8)
+    c = r.counters
+    q = 64e6
+    q_photon = round(0.511 * q)
+    assert c["deposited"] + c["escaped"] == c["emitted"]
+    assert c["compton"] == 0 and c["photo"] == 0
+    esc_pos = (c["escaped"] - 2 * N * q_photon) / q / N          # MeV per decay
+    centre = r.tally[2, 2, 2] / q / N
+    rng = np.random.default_rng(17)
+    t = orc.sample_beta(F18_T_MAX, 8, 1_000_000, 23)
+    e_esc, e_centre = _cube_positron_expectation(rho, n_side, vox, t, rng)
+    for got, ref in ((esc_pos, e_esc), (centre, e_centre)):
+        sd = ref.std() * math.sqrt(1.0 / N + 1.0 / ref.size)
+        assert abs(got - ref.mean()) < 4.0 * sd + 1e-6, (got, ref.mean(), sd)
+    assert esc_pos > 0.0 and centre > 0.03
