@@ -97,6 +97,20 @@ typedef struct {
   int32_t history_sigma;     /* 1: also keep history-by-history statistics (the paper's
                                 uncertainty method, §2.1; +16 B per voxel, no warp
                                 aggregation); read with nm_dose_get_history_sigma */
+  double beta_max_mev;       /* decay mode.  0 (default): positron_mev is deposited in the
+                                decay voxel (§2.1's positron, locally absorbed).  > 0
+                                (< 20): the positron's kinetic energy T is drawn from the
+                                allowed beta+ spectrum with this endpoint (18F: 0.6335),
+                                N(T) ~ F(Z, E) p E (T_max - T)^2 with the non-relativistic
+                                Fermi function of a positron, and the positron runs a
+                                straight track in an isotropic direction whose mass range
+                                (g/cm^2) is Katz-Penfold's R(T) = 0.412 T^(1.265 - 0.0954
+                                ln T), each voxel keeping the energy lost in it (the energy
+                                at the remaining range), and both photons start where the
+                                track ends; a track that leaves the grid takes its energy
+                                and both photons out with it.  Not in nm_dose_tally_noalloc. */
+  int32_t beta_z;            /* atomic number of the daughter for the Fermi function
+                                (18F -> 18O: 8, the default), 0..100 */
 } nm_options;
 
 typedef struct {
@@ -254,6 +268,12 @@ nm_status nm_check_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, u
 /* n Klein-Nishina scattering cosines at energy e_mev drawn by the device's
  * Kahn sampler with key (seed) and counters 0..n-1; cos_out[n] host. */
 nm_status nm_check_kahn(double e_mev, int64_t n, uint64_t seed, float* cos_out);
+
+/* n positron kinetic energies (MeV) as the transport draws them in the beta+
+ * spectrum mode (beta_max_mev = t_max_mev, beta_z = z), for histories 0..n-1
+ * with key (seed): inverse-CDF table built in FP64 on the host, linear between
+ * its kBetaTable = 1024 nodes.  t_out[n] host. */
+nm_status nm_check_beta(double t_max_mev, int32_t z, int64_t n, uint64_t seed, float* t_out);
 
 /* The handle's alias table: n_active entries of (prob, voxel, alias voxel).
  * Pass NULL arrays to query *n_active only.  Host pointers. */

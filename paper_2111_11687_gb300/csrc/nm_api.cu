@@ -63,6 +63,43 @@ double sigma_kn(double e_mev) {
   return 2.0 * M_PI * kClassicalRadiusCm * kClassicalRadiusCm * (t1 + t2 - t3);
 }
 
+// Inverse CDF of the allowed beta+ spectrum, in FP64: with T the kinetic
+// energy, E = T + m c^2 and p c = sqrt(T (T + 2 m c^2)),
+//   N(T) = F p E (T_max - T)^2,  F = 2 pi eta / (1 - exp(-2 pi eta)),
+//   eta = -Z alpha E / (p c)  (the non-relativistic Fermi function, positron),
+// integrated by the trapezoid rule on 2^16 panels; node i of the table is the
+// energy below which a fraction i / kBetaTable of the positrons lie (linear in
+// the cumulative sum between panel edges).
+std::vector<float> beta_inverse_cdf(double t_max, int z) {
+  constexpr double kAlpha = 7.2973525693e-3;
+  auto density = [&](double t) {
+    if (!(t > 0.0) || !(t < t_max)) return 0.0;
+    const double e = t + kElectronMassMeV;
+    const double pc = std::sqrt(t * (t + 2.0 * kElectronMassMeV));
+    double f = 1.0;
+    if (z > 0) {
+      const double x = -2.0 * M_PI * z * kAlpha * e / pc;
+      f = x / -std::expm1(-x);
+    }
+    return f * pc * e * (t_max - t) * (t_max - t);
+  };
+  constexpr int kPanels = 1 << 16;
+  std::vector<double> cum(kPanels + 1, 0.0);
+  const double h = t_max / kPanels;
+  for (int i = 0; i < kPanels; ++i) cum[i + 1] = cum[i] + 0.5 * h * (density(i * h) + density((i + 1) * h));
+  std::vector<float> tab(kBetaTable + 1);
+  tab[0] = 0.0f;
+  tab[kBetaTable] = (float)t_max;
+  int j = 0;
+  for (int i = 1; i < kBetaTable; ++i) {
+    const double target = cum[kPanels] * i / kBetaTable;
+    while (cum[j + 1] < target) ++j;
+    const double w = (target - cum[j]) / (cum[j + 1] - cum[j]);
+    tab[i] = (float)((j + w) * h);
+  }
+  return tab;
+}
+
 template <class T>
 cudaError_t dalloc(T** p, size_t n) {
   return cudaMalloc((void**)p, n * sizeof(T) > 0 ? n * sizeof(T) : 1);
@@ -96,6 +133,8 @@ struct nm_dose {
   float* kn = nullptr;
   float* minv = nullptr;
   float* minv_out = nullptr;
+  float* beta_tab = nullptr;   // beta+ spectrum inverse CDF (kBetaTable + 1), or NULL
+  int32_t q_beta_max = 0;      // q_units(beta endpoint): bound of one positron's energy
   ull* s2h_lo = nullptr;       // history statistics (history_sigma): 128-bit sums of squares
   ull* s2h_hi = nullptr;
   ull* counters = nullptr;     // kCtrCount
@@ -124,7 +163,7 @@ struct nm_dose {
   double batch_graph_ms = 0;      // device time of graphs launched by nm_dose_run_batch
 
   ~nm_dose() {
-    void* ptrs[] = {vox, density, labels, alias, tb, tsum, s2, kn, minv, minv_out, s2h_lo, s2h_hi, counters, work, status,
+    void* ptrs[] = {vox, density, labels, alias, tb, tsum, s2, kn, minv, minv_out, beta_tab, s2h_lo, s2h_hi, counters, work, status,
                     rho_max_bits, org_s1, org_s2, organ_count, organ_partial, organ_out,
                     out_dose, out_sigma};
     for (void* p : ptrs)
@@ -148,7 +187,8 @@ struct nm_dose {
     g.inv_dx = 1.0f / dx; g.inv_dy = 1.0f / dy; g.inv_dz = 1.0f / dz;
     g.source_mode = opt.source_mode;
     g.px = opt.point[0] / dx; g.py = opt.point[1] / dy; g.pz = opt.point[2] / dz;
-    g.q_positron = q_pos;
+    g.q_positron = beta_tab ? 0 : q_pos;
+    g.beta_tab = beta_tab;
     for (int a = 0; a < 3; ++a) {
       g.blo[a] = blo[a];
       g.bhi[a] = bhi[a];
@@ -186,9 +226,11 @@ struct nm_dose {
     // one tally unit = 2^-6 eV; mass = rho [g/cm^3] * volume [cm^3] * 1e-3 kg/g
     return kJoulePerEv / 64.0 / (1e-3 * (double)dx * (double)dy * (double)dz);
   }
+  // Upper bound of one history's energy (the exact value with a constant positron).
   uint64_t units_per_history() const {
-    return opt.source_mode == NM_SOURCE_DECAY ? 2ull * (uint64_t)q_e0 + (uint64_t)q_pos
-                                              : (uint64_t)q_e0;
+    return opt.source_mode == NM_SOURCE_DECAY
+               ? 2ull * (uint64_t)q_e0 + (uint64_t)(beta_tab ? q_beta_max : q_pos)
+               : (uint64_t)q_e0;
   }
 };
 
@@ -209,6 +251,8 @@ void nm_options_default(nm_options* o) {
   o->regroup = -1;
   o->max_steps = 100000;
   o->stream = nullptr;
+  o->beta_max_mev = 0.0;
+  o->beta_z = 8;
 }
 
 const char* nm_last_error(void) { return g_err.c_str(); }
@@ -262,13 +306,16 @@ struct Shape {
   }
 };
 
-typedef std::tuple<int, int, int, int, int, int, int> TuneKey;
+// (device, grid, source mode, Rayleigh, free-parameter bits + variant bits,
+//  the fixed values of the parameters that are not tuned)
+typedef std::tuple<int, int, int, int, int, int, int, int, int, int, int, int> TuneKey;
 static std::mutex g_tune_mu;
 static std::map<TuneKey, Shape> g_tune_cache;
 
 static int grid_for_shape(const nm_dose* h, const Shape& sh, bool multi) {
   const int per_sm = transport_max_blocks_per_sm(sh.block, sh.warp_agg, h->rayleigh, sh.regroup, multi,
-                                                 !multi && h->opt.history_sigma != 0);
+                                                 !multi && h->opt.history_sigma != 0,
+                                                 !multi && h->beta_tab != nullptr);
   return per_sm * h->sms;
 }
 
@@ -285,7 +332,10 @@ static nm_status autotune(nm_dose* h, Shape sh, bool free_block, bool free_chunk
                           bool free_regroup, bool free_lanes) {
   const TuneKey key{h->device, h->nx, h->ny, h->nz, h->opt.source_mode, h->rayleigh,
                     (free_block ? 1 : 0) | (free_chunk ? 2 : 0) | (free_agg ? 4 : 0) |
-                        (free_regroup ? 8 : 0) | (free_lanes ? 16 : 0)};
+                        (free_regroup ? 8 : 0) | (free_lanes ? 16 : 0) | (h->opt.history_sigma ? 32 : 0) |
+                        (h->beta_tab ? 64 : 0),
+                    free_block ? 0 : sh.block, free_chunk ? 0 : sh.chunk, free_agg ? 0 : sh.warp_agg,
+                    free_regroup ? 0 : sh.regroup, free_lanes ? 0 : sh.lanes};
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tune_cache.find(key);
@@ -378,16 +428,16 @@ static nm_status choose_shape(nm_dose* h) {
   // A point source concentrates deposits near the source, where lanes of a
   // warp often hit the same voxel; a spread-out source rarely does.
   sh.warp_agg = o.warp_aggregate >= 0 ? (o.warp_aggregate != 0) : (o.source_mode == NM_SOURCE_POINT);
-  if (o.history_sigma) {
-    // per-history totals need lane-wise deposits
-    if (o.warp_aggregate > 0) return fail(NM_ERR_ARG, "history_sigma needs warp_aggregate = 0");
+  if (o.history_sigma || h->beta_tab) {
+    // per-history totals and positron tracks deposit lane by lane
+    if (o.warp_aggregate > 0) return fail(NM_ERR_ARG, "history_sigma and the beta+ spectrum need warp_aggregate = 0");
     sh.warp_agg = 0;
   }
   sh.regroup = o.regroup >= 0 ? (o.regroup != 0) : 1;
   sh.lanes = o.regroup_lanes > 0 ? o.regroup_lanes : 12;
   apply_shape(h, sh);
   if (h->grid <= 0) return fail(NM_ERR_ARG, "transport kernel cannot launch with %d threads", h->block);
-  const bool fb = o.block_threads <= 0, fc = o.chunk <= 0, fa = o.warp_aggregate < 0 && !o.history_sigma,
+  const bool fb = o.block_threads <= 0, fc = o.chunk <= 0, fa = o.warp_aggregate < 0 && !o.history_sigma && !h->beta_tab,
              fr = o.regroup < 0, fl = o.regroup_lanes <= 0 && sh.regroup;
   if (fb || fc || fa || fr || fl) return autotune(h, sh, fb, fc, fa, fr, fl);
   return NM_OK;
@@ -420,6 +470,8 @@ nm_status nm_dose_create(nm_dose** out, const nm_grid* g, const nm_materials* mt
   if (!(o.positron_mev >= 0) || o.positron_mev > 1.0) return fail(NM_ERR_ARG, "positron energy must be in [0, 1] MeV");
   if (!(o.activity_bq >= 0) || !std::isfinite(o.activity_bq)) return fail(NM_ERR_ARG, "activity_bq must be finite and >= 0");
   if (o.max_steps <= 0) return fail(NM_ERR_ARG, "max_steps must be > 0");
+  if (!(o.beta_max_mev >= 0.0 && o.beta_max_mev < 20.0) || o.beta_z < 0 || o.beta_z > 100)
+    return fail(NM_ERR_ARG, "beta_max_mev must be in [0, 20) MeV and beta_z in 0..100");
   for (int m = 0; m < mt->n; ++m)
     if (!(mt->z_over_a[m] >= 0) || !(mt->zeff[m] >= 0)) return fail(NM_ERR_ARG, "material %d: negative constants", m);
   if (o.source_mode == NM_SOURCE_POINT) {
@@ -473,6 +525,14 @@ nm_status nm_dose_create(nm_dose** out, const nm_grid* g, const nm_materials* mt
       (e = dalloc(&h->organ_out, 4 * kLabelSlots)))
     return bail(cuda_fail(e, "device allocation"));
   if (labels && (e = dalloc(&h->labels, V))) return bail(cuda_fail(e, "device allocation"));
+  std::vector<float> beta;
+  if (o.source_mode == NM_SOURCE_DECAY && o.beta_max_mev > 0.0) {
+    beta = beta_inverse_cdf(o.beta_max_mev, o.beta_z);
+    h->q_beta_max = q_units((float)o.beta_max_mev);
+    if ((e = dalloc(&h->beta_tab, kBetaTable + 1)) ||
+        (e = cudaMemcpyAsync(h->beta_tab, beta.data(), (kBetaTable + 1) * sizeof(float), cudaMemcpyHostToDevice, s)))
+      return bail(cuda_fail(e, "beta table"));
+  }
   if (o.history_sigma) {
     if ((e = dalloc(&h->s2h_lo, V)) || (e = dalloc(&h->s2h_hi, V)) ||
         (e = cudaMemsetAsync(h->s2h_lo, 0, V * sizeof(ull), s)) || (e = cudaMemsetAsync(h->s2h_hi, 0, V * sizeof(ull), s)))
@@ -661,8 +721,9 @@ extern "C" nm_status nm_dose_run_batch(nm_dose* const* hs, int32_t n, const uint
     if (!hs[i]) return fail(NM_ERR_ARG, "handle %d is NULL", i);
     for (int j = 0; j < i; ++j)
       if (hs[j] == hs[i]) return fail(NM_ERR_ARG, "handle %d appears twice", i);
-    if (hs[i]->opt.history_sigma)
-      return fail(NM_ERR_ARG, "handle %d: history_sigma handles run with nm_dose_run, not in batches", i);
+    if (hs[i]->opt.history_sigma || hs[i]->beta_tab)
+      return fail(NM_ERR_ARG, "handle %d: history_sigma and beta+ spectrum handles run with nm_dose_run, not in batches",
+                  i);
     if (!same_physics(hs[0], hs[i]))
       return fail(NM_ERR_ARG, "handle %d: all patients of a batch need the same materials, energies, batches and device", i);
     const uint64_t per = hs[i]->units_per_history();
@@ -1137,7 +1198,8 @@ nm_status nm_dose_counters(nm_dose* h, nm_counters* c) {
   memset(c, 0, sizeof *c);
   c->histories = h->hist_next;
   c->batches = h->n_batches;
-  c->emitted = (int64_t)(h->hist_next * h->units_per_history());
+  c->emitted = h->beta_tab ? (int64_t)(h->hist_next * 2ull * (uint64_t)h->q_e0 + v[kCtrPositronUnits])
+                           : (int64_t)(h->hist_next * h->units_per_history());
   c->deposited = (int64_t)v[kCtrDepositedUnits];
   c->escaped = (int64_t)v[kCtrEscapedUnits];
   c->killed = (int64_t)v[kCtrKilledUnits];
@@ -1219,6 +1281,24 @@ nm_status nm_check_kahn(double e_mev, int64_t n, uint64_t seed, float* cos_out) 
   cudaFree(d); cudaFree(st);
   if (e) return cuda_fail(e, "nm_check_kahn");
   if (flags) return fail(NM_ERR_DEVICE, "Kahn trial limit hit");
+  return NM_OK;
+}
+
+nm_status nm_check_beta(double t_max_mev, int32_t z, int64_t n, uint64_t seed, float* t_out) {
+  if (n < 0 || (n > 0 && !t_out) || !(t_max_mev > 0.0 && t_max_mev < 20.0) || z < 0 || z > 100)
+    return fail(NM_ERR_ARG, "bad arguments");
+  if (n == 0) return NM_OK;
+  const std::vector<float> tab = beta_inverse_cdf(t_max_mev, z);
+  float* d = nullptr;
+  float* dt = nullptr;
+  cudaError_t e = dalloc(&d, n);
+  if (!e) e = dalloc(&dt, kBetaTable + 1);
+  if (!e) e = cudaMemcpy(dt, tab.data(), (kBetaTable + 1) * sizeof(float), cudaMemcpyHostToDevice);
+  if (!e) e = launch_check_beta(dt, n, (uint32_t)seed, (uint32_t)(seed >> 32), d, 0);
+  if (!e) e = cudaMemcpy(t_out, d, n * sizeof(float), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  cudaFree(dt);
+  if (e) return cuda_fail(e, "nm_check_beta");
   return NM_OK;
 }
 

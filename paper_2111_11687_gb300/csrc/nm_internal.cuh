@@ -53,7 +53,8 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 __device__ __forceinline__ float u01(uint32_t r) { return ((float)(r >> 9) + 0.5f) * 0x1p-23f; }
 
 // Random-stream ids inside one history.
-enum : uint32_t { kStreamSource = 0, kStreamPhotonA = 1, kStreamPhotonB = 2 };
+enum : uint32_t { kStreamSource = 0, kStreamPhotonA = 1, kStreamPhotonB = 2, kStreamPositron = 3 };
+constexpr int kBetaTable = 1024;   // inverse-CDF nodes of the beta+ spectrum (+1)
 
 struct MaterialCoef {
   float za;       // (Z/A) * N_A * sigma-table scale: mu_c/rho = za * kn(E)
@@ -77,7 +78,11 @@ struct PatientGeom {
   float inv_dx, inv_dy, inv_dz;
   int source_mode;
   float px, py, pz;           // point source, voxel units
-  int32_t q_positron;         // q_units(positron energy), 0 in point mode
+  int32_t q_positron;         // q_units(positron energy), 0 in point mode and with beta_tab
+  // Beta+ spectrum (decay mode, optional): positron kinetic energy (MeV) at
+  // cumulative probability i / kBetaTable, i = 0..kBetaTable; NULL = the
+  // constant local deposit q_positron.
+  const float* beta_tab;
   // Two-region Woodcock tracking: the box [blo, bhi) (voxel units) holds every
   // voxel denser than kRegionDensity plus a one-voxel margin; outside it the
   // majorant is TransportParams::minv_out.
@@ -115,21 +120,24 @@ constexpr int kMaxBatchPatients = 64;
 
 enum CounterSlot {
   kCtrSteps = 0, kCtrCompton, kCtrPhoto, kCtrRayleigh, kCtrCutoff, kCtrEscapes,
-  kCtrEscapedUnits, kCtrKilledUnits, kCtrDepositedUnits, kCtrHistSplits, kCtrCount
+  kCtrEscapedUnits, kCtrKilledUnits, kCtrDepositedUnits, kCtrHistSplits, kCtrPositronUnits, kCtrCount
 };
 
 // Sets the message that nm_last_error() returns on the calling thread.
 void set_error_message(const char* msg);
 
 // ---- launchers (host side), one translation unit each ---------------------
-// history: history-by-history statistics (needs !warp_agg and !multi).
+// history: history-by-history statistics (needs !warp_agg and !multi); a
+// single-patient launch whose p.g.beta_tab is set runs the beta+ variant
+// (needs !warp_agg).
 cudaError_t launch_transport(const TransportParams& p, int grid, int block, bool warp_agg,
                              bool rayleigh, bool regroup, cudaStream_t s, bool multi = false,
                              bool history = false);
 int transport_max_blocks_per_sm(int block, bool warp_agg, bool rayleigh, bool regroup,
-                                bool multi = false, bool history = false);
+                                bool multi = false, bool history = false, bool beta = false);
 cudaError_t launch_check_philox(const uint4* ctr, const uint2* key, int64_t n, uint4* out,
                                 cudaStream_t s);
+cudaError_t launch_check_beta(const float* tab, int64_t n, uint32_t k0, uint32_t k1, float* out, cudaStream_t s);
 cudaError_t launch_check_kahn(float e, int64_t n, uint32_t k0, uint32_t k1, float* out,
                               uint32_t* status, cudaStream_t s);
 cudaError_t launch_check_source(const TransportParams& p, uint64_t first, int64_t n, int32_t* voxel,

@@ -111,6 +111,7 @@ extern "C" nm_status nm_dose_tally_noalloc(const nm_grid* g, const nm_materials*
   if (!(o.photon_mev > mt->photon_cut_mev) || !(mt->photon_cut_mev > 0) || o.photon_mev > 1.0)
     return fail(NM_ERR_ARG, "need 0 < photon cutoff < photon energy <= 1 MeV");
   if (o.max_steps <= 0) return fail(NM_ERR_ARG, "max_steps must be > 0");
+  if (o.beta_max_mev != 0.0) return fail(NM_ERR_ARG, "the beta+ spectrum needs a handle (nm_dose_create)");
   if (!decay) {
     const float L[3] = {g->nx * g->dx, g->ny * g->dy, g->nz * g->dz};
     for (int a = 0; a < 3; ++a)

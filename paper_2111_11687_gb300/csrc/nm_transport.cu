@@ -230,6 +230,103 @@ __device__ __forceinline__ Site sample_site(const PatientGeom& G, uint32_t k0, u
   return s;
 }
 
+// Katz-Penfold range of a positron of kinetic energy t (MeV), g/cm^2:
+// R = 0.412 t^(1.265 - 0.0954 ln t); and its inverse, the lower root of
+// 0.0954 L^2 - 1.265 L + ln(R / 0.412) = 0 in L = ln t.
+__device__ __forceinline__ float kp_range(float t) {
+  const float l = logf(t);
+  return 0.412f * expf((1.265f - 0.0954f * l) * l);
+}
+__device__ __forceinline__ float kp_energy(float r) {
+  if (!(r > 0.0f)) return 0.0f;
+  const float c = logf(r * (1.0f / 0.412f));
+  const float disc = fmaxf(fmaf(-4.0f * 0.0954f, c, 1.265f * 1.265f), 0.0f);
+  return expf((1.265f - sqrtf(disc)) * (1.0f / (2.0f * 0.0954f)));
+}
+
+// Positron kinetic energy (MeV) for the uniform word r: linear interpolation
+// in the inverse-CDF table of the beta+ spectrum.
+__device__ __forceinline__ float beta_energy(const float* __restrict__ tab, uint32_t r) {
+  const float sv = u01(r) * (float)kBetaTable;
+  const int i = min((int)sv, kBetaTable - 1);
+  const float ta = __ldg(tab + i), tb = __ldg(tab + i + 1);
+  return fmaf(sv - (float)i, tb - ta, ta);
+}
+
+// The positron of a decay, beta+ spectrum mode: kinetic energy from the
+// inverse-CDF table (linear between nodes), an isotropic straight track from
+// the decay site (x, y, z, voxel units; in voxel v0) walked voxel by voxel,
+// each voxel using up rho x (path in it) of the mass range and keeping the
+// energy lost there, q(T before) - q(T at the range left), until the range
+// is spent.  On return (x, y, z) is the end of the track, where the pair
+// annihilates, and q0 the positron's energy in tally units.  Returns false if
+// the track left the grid; q_left is then the energy it carried out.
+template <class Dep>
+__device__ __forceinline__ bool positron_track(const PatientGeom& G, uint32_t k0, uint32_t k1, uint32_t hlo,
+                                               uint32_t hhi, int v0, float& x, float& y, float& z,
+                                               uint32_t& q0, uint32_t& q_left, Dep&& dep) {
+  uint32_t ctr = 0;
+  const uint4 r = draw(ctr, kStreamPositron, hlo, hhi, k0, k1);
+  const float t0 = beta_energy(G.beta_tab, r.x);
+  q0 = (uint32_t)q_units(t0);
+  const float cz = fmaf(2.0f, u01(r.y), -1.0f);
+  const float sn = sqrtf(fmaxf(0.0f, fmaf(-cz, cz, 1.0f)));
+  float sp, cp;
+  __sincosf(fmaf(kTwoPi, u01(r.z), -3.14159265f), &sp, &cp);
+  const float ux = sn * cp, uy = sn * sp, uz = cz;
+  const int nxy = G.nx * G.ny;
+  int iz = v0 / nxy;
+  int iy = (v0 - iz * nxy) / G.nx;
+  int ix = v0 - iz * nxy - iy * G.nx;
+  // per axis: track length (cm) to the next voxel plane and between planes
+  const float dx = 1.0f / G.inv_dx, dy = 1.0f / G.inv_dy, dz = 1.0f / G.inv_dz;
+  const int sx = ux > 0.0f ? 1 : -1, sy = uy > 0.0f ? 1 : -1, sz = uz > 0.0f ? 1 : -1;
+  float tnx = ux != 0.0f ? ((float)(ix + (ux > 0.0f)) - x) * dx / ux : kInf;
+  float tny = uy != 0.0f ? ((float)(iy + (uy > 0.0f)) - y) * dy / uy : kInf;
+  float tnz = uz != 0.0f ? ((float)(iz + (uz > 0.0f)) - z) * dz / uz : kInf;
+  const float dtx = ux != 0.0f ? dx / fabsf(ux) : kInf;
+  const float dty = uy != 0.0f ? dy / fabsf(uy) : kInf;
+  const float dtz = uz != 0.0f ? dz / fabsf(uz) : kInf;
+  float r_left = kp_range(t0), tcur = 0.0f;
+  uint32_t q_cur = q0;
+  int v = v0;
+  // a straight line crosses at most nx + ny + nz voxels
+  const int limit = G.nx + G.ny + G.nz + 2;
+  for (int it = 0;; ++it) {
+    const bool bx = tnx <= tny && tnx <= tnz;
+    const bool by = !bx && tny <= tnz;
+    const float tn = bx ? tnx : by ? tny : tnz;
+    const float rho = __uint_as_float(__ldg(G.vox + v) & ~7u);
+    const float seg = fmaxf(tn - tcur, 0.0f);
+    if (rho * seg >= r_left || it + 1 >= limit) {
+      // the range ends in this voxel: it keeps the rest of the energy
+      if (q_cur) dep(v, q_cur);
+      const float send = tcur + fminf(r_left / rho, seg);
+      x = fminf(fmaxf(fmaf(send * G.inv_dx, ux, x), (float)ix), __int_as_float(__float_as_int((float)(ix + 1)) - 1));
+      y = fminf(fmaxf(fmaf(send * G.inv_dy, uy, y), (float)iy), __int_as_float(__float_as_int((float)(iy + 1)) - 1));
+      z = fminf(fmaxf(fmaf(send * G.inv_dz, uz, z), (float)iz), __int_as_float(__float_as_int((float)(iz + 1)) - 1));
+      return true;
+    }
+    r_left -= rho * seg;
+    const uint32_t q_new = min((uint32_t)q_units(kp_energy(r_left)), q_cur);
+    if (q_cur > q_new) dep(v, q_cur - q_new);
+    q_cur = q_new;
+    tcur = tn;
+    bool left;
+    if (bx) {
+      ix += sx; v += sx; tnx += dtx; left = (unsigned)ix >= (unsigned)G.nx;
+    } else if (by) {
+      iy += sy; v += sy * G.nx; tny += dty; left = (unsigned)iy >= (unsigned)G.ny;
+    } else {
+      iz += sz; v += sz * nxy; tnz += dtz; left = (unsigned)iz >= (unsigned)G.nz;
+    }
+    if (left) {
+      q_left = q_cur;
+      return false;
+    }
+  }
+}
+
 // Adds dq units to *cell.  With WARP_AGG the lanes that hit the same cell
 // (same address, so lanes of different patients never merge) add their
 // deposits with one warp reduction and one atomic.
@@ -318,9 +415,10 @@ __device__ __forceinline__ void hist_add(const HistList& L, int& n, uint32_t v, 
   ++n;
 }
 
-template <bool WARP_AGG, bool RAYLEIGH, bool REGROUP, bool MULTI, bool HIST>
+template <bool WARP_AGG, bool RAYLEIGH, bool REGROUP, bool MULTI, bool HIST, bool BETA>
 __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams p) {
   static_assert(!HIST || (!WARP_AGG && !MULTI), "history statistics: one patient, lane-wise deposits");
+  static_assert(!BETA || (!WARP_AGG && !MULTI), "beta+ spectrum: one patient, lane-wise deposits");
   __shared__ float s_kn[kKnTable];
   __shared__ float s_minv[kKnTable];
   __shared__ float s_minv_out[kKnTable];
@@ -330,7 +428,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
   // Per patient, indexed by CounterSlot: the rare events (photo, cutoff,
   // rayleigh, killed units) counted here directly, and (multi) the lanes'
   // register counters handed over when a lane changes patient.
-  __shared__ unsigned long long s_cnt[MULTI ? kMaxBatchPatients : 1][8];
+  __shared__ unsigned long long s_cnt[MULTI ? kMaxBatchPatients : 1][9];   // [8]: positron units
   __shared__ PatientGeom s_geom[MULTI ? kMaxBatchPatients : 1];
   extern __shared__ float s_site[];         // [7][blockDim]: decay site, photon A direction, photon B's
                                             // distance to its region boundary
@@ -341,7 +439,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
     s_minv_out[i] = p.minv_out[i];
   }
   if (threadIdx.x < NM_MAX_MATERIALS) s_mat[threadIdx.x] = p.mat[threadIdx.x];
-  for (int i = threadIdx.x; i < n_pat * 8; i += blockDim.x) s_cnt[i / 8][i % 8] = 0;
+  for (int i = threadIdx.x; i < n_pat * 9; i += blockDim.x) s_cnt[i / 9][i % 9] = 0;
   if (MULTI)
     for (int i = threadIdx.x; i < n_pat; i += blockDim.x) s_geom[i] = p.patients[i];
   __syncthreads();
@@ -457,7 +555,22 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
           const uint64_t h = G.hist_begin + idx;
           hlo = (uint32_t)h;
           hhi = (uint32_t)(h >> 32);
-          const Site st = sample_site(G, p.key0, p.key1, hlo, hhi);
+          Site st = sample_site(G, p.key0, p.key1, hlo, hhi);
+          bool pair = true;                  // the annihilation photons start inside the grid
+          if (BETA && G.beta_tab) {
+            uint32_t q0 = 0, q_left = 0;
+            pair = positron_track(G, p.key0, p.key1, hlo, hhi, st.v, st.x, st.y, st.z, q0, q_left,
+                                  [&](int v, uint32_t dq) {
+                                    if (HIST)
+                                      hist_add(hl, hn, (uint32_t)v, dq, p.g.tally, p.s2h_lo, p.s2h_hi,
+                                               p.g.counters + kCtrHistSplits);
+                                    else
+                                      atomicAdd(G.tally + v, (ull)dq);
+                                  });
+            atomicAdd(&s_cnt[MULTI ? pi : 0][8], (ull)q0);
+            if (!pair) escaped += (ull)q_left + 2ull * (ull)(uint32_t)p.q_e0;
+          }
+          if (pair) {
           px = st.x; py = st.y; pz = st.z;
           ux = st.u; uy = st.v_; uz = st.w;
           e = p.e0; qe = p.q_e0; f = s_f0;
@@ -480,6 +593,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
               has = G.q_positron > 0;
               cell = G.tally + st.v;
             }
+          }
           }
         }
       }
@@ -617,10 +731,20 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
   const unsigned fl = __reduce_or_sync(kFull, flags);
   if (lane == 0 && fl) atomicOr(p.status, fl);
   __syncthreads();
-  for (int i = threadIdx.x; i < n_pat * 8; i += blockDim.x) {
-    const int q = i / 8, k = i % 8;   // k is the CounterSlot
-    if (s_cnt[q][k]) atomicAdd((MULTI ? s_geom[q].counters : p.g.counters) + k, s_cnt[q][k]);
+  for (int i = threadIdx.x; i < n_pat * 9; i += blockDim.x) {
+    const int q = i / 9, k = i % 9;   // k is the CounterSlot, 8 the positron units
+    if (s_cnt[q][k])
+      atomicAdd((MULTI ? s_geom[q].counters : p.g.counters) + (k < 8 ? k : (int)kCtrPositronUnits), s_cnt[q][k]);
   }
+}
+
+// Positron energies of histories 0..n-1 as the transport draws them.
+__global__ void check_beta_kernel(const float* tab, int64_t n, uint32_t k0, uint32_t k1, float* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t ctr = 0;
+  const uint4 r = draw(ctr, kStreamPositron, (uint32_t)i, (uint32_t)(i >> 32), k0, k1);
+  out[i] = beta_energy(tab, r.x);
 }
 
 __global__ void check_philox_kernel(const uint4* ctr, const uint2* key, int64_t n, uint4* out) {
@@ -659,9 +783,9 @@ size_t transport_smem(int block, bool history) {
   return ((size_t)7 + (history ? 2 * kHistVoxels : 0)) * block * sizeof(float);
 }
 
-template <bool A, bool R, bool G, bool M, bool H>
+template <bool A, bool R, bool G, bool M, bool H, bool B = false>
 void* kernel_ptr() {
-  return (void*)transport_kernel<A, R, G, M, H>;
+  return (void*)transport_kernel<A, R, G, M, H, B>;
 }
 
 template <bool M>
@@ -674,8 +798,19 @@ void* pick_m(bool a, bool r, bool g) {
   return g ? kernel_ptr<false, false, true, M, false>() : kernel_ptr<false, false, false, M, false>();
 }
 
-// History statistics exist only without warp aggregation and for one patient.
-void* pick(bool a, bool r, bool g, bool m, bool h) {
+template <bool H>
+void* pick_beta(bool r, bool g) {
+  if (r) return g ? kernel_ptr<false, true, true, false, H, true>() : kernel_ptr<false, true, false, false, H, true>();
+  return g ? kernel_ptr<false, false, true, false, H, true>() : kernel_ptr<false, false, false, false, H, true>();
+}
+
+// History statistics and the beta+ spectrum exist only without warp
+// aggregation and for one patient.
+void* pick(bool a, bool r, bool g, bool m, bool h, bool beta) {
+  if (beta) {
+    if (a || m) return nullptr;
+    return h ? pick_beta<true>(r, g) : pick_beta<false>(r, g);
+  }
   if (h) {
     if (a || m) return nullptr;
     if (r) return g ? kernel_ptr<false, true, true, false, true>() : kernel_ptr<false, true, false, false, true>();
@@ -688,7 +823,7 @@ void* pick(bool a, bool r, bool g, bool m, bool h) {
 
 cudaError_t launch_transport(const TransportParams& p, int grid, int block, bool warp_agg,
                              bool rayleigh, bool regroup, cudaStream_t s, bool multi, bool history) {
-  void* fn = pick(warp_agg, rayleigh, regroup, multi, history);
+  void* fn = pick(warp_agg, rayleigh, regroup, multi, history, !multi && p.g.beta_tab != nullptr);
   if (!fn) return cudaErrorInvalidValue;
   void* args[] = {(void*)&p};
   // the history lists take the static + dynamic total past the 48 KB default
@@ -699,9 +834,10 @@ cudaError_t launch_transport(const TransportParams& p, int grid, int block, bool
   return e;
 }
 
-int transport_max_blocks_per_sm(int block, bool warp_agg, bool rayleigh, bool regroup, bool multi, bool history) {
+int transport_max_blocks_per_sm(int block, bool warp_agg, bool rayleigh, bool regroup, bool multi, bool history,
+                                bool beta) {
   int n = 0;
-  void* fn = pick(warp_agg, rayleigh, regroup, multi, history);
+  void* fn = pick(warp_agg, rayleigh, regroup, multi, history, beta);
   if (!fn ||
       cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)transport_smem(block, history)) !=
           cudaSuccess ||
@@ -710,6 +846,12 @@ int transport_max_blocks_per_sm(int block, bool warp_agg, bool rayleigh, bool re
     return 0;
   }
   return n;
+}
+
+cudaError_t launch_check_beta(const float* tab, int64_t n, uint32_t k0, uint32_t k1, float* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  check_beta_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(tab, n, k0, k1, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_check_philox(const uint4* ctr, const uint2* key, int64_t n, uint4* out,

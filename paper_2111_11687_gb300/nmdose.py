@@ -50,7 +50,8 @@ class nm_options(C.Structure):
                 ("n_labels", C.c_int32), ("block_threads", C.c_int32), ("chunk", C.c_int32),
                 ("warp_aggregate", C.c_int32), ("regroup", C.c_int32), ("regroup_lanes", C.c_int32),
                 ("max_steps", C.c_int32),
-                ("stream", C.c_void_p), ("history_sigma", C.c_int32)]
+                ("stream", C.c_void_p), ("history_sigma", C.c_int32), ("beta_max_mev", C.c_double),
+                ("beta_z", C.c_int32)]
 
 
 class nm_counters(C.Structure):
@@ -100,6 +101,7 @@ _SIGS = {
     "nm_dose_destroy": (None, [C.c_void_p]),
     "nm_check_philox": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "nm_check_kahn": (C.c_int, [C.c_double, C.c_int64, C.c_uint64, C.c_void_p]),
+    "nm_check_beta": (C.c_int, [C.c_double, C.c_int32, C.c_int64, C.c_uint64, C.c_void_p]),
     "nm_dose_alias_table": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.c_void_p, C.c_void_p, C.c_void_p]),
     "nm_check_source": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int64, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "nm_conv3d_kpad": (C.c_int32, [C.c_int32]),
@@ -286,6 +288,12 @@ def nm_check_philox(ctr: np.ndarray, key: np.ndarray) -> np.ndarray:
 def nm_check_kahn(e_mev: float, n: int, seed: int) -> np.ndarray:
     out = np.empty(n, np.float32)
     _check(load().nm_check_kahn(float(e_mev), n, seed, ptr(out)))
+    return out
+
+
+def nm_check_beta(t_max_mev: float, z: int, n: int, seed: int) -> np.ndarray:
+    out = np.empty(n, np.float32)
+    _check(load().nm_check_beta(float(t_max_mev), int(z), n, seed, ptr(out)))
     return out
 
 

@@ -12,6 +12,8 @@ import numpy as np
 import pytest
 from scipy import integrate, stats
 
+from tests.positron_expect import cube_positron_expectation
+
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 ME = 0.51099895            # m_e c^2, MeV (CODATA 2018)
 RE = 2.8179403262e-13      # classical electron radius, cm
@@ -500,45 +502,6 @@ def test_positron_range_against_estar(orc):
     assert orc.range_kp(0.0) == 0.0 and orc.energy_at_range(0.0) == 0.0
 
 
-def _cube_positron_expectation(rho, n_side, vox, t, rng):
-    """Per decay, brute force: straight tracks from a uniform point of the
-    central voxel in isotropic directions; the energy left when a track
-    reaches the cube's surface escapes, the energy lost before it leaves the
-    central voxel stays there."""
-    L = n_side * vox
-    c0 = (n_side // 2) * vox
-    n = t.size
-    x = c0 + vox * rng.random((n, 3))
-    u = rng.normal(size=(n, 3))
-    u /= np.linalg.norm(u, axis=1, keepdims=True)
-
-    def exit_dist(lo, hi):
-        with np.errstate(divide="ignore"):
-            d = np.where(u > 0, (hi - x) / u, np.where(u < 0, (lo - x) / u, np.inf))
-        return d.min(axis=1)
-
-    def kp(tt):
-        lt = np.log(tt)
-        return 0.412 * np.exp((1.265 - 0.0954 * lt) * lt)
-
-    def kp_inv(r):
-        c = np.log(r / 0.412)
-        return np.exp((1.265 - np.sqrt(1.265 ** 2 - 4 * 0.0954 * c)) / (2 * 0.0954))
-
-    r = kp(t)
-
-    def residual(d):
-        left = r - rho * d
-        out = np.zeros_like(t)
-        m = left > 0
-        out[m] = kp_inv(left[m])
-        return out
-
-    esc = residual(exit_dist(0.0, L))
-    centre = t - residual(exit_dist(c0, c0 + vox))
-    return esc, centre
-
-
 @pytest.mark.parametrize("rho", [1.0, 0.5])
 def test_positron_track_escape_and_local_deposit(orc, rho):
     # Photons that never interact (mu = 0) leave the 5^3 cube; what stays is
@@ -561,7 +524,7 @@ def test_positron_track_escape_and_local_deposit(orc, rho):
     centre = r.tally[2, 2, 2] / q / N
     rng = np.random.default_rng(17)
     t = orc.sample_beta(F18_T_MAX, 8, 1_000_000, 23)
-    e_esc, e_centre = _cube_positron_expectation(rho, n_side, vox, t, rng)
+    e_esc, e_centre = cube_positron_expectation(rho, n_side, vox, t, rng)
     for got, ref in ((esc_pos, e_esc), (centre, e_centre)):
         sd = ref.std() * math.sqrt(1.0 / N + 1.0 / ref.size)
         assert abs(got - ref.mean()) < 4.0 * sd + 1e-6, (got, ref.mean(), sd)
