@@ -1,26 +1,28 @@
 // Weight gradient of a 3x3x3 convolution by shifted windows:
 //   dW[co][tap][ci] = sum over voxels v of dY[v][co] * X[v + off_tap][ci].
 //
-// Per tap this is a GEMM over voxels (K) with M = output channels and N = one
-// 16-channel chunk of input channels.  Both operands come from halo tiles in
-// shared memory in the 32-byte-swizzled MN-major layout (a voxel row of 16
-// channels, 32 bytes), loaded by TMA: dY over the tile's z-planes, X with its
-// one-voxel halo.  The K rows run over the padded tile's centre indices as in
-// the forward kernel; dY is zeroed at the halo positions (they belong to other
-// tiles), so those rows add nothing, and tap (dz, dy, dx) reads X from the
-// same rows shifted by (dz*PY + dy)*PX + dx: a different start address.  The
-// MMA shape is M = 64 (the 16 or 32 real output channels; the rest of D is
-// never read), N = 16, 32 or 48 input channels, K = 16; a pass's taps keep
-// their accumulators in TMEM across all of a CTA's tiles.
+// A GEMM over voxels (K) with M = output channels and N = 16-channel chunks
+// of input channels.  Both operands come from halo tiles in shared memory in
+// the 32-byte-swizzled MN-major layout (a voxel row of 16 channels, 32 bytes),
+// loaded by TMA: dY over the tile's z-planes, X with its one-voxel halo.  dY
+// is zeroed at the halo positions (they belong to other tiles), so K may run
+// over padded rows.  Substituting v' = v + off moves the tap's shift from X to
+// dY: sum over v' of dY[v' - off][co] X[v'][ci].  The three taps dx = +1, 0,
+// -1 of one (dy, dz) pair then read dY at three consecutive rows, which one
+// MMA covers: its M = 64 operand is four 16-row atoms (16 output channels
+// each) at a leading-byte offset of one row (32 bytes), so atom q reads dY
+// shifted by q rows (taps dx = 1 - q; the fourth atom's rows of D are never
+// read).  Per tile 9 (dy, dz) groups x 39 K-steps of 16 voxel rows; X moves
+// by the group's (dz PY + dy) PX rows.  N = 16, 32 or 48 input channels per
+// MMA; the groups' accumulators stay in TMEM across all of a CTA's tiles.
 //
 // Persistent, warp-specialised (one CTA per SM), passes over groups of input
-// chunks and of taps:
+// chunks (and of (dy, dz) groups where TMEM needs it):
 //   warp 0    TMA producer (dY atoms + the pass's X chunks per tile) into a stage ring;
-//   warp 1    MMA issuer: per tile the pass's taps x 40 K-steps, commits to "empty";
+//   warp 1    MMA issuer: per tile the pass's groups x 39 K-steps, commits to "empty";
 //   warps 2-5 zero dY's halo rows of each landed stage (then "ready"), and at
-//             the end of a pass warps 4 and 5 (the TMEM lane quarters that
-//             hold D's rows 0-15 and 16-31) write the CTA's partial dW for
-//             that chunk.
+//             the end of a pass the warps whose TMEM lane quarters hold the
+//             taps dx = +1, 0, -1 (warps 4, 5, 2) write the CTA's partial dW.
 // Partials are summed over CTAs in a fixed order by the caller (deterministic);
 // the bias gradient is a separate fixed-order reduction.  Every wait is
 // bounded; a time-out sets NM_DEV_TIMEOUT and drains what is in flight.
@@ -45,12 +47,17 @@ constexpr int kRows = PX * PY * PZ;                          // X box rows
 constexpr int kCmin = (1 * PY + 1) * PX + 1;                 // first centre
 constexpr int kCmax = (TZ * PY + TY) * PX + TX;              // last centre
 constexpr int kKRows = ((kCmax - kCmin + 1 + 127) / 128) * 128;  // K rows per tile (640)
-constexpr int kKSteps = kKRows / 16;
 constexpr int kDelta = PY * PX + PX + 1;                     // largest tap shift
 constexpr int kXRows = (kCmin + kKRows + kDelta + 15) / 16 * 16;  // rows any MMA may read from X
 constexpr int kYOff = PY * PX;                               // dY box starts one z-plane in
 constexpr int kYBox = PX * PY * TZ;                          // dY box rows
 constexpr int kYRows = (kCmin - kYOff + kKRows + 15) / 16 * 16;   // rows read from dY (>= kYBox)
+// the three x-taps of a group: X rows from kCmin - 1 + group shift, 612 of them
+constexpr int kKSteps3 = (kCmax - kCmin + 1 + 2 + 15) / 16;  // 39
+constexpr int kARow0 = kCmin - 1 - 1 - kYOff;               // dY row of atom 0 (dx = +1) at K row 0
+static_assert(kARow0 >= 0 && kARow0 + kKSteps3 * 16 + 3 <= kYBox, "dY rows of the shifted atoms");
+static_assert(kCmin - 1 - (PY + 1) * PX >= 0 && kCmin - 1 + (PY + 1) * PX + kKSteps3 * 16 <= kXRows,
+              "X rows of the groups");
 constexpr uint32_t kXBytes = kXRows * 32;
 constexpr uint32_t kYBytes = kYRows * 32;
 constexpr int kThreads = 192;
@@ -62,16 +69,14 @@ static_assert(kXRows >= kRows && kYRows >= kYBox, "tile rows");
 // G = input-channel atoms (16 channels each) per MMA: N = 16 G.  With more
 // atoms one MMA covers more of the input channels, so fewer instructions are
 // issued (their rate, not the tensor math, bounds these small GEMMs); the
-// taps of a pass are limited by TMEM (T taps x 16 G columns <= 512).
+// (dy, dz) groups of a pass are limited by TMEM (groups x output halves x
+// 16 G columns <= 512).
 template <int COUT, int G>
 struct WLayout {
   static constexpr int kYAtoms = COUT / 16;
-  static constexpr int kTaps = 512 / (16 * G) < 27 ? 512 / (16 * G) : 27;
-  // the M = 64 operand reads four 16-channel atoms at the LBO stride: with 32
-  // outputs the two spare atoms must fall inside the stage, so it spans at
-  // least 4 x kYBytes
+  static constexpr int kGroups = 512 / (16 * G * kYAtoms) < 9 ? 512 / (16 * G * kYAtoms) : 9;
   static constexpr uint32_t kUsed = kYAtoms * kYBytes + G * kXBytes;
-  static constexpr uint32_t kSpan = COUT == 16 ? kUsed : (4 * kYBytes > kUsed ? 4 * kYBytes : kUsed);
+  static constexpr uint32_t kSpan = kUsed;
   static constexpr uint32_t kStage = (kSpan + 1023) / 1024 * 1024;
   static constexpr int kStages = 3 * kStage <= 220 * 1024 ? 3 : 2 * kStage <= 220 * 1024 ? 2 : 1;
   static constexpr size_t kSmem = (size_t)kStages * kStage;
@@ -101,15 +106,15 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_tile_kernel(const __grid_co
                                                                  const WGrid g, float* __restrict__ part,
                                                                  uint32_t* status) {
   typedef WLayout<COUT, G> L;
-  constexpr int S = L::kStages, T = L::kTaps;
+  constexpr int S = L::kStages, GP = L::kGroups;
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t full[S], ready[S], empty[S], acc_full, acc_empty;
   __shared__ uint32_t s_tmem;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nchunks = (g.cin + 15) / 16;
   const long long my_tiles = g.tiles > blockIdx.x ? (g.tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  // passes: groups of G input chunks x groups of T taps
-  const int n_tg = (27 + T - 1) / T;
+  // passes: groups of G input chunks x runs of GP (dy, dz) groups
+  const int n_tg = (9 + GP - 1) / GP;
   const int passes = (nchunks + G - 1) / G * n_tg;
 
   if (warp == 0) tc::tmem_alloc(&s_tmem, 512);
@@ -134,7 +139,7 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_tile_kernel(const __grid_co
       tc::mbar_init(&empty[i], 1);
     }
     tc::mbar_init(&acc_full, 1);
-    tc::mbar_init(&acc_empty, 64);
+    tc::mbar_init(&acc_empty, 96);
     tc::mbar_fence_init();
   }
   tc::fence_async_smem();
@@ -177,7 +182,7 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_tile_kernel(const __grid_co
       long long it = 0;
       for (int ps = 0; ps < passes && !timeout; ++ps) {
         const int c0 = ps / n_tg * G, na = min(G, nchunks - c0);
-        const int t0 = ps % n_tg * T, t1 = min(27, t0 + T);
+        const int g0 = ps % n_tg * GP, g1 = min(9, g0 + GP);
         const uint32_t idesc = tc::idesc_bf16_f32(64, 16 * na, true, true);
         // the previous pass's accumulators have been read out
         if (ps > 0 && !tc::mbar_wait_bounded(&acc_empty, (uint32_t)((ps - 1) & 1), kWaitCycles)) {
@@ -194,15 +199,18 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_tile_kernel(const __grid_co
           tc::fence_after_sync();
           const uint32_t sy = base + s * L::kStage;
           const uint32_t sx = sy + L::kYAtoms * kYBytes;
-          const uint64_t a_base = desc_mn_sw32(sy + (kCmin - kYOff) * 32, COUT == 16 ? 0 : kYBytes, 256);
-          const uint64_t b_base = desc_mn_sw32(sx + kCmin * 32, kXBytes, 256);
           const uint32_t first = k == 0 ? 0u : 1u;
-          for (int ks = 0; ks < kKSteps; ++ks) {
-            const uint64_t adesc = a_base + (uint64_t)(ks * 16 * 32 >> 4);
-            for (int tap = t0; tap < t1; ++tap) {
-              const int delta = ((tap / 9 - 1) * PY + ((tap / 3) % 3 - 1)) * PX + (tap % 3 - 1);
-              const uint64_t bdesc = b_base + (uint64_t)((ks * 16 + delta) * 32 >> 4);
-              tc::mma_bf16(tmem + (tap - t0) * 16 * G, adesc, bdesc, idesc, ks == 0 ? first : 1u);
+          for (int ks = 0; ks < kKSteps3; ++ks) {
+            for (int g = g0; g < g1; ++g) {
+              // group g = (dz + 1) 3 + (dy + 1); X rows from kCmin - 1 + shift
+              const int shift = ((g / 3 - 1) * PY + (g % 3 - 1)) * PX;
+              const uint64_t bdesc = desc_mn_sw32(sx + (kCmin - 1 + shift + ks * 16) * 32, kXBytes, 256);
+#pragma unroll
+              for (int h = 0; h < L::kYAtoms; ++h) {
+                const uint64_t adesc = desc_mn_sw32(sy + h * kYBytes + (kARow0 + ks * 16) * 32, 32, 256);
+                tc::mma_bf16(tmem + ((g - g0) * L::kYAtoms + h) * 16 * G, adesc, bdesc, idesc,
+                             ks == 0 ? first : 1u);
+              }
             }
           }
           tc::mma_commit(&empty[s]);
@@ -219,7 +227,7 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_tile_kernel(const __grid_co
     long long it = 0;
     for (int ps = 0; ps < passes && !timeout; ++ps) {
       const int c0 = ps / n_tg * G, na = min(G, nchunks - c0);
-      const int t0 = ps % n_tg * T, t1 = min(27, t0 + T);
+      const int g0 = ps % n_tg * GP, g1 = min(9, g0 + GP);
       for (long long k = 0; k < my_tiles; ++k, ++it) {
         const int s = (int)(it % S);
         const bool got = tc::mbar_wait_bounded(&full[s], (uint32_t)((it / S) & 1), kWaitCycles);
@@ -244,9 +252,11 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_tile_kernel(const __grid_co
       }
       if (timeout) break;
       // end of the pass: with M = 64, D row i sits in TMEM lane (i % 16) +
-      // 32 (i / 16), so output channels 0-15 are lanes 0-15 (warp 4's quarter)
-      // and 16-31 lanes 32-47 (warp 5's quarter)
-      if (warp == 4 || warp == 5) {
+      // 32 (i / 16), so atom q (tap dx = 1 - q) is lanes 0-15 of quarter q,
+      // read by the warp of that quarter (warp 4: q 0, 5: 1, 2: 2; quarter 3
+      // holds the unused fourth atom)
+      const int q = warp & 3;
+      if (q != 3) {
         const bool got = tc::mbar_wait_bounded(&acc_full, (uint32_t)(ps & 1), kWaitCycles);
         if (!__all_sync(0xffffffffu, got)) {
           timeout = true;
@@ -254,18 +264,20 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_tile_kernel(const __grid_co
         }
         tc::fence_after_sync();
         float* dst = part + (size_t)blockIdx.x * g.kpad * COUT;
-        const int q = warp & 3, co = q * 16 + lane;
-        for (int tap = t0; tap < t1; ++tap)
-          for (int a = 0; a < na; ++a) {
-            float v[16];
-            tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (tap - t0) * 16 * G + a * 16, v);
-            if (lane < 16 && co < COUT)
+        for (int gg = g0; gg < g1; ++gg) {
+          const int tap = gg * 3 + (2 - q);   // (dz + 1) 9 + (dy + 1) 3 + (dx + 1)
+          for (int h = 0; h < L::kYAtoms; ++h)
+            for (int a = 0; a < na; ++a) {
+              float v[16];
+              tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + ((gg - g0) * L::kYAtoms + h) * 16 * G + a * 16, v);
+              if (lane < 16)
 #pragma unroll
-              for (int j = 0; j < 16; ++j) {
-                const int ci = (c0 + a) * 16 + j;
-                if (ci < g.cin) dst[(size_t)(tap * g.cin + ci) * COUT + co] = v[j];
-              }
-          }
+                for (int j = 0; j < 16; ++j) {
+                  const int ci = (c0 + a) * 16 + j;
+                  if (ci < g.cin) dst[(size_t)(tap * g.cin + ci) * COUT + h * 16 + lane] = v[j];
+                }
+            }
+        }
         tc::fence_before_sync();
         tc::mbar_arrive(&acc_empty);
       }
