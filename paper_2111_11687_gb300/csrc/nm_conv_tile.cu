@@ -379,7 +379,8 @@ cudaError_t launch_tile(const nm_conv3d_desc& d, const void* x, const void* w, c
 }  // namespace
 
 bool conv_tile_ok(const nm_conv3d_desc& d) {
-  return d.c1 == 0 && !d.src0_coarse && d.c0 % 8 == 0 && (d.cout == 16 || d.cout == 32 || d.cout == 64);
+  return d.c1 == 0 && !d.src0_coarse && d.c0 % 8 == 0 &&
+         (d.cout == 16 || d.cout == 32 || d.cout == 48 || d.cout == 64);
 }
 
 cudaError_t conv3d_fwd_tile(const nm_conv3d_desc& d, const void* x, const void* w, const float* bias, void* y,
@@ -388,6 +389,7 @@ cudaError_t conv3d_fwd_tile(const nm_conv3d_desc& d, const void* x, const void* 
   const TileHead none{nullptr, nullptr, 0, nullptr};
   if (d.cout == 16) return launch_tile<16, 4, kSwz>(d, x, w, bias, y, relu, none, status, s);
   if (d.cout == 32) return launch_tile<32, 2, kSwz>(d, x, w, bias, y, relu, none, status, s);
+  if (d.cout == 48) return launch_tile<48, 2, kSwz>(d, x, w, bias, y, relu, none, status, s);
   return launch_tile<64, 2, kSwz>(d, x, w, bias, y, relu, none, status, s);
 }
 

@@ -289,20 +289,38 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_tile_kernel(const __grid_co
   if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
-// Bias gradient db[co] = sum over voxels of dY[v][co]: per-CTA partial sums
-// in a fixed order, then CTAs in index order.
-__global__ void bias_grad_partial(const bf16* __restrict__ dy, long long m, int cout, float* __restrict__ part) {
-  extern __shared__ float red[];                    // [blockDim][cout]
-  float acc[32];
-  for (int c = 0; c < cout; ++c) acc[c] = 0.0f;
-  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < m; v += (long long)gridDim.x * blockDim.x)
-    for (int c = 0; c < cout; ++c) acc[c] += __bfloat162float(dy[v * cout + c]);
-  for (int c = 0; c < cout; ++c) red[threadIdx.x * cout + c] = acc[c];
+// Bias gradient db[co] = sum over voxels of dY[v][co].  Each thread sums one
+// 8-channel octet of a fixed, strided set of voxels (16-byte loads); a
+// block's threads of one octet are added in thread order, the blocks in index
+// order by bias_grad_final.
+template <int COUT>
+__global__ void __launch_bounds__(256) bias_grad_partial(const bf16* __restrict__ dy, long long m,
+                                                         float* __restrict__ part) {
+  constexpr int L = COUT / 8;       // octets per voxel
+  constexpr int VPB = 256 / L;      // voxels per block and step
+  __shared__ float red[256][9];
+  float acc[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) acc[j] = 0.0f;
+  const int oct = threadIdx.x % L;
+  for (long long v = (long long)blockIdx.x * VPB + threadIdx.x / L; v < m; v += (long long)gridDim.x * VPB) {
+    const uint4 w = __ldg(reinterpret_cast<const uint4*>(dy + v * COUT) + oct);
+    const __nv_bfloat162* e = reinterpret_cast<const __nv_bfloat162*>(&w);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float2 f = __bfloat1622float2(e[j]);
+      acc[2 * j] += f.x;
+      acc[2 * j + 1] += f.y;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j) red[threadIdx.x][j] = acc[j];
   __syncthreads();
-  for (int c = threadIdx.x; c < cout; c += blockDim.x) {
+  if (threadIdx.x < COUT) {
+    const int o = threadIdx.x / 8, j = threadIdx.x % 8;
     float s = 0.0f;
-    for (int t = 0; t < (int)blockDim.x; ++t) s += red[t * cout + c];
-    part[(size_t)blockIdx.x * cout + c] = s;
+    for (int t = o; t < 256; t += L) s += red[t][j];
+    part[(size_t)blockIdx.x * COUT + threadIdx.x] = s;
   }
 }
 
@@ -314,15 +332,29 @@ __global__ void bias_grad_final(const float* __restrict__ part, int blocks, int 
   db[c] = s;
 }
 
-__global__ void wgrad_tile_reduce(const float* __restrict__ part, int splits, int kpad, int kreal, int cout,
-                                  float* __restrict__ dw) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (long long)kpad * cout) return;
-  const int co = (int)(i / kpad), k = (int)(i % kpad);
+// dW = the CTAs' partials part[cta][k][co] summed in a fixed order: per
+// element, eight warps each add a contiguous run of CTAs, then the runs are
+// added in order.  A warp reads 32 consecutive floats of the (k, co) layout.
+__global__ void __launch_bounds__(256) wgrad_tile_reduce(const float* __restrict__ part, int splits, int kpad,
+                                                         int kreal, int cout, float* __restrict__ dw) {
+  __shared__ float red[8][33];
+  const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5;
+  const long long n = (long long)kpad * cout;
+  const long long e = (long long)blockIdx.x * 32 + lane;
+  const int per = (splits + 7) / 8;
+  const int t1 = min(splits, (seg + 1) * per);
   float s = 0.0f;
-  if (k < kreal)
-    for (int t = 0; t < splits; ++t) s += part[((long long)t * kpad + k) * cout + co];
-  dw[(long long)co * kpad + k] = s;
+  if (e < n)
+    for (int t = seg * per; t < t1; ++t) s += part[(long long)t * n + e];
+  red[seg][lane] = s;
+  __syncthreads();
+  if (seg == 0 && e < n) {
+    float r = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) r += red[q][lane];
+    const int k = (int)(e / cout), co = (int)(e % cout);
+    dw[(long long)co * kpad + k] = k < kreal ? r : 0.0f;
+  }
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -386,10 +418,10 @@ cudaError_t launch_wgrad_tile(const nm_conv3d_desc& d, const void* x, const void
   if (e != cudaSuccess) return e;
   wgrad_tile_kernel<COUT, G><<<grid, kThreads, L::kSmem, s>>>(mx, my, g, part, status);
   const long long n = (long long)g.kpad * COUT;
-  wgrad_tile_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(part, grid, g.kpad, 27 * d.c0, COUT, dw);
+  wgrad_tile_reduce<<<(unsigned)((n + 31) / 32), 256, 0, s>>>(part, grid, g.kpad, 27 * d.c0, COUT, dw);
   if (db) {
     const long long m = (long long)d.n * d.d * d.h * d.w;
-    bias_grad_partial<<<kBiasBlocks, 128, 128 * COUT * sizeof(float), s>>>((const bf16*)dy, m, COUT, bpart);
+    bias_grad_partial<COUT><<<kBiasBlocks, 256, 0, s>>>((const bf16*)dy, m, bpart);
     bias_grad_final<<<1, 32, 0, s>>>(bpart, kBiasBlocks, COUT, db);
   }
   return cudaGetLastError();

@@ -54,12 +54,13 @@ CASES = [
     (1, 6, 10, 12, 32, 0, 0, 64),     # 64 outputs, ragged tiles
     (2, 24, 64, 64, 16, 0, 0, 16),    # more tiles than SMs: persistent CTAs take several
     (1, 32, 64, 48, 48, 0, 0, 32),    # several tiles per CTA and three chunks per tile
+    (2, 10, 21, 19, 16, 0, 0, 48),    # 48 outputs (a decoder input's gradient), ragged tiles
 ]
 
 
 @pytest.fixture(params=["default", "gather"])
 def conv_path(request, monkeypatch):
-    # "default": single-source convolutions with 16, 32 or 64 outputs take the
+    # "default": single-source convolutions with 16, 32, 48 or 64 outputs take the
     # shifted-window kernel; "gather": the im2col-gather kernel for everything.
     if request.param == "gather":
         monkeypatch.setenv("NM_CONV_GATHER", "1")
