@@ -115,6 +115,31 @@ def train(nm, torch, net, cases, lows, highs, steps, patch, batch, lr, seed, log
     return losses
 
 
+def validation_loss(nm, torch, net, cases, lows, highs, patch, batch, n_batches=16, seed=11):
+    """The training loss (weighted squared error, forward only) of ``net`` on
+    fixed patches of held-out phantoms."""
+    rng = np.random.default_rng(seed)
+    x = torch.empty((batch, patch, patch, patch, 8), dtype=torch.bfloat16, device="cuda")
+    tgt = torch.empty((batch, patch, patch, patch), dtype=torch.float32, device="cuda")
+    wgt = torch.empty_like(tgt)
+    y = torch.empty_like(tgt)
+    scales = [nm.nm_denoise_scales(lo, c.activity, c.density) for c, lo in zip(cases, lows)]
+    boxes = [body_box(c.density, patch // 2) for c in cases]
+    total = 0.0
+    for b in range(n_batches):
+        i = b % len(cases)
+        (z0, y0, x0), (z1, y1, x1) = boxes[i]
+        corners = np.stack([rng.integers(x0, x1 + 1, batch), rng.integers(y0, y1 + 1, batch),
+                            rng.integers(z0, z1 + 1, batch)], 1) - patch // 2
+        cd = torch.from_numpy(corners.astype(np.int32)).cuda()
+        ds, as_ = scales[i]
+        nm.nm_denoise_make_patches(lows[i], cases[i].density, cases[i].activity, highs[i], ds, as_, cd, patch, x,
+                                   tgt, wgt)
+        net.forward(x, y)
+        total += float((wgt * (y - tgt) ** 2).mean().item())
+    return total / n_batches
+
+
 def organ_error(means, ref, counts, min_voxels=1):
     sel = (counts[1:] >= min_voxels) & (ref[1:] > 0)
     return np.abs(means[1:][sel] / ref[1:][sel] - 1.0)
@@ -175,7 +200,7 @@ def time_to_target_denoised(case, net, ref, counts, step_decays, max_decays, tar
 
 def run(train_n=200, test_n=20, shape=(300, 256, 256), spacing=(0.2, 0.2, 0.3), low=int(1e7), high=int(1e9),
         ref=int(1e10), denoise_low=int(1e7), steps=10000, patch=64, batch=4, lr=1e-3, workers=None,
-        step_decays=int(5e6), max_decays=int(2e9), seed0=1000, log_every=0):
+        step_decays=int(5e6), max_decays=int(2e9), seed0=1000, log_every=0, candidates=3):
     # the pool is started (first next()) before any GPU work
     phantoms = make_phantoms(list(range(seed0, seed0 + train_n + test_n)), shape, spacing, workers)
     first = next(phantoms)
@@ -194,10 +219,30 @@ def run(train_n=200, test_n=20, shape=(300, 256, 256), spacing=(0.2, 0.2, 0.3), 
     lows = [c.dose(low, 7)[0] for c in tr]
     highs = [c.dose(high, 8)[0] for c in tr]
     t_data = time.perf_counter() - t0
-    net = nm.Denoiser(patch=patch, batch=batch, levels=4, base_width=16, seed=1, lr=lr)
+    # Model selection: `candidates` networks (different initial weights and
+    # patch draws) train on the training phantoms but a held-out tenth, and
+    # the one with the lowest loss on that tenth is kept.  Training runs
+    # differ by which minimum they settle in, and the organ errors follow the
+    # loss; the test phantoms play no part in the choice.
+    n_val = max(1, train_n // 10) if candidates > 1 else 0
+    fit = slice(0, train_n - n_val)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    losses = train(nm, torch, net, tr, lows, highs, steps, patch, batch, lr, seed=5, log_every=log_every)
+    net, losses, val_losses, fit_losses = None, None, [], []
+    for k in range(candidates):
+        cand = nm.Denoiser(patch=patch, batch=batch, levels=4, base_width=16, seed=1 + k, lr=lr)
+        cl = train(nm, torch, cand, tr[fit], lows[fit], highs[fit], steps, patch, batch, lr, seed=5 + k,
+                   log_every=log_every)
+        v = (validation_loss(nm, torch, cand, tr[train_n - n_val:], lows[train_n - n_val:],
+                             highs[train_n - n_val:], patch, batch) if n_val else 0.0)
+        val_losses.append(v)
+        fit_losses.append(float(np.mean(cl[-50:])))
+        if net is None or v < min(val_losses[:-1]):
+            if net is not None:
+                net.close()
+            net, losses = cand, cl
+        else:
+            cand.close()
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     del lows, highs
@@ -223,6 +268,7 @@ def run(train_n=200, test_n=20, shape=(300, 256, 256), spacing=(0.2, 0.2, 0.3), 
     summary = dict(train=train_n, test=test_n, grid=list(shape[::-1]), low=low, high=high, ref=ref,
                    denoise_low=denoise_low, steps=steps, patch=patch, batch=batch, data_s=t_data,
                    train_s=t_train, final_loss=float(np.mean(losses[-50:])), first_loss=float(np.mean(losses[:10])),
+                   candidates=candidates, candidate_val_losses=val_losses, candidate_final_losses=fit_losses,
                    plain_mc_s_median=med("plain_mc_s"), mc_denoiser_s_median=med("mc_denoiser_s"),
                    plain_mc_decays_median=med("plain_mc_decays"), mc_denoiser_decays_median=med("mc_denoiser_decays"),
                    denoiser_faster=sum(1 for r in results if r["mc_denoiser_s"] is not None and
@@ -249,11 +295,12 @@ def main():
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--workers", type=int, default=0)
     ap.add_argument("--log-every", type=int, default=0)
+    ap.add_argument("--candidates", type=int, default=3, help="networks trained; the best on held-out phantoms is kept")
     a = ap.parse_args()
     nx, ny, nz = (int(v) for v in a.grid.split(","))
     sp = tuple(float(v) / 10 for v in a.voxel_mm.split(","))
     out = run(a.train, a.test, (nz, ny, nx), sp, int(a.low), int(a.high), int(a.ref), int(a.denoise_low), a.steps,
-              a.patch, a.batch, a.lr, a.workers or None, log_every=a.log_every)
+              a.patch, a.batch, a.lr, a.workers or None, log_every=a.log_every, candidates=a.candidates)
     print(json.dumps(out))
 
 

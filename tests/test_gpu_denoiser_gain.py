@@ -16,8 +16,10 @@ def test_denoiser_reduces_low_count_organ_error():
     from paper_2111_11687_gb300 import experiment
     out = experiment.run(train_n=10, test_n=3, shape=(75, 64, 64), spacing=(0.8, 0.8, 1.2), low=int(2e5),
                          high=int(2e7), ref=int(2e8), denoise_low=int(2e5), steps=1200, patch=32, batch=4, lr=2e-3,
-                         workers=1, step_decays=int(2e5), max_decays=int(2e8))
+                         workers=1, step_decays=int(2e5), max_decays=int(2e8), candidates=2)
     assert out["final_loss"] < out["first_loss"]
+    # two candidates trained, the one kept has the lower held-out loss
+    assert len(out["candidate_val_losses"]) == 2 and all(v > 0 for v in out["candidate_val_losses"])
     dn = np.array([c["denoiser_mean_err"] for c in out["cases"]])
     lo = np.array([c["low_mc_mean_err"] for c in out["cases"]])
     # the trained network must lower the mean organ error of its own input
