@@ -269,6 +269,17 @@ nm_status nm_check_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, u
  * Kahn sampler with key (seed) and counters 0..n-1; cos_out[n] host. */
 nm_status nm_check_kahn(double e_mev, int64_t n, uint64_t seed, float* cos_out);
 
+/* Fault injection: the n-th device allocation made by the library from now
+ * on (nm_dose_create and the calls it makes) fails as if the device were out
+ * of memory; 0 switches it off.  The failing call returns NM_ERR_OOM and frees
+ * what it had allocated. */
+void nm_debug_fail_alloc(int32_t n);
+
+/* Runs one bounded device wait on an mbarrier that nothing completes (the
+ * wait of the tensor-core kernels) with a limit of max_cycles SM clocks:
+ * returns NM_ERR_TIMEOUT once it gives up; the context stays usable. */
+nm_status nm_check_wait_timeout(int64_t max_cycles);
+
 /* n positron kinetic energies (MeV) as the transport draws them in the beta+
  * spectrum mode (beta_max_mev = t_max_mev, beta_z = z), for histories 0..n-1
  * with key (seed): inverse-CDF table built in FP64 on the host, linear between

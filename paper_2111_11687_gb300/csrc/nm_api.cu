@@ -1,6 +1,7 @@
 // C ABI of libnmdose (include/nm_dose.h): argument checks, device memory,
 // the batch loop of nm_dose_run, and the read-out calls.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -100,8 +101,19 @@ std::vector<float> beta_inverse_cdf(double t_max, int z) {
   return tab;
 }
 
+// Fault injection for the tests: the n-th device allocation from now (through
+// dalloc) fails as if the device were out of memory (0 = off).
+std::atomic<int> g_fail_alloc{0};
+
 template <class T>
 cudaError_t dalloc(T** p, size_t n) {
+  int k = g_fail_alloc.load();
+  while (k > 0 && !g_fail_alloc.compare_exchange_weak(k, k - 1)) {
+  }
+  if (k == 1) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
   return cudaMalloc((void**)p, n * sizeof(T) > 0 ? n * sizeof(T) : 1);
 }
 
@@ -597,8 +609,8 @@ nm_status nm_dose_create(nm_dose** out, const nm_grid* g, const nm_materials* mt
   // Decay sampler: alias table over the active voxels, FP64 on the device.
   if (o.source_mode == NM_SOURCE_DECAY) {
     float* act = nullptr;
-    void* scratch = nullptr;
-    if ((e = dalloc(&act, V)) || (e = cudaMalloc(&scratch, AliasScratch::bytes(V)))) {
+    uint8_t* scratch = nullptr;
+    if ((e = dalloc(&act, V)) || (e = dalloc(&scratch, AliasScratch::bytes(V)))) {
       if (act) cudaFree(act);
       return bail(cuda_fail(e, "alias scratch"));
     }
@@ -1281,6 +1293,23 @@ nm_status nm_check_kahn(double e_mev, int64_t n, uint64_t seed, float* cos_out) 
   cudaFree(d); cudaFree(st);
   if (e) return cuda_fail(e, "nm_check_kahn");
   if (flags) return fail(NM_ERR_DEVICE, "Kahn trial limit hit");
+  return NM_OK;
+}
+
+void nm_debug_fail_alloc(int32_t n) { g_fail_alloc.store(n > 0 ? n : 0); }
+
+nm_status nm_check_wait_timeout(int64_t max_cycles) {
+  if (max_cycles < 0) return fail(NM_ERR_ARG, "max_cycles must be >= 0");
+  uint32_t* st = nullptr;
+  uint32_t flags = 0;
+  cudaError_t e = dalloc(&st, 1);
+  if (!e) e = cudaMemset(st, 0, 4);
+  if (!e) e = launch_check_wait(max_cycles, st, 0);
+  if (!e) e = cudaMemcpy(&flags, st, 4, cudaMemcpyDeviceToHost);
+  cudaFree(st);
+  if (e) return cuda_fail(e, "nm_check_wait_timeout");
+  if (flags & NM_DEV_TIMEOUT) return fail(NM_ERR_TIMEOUT, "a bounded device wait gave up after %lld cycles",
+                                          (long long)max_cycles);
   return NM_OK;
 }
 

@@ -378,6 +378,28 @@ cudaError_t launch_tile(const nm_conv3d_desc& d, const void* x, const void* w, c
 
 }  // namespace
 
+namespace {
+
+// An mbarrier that nothing ever arrives on, waited for with the bounded wait
+// of the tensor-core kernels: the wait must give up after max_cycles and
+// record NM_DEV_TIMEOUT, leaving the context usable.
+__global__ void check_wait_kernel(long long max_cycles, uint32_t* status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !tc::mbar_wait_bounded(&bar, 0, max_cycles)) atomicOr(status, NM_DEV_TIMEOUT);
+}
+
+}  // namespace
+
+cudaError_t launch_check_wait(long long max_cycles, uint32_t* status, cudaStream_t s) {
+  check_wait_kernel<<<1, 32, 0, s>>>(max_cycles, status);
+  return cudaGetLastError();
+}
+
 bool conv_tile_ok(const nm_conv3d_desc& d) {
   return d.c1 == 0 && !d.src0_coarse && d.c0 % 8 == 0 &&
          (d.cout == 16 || d.cout == 32 || d.cout == 48 || d.cout == 64);

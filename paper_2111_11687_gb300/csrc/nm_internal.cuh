@@ -137,6 +137,7 @@ int transport_max_blocks_per_sm(int block, bool warp_agg, bool rayleigh, bool re
                                 bool multi = false, bool history = false, bool beta = false);
 cudaError_t launch_check_philox(const uint4* ctr, const uint2* key, int64_t n, uint4* out,
                                 cudaStream_t s);
+cudaError_t launch_check_wait(long long max_cycles, uint32_t* status, cudaStream_t s);
 cudaError_t launch_check_beta(const float* tab, int64_t n, uint32_t k0, uint32_t k1, float* out, cudaStream_t s);
 cudaError_t launch_check_kahn(float e, int64_t n, uint32_t k0, uint32_t k1, float* out,
                               uint32_t* status, cudaStream_t s);

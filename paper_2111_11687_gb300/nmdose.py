@@ -102,6 +102,8 @@ _SIGS = {
     "nm_check_philox": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "nm_check_kahn": (C.c_int, [C.c_double, C.c_int64, C.c_uint64, C.c_void_p]),
     "nm_check_beta": (C.c_int, [C.c_double, C.c_int32, C.c_int64, C.c_uint64, C.c_void_p]),
+    "nm_debug_fail_alloc": (None, [C.c_int32]),
+    "nm_check_wait_timeout": (C.c_int, [C.c_int64]),
     "nm_dose_alias_table": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.c_void_p, C.c_void_p, C.c_void_p]),
     "nm_check_source": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int64, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "nm_conv3d_kpad": (C.c_int32, [C.c_int32]),

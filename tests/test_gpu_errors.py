@@ -81,3 +81,41 @@ def test_step_limit_reports_device_status(nm):
         c = d.counters()
         assert c["killed"] > 0
         assert c["emitted"] == c["deposited"] + c["escaped"] + c["killed"]
+
+
+def test_bounded_wait_gives_up_and_the_context_survives(nm):
+    # the wait every tensor-core kernel uses, on an mbarrier that nothing
+    # completes: it must return NM_ERR_TIMEOUT, and the device stays usable
+    for cycles in (0, 1_000_000):
+        with pytest.raises(nm.NmError) as e:
+            nm._check(nm.load().nm_check_wait_timeout(cycles))
+        assert e.value.status == nm.NM_ERR_TIMEOUT
+    with _mk(nm) as d:
+        d.run(10_000, seed=3)
+        assert d.counters()["deposited"] > 0
+
+
+def test_allocation_failures_are_reported_and_leave_nothing_behind(nm):
+    import torch
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    failed = 0
+    try:
+        for n in range(1, 40):
+            nm.load().nm_debug_fail_alloc(n)
+            try:
+                with _mk(nm, labels=np.zeros((4, 5, 6), np.uint8), n_labels=2) as d:
+                    d.run(1000, seed=1)
+            except nm.NmError as e:
+                assert e.status == nm.NM_ERR_OOM, e
+                failed += 1
+            else:
+                break   # n is past the last allocation: creation went through
+    finally:
+        nm.load().nm_debug_fail_alloc(0)
+    assert failed >= 10
+    torch.cuda.synchronize()
+    assert abs(torch.cuda.mem_get_info()[0] - free0) < (64 << 20)
+    with _mk(nm) as d:
+        d.run(10_000, seed=3)
+        assert d.counters()["deposited"] > 0
