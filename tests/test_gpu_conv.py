@@ -55,6 +55,7 @@ CASES = [
     (2, 24, 64, 64, 16, 0, 0, 16),    # more tiles than SMs: persistent CTAs take several
     (1, 32, 64, 48, 48, 0, 0, 32),    # several tiles per CTA and three chunks per tile
     (2, 10, 21, 19, 16, 0, 0, 48),    # 48 outputs (a decoder input's gradient), ragged tiles
+    (1, 8, 20, 18, 96, 0, 0, 32),     # 96 inputs: two groups of three chunks, two passes each
 ]
 
 
