@@ -170,8 +170,8 @@ def time_to_target_denoised(case, net, ref, counts, step_decays, max_decays, tar
     same run, denoises the whole accumulated map and checks it, so a case the
     network cannot bring within target at the first checkpoint falls back to
     more Monte Carlo.  With organ_roi the network runs on the organs' bounding
-    box (the label map) instead of the whole body: only organ doses are
-    judged.  Also returns the errors at the first checkpoint."""
+    box (the label map) instead of the whole body: only organ doses enter the
+    criterion.  Also returns the errors at the first checkpoint."""
     torch, nm = case.torch, case.nm
     raw = torch.empty(case.shape, dtype=torch.float32, device="cuda")
     den = torch.empty_like(raw)
