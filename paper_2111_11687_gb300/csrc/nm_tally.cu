@@ -260,13 +260,9 @@ cudaError_t launch_fold(const FoldParams& p, cudaStream_t s) {
 cudaError_t launch_finalize(const FinalizeParams& p, cudaStream_t s) {
   const int nb = fold_blocks(p.V);
   const size_t smem = 2 * kLabelSlots * kFoldThreads * sizeof(double);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(finalize_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  // per call: cheap, and correct for every device and calling thread
+  cudaError_t e = cudaFuncSetAttribute(finalize_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   finalize_kernel<<<nb, kFoldThreads, smem, s>>>(p);
   if (p.labels) finalize_organs_kernel<<<(kLabelSlots + 3) / 4, 128, 0, s>>>(p, nb);
   return cudaGetLastError();
