@@ -111,6 +111,10 @@ typedef struct {
                                 and both photons out with it.  Not in nm_dose_tally_noalloc. */
   int32_t beta_z;            /* atomic number of the daughter for the Fermi function
                                 (18F -> 18O: 8, the default), 0..100 */
+  int32_t kn_sampler;        /* Compton angle (Klein-Nishina, §2.1): 0 (default) = inverse
+                                CDF tabulated in FP64 at 64 energies x 257 probabilities
+                                and interpolated (one draw, CDF error < 2e-5); 1 = Kahn's
+                                rejection sampler.  Batched runs need one value for all. */
 } nm_options;
 
 typedef struct {
@@ -268,6 +272,12 @@ nm_status nm_check_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, u
 /* n Klein-Nishina scattering cosines at energy e_mev drawn by the device's
  * Kahn sampler with key (seed) and counters 0..n-1; cos_out[n] host. */
 nm_status nm_check_kahn(double e_mev, int64_t n, uint64_t seed, float* cos_out);
+
+/* n scattering cosines at energy e_mev drawn by the transport's tabulated
+ * Klein-Nishina sampler (kn_sampler = 0) built for photons between cut_mev
+ * and e0_mev, key (seed), counters 0..n-1; cos_out[n] host. */
+nm_status nm_check_kn_table(double e_mev, double cut_mev, double e0_mev, int64_t n, uint64_t seed,
+                            float* cos_out);
 
 /* Fault injection: the n-th device allocation made by the library from now
  * on (nm_dose_create and the calls it makes) fails as if the device were out

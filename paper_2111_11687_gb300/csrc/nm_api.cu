@@ -105,6 +105,43 @@ std::vector<float> beta_inverse_cdf(double t_max, int z) {
 // dalloc) fails as if the device were out of memory (0 = off).
 std::atomic<int> g_fail_alloc{0};
 
+// Inverse CDF of the Klein-Nishina distribution of x = 1 - cos(theta) (per
+// unit x proportional to P^2 (P + 1/P - x (2 - x)), P = 1 / (1 + k x),
+// k = E / m c^2) at kKnInvE energies log spaced over [e_lo, e_hi]: node j of
+// row i is the x below which a fraction j / kKnInvU of the scatters at energy
+// i lie.  Trapezoid rule on 2^14 panels in FP64, linear between panel edges.
+std::vector<float> kn_inverse_cdf(double e_lo, double e_hi) {
+  constexpr int kPanels = 1 << 14;
+  std::vector<float> tab((size_t)kKnInvE * (kKnInvU + 1));
+  std::vector<double> cum(kPanels + 1);
+  const double dln = (std::log(e_hi) - std::log(e_lo)) / (kKnInvE - 1);
+  const double h = 2.0 / kPanels;
+  for (int i = 0; i < kKnInvE; ++i) {
+    const double k = std::exp(std::log(e_lo) + i * dln) / kElectronMassMeV;
+    auto f = [k](double x) {
+      const double P = 1.0 / (1.0 + k * x);
+      return P * P * (P + 1.0 / P - x * (2.0 - x));
+    };
+    cum[0] = 0.0;
+    double prev = f(0.0);
+    for (int q = 0; q < kPanels; ++q) {
+      const double next = f((q + 1) * h);
+      cum[q + 1] = cum[q] + 0.5 * h * (prev + next);
+      prev = next;
+    }
+    float* row = &tab[(size_t)i * (kKnInvU + 1)];
+    row[0] = 0.0f;
+    row[kKnInvU] = 2.0f;
+    int q = 0;
+    for (int j = 1; j < kKnInvU; ++j) {
+      const double target = cum[kPanels] * j / kKnInvU;
+      while (cum[q + 1] < target) ++q;
+      row[j] = (float)((q + (target - cum[q]) / (cum[q + 1] - cum[q])) * h);
+    }
+  }
+  return tab;
+}
+
 template <class T>
 cudaError_t dalloc(T** p, size_t n) {
   int k = g_fail_alloc.load();
@@ -146,6 +183,8 @@ struct nm_dose {
   float* minv = nullptr;
   float* minv_out = nullptr;
   float* beta_tab = nullptr;   // beta+ spectrum inverse CDF (kBetaTable + 1), or NULL
+  float* kn_inv = nullptr;     // Klein-Nishina inverse CDF [kKnInvE][kKnInvU + 1]
+  float kn_inv_lo = 0, kn_inv_idln = 0;
   int32_t q_beta_max = 0;      // q_units(beta endpoint): bound of one positron's energy
   ull* s2h_lo = nullptr;       // history statistics (history_sigma): 128-bit sums of squares
   ull* s2h_hi = nullptr;
@@ -175,7 +214,7 @@ struct nm_dose {
   double batch_graph_ms = 0;      // device time of graphs launched by nm_dose_run_batch
 
   ~nm_dose() {
-    void* ptrs[] = {vox, density, labels, alias, tb, tsum, s2, kn, minv, minv_out, beta_tab, s2h_lo, s2h_hi, counters, work, status,
+    void* ptrs[] = {vox, density, labels, alias, tb, tsum, s2, kn, minv, minv_out, beta_tab, kn_inv, s2h_lo, s2h_hi, counters, work, status,
                     rho_max_bits, org_s1, org_s2, organ_count, organ_partial, organ_out,
                     out_dose, out_sigma};
     for (void* p : ptrs)
@@ -216,6 +255,9 @@ struct nm_dose {
     p.kn = kn;
     p.minv = minv;
     p.minv_out = minv_out;
+    p.kn_inv = opt.kn_sampler == 0 ? kn_inv : nullptr;
+    p.kn_inv_lo = kn_inv_lo;
+    p.kn_inv_idln = kn_inv_idln;
     p.s2h_lo = s2h_lo;
     p.s2h_hi = s2h_hi;
     p.key0 = (uint32_t)seed;
@@ -265,6 +307,7 @@ void nm_options_default(nm_options* o) {
   o->stream = nullptr;
   o->beta_max_mev = 0.0;
   o->beta_z = 8;
+  o->kn_sampler = 0;
 }
 
 const char* nm_last_error(void) { return g_err.c_str(); }
@@ -482,6 +525,7 @@ nm_status nm_dose_create(nm_dose** out, const nm_grid* g, const nm_materials* mt
   if (!(o.positron_mev >= 0) || o.positron_mev > 1.0) return fail(NM_ERR_ARG, "positron energy must be in [0, 1] MeV");
   if (!(o.activity_bq >= 0) || !std::isfinite(o.activity_bq)) return fail(NM_ERR_ARG, "activity_bq must be finite and >= 0");
   if (o.max_steps <= 0) return fail(NM_ERR_ARG, "max_steps must be > 0");
+  if (o.kn_sampler != 0 && o.kn_sampler != 1) return fail(NM_ERR_ARG, "kn_sampler must be 0 (table) or 1 (Kahn)");
   if (!(o.beta_max_mev >= 0.0 && o.beta_max_mev < 20.0) || o.beta_z < 0 || o.beta_z > 100)
     return fail(NM_ERR_ARG, "beta_max_mev must be in [0, 20) MeV and beta_z in 0..100");
   for (int m = 0; m < mt->n; ++m)
@@ -537,6 +581,15 @@ nm_status nm_dose_create(nm_dose** out, const nm_grid* g, const nm_materials* mt
       (e = dalloc(&h->organ_out, 4 * kLabelSlots)))
     return bail(cuda_fail(e, "device allocation"));
   if (labels && (e = dalloc(&h->labels, V))) return bail(cuda_fail(e, "device allocation"));
+  {
+    const std::vector<float> kt = kn_inverse_cdf(mt->photon_cut_mev, o.photon_mev);
+    h->kn_inv_lo = (float)std::log(mt->photon_cut_mev);
+    h->kn_inv_idln = (float)((kKnInvE - 1) / (std::log(o.photon_mev) - std::log(mt->photon_cut_mev)));
+    if ((e = dalloc(&h->kn_inv, kt.size())) ||
+        (e = cudaMemcpyAsync(h->kn_inv, kt.data(), kt.size() * sizeof(float), cudaMemcpyHostToDevice, s)) ||
+        (e = cudaStreamSynchronize(s)))
+      return bail(cuda_fail(e, "Klein-Nishina table"));
+  }
   std::vector<float> beta;
   if (o.source_mode == NM_SOURCE_DECAY && o.beta_max_mev > 0.0) {
     beta = beta_inverse_cdf(o.beta_max_mev, o.beta_z);
@@ -713,7 +766,8 @@ nm_status nm_dose_run(nm_dose* h, uint64_t n, uint64_t seed) {
 static bool same_physics(const nm_dose* a, const nm_dose* b) {
   if (a->n_mat != b->n_mat || a->rayleigh != b->rayleigh || a->e0 != b->e0 || a->cut != b->cut ||
       a->ln_e_lo != b->ln_e_lo || a->inv_dln != b->inv_dln || a->device != b->device ||
-      a->opt.batches != b->opt.batches || a->opt.max_steps != b->opt.max_steps)
+      a->opt.batches != b->opt.batches || a->opt.max_steps != b->opt.max_steps ||
+      a->opt.kn_sampler != b->opt.kn_sampler)
     return false;
   for (int m = 0; m < a->n_mat; ++m)
     if (a->mat[m].za != b->mat[m].za || a->mat[m].zp != b->mat[m].zp || a->mat[m].zr != b->mat[m].zr)
@@ -1310,6 +1364,33 @@ nm_status nm_check_wait_timeout(int64_t max_cycles) {
   if (e) return cuda_fail(e, "nm_check_wait_timeout");
   if (flags & NM_DEV_TIMEOUT) return fail(NM_ERR_TIMEOUT, "a bounded device wait gave up after %lld cycles",
                                           (long long)max_cycles);
+  return NM_OK;
+}
+
+nm_status nm_check_kn_table(double e_mev, double cut_mev, double e0_mev, int64_t n, uint64_t seed,
+                            float* cos_out) {
+  if (n < 0 || (n > 0 && !cos_out) || !(cut_mev > 0.0 && cut_mev < e0_mev && e0_mev <= 20.0) ||
+      !(e_mev >= cut_mev && e_mev <= e0_mev))
+    return fail(NM_ERR_ARG, "bad arguments");
+  if (n == 0) return NM_OK;
+  const std::vector<float> kt = kn_inverse_cdf(cut_mev, e0_mev);
+  TransportParams p;
+  memset(&p, 0, sizeof p);
+  p.key0 = (uint32_t)seed;
+  p.key1 = (uint32_t)(seed >> 32);
+  p.kn_inv_lo = (float)std::log(cut_mev);
+  p.kn_inv_idln = (float)((kKnInvE - 1) / (std::log(e0_mev) - std::log(cut_mev)));
+  float* d = nullptr;
+  float* dt = nullptr;
+  cudaError_t e = dalloc(&d, n);
+  if (!e) e = dalloc(&dt, kt.size());
+  if (!e) e = cudaMemcpy(dt, kt.data(), kt.size() * sizeof(float), cudaMemcpyHostToDevice);
+  p.kn_inv = dt;
+  if (!e) e = launch_check_kn_table(p, (float)e_mev, n, d, 0);
+  if (!e) e = cudaMemcpy(cos_out, d, n * sizeof(float), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  cudaFree(dt);
+  if (e) return cuda_fail(e, "nm_check_kn_table");
   return NM_OK;
 }
 

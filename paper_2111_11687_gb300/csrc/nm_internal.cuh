@@ -55,6 +55,10 @@ __device__ __forceinline__ float u01(uint32_t r) { return ((float)(r >> 9) + 0.5
 // Random-stream ids inside one history.
 enum : uint32_t { kStreamSource = 0, kStreamPhotonA = 1, kStreamPhotonB = 2, kStreamPositron = 3 };
 constexpr int kBetaTable = 1024;   // inverse-CDF nodes of the beta+ spectrum (+1)
+// Klein-Nishina inverse CDF of x = 1 - cos(theta): kKnInvE energies (log
+// spaced from the photon cutoff to the source energy) x kKnInvU + 1
+// cumulative-probability nodes.
+constexpr int kKnInvE = 64, kKnInvU = 256;
 
 struct MaterialCoef {
   float za;       // (Z/A) * N_A * sigma-table scale: mu_c/rho = za * kn(E)
@@ -97,6 +101,8 @@ struct TransportParams {
   const float* kn;            // kKnTable nodes of N_A * sigma_KN(E)
   const float* minv;          // kKnTable bins: 1 / majorant (cm) on [E_i, E_i+1)
   const float* minv_out;      // the same outside the tracking box (much larger)
+  const float* kn_inv;        // Klein-Nishina inverse CDF [kKnInvE][kKnInvU + 1]; NULL = Kahn's sampler
+  float kn_inv_lo, kn_inv_idln; // ln of its first energy, 1 / its ln-energy step
   uint32_t key0, key1;        // Philox key = seed
   float e0;                   // photon energy, MeV
   int32_t q_e0;               // q_units(e0)
@@ -138,6 +144,7 @@ int transport_max_blocks_per_sm(int block, bool warp_agg, bool rayleigh, bool re
 cudaError_t launch_check_philox(const uint4* ctr, const uint2* key, int64_t n, uint4* out,
                                 cudaStream_t s);
 cudaError_t launch_check_wait(long long max_cycles, uint32_t* status, cudaStream_t s);
+cudaError_t launch_check_kn_table(const TransportParams& p, float e, int64_t n, float* out, cudaStream_t s);
 cudaError_t launch_check_beta(const float* tab, int64_t n, uint32_t k0, uint32_t k1, float* out, cudaStream_t s);
 cudaError_t launch_check_kahn(float e, int64_t n, uint32_t k0, uint32_t k1, float* out,
                               uint32_t* status, cudaStream_t s);

@@ -90,6 +90,26 @@ __device__ __forceinline__ float kahn_x(float k, uint32_t& ctr, uint32_t stream,
   }
 }
 
+// Klein-Nishina x = 1 - cos(theta) at photon energy e from one uniform word:
+// the inverse CDF tabulated (in FP64, on the host) at kKnInvE log-spaced
+// energies x kKnInvU + 1 cumulative probabilities, interpolated linearly in
+// ln E and in the probability (CDF error below 2e-5 everywhere).  One draw,
+// no rejection loop, so the lanes of a warp never wait for each other.
+__device__ __forceinline__ float kn_table_x(const TransportParams& p, float e, uint32_t r) {
+  float t = (__logf(e) - p.kn_inv_lo) * p.kn_inv_idln;
+  t = fminf(fmaxf(t, 0.0f), (float)(kKnInvE - 1) - 0x1p-10f);
+  const int i = (int)t;
+  const float w = t - (float)i;
+  const float sv = u01(r) * (float)kKnInvU;
+  const int j = min((int)sv, kKnInvU - 1);
+  const float v = sv - (float)j;
+  const float* a = p.kn_inv + i * (kKnInvU + 1) + j;
+  const float* b = a + (kKnInvU + 1);
+  const float a0 = __ldg(a), a1 = __ldg(a + 1), b0 = __ldg(b), b1 = __ldg(b + 1);
+  const float x0 = fmaf(v, a1 - a0, a0), x1 = fmaf(v, b1 - b0, b0);
+  return fmaf(w, x1 - x0, x0);
+}
+
 // New direction at polar cosine c and azimuth phi about (u, v, w).
 __device__ __forceinline__ void rotate(float& u, float& v, float& w, float c, float phi) {
   const float s2 = fmaf(-c, c, 1.0f);
@@ -361,7 +381,14 @@ __device__ __forceinline__ void compton(const TransportParams& p, const float* s
                                         unsigned long long* s_cnt) {
   uint32_t rphi;
   const float k = e * kInvElectronMassMeV;
-  const float x = kahn_x(k, ctr, stream, hlo, hhi, p.key0, p.key1, rphi, flags);
+  float x;
+  if (p.kn_inv) {
+    const uint4 r = draw(ctr, stream, hlo, hhi, p.key0, p.key1);
+    x = kn_table_x(p, e, r.x);
+    rphi = r.y;
+  } else {
+    x = kahn_x(k, ctr, stream, hlo, hhi, p.key0, p.key1, rphi, flags);
+  }
   const float e2 = __fdividef(e, fmaf(k, x, 1.0f));
   rotate(ux, uy, uz, 1.0f - x, fmaf(kTwoPi, u01(rphi), -3.14159265f));
   if (e2 < p.cut) {
@@ -738,6 +765,16 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
   }
 }
 
+// Scattering cosines at energy e as the transport's table sampler draws them
+// (counters 0..n-1 of stream 7, key k0 k1).
+__global__ void check_kn_table_kernel(const TransportParams p, float e, int64_t n, float* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t ctr = 0;
+  const uint4 r = draw(ctr, 7u, (uint32_t)i, (uint32_t)(i >> 32), p.key0, p.key1);
+  out[i] = 1.0f - kn_table_x(p, e, r.x);
+}
+
 // Positron energies of histories 0..n-1 as the transport draws them.
 __global__ void check_beta_kernel(const float* tab, int64_t n, uint32_t k0, uint32_t k1, float* out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -846,6 +883,12 @@ int transport_max_blocks_per_sm(int block, bool warp_agg, bool rayleigh, bool re
     return 0;
   }
   return n;
+}
+
+cudaError_t launch_check_kn_table(const TransportParams& p, float e, int64_t n, float* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  check_kn_table_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, e, n, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_check_beta(const float* tab, int64_t n, uint32_t k0, uint32_t k1, float* out, cudaStream_t s) {

@@ -51,7 +51,7 @@ class nm_options(C.Structure):
                 ("warp_aggregate", C.c_int32), ("regroup", C.c_int32), ("regroup_lanes", C.c_int32),
                 ("max_steps", C.c_int32),
                 ("stream", C.c_void_p), ("history_sigma", C.c_int32), ("beta_max_mev", C.c_double),
-                ("beta_z", C.c_int32)]
+                ("beta_z", C.c_int32), ("kn_sampler", C.c_int32)]
 
 
 class nm_counters(C.Structure):
@@ -103,6 +103,7 @@ _SIGS = {
     "nm_check_kahn": (C.c_int, [C.c_double, C.c_int64, C.c_uint64, C.c_void_p]),
     "nm_check_beta": (C.c_int, [C.c_double, C.c_int32, C.c_int64, C.c_uint64, C.c_void_p]),
     "nm_debug_fail_alloc": (None, [C.c_int32]),
+    "nm_check_kn_table": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_int64, C.c_uint64, C.c_void_p]),
     "nm_check_wait_timeout": (C.c_int, [C.c_int64]),
     "nm_dose_alias_table": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.c_void_p, C.c_void_p, C.c_void_p]),
     "nm_check_source": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int64, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -290,6 +291,12 @@ def nm_check_philox(ctr: np.ndarray, key: np.ndarray) -> np.ndarray:
 def nm_check_kahn(e_mev: float, n: int, seed: int) -> np.ndarray:
     out = np.empty(n, np.float32)
     _check(load().nm_check_kahn(float(e_mev), n, seed, ptr(out)))
+    return out
+
+
+def nm_check_kn_table(e_mev: float, cut_mev: float, e0_mev: float, n: int, seed: int) -> np.ndarray:
+    out = np.empty(n, np.float32)
+    _check(load().nm_check_kn_table(float(e_mev), float(cut_mev), float(e0_mev), n, seed, ptr(out)))
     return out
 
 

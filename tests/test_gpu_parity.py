@@ -157,12 +157,14 @@ def _oracle_phantom_run(orc, ph, N, seed, batches=10):
                    spacing=ph.spacing, n_hist=N, seed=seed, batches=batches, activity_bq=inputs.ACTIVITY_BQ)
 
 
-def test_reduced_phantom_matches_oracle(nm, orc):
+@pytest.mark.parametrize("kn_sampler", [0, 1])
+def test_reduced_phantom_matches_oracle(nm, orc, kn_sampler):
     # The adult phantom's field of view on a 64x64x75 grid of 8x8x12 mm voxels:
-    # several alias columns per warp, ragged grid edges, all five materials.
+    # several alias columns per warp, ragged grid edges, all five materials;
+    # Compton angles from the tabulated inverse CDF (0) and from Kahn's sampler (1).
     ph = _phantom((75, 64, 64), (0.8, 0.8, 1.2), seed=21)
     N = 2_000_000
-    den, mat, g, sg, (gm, ge, gs, cnt), c, _ = _gpu_phantom_run(nm, ph, N, seed=7)
+    den, mat, g, sg, (gm, ge, gs, cnt), c, _ = _gpu_phantom_run(nm, ph, N, seed=7, kn_sampler=kn_sampler)
     assert c["emitted"] == c["deposited"] + c["escaped"] and c["killed"] == 0
     r = _oracle_phantom_run(orc, ph, N, seed=8)
     body = den >= 0.1
