@@ -105,12 +105,26 @@ std::vector<float> beta_inverse_cdf(double t_max, int z) {
 // dalloc) fails as if the device were out of memory (0 = off).
 std::atomic<int> g_fail_alloc{0};
 
+template <class T>
+cudaError_t dalloc(T** p, size_t n) {
+  int k = g_fail_alloc.load();
+  while (k > 0 && !g_fail_alloc.compare_exchange_weak(k, k - 1)) {
+  }
+  if (k == 1) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc((void**)p, n * sizeof(T) > 0 ? n * sizeof(T) : 1);
+}
+
+}  // namespace
+
 // Inverse CDF of the Klein-Nishina distribution of x = 1 - cos(theta) (per
 // unit x proportional to P^2 (P + 1/P - x (2 - x)), P = 1 / (1 + k x),
 // k = E / m c^2) at kKnInvE energies log spaced over [e_lo, e_hi]: node j of
 // row i is the x below which a fraction j / kKnInvU of the scatters at energy
 // i lie.  Trapezoid rule on 2^14 panels in FP64, linear between panel edges.
-std::vector<float> kn_inverse_cdf(double e_lo, double e_hi) {
+std::vector<float> nm::kn_inverse_cdf(double e_lo, double e_hi) {
   constexpr int kPanels = 1 << 14;
   std::vector<float> tab((size_t)kKnInvE * (kKnInvU + 1));
   std::vector<double> cum(kPanels + 1);
@@ -141,20 +155,6 @@ std::vector<float> kn_inverse_cdf(double e_lo, double e_hi) {
   }
   return tab;
 }
-
-template <class T>
-cudaError_t dalloc(T** p, size_t n) {
-  int k = g_fail_alloc.load();
-  while (k > 0 && !g_fail_alloc.compare_exchange_weak(k, k - 1)) {
-  }
-  if (k == 1) {
-    *p = nullptr;
-    return cudaErrorMemoryAllocation;
-  }
-  return cudaMalloc((void**)p, n * sizeof(T) > 0 ? n * sizeof(T) : 1);
-}
-
-}  // namespace
 
 struct nm_dose {
   int nx = 0, ny = 0, nz = 0;

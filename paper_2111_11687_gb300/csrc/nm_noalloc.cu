@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "nm_internal.cuh"
 
@@ -31,6 +32,8 @@ __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {nullptr};
+std::vector<float> g_kn;             // Klein-Nishina table of (g_kn_key[0] cutoff, g_kn_key[1] energy)
+double g_kn_key[2] = {0.0, 0.0};
 
 nm_status fail(nm_status st, const char* fmt, ...) {
   char buf[512];
@@ -112,6 +115,7 @@ extern "C" nm_status nm_dose_tally_noalloc(const nm_grid* g, const nm_materials*
     return fail(NM_ERR_ARG, "need 0 < photon cutoff < photon energy <= 1 MeV");
   if (o.max_steps <= 0) return fail(NM_ERR_ARG, "max_steps must be > 0");
   if (o.beta_max_mev != 0.0) return fail(NM_ERR_ARG, "the beta+ spectrum needs a handle (nm_dose_create)");
+  if (o.kn_sampler != 0 && o.kn_sampler != 1) return fail(NM_ERR_ARG, "kn_sampler must be 0 (table) or 1 (Kahn)");
   if (!decay) {
     const float L[3] = {g->nx * g->dx, g->ny * g->dy, g->nz * g->dz};
     for (int a = 0; a < 3; ++a)
@@ -137,6 +141,7 @@ extern "C" nm_status nm_dose_tally_noalloc(const nm_grid* g, const nm_materials*
   unsigned* work = (unsigned*)take(sizeof(unsigned));
   uint32_t* status = (uint32_t*)take(sizeof(uint32_t));
   uint32_t* rho_bits_d = (uint32_t*)take(4 * NM_MAX_MATERIALS);
+  float* kn_inv_d = (float*)take(sizeof(float) * kKnInvE * (kKnInvU + 1));
   void* alias_scratch = take(AliasScratch::bytes(V));
   if (off > kScratchBytes) return fail(NM_ERR_ARG, "grid too large for the no-allocation scratch");
 
@@ -180,6 +185,21 @@ extern "C" nm_status nm_dose_tally_noalloc(const nm_grid* g, const nm_materials*
       (e = cudaMemcpyAsync(minv_d, minv, sizeof minv, cudaMemcpyHostToDevice, s)) ||
       (e = cudaStreamSynchronize(s)))
     return cuda_fail(e, "physics tables");
+  if (o.kn_sampler == 0) {
+    // the Klein-Nishina table of the last (cutoff, energy) pair is kept on the host
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (g_kn_key[0] != mt->photon_cut_mev || g_kn_key[1] != o.photon_mev) {
+      g_kn = kn_inverse_cdf(mt->photon_cut_mev, o.photon_mev);
+      g_kn_key[0] = mt->photon_cut_mev;
+      g_kn_key[1] = o.photon_mev;
+    }
+    if ((e = cudaMemcpyAsync(kn_inv_d, g_kn.data(), g_kn.size() * sizeof(float), cudaMemcpyHostToDevice, s)) ||
+        (e = cudaStreamSynchronize(s)))
+      return cuda_fail(e, "Klein-Nishina table");
+    p.kn_inv = kn_inv_d;
+    p.kn_inv_lo = (float)std::log(mt->photon_cut_mev);
+    p.kn_inv_idln = (float)((kKnInvE - 1) / (std::log(o.photon_mev) - std::log(mt->photon_cut_mev)));
+  }
 
   int64_t n_active = 0;
   if (decay) {
