@@ -279,6 +279,70 @@ def run(train_n=200, test_n=20, shape=(300, 256, 256), spacing=(0.2, 0.2, 0.3), 
     return summary
 
 
+def configs(wb_ref=int(1e10), wb_step=int(5e6), wb_low=int(1e8), seed=1):
+    """The workloads other than the adult phantom, measured on one GPU:
+
+    * the 64^3 x 5 mm water cube with a central 0.511 MeV point source (one
+      photon per history), decays/s at its 1e6 histories and at 1e8;
+    * the 512 x 512 x 600 x (1 x 1 x 3 mm) whole-body phantom with lesions:
+      decays/s; plain MC's wall time until all 27 organ means are within 2 %
+      of a 1e10-decay reference; and the MC + denoiser arm's cost before any
+      check, MC of 1e8 decays plus one inference on the organs' bounding box
+      (a network of the configured shape; its time does not depend on the
+      weights).  A network is trained only at 2 x 2 x 3 mm here, so that
+      cost is the arm's lower bound, not a measured time to 2 %.
+    """
+    import torch
+
+    from paper_2111_11687_gb300 import build, inputs, nmdose as nm
+    build.build()
+    out = {}
+    # water cube, point source
+    cube = inputs.water_cube()
+    water = nm.Materials([0.5551], [7.42], inputs.PE_COEFF, inputs.PE_EXP)
+    den = torch.from_numpy(cube.density).cuda()
+    mat = torch.from_numpy(cube.material).cuda()
+    for n in (int(1e6), int(1e8)):
+        with nm.Dose(den, mat, cube.spacing, water, source_mode=nm.NM_SOURCE_POINT, point=cube.point) as d:
+            d.run(n, seed)                      # first run: autotuning, code loading
+            d.reset()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            d.run(n, seed)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            c = d.counters()
+        out[f"water_cube_{n:.0e}"] = dict(histories=n, wall_s=wall, decays_per_s_wall=n / wall,
+                                          decays_per_s_device=n / (c["transport_ms"] * 1e-3))
+    # whole body
+    mats = nm.Materials(inputs.MATERIAL_Z_OVER_A, inputs.MATERIAL_ZEFF, inputs.PE_COEFF, inputs.PE_EXP)
+    ph = inputs.whole_body_phantom(seed=seed)
+    case = Case(nm, torch, (ph.hu, ph.activity, ph.labels, ph.spacing), mats, inputs.N_LABELS,
+                inputs.ACTIVITY_BQ)
+    del ph
+    _, t_1e9 = case.dose(int(1e9), 11)
+    refmap, t_ref = case.dose(wb_ref, 12)
+    with case.handle() as h:
+        ref_org = h.map_organs(refmap)
+    del refmap
+    t_mc, n_mc, e_mc = time_to_target(case, ref_org, wb_step, int(2e9), 0.02, 13)
+    low, t_low = case.dose(wb_low, 14)
+    net = nm.Denoiser(patch=64, batch=1, levels=4, base_width=16, seed=1)
+    dn = torch.empty_like(low)
+    net.apply(low, case.density, case.activity, dn, roi=case.labels)   # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    net.apply(low, case.density, case.activity, dn, roi=case.labels)
+    torch.cuda.synchronize()
+    t_inf = time.perf_counter() - t0
+    net.close()
+    out["whole_body"] = dict(grid=[512, 512, 600], voxel_mm=[1, 1, 3], decays_per_s_1e9=1e9 / t_1e9,
+                             reference_decays=wb_ref, reference_s=t_ref, plain_mc_s=t_mc, plain_mc_decays=n_mc,
+                             plain_mc_err=e_mc, mc_low_decays=wb_low, mc_low_s=t_low, inference_s=t_inf,
+                             mc_denoiser_lower_bound_s=t_low + t_inf)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--train", type=int, default=200)
@@ -296,7 +360,11 @@ def main():
     ap.add_argument("--workers", type=int, default=0)
     ap.add_argument("--log-every", type=int, default=0)
     ap.add_argument("--candidates", type=int, default=3, help="networks trained; the best on held-out phantoms is kept")
+    ap.add_argument("--configs", action="store_true", help="measure the water-cube and whole-body workloads instead")
     a = ap.parse_args()
+    if a.configs:
+        print(json.dumps(configs()))
+        return
     nx, ny, nz = (int(v) for v in a.grid.split(","))
     sp = tuple(float(v) / 10 for v in a.voxel_mm.split(","))
     out = run(a.train, a.test, (nz, ny, nx), sp, int(a.low), int(a.high), int(a.ref), int(a.denoise_low), a.steps,
