@@ -196,7 +196,11 @@ nm_status nm_dose_get(nm_dose* h, float* dose, float* sigma, double* organ_dose)
 /* Per organ label 0..n_labels (arrays of n_labels + 1 doubles, any may be
  * NULL): Eq. 2 mean dose rate (Gy/s), Eq. 3 RMS of the voxels' relative
  * uncertainties (a voxel with zero dose counts as 1), batch standard deviation
- * of the organ mean (Gy/s), and the organ's voxel count. */
+ * of the organ mean (Gy/s), and the organ's voxel count.  Without eps_rms (and
+ * with a label map) no pass over the voxels is made: the mean and its sigma
+ * come from the per-organ batch sums the fold keeps (the same FP32 voxel
+ * doses, summed per batch in FP64), equal to the full pass's to ~1e-7
+ * relative; cheap enough to poll while a run converges. */
 nm_status nm_dose_get_organs(nm_dose* h, double* mean, double* eps_rms, double* sigma_mean,
                              int64_t* voxels);
 

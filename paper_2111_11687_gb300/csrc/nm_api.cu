@@ -1032,6 +1032,38 @@ nm_status nm_dose_get(nm_dose* h, float* dose, float* sigma, double* organ_dose)
 nm_status nm_dose_get_organs(nm_dose* h, double* mean, double* eps_rms, double* sigma_mean,
                              int64_t* voxels) {
   if (!h) return fail(NM_ERR_ARG, "handle is NULL");
+  if (!eps_rms && h->labels) {
+    // Eq. 2 and the batch sigma from the per-organ batch sums of the fold, no
+    // pass over the voxels: mean = A sum_b O_b / (N cnt) with O_b the batch's
+    // summed voxel doses (the same FP32 voxel doses the full pass sums)
+    if (h->hist_next == 0) return fail(NM_ERR_STATE, "no histories simulated yet");
+    if (sigma_mean && h->n_batches < 2) return fail(NM_ERR_STATE, "need at least 2 batches for the uncertainty");
+    std::vector<double> s1(kLabelSlots), s2(kLabelSlots);
+    std::vector<long long> cnt(kLabelSlots);
+    cudaStream_t s = h->stream;
+    NM_CUDA(cudaMemcpyAsync(s1.data(), h->org_s1, kLabelSlots * sizeof(double), cudaMemcpyDeviceToHost, s), "organ sums");
+    NM_CUDA(cudaMemcpyAsync(s2.data(), h->org_s2, kLabelSlots * sizeof(double), cudaMemcpyDeviceToHost, s), "organ sums");
+    NM_CUDA(cudaMemcpyAsync(cnt.data(), h->organ_count, kLabelSlots * sizeof(long long), cudaMemcpyDeviceToHost, s),
+            "organ counts");
+    NM_CUDA(cudaStreamSynchronize(s), "nm_dose_get_organs");
+    const double N = (double)h->hist_next, A = h->opt.activity_bq;
+    for (int l = 0; l <= h->opt.n_labels; ++l) {
+      const double c = (double)cnt[l];
+      double m = 0.0, sg = 0.0;
+      if (c > 0.0) {
+        const double mbar = s1[l] / (N * c);                  // per decay
+        m = mbar * A;
+        if (h->n_batches >= 2) {
+          const double var = std::max(s2[l] / (c * c) - N * mbar * mbar, 0.0) / ((h->n_batches - 1.0) * N);
+          sg = std::sqrt(var) * A;
+        }
+      }
+      if (mean) mean[l] = m;
+      if (sigma_mean) sigma_mean[l] = sg;
+      if (voxels) voxels[l] = cnt[l];
+    }
+    return NM_OK;
+  }
   nm_status st = finalize(h, nullptr, nullptr);
   if (st != NM_OK) return st;
   std::vector<double> out(4 * kLabelSlots);

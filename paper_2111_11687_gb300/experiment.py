@@ -155,7 +155,7 @@ def time_to_target(case, ref, step_decays, max_decays, target, seed):
         while n < max_decays:
             d.run(step_decays, seed)
             n += step_decays
-            mean, _, _, cnt = d.organs()
+            mean, _, _, cnt = d.organs(eps=False)
             err = organ_error(mean, ref, cnt)
             if err.max() <= target:
                 torch.cuda.synchronize()

@@ -250,12 +250,15 @@ def nm_dose_get(h, dose=None, sigma=None, organ_dose=None):
     _check(load().nm_dose_get(h, ptr(dose), ptr(sigma), ptr(organ_dose)))
 
 
-def nm_dose_get_organs(h, n_labels: int):
+def nm_dose_get_organs(h, n_labels: int, eps: bool = True):
+    """(mean, eps_rms, sigma_mean, voxels) per label; eps=False skips Eq. 3 and
+    with it the pass over the voxels (eps_rms is then None)."""
     n = n_labels + 1
-    mean, eps, sig = np.zeros(n), np.zeros(n), np.zeros(n)
+    mean, sig = np.zeros(n), np.zeros(n)
+    e = np.zeros(n) if eps else None
     cnt = np.zeros(n, np.int64)
-    _check(load().nm_dose_get_organs(h, ptr(mean), ptr(eps), ptr(sig), ptr(cnt)))
-    return mean, eps, sig, cnt
+    _check(load().nm_dose_get_organs(h, ptr(mean), ptr(e), ptr(sig), ptr(cnt)))
+    return mean, e, sig, cnt
 
 
 def nm_dose_get_tally(h, tally):
@@ -456,8 +459,8 @@ class Dose:
         nm_dose_get(self.h, dose, sigma, None)
         return dose, sigma
 
-    def organs(self):
-        return nm_dose_get_organs(self.h, self.n_labels)
+    def organs(self, eps: bool = True):
+        return nm_dose_get_organs(self.h, self.n_labels, eps)
 
     def map_organs(self, dose):
         out = np.zeros(self.n_labels + 1)

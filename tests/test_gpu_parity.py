@@ -162,6 +162,7 @@ def test_reduced_phantom_matches_oracle(nm, orc, kn_sampler):
     # The adult phantom's field of view on a 64x64x75 grid of 8x8x12 mm voxels:
     # several alias columns per warp, ragged grid edges, all five materials;
     # Compton angles from the tabulated inverse CDF (0) and from Kahn's sampler (1).
+    from paper_2111_11687_gb300 import inputs
     ph = _phantom((75, 64, 64), (0.8, 0.8, 1.2), seed=21)
     N = 2_000_000
     den, mat, g, sg, (gm, ge, gs, cnt), c, _ = _gpu_phantom_run(nm, ph, N, seed=7, kn_sampler=kn_sampler)
@@ -176,6 +177,18 @@ def test_reduced_phantom_matches_oracle(nm, orc, kn_sampler):
     # Eq. 3 organ uncertainties agree to within their own scatter (both ~ 1/sqrt(N)).
     ok = sel & (cnt >= 100)
     assert np.all(np.abs(ge[ok] / r.organ_eps[ok] - 1) < 0.25)
+    # the organ means and sigmas without Eq. 3 (no pass over the voxels) equal
+    # the full pass's to FP32 rounding of the voxel doses
+    with nm.Dose(den, mat, ph.spacing, nm.Materials(inputs.MATERIAL_Z_OVER_A, inputs.MATERIAL_ZEFF,
+                                                    inputs.PE_COEFF, inputs.PE_EXP),
+                 activity=ph.activity, labels=ph.labels, n_labels=inputs.N_LABELS, activity_bq=inputs.ACTIVITY_BQ,
+                 kn_sampler=kn_sampler) as d:
+        d.run(N, seed=7)
+        fm, fe, fs, fc = d.organs(eps=False)
+        m2, _, s2, c2 = d.organs()
+    assert fe is None and np.array_equal(fc, c2)
+    np.testing.assert_allclose(fm, m2, rtol=2e-6, atol=0)
+    np.testing.assert_allclose(fs, s2, rtol=1e-4, atol=1e-30)
 
 
 def test_full_size_phantom_organs_match_oracle(nm, orc):
