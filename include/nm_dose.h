@@ -190,7 +190,10 @@ nm_status nm_dose_run_batch(nm_dose* const* hs, int32_t n, const uint64_t* n_dec
 /* Eq. 1: dose rate D/N_evts * A(t_s) per voxel (Gy/s) into dose[V], and the
  * batch standard deviation of that mean into sigma[V] (Gy/s); either may be
  * NULL.  organ_dose[n_labels + 1]: Eq. 2 organ means (index = label; index 0
- * is the mean outside all organs), may be NULL.  NM_ERR_STATE before any run. */
+ * is the mean outside all organs), may be NULL.  NM_ERR_STATE before any run
+ * (and, when sigma or organ_dose is asked for, before two batches).  The dose
+ * alone (sigma and organ_dose NULL) takes one streaming pass and is
+ * bit-identical to the dose written with them. */
 nm_status nm_dose_get(nm_dose* h, float* dose, float* sigma, double* organ_dose);
 
 /* Per organ label 0..n_labels (arrays of n_labels + 1 doubles, any may be

@@ -1018,8 +1018,18 @@ nm_status nm_dose_get(nm_dose* h, float* dose, float* sigma, double* organ_dose)
   }
   float* d_out = dose ? (dd ? dose : h->out_dose) : nullptr;
   float* s_out = sigma ? (ds ? sigma : h->out_sigma) : nullptr;
-  nm_status st = finalize(h, d_out, s_out);
-  if (st != NM_OK) return st;
+  if (dose && !sigma && !organ_dose) {
+    // the dose map alone: one streaming pass, no uncertainty or organ sums
+    if (h->hist_next == 0) return fail(NM_ERR_STATE, "no histories simulated yet");
+    FinalizeParams p;
+    memset(&p, 0, sizeof p);
+    p.tsum = h->tsum; p.density = h->density; p.V = h->V; p.n_total = (double)h->hist_next;
+    p.gy_per_unit_vol = h->gy_per_unit_vol(); p.activity_bq = h->opt.activity_bq; p.dose = d_out;
+    NM_CUDA(launch_dose_only(p, h->sms, s), "dose launch");
+  } else {
+    nm_status st = finalize(h, d_out, s_out);
+    if (st != NM_OK) return st;
+  }
   if (dose && !dd) NM_CUDA(cudaMemcpyAsync(dose, d_out, h->V * sizeof(float), cudaMemcpyDeviceToHost, s), "dose copy");
   if (sigma && !ds) NM_CUDA(cudaMemcpyAsync(sigma, s_out, h->V * sizeof(float), cudaMemcpyDeviceToHost, s), "sigma copy");
   if (organ_dose)

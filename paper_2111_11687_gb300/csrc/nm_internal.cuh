@@ -237,6 +237,8 @@ struct FinalizeParams {
   const long long* organ_count;  // [kLabelSlots]
   double* organ_out;        // [4][kLabelSlots]: mean, eps_rms, sigma_mean, count
 };
+// Eq. 1 dose rate only into p.dose (bit-identical to launch_finalize's).
+cudaError_t launch_dose_only(const FinalizeParams& p, int sms, cudaStream_t s);
 cudaError_t launch_finalize(const FinalizeParams& p, cudaStream_t s);
 cudaError_t launch_label_count(const uint8_t* labels, int64_t V, long long* count, cudaStream_t s);
 // History-by-history sigma of the mean dose rate: sigma[v] = sqrt((S2/N -

@@ -248,6 +248,35 @@ cudaError_t launch_merge_stats(const MergeParams& m, int sms, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+namespace {
+
+// Eq. 1 alone (no uncertainty, no organ sums): the dose rate the finalize
+// pass writes, bit for bit (same FP64 mean, same FP32 conversion), streaming
+// 16 bytes per voxel.
+__global__ void dose_only_kernel(const ull* __restrict__ tsum, const float* __restrict__ density, int64_t V,
+                                 double inv_n, float gy_a, float* __restrict__ dose) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += stride) {
+    const ull ti = tsum[v];
+    float d = 0.0f;
+    if (ti) {
+      const double mean = (double)ti * inv_n;
+      d = (float)mean * __fdiv_rn(gy_a, density[v]);
+    }
+    dose[v] = d;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_dose_only(const FinalizeParams& p, int sms, cudaStream_t s) {
+  const int64_t want = (p.V + 255) / 256;
+  const int grid = (int)(want < 8LL * sms ? (want > 0 ? want : 1) : 8LL * sms);
+  dose_only_kernel<<<grid, 256, 0, s>>>(p.tsum, p.density, p.V, 1.0 / p.n_total,
+                                        (float)(p.gy_per_unit_vol * p.activity_bq), p.dose);
+  return cudaGetLastError();
+}
+
 int fold_blocks(int64_t V) { return (int)((V + kFoldTile - 1) / kFoldTile); }
 
 cudaError_t launch_fold(const FoldParams& p, cudaStream_t s) {

@@ -186,6 +186,10 @@ def test_reduced_phantom_matches_oracle(nm, orc, kn_sampler):
         d.run(N, seed=7)
         fm, fe, fs, fc = d.organs(eps=False)
         m2, _, s2, c2 = d.organs()
+        dfull, _ = d.get()
+        donly = np.empty_like(dfull)
+        nm.nm_dose_get(d.h, donly, None, None)
+    np.testing.assert_array_equal(donly, dfull)              # the dose-only pass, bit for bit
     assert fe is None and np.array_equal(fc, c2)
     np.testing.assert_allclose(fm, m2, rtol=2e-6, atol=0)
     np.testing.assert_allclose(fs, s2, rtol=1e-4, atol=1e-30)
