@@ -123,9 +123,10 @@ cudaError_t dalloc(T** p, size_t n) {
 // unit x proportional to P^2 (P + 1/P - x (2 - x)), P = 1 / (1 + k x),
 // k = E / m c^2) at kKnInvE energies log spaced over [e_lo, e_hi]: node j of
 // row i is the x below which a fraction j / kKnInvU of the scatters at energy
-// i lie.  Trapezoid rule on 2^14 panels in FP64, linear between panel edges.
-std::vector<float> nm::kn_inverse_cdf(double e_lo, double e_hi) {
-  constexpr int kPanels = 1 << 14;
+// i lie.  Trapezoid rule on 2^12 panels in FP64 (CDF error ~1e-7), linear
+// between panel edges.
+static std::vector<float> build_kn_inverse_cdf(double e_lo, double e_hi) {
+  constexpr int kPanels = 1 << 12;
   std::vector<float> tab((size_t)kKnInvE * (kKnInvU + 1));
   std::vector<double> cum(kPanels + 1);
   const double dln = (std::log(e_hi) - std::log(e_lo)) / (kKnInvE - 1);
@@ -154,6 +155,17 @@ std::vector<float> nm::kn_inverse_cdf(double e_lo, double e_hi) {
     }
   }
   return tab;
+}
+
+// The table depends only on (cutoff, source energy): built once per pair and
+// kept, so that creating a handle costs no host integration after the first.
+const std::vector<float>& nm::kn_inverse_cdf(double e_lo, double e_hi) {
+  static std::mutex mu;
+  static std::map<std::pair<double, double>, std::vector<float>> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find({e_lo, e_hi});
+  if (it == cache.end()) it = cache.emplace(std::make_pair(e_lo, e_hi), build_kn_inverse_cdf(e_lo, e_hi)).first;
+  return it->second;
 }
 
 struct nm_dose {
@@ -582,7 +594,7 @@ nm_status nm_dose_create(nm_dose** out, const nm_grid* g, const nm_materials* mt
     return bail(cuda_fail(e, "device allocation"));
   if (labels && (e = dalloc(&h->labels, V))) return bail(cuda_fail(e, "device allocation"));
   {
-    const std::vector<float> kt = kn_inverse_cdf(mt->photon_cut_mev, o.photon_mev);
+    const std::vector<float>& kt = kn_inverse_cdf(mt->photon_cut_mev, o.photon_mev);
     h->kn_inv_lo = (float)std::log(mt->photon_cut_mev);
     h->kn_inv_idln = (float)((kKnInvE - 1) / (std::log(o.photon_mev) - std::log(mt->photon_cut_mev)));
     if ((e = dalloc(&h->kn_inv, kt.size())) ||
@@ -1415,7 +1427,7 @@ nm_status nm_check_kn_table(double e_mev, double cut_mev, double e0_mev, int64_t
       !(e_mev >= cut_mev && e_mev <= e0_mev))
     return fail(NM_ERR_ARG, "bad arguments");
   if (n == 0) return NM_OK;
-  const std::vector<float> kt = kn_inverse_cdf(cut_mev, e0_mev);
+  const std::vector<float>& kt = kn_inverse_cdf(cut_mev, e0_mev);
   TransportParams p;
   memset(&p, 0, sizeof p);
   p.key0 = (uint32_t)seed;

@@ -146,8 +146,9 @@ int transport_max_blocks_per_sm(int block, bool warp_agg, bool rayleigh, bool re
 cudaError_t launch_check_philox(const uint4* ctr, const uint2* key, int64_t n, uint4* out,
                                 cudaStream_t s);
 // Klein-Nishina inverse-CDF table [kKnInvE][kKnInvU + 1] of x = 1 - cos(theta)
-// for photons between e_lo and e_hi (MeV), built in FP64 on the host.
-std::vector<float> kn_inverse_cdf(double e_lo, double e_hi);
+// for photons between e_lo and e_hi (MeV), built in FP64 on the host once per
+// pair and kept (thread-safe; the reference stays valid).
+const std::vector<float>& kn_inverse_cdf(double e_lo, double e_hi);
 
 cudaError_t launch_check_wait(long long max_cycles, uint32_t* status, cudaStream_t s);
 cudaError_t launch_check_kn_table(const TransportParams& p, float e, int64_t n, float* out, cudaStream_t s);

@@ -32,8 +32,6 @@ __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {nullptr};
-std::vector<float> g_kn;             // Klein-Nishina table of (g_kn_key[0] cutoff, g_kn_key[1] energy)
-double g_kn_key[2] = {0.0, 0.0};
 
 nm_status fail(nm_status st, const char* fmt, ...) {
   char buf[512];
@@ -186,14 +184,8 @@ extern "C" nm_status nm_dose_tally_noalloc(const nm_grid* g, const nm_materials*
       (e = cudaStreamSynchronize(s)))
     return cuda_fail(e, "physics tables");
   if (o.kn_sampler == 0) {
-    // the Klein-Nishina table of the last (cutoff, energy) pair is kept on the host
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (g_kn_key[0] != mt->photon_cut_mev || g_kn_key[1] != o.photon_mev) {
-      g_kn = kn_inverse_cdf(mt->photon_cut_mev, o.photon_mev);
-      g_kn_key[0] = mt->photon_cut_mev;
-      g_kn_key[1] = o.photon_mev;
-    }
-    if ((e = cudaMemcpyAsync(kn_inv_d, g_kn.data(), g_kn.size() * sizeof(float), cudaMemcpyHostToDevice, s)) ||
+    const std::vector<float>& kt = kn_inverse_cdf(mt->photon_cut_mev, o.photon_mev);
+    if ((e = cudaMemcpyAsync(kn_inv_d, kt.data(), kt.size() * sizeof(float), cudaMemcpyHostToDevice, s)) ||
         (e = cudaStreamSynchronize(s)))
       return cuda_fail(e, "Klein-Nishina table");
     p.kn_inv = kn_inv_d;
