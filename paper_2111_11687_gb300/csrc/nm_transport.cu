@@ -373,19 +373,21 @@ __device__ __forceinline__ ull warp_sum(ull x) {
 // Compton event at energy e: Kahn-sampled angle, new energy and direction, and
 // the local deposit (the electron's energy, or everything below the cutoff).
 template <bool RAYLEIGH>
+// With the tabulated sampler the angle takes the two words (rk, rp) that
+// the flight step which found the event drew but did not use; Kahn's sampler
+// draws its own blocks.
 __device__ __forceinline__ void compton(const TransportParams& p, const float* s_kn,
                                         const float* s_minv, float& e, int32_t& qe, Energy& f,
                                         float& ux, float& uy, float& uz, uint32_t& ctr,
                                         uint32_t stream, uint32_t hlo, uint32_t hhi,
                                         bool& alive, uint32_t& dq, uint32_t& flags,
-                                        unsigned long long* s_cnt) {
+                                        unsigned long long* s_cnt, uint32_t rk, uint32_t rp) {
   uint32_t rphi;
   const float k = e * kInvElectronMassMeV;
   float x;
   if (p.kn_inv) {
-    const uint4 r = draw(ctr, stream, hlo, hhi, p.key0, p.key1);
-    x = kn_table_x(p, e, r.x);
-    rphi = r.y;
+    x = kn_table_x(p, e, rk);
+    rphi = rp;
   } else {
     x = kahn_x(k, ctr, stream, hlo, hhi, p.key0, p.key1, rphi, flags);
   }
@@ -457,8 +459,8 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
   // register counters handed over when a lane changes patient.
   __shared__ unsigned long long s_cnt[MULTI ? kMaxBatchPatients : 1][9];   // [8]: positron units
   __shared__ PatientGeom s_geom[MULTI ? kMaxBatchPatients : 1];
-  extern __shared__ float s_site[];         // [7][blockDim]: decay site, photon A direction, photon B's
-                                            // distance to its region boundary
+  extern __shared__ float s_site[];         // [9][blockDim]: decay site, photon A direction, photon B's
+                                            // distance to its region boundary, a pending Compton's two words
   const int n_pat = MULTI ? p.n_patients : 1;
   for (int i = threadIdx.x; i < kKnTable; i += blockDim.x) {
     s_kn[i] = p.kn[i];
@@ -477,8 +479,8 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
   __syncthreads();
   float* site = s_site + threadIdx.x;
   const int nb = blockDim.x;
-  const HistList hl{reinterpret_cast<uint32_t*>(s_site + 7 * nb) + threadIdx.x,
-                    reinterpret_cast<uint32_t*>(s_site + (7 + kHistVoxels) * nb) + threadIdx.x, nb};
+  const HistList hl{reinterpret_cast<uint32_t*>(s_site + 9 * nb) + threadIdx.x,
+                    reinterpret_cast<uint32_t*>(s_site + (9 + kHistVoxels) * nb) + threadIdx.x, nb};
   int hn = 0;                            // entries in this lane's history list
 
   const uint32_t lane = threadIdx.x & 31u;
@@ -646,8 +648,9 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
       if (waiting && (__popc(waiting) >= (unsigned)p.regroup_compton || flying == 0)) {
         if (pending_c) {
           pending_c = false;
+          const uint32_t* words = reinterpret_cast<const uint32_t*>(site);
           compton<RAYLEIGH>(p, s_kn, out ? s_minv_out : s_minv, e, qe, f, ux, uy, uz, ctr, stream, hlo, hhi,
-                            alive, dq, flags, s_cnt[MULTI ? pi : 0]);
+                            alive, dq, flags, s_cnt[MULTI ? pi : 0], words[7 * nb], words[8 * nb]);
           rem = region_distance(G, out, px, py, pz, ux, uy, uz);
           has = true;
           dv = cv;
@@ -656,8 +659,9 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
     }
     // ---- one Woodcock flight step per live lane -------------------------------
     if (alive && !pending_c && !has) {
-      // A fresh Philox block every step (words x and y): keeping the other two
-      // for the next step saves draws per lane but not per warp, where lanes
+      // A fresh Philox block every step (words x and y; z and w serve the
+      // Compton angle if the step finds one): keeping them for the next step
+      // would save draws per lane but not per warp, where lanes
       // are out of phase, and costs registers.
       const uint4 rr = draw(ctr, stream, hlo, hhi, p.key0, p.key1);
       const uint32_t r0 = rr.x, r1 = rr.y;
@@ -696,9 +700,13 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
           if (REGROUP) {
             pending_c = true;
             cv = v;
+            // the step's two unused words wait in the stash for the Compton pass
+            uint32_t* words = reinterpret_cast<uint32_t*>(site);
+            words[7 * nb] = rr.z;
+            words[8 * nb] = rr.w;
           } else {
             compton<RAYLEIGH>(p, s_kn, out ? s_minv_out : s_minv, e, qe, f, ux, uy, uz, ctr, stream, hlo,
-                              hhi, alive, dq, flags, s_cnt[MULTI ? pi : 0]);
+                              hhi, alive, dq, flags, s_cnt[MULTI ? pi : 0], rr.z, rr.w);
             rem = region_distance(G, out, px, py, pz, ux, uy, uz);
             has = true;
             dv = v;
@@ -817,7 +825,7 @@ __global__ void check_source_kernel(const TransportParams p, uint64_t first, int
 
 // Dynamic shared memory: the site stash, and the history lists when kept.
 size_t transport_smem(int block, bool history) {
-  return ((size_t)7 + (history ? 2 * kHistVoxels : 0)) * block * sizeof(float);
+  return ((size_t)9 + (history ? 2 * kHistVoxels : 0)) * block * sizeof(float);
 }
 
 template <bool A, bool R, bool G, bool M, bool H, bool B = false>
