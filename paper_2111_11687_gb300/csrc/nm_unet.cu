@@ -37,47 +37,55 @@ typedef __nv_bfloat16 bf16;
 // Volumes are [n][d][h][w][c] with d, h, w even; the coarse level is half of each.
 __global__ void avgpool_kernel(const bf16* __restrict__ x, int n, int d, int h, int w, int c,
                                bf16* __restrict__ y) {
-  const int d2 = d >> 1, h2 = h >> 1, w2 = w >> 1;
-  const long long total = (long long)n * d2 * h2 * w2 * c;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int ch = (int)(i % c);
-    long long v = i / c;
-    const int xx = (int)(v % w2); v /= w2;
-    const int yy = (int)(v % h2); v /= h2;
-    const int zz = (int)(v % d2);
-    const int b = (int)(v / d2);
-    float sum = 0.0f;
+  // one thread per output voxel and 8-channel octet (16-byte loads and
+  // store), each channel summed over the 2x2x2 block in the same order;
+  // 32-bit indices (callers keep the element count below 2^32)
+  const unsigned d2 = d >> 1, h2 = h >> 1, w2 = w >> 1, q = c / 8;
+  const unsigned total = (unsigned)n * d2 * h2 * w2 * q;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const unsigned j = i % q, v = i / q;
+    const unsigned xx = v % w2, r = v / w2, yy = r % h2, r2 = r / h2, zz = r2 % d2, b = r2 / d2;
+    float sum[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) sum[e] = 0.0f;
     for (int dz = 0; dz < 2; ++dz)
       for (int dy = 0; dy < 2; ++dy)
-        for (int dx = 0; dx < 2; ++dx)
-          sum += __bfloat162float(x[((((long long)b * d + 2 * zz + dz) * h + 2 * yy + dy) * w + 2 * xx + dx) * c + ch]);
-    y[i] = __float2bfloat16_rn(sum * 0.125f);
+        for (int dx = 0; dx < 2; ++dx) {
+          const size_t src = (((size_t)b * d + 2 * zz + dz) * h + 2 * yy + dy) * w + 2 * xx + dx;
+          const uint4 u = *reinterpret_cast<const uint4*>(x + src * c + j * 8);
+          const __nv_bfloat162* e2 = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float2 f = __bfloat1622float2(e2[e]);
+            sum[2 * e] += f.x;
+            sum[2 * e + 1] += f.y;
+          }
+        }
+    uint4 o;
+    __nv_bfloat162* o2 = reinterpret_cast<__nv_bfloat162*>(&o);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) o2[e] = __floats2bfloat162_rn(sum[2 * e] * 0.125f, sum[2 * e + 1] * 0.125f);
+    *reinterpret_cast<uint4*>(y + (size_t)v * c + j * 8) = o;
   }
 }
 
 // cat[v] = [coarse[parent(v)] (c0 channels) | skip[v] (c1 channels)], 16 bytes at a time.
 __global__ void upsample_concat_kernel(const bf16* __restrict__ coarse, const bf16* __restrict__ skip, int n, int d,
                                        int h, int w, int c0, int c1, bf16* __restrict__ cat) {
-  const int h2 = h >> 1, w2 = w >> 1, c = c0 + c1, q = c / 8;
-  const long long total = (long long)n * d * h * w * q;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int j = (int)(i % q);
-    long long v = i / q;
+  // 32-bit index arithmetic: callers keep n d h w (c0 + c1) / 8 below 2^32
+  const unsigned h2 = h >> 1, w2 = w >> 1, c = c0 + c1, q = c / 8;
+  const unsigned total = (unsigned)n * d * h * w * q;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const unsigned j = i % q, v = i / q;
     uint4 val;
-    if (j * 8 < c0) {
-      long long t = v;
-      const int xx = (int)(t % w); t /= w;
-      const int yy = (int)(t % h); t /= h;
-      const int zz = (int)(t % d);
-      const int b = (int)(t / d);
-      const long long pv = (((long long)b * (d >> 1) + (zz >> 1)) * h2 + (yy >> 1)) * w2 + (xx >> 1);
-      val = *reinterpret_cast<const uint4*>(coarse + pv * c0 + j * 8);
+    if (j * 8 < (unsigned)c0) {
+      const unsigned xx = v % w, r = v / w, yy = r % h, r2 = r / h, zz = r2 % d, b = r2 / d;
+      const unsigned pv = ((b * (d >> 1) + (zz >> 1)) * h2 + (yy >> 1)) * w2 + (xx >> 1);
+      val = *reinterpret_cast<const uint4*>(coarse + (size_t)pv * c0 + j * 8);
     } else {
-      val = *reinterpret_cast<const uint4*>(skip + v * c1 + (j * 8 - c0));
+      val = *reinterpret_cast<const uint4*>(skip + (size_t)v * c1 + (j * 8 - c0));
     }
-    *reinterpret_cast<uint4*>(cat + v * c + j * 8) = val;
+    *reinterpret_cast<uint4*>(cat + (size_t)v * c + j * 8) = val;
   }
 }
 
@@ -292,24 +300,28 @@ __global__ void __launch_bounds__(256) body_stats_kernel(const float* __restrict
                                                          double* __restrict__ part, int* __restrict__ box) {
   __shared__ double sd[256], sa[256], sc[256];
   __shared__ int sb[8][6];
-  double vd = 0.0, va = 0.0, c = 0.0;
+  // per thread FP32 sums of its ~n / 2^18 voxels, then FP64 across threads
+  // (fixed tree); 32-bit coordinates (grids hold fewer than 2^31 voxels)
+  float vd = 0.0f, va = 0.0f;
+  unsigned c = 0;
   int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {-1, -1, -1};
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+  const unsigned unx = (unsigned)nx, uny = (unsigned)ny;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < (unsigned long long)n; i += gridDim.x * blockDim.x) {
     const bool body = density[i] >= 0.1f;
     if (body) {
       vd += dose[i];
       va += act[i];
-      c += 1.0;
+      ++c;
     }
     if (box && (roi ? roi[i] != 0 : body)) {
-      const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long long)nx * ny));
-      lo[0] = min(lo[0], x); lo[1] = min(lo[1], y); lo[2] = min(lo[2], z);
-      hi[0] = max(hi[0], x); hi[1] = max(hi[1], y); hi[2] = max(hi[2], z);
+      const unsigned r = i / unx, x = i - r * unx, y = r % uny, z = r / uny;
+      lo[0] = min(lo[0], (int)x); lo[1] = min(lo[1], (int)y); lo[2] = min(lo[2], (int)z);
+      hi[0] = max(hi[0], (int)x); hi[1] = max(hi[1], (int)y); hi[2] = max(hi[2], (int)z);
     }
   }
   sd[threadIdx.x] = vd;
   sa[threadIdx.x] = va;
-  sc[threadIdx.x] = c;
+  sc[threadIdx.x] = (double)c;
   if (box) {
     const int w = threadIdx.x >> 5;
     for (int a = 0; a < 3; ++a) {
@@ -532,7 +544,7 @@ nm_status forward(nm_denoiser* h, bool fuse_head = false, bool* fused = nullptr)
     CK(conv3d_fwd(h->desc(lb), h->ea[i], nullptr, h->wb + lb.w_off, h->w + lb.b_off, h->eb[i], 1, h->status, s), "conv");
     if (i < L - 1) {
       const long long n = h->vox(i + 1) * h->widths[i];
-      avgpool_kernel<<<grid1d(n), 256, 0, s>>>(h->eb[i], h->B, h->PD >> i, h->PH >> i, h->PW >> i, h->widths[i],
+      avgpool_kernel<<<grid1d(n / 8), 256, 0, s>>>(h->eb[i], h->B, h->PD >> i, h->PH >> i, h->PW >> i, h->widths[i],
                                                h->pool[i]);
       in = h->pool[i];
     }
