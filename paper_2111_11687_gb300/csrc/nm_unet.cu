@@ -89,10 +89,19 @@ __global__ void upsample_concat_kernel(const bf16* __restrict__ coarse, const bf
   }
 }
 
-// g *= (act > 0)
+// g *= (act > 0), 8 elements (16 bytes) per thread; n is a multiple of 8
 __global__ void relu_mask_kernel(bf16* __restrict__ g, const bf16* __restrict__ act, long long n) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    if (!(__bfloat162float(act[i]) > 0.0f)) g[i] = __float2bfloat16_rn(0.0f);
+  const unsigned n8 = (unsigned)(n / 8);
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n8; i += gridDim.x * blockDim.x) {
+    uint4 gv = reinterpret_cast<const uint4*>(g)[i];
+    const uint4 av = reinterpret_cast<const uint4*>(act)[i];
+    bf16* ge = reinterpret_cast<bf16*>(&gv);
+    const bf16* ae = reinterpret_cast<const bf16*>(&av);
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+      if (!(__bfloat162float(ae[e]) > 0.0f)) ge[e] = __float2bfloat16_rn(0.0f);
+    reinterpret_cast<uint4*>(g)[i] = gv;
+  }
 }
 
 // Gradient of a decoder input [n][s]^3[c0 + c1] split into the coarse source
@@ -101,29 +110,23 @@ __global__ void relu_mask_kernel(bf16* __restrict__ g, const bf16* __restrict__ 
 __global__ void split_concat_grad_kernel(const bf16* __restrict__ dx, int n, int d, int h, int w, int c0, int c1,
                                          const bf16* __restrict__ coarse_act, bf16* __restrict__ g_coarse,
                                          bf16* __restrict__ g_skip) {
-  const int d2 = d >> 1, h2 = h >> 1, w2 = w >> 1, c = c0 + c1;
-  const long long nc = (long long)n * d2 * h2 * w2 * c0;
-  const long long ns = (long long)n * d * h * w * c1;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nc + ns;
-       i += (long long)gridDim.x * blockDim.x) {
+  // 32-bit index arithmetic (training volumes hold far fewer than 2^32 elements)
+  const unsigned d2 = d >> 1, h2 = h >> 1, w2 = w >> 1, c = c0 + c1, uc0 = c0, uc1 = c1;
+  const unsigned nc = (unsigned)n * d2 * h2 * w2 * c0;
+  const unsigned ns = (unsigned)n * d * h * w * c1;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < nc + ns; i += gridDim.x * blockDim.x) {
     if (i < nc) {
-      const int ch = (int)(i % c0);
-      long long v = i / c0;
-      const int xx = (int)(v % w2); v /= w2;
-      const int yy = (int)(v % h2); v /= h2;
-      const int zz = (int)(v % d2);
-      const int b = (int)(v / d2);
+      const unsigned ch = i % uc0, v = i / uc0;
+      const unsigned xx = v % w2, r = v / w2, yy = r % h2, r2 = r / h2, zz = r2 % d2, b = r2 / d2;
       float sum = 0.0f;
       for (int dz = 0; dz < 2; ++dz)
         for (int dy = 0; dy < 2; ++dy)
           for (int dx2 = 0; dx2 < 2; ++dx2)
-            sum += __bfloat162float(dx[((((long long)b * d + 2 * zz + dz) * h + 2 * yy + dy) * w + 2 * xx + dx2) * c + ch]);
+            sum += __bfloat162float(dx[((((size_t)b * d + 2 * zz + dz) * h + 2 * yy + dy) * w + 2 * xx + dx2) * c + ch]);
       g_coarse[i] = __float2bfloat16_rn(__bfloat162float(coarse_act[i]) > 0.0f ? sum : 0.0f);
     } else {
-      const long long j = i - nc;
-      const long long vox = j / c1;
-      const int ch = (int)(j % c1);
-      g_skip[j] = dx[vox * c + c0 + ch];
+      const unsigned j = i - nc;
+      g_skip[j] = dx[(size_t)(j / uc1) * c + uc0 + j % uc1];
     }
   }
 }
@@ -132,19 +135,14 @@ __global__ void split_concat_grad_kernel(const bf16* __restrict__ dx, int n, int
 __global__ void encoder_grad_kernel(const bf16* __restrict__ g_coarse, const bf16* __restrict__ g_skip,
                                     const bf16* __restrict__ act, int n, int d, int h, int w, int c,
                                     bf16* __restrict__ g) {
-  const int h2 = h >> 1, w2 = w >> 1;
-  const long long total = (long long)n * d * h * w * c;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int ch = (int)(i % c);
-    long long v = i / c;
-    const int xx = (int)(v % w); v /= w;
-    const int yy = (int)(v % h); v /= h;
-    const int zz = (int)(v % d);
-    const int b = (int)(v / d);
+  // 32-bit index arithmetic (training volumes hold far fewer than 2^32 elements)
+  const unsigned h2 = h >> 1, w2 = w >> 1, uc = c, uw = w, uh = h, ud = d;
+  const unsigned total = (unsigned)n * d * h * w * c;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const unsigned ch = i % uc, v = i / uc;
+    const unsigned xx = v % uw, r = v / uw, yy = r % uh, r2 = r / uh, zz = r2 % ud, b = r2 / ud;
     float t = __bfloat162float(g_skip[i]);
-    t += 0.125f * __bfloat162float(
-                      g_coarse[((((long long)b * (d >> 1) + (zz >> 1)) * h2 + (yy >> 1)) * w2 + (xx >> 1)) * c + ch]);
+    t += 0.125f * __bfloat162float(g_coarse[(((b * (ud >> 1) + (zz >> 1)) * h2 + (yy >> 1)) * w2 + (xx >> 1)) * uc + ch]);
     g[i] = __float2bfloat16_rn(__bfloat162float(act[i]) > 0.0f ? t : 0.0f);
   }
 }
@@ -674,9 +672,9 @@ nm_status backward(nm_denoiser* h) {
     const Layer& lb = lay("d" + std::to_string(i) + "b");
     const Layer& la = lay("d" + std::to_string(i) + "a");
     const long long nb = h->vox(i) * h->widths[i];
-    relu_mask_kernel<<<grid1d(nb), 256, 0, s>>>(g, h->db[i], nb);
+    relu_mask_kernel<<<grid1d(nb / 8), 256, 0, s>>>(g, h->db[i], nb);
     if ((st = conv_back(lb, h->da[i], nullptr, g, h->gA)) != NM_OK) return st;
-    relu_mask_kernel<<<grid1d(nb), 256, 0, s>>>(h->gA, h->da[i], nb);
+    relu_mask_kernel<<<grid1d(nb / 8), 256, 0, s>>>(h->gA, h->da[i], nb);
     const bf16* coarse = i + 1 <= L - 2 ? h->db[i + 1] : h->eb[L - 1];
     if (use_cat(h, la)) {
       // same im2col rows, read from the materialised input
@@ -705,7 +703,7 @@ nm_status backward(nm_denoiser* h) {
       g = h->gC;
     }
     if ((st = conv_back(lb, h->ea[i], nullptr, g, h->gA)) != NM_OK) return st;
-    relu_mask_kernel<<<grid1d(nb), 256, 0, s>>>(h->gA, h->ea[i], nb);
+    relu_mask_kernel<<<grid1d(nb / 8), 256, 0, s>>>(h->gA, h->ea[i], nb);
     const bf16* in = i == 0 ? h->x_in : h->pool[i - 1];
     if ((st = conv_back(la, in, nullptr, h->gA, i > 0 ? h->gB : nullptr)) != NM_OK) return st;
     if (i > 0) {
