@@ -25,7 +25,12 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle into ``oracle/liboracle.so`` (plain g++, -O2)."""
+    """Compile the oracle into ``oracle/liboracle.so`` (plain g++, -O2).  With
+    NM_ORACLE_LIB set (the sanitizer test) that prebuilt library is used."""
+    global _LIB_PATH
+    if os.environ.get("NM_ORACLE_LIB"):
+        _LIB_PATH = os.environ["NM_ORACLE_LIB"]
+        return _LIB_PATH
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         subprocess.check_call(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-o", tmp, _SRC, "-lpthread"])
