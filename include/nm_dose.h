@@ -4,7 +4,8 @@
  *
  * The engine simulates positron-emitter decays drawn from a PET-derived
  * activity map (§2.1: linear PET -> decay PDF), each giving two back-to-back
- * 0.511 MeV photons (§2.1) plus a locally deposited positron kinetic energy,
+ * 0.511 MeV photons (§2.1) plus a locally deposited positron kinetic energy
+ * (or, as an option, a positron drawn from the beta+ spectrum and tracked),
  * transports the photons through a CT-derived density/material voxel grid with
  * Compton (Klein-Nishina) and photoelectric events and a 10 keV photon cutoff
  * (§2.1), tallies deposited energy per voxel, and reports the dose-rate map
