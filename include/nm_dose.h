@@ -450,17 +450,20 @@ nm_status nm_denoise_apply_roi(nm_denoiser* h, const float* dose, const float* d
  * nm_dose_run; bit-identical to a handle's tally after nm_dose_run(n_decays,
  * seed)) into tally[V] (int64 energy units, device memory, overwritten).
  * grid->density, grid->material, activity (decay mode) and tally must be
- * device pointers; materials and opts are host structs as for nm_dose_create;
- * labels and batch statistics are not part of this call.  counters may be NULL;
- * its deposited field is emitted - escaped - killed.
+ * memory of the current device (or managed memory); materials and opts are
+ * host structs, checked as nm_dose_create checks them (NM_ERR_ARG before any
+ * device work); labels and batch statistics are not part of this call; the
+ * beta+ spectrum option is refused.  counters may be NULL; its deposited
+ * field is emitted - escaped - killed.
  *
  * All working memory (packed voxels, alias table and its FP64 scans, physics
  * tables, counters) lives in one fixed device array of 24 MiB that every GPU
  * which loads the library holds until the process exits; grids above 2^18
  * voxels (64^3) are rejected with NM_ERR_ARG.  The call allocates no device
  * memory.  Its first call on a device looks up that array's device address
- * (with the device current) and keeps it; make that first call before any
- * stream capture.  Every call uses the same array, so calls that overlap on
+ * (with the device current) and keeps it, keyed by the device's context, so
+ * a call after cudaDeviceReset looks it up again; make that first call
+ * before any stream capture.  Every call uses the same array, so calls that overlap on
  * the GPU (other streams or threads, the same device) race and must be
  * serialised by the caller; nothing in the array needs clearing between
  * calls.  The call synchronises opts->stream. */

@@ -328,6 +328,48 @@ const char* nm_last_error(void) { return g_err.c_str(); }
 
 void nm::set_error_message(const char* msg) { g_err = msg; }
 
+// Checks shared by every entry point that takes a phantom: grid sizes and
+// spacing, material constants, energies and options.  The positron energy is
+// checked before anything derives fixed-point units from it, so a negative or
+// NaN value never reaches q_units() or the overflow bound.
+nm_status nm::check_problem(const nm_grid* g, const nm_materials* mt, const nm_options& o, const float* activity) {
+  if (!g || !mt) return fail(NM_ERR_ARG, "grid or materials is NULL");
+  if (g->nx <= 0 || g->ny <= 0 || g->nz <= 0) return fail(NM_ERR_ARG, "grid dimensions must be > 0");
+  const int64_t V = (int64_t)g->nx * g->ny * g->nz;
+  if (V >= (int64_t)1 << 31) return fail(NM_ERR_ARG, "grid has %lld voxels; the limit is 2^31 - 1", (long long)V);
+  if (!(g->dx > 0 && g->dy > 0 && g->dz > 0) || !std::isfinite(g->dx) || !std::isfinite(g->dy) ||
+      !std::isfinite(g->dz))
+    return fail(NM_ERR_ARG, "voxel sizes must be finite and > 0");
+  if (!g->density || !g->material) return fail(NM_ERR_ARG, "density or material is NULL");
+  if (mt->n < 1 || mt->n > NM_MAX_MATERIALS || !mt->z_over_a || !mt->zeff)
+    return fail(NM_ERR_ARG, "materials: need 1..%d materials with z_over_a and zeff", NM_MAX_MATERIALS);
+  if (o.source_mode != NM_SOURCE_DECAY && o.source_mode != NM_SOURCE_POINT)
+    return fail(NM_ERR_ARG, "unknown source_mode %d", o.source_mode);
+  if (o.source_mode == NM_SOURCE_DECAY && !activity)
+    return fail(NM_ERR_ARG, "decay mode needs an activity map");
+  if (!(o.photon_mev > mt->photon_cut_mev) || !(mt->photon_cut_mev > 0) || !(o.photon_mev <= 1.0))
+    return fail(NM_ERR_ARG, "need 0 < photon cutoff < photon energy <= 1 MeV");
+  if (!(o.positron_mev >= 0) || o.positron_mev > 1.0) return fail(NM_ERR_ARG, "positron energy must be in [0, 1] MeV");
+  if (!(o.activity_bq >= 0) || !std::isfinite(o.activity_bq)) return fail(NM_ERR_ARG, "activity_bq must be finite and >= 0");
+  if (o.max_steps <= 0) return fail(NM_ERR_ARG, "max_steps must be > 0");
+  if (o.kn_sampler != 0 && o.kn_sampler != 1) return fail(NM_ERR_ARG, "kn_sampler must be 0 (table) or 1 (Kahn)");
+  if (!(o.beta_max_mev >= 0.0 && o.beta_max_mev < 20.0) || o.beta_z < 0 || o.beta_z > 100)
+    return fail(NM_ERR_ARG, "beta_max_mev must be in [0, 20) MeV and beta_z in 0..100");
+  for (int m = 0; m < mt->n; ++m)
+    if (!(mt->z_over_a[m] >= 0) || !(mt->zeff[m] >= 0) || !std::isfinite(mt->z_over_a[m]) ||
+        !std::isfinite(mt->zeff[m]))
+      return fail(NM_ERR_ARG, "material %d: constants must be finite and >= 0", m);
+  if (!(mt->pe_coeff >= 0) || !std::isfinite(mt->pe_coeff) || !std::isfinite(mt->pe_exp) ||
+      !(mt->rayleigh_coeff >= 0) || !std::isfinite(mt->rayleigh_coeff))
+    return fail(NM_ERR_ARG, "photoelectric and Rayleigh constants must be finite and >= 0");
+  if (o.source_mode == NM_SOURCE_POINT) {
+    const float L[3] = {g->nx * g->dx, g->ny * g->dy, g->nz * g->dz};
+    for (int a = 0; a < 3; ++a)
+      if (!(o.point[a] >= 0.0f && o.point[a] < L[a])) return fail(NM_ERR_ARG, "point source outside the grid");
+  }
+  return NM_OK;
+}
+
 extern "C" {
 
 nm_status nm_ct_to_phantom(const int16_t* hu, int64_t n, float* density, uint8_t* material,
@@ -514,39 +556,13 @@ nm_status nm_dose_create(nm_dose** out, const nm_grid* g, const nm_materials* mt
                          const float* activity, const uint8_t* labels, const nm_options* opts) {
   if (!out) return fail(NM_ERR_ARG, "out is NULL");
   *out = nullptr;
-  if (!g || !mt) return fail(NM_ERR_ARG, "grid or materials is NULL");
-  if (g->nx <= 0 || g->ny <= 0 || g->nz <= 0) return fail(NM_ERR_ARG, "grid dimensions must be > 0");
-  const int64_t V = (int64_t)g->nx * g->ny * g->nz;
-  if (V >= (int64_t)1 << 31) return fail(NM_ERR_ARG, "grid has %lld voxels; the limit is 2^31 - 1", (long long)V);
-  if (!(g->dx > 0 && g->dy > 0 && g->dz > 0) || !std::isfinite(g->dx) || !std::isfinite(g->dy) ||
-      !std::isfinite(g->dz))
-    return fail(NM_ERR_ARG, "voxel sizes must be finite and > 0");
-  if (!g->density || !g->material) return fail(NM_ERR_ARG, "density or material is NULL");
-  if (mt->n < 1 || mt->n > NM_MAX_MATERIALS || !mt->z_over_a || !mt->zeff)
-    return fail(NM_ERR_ARG, "materials: need 1..%d materials with z_over_a and zeff", NM_MAX_MATERIALS);
   nm_options o;
   if (opts) o = *opts; else nm_options_default(&o);
-  if (o.source_mode != NM_SOURCE_DECAY && o.source_mode != NM_SOURCE_POINT)
-    return fail(NM_ERR_ARG, "unknown source_mode %d", o.source_mode);
-  if (o.source_mode == NM_SOURCE_DECAY && !activity)
-    return fail(NM_ERR_ARG, "decay mode needs an activity map");
+  const nm_status cp = check_problem(g, mt, o, activity);
+  if (cp != NM_OK) return cp;
   if (o.batches < 2) return fail(NM_ERR_ARG, "batches must be >= 2");
   if (o.n_labels < 0 || o.n_labels > NM_MAX_LABELS) return fail(NM_ERR_ARG, "n_labels must be 0..%d", NM_MAX_LABELS);
-  if (!(o.photon_mev > mt->photon_cut_mev) || !(mt->photon_cut_mev > 0) || !(o.photon_mev <= 1.0))
-    return fail(NM_ERR_ARG, "need 0 < photon cutoff < photon energy <= 1 MeV");
-  if (!(o.positron_mev >= 0) || o.positron_mev > 1.0) return fail(NM_ERR_ARG, "positron energy must be in [0, 1] MeV");
-  if (!(o.activity_bq >= 0) || !std::isfinite(o.activity_bq)) return fail(NM_ERR_ARG, "activity_bq must be finite and >= 0");
-  if (o.max_steps <= 0) return fail(NM_ERR_ARG, "max_steps must be > 0");
-  if (o.kn_sampler != 0 && o.kn_sampler != 1) return fail(NM_ERR_ARG, "kn_sampler must be 0 (table) or 1 (Kahn)");
-  if (!(o.beta_max_mev >= 0.0 && o.beta_max_mev < 20.0) || o.beta_z < 0 || o.beta_z > 100)
-    return fail(NM_ERR_ARG, "beta_max_mev must be in [0, 20) MeV and beta_z in 0..100");
-  for (int m = 0; m < mt->n; ++m)
-    if (!(mt->z_over_a[m] >= 0) || !(mt->zeff[m] >= 0)) return fail(NM_ERR_ARG, "material %d: negative constants", m);
-  if (o.source_mode == NM_SOURCE_POINT) {
-    const float L[3] = {g->nx * g->dx, g->ny * g->dy, g->nz * g->dz};
-    for (int a = 0; a < 3; ++a)
-      if (!(o.point[a] >= 0.0f && o.point[a] < L[a])) return fail(NM_ERR_ARG, "point source outside the grid");
-  }
+  const int64_t V = (int64_t)g->nx * g->ny * g->nz;
 
   nm_dose* h = new nm_dose();
   h->nx = g->nx; h->ny = g->ny; h->nz = g->nz;

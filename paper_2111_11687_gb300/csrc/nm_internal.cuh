@@ -134,6 +134,11 @@ enum CounterSlot {
 // Sets the message that nm_last_error() returns on the calling thread.
 void set_error_message(const char* msg);
 
+// Argument checks shared by nm_dose_create and nm_dose_tally_noalloc (grid,
+// materials, energies, options; nothing about where the pointers live).
+// NM_OK, or NM_ERR_ARG with the message set.
+nm_status check_problem(const nm_grid* g, const nm_materials* mt, const nm_options& o, const float* activity);
+
 // ---- launchers (host side), one translation unit each ---------------------
 // history: history-by-history statistics (needs !warp_agg and !multi); a
 // single-patient launch whose p.g.beta_tab is set runs the beta+ variant

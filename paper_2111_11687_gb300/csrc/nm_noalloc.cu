@@ -16,6 +16,8 @@
 #include <mutex>
 #include <vector>
 
+#include <cuda.h>
+
 #include "nm_internal.cuh"
 
 using namespace nm;
@@ -32,6 +34,7 @@ __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {nullptr};
+CUcontext g_scratch_ctx[kMaxDevices] = {nullptr};
 
 nm_status fail(nm_status st, const char* fmt, ...) {
   char buf[512];
@@ -47,14 +50,17 @@ nm_status cuda_fail(cudaError_t e, const char* what) {
   return fail(NM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-bool on_device(const void* p) {
+// True for device memory of the current device, or managed memory.  Memory
+// of another GPU is refused: this call has no handle that names a device, so
+// every pointer must belong to the one that is current.
+bool on_device(const void* p, int dev) {
   if (!p) return false;
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  return (a.type == cudaMemoryTypeDevice && a.device == dev) || a.type == cudaMemoryTypeManaged;
 }
 
 double kn_sigma(double e_mev) {
@@ -72,18 +78,41 @@ size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // The address of the scratch array on the current device.  Host code cannot
 // use the array's name as a device address, so the address is looked up once
-// per device (with that device current) and kept.
+// per device, with that device current, and kept.  The entry is keyed by the
+// device's current context as well: after cudaDeviceReset the runtime makes a
+// new primary context and loads the module again, possibly at another
+// address, and the lookup is then repeated instead of trusting the old one.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+
+static CUcontext current_context() {
+  static CtxGetCurrentFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      f = nullptr;
+    }
+    return (CtxGetCurrentFn)f;
+  }();
+  CUcontext c = nullptr;
+  if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+  return c;
+}
+
 static nm_status scratch_for_current_device(unsigned char** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   if (dev < 0 || dev >= kMaxDevices) return fail(NM_ERR_ARG, "device %d out of range", dev);
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_ptr[dev]) {
+  const CUcontext ctx = current_context();
+  if (!g_scratch_ptr[dev] || !ctx || ctx != g_scratch_ctx[dev]) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_scratch);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
     g_scratch_ptr[dev] = p;
+    g_scratch_ctx[dev] = current_context();   // the lookup made the context current if it was not
   }
   *out = (unsigned char*)g_scratch_ptr[dev];
   return NM_OK;
@@ -94,31 +123,25 @@ extern "C" nm_status nm_dose_tally_noalloc(const nm_grid* g, const nm_materials*
                                            uint64_t n_decays, uint64_t seed, int64_t* tally,
                                            nm_counters* counters) {
   if (!g || !mt || !tally) return fail(NM_ERR_ARG, "grid, materials and tally are required");
-  if (g->nx <= 0 || g->ny <= 0 || g->nz <= 0) return fail(NM_ERR_ARG, "grid dimensions must be > 0");
+  nm_options o;
+  if (opts) o = *opts; else nm_options_default(&o);
+  // The same checks as nm_dose_create (sizes, spacing, constants, energies),
+  // before anything below derives fixed-point units or table sizes from them.
+  const nm_status cp = check_problem(g, mt, o, activity);
+  if (cp != NM_OK) return cp;
   const int64_t V = (int64_t)g->nx * g->ny * g->nz;
   if (V > kMaxVoxels)
     return fail(NM_ERR_ARG, "grid of %lld voxels exceeds the no-allocation limit of %lld voxels",
                 (long long)V, (long long)kMaxVoxels);
-  if (!(g->dx > 0 && g->dy > 0 && g->dz > 0)) return fail(NM_ERR_ARG, "voxel sizes must be > 0");
-  if (mt->n < 1 || mt->n > NM_MAX_MATERIALS || !mt->z_over_a || !mt->zeff)
-    return fail(NM_ERR_ARG, "materials: need 1..%d materials", NM_MAX_MATERIALS);
-  nm_options o;
-  if (opts) o = *opts; else nm_options_default(&o);
   const bool decay = o.source_mode == NM_SOURCE_DECAY;
-  if (!decay && o.source_mode != NM_SOURCE_POINT) return fail(NM_ERR_ARG, "unknown source_mode");
-  if (!on_device(g->density) || !on_device(g->material) || !on_device(tally) ||
-      (decay && !on_device(activity)))
-    return fail(NM_ERR_ARG, "density, material, tally (and activity in decay mode) must be device pointers");
-  if (!(o.photon_mev > mt->photon_cut_mev) || !(mt->photon_cut_mev > 0) || o.photon_mev > 1.0)
-    return fail(NM_ERR_ARG, "need 0 < photon cutoff < photon energy <= 1 MeV");
-  if (o.max_steps <= 0) return fail(NM_ERR_ARG, "max_steps must be > 0");
+  int cur = 0;
+  cudaError_t ce = cudaGetDevice(&cur);
+  if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
+  if (!on_device(g->density, cur) || !on_device(g->material, cur) || !on_device(tally, cur) ||
+      (decay && !on_device(activity, cur)))
+    return fail(NM_ERR_ARG,
+                "density, material, tally (and activity in decay mode) must be memory of the current device");
   if (o.beta_max_mev != 0.0) return fail(NM_ERR_ARG, "the beta+ spectrum needs a handle (nm_dose_create)");
-  if (o.kn_sampler != 0 && o.kn_sampler != 1) return fail(NM_ERR_ARG, "kn_sampler must be 0 (table) or 1 (Kahn)");
-  if (!decay) {
-    const float L[3] = {g->nx * g->dx, g->ny * g->dy, g->nz * g->dz};
-    for (int a = 0; a < 3; ++a)
-      if (!(o.point[a] >= 0.0f && o.point[a] < L[a])) return fail(NM_ERR_ARG, "point source outside the grid");
-  }
   const int32_t q_e0 = q_units((float)o.photon_mev);
   const int32_t q_pos = decay ? q_units((float)o.positron_mev) : 0;
   const uint64_t per = decay ? 2ull * q_e0 + q_pos : (uint64_t)q_e0;

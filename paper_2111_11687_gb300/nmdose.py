@@ -175,6 +175,33 @@ def ptr(x):
     raise TypeError(type(x))
 
 
+def _dtype(x) -> str:
+    """Element type name of a numpy array or torch tensor ('float32', 'int64', ...)."""
+    return x.dtype.name if isinstance(x, np.ndarray) else str(x.dtype).replace("torch.", "")
+
+
+def _cuda_device(x):
+    """CUDA device index of a torch tensor, or None for host memory."""
+    return x.device.index if getattr(x, "is_cuda", False) else None
+
+
+def _want(name, x, dtype, numel, cuda=None):
+    """Checks an array argument before its pointer crosses the C ABI, which
+    cannot see the size or type of a device buffer: ``dtype`` and ``numel``
+    must match, and with ``cuda`` = a device index the tensor must live on
+    that CUDA device.  Raises ValueError; None passes (the C side decides
+    whether it is allowed)."""
+    if x is None:
+        return
+    if _dtype(x) != dtype:
+        raise ValueError(f"{name}: expected {dtype}, got {_dtype(x)}")
+    n = int(np.prod(x.shape))
+    if n != numel:
+        raise ValueError(f"{name}: expected {numel} elements, got {n}")
+    if cuda is not None and _cuda_device(x) != cuda:
+        raise ValueError(f"{name}: must be a CUDA tensor on device {cuda}")
+
+
 def _stream_ptr(stream):
     if stream is None:
         return None
@@ -219,6 +246,9 @@ class Materials:
 
 def nm_ct_to_phantom(hu, density, material, stream=None):
     n = int(np.prod(hu.shape))
+    _want("hu", hu, "int16", n)
+    _want("density", density, "float32", n)
+    _want("material", material, "uint8", n)
     _check(load().nm_ct_to_phantom(ptr(hu), n, ptr(density), ptr(material), _stream_ptr(stream)))
 
 
@@ -226,6 +256,11 @@ def nm_dose_create(density, material, spacing, materials: Materials, activity=No
                    opts: nm_options | None = None):
     """density/material/activity/labels are [nz, ny, nx] (x fastest); spacing (dx, dy, dz) cm."""
     nz, ny, nx = density.shape
+    V = nx * ny * nz
+    _want("density", density, "float32", V)
+    _want("material", material, "uint8", V)
+    _want("activity", activity, "float32", V)
+    _want("labels", labels, "uint8", V)
     g = nm_grid(nx, ny, nz, float(spacing[0]), float(spacing[1]), float(spacing[2]), ptr(density), ptr(material))
     m = materials.c()
     h = C.c_void_p()
@@ -330,8 +365,21 @@ def nm_check_source(h, first: int, n: int, seed: int):
 def nm_dose_tally_noalloc(density, material, spacing, materials: Materials, tally, n_decays: int, seed: int,
                           activity=None, opts: nm_options | None = None) -> dict:
     """Tally without device allocation; density, material, activity and tally must
-    be device tensors.  Returns the counters."""
+    be CUDA tensors on one device (float32, uint8, float32, int64, all with the
+    grid's voxel count): the C side writes 8 bytes per voxel into tally and
+    cannot check its size.  Returns the counters."""
     nz, ny, nx = density.shape
+    V = nx * ny * nz
+    dev = _cuda_device(density)
+    if dev is None:
+        raise ValueError("density: must be a CUDA tensor")
+    _want("density", density, "float32", V, dev)
+    _want("material", material, "uint8", V, dev)
+    _want("tally", tally, "int64", V, dev)
+    if activity is not None or opts is None or opts.source_mode == NM_SOURCE_DECAY:
+        if activity is None:
+            raise ValueError("activity: decay mode needs an activity map")
+        _want("activity", activity, "float32", V, dev)
     g = nm_grid(nx, ny, nz, float(spacing[0]), float(spacing[1]), float(spacing[2]), ptr(density), ptr(material))
     m = materials.c()
     c = nm_counters()
@@ -452,10 +500,13 @@ class Dose:
         nm_dose_run(self.h, n_decays, seed)
 
     def get(self, dose=None, sigma=None):
+        V = int(np.prod(self.shape))
         if dose is None:
             dose = np.empty(self.shape, np.float32)
         if sigma is None:
             sigma = np.empty(self.shape, np.float32)
+        _want("dose", dose, "float32", V)
+        _want("sigma", sigma, "float32", V)
         nm_dose_get(self.h, dose, sigma, None)
         return dose, sigma
 
@@ -463,6 +514,7 @@ class Dose:
         return nm_dose_get_organs(self.h, self.n_labels, eps)
 
     def map_organs(self, dose):
+        _want("dose", dose, "float32", int(np.prod(self.shape)))
         out = np.zeros(self.n_labels + 1)
         _check(load().nm_dose_map_organs(self.h, ptr(dose), ptr(out)))
         return out
@@ -479,6 +531,7 @@ class Dose:
         """History-by-history sigma of the mean dose rate (Gy/s)."""
         if out is None:
             out = np.empty(self.shape, np.float32)
+        _want("out", out, "float32", int(np.prod(self.shape)))
         _check(load().nm_dose_get_history_sigma(self.h, ptr(out)))
         return out
 

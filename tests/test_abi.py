@@ -67,3 +67,43 @@ def test_product_and_oracle_share_nothing():
             assert not re.search(r"^\s*(import|from)\s+paper_2111_11687_gb300\b", text, flags=re.M), f
             assert "nm_dose.h" not in text and "libnmdose" not in text, f
             assert "nm_internal" not in text, f
+
+
+class _NoCalls:
+    """Stands in for the library: any entry point that is reached fails the test."""
+
+    def __getattr__(self, name):
+        raise AssertionError(f"{name} was called with mismatched buffers")
+
+
+def test_binding_rejects_mismatched_buffers_before_the_call(monkeypatch):
+    """The C side cannot see the size or element type of a device buffer, so
+    the binding checks both before a pointer crosses the ABI."""
+    import numpy as np
+
+    from paper_2111_11687_gb300 import nmdose
+    monkeypatch.setattr(nmdose, "_lib", _NoCalls())
+    shape = (4, 5, 6)
+    den = np.ones(shape, np.float32)
+    mat = np.zeros(shape, np.uint8)
+    act = np.ones(shape, np.float32)
+    m = nmdose.Materials([0.5551], [7.42])
+    bad = [
+        dict(density=den.astype(np.float64)),          # wrong element type
+        dict(material=np.zeros(shape, np.int32)),
+        dict(activity=np.ones((4, 5, 5), np.float32)),  # wrong size
+        dict(labels=np.zeros(shape, np.int8)),
+    ]
+    for kw in bad:
+        args = dict(density=den, material=mat, activity=act, labels=None)
+        args.update(kw)
+        with pytest.raises(ValueError):
+            nmdose.nm_dose_create(args["density"], args["material"], (0.5, 0.5, 0.5), m, args["activity"],
+                                  args["labels"])
+    with pytest.raises(ValueError):
+        nmdose.nm_ct_to_phantom(np.zeros(shape, np.int16), den, np.zeros(shape[:2], np.uint8))
+    # The allocation-free tally writes 8 bytes per voxel into `tally`: host
+    # arrays, an int32 tally or a short one never reach the library.
+    for tally in (np.zeros(shape, np.int64), np.zeros(shape, np.int32), np.zeros(10, np.int64)):
+        with pytest.raises(ValueError):
+            nmdose.nm_dose_tally_noalloc(den, mat, (0.5, 0.5, 0.5), m, tally, 1000, 1, activity=act)
