@@ -106,6 +106,11 @@ def _load():
         lib.orc_sample_dirs.argtypes = [C.c_int64, C.c_uint64, p(d)]
         lib.orc_rotate.restype = None
         lib.orc_rotate.argtypes = [p(d), d, d]
+        lib.orc_sample_thomson_cos.restype = None
+        lib.orc_sample_thomson_cos.argtypes = [C.c_int64, C.c_uint64, p(d)]
+        lib.orc_interactions.restype = None
+        lib.orc_interactions.argtypes = [p(_Materials), C.c_int32, d, d, C.c_int64, C.c_uint64, p(C.c_int32),
+                                         p(d), p(d)]
         lib.orc_beta_density.restype = d
         lib.orc_beta_density.argtypes = [d, d, C.c_int32]
         lib.orc_sample_beta.restype = None
@@ -209,6 +214,26 @@ def sample_dirs(n: int, seed: int) -> np.ndarray:
     out = np.empty((n, 3), np.float64)
     _load().orc_sample_dirs(n, seed, _dp(out))
     return out
+
+
+def sample_thomson_cos(n: int, seed: int) -> np.ndarray:
+    """Rayleigh scattering cosines (Thomson shape) as the transport draws them."""
+    out = np.empty(n, np.float64)
+    _load().orc_sample_thomson_cos(n, seed, _dp(out))
+    return out
+
+
+def interactions(mat: Materials, m: int, rho: float, e_mev: float, n: int, seed: int):
+    """n real interactions at energy e_mev in material m (density rho) drawn by
+    the function the full simulation uses: (type 0 Compton / 1 photoelectric /
+    2 Rayleigh, photon energy after the event, scattering cosine)."""
+    t = np.empty(n, np.int32)
+    e2 = np.empty(n, np.float64)
+    c = np.empty(n, np.float64)
+    cm = mat.c()
+    _load().orc_interactions(C.byref(cm), int(m), float(rho), float(e_mev), n, seed,
+                             t.ctypes.data_as(C.POINTER(C.c_int32)), _dp(e2), _dp(c))
+    return t, e2, c
 
 
 def rotate(d, cos_theta: float, phi: float) -> np.ndarray:

@@ -31,7 +31,10 @@
 //     2002): each history's total deposit per voxel is squared and summed.
 //
 // Functions that no closed form or invariant pins are marked "parity unpinned"
-// at their definition (none at present).
+// at their definition (none at present): the decay-voxel inverse CDF inside
+// orc_run is pinned by a chi-square test of its decay counts, the interaction
+// choice and the Compton kinematics through interact() (which orc_run calls)
+// by binomial and closed-form tests, and the Thomson sampler by chi-square.
 
 #include <algorithm>
 #include <atomic>
@@ -213,6 +216,40 @@ void rotate(double d[3], double c, double phi) {
   for (int i = 0; i < 3; ++i) nd[i] = c * d[i] + s * (cp * e1[i] + sp * e2[i]);
   const double nn = std::sqrt(nd[0] * nd[0] + nd[1] * nd[1] + nd[2] * nd[2]);
   for (int i = 0; i < 3; ++i) d[i] = nd[i] / nn;
+}
+
+// One real interaction of a photon of energy e (MeV) in material m at
+// density rho (§2.1: photoelectric and Compton explicit; Rayleigh optional).
+// The type is drawn in proportion to the linear attenuation coefficients
+// mu_c : mu_pe : mu_R; Compton takes a Klein-Nishina cosine and leaves the
+// photon E' = E / (1 + k (1 - cos)), k = E / m_e c^2 (the recoil electron
+// keeps E - E'); photoelectric absorption leaves nothing; Rayleigh takes a
+// Thomson cosine and keeps E.  Writes the photon's energy after the event
+// (0 when absorbed), the scattering cosine and the azimuth.
+enum { kCompton = 0, kPhoto = 1, kRayleigh = 2 };
+
+int interact(Rng& r, const orc_materials* mt, int m, double rho, double e, double* e2, double* cth,
+             double* phi) {
+  double mc, mp, mr;
+  orc_mu(mt, m, rho, e, &mc, &mp, &mr);
+  const double x = r.u() * (mc + mp + mr);
+  *cth = 1.0;
+  *phi = 0.0;
+  if (x < mc) {
+    *cth = sample_kn_cos(r, e);
+    const double k = e / kElectronMassMeV;
+    *e2 = e / (1.0 + k * (1.0 - *cth));
+    *phi = 2.0 * kPi * r.u();
+    return kCompton;
+  }
+  if (x < mc + mp) {
+    *e2 = 0.0;
+    return kPhoto;
+  }
+  *cth = sample_thomson_cos(r);
+  *phi = 2.0 * kPi * r.u();
+  *e2 = e;
+  return kRayleigh;
 }
 
 struct Grid {
@@ -407,6 +444,27 @@ void orc_sample_dirs(int64_t n, uint64_t seed, double* out) {
 
 void orc_rotate(double* d, double c, double phi) { rotate(d, c, phi); }
 
+// Rayleigh cosines as the transport draws them (Thomson shape by rejection).
+void orc_sample_thomson_cos(int64_t n, uint64_t seed, double* out) {
+  Rng r;
+  r.g.seed(seed);
+  for (int64_t i = 0; i < n; ++i) out[i] = sample_thomson_cos(r);
+}
+
+// n independent real interactions at energy e in material m, density rho,
+// with the function the full simulation uses: type[i] (0 Compton, 1
+// photoelectric, 2 Rayleigh), the photon energy after it e2[i] and the
+// scattering cosine cth[i].
+void orc_interactions(const orc_materials* mt, int32_t m, double rho, double e_mev, int64_t n, uint64_t seed,
+                      int32_t* type, double* e2, double* cth) {
+  Rng r;
+  r.g.seed(seed);
+  for (int64_t i = 0; i < n; ++i) {
+    double phi;
+    type[i] = interact(r, mt, m, rho, e_mev, &e2[i], &cth[i], &phi);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Full simulation.
 // ---------------------------------------------------------------------------
@@ -556,15 +614,10 @@ int orc_run(const orc_problem* pr, int64_t* tally_sum, double* dose_rate, double
       for (int a = 0; a < 3; ++a) p[a] += t_hit * d[a];
       // Keep the collision point inside the collision voxel's grid extent.
       for (int a = 0; a < 3; ++a) p[a] = std::min(std::max(p[a], 0.0), std::nextafter(L[a], 0.0));
-      double mc, mp, mr;
-      orc_mu(&pr->mat, pr->material[v_hit], pr->density[v_hit], e, &mc, &mp, &mr);
-      const double x = r.u() * (mc + mp + mr);
-      if (x < mc) {
+      double e2, cth, phi;
+      const int type = interact(r, &pr->mat, pr->material[v_hit], pr->density[v_hit], e, &e2, &cth, &phi);
+      if (type == kCompton) {
         ++c.compton;
-        const double cth = sample_kn_cos(r, e);
-        const double k = e / kElectronMassMeV;
-        const double e2 = e / (1.0 + k * (1.0 - cth));
-        const double phi = 2.0 * kPi * r.u();
         rotate(d, cth, phi);
         if (e2 < cut) {
           ++c.cutoff;
@@ -573,14 +626,13 @@ int orc_run(const orc_problem* pr, int64_t* tally_sum, double* dose_rate, double
         }
         deposit(v_hit, q_units(e) - q_units(e2), c);
         e = e2;
-      } else if (x < mc + mp) {
+      } else if (type == kPhoto) {
         ++c.photo;
         deposit(v_hit, q_units(e), c);
         return;
       } else {
         ++c.rayleigh;
-        const double cth = sample_thomson_cos(r);
-        rotate(d, cth, 2.0 * kPi * r.u());
+        rotate(d, cth, phi);
       }
     }
   };

@@ -529,3 +529,168 @@ def test_positron_track_escape_and_local_deposit(orc, rho):
         sd = ref.std() * math.sqrt(1.0 / N + 1.0 / ref.size)
         assert abs(got - ref.mean()) < 4.0 * sd + 1e-6, (got, ref.mean(), sd)
     assert esc_pos > 0.0 and centre > 0.03
+
+
+# ---------------------------------------------------------------------------
+# Interactions: the collision step orc_run takes at every real event (type
+# choice, Compton kinematics, Rayleigh angle), called through a test entry of
+# the same function.
+# ---------------------------------------------------------------------------
+NA = 6.02214076e23
+
+
+def _sigma_tr(e):
+    """Klein-Nishina energy-transfer cross section per electron (cm^2), the
+    closed form of Attix (Introduction to Radiological Physics, eq. 7.20)."""
+    k = e / ME
+    a = 1.0 + 2.0 * k
+    lg = math.log(a)
+    return 2 * math.pi * RE * RE * (2 * (1 + k) ** 2 / (k * k * a) - (1 + 3 * k) / a ** 2
+                                    - (1 + k) * (2 * k * k - 2 * k - 1) / (k * k * a * a) - 4 * k * k / (3 * a ** 3)
+                                    - ((1 + k) / k ** 3 - 1 / (2 * k) + 1 / (2 * k ** 3)) * lg)
+
+
+def _dsigma_dt(e, t):
+    """Klein-Nishina spectrum of the recoil electron's kinetic energy T, per
+    electron (cm^2/MeV), with s = T/E (Evans, The Atomic Nucleus, ch. 23)."""
+    k = e / ME
+    s = t / e
+    return math.pi * RE * RE / (ME * k * k) * (2 + s * s / (k * k * (1 - s) ** 2) + s / (1 - s) * (s - 2 / k))
+
+
+def test_energy_transfer_closed_form_matches_quadrature_of_recoil_spectrum():
+    # The two published forms used below agree with each other: E sigma_tr =
+    # integral of T dsigma/dT over 0..T_max.
+    for e in (0.05, 0.2, 0.511):
+        k = e / ME
+        tmax = e * 2 * k / (1 + 2 * k)
+        q = integrate.quad(lambda t: t * _dsigma_dt(e, t), 0, tmax, epsrel=1e-12)[0]
+        assert abs(q / (e * _sigma_tr(e)) - 1) < 1e-9
+
+
+@pytest.mark.parametrize("rayleigh", [0, 1])
+def test_interaction_choice_follows_the_attenuation_coefficients(orc, rayleigh):
+    # Photoelectric and Rayleigh constants chosen so that all three types are
+    # common at 0.2 MeV; the expected fractions come from the definitions of
+    # the coefficients (electron density x sigma_KN, C Zeff^3.8 / E^3,
+    # c_R Zeff^2 / E^2), so swapped thresholds or a dropped term fail.
+    e, za, zeff, rho = 0.2, 0.55, 7.4, 1.3
+    pe_coeff, r_coeff = 6.0e-7, 1.0e-4
+    m = orc.Materials(z_over_a=[za], zeff=[zeff], pe_coeff=pe_coeff, rayleigh_coeff=r_coeff, rayleigh=rayleigh)
+    mu_c = rho * NA * za * orc.sigma_kn(e)
+    mu_pe = rho * pe_coeff * zeff ** 3.8 / e ** 3
+    mu_r = rho * r_coeff * zeff * zeff / e ** 2 if rayleigh else 0.0
+    p = np.array([mu_c, mu_pe, mu_r]) / (mu_c + mu_pe + mu_r)
+    assert p.min() > 0.1 or not rayleigh        # every type is well represented
+    n = 600_000
+    t, e2, c = orc.interactions(m, 0, rho, e, n, seed=31 + rayleigh)
+    h = np.bincount(t, minlength=3)[:3].astype(float)
+    used = p > 0
+    assert h[~used].sum() == 0
+    chi2 = ((h[used] - n * p[used]) ** 2 / (n * p[used])).sum()
+    assert stats.chi2.sf(chi2, used.sum() - 1) > 1e-4, (h / n, p)
+    # after a photoelectric event nothing is left; Rayleigh keeps the energy
+    assert np.all(e2[t == 1] == 0.0)
+    assert np.all(e2[t == 2] == e)
+
+
+@pytest.mark.parametrize("e", [0.511, 0.1])
+def test_compton_energy_transfer_matches_klein_nishina(orc, e):
+    # Compton only: the electron's energy T = E - E' has mean E sigma_tr /
+    # sigma_KN and the recoil spectrum dsigma/dT (published closed forms, not
+    # the oracle's angle formula): E' = E/(1 + k(1 + cos)) or a cosine of the
+    # wrong sign would move both.
+    n = 1_000_000
+    m = water(orc, pe_coeff=0.0)
+    t, e2, c = orc.interactions(m, 0, 1.0, e, n, seed=77)
+    assert np.all(t == 0)
+    T = e - e2
+    k = e / ME
+    tmax = e * 2 * k / (1 + 2 * k)
+    assert T.min() >= 0 and T.max() <= tmax * (1 + 1e-12)
+    mean = e * _sigma_tr(e) / orc.sigma_kn(e)
+    z = (T.mean() - mean) / (T.std() / math.sqrt(n))
+    assert abs(z) < 4.5, (T.mean(), mean, z)
+    edges = np.linspace(0.0, tmax, 41)
+    tot = integrate.quad(lambda x: _dsigma_dt(e, x), 0, tmax, epsrel=1e-12)[0]
+    pb = np.array([integrate.quad(lambda x: _dsigma_dt(e, x), a, b, epsrel=1e-12)[0]
+                   for a, b in zip(edges[:-1], edges[1:])]) / tot
+    hb, _ = np.histogram(T, edges)
+    chi2 = ((hb - n * pb) ** 2 / (n * pb)).sum()
+    assert stats.chi2.sf(chi2, len(pb) - 1) > 1e-4, chi2
+
+
+def test_thomson_sampler_chi2(orc):
+    # Rayleigh angle with the Thomson shape: p(cos) = 3/8 (1 + cos^2).
+    n = 1_000_000
+    s = orc.sample_thomson_cos(n, seed=5)
+    assert s.min() >= -1 and s.max() <= 1
+    edges = np.linspace(-1, 1, 41)
+    a, b = edges[:-1], edges[1:]
+    p = 3.0 / 8.0 * ((b - a) + (b ** 3 - a ** 3) / 3.0)
+    assert abs(p.sum() - 1) < 1e-12
+    h, _ = np.histogram(s, edges)
+    chi2 = ((h - n * p) ** 2 / (n * p)).sum()
+    assert stats.chi2.sf(chi2, len(p) - 1) > 1e-4, chi2
+    # <cos^2> = 2/5 for this shape (isotropic would give 1/3)
+    assert abs((s * s).mean() - 0.4) < 5 * math.sqrt(((s ** 4).mean() - 0.16) / n)
+
+
+# ---------------------------------------------------------------------------
+# Decay sampling inside orc_run (§2.1: linear PET -> decay PDF)
+# ---------------------------------------------------------------------------
+def _uneven_activity(shape, seed):
+    rng = np.random.default_rng(seed)
+    act = np.zeros(int(np.prod(shape)))
+    # active voxels of unequal activity with inactive voxels between them; the
+    # first voxel is inactive and the last one active (ends of the table)
+    idx = np.array([3, 4, 9, 17, 18, 40, 57, 58, 90, act.size - 1])
+    act[idx] = rng.uniform(0.2, 5.0, idx.size)
+    return act.reshape(shape), idx
+
+
+def test_decay_voxels_follow_the_activity_exactly(orc):
+    # No attenuation at all: both photons leave the grid untouched, so each
+    # voxel's tally is exactly (decays in it) x q(positron).  Counts follow
+    # N A_v / sum A (chi-square); inactive voxels get exactly none.
+    shape = (4, 5, 6)
+    act, idx = _uneven_activity(shape, 3)
+    n = 2_000_000
+    q = round(0.25 * 64e6)
+    vac = orc.Materials(z_over_a=[0.0], zeff=[0.0], pe_coeff=0.0)
+    r = orc.run(np.ones(shape), np.zeros(shape, np.uint8), vac, activity=act, spacing=(0.7, 0.9, 1.1),
+                n_hist=n, seed=8, batches=4, positron_mev=0.25)
+    t = r.tally.ravel()
+    assert np.all(t % q == 0)
+    cnt = t // q
+    assert cnt.sum() == n
+    inactive = np.ones(t.size, bool)
+    inactive[idx] = False
+    assert np.all(cnt[inactive] == 0)
+    p = act.ravel()[idx] / act.sum()
+    chi2 = ((cnt[idx] - n * p) ** 2 / (n * p)).sum()
+    assert stats.chi2.sf(chi2, idx.size - 1) > 1e-4, (cnt[idx] / n, p)
+    assert r.counters["compton"] == 0 and r.counters["photo"] == 0
+    assert r.counters["escaped"] == 2 * n * round(0.511 * 64e6)
+
+
+def test_decay_positions_stay_in_the_decay_voxel(orc):
+    # A pure absorber with a free path of ~1e-13 cm: both photons end where the
+    # decay happened, so every voxel keeps (decays in it) x (positron + 2
+    # photons).  Unequal voxel sides catch a position scaled by the wrong side.
+    shape = (4, 5, 6)
+    act, idx = _uneven_activity(shape, 4)
+    n = 500_000
+    per = round(0.25 * 64e6) + 2 * round(0.511 * 64e6)
+    absorber = orc.Materials(z_over_a=[0.0], zeff=[1.0], pe_coeff=1e12)
+    r = orc.run(np.ones(shape), np.zeros(shape, np.uint8), absorber, activity=act, spacing=(0.3, 1.7, 0.8),
+                n_hist=n, seed=9, batches=4, positron_mev=0.25)
+    t = r.tally.ravel()
+    assert np.all(t % per == 0) and t.sum() == n * per
+    cnt = t // per
+    inactive = np.ones(t.size, bool)
+    inactive[idx] = False
+    assert np.all(cnt[inactive] == 0)
+    p = act.ravel()[idx] / act.sum()
+    chi2 = ((cnt[idx] - n * p) ** 2 / (n * p)).sum()
+    assert stats.chi2.sf(chi2, idx.size - 1) > 1e-4
