@@ -314,6 +314,26 @@ nm_status nm_dose_alias_table(nm_dose* h, int64_t* n_active, float* prob, int32_
 nm_status nm_check_source(nm_dose* h, uint64_t first, int64_t n, uint64_t seed, int32_t* voxel,
                           float* pos, float* dir);
 
+/* ---- Ceilings of this GPU for the transport's roofline --------------------
+ *
+ * The paper has no counterpart (it quotes wall times only); these measure
+ * the two hardware rates the transport's memory traffic is bounded by, for
+ * which no published GB300 figure exists.  Each allocates its own buffer,
+ * runs one untimed warm-up launch and one launch timed with CUDA events on a
+ * private stream of the current device, and frees the buffer. */
+
+/* L2 read bandwidth: every thread streams 16-byte words of a bytes-long
+ * buffer (1 MiB .. 2 GiB, a multiple of 16; below the L2's size for an L2
+ * figure) reps times (1..1000) with L2-only loads.  *gb_per_s = bytes * reps
+ * / time / 1e9. */
+nm_status nm_probe_l2_read(int64_t bytes, int32_t reps, double* gb_per_s);
+
+/* Scattered 64-bit atomic adds with unused results (the form of the tally
+ * deposits): about `ops` adds (2^20 .. 2^34) of 1 to slots of a buffer of
+ * `slots` 8-byte words (a power of two, 2^10 .. 2^28) picked by a per-thread
+ * xorshift generator.  *ops_per_s = adds / time. */
+nm_status nm_probe_atomic_add_u64(int64_t slots, int64_t ops, double* ops_per_s);
+
 /* ---- 3x3x3 convolutions of the dose denoiser (tensor cores, BF16 in, FP32 accumulate)
  *
  * The denoiser (a 3D U-Net) is not in the paper; these are its building blocks.

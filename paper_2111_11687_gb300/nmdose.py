@@ -107,6 +107,8 @@ _SIGS = {
     "nm_check_wait_timeout": (C.c_int, [C.c_int64]),
     "nm_dose_alias_table": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.c_void_p, C.c_void_p, C.c_void_p]),
     "nm_check_source": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int64, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "nm_probe_l2_read": (C.c_int, [C.c_int64, C.c_int32, C.POINTER(C.c_double)]),
+    "nm_probe_atomic_add_u64": (C.c_int, [C.c_int64, C.c_int64, C.POINTER(C.c_double)]),
     "nm_conv3d_kpad": (C.c_int32, [C.c_int32]),
     "nm_conv3d_fwd": (C.c_int, [C.POINTER(nm_conv3d_desc), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                 C.c_void_p, C.c_int32, C.c_void_p]),
@@ -387,6 +389,20 @@ def nm_dose_tally_noalloc(density, material, spacing, materials: Materials, tall
                                         C.byref(opts) if opts is not None else None,
                                         int(n_decays), int(seed), ptr(tally), C.byref(c)))
     return c.as_dict()
+
+
+def nm_probe_l2_read(nbytes: int, reps: int) -> float:
+    """L2 read bandwidth (GB/s) over an nbytes buffer read reps times."""
+    out = C.c_double()
+    _check(load().nm_probe_l2_read(int(nbytes), int(reps), C.byref(out)))
+    return out.value
+
+
+def nm_probe_atomic_add_u64(slots: int, ops: int) -> float:
+    """Scattered 64-bit atomic adds per second into `slots` 8-byte words."""
+    out = C.c_double()
+    _check(load().nm_probe_atomic_add_u64(int(slots), int(ops), C.byref(out)))
+    return out.value
 
 
 def nm_conv3d_kpad(cin: int) -> int:
