@@ -116,6 +116,28 @@ typedef struct {
                                 CDF tabulated in FP64 at 64 energies x 257 probabilities
                                 and interpolated (one draw, CDF error < 2e-5); 1 = Kahn's
                                 rejection sampler.  Batched runs need one value for all. */
+  /* Other radionuclides (§4 names 177Lu and 131I as the next ones), decay mode.
+   * The fields below describe one decay; zero (the default) gives 18F as
+   * above.  Not in nm_dose_run_batch or nm_dose_tally_noalloc. */
+  int32_t no_annihilation;   /* 0 (default): the positron of each decay annihilates into two
+                                back-to-back photons of photon_mev (where its track ends);
+                                1: no annihilation photons (a beta- emitter) */
+  int32_t beta_electron;     /* 0 (default): the beta particle is a positron; 1: an electron
+                                (the Fermi function's sign in its spectrum) */
+  int32_t n_beta;            /* 0 (default): one branch with endpoint beta_max_mev; 1..8:
+                                branch b has endpoint beta_endpoint_mev[b] (0 < E < 20 MeV)
+                                and is taken by a fraction beta_intensity[b] (>= 0, positive
+                                sum, normalised) of the decays; the particle is tracked as
+                                described under beta_max_mev.  Host arrays. */
+  const double* beta_endpoint_mev;
+  const double* beta_intensity;
+  int32_t n_gamma;           /* 0..8 gamma lines: line j of gamma_mev[j] MeV (above the
+                                photon cutoff, at most 1 MeV) leaves the decay site (the
+                                nucleus, not the end of the beta track) with probability
+                                gamma_yield[j] (0..1) per decay, independently of the other
+                                lines, in an isotropic direction.  Host arrays. */
+  const double* gamma_mev;
+  const double* gamma_yield;
 } nm_options;
 
 typedef struct {
@@ -212,6 +234,22 @@ nm_status nm_dose_get_organs(nm_dose* h, double* mean, double* eps_rms, double* 
  * unweighted mean of dose[V] (host or device FP32) over each label's voxels,
  * into mean[n_labels + 1] (host or device).  NM_ERR_STATE without labels. */
 nm_status nm_dose_map_organs(nm_dose* h, const float* dose, double* mean);
+
+/* Multi-time-point dosimetry (§4: dose over time from activity measured at
+ * several time points).  act[k] (k < n_points <= 16) are activity maps [V]
+ * (Bq per voxel, host or device) measured at times t_h[k] (hours, 0 <= t_0 <
+ * t_1 < ...); out[V] (host or device) receives each voxel's time-integrated
+ * activity, the number of decays from injection (t = 0) on, in Bq s:
+ *   uptake before t_0 as a linear rise from 0:   A_0 t_0 / 2,
+ *   between time points by the trapezoid rule:   (A_k + A_k+1)(t_k+1 - t_k) / 2,
+ *   after the last point by physical decay only: A_n T_1/2 / ln 2,
+ * times 3600 s/h, in FP64, rounded to FP32 at the end.  *total (may be NULL)
+ * is the FP64 sum over voxels.  Used as a decay map with activity_bq =
+ * *total, nm_dose_get then gives the absorbed dose (Gy) instead of the dose
+ * rate.  NM_ERR_ARG for negative or non-finite activities, times out of
+ * order, or a half-life that is not > 0. */
+nm_status nm_time_integrated_activity(const float* const* act, const double* t_h, int32_t n_points, int64_t V,
+                                      double half_life_h, float* out, double* total, void* stream);
 
 /* Exact cumulative tally, int64 energy units per voxel, into tally[V]. */
 nm_status nm_dose_get_tally(nm_dose* h, int64_t* tally);
@@ -418,6 +456,25 @@ nm_status nm_denoise_layer(const nm_denoiser* h, int32_t i, int32_t* cin, int32_
  * and/or the last step's gradients out (grads); any may be NULL; host or
  * device pointers of nm_denoise_param_count floats. */
 nm_status nm_denoise_params(nm_denoiser* h, float* get, const float* set, float* grads);
+
+/* Adam's state (Kingma and Ba, 2015): the first and second moment estimates
+ * (nm_denoise_param_count floats each, host or device; either may be NULL) and
+ * the number of updates made so far.  After update t with gradient g:
+ * m1 = beta1 m1 + (1 - beta1) g, m2 = beta2 m2 + (1 - beta2) g^2, and
+ * w -= lr (m1 / (1 - beta1^t)) / (sqrt(m2 / (1 - beta2^t)) + eps). */
+nm_status nm_denoise_adam_state(nm_denoiser* h, float* m1, float* m2, int64_t* step);
+
+/* Test support for checking the network layer by layer.  With on != 0 every
+ * later train step keeps, for each convolution layer i (0 .. 2*(2*levels-1)-1,
+ * forward order), three BF16 tensors: kind 0 its input [batch][s]^3[cin]
+ * (s = P >> level; a decoder layer's input as the channel concatenation
+ * [nearest-upsampled coarse | skip]), kind 1 its output activation after
+ * ReLU [batch][s]^3[cout], kind 2 the loss gradient at its output after the
+ * ReLU mask [batch][s]^3[cout].  on = 0 frees them.  nm_denoise_captured
+ * copies one out (host or device; NM_ERR_ARG if `bytes` is too small,
+ * NM_ERR_STATE with capture off). */
+nm_status nm_denoise_capture(nm_denoiser* h, int32_t on);
+nm_status nm_denoise_captured(nm_denoiser* h, int32_t layer, int32_t kind, uint16_t* out, int64_t bytes);
 
 /* One training step on device tensors: x [batch][P]^3[8] BF16, target
  * [batch][P]^3 FP32, weight [batch][P]^3 FP32 or NULL (= 1); loss = mean of

@@ -73,6 +73,14 @@ class _Problem(C.Structure):
         ("activity_bq", C.c_double),
         ("beta_max_mev", C.c_double),
         ("beta_z", C.c_int32),
+        ("annihilation", C.c_int32),
+        ("beta_sign", C.c_int32),
+        ("n_beta", C.c_int32),
+        ("beta_endpoint_mev", C.POINTER(C.c_double)),
+        ("beta_intensity", C.POINTER(C.c_double)),
+        ("n_gamma", C.c_int32),
+        ("gamma_mev", C.POINTER(C.c_double)),
+        ("gamma_yield", C.POINTER(C.c_double)),
     ]
 
 
@@ -113,6 +121,11 @@ def _load():
                                          p(d), p(d)]
         lib.orc_beta_density.restype = d
         lib.orc_beta_density.argtypes = [d, d, C.c_int32]
+        lib.orc_beta_density_signed.restype = d
+        lib.orc_beta_density_signed.argtypes = [d, d, C.c_int32, C.c_int32]
+        lib.orc_sample_beta_branches.restype = None
+        lib.orc_sample_beta_branches.argtypes = [p(d), p(d), C.c_int32, C.c_int32, C.c_int32, C.c_int64, C.c_uint64,
+                                                 p(d)]
         lib.orc_sample_beta.restype = None
         lib.orc_sample_beta.argtypes = [d, C.c_int32, C.c_int64, C.c_uint64, p(d)]
         lib.orc_range_kp.restype = d
@@ -259,6 +272,20 @@ def beta_density(t: float, t_max: float, z: int) -> float:
     return _load().orc_beta_density(float(t), float(t_max), int(z))
 
 
+def beta_density_signed(t: float, t_max: float, z: int, sign: int) -> float:
+    """Unnormalised allowed beta spectrum of a positron (sign +1) or an electron (-1)."""
+    return _load().orc_beta_density_signed(float(t), float(t_max), int(z), int(sign))
+
+
+def sample_beta_branches(endpoints, intensities, z: int, sign: int, n: int, seed: int) -> np.ndarray:
+    """Kinetic energies (MeV) from a spectrum of several branches."""
+    e = np.ascontiguousarray(endpoints, np.float64)
+    i = np.ascontiguousarray(intensities, np.float64)
+    out = np.empty(n)
+    _load().orc_sample_beta_branches(_dp(e), _dp(i), len(e), int(z), int(sign), n, seed, _dp(out))
+    return out
+
+
 def sample_beta(t_max: float, z: int, n: int, seed: int) -> np.ndarray:
     """Positron kinetic energies (MeV) drawn from N(T) by rejection."""
     out = np.empty(n)
@@ -280,14 +307,20 @@ def run(density, material, mat: Materials, *, activity=None, labels=None, n_labe
         spacing=(1.0, 1.0, 1.0), point=None, photon_mev: float = 0.511, positron_mev: float = 0.25,
         n_hist: int, seed: int = 1, batches: int = 10, threads: int = 0, first_history: int = 0,
         activity_bq: float = 1.0, history_sigma: bool = False, beta_max_mev: float = 0.0,
-        beta_z: int = 8) -> Result:
+        beta_z: int = 8, annihilation: bool = True, beta_sign: int = 1, beta_branches=None,
+        gamma_lines=None) -> Result:
     """Run the oracle MC.  Arrays are [nz, ny, nx] (x fastest); spacing (dx, dy, dz) in cm.
 
     ``point`` (cm, xyz) selects point-photon mode (one photon per history);
     otherwise decays are drawn from ``activity``.  ``beta_max_mev`` > 0 draws
     each positron's energy from the allowed beta+ spectrum with that endpoint
     (daughter atomic number ``beta_z``) and follows it along a straight track
-    of Katz-Penfold range; else ``positron_mev`` is deposited at the decay.  ``history_sigma`` also
+    of Katz-Penfold range; else ``positron_mev`` is deposited at the decay.
+    Other radionuclides: ``annihilation=False`` drops the two 0.511 MeV
+    photons (a beta- emitter), ``beta_sign`` -1 makes the tracked particle an
+    electron, ``beta_branches`` [(endpoint MeV, intensity), ...] replaces the
+    single endpoint, ``gamma_lines`` [(MeV, yield per decay), ...] adds photons
+    from the decay site (each line independently).  ``history_sigma`` also
     returns the history-by-history sigma of the mean dose rate (Walters et al.
     2002: the spread of each history's total deposit per voxel).
     """
@@ -320,6 +353,19 @@ def run(density, material, mat: Materials, *, activity=None, labels=None, n_labe
     pr.activity_bq = activity_bq
     pr.beta_max_mev = beta_max_mev
     pr.beta_z = beta_z
+    pr.annihilation = 1 if annihilation else 0
+    pr.beta_sign = -1 if beta_sign < 0 else 1
+    keep = []
+    if beta_branches:
+        be = np.ascontiguousarray([b[0] for b in beta_branches], np.float64)
+        bi = np.ascontiguousarray([b[1] for b in beta_branches], np.float64)
+        keep += [be, bi]
+        pr.n_beta, pr.beta_endpoint_mev, pr.beta_intensity = len(be), _dp(be), _dp(bi)
+    if gamma_lines:
+        ge = np.ascontiguousarray([g[0] for g in gamma_lines], np.float64)
+        gy = np.ascontiguousarray([g[1] for g in gamma_lines], np.float64)
+        keep += [ge, gy]
+        pr.n_gamma, pr.gamma_mev, pr.gamma_yield = len(ge), _dp(ge), _dp(gy)
     tally = np.empty(density.shape, np.int64)
     dr = np.empty(density.shape, np.float64)
     sg = np.empty(density.shape, np.float64)
@@ -340,3 +386,18 @@ def rel_diff_percent(test, ref):
     test = np.asarray(test, np.float64)
     ref = np.asarray(ref, np.float64)
     return 100.0 * (test - ref) / ref
+
+
+def time_integrated_activity(maps, t_h, half_life_h: float) -> np.ndarray:
+    """Decays per voxel from injection on (Bq s), from activity maps (Bq per
+    voxel) measured at increasing times t_h (hours): a linear rise from zero
+    before the first time point, the trapezoid rule between time points, and
+    physical decay alone after the last one (its integral A_n T_1/2 / ln 2).
+    This is the multi-time-point reading of the paper's outlook (§4), written
+    out in FP64."""
+    t = [3600.0 * float(x) for x in t_h]
+    a = [np.asarray(m, np.float64) for m in maps]
+    out = 0.5 * a[0] * t[0]
+    for k in range(1, len(a)):
+        out = out + 0.5 * (a[k - 1] + a[k]) * (t[k] - t[k - 1])
+    return out + a[-1] * (3600.0 * half_life_h / np.log(2.0))

@@ -176,3 +176,15 @@ def unet_init(rng, cin=8, widths=(16, 32, 64, 128), scale=1.0):
         params[name] = (rng.normal(0, std, (co, 27, ci)), rng.normal(0, 0.01, co))
     params["head"] = (rng.normal(0, np.sqrt(1.0 / widths[0]), (1, widths[0])), np.zeros(1))
     return params
+
+
+def adam_step(w, g, m1, m2, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (Kingma and Ba, 2015, Algorithm 1) in FP64: the biased
+    first and second moment estimates, their bias corrections at update t
+    (counted from 1), and the parameter step.  Returns new (w, m1, m2)."""
+    w, g = np.asarray(w, np.float64), np.asarray(g, np.float64)
+    m1 = beta1 * np.asarray(m1, np.float64) + (1.0 - beta1) * g
+    m2 = beta2 * np.asarray(m2, np.float64) + (1.0 - beta2) * g * g
+    m_hat = m1 / (1.0 - beta1 ** t)
+    v_hat = m2 / (1.0 - beta2 ** t)
+    return w - lr * m_hat / (np.sqrt(v_hat) + eps), m1, m2

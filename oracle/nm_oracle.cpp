@@ -314,39 +314,58 @@ bool traverse(const Grid& g, const double p[3], const double dir[3], F&& visit) 
 }
 
 // ---- beta+ spectrum and positron range --------------------------------------
-// Allowed beta+ spectrum (Fermi's theory of beta decay): with T the positron's
-// kinetic energy, E = T + m c^2 its total energy and p c = sqrt(T (T + 2 m c^2)),
+// Allowed beta spectrum (Fermi's theory of beta decay): with T the beta
+// particle's kinetic energy, E = T + m c^2 its total energy and
+// p c = sqrt(T (T + 2 m c^2)),
 //   N(T) dT  proportional to  F(Z, E) p E (T_max - T)^2 dT,   0 < T < T_max,
-// where F is the non-relativistic Fermi function of a positron leaving a
-// daughter of atomic number Z: F = 2 pi eta / (1 - exp(-2 pi eta)) with
-// eta = -Z alpha E / (p c) (repulsion: F < 1, vanishing at low T).
-double beta_density(double t, double t_max, int z) {
+// where F is the non-relativistic Fermi function for a daughter of atomic
+// number Z: F = 2 pi eta / (1 - exp(-2 pi eta)) with eta = -sign Z alpha E /
+// (p c); sign = +1 for a positron (repulsion: F < 1, vanishing at low T),
+// -1 for an electron (attraction: F > 1).
+double beta_density(double t, double t_max, int z, int sign) {
   if (!(t > 0.0) || !(t < t_max)) return 0.0;
   const double e = t + kElectronMassMeV;
   const double pc = std::sqrt(t * (t + 2.0 * kElectronMassMeV));
   double f = 1.0;
   if (z != 0) {
-    const double x = 2.0 * kPi * (-(double)z * kFineStructure * e / pc);
+    const double x = 2.0 * kPi * (-(double)sign * (double)z * kFineStructure * e / pc);
     f = x / (-std::expm1(-x));
   }
   return f * pc * e * (t_max - t) * (t_max - t);
 }
 
-// Rejection sampling of N(T): T uniform on (0, T_max), accepted with
-// probability N(T) / envelope; the envelope is the density's maximum over a
-// fine scan, raised by 2 % (N is smooth, so the scan is within far less).
+// Sampling of a spectrum of one or more branches (endpoint T_b reached by a
+// fraction I_b of the decays): the branch by its share I_b / sum I, then T
+// by rejection from that branch's N(T): uniform on (0, T_b), accepted with
+// probability N(T) / envelope, the envelope being the branch density's
+// maximum over a fine scan raised by 2 % (N is smooth, so the scan is
+// within far less).
 struct BetaSampler {
-  double t_max = 0.0, env = 0.0;
-  int z = 0;
-  BetaSampler(double tm, int zz) : t_max(tm), z(zz) {
+  std::vector<double> t_max, env, cum;
+  int z = 0, sign = 1;
+  BetaSampler(const double* tm, const double* inten, int n, int zz, int sg) : z(zz), sign(sg) {
     constexpr int kScan = 1 << 16;
-    for (int i = 1; i < kScan; ++i) env = std::max(env, beta_density(t_max * i / kScan, t_max, z));
-    env *= 1.02;
+    double tot = 0.0;
+    for (int b = 0; b < n; ++b) tot += inten[b];
+    double acc = 0.0;
+    for (int b = 0; b < n; ++b) {
+      double m = 0.0;
+      for (int i = 1; i < kScan; ++i) m = std::max(m, beta_density(tm[b] * i / kScan, tm[b], z, sign));
+      t_max.push_back(tm[b]);
+      env.push_back(1.02 * m);
+      acc += inten[b] / tot;
+      cum.push_back(acc);
+    }
   }
   double operator()(Rng& r) const {
+    size_t b = 0;
+    if (cum.size() > 1) {
+      const double u = r.u();
+      while (b + 1 < cum.size() && u >= cum[b]) ++b;
+    }
     for (;;) {
-      const double t = r.u() * t_max;
-      if (r.u() * env < beta_density(t, t_max, z)) return t;
+      const double t = r.u() * t_max[b];
+      if (r.u() * env[b] < beta_density(t, t_max[b], z, sign)) return t;
     }
   }
 };
@@ -374,12 +393,29 @@ extern "C" {
 
 // Unnormalised beta+ spectrum N(T) (pinned by the tests through its mean and
 // its statistical-shape limit).
-double orc_beta_density(double t, double t_max, int32_t z) { return beta_density(t, t_max, z); }
+double orc_beta_density(double t, double t_max, int32_t z) { return beta_density(t, t_max, z, 1); }
+
+// The same for a positron (sign +1) or an electron (sign -1).
+double orc_beta_density_signed(double t, double t_max, int32_t z, int32_t sign) {
+  return beta_density(t, t_max, z, sign >= 0 ? 1 : -1);
+}
 
 void orc_sample_beta(double t_max, int32_t z, int64_t n, uint64_t seed, double* out) {
   Rng r;
   r.g.seed(seed);
-  const BetaSampler s(t_max, z);
+  const double one = 1.0;
+  const BetaSampler s(&t_max, &one, 1, z, 1);
+  for (int64_t i = 0; i < n; ++i) out[i] = s(r);
+}
+
+// Kinetic energies from a spectrum of n_b branches (endpoints, intensities)
+// for a positron (sign +1) or an electron (sign -1), as the full simulation
+// draws them.
+void orc_sample_beta_branches(const double* t_max, const double* intensity, int32_t n_b, int32_t z, int32_t sign,
+                              int64_t n, uint64_t seed, double* out) {
+  Rng r;
+  r.g.seed(seed);
+  const BetaSampler s(t_max, intensity, n_b, z, sign >= 0 ? 1 : -1);
   for (int64_t i = 0; i < n; ++i) out[i] = s(r);
 }
 
@@ -489,6 +525,21 @@ typedef struct {
   double activity_bq;           // A(t_s) of Eq. 1
   double beta_max_mev;          // > 0: positron energy from the beta+ spectrum, positron range
   int32_t beta_z;               // daughter's atomic number (Fermi function)
+  // Other radionuclides (decay mode).  annihilation: 1 = the positron of every
+  // decay gives two back-to-back photons of photon_mev (18F); 0 = none (a
+  // beta- emitter).  beta_sign: +1 positron, -1 electron (Fermi function's
+  // sign).  n_beta > 0: the spectrum's branches (endpoint, intensity), in
+  // place of the single beta_max_mev branch.  Gamma lines: line j is emitted
+  // from the decay site with probability gamma_yield[j], independently of
+  // the others, in an isotropic direction.
+  int32_t annihilation;
+  int32_t beta_sign;
+  int32_t n_beta;
+  const double* beta_endpoint_mev;
+  const double* beta_intensity;
+  int32_t n_gamma;
+  const double* gamma_mev;
+  const double* gamma_yield;
 } orc_problem;
 
 typedef struct {
@@ -529,9 +580,13 @@ int orc_run(const orc_problem* pr, int64_t* tally_sum, double* dose_rate, double
       pr->threads > 0 ? pr->threads : std::max(1u, std::thread::hardware_concurrency());
   const int64_t q_photon = q_units(pr->photon_mev);
   const int64_t q_positron = pr->point_mode ? 0 : q_units(pr->positron_mev);
-  const bool beta = !pr->point_mode && pr->beta_max_mev > 0.0;
-  if (beta && !(pr->beta_max_mev < 20.0)) return 1;
-  const BetaSampler beta_sampler(beta ? pr->beta_max_mev : 1.0, pr->beta_z);
+  const bool beta = !pr->point_mode && (pr->beta_max_mev > 0.0 || pr->n_beta > 0);
+  if (beta && pr->n_beta == 0 && !(pr->beta_max_mev < 20.0)) return 1;
+  if (pr->n_gamma < 0 || pr->n_gamma > 64 || pr->n_beta < 0 || pr->n_beta > 16) return 1;
+  const bool annihilate = pr->annihilation != 0;
+  const double one = 1.0, tm1 = beta && pr->n_beta == 0 ? pr->beta_max_mev : 1.0;
+  const BetaSampler beta_sampler(pr->n_beta > 0 ? pr->beta_endpoint_mev : &tm1, pr->n_beta > 0 ? pr->beta_intensity : &one,
+                                 pr->n_beta > 0 ? pr->n_beta : 1, pr->beta_z, pr->beta_sign < 0 ? -1 : 1);
   const double cut = pr->mat.photon_cut_mev;
 
   std::vector<int64_t> tb(V);
@@ -576,12 +631,12 @@ int orc_run(const orc_problem* pr, int64_t* tally_sum, double* dose_rate, double
     c.hist.clear();
   };
 
-  // Transport of one photon from p along dir with energy e (§2.1).
-  auto transport = [&](Rng& r, const double p0[3], const double d0[3], Counters& c) {
+  // Transport of one photon from p along dir with energy e0 (§2.1).
+  auto transport = [&](Rng& r, const double p0[3], const double d0[3], double e0, Counters& c) {
     double p[3] = {p0[0], p0[1], p0[2]};
     double d[3] = {d0[0], d0[1], d0[2]};
-    double e = pr->photon_mev;
-    c.emitted += q_photon;
+    double e = e0;
+    c.emitted += q_units(e0);
     for (;;) {
       // The energy is fixed during a flight: mass attenuation per material once.
       double mass_tot[64];
@@ -637,6 +692,17 @@ int orc_run(const orc_problem* pr, int64_t* tally_sum, double* dose_rate, double
     }
   };
 
+  // Gamma lines of one decay: each emitted with its yield, from the decay
+  // site, in its own isotropic direction.
+  auto emit_gammas = [&](Rng& r, const double site[3], Counters& c) {
+    for (int j = 0; j < pr->n_gamma; ++j) {
+      if (!(r.u() < pr->gamma_yield[j])) continue;
+      double dg[3];
+      marsaglia(r, dg);
+      transport(r, site, dg, pr->gamma_mev[j], c);
+    }
+  };
+
   constexpr uint64_t kChunk = 1024;
   uint64_t hist0 = pr->first_history;
   for (int b = 0; b < B; ++b) {
@@ -660,7 +726,7 @@ int orc_run(const orc_problem* pr, int64_t* tally_sum, double* dose_rate, double
                          (uint32_t)(h_lo >> 32)};
         r.g.seed(ss);
         for (uint64_t h = h_lo; h < h_hi; ++h) {
-          double p[3], d[3];
+          double p[3], d[3], site[3] = {0.0, 0.0, 0.0};
           int64_t v0 = -1;
           if (pr->point_mode) {
             for (int a = 0; a < 3; ++a) p[a] = pr->point[a];
@@ -674,6 +740,7 @@ int orc_run(const orc_problem* pr, int64_t* tally_sum, double* dose_rate, double
             p[0] = (ix + r.u()) * pr->dx;
             p[1] = (iy + r.u()) * pr->dy;
             p[2] = (iz + r.u()) * pr->dz;
+            site[0] = p[0]; site[1] = p[1]; site[2] = p[2];
             if (!beta) {
               // Positron kinetic energy deposited in the decay voxel.
               c.emitted += q_positron;
@@ -703,22 +770,30 @@ int orc_run(const orc_problem* pr, int64_t* tally_sum, double* dose_rate, double
                 return true;
               });
               if (left) {
-                // annihilation outside the grid (vacuum): both photons escape
-                c.emitted += 2 * q_photon;
-                c.escaped += q_units(t_cur) + 2 * q_photon;
+                // the track leaves the grid (vacuum) with what it has left
+                // and, for a positron, annihilates outside: both photons escape
+                c.escaped += q_units(t_cur);
+                if (annihilate) {
+                  c.emitted += 2 * q_photon;
+                  c.escaped += 2 * q_photon;
+                }
+                emit_gammas(r, site, c);
                 if (sigma_history) end_history(c);
                 continue;
               }
               for (int a = 0; a < 3; ++a) p[a] += s_end * dp[a];
             }
           }
-          marsaglia(r, d);
-          transport(r, p, d, c);
-          if (!pr->point_mode) {
-            // Annihilation partner: same point, opposite direction (§2.1).
-            const double d2[3] = {-d[0], -d[1], -d[2]};
-            transport(r, p, d2, c);
+          if (pr->point_mode || annihilate) {
+            marsaglia(r, d);
+            transport(r, p, d, pr->photon_mev, c);
+            if (!pr->point_mode) {
+              // Annihilation partner: same point, opposite direction (§2.1).
+              const double d2[3] = {-d[0], -d[1], -d[2]};
+              transport(r, p, d2, pr->photon_mev, c);
+            }
           }
+          if (!pr->point_mode) emit_gammas(r, site, c);
           if (sigma_history) end_history(c);
         }
       }

@@ -71,23 +71,42 @@ double sigma_kn(double e_mev) {
 // integrated by the trapezoid rule on 2^16 panels; node i of the table is the
 // energy below which a fraction i / kBetaTable of the positrons lie (linear in
 // the cumulative sum between panel edges).
-std::vector<float> beta_inverse_cdf(double t_max, int z) {
+// Several branches (endpoint T_b, fraction I_b of the decays) make the
+// mixture sum_b I_b N_b(T) / integral(N_b); for an electron (sign -1) eta
+// changes sign (attraction: F > 1).
+std::vector<float> beta_inverse_cdf(const double* t_maxs, const double* inten, int n, int z, int sign) {
   constexpr double kAlpha = 7.2973525693e-3;
-  auto density = [&](double t) {
+  auto density = [&](double t, double t_max) {
     if (!(t > 0.0) || !(t < t_max)) return 0.0;
     const double e = t + kElectronMassMeV;
     const double pc = std::sqrt(t * (t + 2.0 * kElectronMassMeV));
     double f = 1.0;
     if (z > 0) {
-      const double x = -2.0 * M_PI * z * kAlpha * e / pc;
+      const double x = -2.0 * M_PI * sign * z * kAlpha * e / pc;
       f = x / -std::expm1(-x);
     }
     return f * pc * e * (t_max - t) * (t_max - t);
   };
+  double t_max = 0.0, itot = 0.0;
+  for (int b = 0; b < n; ++b) {
+    t_max = std::max(t_max, t_maxs[b]);
+    itot += inten[b];
+  }
   constexpr int kPanels = 1 << 16;
-  std::vector<double> cum(kPanels + 1, 0.0);
   const double h = t_max / kPanels;
-  for (int i = 0; i < kPanels; ++i) cum[i + 1] = cum[i] + 0.5 * h * (density(i * h) + density((i + 1) * h));
+  std::vector<double> weight(n);
+  for (int b = 0; b < n; ++b) {
+    double norm = 0.0;
+    for (int i = 0; i < kPanels; ++i) norm += 0.5 * h * (density(i * h, t_maxs[b]) + density((i + 1) * h, t_maxs[b]));
+    weight[b] = norm > 0.0 ? inten[b] / itot / norm : 0.0;
+  }
+  auto mix = [&](double t) {
+    double d = 0.0;
+    for (int b = 0; b < n; ++b) d += weight[b] * density(t, t_maxs[b]);
+    return d;
+  };
+  std::vector<double> cum(kPanels + 1, 0.0);
+  for (int i = 0; i < kPanels; ++i) cum[i + 1] = cum[i] + 0.5 * h * (mix(i * h) + mix((i + 1) * h));
   std::vector<float> tab(kBetaTable + 1);
   tab[0] = 0.0f;
   tab[kBetaTable] = (float)t_max;
@@ -99,6 +118,11 @@ std::vector<float> beta_inverse_cdf(double t_max, int z) {
     tab[i] = (float)((j + w) * h);
   }
   return tab;
+}
+
+std::vector<float> beta_inverse_cdf(double t_max, int z) {
+  const double one = 1.0;
+  return beta_inverse_cdf(&t_max, &one, 1, z, 1);
 }
 
 // Fault injection for the tests: the n-th device allocation from now (through
@@ -198,6 +222,15 @@ struct nm_dose {
   float* kn_inv = nullptr;     // Klein-Nishina inverse CDF [kKnInvE][kKnInvU + 1]
   float kn_inv_lo = 0, kn_inv_idln = 0;
   int32_t q_beta_max = 0;      // q_units(beta endpoint): bound of one positron's energy
+  // another radionuclide: annihilation pair on/off, gamma lines; `nuclide`
+  // selects the transport variant that handles them (and the beta track)
+  int annihilate = 1;
+  int n_gamma = 0;
+  float gamma_e[kMaxGammaLines] = {};
+  int32_t gamma_q[kMaxGammaLines] = {};
+  float gamma_y[kMaxGammaLines] = {};
+  uint64_t q_gamma_sum = 0;
+  bool nuclide = false;
   ull* s2h_lo = nullptr;       // history statistics (history_sigma): 128-bit sums of squares
   ull* s2h_hi = nullptr;
   ull* counters = nullptr;     // kCtrCount
@@ -285,6 +318,13 @@ struct nm_dose {
     p.max_steps = opt.max_steps;
     p.regroup_compton = regroup_lanes;
     p.regroup_refill = regroup_lanes;
+    p.annihilate = annihilate;
+    p.n_gamma = n_gamma;
+    for (int j = 0; j < kMaxGammaLines; ++j) {
+      p.gamma_e[j] = gamma_e[j];
+      p.gamma_q[j] = gamma_q[j];
+      p.gamma_y[j] = gamma_y[j];
+    }
     return p;
   }
 
@@ -295,8 +335,15 @@ struct nm_dose {
   // Upper bound of one history's energy (the exact value with a constant positron).
   uint64_t units_per_history() const {
     return opt.source_mode == NM_SOURCE_DECAY
-               ? 2ull * (uint64_t)q_e0 + (uint64_t)(beta_tab ? q_beta_max : q_pos)
+               ? (annihilate ? 2ull * (uint64_t)q_e0 : 0ull) + (uint64_t)(beta_tab ? q_beta_max : q_pos) + q_gamma_sum
                : (uint64_t)q_e0;
+  }
+  // Energy emitted by the histories so far, from the counters of the
+  // sampled parts (beta particles, gamma lines).
+  int64_t emitted(const ull* v) const {
+    if (opt.source_mode != NM_SOURCE_DECAY) return (int64_t)(hist_next * (uint64_t)q_e0);
+    return (int64_t)(hist_next * (annihilate ? 2ull * (uint64_t)q_e0 : 0ull) +
+                     (beta_tab ? v[kCtrPositronUnits] : hist_next * (uint64_t)q_pos) + v[kCtrGammaUnits]);
   }
 };
 
@@ -320,6 +367,10 @@ void nm_options_default(nm_options* o) {
   o->beta_max_mev = 0.0;
   o->beta_z = 8;
   o->kn_sampler = 0;
+  o->no_annihilation = 0;
+  o->beta_electron = 0;
+  o->n_beta = 0;
+  o->n_gamma = 0;
 }
 
 const char* nm_last_error(void) { return g_err.c_str(); }
@@ -355,6 +406,26 @@ nm_status nm::check_problem(const nm_grid* g, const nm_materials* mt, const nm_o
   if (o.kn_sampler != 0 && o.kn_sampler != 1) return fail(NM_ERR_ARG, "kn_sampler must be 0 (table) or 1 (Kahn)");
   if (!(o.beta_max_mev >= 0.0 && o.beta_max_mev < 20.0) || o.beta_z < 0 || o.beta_z > 100)
     return fail(NM_ERR_ARG, "beta_max_mev must be in [0, 20) MeV and beta_z in 0..100");
+  if ((o.no_annihilation != 0 && o.no_annihilation != 1) || (o.beta_electron != 0 && o.beta_electron != 1))
+    return fail(NM_ERR_ARG, "no_annihilation and beta_electron must be 0 or 1");
+  if (o.n_beta < 0 || o.n_beta > kMaxBetaBranches || (o.n_beta > 0 && (!o.beta_endpoint_mev || !o.beta_intensity)))
+    return fail(NM_ERR_ARG, "n_beta must be 0..%d with endpoint and intensity arrays", kMaxBetaBranches);
+  if (o.n_beta > 0) {
+    double sum = 0.0;
+    for (int b = 0; b < o.n_beta; ++b) {
+      if (!(o.beta_endpoint_mev[b] > 0.0 && o.beta_endpoint_mev[b] < 20.0) || !(o.beta_intensity[b] >= 0.0) ||
+          !std::isfinite(o.beta_intensity[b]))
+        return fail(NM_ERR_ARG, "beta branch %d: endpoint in (0, 20) MeV and intensity finite and >= 0", b);
+      sum += o.beta_intensity[b];
+    }
+    if (!(sum > 0.0)) return fail(NM_ERR_ARG, "beta branch intensities sum to zero");
+  }
+  if (o.n_gamma < 0 || o.n_gamma > kMaxGammaLines || (o.n_gamma > 0 && (!o.gamma_mev || !o.gamma_yield)))
+    return fail(NM_ERR_ARG, "n_gamma must be 0..%d with energy and yield arrays", kMaxGammaLines);
+  for (int j = 0; j < o.n_gamma; ++j)
+    if (!(o.gamma_mev[j] > mt->photon_cut_mev && o.gamma_mev[j] <= 1.0) ||
+        !(o.gamma_yield[j] >= 0.0 && o.gamma_yield[j] <= 1.0))
+      return fail(NM_ERR_ARG, "gamma line %d: energy in (photon cutoff, 1] MeV and yield in [0, 1]", j);
   for (int m = 0; m < mt->n; ++m)
     if (!(mt->z_over_a[m] >= 0) || !(mt->zeff[m] >= 0) || !std::isfinite(mt->z_over_a[m]) ||
         !std::isfinite(mt->zeff[m]))
@@ -424,7 +495,7 @@ static std::map<TuneKey, Shape> g_tune_cache;
 static int grid_for_shape(const nm_dose* h, const Shape& sh, bool multi) {
   const int per_sm = transport_max_blocks_per_sm(sh.block, sh.warp_agg, h->rayleigh, sh.regroup, multi,
                                                  !multi && h->opt.history_sigma != 0,
-                                                 !multi && h->beta_tab != nullptr);
+                                                 !multi && h->nuclide);
   return per_sm * h->sms;
 }
 
@@ -442,7 +513,7 @@ static nm_status autotune(nm_dose* h, Shape sh, bool free_block, bool free_chunk
   const TuneKey key{h->device, h->nx, h->ny, h->nz, h->opt.source_mode, h->rayleigh,
                     (free_block ? 1 : 0) | (free_chunk ? 2 : 0) | (free_agg ? 4 : 0) |
                         (free_regroup ? 8 : 0) | (free_lanes ? 16 : 0) | (h->opt.history_sigma ? 32 : 0) |
-                        (h->beta_tab ? 64 : 0),
+                        (h->nuclide ? 64 : 0),
                     free_block ? 0 : sh.block, free_chunk ? 0 : sh.chunk, free_agg ? 0 : sh.warp_agg,
                     free_regroup ? 0 : sh.regroup, free_lanes ? 0 : sh.lanes};
   {
@@ -537,7 +608,7 @@ static nm_status choose_shape(nm_dose* h) {
   // A point source concentrates deposits near the source, where lanes of a
   // warp often hit the same voxel; a spread-out source rarely does.
   sh.warp_agg = o.warp_aggregate >= 0 ? (o.warp_aggregate != 0) : (o.source_mode == NM_SOURCE_POINT);
-  if (o.history_sigma || h->beta_tab) {
+  if (o.history_sigma || h->nuclide) {
     // per-history totals and positron tracks deposit lane by lane
     if (o.warp_aggregate > 0) return fail(NM_ERR_ARG, "history_sigma and the beta+ spectrum need warp_aggregate = 0");
     sh.warp_agg = 0;
@@ -546,7 +617,7 @@ static nm_status choose_shape(nm_dose* h) {
   sh.lanes = o.regroup_lanes > 0 ? o.regroup_lanes : 12;
   apply_shape(h, sh);
   if (h->grid <= 0) return fail(NM_ERR_ARG, "transport kernel cannot launch with %d threads", h->block);
-  const bool fb = o.block_threads <= 0, fc = o.chunk <= 0, fa = o.warp_aggregate < 0 && !o.history_sigma && !h->beta_tab,
+  const bool fb = o.block_threads <= 0, fc = o.chunk <= 0, fa = o.warp_aggregate < 0 && !o.history_sigma && !h->nuclide,
              fr = o.regroup < 0, fl = o.regroup_lanes <= 0 && sh.regroup;
   if (fb || fc || fa || fr || fl) return autotune(h, sh, fb, fc, fa, fr, fl);
   return NM_OK;
@@ -576,6 +647,21 @@ nm_status nm_dose_create(nm_dose** out, const nm_grid* g, const nm_materials* mt
   h->e0 = (float)o.photon_mev;
   h->q_e0 = q_units(h->e0);
   h->q_pos = o.source_mode == NM_SOURCE_DECAY ? q_units((float)o.positron_mev) : 0;
+  // The tables span the highest photon energy: the annihilation photons' or
+  // a gamma line's.
+  double e_top = o.photon_mev;
+  if (o.source_mode == NM_SOURCE_DECAY) {
+    h->annihilate = o.no_annihilation ? 0 : 1;
+    h->n_gamma = o.n_gamma;
+    for (int j = 0; j < o.n_gamma; ++j) {
+      h->gamma_e[j] = (float)o.gamma_mev[j];
+      h->gamma_q[j] = q_units(h->gamma_e[j]);
+      h->gamma_y[j] = (float)o.gamma_yield[j];
+      h->q_gamma_sum += (uint64_t)h->gamma_q[j];
+      e_top = std::max(e_top, o.gamma_mev[j]);
+    }
+    h->nuclide = o.beta_max_mev > 0.0 || o.n_beta > 0 || o.n_gamma > 0 || o.no_annihilation;
+  }
   auto bail = [&](nm_status st) { delete h; return st; };
 
   cudaError_t e;
@@ -585,7 +671,7 @@ nm_status nm_dose_create(nm_dose** out, const nm_grid* g, const nm_materials* mt
   cudaStream_t s = h->stream;
 
   // Physics tables: N_A sigma_KN(E) on a log-energy grid (FP64 -> FP32).
-  const double e_lo = 0.5 * mt->photon_cut_mev, e_hi = 1.05 * o.photon_mev;
+  const double e_lo = 0.5 * mt->photon_cut_mev, e_hi = 1.05 * e_top;
   const double dln = (std::log(e_hi) - std::log(e_lo)) / (kKnTable - 1);
   h->ln_e_lo = (float)std::log(e_lo);
   h->inv_dln = (float)(1.0 / dln);
@@ -610,18 +696,27 @@ nm_status nm_dose_create(nm_dose** out, const nm_grid* g, const nm_materials* mt
     return bail(cuda_fail(e, "device allocation"));
   if (labels && (e = dalloc(&h->labels, V))) return bail(cuda_fail(e, "device allocation"));
   {
-    const std::vector<float>& kt = kn_inverse_cdf(mt->photon_cut_mev, o.photon_mev);
+    const std::vector<float>& kt = kn_inverse_cdf(mt->photon_cut_mev, e_top);
     h->kn_inv_lo = (float)std::log(mt->photon_cut_mev);
-    h->kn_inv_idln = (float)((kKnInvE - 1) / (std::log(o.photon_mev) - std::log(mt->photon_cut_mev)));
+    h->kn_inv_idln = (float)((kKnInvE - 1) / (std::log(e_top) - std::log(mt->photon_cut_mev)));
     if ((e = dalloc(&h->kn_inv, kt.size())) ||
         (e = cudaMemcpyAsync(h->kn_inv, kt.data(), kt.size() * sizeof(float), cudaMemcpyHostToDevice, s)) ||
         (e = cudaStreamSynchronize(s)))
       return bail(cuda_fail(e, "Klein-Nishina table"));
   }
   std::vector<float> beta;
-  if (o.source_mode == NM_SOURCE_DECAY && o.beta_max_mev > 0.0) {
-    beta = beta_inverse_cdf(o.beta_max_mev, o.beta_z);
-    h->q_beta_max = q_units((float)o.beta_max_mev);
+  if (o.source_mode == NM_SOURCE_DECAY && (o.beta_max_mev > 0.0 || o.n_beta > 0)) {
+    const double one = 1.0;
+    const int sign = o.beta_electron ? -1 : 1;
+    if (o.n_beta > 0) {
+      beta = beta_inverse_cdf(o.beta_endpoint_mev, o.beta_intensity, o.n_beta, o.beta_z, sign);
+      double tm = 0.0;
+      for (int b = 0; b < o.n_beta; ++b) tm = std::max(tm, o.beta_endpoint_mev[b]);
+      h->q_beta_max = q_units((float)tm);
+    } else {
+      beta = beta_inverse_cdf(&o.beta_max_mev, &one, 1, o.beta_z, sign);
+      h->q_beta_max = q_units((float)o.beta_max_mev);
+    }
     if ((e = dalloc(&h->beta_tab, kBetaTable + 1)) ||
         (e = cudaMemcpyAsync(h->beta_tab, beta.data(), (kBetaTable + 1) * sizeof(float), cudaMemcpyHostToDevice, s)))
       return bail(cuda_fail(e, "beta table"));
@@ -815,7 +910,7 @@ extern "C" nm_status nm_dose_run_batch(nm_dose* const* hs, int32_t n, const uint
     if (!hs[i]) return fail(NM_ERR_ARG, "handle %d is NULL", i);
     for (int j = 0; j < i; ++j)
       if (hs[j] == hs[i]) return fail(NM_ERR_ARG, "handle %d appears twice", i);
-    if (hs[i]->opt.history_sigma || hs[i]->beta_tab)
+    if (hs[i]->opt.history_sigma || hs[i]->nuclide)
       return fail(NM_ERR_ARG, "handle %d: history_sigma and beta+ spectrum handles run with nm_dose_run, not in batches",
                   i);
     if (!same_physics(hs[0], hs[i]))
@@ -1151,6 +1246,75 @@ nm_status nm_dose_map_organs(nm_dose* h, const float* dose, double* mean) {
   return NM_OK;
 }
 
+nm_status nm_time_integrated_activity(const float* const* act, const double* t_h, int32_t n, int64_t V,
+                                      double half_life_h, float* out, double* total, void* stream) {
+  if (!act || !t_h || !out || n < 1 || n > 16 || V < 1 || V >= ((int64_t)1 << 31))
+    return fail(NM_ERR_ARG, "nm_time_integrated_activity: 1..16 maps of 1..2^31-1 voxels and an output");
+  if (!(half_life_h > 0.0) || !std::isfinite(half_life_h))
+    return fail(NM_ERR_ARG, "nm_time_integrated_activity: the half-life must be finite and > 0");
+  double t_s[16];
+  for (int k = 0; k < n; ++k) {
+    if (!act[k]) return fail(NM_ERR_ARG, "nm_time_integrated_activity: map %d is NULL", k);
+    if (!std::isfinite(t_h[k]) || !(t_h[k] >= 0.0) || (k > 0 && !(t_h[k] > t_h[k - 1])))
+      return fail(NM_ERR_ARG, "nm_time_integrated_activity: times must be finite, >= 0 and increasing");
+    t_s[k] = 3600.0 * t_h[k];
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  NM_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+  NM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
+  const int blocks = (int)std::min<int64_t>((V + 255) / 256, (int64_t)sms * 8);
+  // host maps and a host output go through device copies
+  std::vector<float*> staged;
+  auto cleanup = [&]() {
+    for (float* q : staged) cudaFree(q);
+  };
+  const float* dmaps[16];
+  for (int k = 0; k < n; ++k) {
+    if (is_device_ptr(act[k])) {
+      dmaps[k] = act[k];
+    } else {
+      float* d = nullptr;
+      cudaError_t e = dalloc(&d, V);
+      if (!e) {
+        staged.push_back(d);
+        e = cudaMemcpyAsync(d, act[k], V * sizeof(float), cudaMemcpyHostToDevice, s);
+      }
+      if (e) { cleanup(); return cuda_fail(e, "nm_time_integrated_activity: staging"); }
+      dmaps[k] = d;
+    }
+  }
+  float* dout = out;
+  if (!is_device_ptr(out)) {
+    float* d = nullptr;
+    cudaError_t e = dalloc(&d, V);
+    if (e) { cleanup(); return cuda_fail(e, "nm_time_integrated_activity: staging"); }
+    staged.push_back(d);
+    dout = d;
+  }
+  double* sums = nullptr;
+  cudaError_t e = dalloc(&sums, (size_t)blocks + 1);   // + the status word
+  if (e) { cleanup(); return cuda_fail(e, "nm_time_integrated_activity: sums"); }
+  std::vector<double> hs(blocks);
+  uint32_t st = 0;
+  e = cudaMemsetAsync(sums + blocks, 0, sizeof(double), s);
+  if (!e) e = launch_time_integral(dmaps, t_s, n, V, 3600.0 * half_life_h / std::log(2.0), dout, sums, blocks, s);
+  if (!e) e = cudaMemcpyAsync(hs.data(), sums, blocks * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (!e) e = cudaMemcpyAsync(&st, sums + blocks, sizeof st, cudaMemcpyDeviceToHost, s);
+  if (!e && dout != out) e = cudaMemcpyAsync(out, dout, V * sizeof(float), cudaMemcpyDeviceToHost, s);
+  if (!e) e = cudaStreamSynchronize(s);
+  cudaFree(sums);
+  cleanup();
+  if (e) return cuda_fail(e, "nm_time_integrated_activity");
+  if (st & NM_DEV_BAD_ACTIVITY) return fail(NM_ERR_ARG, "nm_time_integrated_activity: activities must be finite and >= 0");
+  if (total) {
+    double acc = 0.0;
+    for (double x : hs) acc += x;
+    *total = acc;
+  }
+  return NM_OK;
+}
+
 nm_status nm_dose_get_tally(nm_dose* h, int64_t* tally) {
   if (!h || !tally) return fail(NM_ERR_ARG, "bad arguments");
   NM_CUDA(cudaMemcpyAsync(tally, h->tsum, h->V * sizeof(int64_t), cudaMemcpyDefault, h->stream), "tally copy");
@@ -1334,8 +1498,7 @@ nm_status nm_dose_counters(nm_dose* h, nm_counters* c) {
   memset(c, 0, sizeof *c);
   c->histories = h->hist_next;
   c->batches = h->n_batches;
-  c->emitted = h->beta_tab ? (int64_t)(h->hist_next * 2ull * (uint64_t)h->q_e0 + v[kCtrPositronUnits])
-                           : (int64_t)(h->hist_next * h->units_per_history());
+  c->emitted = h->emitted(v);
   c->deposited = (int64_t)v[kCtrDepositedUnits];
   c->escaped = (int64_t)v[kCtrEscapedUnits];
   c->killed = (int64_t)v[kCtrKilledUnits];

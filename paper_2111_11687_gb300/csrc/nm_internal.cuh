@@ -54,8 +54,14 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 // Uniform float in the open interval (0, 1) from 23 random bits.
 __device__ __forceinline__ float u01(uint32_t r) { return ((float)(r >> 9) + 0.5f) * 0x1p-23f; }
 
-// Random-stream ids inside one history.
-enum : uint32_t { kStreamSource = 0, kStreamPhotonA = 1, kStreamPhotonB = 2, kStreamPositron = 3 };
+// Random-stream ids inside one history: gamma line j flies on stream
+// kStreamGamma0 + j after the emission draws of kStreamGammaSelect.
+enum : uint32_t {
+  kStreamSource = 0, kStreamPhotonA = 1, kStreamPhotonB = 2, kStreamPositron = 3, kStreamGammaSelect = 4,
+  kStreamGamma0 = 8
+};
+constexpr int kMaxGammaLines = 8;
+constexpr int kMaxBetaBranches = 8;
 constexpr int kBetaTable = 1024;   // inverse-CDF nodes of the beta+ spectrum (+1)
 // Klein-Nishina inverse CDF of x = 1 - cos(theta): kKnInvE energies (log
 // spaced from the photon cutoff to the source energy) x kKnInvU + 1
@@ -120,6 +126,14 @@ struct TransportParams {
   // 128-bit sum over histories of each history's squared total deposit.
   ull* s2h_lo;
   ull* s2h_hi;
+  // Decay of another radionuclide (single-patient launches, the nuclide
+  // variant): whether the annihilation pair is emitted, and the gamma lines
+  // (energy, fixed-point energy, emission probability per decay).
+  int annihilate;
+  int n_gamma;
+  float gamma_e[kMaxGammaLines];
+  int32_t gamma_q[kMaxGammaLines];
+  float gamma_y[kMaxGammaLines];
 };
 
 constexpr int kHistVoxels = 16;     // voxels a lane keeps per history (history statistics)
@@ -128,7 +142,8 @@ constexpr int kMaxBatchPatients = 64;
 
 enum CounterSlot {
   kCtrSteps = 0, kCtrCompton, kCtrPhoto, kCtrRayleigh, kCtrCutoff, kCtrEscapes,
-  kCtrEscapedUnits, kCtrKilledUnits, kCtrDepositedUnits, kCtrHistSplits, kCtrPositronUnits, kCtrCount
+  kCtrEscapedUnits, kCtrKilledUnits, kCtrDepositedUnits, kCtrHistSplits, kCtrPositronUnits, kCtrGammaUnits,
+  kCtrCount
 };
 
 // Sets the message that nm_last_error() returns on the calling thread.
@@ -146,6 +161,13 @@ nm_status check_problem(const nm_grid* g, const nm_materials* mt, const nm_optio
 cudaError_t launch_transport(const TransportParams& p, int grid, int block, bool warp_agg,
                              bool rayleigh, bool regroup, cudaStream_t s, bool multi = false,
                              bool history = false);
+// True for a single-patient launch that needs the nuclide variant (a beta
+// spectrum, gamma lines or no annihilation pair).
+bool nuclide_launch(const TransportParams& p);
+// Per-voxel time-integrated activity (trapezoid between time points, linear
+// uptake before the first, physical decay after the last), FP64 per voxel.
+cudaError_t launch_time_integral(const float* const* act, const double* t_s, int n, int64_t V, double tail_s,
+                                 float* out, double* block_sums, int blocks, cudaStream_t s);
 int transport_max_blocks_per_sm(int block, bool warp_agg, bool rayleigh, bool regroup,
                                 bool multi = false, bool history = false, bool beta = false);
 cudaError_t launch_check_philox(const uint4* ctr, const uint2* key, int64_t n, uint4* out,

@@ -141,7 +141,8 @@ extern "C" nm_status nm_dose_tally_noalloc(const nm_grid* g, const nm_materials*
       (decay && !on_device(activity, cur)))
     return fail(NM_ERR_ARG,
                 "density, material, tally (and activity in decay mode) must be memory of the current device");
-  if (o.beta_max_mev != 0.0) return fail(NM_ERR_ARG, "the beta+ spectrum needs a handle (nm_dose_create)");
+  if (o.beta_max_mev != 0.0 || o.n_beta != 0 || o.n_gamma != 0 || o.no_annihilation != 0)
+    return fail(NM_ERR_ARG, "beta spectra, gamma lines and other radionuclides need a handle (nm_dose_create)");
   const int32_t q_e0 = q_units((float)o.photon_mev);
   const int32_t q_pos = decay ? q_units((float)o.positron_mev) : 0;
   const uint64_t per = decay ? 2ull * q_e0 + q_pos : (uint64_t)q_e0;
@@ -238,6 +239,7 @@ extern "C" nm_status nm_dose_tally_noalloc(const nm_grid* g, const nm_materials*
   p.g.source_mode = o.source_mode;
   p.g.px = o.point[0] / g->dx; p.g.py = o.point[1] / g->dy; p.g.pz = o.point[2] / g->dz;
   p.g.q_positron = q_pos;
+  p.annihilate = 1;
   p.status = status;
   p.kn = kn_d;
   p.minv = minv_d;

@@ -298,3 +298,71 @@ cudaError_t launch_finalize(const FinalizeParams& p, cudaStream_t s) {
 }
 
 }  // namespace nm
+
+// ---------------------------------------------------------------------------
+// Multi-time-point dosimetry: time-integrated activity per voxel.
+// ---------------------------------------------------------------------------
+namespace nm {
+namespace {
+
+constexpr int kMaxTimePoints = 16;
+
+struct TimeIntegralArgs {
+  const float* act[kMaxTimePoints];   // activity maps (Bq per voxel)
+  double t[kMaxTimePoints];           // their times, seconds
+  int n;
+};
+
+// Per voxel, in FP64: A_0 t_0 / 2 (linear uptake from zero), the trapezoids
+// between time points, and A_n / lambda after the last one (physical decay,
+// tail_s = 1 / lambda); the FP64 sum of a CTA's results goes to
+// block_sums[block] (fixed tree).  A negative or non-finite activity sets
+// NM_DEV_BAD_ACTIVITY.
+__global__ void __launch_bounds__(256) time_integral_kernel(const TimeIntegralArgs a, int64_t V, double tail_s,
+                                                            float* __restrict__ out, double* __restrict__ block_sums,
+                                                            uint32_t* __restrict__ status) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  bool bad = false;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
+    double prev = (double)a.act[0][v];
+    bad |= !(prev >= 0.0) || isinf(prev);
+    double s = 0.5 * prev * a.t[0];
+    for (int k = 1; k < a.n; ++k) {
+      const double cur = (double)a.act[k][v];
+      bad |= !(cur >= 0.0) || isinf(cur);
+      s += 0.5 * (prev + cur) * (a.t[k] - a.t[k - 1]);
+      prev = cur;
+    }
+    s += prev * tail_s;
+    out[v] = (float)s;
+    acc += s;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = red[0];
+  if (bad) atomicOr(status, (uint32_t)NM_DEV_BAD_ACTIVITY);
+}
+
+}  // namespace
+
+cudaError_t launch_time_integral(const float* const* act, const double* t_s, int n, int64_t V, double tail_s,
+                                 float* out, double* block_sums, int blocks, cudaStream_t s) {
+  if (n < 1 || n > kMaxTimePoints || blocks < 1) return cudaErrorInvalidValue;
+  TimeIntegralArgs a;
+  for (int k = 0; k < kMaxTimePoints; ++k) {
+    a.act[k] = k < n ? act[k] : nullptr;
+    a.t[k] = k < n ? t_s[k] : 0.0;
+  }
+  a.n = n;
+  // the status word follows the block sums
+  time_integral_kernel<<<blocks, 256, 0, s>>>(a, V, tail_s, out, block_sums,
+                                              reinterpret_cast<uint32_t*>(block_sums + blocks));
+  return cudaGetLastError();
+}
+
+}  // namespace nm

@@ -457,10 +457,11 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
   // Per patient, indexed by CounterSlot: the rare events (photo, cutoff,
   // rayleigh, killed units) counted here directly, and (multi) the lanes'
   // register counters handed over when a lane changes patient.
-  __shared__ unsigned long long s_cnt[MULTI ? kMaxBatchPatients : 1][9];   // [8]: positron units
+  __shared__ unsigned long long s_cnt[MULTI ? kMaxBatchPatients : 1][10];  // [8]: positron, [9]: gamma units
   __shared__ PatientGeom s_geom[MULTI ? kMaxBatchPatients : 1];
   extern __shared__ float s_site[];         // [9][blockDim]: decay site, photon A direction, photon B's
-                                            // distance to its region boundary, a pending Compton's two words
+                                            // distance to its region boundary, a pending Compton's two words;
+                                            // then the history lists (HIST) and the gamma origin (BETA)
   const int n_pat = MULTI ? p.n_patients : 1;
   for (int i = threadIdx.x; i < kKnTable; i += blockDim.x) {
     s_kn[i] = p.kn[i];
@@ -468,7 +469,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
     s_minv_out[i] = p.minv_out[i];
   }
   if (threadIdx.x < NM_MAX_MATERIALS) s_mat[threadIdx.x] = p.mat[threadIdx.x];
-  for (int i = threadIdx.x; i < n_pat * 9; i += blockDim.x) s_cnt[i / 9][i % 9] = 0;
+  for (int i = threadIdx.x; i < n_pat * 10; i += blockDim.x) s_cnt[i / 10][i % 10] = 0;
   if (MULTI)
     for (int i = threadIdx.x; i < n_pat; i += blockDim.x) s_geom[i] = p.patients[i];
   __syncthreads();
@@ -482,6 +483,10 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
   const HistList hl{reinterpret_cast<uint32_t*>(s_site + 9 * nb) + threadIdx.x,
                     reinterpret_cast<uint32_t*>(s_site + (9 + kHistVoxels) * nb) + threadIdx.x, nb};
   int hn = 0;                            // entries in this lane's history list
+  // nuclide variant: the decay site (origin of the gamma lines) and the lines
+  // of this decay still to be emitted
+  float* gsite = s_site + (9 + (HIST ? 2 * kHistVoxels : 0)) * nb + threadIdx.x;
+  uint32_t gmask = 0;
 
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t lt_mask = (1u << lane) - 1u;
@@ -517,6 +522,24 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
       out = outside_box(GB, px, py, pz);
       rem = site[6 * nb];
       if (out) f.inv_mubar = s_inv0_out;
+    } else if (BETA && !alive && gmask) {
+      // ---- next gamma line of the decay: from the decay site, isotropic ------
+      const int j = __ffs(gmask) - 1;
+      gmask &= gmask - 1;
+      alive = true;
+      px = gsite[0]; py = gsite[nb]; pz = gsite[2 * nb];
+      stream = kStreamGamma0 + (uint32_t)j; ctr = 0; steps = 0;
+      const uint4 rd = draw(ctr, stream, hlo, hhi, p.key0, p.key1);
+      const float c = fmaf(2.0f, u01(rd.x), -1.0f);
+      const float sn = sqrtf(fmaxf(0.0f, fmaf(-c, c, 1.0f)));
+      float sp, cp;
+      __sincosf(fmaf(kTwoPi, u01(rd.y), -3.14159265f), &sp, &cp);
+      ux = sn * cp; uy = sn * sp; uz = c;
+      e = p.gamma_e[j]; qe = p.gamma_q[j];
+      atomicAdd(&s_cnt[0][9], (ull)(uint32_t)qe);
+      out = outside_box(p.g, px, py, pz);
+      f = energy_factors<RAYLEIGH>(e, s_kn, out ? s_minv_out : s_minv, p.ln_e_lo, p.inv_dln_e);
+      rem = region_distance(p.g, out, px, py, pz, ux, uy, uz);
     }
     // ---- refill: lanes without a photon take new histories from the pool ----
     const unsigned need = __ballot_sync(kFull, !alive && !done);
@@ -586,6 +609,19 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
           hhi = (uint32_t)(h >> 32);
           Site st = sample_site(G, p.key0, p.key1, hlo, hhi);
           bool pair = true;                  // the annihilation photons start inside the grid
+          if (BETA && G.source_mode == NM_SOURCE_DECAY) {
+            // another radionuclide: gamma lines of this decay, emitted later
+            // from the decay site (the nucleus), one photon at a time
+            gsite[0] = st.x; gsite[nb] = st.y; gsite[2 * nb] = st.z;
+            uint32_t m = 0, gc = 0;
+            for (int j0 = 0; j0 < p.n_gamma; j0 += 4) {
+              const uint4 rg = draw(gc, kStreamGammaSelect, hlo, hhi, p.key0, p.key1);
+              const uint32_t w4[4] = {rg.x, rg.y, rg.z, rg.w};
+              for (int k = 0; k < 4 && j0 + k < p.n_gamma; ++k)
+                if (u01(w4[k]) < p.gamma_y[j0 + k]) m |= 1u << (j0 + k);
+            }
+            gmask = m;
+          }
           if (BETA && G.beta_tab) {
             uint32_t q0 = 0, q_left = 0;
             pair = positron_track(G, p.key0, p.key1, hlo, hhi, st.v, st.x, st.y, st.z, q0, q_left,
@@ -597,8 +633,17 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
                                       atomicAdd(G.tally + v, (ull)dq);
                                   });
             atomicAdd(&s_cnt[MULTI ? pi : 0][8], (ull)q0);
-            if (!pair) escaped += (ull)q_left + 2ull * (ull)(uint32_t)p.q_e0;
+            if (!pair) escaped += (ull)q_left + (p.annihilate ? 2ull * (ull)(uint32_t)p.q_e0 : 0ull);
           }
+          if (BETA && G.source_mode == NM_SOURCE_DECAY && G.q_positron > 0 && !p.annihilate) {
+            // no annihilation photon to carry the local deposit: tally it here
+            if (HIST)
+              hist_add(hl, hn, (uint32_t)st.v, (uint32_t)G.q_positron, p.g.tally, p.s2h_lo, p.s2h_hi,
+                       p.g.counters + kCtrHistSplits);
+            else
+              atomicAdd(G.tally + st.v, (ull)(uint32_t)G.q_positron);
+          }
+          if (BETA && !p.annihilate && G.source_mode == NM_SOURCE_DECAY) pair = false;
           if (pair) {
           px = st.x; py = st.y; pz = st.z;
           ux = st.u; uy = st.v_; uz = st.w;
@@ -655,6 +700,16 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
           has = true;
           dv = cv;
         }
+        // The scattered photons tally their deposit now and take their next
+        // flight step in this same iteration instead of idling through it.
+        if (HIST) {
+          if (has) hist_add(hl, hn, (uint32_t)dv, dq, p.g.tally, p.s2h_lo, p.s2h_hi, p.g.counters + kCtrHistSplits);
+        } else {
+          tally_flush<WARP_AGG>(G.tally + dv, has, dq, lane);
+        }
+        has = false;
+        dq = 0;
+        dv = 0;
       }
     }
     // ---- one Woodcock flight step per live lane -------------------------------
@@ -766,10 +821,12 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
   const unsigned fl = __reduce_or_sync(kFull, flags);
   if (lane == 0 && fl) atomicOr(p.status, fl);
   __syncthreads();
-  for (int i = threadIdx.x; i < n_pat * 9; i += blockDim.x) {
-    const int q = i / 9, k = i % 9;   // k is the CounterSlot, 8 the positron units
+  for (int i = threadIdx.x; i < n_pat * 10; i += blockDim.x) {
+    const int q = i / 10, k = i % 10;   // k is the CounterSlot, 8 the positron and 9 the gamma units
     if (s_cnt[q][k])
-      atomicAdd((MULTI ? s_geom[q].counters : p.g.counters) + (k < 8 ? k : (int)kCtrPositronUnits), s_cnt[q][k]);
+      atomicAdd((MULTI ? s_geom[q].counters : p.g.counters) +
+                    (k < 8 ? k : k == 8 ? (int)kCtrPositronUnits : (int)kCtrGammaUnits),
+                s_cnt[q][k]);
   }
 }
 
@@ -823,9 +880,10 @@ __global__ void check_source_kernel(const TransportParams p, uint64_t first, int
   dir[3 * i + 2] = s.w;
 }
 
-// Dynamic shared memory: the site stash, and the history lists when kept.
-size_t transport_smem(int block, bool history) {
-  return ((size_t)9 + (history ? 2 * kHistVoxels : 0)) * block * sizeof(float);
+// Dynamic shared memory: the site stash, the history lists when kept, and
+// (nuclide variant) the origin of the gamma lines.
+size_t transport_smem(int block, bool history, bool beta = false) {
+  return ((size_t)9 + (history ? 2 * kHistVoxels : 0) + (beta ? 3 : 0)) * block * sizeof(float);
 }
 
 template <bool A, bool R, bool G, bool M, bool H, bool B = false>
@@ -866,15 +924,20 @@ void* pick(bool a, bool r, bool g, bool m, bool h, bool beta) {
 
 }  // namespace
 
+bool nuclide_launch(const TransportParams& p) {
+  return p.g.beta_tab != nullptr || p.n_gamma > 0 || (p.g.source_mode == NM_SOURCE_DECAY && !p.annihilate);
+}
+
 cudaError_t launch_transport(const TransportParams& p, int grid, int block, bool warp_agg,
                              bool rayleigh, bool regroup, cudaStream_t s, bool multi, bool history) {
-  void* fn = pick(warp_agg, rayleigh, regroup, multi, history, !multi && p.g.beta_tab != nullptr);
+  const bool beta = !multi && nuclide_launch(p);
+  void* fn = pick(warp_agg, rayleigh, regroup, multi, history, beta);
   if (!fn) return cudaErrorInvalidValue;
   void* args[] = {(void*)&p};
   // the history lists take the static + dynamic total past the 48 KB default
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)transport_smem(block, history));
-  if (e == cudaSuccess) e = cudaLaunchKernel(fn, dim3(grid), dim3(block), args, transport_smem(block, history), s);
+  const size_t smem = transport_smem(block, history, beta);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, s);
   if (e != cudaSuccess) cudaGetLastError();  // a refused launch must not linger as the last error
   return e;
 }
@@ -883,10 +946,9 @@ int transport_max_blocks_per_sm(int block, bool warp_agg, bool rayleigh, bool re
                                 bool beta) {
   int n = 0;
   void* fn = pick(warp_agg, rayleigh, regroup, multi, history, beta);
-  if (!fn ||
-      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)transport_smem(block, history)) !=
-          cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, transport_smem(block, history)) != cudaSuccess) {
+  const size_t smem = transport_smem(block, history, beta);
+  if (!fn || cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }

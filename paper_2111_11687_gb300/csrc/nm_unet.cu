@@ -414,6 +414,12 @@ struct nm_denoiser {
   uint32_t* status = nullptr;
   long long step = 0;
   int head_blocks = 0;
+  // Test support (nm_denoise_capture): per convolution layer, in forward
+  // order, its input (decoder inputs as the concatenation [upsampled coarse |
+  // skip]), its output activation and the loss gradient at its output after
+  // the ReLU mask, all BF16, refreshed by every train step while on.
+  bool capture = false;
+  std::vector<bf16*> cap_x, cap_y, cap_g;
 
   ~nm_denoiser() {
     auto f = [](void* p) { if (p) cudaFree(p); };
@@ -431,6 +437,14 @@ struct nm_denoiser {
     for (auto p : cat) f(p);
     f(gA); f(gB); f(gC); f(gD); f(x_in); f(y); f(target); f(weight); f(dtop); f(head_part); f(head_sum);
     f(ws);
+    free_capture();
+  }
+
+  void free_capture() {
+    for (auto v : {&cap_x, &cap_y, &cap_g})
+      for (auto p : *v)
+        if (p) cudaFree(p);
+    cap_x.clear(); cap_y.clear(); cap_g.clear();
   }
 
   long long vox(int level) const { return (long long)B * (PD >> level) * (PH >> level) * (PW >> level); }
@@ -535,11 +549,23 @@ nm_status forward(nm_denoiser* h, bool fuse_head = false, bool* fused = nullptr)
   const int L = h->L;
   const bf16* in = h->x_in;
   int li = 0;
+  // test capture: layer k's input and output activation
+  auto keep = [&](int k, const bf16* x, const bf16* y) -> cudaError_t {
+    if (!h->capture) return cudaSuccess;
+    const Layer& l = h->layers[k];
+    const long long v = h->vox(l.level);
+    cudaError_t e = x ? cudaMemcpyAsync(h->cap_x[k], x, v * l.cin * sizeof(bf16), cudaMemcpyDeviceToDevice, s)
+                      : cudaSuccess;
+    if (!e) e = cudaMemcpyAsync(h->cap_y[k], y, v * l.cout * sizeof(bf16), cudaMemcpyDeviceToDevice, s);
+    return e;
+  };
   for (int i = 0; i < L; ++i) {
     const Layer& la = h->layers[li++];
     const Layer& lb = h->layers[li++];
     CK(conv3d_fwd(h->desc(la), in, nullptr, h->wb + la.w_off, h->w + la.b_off, h->ea[i], 1, h->status, s), "conv");
     CK(conv3d_fwd(h->desc(lb), h->ea[i], nullptr, h->wb + lb.w_off, h->w + lb.b_off, h->eb[i], 1, h->status, s), "conv");
+    CK(keep(li - 2, in, h->ea[i]), "capture");
+    CK(keep(li - 1, h->ea[i], h->eb[i]), "capture");
     if (i < L - 1) {
       const long long n = h->vox(i + 1) * h->widths[i];
       avgpool_kernel<<<grid1d(n / 8), 256, 0, s>>>(h->eb[i], h->B, h->PD >> i, h->PH >> i, h->PW >> i, h->widths[i],
@@ -561,6 +587,13 @@ nm_status forward(nm_denoiser* h, bool fuse_head = false, bool* fused = nullptr)
       CK(conv3d_fwd(h->desc(la), coarse, h->eb[i], h->wb + la.w_off, h->w + la.b_off, h->da[i], 1, h->status, s),
          "conv");
     }
+    if (h->capture) {
+      // the decoder input as one tensor, whichever form the convolution read
+      const long long n = h->vox(i) * (la.cin / 8);
+      upsample_concat_kernel<<<grid1d(n), 256, 0, s>>>(coarse, h->eb[i], h->B, h->PD >> i, h->PH >> i, h->PW >> i,
+                                                       la.c0, la.c1, h->cap_x[li - 2]);
+      CK(keep(li - 2, nullptr, h->da[i]), "capture");
+    }
     if (i == 0 && fuse_head && lb.cout == 16 && conv_tile_ok(h->desc(lb))) {
       CK(conv3d_fwd_tile_head(h->desc(lb), h->da[0], h->wb + lb.w_off, h->w + lb.b_off, h->w + h->head_off, h->x_in,
                               h->cx, h->y, h->status, s),
@@ -569,6 +602,7 @@ nm_status forward(nm_denoiser* h, bool fuse_head = false, bool* fused = nullptr)
       return NM_OK;
     }
     CK(conv3d_fwd(h->desc(lb), h->da[i], nullptr, h->wb + lb.w_off, h->w + lb.b_off, h->db[i], 1, h->status, s), "conv");
+    CK(keep(li - 1, h->da[i], h->db[i]), "capture");
     coarse = h->db[i];
   }
   return NM_OK;
@@ -665,6 +699,12 @@ nm_status backward(nm_denoiser* h) {
     }
     return NM_OK;
   };
+  // test capture: the gradient at layer l's output, after its ReLU mask
+  auto keep_grad = [&](const Layer& l, const bf16* gm) -> cudaError_t {
+    if (!h->capture) return cudaSuccess;
+    const int k = (int)(&l - h->layers.data());
+    return cudaMemcpyAsync(h->cap_g[k], gm, h->vox(l.level) * l.cout * sizeof(bf16), cudaMemcpyDeviceToDevice, s);
+  };
   nm_status st;
   // gradient wrt the top decoder output
   bf16* g = h->dtop;
@@ -673,8 +713,10 @@ nm_status backward(nm_denoiser* h) {
     const Layer& la = lay("d" + std::to_string(i) + "a");
     const long long nb = h->vox(i) * h->widths[i];
     relu_mask_kernel<<<grid1d(nb / 8), 256, 0, s>>>(g, h->db[i], nb);
+    CK(keep_grad(lb, g), "capture");
     if ((st = conv_back(lb, h->da[i], nullptr, g, h->gA)) != NM_OK) return st;
     relu_mask_kernel<<<grid1d(nb / 8), 256, 0, s>>>(h->gA, h->da[i], nb);
+    CK(keep_grad(la, h->gA), "capture");
     const bf16* coarse = i + 1 <= L - 2 ? h->db[i + 1] : h->eb[L - 1];
     if (use_cat(h, la)) {
       // same im2col rows, read from the materialised input
@@ -702,8 +744,10 @@ nm_status backward(nm_denoiser* h) {
                                                      h->PW >> i, h->widths[i], h->gC);
       g = h->gC;
     }
+    CK(keep_grad(lb, g), "capture");
     if ((st = conv_back(lb, h->ea[i], nullptr, g, h->gA)) != NM_OK) return st;
     relu_mask_kernel<<<grid1d(nb / 8), 256, 0, s>>>(h->gA, h->ea[i], nb);
+    CK(keep_grad(la, h->gA), "capture");
     const bf16* in = i == 0 ? h->x_in : h->pool[i - 1];
     if ((st = conv_back(la, in, nullptr, h->gA, i > 0 ? h->gB : nullptr)) != NM_OK) return st;
     if (i > 0) {
@@ -876,6 +920,52 @@ nm_status nm_denoise_params(nm_denoiser* h, float* get, const float* set, float*
   return NM_OK;
 }
 
+nm_status nm_denoise_adam_state(nm_denoiser* h, float* m1, float* m2, int64_t* step) {
+  if (!h) return fail(NM_ERR_ARG, "handle is NULL");
+  const size_t bytes = h->n_params * sizeof(float);
+  if (m1) CK(cudaMemcpyAsync(m1, h->m1, bytes, cudaMemcpyDefault, h->s), "adam state");
+  if (m2) CK(cudaMemcpyAsync(m2, h->m2, bytes, cudaMemcpyDefault, h->s), "adam state");
+  CK(cudaStreamSynchronize(h->s), "adam state");
+  if (step) *step = h->step;
+  return NM_OK;
+}
+
+nm_status nm_denoise_capture(nm_denoiser* h, int32_t on) {
+  if (!h) return fail(NM_ERR_ARG, "handle is NULL");
+  CK(cudaStreamSynchronize(h->s), "capture");
+  h->free_capture();
+  h->capture = false;
+  if (!on) return NM_OK;
+  const size_t n = h->layers.size();
+  h->cap_x.assign(n, nullptr); h->cap_y.assign(n, nullptr); h->cap_g.assign(n, nullptr);
+  for (size_t k = 0; k < n; ++k) {
+    const Layer& l = h->layers[k];
+    const long long v = h->vox(l.level);
+    cudaError_t e;
+    if ((e = dmalloc(&h->cap_x[k], v * l.cin)) || (e = dmalloc(&h->cap_y[k], v * l.cout)) ||
+        (e = dmalloc(&h->cap_g[k], v * l.cout))) {
+      h->free_capture();
+      return cfail(e, "capture buffers");
+    }
+  }
+  h->capture = true;
+  return NM_OK;
+}
+
+nm_status nm_denoise_captured(nm_denoiser* h, int32_t layer, int32_t kind, uint16_t* out, int64_t bytes) {
+  if (!h || !out) return fail(NM_ERR_ARG, "bad arguments");
+  if (!h->capture) return fail(NM_ERR_STATE, "capture is off");
+  if (layer < 0 || layer >= (int32_t)h->layers.size() || kind < 0 || kind > 2)
+    return fail(NM_ERR_ARG, "layer or kind out of range");
+  const Layer& l = h->layers[layer];
+  const long long need = h->vox(l.level) * (kind == 0 ? l.cin : l.cout) * (long long)sizeof(bf16);
+  if (bytes < need) return fail(NM_ERR_ARG, "output buffer too small");
+  const bf16* src = kind == 0 ? h->cap_x[layer] : kind == 1 ? h->cap_y[layer] : h->cap_g[layer];
+  CK(cudaMemcpyAsync(out, src, need, cudaMemcpyDefault, h->s), "capture");
+  CK(cudaStreamSynchronize(h->s), "capture");
+  return NM_OK;
+}
+
 nm_status nm_denoise_train_step(nm_denoiser* h, const uint16_t* x, const float* target, const float* weight,
                                 float lr, float* loss) {
   if (!h || !x || !target) return fail(NM_ERR_ARG, "bad arguments");
@@ -897,8 +987,10 @@ nm_status nm_denoise_train_step(nm_denoiser* h, const uint16_t* x, const float* 
   if ((st = backward(h)) != NM_OK) return st;
   if (lr > 0.0f) {
     h->step += 1;
-    const float c1 = 1.0f - std::pow(h->opt.beta1, (float)h->step);
-    const float c2 = 1.0f - std::pow(h->opt.beta2, (float)h->step);
+    // bias corrections 1 - beta^t in FP64: in FP32 the subtraction cancels
+    // (1 - 0.999^2 loses ~3e-5 of its value)
+    const float c1 = (float)(1.0 - std::pow((double)h->opt.beta1, (double)h->step));
+    const float c2 = (float)(1.0 - std::pow((double)h->opt.beta2, (double)h->step));
     adam_kernel<<<grid1d(h->n_params), 256, 0, s>>>(h->w, h->g, h->m1, h->m2, h->n_params, lr, h->opt.beta1,
                                                    h->opt.beta2, h->opt.eps, c1, c2, h->wb);
     CK(cudaGetLastError(), "adam");

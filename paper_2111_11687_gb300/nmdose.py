@@ -51,7 +51,11 @@ class nm_options(C.Structure):
                 ("warp_aggregate", C.c_int32), ("regroup", C.c_int32), ("regroup_lanes", C.c_int32),
                 ("max_steps", C.c_int32),
                 ("stream", C.c_void_p), ("history_sigma", C.c_int32), ("beta_max_mev", C.c_double),
-                ("beta_z", C.c_int32), ("kn_sampler", C.c_int32)]
+                ("beta_z", C.c_int32), ("kn_sampler", C.c_int32), ("no_annihilation", C.c_int32),
+                ("beta_electron", C.c_int32), ("n_beta", C.c_int32),
+                ("beta_endpoint_mev", C.POINTER(C.c_double)), ("beta_intensity", C.POINTER(C.c_double)),
+                ("n_gamma", C.c_int32), ("gamma_mev", C.POINTER(C.c_double)),
+                ("gamma_yield", C.POINTER(C.c_double))]
 
 
 class nm_counters(C.Structure):
@@ -89,6 +93,8 @@ _SIGS = {
     "nm_dose_get": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "nm_dose_get_organs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "nm_dose_get_tally": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "nm_time_integrated_activity": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(C.c_double), C.c_int32, C.c_int64,
+                                              C.c_double, C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
     "nm_dose_get_history_sigma": (C.c_int, [C.c_void_p, C.c_void_p]),
     "nm_dose_map_organs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "nm_dose_counters": (C.c_int, [C.c_void_p, C.POINTER(nm_counters)]),
@@ -122,6 +128,9 @@ _SIGS = {
     "nm_denoise_layer": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                    C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "nm_denoise_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "nm_denoise_adam_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int64)]),
+    "nm_denoise_capture": (C.c_int, [C.c_void_p, C.c_int32]),
+    "nm_denoise_captured": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int64]),
     "nm_denoise_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_float,
                                         C.POINTER(C.c_float)]),
     "nm_denoise_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -213,13 +222,31 @@ def _stream_ptr(stream):
 
 
 def options(**kw) -> nm_options:
+    """nm_options from keyword arguments.  ``beta_branches`` [(endpoint MeV,
+    intensity), ...] and ``gamma_lines`` [(MeV, yield per decay), ...] fill the
+    radionuclide arrays (kept alive by the returned struct)."""
     o = nm_options()
     load().nm_options_default(C.byref(o))
+    o._keep = []
     for k, v in kw.items():
         if k == "point":
             o.point[:] = [float(a) for a in v]
         elif k == "stream":
             o.stream = _stream_ptr(v)
+        elif k == "beta_branches":
+            e = np.ascontiguousarray([b[0] for b in v], np.float64)
+            i = np.ascontiguousarray([b[1] for b in v], np.float64)
+            o._keep += [e, i]
+            o.n_beta = len(e)
+            o.beta_endpoint_mev = e.ctypes.data_as(C.POINTER(C.c_double))
+            o.beta_intensity = i.ctypes.data_as(C.POINTER(C.c_double))
+        elif k == "gamma_lines":
+            e = np.ascontiguousarray([g[0] for g in v], np.float64)
+            y = np.ascontiguousarray([g[1] for g in v], np.float64)
+            o._keep += [e, y]
+            o.n_gamma = len(e)
+            o.gamma_mev = e.ctypes.data_as(C.POINTER(C.c_double))
+            o.gamma_yield = y.ctypes.data_as(C.POINTER(C.c_double))
         else:
             setattr(o, k, v)
     return o
@@ -300,6 +327,21 @@ def nm_dose_get_organs(h, n_labels: int, eps: bool = True):
 
 def nm_dose_get_tally(h, tally):
     _check(load().nm_dose_get_tally(h, ptr(tally)))
+
+
+def nm_time_integrated_activity(maps, t_h, half_life_h: float, out, stream=None) -> float:
+    """Time-integrated activity (Bq s per voxel) of activity maps measured at
+    times t_h (hours) into ``out``; returns the total over voxels."""
+    V = int(np.prod(maps[0].shape))
+    for k, m in enumerate(maps):
+        _want(f"maps[{k}]", m, "float32", V)
+    _want("out", out, "float32", V)
+    arr = (C.c_void_p * len(maps))(*[ptr(m) for m in maps])
+    t = (C.c_double * len(maps))(*[float(x) for x in t_h])
+    total = C.c_double()
+    _check(load().nm_time_integrated_activity(arr, t, len(maps), V, float(half_life_h), ptr(out), C.byref(total),
+                                              _stream_ptr(stream)))
+    return total.value
 
 
 def nm_dose_counters(h) -> dict:
@@ -453,6 +495,26 @@ class Denoiser:
 
     def params(self, get=None, set=None, grads=None):
         _check(load().nm_denoise_params(self.h, ptr(get), ptr(set), ptr(grads)))
+
+    def adam_state(self):
+        """(first moments, second moments, updates made) of Adam, host copies."""
+        m1 = np.empty(self.n_params, np.float32)
+        m2 = np.empty(self.n_params, np.float32)
+        t = C.c_int64()
+        _check(load().nm_denoise_adam_state(self.h, ptr(m1), ptr(m2), C.byref(t)))
+        return m1, m2, t.value
+
+    def capture(self, on: bool = True):
+        """Keep every layer's input, output activation and masked output
+        gradient on later train steps (test support)."""
+        _check(load().nm_denoise_capture(self.h, 1 if on else 0))
+
+    def captured(self, layer: int, kind: int, shape):
+        """Layer `layer`'s captured tensor (kind 0 input, 1 output activation,
+        2 masked output gradient) as a host BF16 bit-pattern array of `shape`."""
+        out = np.empty(shape, np.uint16)
+        _check(load().nm_denoise_captured(self.h, int(layer), int(kind), ptr(out), out.nbytes))
+        return out
 
     def train_step(self, x, target, weight=None, lr=None) -> float:
         loss = C.c_float()

@@ -85,3 +85,32 @@ def test_unet_backward_matches_finite_differences(dn):
             assert abs(fd - an) <= 1e-5 * max(1.0, abs(fd)), (name, which, fd, an)
             checked += 1
     assert checked == 2 * len(names)
+
+
+def test_adam_two_steps_by_hand():
+    # w0 = 1, gradients 0.5 then -0.25, lr 0.1, beta1 0.9, beta2 0.999, eps 1e-8.
+    # Step 1: m = 0.1*0.5 = 0.05, v = 0.001*0.25 = 0.00025; corrected 0.5 and
+    #   0.25; w = 1 - 0.1*0.5/(0.5 + 1e-8) = 0.90000000199999996...
+    # Step 2: m = 0.9*0.05 - 0.1*0.25 = 0.02, v = 0.999*0.00025 + 0.001*0.0625
+    #   = 0.00031225; corrected 0.02/0.19 and 0.00031225/0.001999;
+    #   w = 0.9000000019999... - 0.1*0.105263157894737/(0.395225379... + 1e-8)
+    #     = 0.87336629870784616...  (40-digit decimal arithmetic)
+    from oracle import denoise as dn
+    w, m, v = dn.adam_step(np.array([1.0]), np.array([0.5]), 0.0, 0.0, 1, 0.1)
+    # (1 - 0.9 is 0.09999999999999998 in FP64: relative 1e-14 covers the rounding)
+    assert abs(m[0] / 0.05 - 1) < 1e-14 and abs(v[0] / 0.00025 - 1) < 1e-14
+    assert abs(w[0] - 0.90000000199999996) < 1e-15
+    w, m, v = dn.adam_step(w, np.array([-0.25]), m, v, 2, 0.1)
+    assert abs(m[0] / 0.02 - 1) < 1e-14 and abs(v[0] / 0.00031225 - 1) < 1e-14
+    assert abs(w[0] - 0.87336629870784616) < 1e-15
+
+
+def test_adam_first_step_moves_every_weight_by_lr():
+    # At t = 1 the corrected moments are g and g^2, so each weight moves by
+    # lr g / (|g| + eps): lr against the gradient's sign, whatever its size.
+    from oracle import denoise as dn
+    rng = np.random.default_rng(0)
+    g = rng.normal(size=1000) * 10.0 ** rng.uniform(-3, 3, 1000)
+    w0 = rng.normal(size=1000)
+    w, _, _ = dn.adam_step(w0, g, 0.0, 0.0, 1, 1e-3, eps=0.0)
+    assert np.allclose(w0 - w, 1e-3 * np.sign(g), rtol=1e-12, atol=0)

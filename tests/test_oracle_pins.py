@@ -694,3 +694,93 @@ def test_decay_positions_stay_in_the_decay_voxel(orc):
     p = act.ravel()[idx] / act.sum()
     chi2 = ((cnt[idx] - n * p) ** 2 / (n * p)).sum()
     assert stats.chi2.sf(chi2, idx.size - 1) > 1e-4
+
+
+# ---------------------------------------------------------------------------
+# Other radionuclides (paper §4: 177Lu, 131I) and multi-time-point dosimetry
+# ---------------------------------------------------------------------------
+# Published decay data (NNDC / ICRP 107): beta- branches (endpoint MeV,
+# fraction of decays), mean beta- energy per decay, daughter Z.
+LU177 = dict(branches=[(0.4983, 0.794), (0.3849, 0.091), (0.1765, 0.116)], mean=0.1336, z=72)
+I131 = dict(branches=[(0.6063, 0.896), (0.3338, 0.0723), (0.2479, 0.0208), (0.8069, 0.0039)], mean=0.1819, z=54)
+
+
+@pytest.mark.parametrize("nuc", [LU177, I131], ids=["177Lu", "131I"])
+def test_beta_minus_spectra_against_published_mean_energies(orc, nuc):
+    # The allowed shape with the non-relativistic Fermi function of an
+    # electron is an approximation for these heavy daughters (forbidden
+    # branches, relativistic and screening corrections): its mean lies a few
+    # percent above the tabulated one.  A positron's Fermi function (the wrong
+    # sign) would move the mean by far more than the 6 % allowed here.
+    n = 400_000
+    e = [b[0] for b in nuc["branches"]]
+    s = orc.sample_beta_branches(e, [b[1] for b in nuc["branches"]], nuc["z"], -1, n, seed=21)
+    assert s.min() > 0 and s.max() < max(e)
+    assert abs(s.mean() / nuc["mean"] - 1) < 0.06, (s.mean(), nuc["mean"])
+    wrong = orc.sample_beta_branches(e, [b[1] for b in nuc["branches"]], nuc["z"], +1, n, seed=21)
+    assert abs(wrong.mean() / nuc["mean"] - 1) > 0.15, wrong.mean()
+
+
+def test_beta_branch_mixture_chi2(orc):
+    # Samples of a two-branch electron spectrum against the mixture of the
+    # normalised branch densities (quadrature of the pinned density).
+    br = [(0.5, 0.7), (0.2, 0.3)]
+    z = 30
+    n = 400_000
+    s = orc.sample_beta_branches([b[0] for b in br], [b[1] for b in br], z, -1, n, seed=3)
+    edges = np.linspace(0, 0.5, 26)
+    p = np.zeros(len(edges) - 1)
+    for tm, w in br:
+        f = lambda t: orc.beta_density_signed(t, tm, z, -1)
+        norm = integrate.quad(f, 0, tm, limit=200)[0]
+        p += w * np.array([integrate.quad(f, a, min(b, tm), limit=100)[0] if a < tm else 0.0
+                           for a, b in zip(edges[:-1], edges[1:])]) / norm
+    h, _ = np.histogram(s, edges)
+    ok = p > 0
+    chi2 = ((h[ok] - n * p[ok]) ** 2 / (n * p[ok])).sum()
+    assert stats.chi2.sf(chi2, ok.sum() - 1) > 1e-4, chi2
+
+
+def test_gamma_lines_follow_their_yields(orc):
+    # No attenuation: every photon leaves, so the escaped energy and the
+    # number of escapes give each line's count exactly (two lines, two
+    # equations); counts against N x yield (binomial).  No annihilation pair.
+    lines = [(0.2084, 0.104), (0.1130, 0.062)]
+    n = 1_000_000
+    vac = orc.Materials(z_over_a=[0.0], zeff=[0.0], pe_coeff=0.0)
+    shape = (3, 3, 3)
+    act = np.ones(shape)
+    r = orc.run(np.ones(shape), np.zeros(shape, np.uint8), vac, activity=act, spacing=(1.0, 1.0, 1.0), n_hist=n,
+                seed=5, batches=2, positron_mev=0.1336, annihilation=False, gamma_lines=lines)
+    q1, q2 = (round(e * 64e6) for e, _ in lines)
+    esc, k = r.counters["escaped"], r.counters["escapes"]
+    n2 = (esc - q1 * k) / (q2 - q1)
+    n1 = k - n2
+    assert n1 == int(n1) and n2 == int(n2) and n1 >= 0 and n2 >= 0
+    for cnt, (_, y) in zip((n1, n2), lines):
+        assert abs(cnt - n * y) < 4.5 * math.sqrt(n * y * (1 - y)), (cnt, n * y)
+    # emitted = local beta energy + gamma photons; deposited = the beta part
+    assert r.counters["emitted"] == n * round(0.1336 * 64e6) + esc
+    assert r.tally.sum() == n * round(0.1336 * 64e6)
+
+
+def test_time_integrated_activity_by_hand(orc):
+    # Points (1 h, 100 Bq) and (3 h, 80 Bq), half-life 6 h:
+    #   uptake 100 x 3600 / 2 = 180000; trapezoid (100 + 80)/2 x 7200 = 648000;
+    #   tail 80 x 6 x 3600 / ln 2 = 2492977.03...; total 3320977.03... Bq s
+    out = orc.time_integrated_activity([np.array([100.0]), np.array([80.0])], [1.0, 3.0], 6.0)
+    assert abs(out[0] - (180000 + 648000 + 80 * 21600 / math.log(2))) < 1e-6
+    assert abs(out[0] - 3320977.0307) < 1e-3
+
+
+def test_time_integrated_activity_exact_for_physical_decay(orc):
+    # A map measured at t = 0 that then only decays physically integrates to
+    # A_0 T_1/2 / ln 2 exactly, and the result is linear in the maps.
+    a = np.array([1.0, 2.5, 0.0, 7.0])
+    out = orc.time_integrated_activity([a], [0.0], 109.77 / 60.0)
+    assert np.allclose(out, a * 109.77 * 60.0 / math.log(2), rtol=1e-15, atol=0)
+    b = np.array([3.0, 0.5, 1.0, 2.0])
+    t = [0.5, 2.0, 24.0]
+    lhs = orc.time_integrated_activity([2 * a, 2 * b, a + b], t, 6.65 * 24)
+    rhs = 2 * orc.time_integrated_activity([a, b, 0.5 * (a + b)], t, 6.65 * 24)
+    assert np.allclose(lhs, rhs, rtol=1e-14, atol=0)
