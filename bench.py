@@ -239,6 +239,8 @@ def run_gpu(args):
     dose_map = torch.empty(SHAPE, dtype=torch.float32, device="cuda")
     nmdose.nm_dose_get(d.h, dose_map, None, None)
     d.close()
+    variants = (variant_perf(nmdose, (den_d, mat_d, act_d, lab_d), gm, opts, args.variant_decays)
+                if args.variant_decays > 0 and rank == 0 else None)
 
     # ---- end to end through the C ABI from pinned host buffers ---------------
     e2e = None
@@ -271,7 +273,7 @@ def run_gpu(args):
         e2e = {"value": e2e_val, "unit": METRIC, "h2d_bytes_per_step": int(V * (2 + 4 + 1)),
                "d2h_bytes_per_step": int(V * 8 + 8 * (inputs.N_LABELS + 1)), "steps": args.e2e_steps}
 
-    den = (denoiser_perf(torch, nmdose, args.denoiser_steps, peaks, (dose_map, den_d, act_d))
+    den = (denoiser_perf(torch, nmdose, args.denoiser_steps, _peaks(), (dose_map, den_d, act_d))
            if args.denoiser_steps > 0 else None)
     batched = batched_perf(torch, nmdose, phs, args.batch_decays, 3, 1) if phs else None
 
@@ -290,11 +292,50 @@ def run_gpu(args):
                            "l2": "working set (tallies 2x157 MB + grid 79 MB + alias 41 MB) exceeds the 129 MB L2",
                            "parallelism": f"histories sharded over {ws} GPU(s)"},
                 "gpu_launches": launches, "roofline": roofline, "clocks": clocks, "e2e": e2e,
-                "cpu_baseline": cpu, "denoiser": den, "batched": batched, "time_to_2pct": ttt}
+                "cpu_baseline": cpu, "denoiser": den, "batched": batched, "time_to_2pct": ttt,
+                "variants": variants}
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+# Published decay data (NNDC / ICRP 107): beta- branches (endpoint MeV, fraction
+# of decays), daughter Z, main gamma lines (MeV, photons per decay).
+NUCLIDES = {
+    "177Lu": dict(no_annihilation=1, beta_electron=1, beta_z=72, positron_mev=0.0,
+                  beta_branches=[(0.4983, 0.794), (0.3849, 0.091), (0.1765, 0.116)],
+                  gamma_lines=[(0.2084, 0.104), (0.1130, 0.062)]),
+    "131I": dict(no_annihilation=1, beta_electron=1, beta_z=54, positron_mev=0.0,
+                 beta_branches=[(0.6063, 0.896), (0.3338, 0.0723), (0.2479, 0.0208), (0.8069, 0.0039)],
+                 gamma_lines=[(0.3645, 0.815), (0.6370, 0.0716), (0.2843, 0.0612), (0.0802, 0.0262),
+                              (0.7229, 0.0177)]),
+}
+
+
+def variant_perf(nm, arrays, gm, opts, decays):
+    """Decays/s of the transport variants on the benchmark phantom (device
+    time of the transport launches): 18F with history-by-history sigma (and
+    the fraction of histories whose deposits spread over more voxels than a
+    lane keeps), 18F with the beta+ spectrum and positron tracks, 177Lu and
+    131I (beta- tracks, gamma lines, no annihilation pair)."""
+    den, mat, act, lab = arrays
+    cases = {"18F_history_sigma": dict(history_sigma=1), "18F_beta_tracks": dict(beta_max_mev=0.6335, beta_z=8),
+             **NUCLIDES}
+    out = {}
+    for name, kw in cases.items():
+        with nm.Dose(den, mat, SPACING, gm, activity=act, labels=lab, **opts, **kw) as d:
+            d.run(decays // 5, seed=1)
+            c0 = d.counters()
+            d.run(decays, seed=2)
+            c1 = d.counters()
+        ms = c1["transport_ms"] - c0["transport_ms"]
+        r = {"decays_per_s": decays / (ms * 1e-3), "emitted_mev_per_decay":
+             (c1["emitted"] - c0["emitted"]) / 64e6 / decays}
+        if name == "18F_history_sigma":
+            r["split_histories_fraction"] = (c1["history_splits"] - c0["history_splits"]) / decays
+        out[name] = r
+    return out
 
 
 def time_to_2pct(args):
@@ -601,6 +642,8 @@ def main():
     ap.add_argument("--denoiser-steps", type=int, default=10)
     ap.add_argument("--batch-patients", type=int, default=16)
     ap.add_argument("--batch-decays", type=int, default=100_000_000)
+    ap.add_argument("--variant-decays", type=int, default=500_000_000,
+                    help="decays per transport variant (history sigma, beta tracks, 177Lu, 131I; 0 = skip)")
     ap.add_argument("--ttt-train", type=int, default=200, help="time-to-2%% block: training phantoms (0 = skip)")
     ap.add_argument("--ttt-test", type=int, default=20, help="time-to-2%% block: held-out phantoms")
     ap.add_argument("--ttt-steps", type=int, default=10000, help="time-to-2%% block: training steps per network")

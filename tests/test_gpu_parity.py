@@ -5,6 +5,7 @@ and different sampling algorithms): the voxel criterion is |gpu - oracle| <=
 and organ (or radial-shell) means must agree within 4 combined sigma and
 within 1 % wherever the combined sigma makes a 1 % test meaningful."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -195,22 +196,54 @@ def test_reduced_phantom_matches_oracle(nm, orc, kn_sampler):
     np.testing.assert_allclose(fs, s2, rtol=1e-4, atol=1e-30)
 
 
-def test_full_size_phantom_organs_match_oracle(nm, orc):
-    # 256x256x300 voxels of 2x2x3 mm, 1e9 decays on the GPU (the benchmark
-    # workload) against 2e6 oracle decays on the same phantom: organ means
-    # within 4 combined sigma (the oracle's sigma dominates), and within 1 %
-    # where that is resolvable; exact energy bookkeeping at full size.
+def _golden_organs():
+    """The oracle's organ means and their batch sigma for the benchmark phantom
+    (tests/golden/make_adult_phantom_organs.py, 1e9 oracle decays)."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "adult_phantom_organs_oracle.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    lab = np.array([int(r[0]) for r in rows])
+    assert np.array_equal(lab, np.arange(len(rows)))
+    return (np.array([float(r[1]) for r in rows]), np.array([float(r[2]) for r in rows]),
+            np.array([int(r[3]) for r in rows]))
+
+
+def test_full_size_phantom_every_organ_within_1_percent(nm):
+    # The benchmark workload, 256x256x300 voxels of 2x2x3 mm: 1e10 GPU decays
+    # against the stored 1e9-decay oracle means.  Every one of the 27 organs
+    # must be within 1 % and within 4 combined sigma; an organ whose three
+    # combined sigma reach 1 % makes the check underpowered, which fails too
+    # rather than passing on the organs that are resolvable.
+    from paper_2111_11687_gb300 import inputs
+    om, os_, ocnt = _golden_organs()
     ph = _phantom((300, 256, 256), (0.2, 0.2, 0.3), seed=1)
-    N = 1_000_000_000
-    den, mat, g, sg, (gm, ge, gs, cnt), c, t = _gpu_phantom_run(nm, ph, N, seed=1)
+    N = 10_000_000_000
+    den, mat, g, sg, (gm, ge, gs, cnt), c, t = _gpu_phantom_run(nm, ph, N, seed=1, batches=20)
     assert c["emitted"] == c["deposited"] + c["escaped"] and c["killed"] == 0
     assert int(t.sum()) == c["deposited"]
-    r = _oracle_phantom_run(orc, ph, 2_000_000, seed=2)
+    assert np.array_equal(cnt, ocnt)
+    organs = np.arange(1, inputs.N_LABELS + 1)
+    comb = np.sqrt(gs[organs] ** 2 + os_[organs] ** 2)
+    under = organs[3 * comb >= 0.01 * om[organs]]
+    assert under.size == 0, f"underpowered: organs {under.tolist()} have 3 combined sigma >= 1 %"
+    rel = gm[organs] / om[organs] - 1
+    z = (gm[organs] - om[organs]) / comb
+    assert np.all(np.abs(rel) < 0.01), dict(zip(organs[np.abs(rel) >= 0.01].tolist(), rel[np.abs(rel) >= 0.01]))
+    assert np.all(np.abs(z) < 4.0), dict(zip(organs[np.abs(z) >= 4].tolist(), z[np.abs(z) >= 4]))
+
+
+def test_reduced_size_phantom_voxel_criterion(nm, orc):
+    # The adult phantom on the 128x128x150 grid of 4x4x6 mm (half the
+    # benchmark's resolution): 1e9 GPU decays against 1e8 oracle decays, both
+    # in 20 batches; >= 99 % of the body voxels above 5 % of the maximum dose
+    # within 3 combined sigma, and every organ within 4 combined sigma.
+    ph = _phantom((150, 128, 128), (0.4, 0.4, 0.6), seed=1)
+    den, mat, g, sg, (gm, ge, gs, cnt), c, _ = _gpu_phantom_run(nm, ph, 1_000_000_000, seed=5, batches=20)
+    r = _oracle_phantom_run(orc, ph, 100_000_000, seed=6, batches=20)
+    frac, nsel = voxel_criterion(g, sg, r.dose_rate, r.sigma, den >= 0.1)
+    assert nsel > 20000 and frac >= 0.99, (frac, nsel)
     zmax, npow, worst, z, sel = organ_check(gm, gs, r.organ_mean, r.organ_sigma, cnt)
-    assert zmax < 4.0, z[sel]
-    assert npow >= 3 and worst < 0.01, (npow, worst)
-    # GPU organ sigma at 1e9 decays: the well-sampled organs are below 1 %.
-    assert np.all(gs[sel] / gm[sel] < 0.05)
+    assert sel.sum() >= 25 and zmax < 4.0, z[sel]
+    assert worst < 0.01, (npow, worst)
 
 
 def test_whole_body_phantom_organs_match_oracle(nm, orc):
