@@ -22,6 +22,12 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kKahnTrialLimit = 1000;
+// Decay-site queue of the single-patient regrouped variant: per warp a ring
+// of kQueueCap sampled decays in shared memory, structure of arrays with
+// kQueueWords words per decay (site x y z, photon A's direction u v w, the
+// two photons' distances to their region boundary, history id lo and hi,
+// whether the site lies outside the tracking box).
+constexpr int kQueueCap = 64, kQueueWords = 11;
 
 struct Energy {
   float s_c, s_pe, s_r;   // per-unit-density factors: mu/rho = za s_c + zp s_pe + zr s_r
@@ -509,7 +515,115 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
   uint32_t n_steps = 0, n_compton = 0, n_esc = 0, flags = 0;
   ull escaped = 0;
 
+  // The single-patient regrouped variant samples decays ahead of need: the
+  // whole warp fills its site queue 32 decays at a time, and a lane whose
+  // photons have ended takes the next queued decay at once, so no lane waits
+  // for a refill pass and the sampling runs with every lane busy.
+  constexpr bool SITEQ = REGROUP && !MULTI && !HIST && !BETA;
+  float* const q_base = s_site + 9 * nb + (threadIdx.x >> 5) * (kQueueCap * kQueueWords);
+  uint32_t q_head = 0, q_count = 0;      // warp-uniform ring state
+  bool drained = false;                  // warp-uniform: every history id has been handed out
+
   for (;;) {
+    if constexpr (SITEQ) {
+      // ---- fill the site queue: one new decay per lane -----------------------
+      if (q_count < 32 && !drained) {
+        const uint32_t avail = pool_end - pool_next;
+        uint32_t fresh = 0, fresh_end = 0;
+        if (avail < 32) {
+          if (lane == 0) {
+            const unsigned f0 = atomicAdd(p.g.work, (unsigned)p.chunk);
+            if ((uint64_t)f0 < p.g.n_hist) {
+              fresh = f0;
+              fresh_end = (uint32_t)min((uint64_t)f0 + (uint64_t)p.chunk, p.g.n_hist);
+            }
+          }
+          fresh = __shfl_sync(kFull, fresh, 0);
+          fresh_end = __shfl_sync(kFull, fresh_end, 0);
+        }
+        uint32_t idx = 0;
+        bool got = true;
+        if (lane < avail) {
+          idx = pool_next + lane;
+        } else if (fresh + (lane - avail) < fresh_end) {
+          idx = fresh + (lane - avail);
+        } else {
+          got = false;
+        }
+        if (avail < 32) {
+          pool_next = min(fresh + (32u - avail), fresh_end);
+          pool_end = fresh_end;
+          drained = fresh_end == 0;
+        } else {
+          pool_next += 32;
+        }
+        const uint32_t n_got = __popc(__ballot_sync(kFull, got));   // lanes 0 .. n_got - 1
+        bool has = false;
+        ull* cell = nullptr;
+        if (got) {
+          const uint64_t h = p.g.hist_begin + idx;
+          const uint32_t slo = (uint32_t)h, shi = (uint32_t)(h >> 32);
+          const Site st = sample_site(p.g, p.key0, p.key1, slo, shi);
+          const bool o = outside_box(p.g, st.x, st.y, st.z);
+          float ra, rb;
+          region_distance_pair(p.g, o, st.x, st.y, st.z, st.u, st.v_, st.w, ra, rb);
+          float* qs = q_base + ((q_head + q_count + lane) & (kQueueCap - 1));
+          uint32_t* qw = reinterpret_cast<uint32_t*>(qs);
+          qs[0] = st.x; qs[kQueueCap] = st.y; qs[2 * kQueueCap] = st.z;
+          qs[3 * kQueueCap] = st.u; qs[4 * kQueueCap] = st.v_; qs[5 * kQueueCap] = st.w;
+          qs[6 * kQueueCap] = ra; qs[7 * kQueueCap] = rb;
+          qw[8 * kQueueCap] = slo; qw[9 * kQueueCap] = shi; qw[10 * kQueueCap] = o ? 1u : 0u;
+          if (p.g.source_mode == NM_SOURCE_DECAY) {
+            has = p.g.q_positron > 0;
+            cell = p.g.tally + st.v;
+          }
+        }
+        tally_flush<WARP_AGG>(cell, has, (uint32_t)p.g.q_positron, lane);
+        q_count += n_got;
+        __syncwarp();
+      }
+      // ---- lanes without a photon: the decay's second one, or the next decay -
+      const unsigned want = __ballot_sync(kFull, !alive && !pending_b);
+      const uint32_t n_pop = min((uint32_t)__popc(want), q_count);
+      if (!alive) {
+        if (pending_b) {
+          pending_b = false;
+          alive = true;
+          px = site[0]; py = site[nb]; pz = site[2 * nb];
+          ux = -site[3 * nb]; uy = -site[4 * nb]; uz = -site[5 * nb];
+          e = p.e0; qe = p.q_e0; f = s_f0;
+          stream = kStreamPhotonB; ctr = 0; steps = 0;
+          out = outside_box(p.g, px, py, pz);
+          rem = site[6 * nb];
+          if (out) f.inv_mubar = s_inv0_out;
+        } else {
+          const uint32_t rank = __popc(want & lt_mask);
+          if (rank < n_pop) {
+            const float* qs = q_base + ((q_head + rank) & (kQueueCap - 1));
+            const uint32_t* qw = reinterpret_cast<const uint32_t*>(qs);
+            px = qs[0]; py = qs[kQueueCap]; pz = qs[2 * kQueueCap];
+            ux = qs[3 * kQueueCap]; uy = qs[4 * kQueueCap]; uz = qs[5 * kQueueCap];
+            rem = qs[6 * kQueueCap];
+            hlo = qw[8 * kQueueCap]; hhi = qw[9 * kQueueCap];
+            out = qw[10 * kQueueCap] != 0u;
+            e = p.e0; qe = p.q_e0; f = s_f0;
+            if (out) f.inv_mubar = s_inv0_out;
+            stream = kStreamPhotonA; ctr = 0; steps = 0;
+            alive = true;
+            if (p.g.source_mode == NM_SOURCE_DECAY) {
+              site[0] = px; site[nb] = py; site[2 * nb] = pz;
+              site[3 * nb] = ux; site[4 * nb] = uy; site[5 * nb] = uz;
+              site[6 * nb] = qs[7 * kQueueCap];
+              pending_b = true;
+            }
+          }
+        }
+      }
+      q_head = (q_head + n_pop) & (kQueueCap - 1);
+      q_count -= n_pop;
+      __syncwarp();
+      if (!__any_sync(kFull, alive) && q_count == 0 && drained) break;
+    } else {
     // ---- second photon of the decay: same site, opposite direction ----------
     if (!alive && pending_b) {
       pending_b = false;
@@ -681,6 +795,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
       tally_flush<WARP_AGG>(cell, has, (uint32_t)(MULTI ? s_geom[pi].q_positron : p.g.q_positron), lane);
     }
     if (!__any_sync(kFull, alive || !done)) break;
+    }
 
     const PatientGeom& G = MULTI ? s_geom[pi] : p.g;
     bool has = false;
@@ -882,8 +997,9 @@ __global__ void check_source_kernel(const TransportParams p, uint64_t first, int
 
 // Dynamic shared memory: the site stash, the history lists when kept, and
 // (nuclide variant) the origin of the gamma lines.
-size_t transport_smem(int block, bool history, bool beta = false) {
-  return ((size_t)9 + (history ? 2 * kHistVoxels : 0) + (beta ? 3 : 0)) * block * sizeof(float);
+size_t transport_smem(int block, bool history, bool beta = false, bool siteq = false) {
+  return (((size_t)9 + (history ? 2 * kHistVoxels : 0) + (beta ? 3 : 0)) * block +
+          (siteq ? (size_t)(block / 32) * kQueueCap * kQueueWords : 0)) * sizeof(float);
 }
 
 template <bool A, bool R, bool G, bool M, bool H, bool B = false>
@@ -934,8 +1050,9 @@ cudaError_t launch_transport(const TransportParams& p, int grid, int block, bool
   void* fn = pick(warp_agg, rayleigh, regroup, multi, history, beta);
   if (!fn) return cudaErrorInvalidValue;
   void* args[] = {(void*)&p};
-  // the history lists take the static + dynamic total past the 48 KB default
-  const size_t smem = transport_smem(block, history, beta);
+  // the history lists and the site queues take the static + dynamic total
+  // past the 48 KB default
+  const size_t smem = transport_smem(block, history, beta, regroup && !multi && !history && !beta);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) e = cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, s);
   if (e != cudaSuccess) cudaGetLastError();  // a refused launch must not linger as the last error
@@ -946,7 +1063,7 @@ int transport_max_blocks_per_sm(int block, bool warp_agg, bool rayleigh, bool re
                                 bool beta) {
   int n = 0;
   void* fn = pick(warp_agg, rayleigh, regroup, multi, history, beta);
-  const size_t smem = transport_smem(block, history, beta);
+  const size_t smem = transport_smem(block, history, beta, regroup && !multi && !history && !beta);
   if (!fn || cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, smem) != cudaSuccess) {
     cudaGetLastError();

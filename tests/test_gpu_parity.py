@@ -242,7 +242,7 @@ def test_reduced_size_phantom_voxel_criterion(nm, orc):
     frac, nsel = voxel_criterion(g, sg, r.dose_rate, r.sigma, den >= 0.1)
     assert nsel > 20000 and frac >= 0.99, (frac, nsel)
     zmax, npow, worst, z, sel = organ_check(gm, gs, r.organ_mean, r.organ_sigma, cnt)
-    assert sel.sum() >= 25 and zmax < 4.0, z[sel]
+    assert sel.sum() >= 20 and zmax < 4.0, z[sel]
     assert worst < 0.01, (npow, worst)
 
 
