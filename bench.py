@@ -278,6 +278,8 @@ def run_gpu(args):
     batched = batched_perf(torch, nmdose, phs, args.batch_decays, 3, 1) if phs else None
 
     ttt = time_to_2pct(args) if rank == 0 and ws == 1 and args.ttt_train > 0 else None
+    if ttt is not None and args.whole_body:
+        ttt["whole_body"] = whole_body_time_to_2pct()
     cpu = None
     if rank == 0 and ws == 1 and args.cpu_decays > 0:
         cpu = cpu_baseline(args.cpu_decays)
@@ -377,6 +379,22 @@ def time_to_2pct(args):
                         "final_loss": r["final_loss"], "candidate_val_losses": r["candidate_val_losses"],
                         "data_s": r["data_s"], "train_s": r["train_s"]},
             "wall_s": time.perf_counter() - t0, "per_phantom": cases}
+
+
+def whole_body_time_to_2pct():
+    """The whole-body workload (512x512x600 voxels of 1x1x3 mm with 1-3 cm
+    lesions): plain MC's wall time until all 27 organ means are within 2 % of
+    a 1e10-decay reference (organ means from the fold's sums every 5e6
+    decays), and the MC + denoiser arm's cost before any check (MC of 1e8
+    decays and one inference on the organs' bounding box), a lower bound of
+    that arm: no network is trained at 1 x 1 x 3 mm."""
+    from paper_2111_11687_gb300 import experiment
+    wb = experiment.configs()["whole_body"]
+    return {"grid": wb["grid"], "voxel_mm": wb["voxel_mm"], "reference_decays": wb["reference_decays"],
+            "plain_mc_ms": None if wb["plain_mc_s"] is None else 1e3 * wb["plain_mc_s"],
+            "plain_mc_decays": wb["plain_mc_decays"], "plain_mc_worst_organ_err": wb["plain_mc_err"],
+            "mc_denoiser_lower_bound_ms": 1e3 * wb["mc_denoiser_lower_bound_s"],
+            "decays_per_s_1e9": wb["decays_per_s_1e9"]}
 
 
 def measure_ceilings(nm):
@@ -648,6 +666,7 @@ def main():
     ap.add_argument("--ttt-test", type=int, default=20, help="time-to-2%% block: held-out phantoms")
     ap.add_argument("--ttt-steps", type=int, default=10000, help="time-to-2%% block: training steps per network")
     ap.add_argument("--ttt-candidates", type=int, default=3, help="time-to-2%% block: networks trained")
+    ap.add_argument("--whole-body", type=int, default=1, help="time-to-2%% block: add the whole-body phantom")
     ap.add_argument("--denoiser-only", action="store_true", help="only the U-Net throughput (for ncu)")
     ap.add_argument("--profile", action="store_true", help="one short run for ncu")
     ap.add_argument("--decays", type=int, default=200_000_000)
