@@ -162,6 +162,7 @@ typedef struct {
 #define NM_DEV_BAD_VOXEL 4u    /* material id out of range, density not > 0 */
 #define NM_DEV_BAD_ACTIVITY 8u /* activity negative or not finite */
 #define NM_DEV_TIMEOUT 16u     /* a bounded wait on the tensor cores gave up */
+#define NM_DEV_RAYLEIGH_LIMIT 32u /* the Rayleigh (Thomson) angle hit its trial limit */
 
 /* Fills *o with the defaults: decay mode, 0.511 MeV photons, 0.25 MeV positron,
  * 10 batches, A(t_s) = 8.0 mCi decayed 60 min with T1/2 = 109.77 min (§2.2),

@@ -873,9 +873,10 @@ nm_status nm_dose_run(nm_dose* h, uint64_t n, uint64_t seed) {
   h->status_seen |= st;
   if (st) {
     NM_CUDA(cudaMemsetAsync(h->status, 0, 4, s), "status reset");
-    return fail(NM_ERR_DEVICE, "device check fired (flags 0x%x: %s%s)", st,
+    return fail(NM_ERR_DEVICE, "device check fired (flags 0x%x: %s%s%s)", st,
                 (st & NM_DEV_STEP_LIMIT) ? "photon step limit " : "",
-                (st & NM_DEV_KAHN_LIMIT) ? "Kahn trial limit" : "");
+                (st & NM_DEV_KAHN_LIMIT) ? "Kahn trial limit " : "",
+                (st & NM_DEV_RAYLEIGH_LIMIT) ? "Rayleigh trial limit" : "");
   }
   return NM_OK;
 }

@@ -273,3 +273,46 @@ def test_whole_body_phantom_organs_match_oracle(nm, orc):
     assert np.all(np.isfinite(o))
     body = den >= 0.1
     assert np.allclose(o[body], g[body], rtol=1e-2, atol=1e-3 * g[body].max())
+
+
+def test_rayleigh_on_matches_oracle(nm, orc):
+    # The optional Rayleigh events (R4: mu_R/rho = c_R Zeff^2 / E^2, Thomson
+    # angles) on the reduced phantom with a coefficient large enough that they
+    # matter (mu_R is about 0.4 mu_c at 511 keV and grows as 1/E^2 below it):
+    # voxel criterion and organs against the oracle with Rayleigh on, the
+    # Rayleigh-to-Compton event ratio within binomial scatter, and no device
+    # flag (the Thomson rejection loop never hits its trial limit).
+    from paper_2111_11687_gb300 import inputs
+    ph = _phantom((75, 64, 64), (0.8, 0.8, 1.2), seed=21)
+    N = 2_000_000
+    rc = 2.0e-4
+    den = np.empty(ph.shape, np.float32)
+    mat = np.empty(ph.shape, np.uint8)
+    nm.nm_ct_to_phantom(ph.hu, den, mat)
+    gmat = nm.Materials(inputs.MATERIAL_Z_OVER_A, inputs.MATERIAL_ZEFF, inputs.PE_COEFF, inputs.PE_EXP,
+                        rayleigh_coeff=rc, rayleigh=1)
+    with nm.Dose(den, mat, ph.spacing, gmat, activity=ph.activity, labels=ph.labels, n_labels=inputs.N_LABELS,
+                 activity_bq=inputs.ACTIVITY_BQ, batches=10) as d:
+        d.run(N, seed=7)
+        g, sg = d.get()
+        gm, ge, gs, cnt = d.organs()
+        c = d.counters()
+    assert c["device_status"] == 0 and c["rayleigh"] > 0.1 * c["compton"]
+    assert c["emitted"] == c["deposited"] + c["escaped"] and c["killed"] == 0
+    oden, omat = orc.hu_to_phantom(ph.hu)
+    om = orc.Materials(inputs.MATERIAL_Z_OVER_A, inputs.MATERIAL_ZEFF, inputs.PE_COEFF, inputs.PE_EXP,
+                       rayleigh_coeff=rc, rayleigh=1)
+    r = orc.run(oden, omat, om, activity=ph.activity, labels=ph.labels, n_labels=inputs.N_LABELS,
+                spacing=ph.spacing, n_hist=N, seed=8, batches=10, activity_bq=inputs.ACTIVITY_BQ)
+    frac, nsel = voxel_criterion(g, sg, r.dose_rate, r.sigma, den >= 0.1)
+    assert nsel > 1000 and frac >= 0.99, (frac, nsel)
+    zmax, npow, worst, z, sel = organ_check(gm, gs, r.organ_mean, r.organ_sigma, cnt)
+    assert zmax < 4.0, z[sel]
+    # events per decay: Rayleigh / (Rayleigh + Compton) on both sides
+    fg = c["rayleigh"] / (c["rayleigh"] + c["compton"])
+    fo = r.counters["rayleigh"] / (r.counters["rayleigh"] + r.counters["compton"])
+    ng = c["rayleigh"] + c["compton"]
+    no = r.counters["rayleigh"] + r.counters["compton"]
+    sd = math.sqrt(fg * (1 - fg) / ng + fo * (1 - fo) / no)
+    # photon histories make events correlated within a decay: allow 8 binomial sigma
+    assert abs(fg - fo) < 8 * sd, (fg, fo, sd)
