@@ -302,28 +302,16 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-# Published decay data (NNDC / ICRP 107): beta- branches (endpoint MeV, fraction
-# of decays), daughter Z, main gamma lines (MeV, photons per decay).
-NUCLIDES = {
-    "177Lu": dict(no_annihilation=1, beta_electron=1, beta_z=72, positron_mev=0.0,
-                  beta_branches=[(0.4983, 0.794), (0.3849, 0.091), (0.1765, 0.116)],
-                  gamma_lines=[(0.2084, 0.104), (0.1130, 0.062)]),
-    "131I": dict(no_annihilation=1, beta_electron=1, beta_z=54, positron_mev=0.0,
-                 beta_branches=[(0.6063, 0.896), (0.3338, 0.0723), (0.2479, 0.0208), (0.8069, 0.0039)],
-                 gamma_lines=[(0.3645, 0.815), (0.6370, 0.0716), (0.2843, 0.0612), (0.0802, 0.0262),
-                              (0.7229, 0.0177)]),
-}
-
-
 def variant_perf(nm, arrays, gm, opts, decays):
     """Decays/s of the transport variants on the benchmark phantom (device
     time of the transport launches): 18F with history-by-history sigma (and
     the fraction of histories whose deposits spread over more voxels than a
     lane keeps), 18F with the beta+ spectrum and positron tracks, 177Lu and
     131I (beta- tracks, gamma lines, no annihilation pair)."""
+    from paper_2111_11687_gb300 import nuclides
     den, mat, act, lab = arrays
-    cases = {"18F_history_sigma": dict(history_sigma=1), "18F_beta_tracks": dict(beta_max_mev=0.6335, beta_z=8),
-             **NUCLIDES}
+    cases = {"18F_history_sigma": dict(history_sigma=1), "18F_beta_tracks": nuclides.F18_TRACKED,
+             "177Lu": nuclides.LU177, "131I": nuclides.I131}
     out = {}
     for name, kw in cases.items():
         with nm.Dose(den, mat, SPACING, gm, activity=act, labels=lab, **opts, **kw) as d:

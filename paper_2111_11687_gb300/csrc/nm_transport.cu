@@ -22,12 +22,12 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kKahnTrialLimit = 1000;
-// Decay-site queue of the regrouped variants: per warp a ring of kQueueCap
-// sampled decays in shared memory, structure of arrays with kQueueWords
-// words per decay (site x y z, photon A's direction u v w, the two photons'
-// distances to their region boundary, history id lo and hi, whether the site
-// lies outside the tracking box, the patient).
-constexpr int kQueueCap = 64, kQueueWords = 12;
+// Decay-site queue of the single-patient regrouped variant: per warp a ring
+// of kQueueCap sampled decays in shared memory, structure of arrays with
+// kQueueWords words per decay (site x y z, photon A's direction u v w, the
+// two photons' distances to their region boundary, history id lo and hi,
+// whether the site lies outside the tracking box).
+constexpr int kQueueCap = 64, kQueueWords = 11;
 
 struct Energy {
   float s_c, s_pe, s_r;   // per-unit-density factors: mu/rho = za s_c + zp s_pe + zr s_r
@@ -515,11 +515,11 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
   uint32_t n_steps = 0, n_compton = 0, n_esc = 0, flags = 0;
   ull escaped = 0;
 
-  // The regrouped variants sample decays ahead of need: the whole warp fills
-  // its site queue 32 decays at a time, and a lane whose photons have ended
-  // takes the next queued decay at once, so no lane waits for a refill pass
-  // and the sampling runs with every lane busy.
-  constexpr bool SITEQ = REGROUP && !HIST && !BETA;
+  // The single-patient regrouped variant samples decays ahead of need: the
+  // whole warp fills its site queue 32 decays at a time, and a lane whose
+  // photons have ended takes the next queued decay at once, so no lane waits
+  // for a refill pass and the sampling runs with every lane busy.
+  constexpr bool SITEQ = REGROUP && !MULTI && !HIST && !BETA;
   float* const q_base = s_site + 9 * nb + (threadIdx.x >> 5) * (kQueueCap * kQueueWords);
   uint32_t q_head = 0, q_count = 0;      // warp-uniform ring state
   bool drained = false;                  // warp-uniform: every history id has been handed out
@@ -530,42 +530,23 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
       if (q_count < 32 && !drained) {
         const uint32_t avail = pool_end - pool_next;
         uint32_t fresh = 0, fresh_end = 0;
-        int nwp = wp;
         if (avail < 32) {
-          // a chunk from the current patient's queue; a drained queue moves
-          // the warp on to the next patient
           if (lane == 0) {
-            if constexpr (MULTI) {
-              for (int t = 0; t < n_pat; ++t) {
-                const PatientGeom& Q = s_geom[nwp];
-                const unsigned f0 = atomicAdd(Q.work, (unsigned)p.chunk);
-                if ((uint64_t)f0 < Q.n_hist) {
-                  fresh = f0;
-                  fresh_end = (uint32_t)min((uint64_t)f0 + (uint64_t)p.chunk, Q.n_hist);
-                  break;
-                }
-                nwp = nwp + 1 < n_pat ? nwp + 1 : 0;
-              }
-            } else {
-              const unsigned f0 = atomicAdd(p.g.work, (unsigned)p.chunk);
-              if ((uint64_t)f0 < p.g.n_hist) {
-                fresh = f0;
-                fresh_end = (uint32_t)min((uint64_t)f0 + (uint64_t)p.chunk, p.g.n_hist);
-              }
+            const unsigned f0 = atomicAdd(p.g.work, (unsigned)p.chunk);
+            if ((uint64_t)f0 < p.g.n_hist) {
+              fresh = f0;
+              fresh_end = (uint32_t)min((uint64_t)f0 + (uint64_t)p.chunk, p.g.n_hist);
             }
           }
           fresh = __shfl_sync(kFull, fresh, 0);
           fresh_end = __shfl_sync(kFull, fresh_end, 0);
-          if (MULTI) nwp = __shfl_sync(kFull, nwp, 0);
         }
         uint32_t idx = 0;
-        int qpi = MULTI ? wp : 0;
         bool got = true;
         if (lane < avail) {
           idx = pool_next + lane;
         } else if (fresh + (lane - avail) < fresh_end) {
           idx = fresh + (lane - avail);
-          if (MULTI) qpi = nwp;
         } else {
           got = false;
         }
@@ -573,34 +554,31 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
           pool_next = min(fresh + (32u - avail), fresh_end);
           pool_end = fresh_end;
           drained = fresh_end == 0;
-          if (MULTI) wp = nwp;
         } else {
           pool_next += 32;
         }
         const uint32_t n_got = __popc(__ballot_sync(kFull, got));   // lanes 0 .. n_got - 1
-        const PatientGeom& GQ = MULTI ? s_geom[qpi] : p.g;
         bool has = false;
         ull* cell = nullptr;
         if (got) {
-          const uint64_t h = GQ.hist_begin + idx;
+          const uint64_t h = p.g.hist_begin + idx;
           const uint32_t slo = (uint32_t)h, shi = (uint32_t)(h >> 32);
-          const Site st = sample_site(GQ, p.key0, p.key1, slo, shi);
-          const bool o = outside_box(GQ, st.x, st.y, st.z);
+          const Site st = sample_site(p.g, p.key0, p.key1, slo, shi);
+          const bool o = outside_box(p.g, st.x, st.y, st.z);
           float ra, rb;
-          region_distance_pair(GQ, o, st.x, st.y, st.z, st.u, st.v_, st.w, ra, rb);
+          region_distance_pair(p.g, o, st.x, st.y, st.z, st.u, st.v_, st.w, ra, rb);
           float* qs = q_base + ((q_head + q_count + lane) & (kQueueCap - 1));
           uint32_t* qw = reinterpret_cast<uint32_t*>(qs);
           qs[0] = st.x; qs[kQueueCap] = st.y; qs[2 * kQueueCap] = st.z;
           qs[3 * kQueueCap] = st.u; qs[4 * kQueueCap] = st.v_; qs[5 * kQueueCap] = st.w;
           qs[6 * kQueueCap] = ra; qs[7 * kQueueCap] = rb;
           qw[8 * kQueueCap] = slo; qw[9 * kQueueCap] = shi; qw[10 * kQueueCap] = o ? 1u : 0u;
-          if (MULTI) qw[11 * kQueueCap] = (uint32_t)qpi;
-          if (GQ.source_mode == NM_SOURCE_DECAY) {
-            has = GQ.q_positron > 0;
-            cell = GQ.tally + st.v;
+          if (p.g.source_mode == NM_SOURCE_DECAY) {
+            has = p.g.q_positron > 0;
+            cell = p.g.tally + st.v;
           }
         }
-        tally_flush<WARP_AGG>(cell, has, (uint32_t)GQ.q_positron, lane);
+        tally_flush<WARP_AGG>(cell, has, (uint32_t)p.g.q_positron, lane);
         q_count += n_got;
         __syncwarp();
       }
@@ -615,7 +593,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
           ux = -site[3 * nb]; uy = -site[4 * nb]; uz = -site[5 * nb];
           e = p.e0; qe = p.q_e0; f = s_f0;
           stream = kStreamPhotonB; ctr = 0; steps = 0;
-          out = outside_box(MULTI ? s_geom[pi] : p.g, px, py, pz);
+          out = outside_box(p.g, px, py, pz);
           rem = site[6 * nb];
           if (out) f.inv_mubar = s_inv0_out;
         } else {
@@ -623,20 +601,6 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
           if (rank < n_pop) {
             const float* qs = q_base + ((q_head + rank) & (kQueueCap - 1));
             const uint32_t* qw = reinterpret_cast<const uint32_t*>(qs);
-            if (MULTI) {
-              const int npi = (int)qw[11 * kQueueCap];
-              if (npi != cpi) {
-                // counters belong to one patient: hand them over before switching
-                atomicAdd(&s_cnt[cpi][kCtrSteps], (ull)n_steps);
-                atomicAdd(&s_cnt[cpi][kCtrCompton], (ull)n_compton);
-                atomicAdd(&s_cnt[cpi][kCtrEscapes], (ull)n_esc);
-                atomicAdd(&s_cnt[cpi][kCtrEscapedUnits], escaped);
-                n_steps = n_compton = n_esc = 0;
-                escaped = 0;
-                cpi = npi;
-              }
-              pi = npi;
-            }
             px = qs[0]; py = qs[kQueueCap]; pz = qs[2 * kQueueCap];
             ux = qs[3 * kQueueCap]; uy = qs[4 * kQueueCap]; uz = qs[5 * kQueueCap];
             rem = qs[6 * kQueueCap];
@@ -646,7 +610,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
             if (out) f.inv_mubar = s_inv0_out;
             stream = kStreamPhotonA; ctr = 0; steps = 0;
             alive = true;
-            if ((MULTI ? s_geom[pi] : p.g).source_mode == NM_SOURCE_DECAY) {
+            if (p.g.source_mode == NM_SOURCE_DECAY) {
               site[0] = px; site[nb] = py; site[2 * nb] = pz;
               site[3 * nb] = ux; site[4 * nb] = uy; site[5 * nb] = uz;
               site[6 * nb] = qs[7 * kQueueCap];
@@ -1090,7 +1054,7 @@ cudaError_t launch_transport(const TransportParams& p, int grid, int block, bool
   void* args[] = {(void*)&p};
   // the history lists and the site queues take the static + dynamic total
   // past the 48 KB default
-  const size_t smem = transport_smem(block, history, beta, regroup && !history && !beta);
+  const size_t smem = transport_smem(block, history, beta, regroup && !multi && !history && !beta);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) e = cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, s);
   if (e != cudaSuccess) cudaGetLastError();  // a refused launch must not linger as the last error
@@ -1101,7 +1065,7 @@ int transport_max_blocks_per_sm(int block, bool warp_agg, bool rayleigh, bool re
                                 bool beta) {
   int n = 0;
   void* fn = pick(warp_agg, rayleigh, regroup, multi, history, beta);
-  const size_t smem = transport_smem(block, history, beta, regroup && !history && !beta);
+  const size_t smem = transport_smem(block, history, beta, regroup && !multi && !history && !beta);
   if (!fn || cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, smem) != cudaSuccess) {
     cudaGetLastError();
