@@ -59,21 +59,25 @@ CASES = [
 ]
 
 
-@pytest.fixture(params=["default", "gather"])
+@pytest.fixture(params=["default", "unpacked", "gather"])
 def conv_path(request, monkeypatch):
     # "default": single-source convolutions with 16, 32, 48 or 64 outputs take the
-    # shifted-window kernel; "gather": the im2col-gather kernel for everything.
+    # shifted-window kernel, whose 16- and 32-output forms put the three x-taps
+    # in one MMA; "unpacked": that kernel with one tap per MMA throughout;
+    # "gather": the im2col-gather kernel for everything.
+    monkeypatch.delenv("NM_CONV_GATHER", raising=False)
+    monkeypatch.delenv("NM_CONV_TILE_UNPACKED", raising=False)
     if request.param == "gather":
         monkeypatch.setenv("NM_CONV_GATHER", "1")
-    else:
-        monkeypatch.delenv("NM_CONV_GATHER", raising=False)
+    elif request.param == "unpacked":
+        monkeypatch.setenv("NM_CONV_TILE_UNPACKED", "1")
     return request.param
 
 
 def wgrad_chain(nm, conv_path, n, d, h, w, c0, c1, coarse, cout, kpad):
     """Longest chain of FP32 additions behind one weight-gradient entry."""
     m = n * d * h * w
-    tile = conv_path == "default" and c1 == 0 and not coarse and c0 % 8 == 0 and cout in (16, 32)
+    tile = conv_path != "gather" and c1 == 0 and not coarse and c0 % 8 == 0 and cout in (16, 32)
     if tile:
         # per CTA: its tiles x 39 K-steps of 16 voxel rows in TMEM; then 8
         # runs of up to 19 CTAs and the 8 runs (the reduction), and the bias

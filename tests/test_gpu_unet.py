@@ -187,12 +187,18 @@ def _oracle_box(torch, dn, params, dose, den, act, s, a, corner, dims):
     return y[0]
 
 
-@pytest.mark.parametrize("budget", [0, 48 * 32 * 24])
-def test_apply_whole_volume_matches_oracle(env, budget):
+@pytest.mark.parametrize("budget,form", [(0, "packed"), (48 * 32 * 24, "packed"), (0, "unpacked")])
+def test_apply_whole_volume_matches_oracle(env, budget, form, monkeypatch):
     """Whole-volume inference on a non-cubic body box (one pass, and in z slabs
     under a small voxel budget) against the FP64 oracle U-Net run on the same
-    boxes; outside the body box the input is returned unchanged."""
+    boxes; outside the body box the input is returned unchanged.  "unpacked"
+    runs the 16- and 32-output convolutions (the fused head among them) with
+    one tap per MMA instead of three."""
     torch, nm, dn = env
+    if form == "unpacked":
+        monkeypatch.setenv("NM_CONV_TILE_UNPACKED", "1")
+    else:
+        monkeypatch.delenv("NM_CONV_TILE_UNPACKED", raising=False)
     rng = np.random.default_rng(11)
     shape = (20, 28, 36)
     body = ((4, 16), (6, 22), (5, 31))
