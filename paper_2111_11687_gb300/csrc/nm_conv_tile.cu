@@ -23,6 +23,17 @@
 //             BF16, 16-byte stores; then they release the accumulator.
 // A ring of shared-memory stages and two TMEM accumulators (one when they do
 // not fit) let loads, MMAs and the epilogue of consecutive tiles overlap.
+//
+// Packed variant (16 and 32 outputs): an MMA of N = Cout is as slow as one of
+// N = 128, bound by reading its 128-row voxel operand from shared memory, so
+// the three x-taps of each (dz, dy) share one MMA of N = 3 Cout: its A operand
+// is the tile shifted for dx = -1, and its B operand the three taps' weight
+// rows, which lie next to each other in the weight image.  Column block j of
+// the accumulator then holds tap dx = j - 1 evaluated one row too early per
+// unit of dx, and the epilogue adds rows r, r + 1 and r + 2 of the three
+// blocks (two warp shuffles per output; the two rows past each warp's last
+// lane come from the next warp through shared memory): 9 MMAs per 128 rows and
+// chunk instead of 27.
 // Every wait is bounded; a time-out sets NM_DEV_TIMEOUT, drains the copies
 // and MMAs in flight and frees the tensor memory.
 #include <cuda.h>
@@ -30,6 +41,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <mutex>
 
 #include "nm_internal.cuh"
@@ -49,13 +61,16 @@ constexpr long long kWaitCycles = 4ll << 30;
 // Every 128-row M-tile accumulates its 27 taps in order, so the M-tiles are
 // the independent MMA chains in flight: 16-output layers, whose small MMAs
 // are bound by that chain latency, take deeper tiles (more M-tiles).
-template <int COUT, int TZ, bool SWZ>
+template <int COUT, int TZ, bool SWZ, bool PACK = false>
 struct TileLayout {
   static constexpr int PX = TX + 2, PY = TY + 2, PZ = TZ + 2;
   static constexpr int kRows = PX * PY * PZ;                // padded tile voxels
   static constexpr int kCmin = (1 * PY + 1) * PX + 1;       // first centre
   static constexpr int kCmax = (TZ * PY + TY) * PX + TX;    // last centre
-  static constexpr int kMt = (kCmax - kCmin + 1 + 127) / 128;  // 128-row MMA tiles
+  // 128-row MMA tiles; packed: two rows of slack, which the epilogue reads
+  // past the last centre
+  static constexpr int kMt = (kCmax - kCmin + 1 + (PACK ? 2 : 0) + 127) / 128;
+  static constexpr int kNcol = PACK ? 3 * COUT : COUT;      // accumulator columns per M-tile
   static constexpr int kDelta = PY * PX + PX + 1;           // largest tap shift
   static constexpr int kRowsAlloc = (kCmin + kMt * 128 + kDelta + 15) / 16 * 16;  // rows any MMA may read
   // SWZ: one 16-channel plane of 32-byte swizzled rows; else two 8-channel
@@ -67,7 +82,7 @@ struct TileLayout {
   static constexpr uint32_t kB = COUT / 8 * kSboB;          // one chunk's weights
   static constexpr uint32_t kStage = (kPlanes * kPlane + kB + 1023) / 1024 * 1024;
   static constexpr int kStages = (3 * kStage <= 220 * 1024) ? 3 : 2;
-  static constexpr int kAccCols = kMt * COUT;
+  static constexpr int kAccCols = kMt * kNcol;
   static constexpr int kNacc = 2 * kAccCols <= 512 ? 2 : 1;
   static constexpr int kNcols = kNacc * kAccCols <= 32 ? 32 : kNacc * kAccCols <= 64 ? 64
                                 : kNacc * kAccCols <= 128 ? 128 : kNacc * kAccCols <= 256 ? 256 : 512;
@@ -76,7 +91,26 @@ struct TileLayout {
   static_assert(kPlane % 256 == 0, "planes keep 256-byte (swizzle atom) alignment");
   static_assert(kAccCols <= 512, "accumulator fits the tensor memory");
   static_assert(kSmem <= 227 * 1024, "shared memory");
+  static_assert(!PACK || SWZ, "the packed variant reads three taps' rows of the swizzled weight image");
+  static_assert(!PACK || kNcol <= 256, "N of one MMA");
 };
+
+// Named barrier 1 joins the four epilogue warps (128 threads) of the packed
+// variant; epi_all is the same barrier with an AND vote, so that the warps
+// leave their loop together when a bounded wait gives up in any of them.
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ bool epi_all(bool ok) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 q, %1, 0;\n\t"
+      "bar.red.and.pred p, 1, 128, q;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(r)
+      : "r"(ok ? 1u : 0u)
+      : "memory");
+  return r != 0;
+}
 
 // Optional fused 1x1x1 head (16-output layers): instead of the activations,
 // write yh[v] = hb + x[v][0] + sum_c hw[c] * bf16(act[v][c]) (FP32), the same
@@ -99,20 +133,25 @@ struct TileGrid {
   }
 };
 
-template <int COUT, int TZ, bool SWZ>
+template <int COUT, int TZ, bool SWZ, bool PACK>
 __global__ void __launch_bounds__(kThreads, 1) conv_tile_kernel(const __grid_constant__ CUtensorMap tmx,
                                                                 const TileGrid g, int nchunks,
                                                                 const bf16* __restrict__ wt,
                                                                 const float* __restrict__ bias,
                                                                 bf16* __restrict__ y, int relu,
                                                                 const TileHead hd, uint32_t* status) {
-  typedef TileLayout<COUT, TZ, SWZ> L;
+  typedef TileLayout<COUT, TZ, SWZ, PACK> L;
+  constexpr int NC = L::kNcol;
   constexpr int S = L::kStages, NA = L::kNacc;
   constexpr int PX = L::PX, PY = L::PY, kMt = L::kMt, kCmin = L::kCmin, kCmax = L::kCmax;
   constexpr uint32_t kPlane = L::kPlane;
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t full[S], empty[S], tfull[NA], tempty[NA];
   __shared__ uint32_t s_tmem;
+  // packed: per M-tile and lane quarter, the accumulator rows of its lanes 0
+  // and 1 that the previous quarter adds past its last lane (block 1 of lane
+  // 0, block 2 of lanes 0 and 1)
+  __shared__ float s_xch[PACK ? kMt * 12 * COUT : 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (warp == 0) tc::tmem_alloc(&s_tmem, L::kNcols);
@@ -164,7 +203,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tile_kernel(const __grid_con
   } else if (warp == 1) {
     // ---- MMA issuer --------------------------------------------------------------
     if (lane == 0) {
-      constexpr uint32_t idesc = tc::idesc_bf16_f32(128, COUT, false, false);
+      constexpr uint32_t idesc = tc::idesc_bf16_f32(128, NC, false, false);
       long long it = 0;
       for (long long k = 0; k < my_tiles && !timeout; ++k) {
         const int a = (int)(k % NA);
@@ -190,14 +229,17 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tile_kernel(const __grid_con
           const uint64_t a_base = SWZ ? tc::smem_desc_sw32(sa, 256) : tc::smem_desc(sa, kPlane, 128);
           const uint64_t b_base = SWZ ? tc::smem_desc_sw32(sb, 256) : tc::smem_desc(sb, 128, kSboB);
           const uint32_t first = cc != 0;
+          // packed: the three x-taps of a (dz, dy) pair in one MMA, the voxel
+          // operand shifted for the first (dx = -1)
 #pragma unroll
-          for (int tap = 0; tap < 27; ++tap) {
+          for (int it2 = 0; it2 < (PACK ? 9 : 27); ++it2) {
+            const int tap = PACK ? 3 * it2 : it2;
             const int delta = ((tap / 9 - 1) * PY + ((tap / 3) % 3 - 1)) * PX + (tap % 3 - 1);
             const uint64_t bdesc = b_base + (uint64_t)((SWZ ? tap * COUT * 32 : tap * 256) >> 4);
 #pragma unroll
             for (int mt = 0; mt < kMt; ++mt) {
               const uint64_t adesc = a_base + (uint64_t)(((kCmin + mt * 128 + delta) * (int)L::kRowBytes) >> 4);
-              tc::mma_bf16(acc + mt * COUT, adesc, bdesc, idesc, tap == 0 ? first : 1u);
+              tc::mma_bf16(acc + mt * NC, adesc, bdesc, idesc, it2 == 0 ? first : 1u);
             }
           }
           tc::mma_commit(&empty[s]);
@@ -213,15 +255,42 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tile_kernel(const __grid_con
   } else {
     // ---- epilogue ----------------------------------------------------------------
     const int q = warp & 3;                  // TMEM lane quarter of this warp
+    const uint32_t lanes = tmem + ((uint32_t)(q * 32) << 16);
     for (long long k = 0; k < my_tiles; ++k) {
       const int a = (int)(k % NA);
+      bool got = tc::mbar_wait_bounded(&tfull[a], (uint32_t)((k / NA) & 1), kWaitCycles);
+      if (PACK) got = epi_all(got);          // the four warps meet at barriers below: decide together
       // the warp leaves together (tcgen05.ld below is warp-collective)
-      const bool got = tc::mbar_wait_bounded(&tfull[a], (uint32_t)((k / NA) & 1), kWaitCycles);
       if (!__all_sync(0xffffffffu, got)) {
         timeout = true;
         break;
       }
       tc::fence_after_sync();
+      const uint32_t acc = lanes + a * L::kAccCols;
+      if (PACK) {
+        // rows that the previous quarter needs past its last lane
+#pragma unroll 1
+        for (int mt = 0; mt < kMt; ++mt) {
+#pragma unroll
+          for (int cq = 0; cq < COUT / 16; ++cq) {
+            float v2[16], v3[16];
+            tc::tmem_ld16(acc + mt * NC + COUT + cq * 16, v2);
+            tc::tmem_ld16(acc + mt * NC + 2 * COUT + cq * 16, v3);
+            float* xb = s_xch + ((mt * 4 + q) * 3) * COUT + cq * 16;
+            if (lane == 0) {
+#pragma unroll
+              for (int j = 0; j < 16; ++j) {
+                xb[j] = v2[j];
+                xb[COUT + j] = v3[j];
+              }
+            } else if (lane == 1) {
+#pragma unroll
+              for (int j = 0; j < 16; ++j) xb[2 * COUT + j] = v3[j];
+            }
+          }
+        }
+        epi_sync();
+      }
       int b, x0, y0, z0;
       g.coords(blockIdx.x + k * gridDim.x, b, x0, y0, z0);
       for (int mt = 0; mt < kMt; ++mt) {
@@ -231,9 +300,33 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tile_kernel(const __grid_con
         const bool ok = c <= kCmax && px >= 1 && px <= TX && py >= 1 && py <= TY && pz >= 1 && pz <= TZ &&
                         gz < g.d && gy < g.h && gx < g.w;
         const long long vox = (((long long)b * g.d + gz) * g.h + gy) * g.w + gx;
+        // outputs cq*16 .. cq*16+15 of this lane's centre; packed: block 0 of
+        // this row plus blocks 1 and 2 of the next two rows
+        auto row16 = [&](int cq, float (&v)[16]) {
+          tc::tmem_ld16(acc + mt * NC + cq * 16, v);
+          if (PACK) {
+            float v2[16], v3[16];
+            tc::tmem_ld16(acc + mt * NC + COUT + cq * 16, v2);
+            tc::tmem_ld16(acc + mt * NC + 2 * COUT + cq * 16, v3);
+            const int nmt = q < 3 ? mt : min(mt + 1, kMt - 1), nq = q < 3 ? q + 1 : 0;
+            const float* xb = s_xch + ((nmt * 4 + nq) * 3) * COUT + cq * 16;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              float n2 = __shfl_down_sync(0xffffffffu, v2[j], 1);
+              float n3 = __shfl_down_sync(0xffffffffu, v3[j], 2);
+              if (lane == 31) {
+                n2 = xb[j];
+                n3 = xb[2 * COUT + j];
+              } else if (lane == 30) {
+                n3 = xb[COUT + j];
+              }
+              v[j] += n2 + n3;
+            }
+          }
+        };
         if (COUT == 16 && hd.hw) {
           float v[16];
-          tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + a * L::kAccCols + mt * COUT, v);
+          row16(0, v);
           if (ok) {
             float out = __ldg(hd.hw + 16) + __bfloat162float(hd.x[vox * hd.cx]);
 #pragma unroll
@@ -249,7 +342,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tile_kernel(const __grid_con
 #pragma unroll
         for (int cq = 0; cq < COUT / 16; ++cq) {
           float v[16];
-          tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + a * L::kAccCols + mt * COUT + cq * 16, v);
+          row16(cq, v);
           if (ok) {
             __align__(16) bf16 o[16];
 #pragma unroll
@@ -264,6 +357,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tile_kernel(const __grid_con
           }
         }
       }
+      if (PACK) epi_sync();                  // the exchange rows are rewritten by the next tile
       tc::fence_before_sync();
       tc::mbar_arrive(&tempty[a]);
     }
@@ -331,10 +425,10 @@ int sm_count() {
   return n;
 }
 
-template <int COUT, int TZ, bool SWZ>
+template <int COUT, int TZ, bool SWZ, bool PACK = false>
 cudaError_t launch_tile(const nm_conv3d_desc& d, const void* x, const void* w, const float* bias, void* y,
                         int relu, const TileHead& hd, uint32_t* status, cudaStream_t s) {
-  typedef TileLayout<COUT, TZ, SWZ> L;
+  typedef TileLayout<COUT, TZ, SWZ, PACK> L;
   const int cin = d.c0;
   const int nchunks = (cin + 15) / 16;
   // the input as a 5-D tensor (c, x, y, z, n); boxes of 8 channels x the padded tile
@@ -364,12 +458,12 @@ cudaError_t launch_tile(const nm_conv3d_desc& d, const void* x, const void* w, c
   g.tz = TZ;
   g.tiles_z = (d.d + TZ - 1) / TZ;
   g.tiles = (long long)g.tiles_x * g.tiles_y * g.tiles_z * g.n;
-  e = cudaFuncSetAttribute(conv_tile_kernel<COUT, TZ, SWZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(conv_tile_kernel<COUT, TZ, SWZ, PACK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)L::kSmem);
   if (e == cudaSuccess) {
     const long long grid = std::min<long long>(g.tiles, sm_count());
-    conv_tile_kernel<COUT, TZ, SWZ><<<(unsigned)grid, kThreads, L::kSmem, s>>>(map, g, nchunks, wt, bias,
-                                                                                (bf16*)y, relu, hd, status);
+    conv_tile_kernel<COUT, TZ, SWZ, PACK><<<(unsigned)grid, kThreads, L::kSmem, s>>>(map, g, nchunks, wt, bias,
+                                                                                      (bf16*)y, relu, hd, status);
     e = cudaGetLastError();
   }
   cudaFreeAsync(wt, s);
@@ -405,10 +499,19 @@ bool conv_tile_ok(const nm_conv3d_desc& d) {
          (d.cout == 16 || d.cout == 32 || d.cout == 48 || d.cout == 64);
 }
 
+// The packed variant serves 16 and 32 outputs; NM_CONV_TILE_UNPACKED=1 selects
+// the one-tap-per-MMA form instead (both are tested).
+static bool packed_tiles() {
+  const char* e = getenv("NM_CONV_TILE_UNPACKED");
+  return !(e && e[0] == '1');
+}
+
 cudaError_t conv3d_fwd_tile(const nm_conv3d_desc& d, const void* x, const void* w, const float* bias, void* y,
                             int relu, uint32_t* status, cudaStream_t s) {
   constexpr bool kSwz = true;
   const TileHead none{nullptr, nullptr, 0, nullptr};
+  if (d.cout == 16 && packed_tiles()) return launch_tile<16, 2, kSwz, true>(d, x, w, bias, y, relu, none, status, s);
+  if (d.cout == 32 && packed_tiles()) return launch_tile<32, 2, kSwz, true>(d, x, w, bias, y, relu, none, status, s);
   if (d.cout == 16) return launch_tile<16, 4, kSwz>(d, x, w, bias, y, relu, none, status, s);
   if (d.cout == 32) return launch_tile<32, 2, kSwz>(d, x, w, bias, y, relu, none, status, s);
   if (d.cout == 48) return launch_tile<48, 2, kSwz>(d, x, w, bias, y, relu, none, status, s);
@@ -420,6 +523,7 @@ cudaError_t conv3d_fwd_tile_head(const nm_conv3d_desc& d, const void* x, const v
                                  cudaStream_t s) {
   if (d.cout != 16 || !conv_tile_ok(d)) return cudaErrorInvalidValue;
   const TileHead hd{head_w, (const bf16*)xin, cx, yh};
+  if (packed_tiles()) return launch_tile<16, 2, true, true>(d, x, w, bias, nullptr, 1, hd, status, s);
   return launch_tile<16, 4, true>(d, x, w, bias, nullptr, 1, hd, status, s);
 }
 
