@@ -529,7 +529,9 @@ static nm_status autotune(nm_dose* h, Shape sh, bool free_block, bool free_chunk
   cudaEvent_t e0, e1;
   NM_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
   NM_CUDA(cudaEventCreate(&e1), "cudaEventCreate");
-  const uint64_t n_trial = 1ull << 22;
+  // 2^25 decays (several ms) per trial: shorter trials, dominated by the
+  // launch's tail, ranked shapes 1 % apart differently from run to run
+  const uint64_t n_trial = 1ull << 25;
   const uint64_t first = 1ull << 62;
   std::map<Shape, float> seen;
   auto trial = [&](const Shape& t, float* ms) -> nm_status {

@@ -19,12 +19,15 @@
 //   warp 1    one thread issues 27 taps x (tile rows / 128) MMAs per chunk
 //             into a TMEM accumulator and commits them to the stage's "empty"
 //             barrier, then the tile to the accumulator's "full" barrier;
-//   warps 2-5 the epilogue: tcgen05.ld of their TMEM lane quarter, bias, ReLU,
-//             BF16, 16-byte stores; then they release the accumulator.
+//   warps 2-9 the epilogue, two warps per TMEM lane quarter (a warp reads only
+//             its quarter, warp % 4), one taking the even 128-row M-tiles and
+//             one the odd: tcgen05.ld, bias, ReLU, BF16, 16-byte stores; then
+//             they release the accumulator.  Eight warps, not four, because the
+//             epilogue is bound by the latency of its loads and shuffles.
 // A ring of shared-memory stages and two TMEM accumulators (one when they do
 // not fit) let loads, MMAs and the epilogue of consecutive tiles overlap.
 //
-// Packed variant (16 and 32 outputs): an MMA of N = Cout is as slow as one of
+// Packed variant (16 outputs): an MMA of N = Cout is as slow as one of
 // N = 128, bound by reading its 128-row voxel operand from shared memory, so
 // the three x-taps of each (dz, dy) share one MMA of N = 3 Cout: its A operand
 // is the tile shifted for dx = -1, and its B operand the three taps' weight
@@ -54,7 +57,8 @@ typedef __nv_bfloat16 bf16;
 
 constexpr int TX = 16, TY = 16;
 constexpr uint32_t kSboB = 27 * 16 / 8 * 128;               // 8 weight rows of 27 x 16 channels
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;
+constexpr int kEpiThreads = kThreads - 64;                 // warps 2-9
 constexpr long long kWaitCycles = 4ll << 30;
 
 // Tile geometry and resources for COUT outputs and tiles TZ voxels deep.
@@ -92,22 +96,22 @@ struct TileLayout {
   static_assert(kAccCols <= 512, "accumulator fits the tensor memory");
   static_assert(kSmem <= 227 * 1024, "shared memory");
   static_assert(!PACK || SWZ, "the packed variant reads three taps' rows of the swizzled weight image");
-  static_assert(!PACK || kNcol <= 256, "N of one MMA");
+  static_assert(!PACK || COUT == 16, "the packed variant serves 16 outputs");
 };
 
-// Named barrier 1 joins the four epilogue warps (128 threads) of the packed
-// variant; epi_all is the same barrier with an AND vote, so that the warps
-// leave their loop together when a bounded wait gives up in any of them.
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+// Named barrier 1 joins the eight epilogue warps of the packed variant;
+// epi_all is the same barrier with an AND vote, so that the warps leave their
+// loop together when a bounded wait gives up in any of them.
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
 __device__ __forceinline__ bool epi_all(bool ok) {
   uint32_t r;
   asm volatile(
       "{\n\t.reg .pred p, q;\n\t"
       "setp.ne.u32 q, %1, 0;\n\t"
-      "bar.red.and.pred p, 1, 128, q;\n\t"
+      "bar.red.and.pred p, 1, %2, q;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}\n"
       : "=r"(r)
-      : "r"(ok ? 1u : 0u)
+      : "r"(ok ? 1u : 0u), "n"(kEpiThreads)
       : "memory");
   return r != 0;
 }
@@ -148,10 +152,12 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tile_kernel(const __grid_con
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t full[S], empty[S], tfull[NA], tempty[NA];
   __shared__ uint32_t s_tmem;
-  // packed: per M-tile and lane quarter, the accumulator rows of its lanes 0
+  // packed, per M-tile and lane quarter: the accumulator rows of its lanes 0
   // and 1 that the previous quarter adds past its last lane (block 1 of lane
-  // 0, block 2 of lanes 0 and 1)
-  __shared__ float s_xch[PACK ? kMt * 12 * COUT : 1];
+  // 0, block 2 of lanes 0 and 1), and the partial sums of its lanes 30 and 31,
+  // which wait for the next quarter's rows
+  __shared__ __align__(16) float s_xch[PACK ? kMt * 4 * 48 : 4];
+  __shared__ __align__(16) float s_part[PACK ? kMt * 4 * 32 : 4];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (warp == 0) tc::tmem_alloc(&s_tmem, L::kNcols);
@@ -162,7 +168,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tile_kernel(const __grid_con
     }
     for (int i = 0; i < NA; ++i) {
       tc::mbar_init(&tfull[i], 1);
-      tc::mbar_init(&tempty[i], 128);
+      tc::mbar_init(&tempty[i], kEpiThreads);
     }
     tc::mbar_fence_init();
   }
@@ -255,111 +261,193 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tile_kernel(const __grid_con
   } else {
     // ---- epilogue ----------------------------------------------------------------
     const int q = warp & 3;                  // TMEM lane quarter of this warp
+    const int half = (warp - 2) >> 2;        // even (0) or odd (1) M-tiles
     const uint32_t lanes = tmem + ((uint32_t)(q * 32) << 16);
-    for (long long k = 0; k < my_tiles; ++k) {
-      const int a = (int)(k % NA);
-      bool got = tc::mbar_wait_bounded(&tfull[a], (uint32_t)((k / NA) & 1), kWaitCycles);
-      if (PACK) got = epi_all(got);          // the four warps meet at barriers below: decide together
-      // the warp leaves together (tcgen05.ld below is warp-collective)
-      if (!__all_sync(0xffffffffu, got)) {
-        timeout = true;
-        break;
-      }
-      tc::fence_after_sync();
-      const uint32_t acc = lanes + a * L::kAccCols;
-      if (PACK) {
-        // rows that the previous quarter needs past its last lane
-#pragma unroll 1
-        for (int mt = 0; mt < kMt; ++mt) {
+    // padded-tile coordinates of centre c packed as pz << 16 | py << 8 | px,
+    // or -1 when c is not a centre of the tile
+    auto centre_code = [](int c) {
+      const int pz = c / (PY * PX), py = (c / PX) % PY, px = c % PX;
+      return c >= kCmin && c <= kCmax && px >= 1 && px <= TX && py >= 1 && py <= TY && pz >= 1 && pz <= TZ
+                 ? (pz << 16) | (py << 8) | px
+                 : -1;
+    };
+    if constexpr (PACK) {
+      // Output row r = block 0 of row r + block 1 of row r + 1 + block 2 of
+      // row r + 2.  One pass over this warp's M-tiles: lanes 0-29 finish with
+      // two shuffles; lanes 0 and 1 export the rows the previous quarter
+      // needs and lanes 30 and 31 park their partial sums; the accumulator is
+      // released; after one barrier every parked row is finished by one
+      // thread.  The next tile's opening barrier orders the reuse of the
+      // exchange rows.
+      constexpr int kSlots = (kMt + 1) / 2;  // M-tiles per warp (at most)
+      static_assert(kMt * 8 <= kEpiThreads, "one parked row per thread");
+      float bs[16], hw[17];                  // biases and the head's weights, per kernel
 #pragma unroll
-          for (int cq = 0; cq < COUT / 16; ++cq) {
-            float v2[16], v3[16];
-            tc::tmem_ld16(acc + mt * NC + COUT + cq * 16, v2);
-            tc::tmem_ld16(acc + mt * NC + 2 * COUT + cq * 16, v3);
-            float* xb = s_xch + ((mt * 4 + q) * 3) * COUT + cq * 16;
-            if (lane == 0) {
+      for (int j = 0; j < 16; ++j) bs[j] = bias ? __ldg(bias + j) : 0.0f;
 #pragma unroll
-              for (int j = 0; j < 16; ++j) {
-                xb[j] = v2[j];
-                xb[COUT + j] = v3[j];
-              }
-            } else if (lane == 1) {
+      for (int j = 0; j < 17; ++j) hw[j] = hd.hw ? __ldg(hd.hw + j) : 0.0f;
+      int pc[kSlots];                        // this lane's centre in each of its M-tiles
 #pragma unroll
-              for (int j = 0; j < 16; ++j) xb[2 * COUT + j] = v3[j];
-            }
-          }
+      for (int i = 0; i < kSlots; ++i) pc[i] = centre_code(kCmin + (2 * i + half) * 128 + q * 32 + lane);
+      const int item = threadIdx.x - 64;     // the parked row this thread finishes
+      const int imq = item >> 1, il2 = item & 1;
+      const int icode = item < kMt * 8 ? centre_code(kCmin + (imq >> 2) * 128 + (imq & 3) * 32 + 30 + il2) : -1;
+      for (long long k = 0; k < my_tiles; ++k) {
+        const int a = (int)(k % NA);
+        bool got = tc::mbar_wait_bounded(&tfull[a], (uint32_t)((k / NA) & 1), kWaitCycles);
+        got = epi_all(got);                  // the warps meet at barriers below: decide together
+        if (!got) {
+          timeout = true;
+          break;
         }
-        epi_sync();
-      }
-      int b, x0, y0, z0;
-      g.coords(blockIdx.x + k * gridDim.x, b, x0, y0, z0);
-      for (int mt = 0; mt < kMt; ++mt) {
-        const int c = kCmin + mt * 128 + q * 32 + lane;   // this lane's centre
-        const int pz = c / (PY * PX), py = (c / PX) % PY, px = c % PX;
-        const int gz = z0 + pz - 1, gy = y0 + py - 1, gx = x0 + px - 1;
-        const bool ok = c <= kCmax && px >= 1 && px <= TX && py >= 1 && py <= TY && pz >= 1 && pz <= TZ &&
-                        gz < g.d && gy < g.h && gx < g.w;
-        const long long vox = (((long long)b * g.d + gz) * g.h + gy) * g.w + gx;
-        // outputs cq*16 .. cq*16+15 of this lane's centre; packed: block 0 of
-        // this row plus blocks 1 and 2 of the next two rows
-        auto row16 = [&](int cq, float (&v)[16]) {
-          tc::tmem_ld16(acc + mt * NC + cq * 16, v);
-          if (PACK) {
-            float v2[16], v3[16];
-            tc::tmem_ld16(acc + mt * NC + COUT + cq * 16, v2);
-            tc::tmem_ld16(acc + mt * NC + 2 * COUT + cq * 16, v3);
-            const int nmt = q < 3 ? mt : min(mt + 1, kMt - 1), nq = q < 3 ? q + 1 : 0;
-            const float* xb = s_xch + ((nmt * 4 + nq) * 3) * COUT + cq * 16;
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              float n2 = __shfl_down_sync(0xffffffffu, v2[j], 1);
-              float n3 = __shfl_down_sync(0xffffffffu, v3[j], 2);
-              if (lane == 31) {
-                n2 = xb[j];
-                n3 = xb[2 * COUT + j];
-              } else if (lane == 30) {
-                n3 = xb[COUT + j];
-              }
-              v[j] += n2 + n3;
-            }
-          }
+        tc::fence_after_sync();
+        const uint32_t acc = lanes + a * L::kAccCols;
+        int b, x0, y0, z0;
+        g.coords(blockIdx.x + k * gridDim.x, b, x0, y0, z0);
+        auto voxel = [&](int code, long long& vox) {
+          const int gz = z0 + (code >> 16) - 1, gy = y0 + ((code >> 8) & 255) - 1, gx = x0 + (code & 255) - 1;
+          vox = (((long long)b * g.d + gz) * g.h + gy) * g.w + gx;
+          return code >= 0 && gz < g.d && gy < g.h && gx < g.w;
         };
-        if (COUT == 16 && hd.hw) {
-          float v[16];
-          row16(0, v);
-          if (ok) {
-            float out = __ldg(hd.hw + 16) + __bfloat162float(hd.x[vox * hd.cx]);
+        // bias, ReLU, BF16 and the 32-byte store (or the fused head's dot
+        // product, in the order of the separate head)
+        auto emit16 = [&](const float (&v)[16], long long vox) {
+          if (hd.hw) {
+            float out = hw[16] + __bfloat162float(hd.x[vox * hd.cx]);
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-              float tv = v[j] + (bias ? __ldg(bias + j) : 0.0f);
+              float tv = v[j] + bs[j];
               if (relu) tv = fmaxf(tv, 0.0f);
-              out = fmaf(__bfloat162float(__float2bfloat16_rn(tv)), __ldg(hd.hw + j), out);
+              out = fmaf(__bfloat162float(__float2bfloat16_rn(tv)), hw[j], out);
             }
             hd.yh[vox] = out;
+            return;
           }
-          continue;
-        }
+          uint32_t o[8];
 #pragma unroll
-        for (int cq = 0; cq < COUT / 16; ++cq) {
-          float v[16];
-          row16(cq, v);
-          if (ok) {
-            __align__(16) bf16 o[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              float tv = v[j] + (bias ? __ldg(bias + cq * 16 + j) : 0.0f);
-              if (relu) tv = fmaxf(tv, 0.0f);
-              o[j] = __float2bfloat16_rn(tv);
+          for (int j = 0; j < 8; ++j) {
+            float t0 = v[2 * j] + bs[2 * j], t1 = v[2 * j + 1] + bs[2 * j + 1];
+            if (relu) {
+              t0 = fmaxf(t0, 0.0f);
+              t1 = fmaxf(t1, 0.0f);
             }
-            uint4* dst = reinterpret_cast<uint4*>(y + vox * COUT + cq * 16);
-            dst[0] = reinterpret_cast<uint4*>(o)[0];
-            dst[1] = reinterpret_cast<uint4*>(o)[1];
+            const __nv_bfloat162 p = __floats2bfloat162_rn(t0, t1);   // t0 in the low half
+            o[j] = *reinterpret_cast<const uint32_t*>(&p);
           }
+          uint4* dst = reinterpret_cast<uint4*>(y + vox * 16);
+          dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
+          dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
+        };
+#pragma unroll
+        for (int i = 0; i < kSlots; ++i) {
+          const int mt = 2 * i + half;
+          if (mt >= kMt) break;              // warp-uniform
+          float v[16], v2[16], v3[16];
+          __syncwarp();
+          tc::tmem_ld16x3(acc + mt * NC, acc + mt * NC + 16, acc + mt * NC + 32, v, v2, v3);
+          float4* xb = reinterpret_cast<float4*>(s_xch + (mt * 4 + q) * 48);
+          if (lane == 0) {
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+              xb[m] = make_float4(v2[4 * m], v2[4 * m + 1], v2[4 * m + 2], v2[4 * m + 3]);
+              xb[4 + m] = make_float4(v3[4 * m], v3[4 * m + 1], v3[4 * m + 2], v3[4 * m + 3]);
+            }
+          } else if (lane == 1) {
+#pragma unroll
+            for (int m = 0; m < 4; ++m) xb[8 + m] = make_float4(v3[4 * m], v3[4 * m + 1], v3[4 * m + 2], v3[4 * m + 3]);
+          }
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const float n2 = __shfl_down_sync(0xffffffffu, v2[j], 1);
+            const float n3 = __shfl_down_sync(0xffffffffu, v3[j], 2);
+            v[j] += lane < 31 ? n2 : 0.0f;
+            v[j] += lane < 30 ? n3 : 0.0f;
+          }
+          long long vox;
+          if (lane >= 30) {
+            float4* pp = reinterpret_cast<float4*>(s_part + ((mt * 4 + q) * 2 + lane - 30) * 16);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) pp[m] = make_float4(v[4 * m], v[4 * m + 1], v[4 * m + 2], v[4 * m + 3]);
+          } else if (voxel(pc[i], vox)) {
+            emit16(v, vox);
+          }
+        }
+        tc::fence_before_sync();
+        tc::mbar_arrive(&tempty[a]);         // the accumulator has been read
+        epi_sync();
+        long long vox;
+        if (voxel(icode, vox)) {             // the last quarter's parked rows are never centres
+          const float4* xb = reinterpret_cast<const float4*>(s_xch + (imq + 1) * 48);
+          const float4* pp = reinterpret_cast<const float4*>(s_part + item * 16);
+          float v[16];
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            const float4 p = pp[m];
+            if (il2) {                       // lane 31: rows r + 1 and r + 2 are the next quarter's lanes 0, 1
+              const float4 n2 = xb[m], n3 = xb[8 + m];
+              v[4 * m] = (p.x + n2.x) + n3.x;
+              v[4 * m + 1] = (p.y + n2.y) + n3.y;
+              v[4 * m + 2] = (p.z + n2.z) + n3.z;
+              v[4 * m + 3] = (p.w + n2.w) + n3.w;
+            } else {                         // lane 30: row r + 2 is the next quarter's lane 0
+              const float4 n3 = xb[4 + m];
+              v[4 * m] = p.x + n3.x;
+              v[4 * m + 1] = p.y + n3.y;
+              v[4 * m + 2] = p.z + n3.z;
+              v[4 * m + 3] = p.w + n3.w;
+            }
+          }
+          emit16(v, vox);
         }
       }
-      if (PACK) epi_sync();                  // the exchange rows are rewritten by the next tile
-      tc::fence_before_sync();
-      tc::mbar_arrive(&tempty[a]);
+    } else {
+      for (long long k = 0; k < my_tiles; ++k) {
+        const int a = (int)(k % NA);
+        // the warp leaves together (tcgen05.ld below is warp-collective)
+        if (!__all_sync(0xffffffffu, tc::mbar_wait_bounded(&tfull[a], (uint32_t)((k / NA) & 1), kWaitCycles))) {
+          timeout = true;
+          break;
+        }
+        tc::fence_after_sync();
+        const uint32_t acc = lanes + a * L::kAccCols;
+        int b, x0, y0, z0;
+        g.coords(blockIdx.x + k * gridDim.x, b, x0, y0, z0);
+        for (int mt = half; mt < kMt; mt += 2) {
+          const int code = centre_code(kCmin + mt * 128 + q * 32 + lane);   // this lane's centre
+          const int gz = z0 + (code >> 16) - 1, gy = y0 + ((code >> 8) & 255) - 1, gx = x0 + (code & 255) - 1;
+          const long long vox = (((long long)b * g.d + gz) * g.h + gy) * g.w + gx;
+          const bool ok = code >= 0 && gz < g.d && gy < g.h && gx < g.w;
+#pragma unroll
+          for (int cq = 0; cq < COUT / 16; ++cq) {
+            float v[16];
+            __syncwarp();
+            tc::tmem_ld16(acc + mt * NC + cq * 16, v);
+            if (ok && COUT == 16 && hd.hw) {  // fused head: the order of the separate head
+              float out = __ldg(hd.hw + 16) + __bfloat162float(hd.x[vox * hd.cx]);
+#pragma unroll
+              for (int j = 0; j < 16; ++j) {
+                float tv = v[j] + (bias ? __ldg(bias + j) : 0.0f);
+                if (relu) tv = fmaxf(tv, 0.0f);
+                out = fmaf(__bfloat162float(__float2bfloat16_rn(tv)), __ldg(hd.hw + j), out);
+              }
+              hd.yh[vox] = out;
+            } else if (ok) {
+              __align__(16) bf16 o[16];
+#pragma unroll
+              for (int j = 0; j < 16; ++j) {
+                float tv = v[j] + (bias ? __ldg(bias + cq * 16 + j) : 0.0f);
+                if (relu) tv = fmaxf(tv, 0.0f);
+                o[j] = __float2bfloat16_rn(tv);
+              }
+              uint4* dst = reinterpret_cast<uint4*>(y + vox * COUT + cq * 16);
+              dst[0] = reinterpret_cast<uint4*>(o)[0];
+              dst[1] = reinterpret_cast<uint4*>(o)[1];
+            }
+          }
+        }
+        tc::fence_before_sync();
+        tc::mbar_arrive(&tempty[a]);
+      }
     }
   }
   if (timeout) atomicOr(status, NM_DEV_TIMEOUT);
@@ -499,8 +587,11 @@ bool conv_tile_ok(const nm_conv3d_desc& d) {
          (d.cout == 16 || d.cout == 32 || d.cout == 48 || d.cout == 64);
 }
 
-// The packed variant serves 16 and 32 outputs; NM_CONV_TILE_UNPACKED=1 selects
-// the one-tap-per-MMA form instead (both are tested).
+// The packed variant serves 16 outputs; NM_CONV_TILE_UNPACKED=1 selects the
+// one-tap-per-MMA form instead (both are tested).  With 32 outputs the packed
+// form measured no faster: its accumulators (N = 96 per M-tile) leave room for
+// one in the tensor memory, so the MMAs of a tile wait for the previous
+// tile's epilogue.
 static bool packed_tiles() {
   const char* e = getenv("NM_CONV_TILE_UNPACKED");
   return !(e && e[0] == '1');
@@ -511,7 +602,6 @@ cudaError_t conv3d_fwd_tile(const nm_conv3d_desc& d, const void* x, const void* 
   constexpr bool kSwz = true;
   const TileHead none{nullptr, nullptr, 0, nullptr};
   if (d.cout == 16 && packed_tiles()) return launch_tile<16, 2, kSwz, true>(d, x, w, bias, y, relu, none, status, s);
-  if (d.cout == 32 && packed_tiles()) return launch_tile<32, 2, kSwz, true>(d, x, w, bias, y, relu, none, status, s);
   if (d.cout == 16) return launch_tile<16, 4, kSwz>(d, x, w, bias, y, relu, none, status, s);
   if (d.cout == 32) return launch_tile<32, 2, kSwz>(d, x, w, bias, y, relu, none, status, s);
   if (d.cout == 48) return launch_tile<48, 2, kSwz>(d, x, w, bias, y, relu, none, status, s);

@@ -62,8 +62,8 @@ CASES = [
 @pytest.fixture(params=["default", "unpacked", "gather"])
 def conv_path(request, monkeypatch):
     # "default": single-source convolutions with 16, 32, 48 or 64 outputs take the
-    # shifted-window kernel, whose 16- and 32-output forms put the three x-taps
-    # in one MMA; "unpacked": that kernel with one tap per MMA throughout;
+    # shifted-window kernel, whose 16-output form puts the three x-taps in one
+    # MMA; "unpacked": that kernel with one tap per MMA throughout;
     # "gather": the im2col-gather kernel for everything.
     monkeypatch.delenv("NM_CONV_GATHER", raising=False)
     monkeypatch.delenv("NM_CONV_TILE_UNPACKED", raising=False)

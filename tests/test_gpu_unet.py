@@ -192,8 +192,8 @@ def test_apply_whole_volume_matches_oracle(env, budget, form, monkeypatch):
     """Whole-volume inference on a non-cubic body box (one pass, and in z slabs
     under a small voxel budget) against the FP64 oracle U-Net run on the same
     boxes; outside the body box the input is returned unchanged.  "unpacked"
-    runs the 16- and 32-output convolutions (the fused head among them) with
-    one tap per MMA instead of three."""
+    runs the 16-output convolutions (the fused head among them) with one tap
+    per MMA instead of three."""
     torch, nm, dn = env
     if form == "unpacked":
         monkeypatch.setenv("NM_CONV_TILE_UNPACKED", "1")
