@@ -15,6 +15,10 @@
 // read).  Per tile 9 (dy, dz) groups x 39 K-steps of 16 voxel rows; X moves
 // by the group's (dz PY + dy) PX rows.  N = 16, 32 or 48 input channels per
 // MMA; the groups' accumulators stay in TMEM across all of a CTA's tiles.
+// With one input chunk (N = 16) the three (dy) groups of one dz read X at
+// shifts PX rows apart, so one MMA of N = 48 covers them: its B operand is
+// three 16-channel atoms of the same chunk at a leading-byte offset of PX
+// rows (dy = -1, 0, +1), and a tile takes 3 x 39 MMAs instead of 9 x 39.
 //
 // Persistent, warp-specialised (one CTA per SM), passes over groups of input
 // chunks (and of (dy, dz) groups where TMEM needs it):
@@ -31,6 +35,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <mutex>
 
 #include "nm_internal.cuh"
@@ -71,10 +76,16 @@ static_assert(kXRows >= kRows && kYRows >= kYBox, "tile rows");
 // issued (their rate, not the tensor math, bounds these small GEMMs); the
 // (dy, dz) groups of a pass are limited by TMEM (groups x output halves x
 // 16 G columns <= 512).
-template <int COUT, int G>
+// DY: one chunk, the three dy groups of a dz in one MMA (groups are then the
+// three dz, N = 48).
+template <int COUT, int G, bool DY = false>
 struct WLayout {
+  static_assert(!DY || G == 1, "dy packing takes one input chunk per MMA");
   static constexpr int kYAtoms = COUT / 16;
-  static constexpr int kGroups = 512 / (16 * G * kYAtoms) < 9 ? 512 / (16 * G * kYAtoms) : 9;
+  static constexpr int kN = DY ? 48 : 16 * G;             // accumulator columns per group and output atom
+  static constexpr int kGroups = DY ? 3 : 512 / (16 * G * kYAtoms) < 9 ? 512 / (16 * G * kYAtoms) : 9;
+  static constexpr int kAllGroups = DY ? 3 : 9;
+  static_assert(kGroups * kYAtoms * kN <= 512, "accumulators fit the tensor memory");
   static constexpr uint32_t kUsed = kYAtoms * kYBytes + G * kXBytes;
   static constexpr uint32_t kSpan = kUsed;
   static constexpr uint32_t kStage = (kSpan + 1023) / 1024 * 1024;
@@ -100,13 +111,13 @@ __device__ __forceinline__ uint64_t desc_mn_sw32(uint32_t saddr, uint32_t lbo, u
   return tc::smem_desc(saddr, lbo, sbo) | ((uint64_t)6 << 61);
 }
 
-template <int COUT, int G>
+template <int COUT, int G, bool DY>
 __global__ void __launch_bounds__(kThreads, 1) wgrad_tile_kernel(const __grid_constant__ CUtensorMap tmx,
                                                                  const __grid_constant__ CUtensorMap tmy,
                                                                  const WGrid g, float* __restrict__ part,
                                                                  uint32_t* status) {
-  typedef WLayout<COUT, G> L;
-  constexpr int S = L::kStages, GP = L::kGroups;
+  typedef WLayout<COUT, G, DY> L;
+  constexpr int S = L::kStages, GP = L::kGroups, NG = L::kAllGroups, NN = L::kN;
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t full[S], ready[S], empty[S], acc_full, acc_empty;
   __shared__ uint32_t s_tmem;
@@ -114,7 +125,7 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_tile_kernel(const __grid_co
   const int nchunks = (g.cin + 15) / 16;
   const long long my_tiles = g.tiles > blockIdx.x ? (g.tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   // passes: groups of G input chunks x runs of GP (dy, dz) groups
-  const int n_tg = (9 + GP - 1) / GP;
+  const int n_tg = (NG + GP - 1) / GP;
   const int passes = (nchunks + G - 1) / G * n_tg;
 
   if (warp == 0) tc::tmem_alloc(&s_tmem, 512);
@@ -182,8 +193,8 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_tile_kernel(const __grid_co
       long long it = 0;
       for (int ps = 0; ps < passes && !timeout; ++ps) {
         const int c0 = ps / n_tg * G, na = min(G, nchunks - c0);
-        const int g0 = ps % n_tg * GP, g1 = min(9, g0 + GP);
-        const uint32_t idesc = tc::idesc_bf16_f32(64, 16 * na, true, true);
+        const int g0 = ps % n_tg * GP, g1 = min(NG, g0 + GP);
+        const uint32_t idesc = tc::idesc_bf16_f32(64, DY ? 48 : 16 * na, true, true);
         // the previous pass's accumulators have been read out
         if (ps > 0 && !tc::mbar_wait_bounded(&acc_empty, (uint32_t)((ps - 1) & 1), kWaitCycles)) {
           timeout = true;
@@ -202,14 +213,15 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_tile_kernel(const __grid_co
           const uint32_t first = k == 0 ? 0u : 1u;
           for (int ks = 0; ks < kKSteps3; ++ks) {
             for (int g = g0; g < g1; ++g) {
-              // group g = (dz + 1) 3 + (dy + 1); X rows from kCmin - 1 + shift
-              const int shift = ((g / 3 - 1) * PY + (g % 3 - 1)) * PX;
-              const uint64_t bdesc = desc_mn_sw32(sx + (kCmin - 1 + shift + ks * 16) * 32, kXBytes, 256);
+              // group g = (dz + 1) 3 + (dy + 1), X rows from kCmin - 1 + shift;
+              // DY: group g = dz + 1, atoms dy = -1, 0, +1 from the dy = -1 shift
+              const int shift = DY ? ((g - 1) * PY - 1) * PX : ((g / 3 - 1) * PY + (g % 3 - 1)) * PX;
+              const uint64_t bdesc =
+                  desc_mn_sw32(sx + (kCmin - 1 + shift + ks * 16) * 32, DY ? PX * 32 : kXBytes, 256);
 #pragma unroll
               for (int h = 0; h < L::kYAtoms; ++h) {
                 const uint64_t adesc = desc_mn_sw32(sy + h * kYBytes + (kARow0 + ks * 16) * 32, 32, 256);
-                tc::mma_bf16(tmem + ((g - g0) * L::kYAtoms + h) * 16 * G, adesc, bdesc, idesc,
-                             ks == 0 ? first : 1u);
+                tc::mma_bf16(tmem + ((g - g0) * L::kYAtoms + h) * NN, adesc, bdesc, idesc, ks == 0 ? first : 1u);
               }
             }
           }
@@ -227,7 +239,7 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_tile_kernel(const __grid_co
     long long it = 0;
     for (int ps = 0; ps < passes && !timeout; ++ps) {
       const int c0 = ps / n_tg * G, na = min(G, nchunks - c0);
-      const int g0 = ps % n_tg * GP, g1 = min(9, g0 + GP);
+      const int g0 = ps % n_tg * GP, g1 = min(NG, g0 + GP);
       for (long long k = 0; k < my_tiles; ++k, ++it) {
         const int s = (int)(it % S);
         const bool got = tc::mbar_wait_bounded(&full[s], (uint32_t)((it / S) & 1), kWaitCycles);
@@ -265,15 +277,18 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_tile_kernel(const __grid_co
         tc::fence_after_sync();
         float* dst = part + (size_t)blockIdx.x * g.kpad * COUT;
         for (int gg = g0; gg < g1; ++gg) {
-          const int tap = gg * 3 + (2 - q);   // (dz + 1) 9 + (dy + 1) 3 + (dx + 1)
           for (int h = 0; h < L::kYAtoms; ++h)
-            for (int a = 0; a < na; ++a) {
+            for (int a = 0; a < (DY ? 3 : na); ++a) {
+              // the column atom a is input chunk c0 + a, or with DY tap dy = a - 1
+              const int grp = DY ? gg * 3 + a : gg;          // (dz + 1) 3 + (dy + 1)
+              const int tap = grp * 3 + (2 - q);             // (dz + 1) 9 + (dy + 1) 3 + (dx + 1)
+              const int cc = DY ? c0 : c0 + a;
               float v[16];
-              tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + ((gg - g0) * L::kYAtoms + h) * 16 * G + a * 16, v);
+              tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + ((gg - g0) * L::kYAtoms + h) * NN + a * 16, v);
               if (lane < 16)
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                  const int ci = (c0 + a) * 16 + j;
+                  const int ci = cc * 16 + j;
                   if (ci < g.cin) dst[(size_t)(tap * g.cin + ci) * COUT + h * 16 + lane] = v[j];
                 }
             }
@@ -393,10 +408,10 @@ bool encode(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap* map, const void*
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int COUT, int G>
+template <int COUT, int G, bool DY = false>
 cudaError_t launch_wgrad_tile(const nm_conv3d_desc& d, const void* x, const void* dy, float* dw, float* db,
                               void* workspace, uint32_t* status, cudaStream_t s) {
-  typedef WLayout<COUT, G> L;
+  typedef WLayout<COUT, G, DY> L;
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
   CUtensorMap mx, my;
@@ -413,10 +428,10 @@ cudaError_t launch_wgrad_tile(const nm_conv3d_desc& d, const void* x, const void
   const int grid = (int)std::min<long long>(g.tiles, sm_count());
   float* part = (float*)workspace;
   float* bpart = part + (size_t)grid * g.kpad * COUT;
-  cudaError_t e = cudaFuncSetAttribute(wgrad_tile_kernel<COUT, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(wgrad_tile_kernel<COUT, G, DY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)L::kSmem);
   if (e != cudaSuccess) return e;
-  wgrad_tile_kernel<COUT, G><<<grid, kThreads, L::kSmem, s>>>(mx, my, g, part, status);
+  wgrad_tile_kernel<COUT, G, DY><<<grid, kThreads, L::kSmem, s>>>(mx, my, g, part, status);
   const long long n = (long long)g.kpad * COUT;
   wgrad_tile_reduce<<<(unsigned)((n + 31) / 32), 256, 0, s>>>(part, grid, g.kpad, 27 * d.c0, COUT, dw);
   if (db) {
@@ -441,11 +456,17 @@ cudaError_t conv3d_wgrad_tile(const nm_conv3d_desc& d, const void* x, const void
                               void* workspace, uint32_t* status, cudaStream_t s) {
   // input-channel atoms per MMA: as many as the input has, up to three
   const int nchunks = (d.c0 + 15) / 16;
+  // one chunk: the three dy groups of a dz share an MMA, unless
+  // NM_WGRAD_TILE_UNPACKED=1 (both forms are tested)
+  const char* env = getenv("NM_WGRAD_TILE_UNPACKED");
+  const bool dyp = !(env && env[0] == '1');
   if (d.cout == 16) {
+    if (nchunks == 1 && dyp) return launch_wgrad_tile<16, 1, true>(d, x, dy, dw, db, workspace, status, s);
     if (nchunks == 1) return launch_wgrad_tile<16, 1>(d, x, dy, dw, db, workspace, status, s);
     if (nchunks == 2) return launch_wgrad_tile<16, 2>(d, x, dy, dw, db, workspace, status, s);
     return launch_wgrad_tile<16, 3>(d, x, dy, dw, db, workspace, status, s);
   }
+  if (nchunks == 1 && dyp) return launch_wgrad_tile<32, 1, true>(d, x, dy, dw, db, workspace, status, s);
   if (nchunks == 1) return launch_wgrad_tile<32, 1>(d, x, dy, dw, db, workspace, status, s);
   if (nchunks == 2) return launch_wgrad_tile<32, 2>(d, x, dy, dw, db, workspace, status, s);
   return launch_wgrad_tile<32, 3>(d, x, dy, dw, db, workspace, status, s);

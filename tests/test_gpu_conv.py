@@ -63,14 +63,16 @@ CASES = [
 def conv_path(request, monkeypatch):
     # "default": single-source convolutions with 16, 32, 48 or 64 outputs take the
     # shifted-window kernel, whose 16-output form puts the three x-taps in one
-    # MMA; "unpacked": that kernel with one tap per MMA throughout;
-    # "gather": the im2col-gather kernel for everything.
-    monkeypatch.delenv("NM_CONV_GATHER", raising=False)
-    monkeypatch.delenv("NM_CONV_TILE_UNPACKED", raising=False)
+    # MMA (and whose single-chunk weight gradient the three y-taps);
+    # "unpacked": those kernels with one tap per MMA; "gather": the
+    # im2col-gather kernel for everything.
+    for v in ("NM_CONV_GATHER", "NM_CONV_TILE_UNPACKED", "NM_WGRAD_TILE_UNPACKED"):
+        monkeypatch.delenv(v, raising=False)
     if request.param == "gather":
         monkeypatch.setenv("NM_CONV_GATHER", "1")
     elif request.param == "unpacked":
         monkeypatch.setenv("NM_CONV_TILE_UNPACKED", "1")
+        monkeypatch.setenv("NM_WGRAD_TILE_UNPACKED", "1")
     return request.param
 
 
