@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tile_kernel(const __grid_con
                                                                 const TileGrid g, int nchunks,
                                                                 const bf16* __restrict__ wt,
                                                                 const float* __restrict__ bias,
-                                                                bf16* __restrict__ y, int relu,
+                                                                bf16* __restrict__ y, int ldy, int relu,
                                                                 const TileHead hd, uint32_t* status) {
   typedef TileLayout<COUT, TZ, SWZ, PACK> L;
   constexpr int NC = L::kNcol;
@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tile_kernel(const __grid_con
             const __nv_bfloat162 p = __floats2bfloat162_rn(t0, t1);   // t0 in the low half
             o[j] = *reinterpret_cast<const uint32_t*>(&p);
           }
-          uint4* dst = reinterpret_cast<uint4*>(y + vox * 16);
+          uint4* dst = reinterpret_cast<uint4*>(y + vox * ldy);
           dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
           dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
         };
@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tile_kernel(const __grid_con
                 if (relu) tv = fmaxf(tv, 0.0f);
                 o[j] = __float2bfloat16_rn(tv);
               }
-              uint4* dst = reinterpret_cast<uint4*>(y + vox * COUT + cq * 16);
+              uint4* dst = reinterpret_cast<uint4*>(y + vox * ldy + cq * 16);
               dst[0] = reinterpret_cast<uint4*>(o)[0];
               dst[1] = reinterpret_cast<uint4*>(o)[1];
             }
@@ -513,9 +513,11 @@ int sm_count() {
   return n;
 }
 
+// y: output voxel v's channels at y + v ldy (ldy = COUT, or the full width
+// when a wider convolution is computed COUT outputs at a time).
 template <int COUT, int TZ, bool SWZ, bool PACK = false>
 cudaError_t launch_tile(const nm_conv3d_desc& d, const void* x, const void* w, const float* bias, void* y,
-                        int relu, const TileHead& hd, uint32_t* status, cudaStream_t s) {
+                        int relu, const TileHead& hd, uint32_t* status, cudaStream_t s, int ldy = COUT) {
   typedef TileLayout<COUT, TZ, SWZ, PACK> L;
   const int cin = d.c0;
   const int nchunks = (cin + 15) / 16;
@@ -551,7 +553,8 @@ cudaError_t launch_tile(const nm_conv3d_desc& d, const void* x, const void* w, c
   if (e == cudaSuccess) {
     const long long grid = std::min<long long>(g.tiles, sm_count());
     conv_tile_kernel<COUT, TZ, SWZ, PACK><<<(unsigned)grid, kThreads, L::kSmem, s>>>(map, g, nchunks, wt, bias,
-                                                                                      (bf16*)y, relu, hd, status);
+                                                                                      (bf16*)y, ldy, relu, hd,
+                                                                                      status);
     e = cudaGetLastError();
   }
   cudaFreeAsync(wt, s);
@@ -584,7 +587,7 @@ cudaError_t launch_check_wait(long long max_cycles, uint32_t* status, cudaStream
 
 bool conv_tile_ok(const nm_conv3d_desc& d) {
   return d.c1 == 0 && !d.src0_coarse && d.c0 % 8 == 0 &&
-         (d.cout == 16 || d.cout == 32 || d.cout == 48 || d.cout == 64);
+         (d.cout == 16 || d.cout == 32 || d.cout == 48 || d.cout == 64 || d.cout == 96 || d.cout == 192);
 }
 
 // The packed variant serves 16 outputs; NM_CONV_TILE_UNPACKED=1 selects the
@@ -605,7 +608,21 @@ cudaError_t conv3d_fwd_tile(const nm_conv3d_desc& d, const void* x, const void* 
   if (d.cout == 16) return launch_tile<16, 4, kSwz>(d, x, w, bias, y, relu, none, status, s);
   if (d.cout == 32) return launch_tile<32, 2, kSwz>(d, x, w, bias, y, relu, none, status, s);
   if (d.cout == 48) return launch_tile<48, 2, kSwz>(d, x, w, bias, y, relu, none, status, s);
-  return launch_tile<64, 2, kSwz>(d, x, w, bias, y, relu, none, status, s);
+  if (d.cout == 64) return launch_tile<64, 2, kSwz>(d, x, w, bias, y, relu, none, status, s);
+  // 96 and 192 outputs (input gradients of the decoders' two-source layers):
+  // 48 or 64 output channels per launch, written at the full channel stride
+  const int P = d.cout == 96 ? 48 : 64;
+  nm_conv3d_desc dp = d;
+  dp.cout = P;
+  for (int p = 0; p < d.cout / P; ++p) {
+    const void* wp = (const bf16*)w + (size_t)p * P * conv_kpad(d.c0);
+    const float* bp = bias ? bias + p * P : nullptr;
+    void* yp = (bf16*)y + p * P;
+    const cudaError_t e = P == 48 ? launch_tile<48, 2, kSwz>(dp, x, wp, bp, yp, relu, none, status, s, d.cout)
+                                  : launch_tile<64, 2, kSwz>(dp, x, wp, bp, yp, relu, none, status, s, d.cout);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t conv3d_fwd_tile_head(const nm_conv3d_desc& d, const void* x, const void* w, const float* bias,

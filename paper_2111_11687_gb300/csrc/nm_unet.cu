@@ -106,68 +106,108 @@ __global__ void relu_mask_kernel(bf16* __restrict__ g, const bf16* __restrict__ 
 
 // Gradient of a decoder input [n][s]^3[c0 + c1] split into the coarse source
 // (summed over its 8 children, times the coarse activation's ReLU mask) and
-// the skip source (copied).
+// the skip source (copied); 8 channels (16 bytes) per thread, c0 and c1
+// multiples of 8.
 __global__ void split_concat_grad_kernel(const bf16* __restrict__ dx, int n, int d, int h, int w, int c0, int c1,
                                          const bf16* __restrict__ coarse_act, bf16* __restrict__ g_coarse,
                                          bf16* __restrict__ g_skip) {
   // 32-bit index arithmetic (training volumes hold far fewer than 2^32 elements)
-  const unsigned d2 = d >> 1, h2 = h >> 1, w2 = w >> 1, c = c0 + c1, uc0 = c0, uc1 = c1;
-  const unsigned nc = (unsigned)n * d2 * h2 * w2 * c0;
-  const unsigned ns = (unsigned)n * d * h * w * c1;
+  const unsigned d2 = d >> 1, h2 = h >> 1, w2 = w >> 1, c = c0 + c1, q0 = c0 / 8, q1 = c1 / 8;
+  const unsigned nc = (unsigned)n * d2 * h2 * w2 * q0;
+  const unsigned ns = (unsigned)n * d * h * w * q1;
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < nc + ns; i += gridDim.x * blockDim.x) {
     if (i < nc) {
-      const unsigned ch = i % uc0, v = i / uc0;
+      const unsigned j = i % q0, v = i / q0;
       const unsigned xx = v % w2, r = v / w2, yy = r % h2, r2 = r / h2, zz = r2 % d2, b = r2 / d2;
-      float sum = 0.0f;
+      float sum[8] = {};
       for (int dz = 0; dz < 2; ++dz)
         for (int dy = 0; dy < 2; ++dy)
-          for (int dx2 = 0; dx2 < 2; ++dx2)
-            sum += __bfloat162float(dx[((((size_t)b * d + 2 * zz + dz) * h + 2 * yy + dy) * w + 2 * xx + dx2) * c + ch]);
-      g_coarse[i] = __float2bfloat16_rn(__bfloat162float(coarse_act[i]) > 0.0f ? sum : 0.0f);
+          for (int dx2 = 0; dx2 < 2; ++dx2) {
+            const uint4 u = *reinterpret_cast<const uint4*>(
+                dx + ((((size_t)b * d + 2 * zz + dz) * h + 2 * yy + dy) * w + 2 * xx + dx2) * c + j * 8);
+            const bf16* e = reinterpret_cast<const bf16*>(&u);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) sum[k] += __bfloat162float(e[k]);
+          }
+      const uint4 av = *reinterpret_cast<const uint4*>(coarse_act + (size_t)i * 8);
+      const bf16* ae = reinterpret_cast<const bf16*>(&av);
+      uint4 o;
+      bf16* oe = reinterpret_cast<bf16*>(&o);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) oe[k] = __float2bfloat16_rn(__bfloat162float(ae[k]) > 0.0f ? sum[k] : 0.0f);
+      *reinterpret_cast<uint4*>(g_coarse + (size_t)i * 8) = o;
     } else {
       const unsigned j = i - nc;
-      g_skip[j] = dx[(size_t)(j / uc1) * c + uc0 + j % uc1];
+      *reinterpret_cast<uint4*>(g_skip + (size_t)j * 8) =
+          *reinterpret_cast<const uint4*>(dx + (size_t)(j / q1) * c + c0 + (j % q1) * 8);
     }
   }
 }
 
-// Encoder output gradient: (pool adjoint of the coarser gradient + skip gradient) * ReLU mask.
+// Encoder output gradient: (pool adjoint of the coarser gradient + skip
+// gradient) * ReLU mask; 8 channels (16 bytes) per thread.
 __global__ void encoder_grad_kernel(const bf16* __restrict__ g_coarse, const bf16* __restrict__ g_skip,
                                     const bf16* __restrict__ act, int n, int d, int h, int w, int c,
                                     bf16* __restrict__ g) {
   // 32-bit index arithmetic (training volumes hold far fewer than 2^32 elements)
-  const unsigned h2 = h >> 1, w2 = w >> 1, uc = c, uw = w, uh = h, ud = d;
-  const unsigned total = (unsigned)n * d * h * w * c;
+  const unsigned h2 = h >> 1, w2 = w >> 1, q = c / 8, uw = w, uh = h, ud = d;
+  const unsigned total = (unsigned)n * d * h * w * q;
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-    const unsigned ch = i % uc, v = i / uc;
+    const unsigned j = i % q, v = i / q;
     const unsigned xx = v % uw, r = v / uw, yy = r % uh, r2 = r / uh, zz = r2 % ud, b = r2 / ud;
-    float t = __bfloat162float(g_skip[i]);
-    t += 0.125f * __bfloat162float(g_coarse[(((b * (ud >> 1) + (zz >> 1)) * h2 + (yy >> 1)) * w2 + (xx >> 1)) * uc + ch]);
-    g[i] = __float2bfloat16_rn(__bfloat162float(act[i]) > 0.0f ? t : 0.0f);
+    const uint4 sv = *reinterpret_cast<const uint4*>(g_skip + (size_t)i * 8);
+    const uint4 cv = *reinterpret_cast<const uint4*>(
+        g_coarse + (size_t)((((b * (ud >> 1) + (zz >> 1)) * h2 + (yy >> 1)) * w2 + (xx >> 1)) * q + j) * 8);
+    const uint4 av = *reinterpret_cast<const uint4*>(act + (size_t)i * 8);
+    const bf16 *se = reinterpret_cast<const bf16*>(&sv), *ce = reinterpret_cast<const bf16*>(&cv),
+               *ae = reinterpret_cast<const bf16*>(&av);
+    uint4 o;
+    bf16* oe = reinterpret_cast<bf16*>(&o);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      float t = __bfloat162float(se[k]);
+      t += 0.125f * __bfloat162float(ce[k]);
+      oe[k] = __float2bfloat16_rn(__bfloat162float(ae[k]) > 0.0f ? t : 0.0f);
+    }
+    *reinterpret_cast<uint4*>(g + (size_t)i * 8) = o;
   }
 }
 
-// Head: y = sum_c top[v][c] hw[c] + hb + x[v][0] (FP32).  With a target, also
-// the weighted squared-error loss partials, dL/dy, d top (BF16) and the head's
-// gradient partials.  One thread per voxel; per-CTA partials summed later in
-// a fixed order.
-__global__ void head_kernel(const bf16* __restrict__ top, int c, const bf16* __restrict__ x, int cx,
-                            const float* __restrict__ hw, const float* __restrict__ target,
-                            const float* __restrict__ weight, long long m, float inv_norm,
-                            float* __restrict__ y, bf16* __restrict__ dtop, float* __restrict__ part) {
-  // part per CTA: [loss, dhb, dhw[0..c-1]]
-  extern __shared__ float red[];  // [blockDim][c + 2]
+// Head: y = sum_c top[v][c] hw[c] + hb + x[v][0] (FP32, c in order).  With a
+// target, also the weighted squared-error loss partials, dL/dy, d top (BF16)
+// and the head's gradient partials.  One thread per voxel (16-byte loads and
+// stores of its C channels); per CTA the partials of [loss, dhb, dhw[0..C-1]]
+// go through fixed warp shuffle trees and then the four warps in order, and
+// are summed over CTAs later in a fixed order.
+template <int C>
+__global__ void __launch_bounds__(128) head_kernel(const bf16* __restrict__ top, const bf16* __restrict__ x, int cx,
+                                                   const float* __restrict__ hw, const float* __restrict__ target,
+                                                   const float* __restrict__ weight, long long m, float inv_norm,
+                                                   float* __restrict__ y, bf16* __restrict__ dtop,
+                                                   float* __restrict__ part) {
+  constexpr int S = C + 2;
+  __shared__ float red[4][S];
   const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int stride = c + 2;
-  float* mine = red + threadIdx.x * stride;
-  for (int j = 0; j < stride; ++j) mine[j] = 0.0f;
+  float mine[S];
+#pragma unroll
+  for (int j = 0; j < S; ++j) mine[j] = 0.0f;
   if (v < m) {
-    float t[64];
-    float out = hw[c] + __bfloat162float(x[v * cx]);
-    for (int j = 0; j < c; ++j) {
-      t[j] = __bfloat162float(top[v * c + j]);
-      out = fmaf(t[j], hw[j], out);
+    float t[C];
+    const uint4* tp = reinterpret_cast<const uint4*>(top + v * C);
+#pragma unroll
+    for (int q = 0; q < C / 8; ++q) {
+      const uint4 u = tp[q];
+      const __nv_bfloat162* e = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float2 f = __bfloat1622float2(e[k]);
+        t[8 * q + 2 * k] = f.x;
+        t[8 * q + 2 * k + 1] = f.y;
+      }
     }
+    float out = __ldg(hw + C) + __bfloat162float(x[v * cx]);
+#pragma unroll
+    for (int j = 0; j < C; ++j) out = fmaf(t[j], __ldg(hw + j), out);
     y[v] = out;
     if (target) {
       const float wv = weight ? weight[v] : 1.0f;
@@ -175,19 +215,34 @@ __global__ void head_kernel(const bf16* __restrict__ top, int c, const bf16* __r
       const float gy = 2.0f * wv * diff * inv_norm;
       mine[0] = wv * diff * diff * inv_norm;
       mine[1] = gy;
-      for (int j = 0; j < c; ++j) {
-        mine[2 + j] = gy * t[j];
-        dtop[v * c + j] = __float2bfloat16_rn(gy * hw[j]);
+      uint4* dp = reinterpret_cast<uint4*>(dtop + v * C);
+#pragma unroll
+      for (int q = 0; q < C / 8; ++q) {
+        uint32_t o[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int j = 8 * q + 2 * k;
+          mine[2 + j] = gy * t[j];
+          mine[3 + j] = gy * t[j + 1];
+          const __nv_bfloat162 p = __floats2bfloat162_rn(gy * __ldg(hw + j), gy * __ldg(hw + j + 1));
+          o[k] = *reinterpret_cast<const uint32_t*>(&p);
+        }
+        dp[q] = make_uint4(o[0], o[1], o[2], o[3]);
       }
     }
   }
   if (!target) return;
-  __syncthreads();
-  for (int j = threadIdx.x; j < stride; j += blockDim.x) {
-    float s = 0.0f;
-    for (int t2 = 0; t2 < (int)blockDim.x; ++t2) s += red[t2 * stride + j];
-    part[(long long)blockIdx.x * stride + j] = s;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < S; ++j) {
+    float sj = mine[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sj += __shfl_xor_sync(0xffffffffu, sj, o);
+    if (lane == 0) red[wid][j] = sj;
   }
+  __syncthreads();
+  for (int j = threadIdx.x; j < S; j += blockDim.x)
+    part[(long long)blockIdx.x * S + j] = ((red[0][j] + red[1][j]) + red[2][j]) + red[3][j];
 }
 
 // out[j] = sum over blocks of part[b][j]: one warp per entry, lanes strided
@@ -414,6 +469,13 @@ struct nm_denoiser {
   uint32_t* status = nullptr;
   long long step = 0;
   int head_blocks = 0;
+  bool use_weight = false;         // the train step's loss has a per-voxel weight map
+  // Forward, head and backward of a train step as one CUDA graph (captured
+  // on a stream of the handle's own, launched on s); re-captured when a
+  // setting it bakes in changes (key).
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t train_exec = nullptr;
+  int train_key = -1;
   // Test support (nm_denoise_capture): per convolution layer, in forward
   // order, its input (decoder inputs as the concatenation [upsampled coarse |
   // skip]), its output activation and the loss gradient at its output after
@@ -438,6 +500,8 @@ struct nm_denoiser {
     f(gA); f(gB); f(gC); f(gD); f(x_in); f(y); f(target); f(weight); f(dtop); f(head_part); f(head_sum);
     f(ws);
     free_capture();
+    if (train_exec) cudaGraphExecDestroy(train_exec);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
   }
 
   void free_capture() {
@@ -612,12 +676,11 @@ nm_status head(nm_denoiser* h, bool train) {
   cudaStream_t s = h->s;
   const long long m = h->vox(0);
   const int c = h->widths[0];
-  const int threads = 128;
-  const size_t smem = (size_t)threads * (c + 2) * sizeof(float);
-  // loss normalisation: mean over all voxels of the batch
-  head_kernel<<<h->head_blocks, threads, smem, s>>>(h->db[0], c, h->x_in, h->cx, h->w + h->head_off,
-                                                    train ? h->target : nullptr, train ? h->weight : nullptr, m,
-                                                    1.0f / (float)m, h->y, h->dtop, h->head_part);
+  // loss normalisation: mean over all voxels of the batch (blocks of 128 voxels)
+  auto kern = c == 16 ? head_kernel<16> : head_kernel<32>;
+  kern<<<h->head_blocks, 128, 0, s>>>(h->db[0], h->x_in, h->cx, h->w + h->head_off, train ? h->target : nullptr,
+                                      train && h->use_weight ? h->weight : nullptr, m, 1.0f / (float)m, h->y,
+                                      h->dtop, h->head_part);
   CK(cudaGetLastError(), "head");
   if (train) {
     sum_parts_kernel<<<(c + 2 + 3) / 4, 128, 0, s>>>(h->head_part, h->head_blocks, c + 2, h->head_sum);
@@ -727,7 +790,7 @@ nm_status backward(nm_denoiser* h) {
       return st;
     }
     const long long total = h->vox(i + 1) * h->widths[i + 1] + nb;
-    split_concat_grad_kernel<<<grid1d(total), 256, 0, s>>>(h->gB, h->B, h->PD >> i, h->PH >> i, h->PW >> i,
+    split_concat_grad_kernel<<<grid1d(total / 8), 256, 0, s>>>(h->gB, h->B, h->PD >> i, h->PH >> i, h->PW >> i,
                                                            h->widths[i + 1], h->widths[i],
                                                            coarse, h->gC, h->gskip[i]);
     // gC now holds the (masked) gradient wrt the coarser output; move it to gD
@@ -740,7 +803,7 @@ nm_status backward(nm_denoiser* h) {
     const Layer& la = lay("e" + std::to_string(i) + "a");
     const long long nb = h->vox(i) * h->widths[i];
     if (i < L - 1) {
-      encoder_grad_kernel<<<grid1d(nb), 256, 0, s>>>(g, h->gskip[i], h->eb[i], h->B, h->PD >> i, h->PH >> i,
+      encoder_grad_kernel<<<grid1d(nb / 8), 256, 0, s>>>(g, h->gskip[i], h->eb[i], h->B, h->PD >> i, h->PH >> i,
                                                      h->PW >> i, h->widths[i], h->gC);
       g = h->gC;
     }
@@ -976,15 +1039,50 @@ nm_status nm_denoise_train_step(nm_denoiser* h, const uint16_t* x, const float* 
   CK(cudaMemcpyAsync(h->x_in, x, m * h->cx * 2, cudaMemcpyDeviceToDevice, s), "input");
   CK(cudaMemcpyAsync(h->target, target, m * 4, cudaMemcpyDeviceToDevice, s), "input");
   if (weight) CK(cudaMemcpyAsync(h->weight, weight, m * 4, cudaMemcpyDeviceToDevice, s), "input");
-  else {
-    std::vector<float> ones(m, 1.0f);
-    CK(cudaMemcpyAsync(h->weight, ones.data(), m * 4, cudaMemcpyHostToDevice, s), "input");
-    CK(cudaStreamSynchronize(s), "input");
-  }
+  h->use_weight = weight != nullptr;      // no map: every voxel weighs 1
   nm_status st;
-  if ((st = forward(h)) != NM_OK) return st;
-  if ((st = head(h, true)) != NM_OK) return st;
-  if ((st = backward(h)) != NM_OK) return st;
+  const char* ng = getenv("NM_DENOISE_NO_GRAPH");
+  if (h->capture || (ng && ng[0] == '1')) {
+    if ((st = forward(h)) != NM_OK) return st;
+    if ((st = head(h, true)) != NM_OK) return st;
+    if ((st = backward(h)) != NM_OK) return st;
+  } else {
+    // the settings a captured graph bakes in: the convolution forms chosen by
+    // the environment, and the weight map's presence
+    int key = h->use_weight ? 1 : 0;
+    const char* envs[] = {"NM_CONV_GATHER", "NM_CONV_TILE_UNPACKED", "NM_WGRAD_TILE_UNPACKED"};
+    for (int i = 0; i < 3; ++i) {
+      const char* e = getenv(envs[i]);
+      if (e && e[0] == '1') key |= 2 << i;
+    }
+    if (!h->train_exec || h->train_key != key) {
+      if (h->train_exec) cudaGraphExecDestroy(h->train_exec);
+      h->train_exec = nullptr;
+      if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), "graph stream");
+      CK(cudaStreamSynchronize(s), "graph capture");
+      CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), "graph capture");
+      h->s = h->cap_stream;
+      st = forward(h);
+      if (st == NM_OK) st = head(h, true);
+      if (st == NM_OK) st = backward(h);
+      h->s = s;
+      cudaGraph_t graph = nullptr;
+      const cudaError_t ec = cudaStreamEndCapture(h->cap_stream, &graph);
+      if (st != NM_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+      }
+      if (ec != cudaSuccess) return cfail(ec, "graph capture");
+      const cudaError_t ei = cudaGraphInstantiate(&h->train_exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ei != cudaSuccess) {
+        h->train_exec = nullptr;
+        return cfail(ei, "graph instantiate");
+      }
+      h->train_key = key;
+    }
+    CK(cudaGraphLaunch(h->train_exec, s), "graph launch");
+  }
   if (lr > 0.0f) {
     h->step += 1;
     // bias corrections 1 - beta^t in FP64: in FP32 the subtraction cancels

@@ -306,8 +306,8 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_tile_kernel(const __grid_co
 
 // Bias gradient db[co] = sum over voxels of dY[v][co].  Each thread sums one
 // 8-channel octet of a fixed, strided set of voxels (16-byte loads); a
-// block's threads of one octet are added in thread order, the blocks in index
-// order by bias_grad_final.
+// block's threads of one octet are added in thread order, the blocks by
+// bias_grad_final in a fixed order.
 template <int COUT>
 __global__ void __launch_bounds__(256) bias_grad_partial(const bf16* __restrict__ dy, long long m,
                                                          float* __restrict__ part) {
@@ -339,12 +339,14 @@ __global__ void __launch_bounds__(256) bias_grad_partial(const bf16* __restrict_
   }
 }
 
+// One warp per channel: lanes strided over the blocks, then a fixed tree.
 __global__ void bias_grad_final(const float* __restrict__ part, int blocks, int cout, float* __restrict__ db) {
-  const int c = threadIdx.x;
-  if (c >= cout) return;
+  const int c = blockIdx.x, lane = threadIdx.x;
   float s = 0.0f;
-  for (int b = 0; b < blocks; ++b) s += part[(size_t)b * cout + c];
-  db[c] = s;
+  for (int b = lane; b < blocks; b += 32) s += part[(size_t)b * cout + c];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) db[c] = s;
 }
 
 // dW = the CTAs' partials part[cta][k][co] summed in a fixed order: per
@@ -437,7 +439,7 @@ cudaError_t launch_wgrad_tile(const nm_conv3d_desc& d, const void* x, const void
   if (db) {
     const long long m = (long long)d.n * d.d * d.h * d.w;
     bias_grad_partial<COUT><<<kBiasBlocks, 256, 0, s>>>((const bf16*)dy, m, bpart);
-    bias_grad_final<<<1, 32, 0, s>>>(bpart, kBiasBlocks, COUT, db);
+    bias_grad_final<<<COUT, 32, 0, s>>>(bpart, kBiasBlocks, COUT, db);
   }
   return cudaGetLastError();
 }

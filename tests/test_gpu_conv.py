@@ -56,6 +56,7 @@ CASES = [
     (1, 32, 64, 48, 48, 0, 0, 32),    # several tiles per CTA and three chunks per tile
     (2, 10, 21, 19, 16, 0, 0, 48),    # 48 outputs (a decoder input's gradient), ragged tiles
     (1, 8, 20, 18, 96, 0, 0, 32),     # 96 inputs: two groups of three chunks, two passes each
+    (2, 6, 10, 12, 64, 32, 1, 32),    # decoder at level 1: its input gradient has 96 channels (2 x 48 per launch)
 ]
 
 
