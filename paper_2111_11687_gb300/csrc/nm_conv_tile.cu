@@ -19,11 +19,12 @@
 //   warp 1    one thread issues 27 taps x (tile rows / 128) MMAs per chunk
 //             into a TMEM accumulator and commits them to the stage's "empty"
 //             barrier, then the tile to the accumulator's "full" barrier;
-//   warps 2-9 the epilogue, two warps per TMEM lane quarter (a warp reads only
-//             its quarter, warp % 4), one taking the even 128-row M-tiles and
-//             one the odd: tcgen05.ld, bias, ReLU, BF16, 16-byte stores; then
-//             they release the accumulator.  Eight warps, not four, because the
-//             epilogue is bound by the latency of its loads and shuffles.
+//   warps 2-13 the epilogue, three warps per TMEM lane quarter (a warp reads
+//             only its quarter, warp % 4), warp w taking the 128-row M-tiles
+//             mt = (w - 2) / 4 modulo 3: tcgen05.ld, bias, ReLU, BF16, 16-byte
+//             stores; then they release the accumulator.  Twelve warps, not
+//             four, because the epilogue is bound by the latency of its loads
+//             and shuffles (no warp takes more than two of five M-tiles).
 // A ring of shared-memory stages and two TMEM accumulators (one when they do
 // not fit) let loads, MMAs and the epilogue of consecutive tiles overlap.
 //
@@ -57,8 +58,9 @@ typedef __nv_bfloat16 bf16;
 
 constexpr int TX = 16, TY = 16;
 constexpr uint32_t kSboB = 27 * 16 / 8 * 128;               // 8 weight rows of 27 x 16 channels
-constexpr int kThreads = 320;
-constexpr int kEpiThreads = kThreads - 64;                 // warps 2-9
+constexpr int kEpiParts = 3;                               // epilogue warps per TMEM lane quarter
+constexpr int kEpiThreads = 128 * kEpiParts;               // warps 2 .. 1 + 4 kEpiParts
+constexpr int kThreads = 64 + kEpiThreads;
 constexpr long long kWaitCycles = 4ll << 30;
 
 // Tile geometry and resources for COUT outputs and tiles TZ voxels deep.
@@ -99,7 +101,7 @@ struct TileLayout {
   static_assert(!PACK || COUT == 16, "the packed variant serves 16 outputs");
 };
 
-// Named barrier 1 joins the eight epilogue warps of the packed variant;
+// Named barrier 1 joins the epilogue warps of the packed variant;
 // epi_all is the same barrier with an AND vote, so that the warps leave their
 // loop together when a bounded wait gives up in any of them.
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
@@ -261,7 +263,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tile_kernel(const __grid_con
   } else {
     // ---- epilogue ----------------------------------------------------------------
     const int q = warp & 3;                  // TMEM lane quarter of this warp
-    const int half = (warp - 2) >> 2;        // even (0) or odd (1) M-tiles
+    const int part = (warp - 2) >> 2;        // this warp's M-tiles: mt = part modulo kEpiParts
     const uint32_t lanes = tmem + ((uint32_t)(q * 32) << 16);
     // padded-tile coordinates of centre c packed as pz << 16 | py << 8 | px,
     // or -1 when c is not a centre of the tile
@@ -279,7 +281,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tile_kernel(const __grid_con
       // released; after one barrier every parked row is finished by one
       // thread.  The next tile's opening barrier orders the reuse of the
       // exchange rows.
-      constexpr int kSlots = (kMt + 1) / 2;  // M-tiles per warp (at most)
+      constexpr int kSlots = (kMt + kEpiParts - 1) / kEpiParts;   // M-tiles per warp (at most)
       static_assert(kMt * 8 <= kEpiThreads, "one parked row per thread");
       float bs[16], hw[17];                  // biases and the head's weights, per kernel
 #pragma unroll
@@ -288,7 +290,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tile_kernel(const __grid_con
       for (int j = 0; j < 17; ++j) hw[j] = hd.hw ? __ldg(hd.hw + j) : 0.0f;
       int pc[kSlots];                        // this lane's centre in each of its M-tiles
 #pragma unroll
-      for (int i = 0; i < kSlots; ++i) pc[i] = centre_code(kCmin + (2 * i + half) * 128 + q * 32 + lane);
+      for (int i = 0; i < kSlots; ++i) pc[i] = centre_code(kCmin + (kEpiParts * i + part) * 128 + q * 32 + lane);
       const int item = threadIdx.x - 64;     // the parked row this thread finishes
       const int imq = item >> 1, il2 = item & 1;
       const int icode = item < kMt * 8 ? centre_code(kCmin + (imq >> 2) * 128 + (imq & 3) * 32 + 30 + il2) : -1;
@@ -340,7 +342,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tile_kernel(const __grid_con
         };
 #pragma unroll
         for (int i = 0; i < kSlots; ++i) {
-          const int mt = 2 * i + half;
+          const int mt = kEpiParts * i + part;
           if (mt >= kMt) break;              // warp-uniform
           float v[16], v2[16], v3[16];
           __syncwarp();
@@ -412,7 +414,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tile_kernel(const __grid_con
         const uint32_t acc = lanes + a * L::kAccCols;
         int b, x0, y0, z0;
         g.coords(blockIdx.x + k * gridDim.x, b, x0, y0, z0);
-        for (int mt = half; mt < kMt; mt += 2) {
+        for (int mt = part; mt < kMt; mt += kEpiParts) {
           const int code = centre_code(kCmin + mt * 128 + q * 32 + lane);   // this lane's centre
           const int gz = z0 + (code >> 16) - 1, gy = y0 + ((code >> 8) & 255) - 1, gx = x0 + (code & 255) - 1;
           const long long vox = (((long long)b * g.d + gz) * g.h + gy) * g.w + gx;
