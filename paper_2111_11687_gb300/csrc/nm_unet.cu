@@ -748,9 +748,17 @@ nm_status backward(nm_denoiser* h) {
     CK(conv3d_fwd(bd, gout, nullptr, h->wflip, nullptr, gin, 0, h->status, s), "dgrad");
     return NM_OK;
   };
+  // the weight-gradient workspace must hold what the kernel chosen for d writes
+  auto wgrad = [&](const nm_conv3d_desc& d, const Layer& l, const bf16* x0, const bf16* x1,
+                   const bf16* gout) -> nm_status {
+    if (conv_wgrad_workspace(d) > h->ws_bytes) return fail(NM_ERR_STATE, "weight-gradient workspace too small");
+    CK(conv3d_wgrad(d, x0, x1, gout, h->g + l.w_off, h->g + l.b_off, h->ws, h->status, s), "wgrad");
+    return NM_OK;
+  };
   auto conv_back = [&](const Layer& l, const bf16* x0, const bf16* x1, const bf16* gout, bf16* gin) -> nm_status {
     // weight/bias gradients, then (if gin) the input gradient through flipped weights
-    CK(conv3d_wgrad(h->desc(l), x0, x1, gout, h->g + l.w_off, h->g + l.b_off, h->ws, h->status, s), "wgrad");
+    nm_status st = wgrad(h->desc(l), l, x0, x1, gout);
+    if (st != NM_OK) return st;
     if (gin) {
       nm_conv3d_desc fd = h->desc(l);
       CK(conv3d_flip_weights(fd, h->wb + l.w_off, h->wflip, s), "flip");
@@ -783,8 +791,7 @@ nm_status backward(nm_denoiser* h) {
     const bf16* coarse = i + 1 <= L - 2 ? h->db[i + 1] : h->eb[L - 1];
     if (use_cat(h, la)) {
       // same im2col rows, read from the materialised input
-      CK(conv3d_wgrad(single_source(h, la), h->cat[i], nullptr, h->gA, h->g + la.w_off, h->g + la.b_off, h->ws,
-                      h->status, s), "wgrad");
+      if ((st = wgrad(single_source(h, la), la, h->cat[i], nullptr, h->gA)) != NM_OK) return st;
       if ((st = conv_back_input(la, h->gA, h->gB)) != NM_OK) return st;
     } else if ((st = conv_back(la, coarse, h->eb[i], h->gA, h->gB)) != NM_OK) {
       return st;
@@ -892,7 +899,11 @@ nm_status nm_denoise_create(nm_denoiser** out, const nm_denoise_options* opts) {
   size_t ws = 0;
   for (auto& l : h->layers) {
     flip = std::max<long long>(flip, (long long)l.cin * conv_kpad(l.cout));
+    // a decoder input's weight gradient runs on the two-source description or,
+    // when its input is materialised, on the single-source one: the kernels
+    // (and workspaces) of the two differ
     ws = std::max(ws, conv_wgrad_workspace(h->desc(l)));
+    if (l.c1 > 0) ws = std::max(ws, conv_wgrad_workspace(single_source(h, l)));
   }
   h->wflip_elems = flip;
   h->ws_bytes = ws;

@@ -154,6 +154,26 @@ def test_train_step_graph_equals_direct_launches(env, weighted, monkeypatch):
     assert np.array_equal(runs[0][1], runs[1][1])
 
 
+def test_train_steps_at_the_benchmark_patch(env):
+    """Training at 64^3 x batch 4 with a weight map (the benchmark's and the
+    time-to-2 % experiment's configuration).  At this size the level-1
+    decoder input's weight gradient runs with one partial per SM, the largest
+    workspace of the network; the handle checks every weight-gradient call
+    against its workspace and raises rather than write past it."""
+    torch, nm, dn = env
+    P, B = 64, 4
+    rng = np.random.default_rng(8)
+    x = torch.from_numpy(rng.normal(0, 1, (B, P, P, P, 8)).astype(np.float32)).to(torch.bfloat16).cuda()
+    t = torch.from_numpy(rng.normal(0, 1, (B, P, P, P)).astype(np.float32)).cuda()
+    w = torch.from_numpy((rng.random((B, P, P, P)) < 0.7).astype(np.float32)).cuda()
+    net = nm.Denoiser(patch=P, batch=B, levels=4, base_width=16, seed=3, lr=1e-3)
+    losses = [net.train_step(x, t, w) for _ in range(3)]
+    flat = np.zeros(net.n_params, np.float32)
+    net.params(get=flat)
+    net.close()
+    assert np.isfinite(losses).all() and np.isfinite(flat).all()
+
+
 def test_apply_covers_the_volume(env):
     torch, nm, dn = env
     # A fresh network's head is zero: it returns its input dose channel, so a
