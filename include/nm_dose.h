@@ -326,6 +326,15 @@ nm_status nm_check_kahn(double e_mev, int64_t n, uint64_t seed, float* cos_out);
 nm_status nm_check_kn_table(double e_mev, double cut_mev, double e0_mev, int64_t n, uint64_t seed,
                             float* cos_out);
 
+/* Device memory released by destroyed handles and by the library's per-call
+ * temporaries is kept (up to 8 GiB, per device and buffer size) and handed to
+ * the next allocation of the same size on the same device, so that a handle
+ * created after one of the same grid maps no new memory.  This call returns
+ * every kept buffer to the device (cudaFree); buffers of live handles are not
+ * affected.  A failed allocation releases them by itself before it retries.
+ * Safe to call at any time from any thread. */
+void nm_release_cached_memory(void);
+
 /* Fault injection: the n-th device allocation made by the library from now
  * on (nm_dose_create and the calls it makes) fails as if the device were out
  * of memory; 0 switches it off.  The failing call returns NM_ERR_OOM and frees

@@ -129,6 +129,30 @@ std::vector<float> beta_inverse_cdf(double t_max, int z) {
 // dalloc) fails as if the device were out of memory (0 = off).
 std::atomic<int> g_fail_alloc{0};
 
+// Device buffers of handles and of per-call temporaries are recycled: dfree
+// keeps a buffer (once nothing on the device can still use it) for the next
+// dalloc of the same size on the same device, so that a handle created after
+// one of the same grid is destroyed maps no new memory.  At most kCacheBytes
+// stay cached; a failed cudaMalloc releases the cache and retries;
+// nm_release_cached_memory releases it on request.
+constexpr size_t kCacheBytes = 8ull << 30;
+struct BufferCache {
+  std::mutex mu;
+  std::map<void*, std::pair<int, size_t>> live;          // dalloc'd: device, bytes
+  std::multimap<std::pair<int, size_t>, void*> free;     // kept for reuse
+  size_t cached = 0;
+};
+BufferCache& buffer_cache() {
+  static BufferCache* c = new BufferCache();   // never destroyed: outlives every handle
+  return *c;
+}
+
+void release_cache_locked(BufferCache& c) {
+  for (auto& kv : c.free) cudaFree(kv.second);
+  c.free.clear();
+  c.cached = 0;
+}
+
 template <class T>
 cudaError_t dalloc(T** p, size_t n) {
   int k = g_fail_alloc.load();
@@ -138,7 +162,49 @@ cudaError_t dalloc(T** p, size_t n) {
     *p = nullptr;
     return cudaErrorMemoryAllocation;
   }
-  return cudaMalloc((void**)p, n * sizeof(T) > 0 ? n * sizeof(T) : 1);
+  const size_t bytes = n * sizeof(T) > 0 ? n * sizeof(T) : 1;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  BufferCache& c = buffer_cache();
+  std::lock_guard<std::mutex> lock(c.mu);
+  auto it = c.free.find(std::make_pair(dev, bytes));
+  if (it != c.free.end()) {
+    *p = (T*)it->second;
+    c.free.erase(it);
+    c.cached -= bytes;
+  } else {
+    e = cudaMalloc((void**)p, bytes);
+    if (e == cudaErrorMemoryAllocation && c.cached) {
+      cudaGetLastError();
+      release_cache_locked(c);
+      e = cudaMalloc((void**)p, bytes);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  c.live[(void*)*p] = std::make_pair(dev, bytes);
+  return cudaSuccess;
+}
+
+// Returns a dalloc'd buffer; the caller guarantees that no device work still
+// uses it (its stream was synchronised).  Other pointers are cudaFree'd.
+void dfree(void* p) {
+  if (!p) return;
+  BufferCache& c = buffer_cache();
+  std::lock_guard<std::mutex> lock(c.mu);
+  auto it = c.live.find(p);
+  if (it == c.live.end()) {
+    cudaFree(p);
+    return;
+  }
+  const std::pair<int, size_t> key = it->second;
+  c.live.erase(it);
+  if (c.cached + key.second > kCacheBytes) {
+    cudaFree(p);
+    return;
+  }
+  c.free.emplace(key, p);
+  c.cached += key.second;
 }
 
 }  // namespace
@@ -210,6 +276,7 @@ struct nm_dose {
   uint32_t* vox = nullptr;
   float* density = nullptr;
   uint8_t* labels = nullptr;
+  unsigned long long* label_bad = nullptr;   // create-time label check: lowest offending voxel
   uint4* alias = nullptr;
   int64_t n_active = 0;
   ull* tb = nullptr;
@@ -259,11 +326,12 @@ struct nm_dose {
   double batch_graph_ms = 0;      // device time of graphs launched by nm_dose_run_batch
 
   ~nm_dose() {
-    void* ptrs[] = {vox, density, labels, alias, tb, tsum, s2, kn, minv, minv_out, beta_tab, kn_inv, s2h_lo, s2h_hi, counters, work, status,
+    // nothing on the device may still use a buffer that is recycled
+    cudaStreamSynchronize(stream);
+    void* ptrs[] = {vox, density, labels, label_bad, alias, tb, tsum, s2, kn, minv, minv_out, beta_tab, kn_inv, s2h_lo, s2h_hi, counters, work, status,
                     rho_max_bits, org_s1, org_s2, organ_count, organ_partial, organ_out,
                     out_dose, out_sigma};
-    for (void* p : ptrs)
-      if (p) cudaFree(p);
+    for (void* p : ptrs) dfree(p);
     for (auto e : ev) cudaEventDestroy(e);
   }
 
@@ -463,10 +531,11 @@ nm_status nm_ct_to_phantom(const int16_t* hu, int64_t n, float* density, uint8_t
   if (!e && !dd) e = cudaMemcpyAsync(density, d, n * sizeof(float), cudaMemcpyDeviceToHost, s);
   if (!e && !dm) e = cudaMemcpyAsync(material, m, n, cudaMemcpyDeviceToHost, s);
   if (!e) e = cudaStreamSynchronize(s);
+  else cudaStreamSynchronize(s);
   if (e) st = cuda_fail(e, "nm_ct_to_phantom");
-  if (h) cudaFree(h);
-  if (d) cudaFree(d);
-  if (m) cudaFree(m);
+  dfree(h);
+  dfree(d);
+  dfree(m);
   return st;
 }
 
@@ -696,7 +765,8 @@ nm_status nm_dose_create(nm_dose** out, const nm_grid* g, const nm_materials* mt
       (e = dalloc(&h->organ_partial, (size_t)fold_blocks(V) * 2 * kLabelSlots)) ||
       (e = dalloc(&h->organ_out, 4 * kLabelSlots)))
     return bail(cuda_fail(e, "device allocation"));
-  if (labels && (e = dalloc(&h->labels, V))) return bail(cuda_fail(e, "device allocation"));
+  if (labels && ((e = dalloc(&h->labels, V)) || (e = dalloc(&h->label_bad, 1))))
+    return bail(cuda_fail(e, "device allocation"));
   {
     const std::vector<float>& kt = kn_inverse_cdf(mt->photon_cut_mev, e_top);
     h->kn_inv_lo = (float)std::log(mt->photon_cut_mev);
@@ -743,22 +813,11 @@ nm_status nm_dose_create(nm_dose** out, const nm_grid* g, const nm_materials* mt
   if (!e) e = cudaMemcpyAsync(rho_bits, h->rho_max_bits, sizeof rho_bits, cudaMemcpyDeviceToHost, s);
   if (!e) e = cudaMemcpyAsync(&st, h->status, 4, cudaMemcpyDeviceToHost, s);
   if (!e) e = cudaStreamSynchronize(s);
-  cudaFree(mat_dev);
+  else cudaStreamSynchronize(s);
+  dfree(mat_dev);
   if (e) return bail(cuda_fail(e, "nm_dose_create: upload"));
   if (st & NM_DEV_BAD_VOXEL)
     return bail(fail(NM_ERR_ARG, "density must be finite and > 0 and material < %d in every voxel", h->n_mat));
-  if (labels) {
-    // labels must be <= n_labels
-    std::vector<uint8_t> lab_host;
-    const uint8_t* lp = labels;
-    if (is_device_ptr(labels)) {
-      lab_host.resize(V);
-      if ((e = cudaMemcpy(lab_host.data(), labels, V, cudaMemcpyDeviceToHost))) return bail(cuda_fail(e, "labels"));
-      lp = lab_host.data();
-    }
-    for (int64_t i = 0; i < V; ++i)
-      if (lp[i] > o.n_labels) return bail(fail(NM_ERR_ARG, "label %d at voxel %lld exceeds n_labels", lp[i], (long long)i));
-  }
   for (int m = 0; m < NM_MAX_MATERIALS; ++m) {
     float r;
     memcpy(&r, &rho_bits[m], 4);
@@ -772,7 +831,8 @@ nm_status nm_dose_create(nm_dose** out, const nm_grid* g, const nm_materials* mt
     int* box_dev = nullptr;
     if ((e = dalloc(&box_dev, 16))) return bail(cuda_fail(e, "device allocation"));
     e = woodcock_regions(h->vox, h->nx, h->ny, h->nz, box_dev, (uint32_t*)(box_dev + 8), h->blo, h->bhi, rho_out, s);
-    cudaFree(box_dev);
+    if (e) cudaStreamSynchronize(s);   // on success it has synchronised: nothing uses the buffer
+    dfree(box_dev);
     if (e) return bail(cuda_fail(e, "tracking regions"));
   }
   std::vector<float> minv(kKnTable), minv_out(kKnTable);
@@ -789,7 +849,7 @@ nm_status nm_dose_create(nm_dose** out, const nm_grid* g, const nm_materials* mt
     float* act = nullptr;
     uint8_t* scratch = nullptr;
     if ((e = dalloc(&act, V)) || (e = dalloc(&scratch, AliasScratch::bytes(V)))) {
-      if (act) cudaFree(act);
+      dfree(act);
       return bail(cuda_fail(e, "alias scratch"));
     }
     e = cudaMemcpyAsync(act, activity, V * sizeof(float), cudaMemcpyDefault, s);
@@ -797,8 +857,9 @@ nm_status nm_dose_create(nm_dose** out, const nm_grid* g, const nm_materials* mt
     if (!e) e = build_alias_table(act, V, AliasScratch{scratch}, h->alias, &h->n_active, h->status, s);
     if (!e) e = cudaMemcpyAsync(&st, h->status, 4, cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaStreamSynchronize(s);
-    cudaFree(act);
-    cudaFree(scratch);
+    else cudaStreamSynchronize(s);
+    dfree(act);
+    dfree(scratch);
     if (e) return bail(cuda_fail(e, "alias table"));
     if (st & NM_DEV_BAD_ACTIVITY) return bail(fail(NM_ERR_ARG, "activity must be finite and >= 0"));
     if (h->n_active == 0) return bail(fail(NM_ERR_ARG, "activity map sums to zero"));
@@ -811,9 +872,20 @@ nm_status nm_dose_create(nm_dose** out, const nm_grid* g, const nm_materials* mt
   if (!e) e = cudaMemsetAsync(h->org_s1, 0, kLabelSlots * sizeof(double), s);
   if (!e) e = cudaMemsetAsync(h->org_s2, 0, kLabelSlots * sizeof(double), s);
   if (!e) e = cudaMemsetAsync(h->organ_count, 0, kLabelSlots * sizeof(long long), s);
-  if (!e && h->labels) e = launch_label_count(h->labels, V, h->organ_count, s);
+  // labels must be <= n_labels: the lowest offending voxel, found with the counts
+  unsigned long long first_bad = ~0ull;
+  if (!e && h->labels) e = cudaMemsetAsync(h->label_bad, 0xff, sizeof(unsigned long long), s);
+  if (!e && h->labels)
+    e = launch_label_count(h->labels, V, o.n_labels, h->organ_count, h->label_bad, s);
+  if (!e && h->labels)
+    e = cudaMemcpyAsync(&first_bad, h->label_bad, sizeof first_bad, cudaMemcpyDeviceToHost, s);
   if (!e) e = cudaStreamSynchronize(s);
   if (e) return bail(cuda_fail(e, "nm_dose_create: init"));
+  if (first_bad != ~0ull) {
+    uint8_t l = 0;
+    if ((e = cudaMemcpy(&l, h->labels + first_bad, 1, cudaMemcpyDeviceToHost))) return bail(cuda_fail(e, "labels"));
+    return bail(fail(NM_ERR_ARG, "label %d at voxel %lld exceeds n_labels", l, (long long)first_bad));
+  }
   nm_status cs = choose_shape(h);
   if (cs != NM_OK) return bail(cs);
   *out = h;
@@ -1587,6 +1659,12 @@ nm_status nm_check_kahn(double e_mev, int64_t n, uint64_t seed, float* cos_out) 
 }
 
 void nm_debug_fail_alloc(int32_t n) { g_fail_alloc.store(n > 0 ? n : 0); }
+
+void nm_release_cached_memory(void) {
+  BufferCache& c = buffer_cache();
+  std::lock_guard<std::mutex> lock(c.mu);
+  release_cache_locked(c);
+}
 
 nm_status nm_check_wait_timeout(int64_t max_cycles) {
   if (max_cycles < 0) return fail(NM_ERR_ARG, "max_cycles must be >= 0");

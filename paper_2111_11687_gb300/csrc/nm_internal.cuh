@@ -268,7 +268,10 @@ struct FinalizeParams {
 // Eq. 1 dose rate only into p.dose (bit-identical to launch_finalize's).
 cudaError_t launch_dose_only(const FinalizeParams& p, int sms, cudaStream_t s);
 cudaError_t launch_finalize(const FinalizeParams& p, cudaStream_t s);
-cudaError_t launch_label_count(const uint8_t* labels, int64_t V, long long* count, cudaStream_t s);
+// Voxels per label into count[kLabelSlots] (labels >= kLabelSlots count as 0),
+// and atomicMin of first_bad with every voxel index whose label exceeds n_labels.
+cudaError_t launch_label_count(const uint8_t* labels, int64_t V, int n_labels, long long* count,
+                               unsigned long long* first_bad, cudaStream_t s);
 // History-by-history sigma of the mean dose rate: sigma[v] = sqrt((S2/N -
 // (T/N)^2) / (N - 1)) * gy_a / density[v], S2 = hi * 2^64 + lo.
 cudaError_t launch_history_sigma(const ull* tsum, const ull* s2h_lo, const ull* s2h_hi, const float* density,

@@ -332,13 +332,17 @@ __global__ void region_rho_out_kernel(const uint32_t* __restrict__ vox, int nx, 
   if (threadIdx.x < NM_MAX_MATERIALS && s_max[threadIdx.x]) atomicMax(rho_max_bits + threadIdx.x, s_max[threadIdx.x]);
 }
 
-__global__ void label_count_kernel(const uint8_t* labels, int64_t V, long long* count) {
+// Voxels per label, and the lowest voxel index whose label exceeds n_labels
+// (first_bad keeps its initial value when there is none).
+__global__ void label_count_kernel(const uint8_t* labels, int64_t V, int n_labels, long long* count,
+                                   ull* first_bad) {
   __shared__ long long s[kLabelSlots];
   if (threadIdx.x < kLabelSlots) s[threadIdx.x] = 0;
   __syncthreads();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int l = labels[i];
+    if (l > n_labels) atomicMin(first_bad, (ull)i);
     atomicAdd((ull*)&s[l < kLabelSlots ? l : 0], 1ull);
   }
   __syncthreads();
@@ -449,8 +453,9 @@ void majorant_table(const MaterialCoef* mat, int n_mat, const float* rho, const 
   }
 }
 
-cudaError_t launch_label_count(const uint8_t* labels, int64_t V, long long* count, cudaStream_t s) {
-  label_count_kernel<<<grid_for(V), 256, 0, s>>>(labels, V, count);
+cudaError_t launch_label_count(const uint8_t* labels, int64_t V, int n_labels, long long* count,
+                               unsigned long long* first_bad, cudaStream_t s) {
+  label_count_kernel<<<grid_for(V), 256, 0, s>>>(labels, V, n_labels, count, first_bad);
   return cudaGetLastError();
 }
 

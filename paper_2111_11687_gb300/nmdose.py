@@ -109,6 +109,7 @@ _SIGS = {
     "nm_check_kahn": (C.c_int, [C.c_double, C.c_int64, C.c_uint64, C.c_void_p]),
     "nm_check_beta": (C.c_int, [C.c_double, C.c_int32, C.c_int64, C.c_uint64, C.c_void_p]),
     "nm_debug_fail_alloc": (None, [C.c_int32]),
+    "nm_release_cached_memory": (None, []),
     "nm_check_kn_table": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_int64, C.c_uint64, C.c_void_p]),
     "nm_check_wait_timeout": (C.c_int, [C.c_int64]),
     "nm_dose_alias_table": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -356,6 +357,12 @@ def nm_dose_reset(h):
 
 def nm_dose_destroy(h):
     load().nm_dose_destroy(h)
+
+
+def nm_release_cached_memory() -> None:
+    """Return the device buffers the library keeps for reuse (from destroyed
+    handles and per-call temporaries) to the device."""
+    load().nm_release_cached_memory()
 
 
 def nm_last_error() -> str:

@@ -40,7 +40,8 @@ def test_invalid_inputs_are_rejected(nm, case):
     elif case == "bad_material":
         mat = np.zeros(shape, np.uint8); mat[1, 1, 1] = 1
     elif case == "bad_label":
-        lab = np.zeros(shape, np.uint8); lab[0, 1, 2] = 5
+        # two offending voxels: the message names the first (flat index 8) and its label
+        lab = np.zeros(shape, np.uint8); lab[0, 1, 2] = 5; lab[3, 4, 5] = 7
         kw["n_labels"] = 3
     elif case == "batches":
         kw["batches"] = 1
@@ -50,6 +51,8 @@ def test_invalid_inputs_are_rejected(nm, case):
         _mk(nm, act, den, mat, lab, **kw)
     assert e.value.status == nm.NM_ERR_ARG
     assert nm.nm_last_error()
+    if case == "bad_label":
+        assert "label 5 at voxel 8 " in nm.nm_last_error(), nm.nm_last_error()
 
 
 def test_get_before_run_is_a_state_error(nm):
@@ -119,3 +122,31 @@ def test_allocation_failures_are_reported_and_leave_nothing_behind(nm):
     with _mk(nm) as d:
         d.run(10_000, seed=3)
         assert d.counters()["deposited"] > 0
+
+
+def test_device_buffers_are_recycled_and_released(nm):
+    """A destroyed handle's buffers stay with the library for the next handle
+    of the same grid (the memory is not returned), nm_release_cached_memory
+    gives them back, and a handle built on recycled buffers tallies exactly
+    what one on fresh buffers does."""
+    import torch
+    shape = (96, 128, 128)                           # 1.57 M voxels: about 80 MB of handle buffers
+    nm.nm_release_cached_memory()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    with _mk(nm, act=np.ones(shape, np.float32), den=np.ones(shape, np.float32),
+             mat=np.zeros(shape, np.uint8)) as d:
+        d.run(200_000, seed=4)
+        t1 = d.tally()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free0 - free1 > 40 * 2 ** 20, (free0, free1)      # kept, not returned
+    with _mk(nm, act=np.ones(shape, np.float32), den=np.ones(shape, np.float32),
+             mat=np.zeros(shape, np.uint8)) as d:
+        d.run(200_000, seed=4)
+        t2 = d.tally()
+    assert np.array_equal(t1, t2)
+    free2 = torch.cuda.mem_get_info()[0]
+    assert abs(free2 - free1) < 16 * 2 ** 20, (free1, free2)  # the second handle reused them
+    nm.nm_release_cached_memory()
+    free3 = torch.cuda.mem_get_info()[0]
+    assert free3 - free2 > 40 * 2 ** 20, (free2, free3)      # released
