@@ -470,12 +470,13 @@ struct nm_denoiser {
   long long step = 0;
   int head_blocks = 0;
   bool use_weight = false;         // the train step's loss has a per-voxel weight map
-  // Forward, head and backward of a train step as one CUDA graph (captured
-  // on a stream of the handle's own, launched on s); re-captured when a
-  // setting it bakes in changes (key).
+  // Forward, head and backward of a train step, and forward and head of
+  // nm_denoise_forward, each as one CUDA graph (captured on a stream of the
+  // handle's own, launched on s); re-captured when a setting it bakes in
+  // changes (key).
   cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t train_exec = nullptr;
-  int train_key = -1;
+  cudaGraphExec_t train_exec = nullptr, fwd_exec = nullptr;   // train step; forward + head
+  int train_key = -1, fwd_key = -1;
   // Test support (nm_denoise_capture): per convolution layer, in forward
   // order, its input (decoder inputs as the concatenation [upsampled coarse |
   // skip]), its output activation and the loss gradient at its output after
@@ -501,6 +502,7 @@ struct nm_denoiser {
     f(ws);
     free_capture();
     if (train_exec) cudaGraphExecDestroy(train_exec);
+    if (fwd_exec) cudaGraphExecDestroy(fwd_exec);
     if (cap_stream) cudaStreamDestroy(cap_stream);
   }
 
@@ -831,6 +833,52 @@ nm_status backward(nm_denoiser* h) {
 
 }  // namespace
 
+namespace {
+
+// Runs `body` (a fixed sequence of launches on h->s) as a CUDA graph captured
+// on a stream of the handle's own and launched on h->s, re-captured when its
+// key changes: `key` with the convolution forms the environment selects.
+// NM_DENOISE_NO_GRAPH=1, or test capture being on, runs body directly.
+template <class F>
+nm_status run_steps(nm_denoiser* h, cudaGraphExec_t& exec, int& key_slot, int key, F body) {
+  const char* ng = getenv("NM_DENOISE_NO_GRAPH");
+  if (h->capture || (ng && ng[0] == '1')) return body();
+  const char* envs[] = {"NM_CONV_GATHER", "NM_CONV_TILE_UNPACKED", "NM_WGRAD_TILE_UNPACKED"};
+  for (int i = 0; i < 3; ++i) {
+    const char* e = getenv(envs[i]);
+    if (e && e[0] == '1') key |= 2 << i;
+  }
+  const cudaStream_t s = h->s;
+  if (!exec || key_slot != key) {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), "graph stream");
+    CK(cudaStreamSynchronize(s), "graph capture");
+    CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), "graph capture");
+    h->s = h->cap_stream;
+    const nm_status st = body();
+    h->s = s;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(h->cap_stream, &graph);
+    if (st != NM_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (ec != cudaSuccess) return cfail(ec, "graph capture");
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+      exec = nullptr;
+      return cfail(ei, "graph instantiate");
+    }
+    key_slot = key;
+  }
+  CK(cudaGraphLaunch(exec, s), "graph launch");
+  return NM_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 void nm_denoise_options_default(nm_denoise_options* o) {
@@ -1051,49 +1099,13 @@ nm_status nm_denoise_train_step(nm_denoiser* h, const uint16_t* x, const float* 
   CK(cudaMemcpyAsync(h->target, target, m * 4, cudaMemcpyDeviceToDevice, s), "input");
   if (weight) CK(cudaMemcpyAsync(h->weight, weight, m * 4, cudaMemcpyDeviceToDevice, s), "input");
   h->use_weight = weight != nullptr;      // no map: every voxel weighs 1
-  nm_status st;
-  const char* ng = getenv("NM_DENOISE_NO_GRAPH");
-  if (h->capture || (ng && ng[0] == '1')) {
-    if ((st = forward(h)) != NM_OK) return st;
-    if ((st = head(h, true)) != NM_OK) return st;
-    if ((st = backward(h)) != NM_OK) return st;
-  } else {
-    // the settings a captured graph bakes in: the convolution forms chosen by
-    // the environment, and the weight map's presence
-    int key = h->use_weight ? 1 : 0;
-    const char* envs[] = {"NM_CONV_GATHER", "NM_CONV_TILE_UNPACKED", "NM_WGRAD_TILE_UNPACKED"};
-    for (int i = 0; i < 3; ++i) {
-      const char* e = getenv(envs[i]);
-      if (e && e[0] == '1') key |= 2 << i;
-    }
-    if (!h->train_exec || h->train_key != key) {
-      if (h->train_exec) cudaGraphExecDestroy(h->train_exec);
-      h->train_exec = nullptr;
-      if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), "graph stream");
-      CK(cudaStreamSynchronize(s), "graph capture");
-      CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), "graph capture");
-      h->s = h->cap_stream;
-      st = forward(h);
-      if (st == NM_OK) st = head(h, true);
-      if (st == NM_OK) st = backward(h);
-      h->s = s;
-      cudaGraph_t graph = nullptr;
-      const cudaError_t ec = cudaStreamEndCapture(h->cap_stream, &graph);
-      if (st != NM_OK) {
-        if (graph) cudaGraphDestroy(graph);
-        return st;
-      }
-      if (ec != cudaSuccess) return cfail(ec, "graph capture");
-      const cudaError_t ei = cudaGraphInstantiate(&h->train_exec, graph, 0);
-      cudaGraphDestroy(graph);
-      if (ei != cudaSuccess) {
-        h->train_exec = nullptr;
-        return cfail(ei, "graph instantiate");
-      }
-      h->train_key = key;
-    }
-    CK(cudaGraphLaunch(h->train_exec, s), "graph launch");
-  }
+  nm_status st = run_steps(h, h->train_exec, h->train_key, h->use_weight ? 1 : 0, [h]() -> nm_status {
+    nm_status r = forward(h);
+    if (r == NM_OK) r = head(h, true);
+    if (r == NM_OK) r = backward(h);
+    return r;
+  });
+  if (st != NM_OK) return st;
   if (lr > 0.0f) {
     h->step += 1;
     // bias corrections 1 - beta^t in FP64: in FP32 the subtraction cancels
@@ -1113,9 +1125,12 @@ nm_status nm_denoise_forward(nm_denoiser* h, const uint16_t* x, float* y) {
   cudaStream_t s = h->s;
   const long long m = h->vox(0);
   CK(cudaMemcpyAsync(h->x_in, x, m * h->cx * 2, cudaMemcpyDeviceToDevice, s), "input");
-  nm_status st;
-  if ((st = forward(h)) != NM_OK) return st;
-  if ((st = head(h, false)) != NM_OK) return st;
+  const nm_status st = run_steps(h, h->fwd_exec, h->fwd_key, 0, [h]() -> nm_status {
+    nm_status r = forward(h);
+    if (r == NM_OK) r = head(h, false);
+    return r;
+  });
+  if (st != NM_OK) return st;
   CK(cudaMemcpyAsync(y, h->y, m * 4, cudaMemcpyDeviceToDevice, s), "output");
   return check_status(h);
 }

@@ -122,10 +122,11 @@ def test_unet_training_reduces_loss(env):
 @pytest.mark.parametrize("weighted", [False, True])
 def test_train_step_graph_equals_direct_launches(env, weighted, monkeypatch):
     """The train step runs its forward, head and backward as one captured CUDA
-    graph; with NM_DENOISE_NO_GRAPH=1 the same kernels are launched one by
-    one.  Both must give bit-identical losses and parameters over several
-    Adam steps (every kernel is deterministic), with and without a weight map,
-    and a change of convolution form between steps must be picked up."""
+    graph, and the forward its forward and head; with NM_DENOISE_NO_GRAPH=1
+    the same kernels are launched one by one.  Both must give bit-identical
+    losses, parameters and forward outputs over several Adam steps (every
+    kernel is deterministic), with and without a weight map, and a change of
+    convolution form between steps must be picked up."""
     torch, nm, dn = env
     P, B = 32, 2
     rng = np.random.default_rng(4)
@@ -148,10 +149,13 @@ def test_train_step_graph_equals_direct_launches(env, weighted, monkeypatch):
             losses.append(net.train_step(xs[k % 3], ts[k % 3], wt))
         flat = np.zeros(net.n_params, np.float32)
         net.params(get=flat)
+        y = torch.empty((B, P, P, P), dtype=torch.float32, device="cuda")
+        net.forward(xs[0], y)                  # the forward is a captured graph of its own
         net.close()
-        runs.append((losses, flat))
+        runs.append((losses, flat, y.cpu().numpy()))
     assert runs[0][0] == runs[1][0]
     assert np.array_equal(runs[0][1], runs[1][1])
+    assert np.array_equal(runs[0][2], runs[1][2])
 
 
 def test_train_steps_at_the_benchmark_patch(env):
