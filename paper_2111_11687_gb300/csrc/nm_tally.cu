@@ -41,18 +41,45 @@ __global__ void __launch_bounds__(kFoldThreads) fold_kernel(const FoldParams p) 
   const int64_t v1 = v0 + kFoldTile < p.V ? v0 + kFoldTile : p.V;
   ull dep = 0;
   const double inv_nb = 1.0 / p.n_b;
-  for (int64_t v = v0 + threadIdx.x; v < v1; v += kFoldThreads) {
-    const ull t = p.tb[v];
-    if (t == 0) continue;
-    p.tb[v] = 0;
-    p.tsum[v] += t;
-    const double x = (double)t;
-    p.s2[v] += x * x * inv_nb;
-    dep += t;
-    if (p.labels) {
-      const int l = p.labels[v];
+  // A thread's voxels v0 + tid + k kFoldThreads, kFold at a time: all their
+  // loads are issued before any update (a lone load per voxel left the kernel
+  // bound by DRAM latency), and the updates then follow in voxel order, so
+  // every sum is formed exactly as one voxel at a time would.
+  constexpr int kFold = 8;
+  for (int64_t vb = v0 + threadIdx.x; vb < v1; vb += (int64_t)kFold * kFoldThreads) {
+    ull t[kFold], ts[kFold];
+    double s2v[kFold];
+    float rho[kFold];
+    int lab[kFold];
+#pragma unroll
+    for (int j = 0; j < kFold; ++j) {
+      const int64_t v = vb + (int64_t)j * kFoldThreads;
+      t[j] = v < v1 ? p.tb[v] : 0ull;
+    }
+#pragma unroll
+    for (int j = 0; j < kFold; ++j) {
+      const int64_t v = vb + (int64_t)j * kFoldThreads;
+      ts[j] = 0; s2v[j] = 0.0; rho[j] = 1.0f; lab[j] = 0;
+      if (t[j]) {
+        ts[j] = p.tsum[v];
+        s2v[j] = p.s2[v];
+        if (p.labels) {
+          lab[j] = p.labels[v];
+          rho[j] = p.density[v];
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kFold; ++j) {
+      if (!t[j]) continue;
+      const int64_t v = vb + (int64_t)j * kFoldThreads;
+      p.tb[v] = 0;
+      p.tsum[v] = ts[j] + t[j];
+      const double x = (double)t[j];
+      p.s2[v] = s2v[j] + x * x * inv_nb;
+      dep += t[j];
       // Gy per unit in FP32 (GB300's FP64 divide is slow); the sum stays FP64
-      acc[l][threadIdx.x] += x * (double)__fdiv_rn((float)p.gy_per_unit_vol, p.density[v]);
+      if (p.labels) acc[lab[j]][threadIdx.x] += x * (double)__fdiv_rn((float)p.gy_per_unit_vol, rho[j]);
     }
   }
   // deposited-energy counter (integer, so the order of the adds does not matter)
