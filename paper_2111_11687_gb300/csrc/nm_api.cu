@@ -302,6 +302,13 @@ struct nm_dose {
   ull* s2h_hi = nullptr;
   ull* counters = nullptr;     // kCtrCount
   unsigned* work = nullptr;
+  // Odd batches of a run go to a second stream with a tally and work counter
+  // of their own, so that a batch's transport starts on the SMs the previous
+  // one releases while its last photons finish (the folds stay in batch order).
+  ull* tb2 = nullptr;
+  unsigned* work2 = nullptr;
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   uint32_t* status = nullptr;
   uint32_t* rho_max_bits = nullptr;
   double* org_s1 = nullptr;
@@ -328,11 +335,15 @@ struct nm_dose {
   ~nm_dose() {
     // nothing on the device may still use a buffer that is recycled
     cudaStreamSynchronize(stream);
-    void* ptrs[] = {vox, density, labels, label_bad, alias, tb, tsum, s2, kn, minv, minv_out, beta_tab, kn_inv, s2h_lo, s2h_hi, counters, work, status,
+    if (side) cudaStreamSynchronize(side);
+    void* ptrs[] = {vox, density, labels, label_bad, alias, tb, tb2, work2, tsum, s2, kn, minv, minv_out, beta_tab, kn_inv, s2h_lo, s2h_hi, counters, work, status,
                     rho_max_bits, org_s1, org_s2, organ_count, organ_partial, organ_out,
                     out_dose, out_sigma};
     for (void* p : ptrs) dfree(p);
     for (auto e : ev) cudaEventDestroy(e);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (side) cudaStreamDestroy(side);
   }
 
   PatientGeom geom(uint64_t first, uint64_t n) const {
@@ -756,6 +767,7 @@ nm_status nm_dose_create(nm_dose** out, const nm_grid* g, const nm_materials* mt
   }
 
   if ((e = dalloc(&h->vox, V)) || (e = dalloc(&h->density, V)) || (e = dalloc(&h->tb, V)) ||
+      (e = dalloc(&h->tb2, V)) || (e = dalloc(&h->work2, 1)) ||
       (e = dalloc(&h->tsum, V)) || (e = dalloc(&h->s2, V)) || (e = dalloc(&h->kn, kKnTable)) ||
       (e = dalloc(&h->minv, kKnTable)) || (e = dalloc(&h->minv_out, kKnTable)) ||
       (e = dalloc(&h->counters, kCtrCount)) || (e = dalloc(&h->work, 1)) ||
@@ -866,6 +878,10 @@ nm_status nm_dose_create(nm_dose** out, const nm_grid* g, const nm_materials* mt
   }
 
   e = cudaMemsetAsync(h->tb, 0, V * sizeof(ull), s);
+  if (!e) e = cudaMemsetAsync(h->tb2, 0, V * sizeof(ull), s);
+  if (!e) e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+  if (!e) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+  if (!e) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
   if (!e) e = cudaMemsetAsync(h->tsum, 0, V * sizeof(ull), s);
   if (!e) e = cudaMemsetAsync(h->s2, 0, V * sizeof(double), s);
   if (!e) e = cudaMemsetAsync(h->counters, 0, kCtrCount * sizeof(ull), s);
@@ -914,28 +930,48 @@ nm_status nm_dose_run(nm_dose* h, uint64_t n, uint64_t seed) {
   fp.labels = h->labels; fp.V = h->V; fp.gy_per_unit_vol = h->gy_per_unit_vol();
   fp.organ_partial = h->organ_partial; fp.org_s1 = h->org_s1; fp.org_s2 = h->org_s2;
   fp.deposited = h->counters + kCtrDepositedUnits;
+  // Even batches run on the handle's stream, odd ones on the side stream,
+  // each with its own batch tally and work counter: a batch's transport takes
+  // the SMs the other stream's transport releases while its last photons
+  // finish.  Batch b's fold follows its transport (same stream) and the fold
+  // of batch b - 1 (an event across the streams), so the folds add the
+  // batches in order and every statistic is the one a single stream gives;
+  // batch b + 2 follows the fold of batch b, which zeroed its tally.
+  NM_CUDA(cudaEventRecord(h->ev_fork, s), "cudaEventRecord");
+  NM_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0), "cudaStreamWaitEvent");
   for (int b = 0; b < B; ++b) {
     const uint64_t nb = n / B + ((uint64_t)b < n % B ? 1 : 0);
-    NM_CUDA(cudaEventRecord(h->ev[4 * b + 0], s), "cudaEventRecord");
+    const bool odd = (b & 1) != 0;
+    cudaStream_t bs = odd ? h->side : s;
+    ull* const tally = odd ? h->tb2 : h->tb;
+    unsigned* const work = odd ? h->work2 : h->work;
+    NM_CUDA(cudaEventRecord(h->ev[4 * b + 0], bs), "cudaEventRecord");
     // A launch hands out at most 2^31 histories (32-bit work counter).
     for (uint64_t done = 0; done < nb;) {
       const uint64_t part = std::min<uint64_t>(nb - done, 1ull << 31);
-      const TransportParams p = h->params(h->id_next + done, part, seed);
-      NM_CUDA(cudaMemsetAsync(h->work, 0, sizeof(unsigned), s), "cudaMemsetAsync");
-      NM_CUDA(launch_transport(p, h->grid, h->block, h->warp_agg, h->rayleigh, h->regroup, s, false,
+      TransportParams p = h->params(h->id_next + done, part, seed);
+      p.g.tally = tally;
+      p.g.work = work;
+      NM_CUDA(cudaMemsetAsync(work, 0, sizeof(unsigned), bs), "cudaMemsetAsync");
+      NM_CUDA(launch_transport(p, h->grid, h->block, h->warp_agg, h->rayleigh, h->regroup, bs, false,
                                h->opt.history_sigma != 0),
               "transport launch");
       done += part;
     }
-    NM_CUDA(cudaEventRecord(h->ev[4 * b + 1], s), "cudaEventRecord");
+    NM_CUDA(cudaEventRecord(h->ev[4 * b + 1], bs), "cudaEventRecord");
+    if (b > 0) NM_CUDA(cudaStreamWaitEvent(bs, h->ev[4 * (b - 1) + 3], 0), "cudaStreamWaitEvent");
     fp.n_b = (double)nb;
-    NM_CUDA(cudaEventRecord(h->ev[4 * b + 2], s), "cudaEventRecord");
-    NM_CUDA(launch_fold(fp, s), "fold launch");
-    NM_CUDA(cudaEventRecord(h->ev[4 * b + 3], s), "cudaEventRecord");
+    fp.tb = tally;
+    NM_CUDA(cudaEventRecord(h->ev[4 * b + 2], bs), "cudaEventRecord");
+    NM_CUDA(launch_fold(fp, bs), "fold launch");
+    NM_CUDA(cudaEventRecord(h->ev[4 * b + 3], bs), "cudaEventRecord");
     h->hist_next += nb;
     h->id_next += nb;
     h->n_batches += 1;
   }
+  // the handle's stream continues after the side stream's last work
+  NM_CUDA(cudaEventRecord(h->ev_join, h->side), "cudaEventRecord");
+  NM_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0), "cudaStreamWaitEvent");
   uint32_t st = 0;
   NM_CUDA(cudaMemcpyAsync(&st, h->status, 4, cudaMemcpyDeviceToHost, s), "status read");
   NM_CUDA(cudaStreamSynchronize(s), "nm_dose_run");
@@ -1512,6 +1548,7 @@ nm_status nm_dose_restore(nm_dose* h, const void* buf, uint64_t bytes) {
     NM_CUDA(cudaMemcpyAsync(h->s2h_hi, b + o.hi, V8, cudaMemcpyDefault, s), "restore");
   }
   NM_CUDA(cudaMemsetAsync(h->tb, 0, V8, s), "restore");
+  NM_CUDA(cudaMemsetAsync(h->tb2, 0, V8, s), "restore");
   NM_CUDA(cudaStreamSynchronize(s), "nm_dose_restore");
   h->hist_next = hd.hist_next;
   h->id_next = hd.id_next;
@@ -1600,6 +1637,7 @@ nm_status nm_dose_reset(nm_dose* h) {
   if (!h) return fail(NM_ERR_ARG, "handle is NULL");
   cudaStream_t s = h->stream;
   NM_CUDA(cudaMemsetAsync(h->tb, 0, h->V * sizeof(ull), s), "reset");
+  NM_CUDA(cudaMemsetAsync(h->tb2, 0, h->V * sizeof(ull), s), "reset");
   NM_CUDA(cudaMemsetAsync(h->tsum, 0, h->V * sizeof(ull), s), "reset");
   NM_CUDA(cudaMemsetAsync(h->s2, 0, h->V * sizeof(double), s), "reset");
   NM_CUDA(cudaMemsetAsync(h->counters, 0, kCtrCount * sizeof(ull), s), "reset");
