@@ -149,8 +149,11 @@ typedef struct {
   int64_t killed;            /* energy units of photons stopped by max_steps */
   uint64_t steps;            /* flight steps (real + virtual) */
   uint64_t compton, photo, rayleigh, cutoff, escapes;
-  double transport_ms;       /* device time of the transport launches */
-  double fold_ms;            /* device time of the batch folds */
+  double transport_ms;       /* device time of the transport launches: per run call, from the first
+                                batch's start to the last transport's end (consecutive batches
+                                overlap on two streams, folds between them inside the span) */
+  double fold_ms;            /* device time of the batch folds (a fold waits for SMs while the other
+                                stream's transport holds them: an upper bound) */
   uint32_t device_status;    /* OR of NM_DEV_* flags seen */
   int32_t block_threads, chunk, warp_aggregate, regroup, regroup_lanes, grid_blocks; /* tuning used */
   uint64_t history_splits;   /* history_sigma: histories whose deposits touched more voxels
