@@ -642,7 +642,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--cpu-decays", type=int, default=12_000_000)
     ap.add_argument("--ref-decays", type=int, default=6_000_000)
     ap.add_argument("--denoiser-steps", type=int, default=10)
