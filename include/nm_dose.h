@@ -84,7 +84,8 @@ typedef struct {
   float point[3];            /* cm, point mode: one photon per history from here */
   double photon_mev;         /* 0.511 */
   double positron_mev;       /* positron energy deposited at the decay, 0.25 */
-  int32_t batches;           /* batches per nm_dose_run call, >= 2 (default 10) */
+  int32_t batches;           /* batches per nm_dose_run call, >= 1 (default 10); the uncertainty
+                                needs two batches in total, over one call or several */
   double activity_bq;        /* A(t_s) of Eq. 1, Bq */
   int32_t n_labels;          /* organs 1..n_labels in the label map (0 = none) */
   int32_t block_threads;     /* transport CTA size; 0 = autotuned */

@@ -713,7 +713,8 @@ nm_status nm_dose_create(nm_dose** out, const nm_grid* g, const nm_materials* mt
   if (opts) o = *opts; else nm_options_default(&o);
   const nm_status cp = check_problem(g, mt, o, activity);
   if (cp != NM_OK) return cp;
-  if (o.batches < 2) return fail(NM_ERR_ARG, "batches must be >= 2");
+  // one batch per call is allowed: the uncertainty needs two batches in total
+  if (o.batches < 1) return fail(NM_ERR_ARG, "batches must be >= 1");
   if (o.n_labels < 0 || o.n_labels > NM_MAX_LABELS) return fail(NM_ERR_ARG, "n_labels must be 0..%d", NM_MAX_LABELS);
   const int64_t V = (int64_t)g->nx * g->ny * g->nz;
 

@@ -315,11 +315,13 @@ def nm_dose_get(h, dose=None, sigma=None, organ_dose=None):
     _check(load().nm_dose_get(h, ptr(dose), ptr(sigma), ptr(organ_dose)))
 
 
-def nm_dose_get_organs(h, n_labels: int, eps: bool = True):
+def nm_dose_get_organs(h, n_labels: int, eps: bool = True, sigma: bool = True):
     """(mean, eps_rms, sigma_mean, voxels) per label; eps=False skips Eq. 3 and
-    with it the pass over the voxels (eps_rms is then None)."""
+    with it the pass over the voxels (eps_rms is then None); sigma=False skips
+    the batch sigma (None), which needs two batches."""
     n = n_labels + 1
-    mean, sig = np.zeros(n), np.zeros(n)
+    mean = np.zeros(n)
+    sig = np.zeros(n) if sigma else None
     e = np.zeros(n) if eps else None
     cnt = np.zeros(n, np.int64)
     _check(load().nm_dose_get_organs(h, ptr(mean), ptr(e), ptr(sig), ptr(cnt)))
@@ -595,8 +597,8 @@ class Dose:
         nm_dose_get(self.h, dose, sigma, None)
         return dose, sigma
 
-    def organs(self, eps: bool = True):
-        return nm_dose_get_organs(self.h, self.n_labels, eps)
+    def organs(self, eps: bool = True, sigma: bool = True):
+        return nm_dose_get_organs(self.h, self.n_labels, eps, sigma)
 
     def map_organs(self, dose):
         _want("dose", dose, "float32", int(np.prod(self.shape)))

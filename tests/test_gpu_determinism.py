@@ -74,3 +74,34 @@ def test_point_source_repeat(nm):
             d.run(200_000, seed=3)
             out.append(d.tally())
     assert np.array_equal(out[0], out[1])
+
+
+def test_one_batch_per_call_equals_the_same_batches_in_one_call(nm, phantom):
+    """Batches may be split over run calls: two calls of one batch each give
+    the batches of one two-batch call (the same histories in the same order),
+    so the statistics are the same bits; the organ means are available after
+    one batch, the uncertainties from the second on (odd and even batches run
+    on different streams, their folds in batch order)."""
+    ph, den, mat, gm = phantom
+    n = 400_000
+    shape = den.shape
+    res = []
+    for batches, calls in ((2, [n]), (1, [n // 2, n // 2])):
+        with nm.Dose(den, mat, ph.spacing, gm, activity=ph.activity, labels=ph.labels, n_labels=27,
+                     batches=batches) as d:
+            for k, m in enumerate(calls):
+                d.run(m, seed=6)
+                if batches == 1 and k == 0:
+                    mean1, _, sig1, _ = d.organs(eps=False, sigma=False)
+                    assert sig1 is None and np.all(np.isfinite(mean1))
+                    with pytest.raises(nm.NmError):
+                        d.organs(eps=False)          # the batch sigma needs two batches
+            dose = np.empty(shape, np.float32)
+            sigma = np.empty(shape, np.float32)
+            nm.nm_dose_get(d.h, dose, sigma, None)
+            mean, _, sig, _ = d.organs(eps=False)
+            res.append((d.tally(), dose, sigma, mean, sig, d.counters()["batches"]))
+    a, b = res
+    assert a[5] == b[5] == 2
+    for x, y in zip(a[:5], b[:5]):
+        assert np.array_equal(x, y)

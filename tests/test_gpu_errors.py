@@ -44,7 +44,7 @@ def test_invalid_inputs_are_rejected(nm, case):
         lab = np.zeros(shape, np.uint8); lab[0, 1, 2] = 5; lab[3, 4, 5] = 7
         kw["n_labels"] = 3
     elif case == "batches":
-        kw["batches"] = 1
+        kw["batches"] = 0
     elif case == "point_outside":
         kw.update(source_mode=nm.NM_SOURCE_POINT, point=(3.0, 0.1, 0.1))
     with pytest.raises(nm.NmError) as e:
