@@ -207,6 +207,18 @@ void dfree(void* p) {
   c.cached += key.second;
 }
 
+// Frees a dalloc'd buffer at once (cudaFree, with its synchronisation),
+// bypassing the cache: for per-call temporaries of the check entry points.
+void dfree_now(void* p) {
+  if (!p) return;
+  {
+    BufferCache& c = buffer_cache();
+    std::lock_guard<std::mutex> lock(c.mu);
+    c.live.erase(p);
+  }
+  cudaFree(p);
+}
+
 }  // namespace
 
 // Inverse CDF of the Klein-Nishina distribution of x = 1 - cos(theta) (per
@@ -1423,7 +1435,7 @@ nm_status nm_time_integrated_activity(const float* const* act, const double* t_h
   if (!e) e = cudaMemcpyAsync(&st, sums + blocks, sizeof st, cudaMemcpyDeviceToHost, s);
   if (!e && dout != out) e = cudaMemcpyAsync(out, dout, V * sizeof(float), cudaMemcpyDeviceToHost, s);
   if (!e) e = cudaStreamSynchronize(s);
-  cudaFree(sums);
+  dfree_now(sums);
   cleanup();
   if (e) return cuda_fail(e, "nm_time_integrated_activity");
   if (st & NM_DEV_BAD_ACTIVITY) return fail(NM_ERR_ARG, "nm_time_integrated_activity: activities must be finite and >= 0");
@@ -1683,7 +1695,7 @@ nm_status nm_check_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, u
   if (!e) e = cudaMemcpy(dk, key, n * 8, cudaMemcpyHostToDevice);
   if (!e) e = launch_check_philox(dc, dk, n, dout, 0);
   if (!e) e = cudaMemcpy(out, dout, n * 16, cudaMemcpyDeviceToHost);
-  cudaFree(dc); cudaFree(dk); cudaFree(dout);
+  dfree_now(dc); dfree_now(dk); dfree_now(dout);
   return e ? cuda_fail(e, "nm_check_philox") : NM_OK;
 }
 
@@ -1699,7 +1711,7 @@ nm_status nm_check_kahn(double e_mev, int64_t n, uint64_t seed, float* cos_out) 
   if (!e) e = cudaMemcpy(cos_out, d, n * 4, cudaMemcpyDeviceToHost);
   uint32_t flags = 0;
   if (!e) e = cudaMemcpy(&flags, st, 4, cudaMemcpyDeviceToHost);
-  cudaFree(d); cudaFree(st);
+  dfree_now(d); dfree_now(st);
   if (e) return cuda_fail(e, "nm_check_kahn");
   if (flags) return fail(NM_ERR_DEVICE, "Kahn trial limit hit");
   return NM_OK;
@@ -1721,7 +1733,7 @@ nm_status nm_check_wait_timeout(int64_t max_cycles) {
   if (!e) e = cudaMemset(st, 0, 4);
   if (!e) e = launch_check_wait(max_cycles, st, 0);
   if (!e) e = cudaMemcpy(&flags, st, 4, cudaMemcpyDeviceToHost);
-  cudaFree(st);
+  dfree_now(st);
   if (e) return cuda_fail(e, "nm_check_wait_timeout");
   if (flags & NM_DEV_TIMEOUT) return fail(NM_ERR_TIMEOUT, "a bounded device wait gave up after %lld cycles",
                                           (long long)max_cycles);
@@ -1749,8 +1761,8 @@ nm_status nm_check_kn_table(double e_mev, double cut_mev, double e0_mev, int64_t
   p.kn_inv = dt;
   if (!e) e = launch_check_kn_table(p, (float)e_mev, n, d, 0);
   if (!e) e = cudaMemcpy(cos_out, d, n * sizeof(float), cudaMemcpyDeviceToHost);
-  cudaFree(d);
-  cudaFree(dt);
+  dfree_now(d);
+  dfree_now(dt);
   if (e) return cuda_fail(e, "nm_check_kn_table");
   return NM_OK;
 }
@@ -1767,8 +1779,8 @@ nm_status nm_check_beta(double t_max_mev, int32_t z, int64_t n, uint64_t seed, f
   if (!e) e = cudaMemcpy(dt, tab.data(), (kBetaTable + 1) * sizeof(float), cudaMemcpyHostToDevice);
   if (!e) e = launch_check_beta(dt, n, (uint32_t)seed, (uint32_t)(seed >> 32), d, 0);
   if (!e) e = cudaMemcpy(t_out, d, n * sizeof(float), cudaMemcpyDeviceToHost);
-  cudaFree(d);
-  cudaFree(dt);
+  dfree_now(d);
+  dfree_now(dt);
   if (e) return cuda_fail(e, "nm_check_beta");
   return NM_OK;
 }
@@ -1804,7 +1816,7 @@ nm_status nm_check_source(nm_dose* h, uint64_t first, int64_t n, uint64_t seed, 
   if (!e) e = cudaMemcpyAsync(pos, dp, 3 * n * 4, cudaMemcpyDeviceToHost, h->stream);
   if (!e) e = cudaMemcpyAsync(dir, dd, 3 * n * 4, cudaMemcpyDeviceToHost, h->stream);
   if (!e) e = cudaStreamSynchronize(h->stream);
-  cudaFree(dv); cudaFree(dp); cudaFree(dd);
+  dfree_now(dv); dfree_now(dp); dfree_now(dd);
   return e ? cuda_fail(e, "nm_check_source") : NM_OK;
 }
 
