@@ -343,7 +343,11 @@ __global__ void label_count_kernel(const uint8_t* labels, int64_t V, int n_label
        i += (int64_t)gridDim.x * blockDim.x) {
     const int l = labels[i];
     if (l > n_labels) atomicMin(first_bad, (ull)i);
-    atomicAdd((ull*)&s[l < kLabelSlots ? l : 0], 1ull);
+    // neighbouring voxels mostly share a label: one shared-memory atomic per
+    // distinct label of the warp instead of one per voxel
+    const int slot = l < kLabelSlots ? l : 0;
+    const unsigned peers = __match_any_sync(__activemask(), slot);
+    if ((int)(threadIdx.x & 31u) == __ffs(peers) - 1) atomicAdd((ull*)&s[slot], (ull)__popc(peers));
   }
   __syncthreads();
   if (threadIdx.x < kLabelSlots && s[threadIdx.x])

@@ -193,3 +193,27 @@ def test_source_sampler_follows_activity(nm):
     assert np.all(np.abs(dr.mean(0)) < 5 / math.sqrt(3 * n))
     h, _ = np.histogram(dr[:, 2], np.linspace(-1, 1, 41))
     assert stats.chisquare(h).pvalue > 1e-4
+
+
+@pytest.mark.parametrize("kind", ["blocks", "noise"])
+def test_organ_voxel_counts_are_exact(nm, kind):
+    """The per-organ voxel counts (the denominators of Eq. 2) counted on the
+    device, warp-aggregated, against np.bincount of the label map: blocky
+    organs (warps mostly see one label) and labels random per voxel (every
+    lane a different one)."""
+    rng = np.random.default_rng(3)
+    shape = (23, 41, 37)
+    n_labels = 27
+    if kind == "blocks":
+        lab = np.zeros(shape, np.uint8)
+        for _ in range(40):
+            z, y, x = (rng.integers(0, s) for s in shape)
+            lab[z:z + rng.integers(2, 9), y:y + rng.integers(3, 15), x:x + rng.integers(3, 15)] = rng.integers(0, 28)
+    else:
+        lab = rng.integers(0, n_labels + 1, shape).astype(np.uint8)
+    den = np.ones(shape, np.float32)
+    with nm.Dose(den, np.zeros(shape, np.uint8), (0.5, 0.5, 0.5), nm.Materials([0.5551], [7.42]),
+                 activity=np.ones(shape, np.float32), labels=lab, n_labels=n_labels, batches=1) as d:
+        d.run(10_000, seed=1)
+        _, _, _, cnt = d.organs(eps=False, sigma=False)
+    assert np.array_equal(cnt, np.bincount(lab.ravel(), minlength=n_labels + 1))
