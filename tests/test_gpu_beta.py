@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 from scipy import stats
 
+from tests.parity_record import record
 from tests.positron_expect import cube_positron_expectation
 
 pytestmark = pytest.mark.gpu
@@ -34,6 +35,8 @@ def test_device_spectrum_sampler(nm, orc):
     assert 0.0 <= t.min() and t.max() <= F18_T_MAX
     assert abs(t.mean() / F18_T_MEAN - 1.0) < 0.005
     ref = orc.sample_beta(F18_T_MAX, 8, 400_000, 6)
+    record("beta_spectrum", mean_rel_vs_tabulated=t.mean() / F18_T_MEAN - 1.0,
+           mean_rel_vs_oracle=t.mean() / ref.mean() - 1.0, ks_p_vs_oracle=stats.ks_2samp(t[:400_000], ref).pvalue)
     assert stats.ks_2samp(t[:400_000], ref).pvalue > 1e-3
     # statistical-shape limit: Beta(3/2, 3) on [0, T_max]
     t0 = nm.nm_check_beta(1e-3, 0, 400_000, 7).astype(np.float64)
@@ -83,6 +86,8 @@ def test_positron_tracks_in_a_cube(nm, orc, rho):
     # 2e7 and 2e6 decays differ there by 0.6 % (median) and 4 % (worst)
     sel = o > 3e-4
     rel = np.abs(g[sel] / o[sel] - 1.0)
+    record("positron_cube", voxels=int(sel.sum()), median_abs_rel=np.median(rel), max_abs_rel=rel.max(),
+           escaped_rel_vs_expectation=esc / e_esc.mean() - 1, centre_rel_vs_expectation=centre / e_centre.mean() - 1)
     assert sel.sum() >= 27 and np.median(rel) < 0.01 and rel.max() < 0.04, (sel.sum(), rel)
 
 

@@ -7,6 +7,8 @@ sum of |terms|, and a BF16 output adds a rounding of 2^-9 relative."""
 import numpy as np
 import pytest
 
+from tests.parity_record import record
+
 pytestmark = pytest.mark.gpu
 
 
@@ -132,6 +134,7 @@ def test_conv_forward_dgrad_wgrad(env, case, conv_path):
     absum = dn.conv3d(np.abs(X), np.abs(W)) + np.abs(as64(bias))
     got = as64(y.cpu())
     tol = 2.0 ** -8 * np.abs(ref) + 27 * cin * 2.0 ** -23 * absum + 1e-30
+    record("conv", case=case, path=conv_path, op="forward", max_err_over_tol=np.max(np.abs(got - ref) / tol))
     assert np.all(np.abs(got - ref) <= tol), np.max(np.abs(got - ref) / tol)
 
     # input gradient
@@ -144,6 +147,7 @@ def test_conv_forward_dgrad_wgrad(env, case, conv_path):
         absum = dn.conv3d_dgrad(np.abs(G), np.abs(W))
         tol = 2.0 ** -8 * np.abs(ref) + 27 * cout * 2.0 ** -23 * absum + 1e-30
         got = as64(dx.cpu())
+        record("conv", case=case, path=conv_path, op="dgrad", max_err_over_tol=np.max(np.abs(got - ref) / tol))
         assert np.all(np.abs(got - ref) <= tol), np.max(np.abs(got - ref) / tol)
 
     # weight and bias gradients.  BF16 x BF16 products are exact in FP32, so
@@ -177,6 +181,8 @@ def test_conv_forward_dgrad_wgrad(env, case, conv_path):
             assert np.all(got[:, 27 * cin:] == 0.0)               # padding columns stay exactly zero
             got3 = got[:, :27 * cin].reshape(cout, 27, cin)
             tol = 4 * L * 2.0 ** -24 * adw + 1e-30
+            record("conv", case=case, path=conv_path, op="wgrad", signed=signed,
+                   max_err_over_tol=np.max(np.abs(got3 - rdw) / tol))
             assert np.all(np.abs(got3 - rdw) <= tol), (signed, np.max(np.abs(got3 - rdw) / tol))
             tolb = 4 * L * 2.0 ** -24 * adb + 1e-30
             assert np.all(np.abs(db.cpu().numpy() - rdb) <= tolb), (signed, np.max(np.abs(db.cpu().numpy() - rdb) / tolb))

@@ -9,6 +9,8 @@ high-count reference of the same phantom."""
 import numpy as np
 import pytest
 
+from tests.parity_record import record
+
 pytestmark = pytest.mark.gpu
 
 
@@ -23,6 +25,7 @@ def test_denoiser_reduces_low_count_organ_error():
     dn = np.array([c["denoiser_mean_err"] for c in out["cases"]])
     lo = np.array([c["low_mc_mean_err"] for c in out["cases"]])
     # the trained network must lower the mean organ error of its own input
+    record("denoiser_gain", mean_organ_err_denoised=dn.mean(), mean_organ_err_low_count=lo.mean())
     assert dn.mean() < lo.mean(), (dn, lo)
     for c in out["cases"]:
         assert c["plain_mc_s"] is not None   # plain MC reaches 2 % within the budget

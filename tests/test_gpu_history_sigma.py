@@ -7,6 +7,8 @@ depend on the scheduling)."""
 import numpy as np
 import pytest
 
+from tests.parity_record import record
+
 pytestmark = pytest.mark.gpu
 
 
@@ -44,6 +46,8 @@ def test_history_sigma_bernoulli_closed_form(nm, absorb):
     assert c["deposited"] == N * T and c["history_splits"] == 0
     p = t / (T * N)
     expect = np.sqrt((1 - p) / ((N - 1) * p))
+    ok = dose > 0
+    record("history_sigma_closed_form", voxels=int(ok.sum()), max_abs_rel=np.abs(sh[ok] / dose[ok] / expect[ok] - 1).max())
     assert np.allclose(sh / dose, expect, rtol=2e-6, atol=0)
 
 
@@ -79,6 +83,8 @@ def test_history_sigma_matches_oracle(nm, orc):
     rg = gh[sel] / g[sel]
     ro = r.sigma_history[sel] / r.dose_rate[sel]
     ratio = rg / ro
+    record("history_sigma_vs_oracle", voxels=int(sel.sum()), median_ratio=np.median(ratio),
+           frac_within_20pct=np.mean(np.abs(ratio - 1) < 0.2), median_batch_over_history=np.median(sg[sel] / gh[sel]))
     assert sel.sum() > 1000
     assert abs(np.median(ratio) - 1) < 0.03, np.median(ratio)
     assert np.mean(np.abs(ratio - 1) < 0.2) > 0.95

@@ -10,6 +10,8 @@ import numpy as np
 import pytest
 from scipy import integrate, stats
 
+from tests.parity_record import record
+
 pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 ME = 0.51099895
@@ -71,6 +73,8 @@ def test_kahn_sampler_chi2(nm, e):
     k = e / ME
     mean_ep = np.mean(1.0 / (1.0 + k * (1.0 - c)))
     ref = integrate.quad(lambda x: _kn_w(x, e) / (1 + k * (1 - x)), -1, 1)[0] / integrate.quad(lambda x: _kn_w(x, e), -1, 1)[0]
+    record("kn_sampler", sampler="kahn", mev=e, draws=n, chi2_p=stats.chi2.sf(chi2, len(p) - 1),
+           mean_e_ratio_rel=mean_ep / ref - 1)
     assert abs(mean_ep - ref) < 5 * np.std(1.0 / (1.0 + k * (1.0 - c))) / math.sqrt(n)
 
 
@@ -90,6 +94,8 @@ def test_kn_table_sampler_chi2(nm, e):
     k = e / ME
     w = 1.0 / (1.0 + k * (1.0 - c))
     ref = integrate.quad(lambda x: _kn_w(x, e) / (1 + k * (1 - x)), -1, 1)[0] / integrate.quad(lambda x: _kn_w(x, e), -1, 1)[0]
+    record("kn_sampler", sampler="table", mev=e, draws=n, chi2_p=stats.chi2.sf(chi2, len(p) - 1),
+           mean_e_ratio_rel=w.mean() / ref - 1)
     assert abs(w.mean() - ref) < 5 * w.std() / math.sqrt(n)
 
 
@@ -107,6 +113,8 @@ def test_ct_to_phantom_matches_oracle(nm, orc):
     mat = np.empty(hu.shape, np.uint8)
     nm.nm_ct_to_phantom(hu, den, mat)
     oden, omat = orc.hu_to_phantom(hu)
+    record("ct_to_phantom", values=hu.size, material_mismatches=int((mat != omat).sum()),
+           max_density_ulps=(np.abs(den - oden) / np.spacing(oden.astype(np.float32))).max())
     assert (mat == omat).all()                              # integer decision: exact
     assert np.all(np.abs(den - oden) <= 2 * np.spacing(oden.astype(np.float32)))  # FP32 vs FP64
     # device pointers, ragged size, empty input
@@ -159,6 +167,8 @@ def test_alias_table_reconstructs_pdf(nm, shape, kind):
     got = _alias_mass(prob, vox, ali, V)
     # each column's split is rounded to FP32 once: error <= (#columns touching v) 2^-24 / n
     touch = np.bincount(ali, minlength=V) + (act.ravel() > 0)
+    record("alias_table", voxels=V, max_abs_err=np.abs(got - target).max(),
+           max_err_over_bound=(np.abs(got - target) / (touch * 2.0 ** -24 / len(prob) + 1e-15)).max())
     assert np.all(np.abs(got - target) <= touch * 2.0 ** -24 / len(prob) + 1e-15)
 
 
@@ -178,6 +188,7 @@ def test_source_sampler_follows_activity(nm):
     assert cnt[p == 0].sum() == 0
     nz = p > 0
     chi2 = ((cnt[nz] - n * p[nz]) ** 2 / (n * p[nz])).sum()
+    record("source_voxels", draws=n, chi2_p=stats.chi2.sf(chi2, nz.sum() - 1))
     assert stats.chi2.sf(chi2, nz.sum() - 1) > 1e-4
     # position inside the sampled voxel, uniform there
     ix, iy, iz = vox % 6, (vox // 6) % 5, vox // 30

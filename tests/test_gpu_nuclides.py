@@ -7,6 +7,7 @@ argument checks."""
 import numpy as np
 import pytest
 
+from tests.parity_record import record
 from tests.test_gpu_parity import organ_check, voxel_criterion
 from tests.test_oracle_pins import I131, LU177
 
@@ -54,6 +55,8 @@ def test_beta_minus_emitter_matches_oracle(nm, orc, nuc, gammas):
     # the gamma lines at their yields (a few per mille statistically)
     per = c["emitted"] / 64e6 / N
     expect_gamma = sum(e * y for e, y in gammas)
+    record("emitted_per_decay", mev=per, expected_mev=expect_gamma + nuc["mean"],
+           rel=per / (expect_gamma + nuc["mean"]) - 1)
     assert abs(per - expect_gamma - nuc["mean"]) < 0.06 * nuc["mean"] + 0.01 * expect_gamma, per
     oden, omat = orc.hu_to_phantom(ph.hu)
     om = orc.Materials(inputs.MATERIAL_Z_OVER_A, inputs.MATERIAL_ZEFF, inputs.PE_COEFF, inputs.PE_EXP)

@@ -12,6 +12,7 @@ import time
 import numpy as np
 import pytest
 
+from parity_record import map_figures, record
 from test_gpu_parity import organ_check, shells
 
 pytestmark = pytest.mark.gpu
@@ -69,6 +70,7 @@ def test_paper_point_source_matches_oracle(nm, orc):
           f"{np.round(np.sqrt((zz - ctr) ** 2 + (yy - ctr) ** 2 + (xx - ctr) ** 2), 1).tolist()}")
     # 20 batches per side: |t| > 3 with ~38 degrees of freedom has probability ~0.5 %
     frac, nsel = (np.abs(zv[top]) <= 3).mean(), top.sum()
+    record("dose_map", **map_figures(g, r.dose_rate, r.sigma, top, comb))
     assert nsel > 500 and frac >= 0.99, (frac, nsel)
     zmax, npow, worst, z, sel = organ_check(gmean, gsig, r.organ_mean, r.organ_sigma, cnt, min_voxels=1)
     assert zmax < 4.0, z[sel]
@@ -81,4 +83,6 @@ def test_paper_point_source_matches_oracle(nm, orc):
     comb = np.sqrt(sg[hi].astype(np.float64) ** 2 + r.sigma[hi] ** 2) / r.dose_rate[hi]
     print(f"voxels above 10 % of max: {hi.sum()}, mean |diff| {rel.mean() * 100:.2f} %, "
           f"mean combined sigma {comb.mean() * 100:.2f} %")
+    record("paper_metric", voxels=int(hi.sum()), mean_abs_rel=rel.mean(), mean_combined_rel_sigma=comb.mean(),
+           gpu_ms=wall * 1e3)
     assert rel.mean() < 1.5 * comb.mean() * np.sqrt(2 / np.pi) + 1e-3

@@ -10,6 +10,11 @@ import os
 import numpy as np
 import pytest
 
+try:
+    from parity_record import map_figures, record
+except ImportError:   # imported as tests.test_gpu_parity
+    from tests.parity_record import map_figures, record
+
 pytestmark = pytest.mark.gpu
 
 
@@ -25,6 +30,7 @@ def voxel_criterion(g, sg, o, so, mask):
     sel = mask & (o > 0.05 * o[mask].max())
     comb = np.sqrt(sg.astype(np.float64) ** 2 + so ** 2)
     ok = np.abs(g.astype(np.float64) - o) <= 3 * comb
+    record("dose_map", **map_figures(g, o, so, sel, comb))
     return ok[sel].mean(), sel.sum()
 
 
@@ -37,6 +43,9 @@ def organ_check(gm, gs, om, os_, cnt, min_voxels=20):
         z = np.where(sel, (gm - om) / comb, 0.0)
         rel = np.where(sel, np.abs(gm / om - 1), 0.0)
     powered = sel & (3 * comb < 0.01 * om)
+    record("organs", organs=int(sel.sum()), max_abs_z=np.abs(z[sel]).max(), powered=int(powered.sum()),
+           max_abs_rel_powered=rel[powered].max() if powered.any() else None,
+           median_abs_rel=np.median(rel[sel]), max_abs_rel=rel[sel].max())
     return np.abs(z[sel]).max(), powered.sum(), (rel[powered].max() if powered.any() else 0.0), z, sel
 
 
@@ -76,6 +85,7 @@ def test_point_source_in_water_matches_oracle(nm, orc):
     # deposited fraction of the emitted energy
     fg = c["deposited"] / c["emitted"]
     fo = r.counters["deposited"] / r.counters["emitted"]
+    record("deposited_fraction", gpu=fg, oracle=fo, diff=fg - fo, bound=5 * math.sqrt(2) * 0.5 / math.sqrt(N))
     assert abs(fg - fo) < 5 * math.sqrt(2) * 0.5 / math.sqrt(N)
 
 
@@ -124,6 +134,7 @@ def test_absorber_matches_first_collision_kernel(nm):
                 sd = math.sqrt(N * prob * (1 - prob)) * q
                 z.append((t[iz, iy, ix] - N * prob * q) / sd)
     z = np.array(z)
+    record("closed_form_kernel", voxels=len(z), max_abs_z=np.abs(z).max(), z_mean=z.mean(), z_rms=np.sqrt((z ** 2).mean()))
     assert np.all(np.abs(z) < 5), z
     assert abs(z.mean()) < 5 / math.sqrt(len(z))
     assert abs((z ** 2).mean() - 1) < 0.5
@@ -177,6 +188,8 @@ def test_reduced_phantom_matches_oracle(nm, orc, kn_sampler):
     assert npow >= 2 and worst < 0.01, (npow, worst)
     # Eq. 3 organ uncertainties agree to within their own scatter (both ~ 1/sqrt(N)).
     ok = sel & (cnt >= 100)
+    record("eq3_organ_eps", organs=int(ok.sum()), max_abs_rel=np.abs(ge[ok] / r.organ_eps[ok] - 1).max(),
+           median_abs_rel=np.median(np.abs(ge[ok] / r.organ_eps[ok] - 1)))
     assert np.all(np.abs(ge[ok] / r.organ_eps[ok] - 1) < 0.25)
     # the organ means and sigmas without Eq. 3 (no pass over the voxels) equal
     # the full pass's to FP32 rounding of the voxel doses
@@ -227,6 +240,10 @@ def test_full_size_phantom_every_organ_within_1_percent(nm):
     assert under.size == 0, f"underpowered: organs {under.tolist()} have 3 combined sigma >= 1 %"
     rel = gm[organs] / om[organs] - 1
     z = (gm[organs] - om[organs]) / comb
+    record("organs", organs=int(organs.size), max_abs_z=np.abs(z).max(), powered=int(organs.size),
+           max_abs_rel_powered=np.abs(rel).max(), median_abs_rel=np.median(np.abs(rel)),
+           max_abs_rel=np.abs(rel).max(), max_oracle_rel_sigma=(os_[organs] / om[organs]).max(),
+           max_gpu_rel_sigma=(gs[organs] / gm[organs]).max(), gpu_decays=N)
     assert np.all(np.abs(rel) < 0.01), dict(zip(organs[np.abs(rel) >= 0.01].tolist(), rel[np.abs(rel) >= 0.01]))
     assert np.all(np.abs(z) < 4.0), dict(zip(organs[np.abs(z) >= 4].tolist(), z[np.abs(z) >= 4]))
 
@@ -314,5 +331,6 @@ def test_rayleigh_on_matches_oracle(nm, orc):
     ng = c["rayleigh"] + c["compton"]
     no = r.counters["rayleigh"] + r.counters["compton"]
     sd = math.sqrt(fg * (1 - fg) / ng + fo * (1 - fo) / no)
+    record("rayleigh_fraction", gpu=fg, oracle=fo, diff_over_binomial_sigma=(fg - fo) / sd)
     # photon histories make events correlated within a decay: allow 8 binomial sigma
     assert abs(fg - fo) < 8 * sd, (fg, fo, sd)

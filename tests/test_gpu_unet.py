@@ -7,6 +7,8 @@ to about a percent, not bitwise; the tolerances below are stated per check."""
 import numpy as np
 import pytest
 
+from tests.parity_record import record
+
 pytestmark = pytest.mark.gpu
 
 
@@ -75,6 +77,7 @@ def test_unet_matches_oracle_forward_and_gradients(env):
     params = to_oracle(flat, layers, widths, names)
     yo, cache = dn.unet_forward(x64, params, widths)
     m = yo.size
+    record("unet_forward", rel_norm=np.linalg.norm(y - yo) / np.linalg.norm(yo))
     assert np.linalg.norm(y - yo) / np.linalg.norm(yo) < 2e-2
     lo = np.sum(weight * (yo - target) ** 2) / m
     assert abs(loss / lo - 1) < 3e-2, (loss, lo)
@@ -88,6 +91,7 @@ def test_unet_matches_oracle_forward_and_gradients(env):
             # BF16 activations and gradients at ~10 stages between the loss and the
             # deepest layers, plus ReLU masks that flip where a pre-activation is
             # within rounding of zero: direction within 8 degrees, norm within 15 %.
+            record("unet_gradient", layer=name, part="wb"[k], rel_norm=rel, cos=cos)
             assert rel < 0.15 and cos > 0.99, (name, k, rel, cos)
     # padding columns of every weight matrix get exactly zero gradient
     for l in layers[:-1]:
@@ -287,6 +291,7 @@ def test_apply_whole_volume_matches_oracle(env, budget, form, monkeypatch):
     inside[z0:z1, y0:y1, x0:x1] = True
     # BF16 activations through ~10 convolutions: 2 % in norm, as for the patch forward
     rel = np.linalg.norm(o[inside] - exp[inside]) / np.linalg.norm(exp[inside])
+    record("apply_volume", budget=budget, form=form, rel_norm=rel)
     assert rel < 2e-2, rel
     assert np.array_equal(o[~inside], dose[~inside])
 
@@ -321,5 +326,6 @@ def test_apply_roi_matches_oracle(env):
     inside[rz0:rz1, ry0:ry1, rx0:rx1] = True
     exp = s * y[8:8 + rz1 - rz0, 8:8 + ry1 - ry0, 8:8 + rx1 - rx0]
     rel = np.linalg.norm(o[inside] - exp.ravel()) / np.linalg.norm(exp)
+    record("apply_roi", rel_norm=rel)
     assert rel < 2e-2, rel
     assert np.array_equal(o[~inside], dose[~inside])

@@ -13,6 +13,8 @@ magnitudes."""
 import numpy as np
 import pytest
 
+from tests.parity_record import record
+
 pytestmark = pytest.mark.gpu
 
 P, WIDTHS = 16, (16, 32, 64, 128)
@@ -105,6 +107,9 @@ def _gw(r, name):
 
 def _close(got, ref, tol, what):
     bad = np.abs(got - ref) > tol
+    err = np.abs(np.asarray(got, np.float64) - ref)
+    record("layer", what=what, elements=int(np.size(ref)), max_err_over_tol=(err / tol).max(),
+           max_err_over_max_ref=err.max() / (np.abs(ref).max() + 1e-300))
     assert not bad.any(), (what, int(bad.sum()), float(np.abs(got - ref)[bad].max()), float(tol[bad].min()))
 
 
