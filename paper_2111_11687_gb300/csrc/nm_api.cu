@@ -396,8 +396,7 @@ struct nm_dose {
     p.kn_inv_idln = kn_inv_idln;
     p.s2h_lo = s2h_lo;
     p.s2h_hi = s2h_hi;
-    p.key0 = (uint32_t)seed;
-    p.key1 = (uint32_t)(seed >> 32);
+    p.key = philox_key((uint32_t)seed, (uint32_t)(seed >> 32));
     p.e0 = e0;
     p.q_e0 = q_e0;
     p.cut = cut;
@@ -1749,8 +1748,7 @@ nm_status nm_check_kn_table(double e_mev, double cut_mev, double e0_mev, int64_t
   const std::vector<float>& kt = kn_inverse_cdf(cut_mev, e0_mev);
   TransportParams p;
   memset(&p, 0, sizeof p);
-  p.key0 = (uint32_t)seed;
-  p.key1 = (uint32_t)(seed >> 32);
+  p.key = philox_key((uint32_t)seed, (uint32_t)(seed >> 32));
   p.kn_inv_lo = (float)std::log(cut_mev);
   p.kn_inv_idln = (float)((kKnInvE - 1) / (std::log(e0_mev) - std::log(cut_mev)));
   float* d = nullptr;

@@ -38,15 +38,29 @@ __host__ __device__ inline int32_t q_units(float e_mev) {
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32
 // -> 64-bit multiplies with the key bumped by the Weyl constants between rounds.
+// The bumped keys depend on the seed alone, so they are formed once per launch
+// (PhiloxKey, in the kernel's parameters): each round then XORs a parameter
+// word instead of first adding a Weyl constant to a register.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+struct PhiloxKey {
+  uint32_t rk[20];            // round r: (k0 + r 0x9E3779B9, k1 + r 0xBB67AE85) at 2r, 2r + 1
+};
+
+__host__ __device__ inline PhiloxKey philox_key(uint32_t k0, uint32_t k1) {
+  PhiloxKey k;
+  for (int r = 0; r < 10; ++r) {
+    k.rk[2 * r] = k0 + (uint32_t)r * 0x9E3779B9u;
+    k.rk[2 * r + 1] = k1 + (uint32_t)r * 0xBB67AE85u;
+  }
+  return k;
+}
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxKey& k) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
     const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
     const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-    k0 += 0x9E3779B9u;
-    k1 += 0xBB67AE85u;
+    c = make_uint4(hi1 ^ c.y ^ k.rk[2 * r], lo1, hi0 ^ c.w ^ k.rk[2 * r + 1], lo0);
   }
   return c;
 }
@@ -111,7 +125,7 @@ struct TransportParams {
   const float* minv_out;      // the same outside the tracking box (much larger)
   const float* kn_inv;        // Klein-Nishina inverse CDF [kKnInvE][kKnInvU + 1]; NULL = Kahn's sampler
   float kn_inv_lo, kn_inv_idln; // ln of its first energy, 1 / its ln-energy step
-  uint32_t key0, key1;        // Philox key = seed
+  PhiloxKey key;              // round keys of the Philox key = seed
   float e0;                   // photon energy, MeV
   int32_t q_e0;               // q_units(e0)
   float cut;                  // photon cutoff, MeV

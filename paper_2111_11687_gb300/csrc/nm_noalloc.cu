@@ -244,8 +244,7 @@ extern "C" nm_status nm_dose_tally_noalloc(const nm_grid* g, const nm_materials*
   p.kn = kn_d;
   p.minv = minv_d;
   p.minv_out = minv_d + kKnTable;
-  p.key0 = (uint32_t)seed;
-  p.key1 = (uint32_t)(seed >> 32);
+  p.key = philox_key((uint32_t)seed, (uint32_t)(seed >> 32));
   p.e0 = (float)o.photon_mev;
   p.q_e0 = q_e0;
   p.cut = (float)mt->photon_cut_mev;

@@ -58,8 +58,8 @@ __device__ __forceinline__ Energy energy_factors(float e, const float* __restric
 }
 
 __device__ __forceinline__ uint4 draw(uint32_t& ctr, uint32_t stream, uint32_t hlo, uint32_t hhi,
-                                      uint32_t k0, uint32_t k1) {
-  return philox4x32_10(make_uint4(ctr++, stream, hlo, hhi), k0, k1);
+                                      const PhiloxKey& key) {
+  return philox4x32_10(make_uint4(ctr++, stream, hlo, hhi), key);
 }
 
 // Kahn's rejection sampler for the Klein-Nishina distribution (Kahn 1954).
@@ -69,12 +69,12 @@ __device__ __forceinline__ uint4 draw(uint32_t& ctr, uint32_t stream, uint32_t h
 // x is formed directly from the uniforms so that cos θ keeps full precision
 // at low energy.  One Philox block per trial; its 4th word is the azimuth.
 __device__ __forceinline__ float kahn_x(float k, uint32_t& ctr, uint32_t stream, uint32_t hlo,
-                                        uint32_t hhi, uint32_t k0, uint32_t k1, uint32_t& r_phi,
+                                        uint32_t hhi, const PhiloxKey& key, uint32_t& r_phi,
                                         uint32_t& flags) {
   const float two_k = 2.0f * k;
   const float thr = __fdividef(1.0f + two_k, 9.0f + two_k);
   for (int trial = 0;; ++trial) {
-    const uint4 r = draw(ctr, stream, hlo, hhi, k0, k1);
+    const uint4 r = draw(ctr, stream, hlo, hhi, key);
     const float r1 = u01(r.x), r2 = u01(r.y), r3 = u01(r.z);
     float x;
     bool acc;
@@ -212,11 +212,11 @@ struct Site {
   float u, v_, w;     // direction of photon A
 };
 
-__device__ __forceinline__ Site sample_site(const PatientGeom& G, uint32_t k0, uint32_t k1,
+__device__ __forceinline__ Site sample_site(const PatientGeom& G, const PhiloxKey& key,
                                            uint32_t hlo, uint32_t hhi) {
   Site s;
   uint32_t ctr = 0;
-  uint4 r = draw(ctr, kStreamSource, hlo, hhi, k0, k1);
+  uint4 r = draw(ctr, kStreamSource, hlo, hhi, key);
   uint32_t rc, rphi;
   if (G.source_mode == NM_SOURCE_DECAY) {
     // Alias table: 64 random bits pick a column uniformly, one more the side.
@@ -230,7 +230,7 @@ __device__ __forceinline__ Site sample_site(const PatientGeom& G, uint32_t k0, u
     const int iy = rem / G.nx;
     const int ix = rem - iy * G.nx;
     const uint32_t rx = r.w;
-    r = draw(ctr, kStreamSource, hlo, hhi, k0, k1);
+    r = draw(ctr, kStreamSource, hlo, hhi, key);
     // Uniform inside the voxel; keep ix + u below ix + 1 after rounding.
     s.x = fminf((float)ix + u01(rx), __int_as_float(__float_as_int((float)(ix + 1)) - 1));
     s.y = fminf((float)iy + u01(r.x), __int_as_float(__float_as_int((float)(iy + 1)) - 1));
@@ -288,11 +288,11 @@ __device__ __forceinline__ float beta_energy(const float* __restrict__ tab, uint
 // annihilates, and q0 the positron's energy in tally units.  Returns false if
 // the track left the grid; q_left is then the energy it carried out.
 template <class Dep>
-__device__ __forceinline__ bool positron_track(const PatientGeom& G, uint32_t k0, uint32_t k1, uint32_t hlo,
+__device__ __forceinline__ bool positron_track(const PatientGeom& G, const PhiloxKey& key, uint32_t hlo,
                                                uint32_t hhi, int v0, float& x, float& y, float& z,
                                                uint32_t& q0, uint32_t& q_left, Dep&& dep) {
   uint32_t ctr = 0;
-  const uint4 r = draw(ctr, kStreamPositron, hlo, hhi, k0, k1);
+  const uint4 r = draw(ctr, kStreamPositron, hlo, hhi, key);
   const float t0 = beta_energy(G.beta_tab, r.x);
   q0 = (uint32_t)q_units(t0);
   const float cz = fmaf(2.0f, u01(r.y), -1.0f);
@@ -395,7 +395,7 @@ __device__ __forceinline__ void compton(const TransportParams& p, const float* s
     x = kn_table_x(p, e, rk);
     rphi = rp;
   } else {
-    x = kahn_x(k, ctr, stream, hlo, hhi, p.key0, p.key1, rphi, flags);
+    x = kahn_x(k, ctr, stream, hlo, hhi, p.key, rphi, flags);
   }
   const float e2 = __fdividef(e, fmaf(k, x, 1.0f));
   rotate(ux, uy, uz, 1.0f - x, fmaf(kTwoPi, u01(rphi), -3.14159265f));
@@ -563,7 +563,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
         if (got) {
           const uint64_t h = p.g.hist_begin + idx;
           const uint32_t slo = (uint32_t)h, shi = (uint32_t)(h >> 32);
-          const Site st = sample_site(p.g, p.key0, p.key1, slo, shi);
+          const Site st = sample_site(p.g, p.key, slo, shi);
           const bool o = outside_box(p.g, st.x, st.y, st.z);
           float ra, rb;
           region_distance_pair(p.g, o, st.x, st.y, st.z, st.u, st.v_, st.w, ra, rb);
@@ -643,7 +643,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
       alive = true;
       px = gsite[0]; py = gsite[nb]; pz = gsite[2 * nb];
       stream = kStreamGamma0 + (uint32_t)j; ctr = 0; steps = 0;
-      const uint4 rd = draw(ctr, stream, hlo, hhi, p.key0, p.key1);
+      const uint4 rd = draw(ctr, stream, hlo, hhi, p.key);
       const float c = fmaf(2.0f, u01(rd.x), -1.0f);
       const float sn = sqrtf(fmaxf(0.0f, fmaf(-c, c, 1.0f)));
       float sp, cp;
@@ -721,7 +721,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
           const uint64_t h = G.hist_begin + idx;
           hlo = (uint32_t)h;
           hhi = (uint32_t)(h >> 32);
-          Site st = sample_site(G, p.key0, p.key1, hlo, hhi);
+          Site st = sample_site(G, p.key, hlo, hhi);
           bool pair = true;                  // the annihilation photons start inside the grid
           if (BETA && G.source_mode == NM_SOURCE_DECAY) {
             // another radionuclide: gamma lines of this decay, emitted later
@@ -729,7 +729,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
             gsite[0] = st.x; gsite[nb] = st.y; gsite[2 * nb] = st.z;
             uint32_t m = 0, gc = 0;
             for (int j0 = 0; j0 < p.n_gamma; j0 += 4) {
-              const uint4 rg = draw(gc, kStreamGammaSelect, hlo, hhi, p.key0, p.key1);
+              const uint4 rg = draw(gc, kStreamGammaSelect, hlo, hhi, p.key);
               const uint32_t w4[4] = {rg.x, rg.y, rg.z, rg.w};
               for (int k = 0; k < 4 && j0 + k < p.n_gamma; ++k)
                 if (u01(w4[k]) < p.gamma_y[j0 + k]) m |= 1u << (j0 + k);
@@ -738,7 +738,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
           }
           if (BETA && G.beta_tab) {
             uint32_t q0 = 0, q_left = 0;
-            pair = positron_track(G, p.key0, p.key1, hlo, hhi, st.v, st.x, st.y, st.z, q0, q_left,
+            pair = positron_track(G, p.key, hlo, hhi, st.v, st.x, st.y, st.z, q0, q_left,
                                   [&](int v, uint32_t dq) {
                                     if (HIST)
                                       hist_add(hl, hn, (uint32_t)v, dq, p.g.tally, p.s2h_lo, p.s2h_hi,
@@ -833,7 +833,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
       // Compton angle if the step finds one): keeping them for the next step
       // would save draws per lane but not per warp, where lanes
       // are out of phase, and costs registers.
-      const uint4 rr = draw(ctr, stream, hlo, hhi, p.key0, p.key1);
+      const uint4 rr = draw(ctr, stream, hlo, hhi, p.key);
       const uint32_t r0 = rr.x, r1 = rr.y;
       const float imaj = f.inv_mubar;
       float s = -__logf(u01(r0)) * imaj;   // cm
@@ -891,7 +891,7 @@ __global__ void __launch_bounds__(512, 2) transport_kernel(const TransportParams
           atomicAdd(&s_cnt[MULTI ? pi : 0][kCtrRayleigh], 1ull);
           // Thomson angular shape (1 + cos^2)/2 by rejection; one block per trial.
           for (int trial = 0;; ++trial) {
-            const uint4 r = draw(ctr, stream, hlo, hhi, p.key0, p.key1);
+            const uint4 r = draw(ctr, stream, hlo, hhi, p.key);
             const float cth = fmaf(2.0f, u01(r.x), -1.0f);
             const bool acc = 2.0f * u01(r.y) <= fmaf(cth, cth, 1.0f);
             if (acc || trial + 1 >= kKahnTrialLimit) {
@@ -953,7 +953,7 @@ __global__ void check_kn_table_kernel(const TransportParams p, float e, int64_t 
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   uint32_t ctr = 0;
-  const uint4 r = draw(ctr, 7u, (uint32_t)i, (uint32_t)(i >> 32), p.key0, p.key1);
+  const uint4 r = draw(ctr, 7u, (uint32_t)i, (uint32_t)(i >> 32), p.key);
   out[i] = 1.0f - kn_table_x(p, e, r.x);
 }
 
@@ -962,13 +962,14 @@ __global__ void check_beta_kernel(const float* tab, int64_t n, uint32_t k0, uint
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   uint32_t ctr = 0;
-  const uint4 r = draw(ctr, kStreamPositron, (uint32_t)i, (uint32_t)(i >> 32), k0, k1);
+  const uint4 r = draw(ctr, kStreamPositron, (uint32_t)i, (uint32_t)(i >> 32), philox_key(k0, k1));
   out[i] = beta_energy(tab, r.x);
 }
 
 __global__ void check_philox_kernel(const uint4* ctr, const uint2* key, int64_t n, uint4* out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = philox4x32_10(ctr[i], key[i].x, key[i].y);
+  // the transport's own path: round keys from philox_key, then the rounds
+  if (i < n) out[i] = philox4x32_10(ctr[i], philox_key(key[i].x, key[i].y));
 }
 
 __global__ void check_kahn_kernel(float e, int64_t n, uint32_t k0, uint32_t k1, float* out,
@@ -976,7 +977,7 @@ __global__ void check_kahn_kernel(float e, int64_t n, uint32_t k0, uint32_t k1, 
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   uint32_t ctr = 0, rphi, flags = 0;
-  const float x = kahn_x(e * kInvElectronMassMeV, ctr, 7u, (uint32_t)i, (uint32_t)(i >> 32), k0, k1,
+  const float x = kahn_x(e * kInvElectronMassMeV, ctr, 7u, (uint32_t)i, (uint32_t)(i >> 32), philox_key(k0, k1),
                          rphi, flags);
   out[i] = 1.0f - x;
   if (flags) atomicOr(status, flags);
@@ -987,7 +988,7 @@ __global__ void check_source_kernel(const TransportParams p, uint64_t first, int
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const uint64_t h = first + (uint64_t)i;
-  const Site s = sample_site(p.g, p.key0, p.key1, (uint32_t)h, (uint32_t)(h >> 32));
+  const Site s = sample_site(p.g, p.key, (uint32_t)h, (uint32_t)(h >> 32));
   voxel[i] = s.v;
   pos[3 * i + 0] = s.x / p.g.inv_dx;
   pos[3 * i + 1] = s.y / p.g.inv_dy;
