@@ -42,3 +42,15 @@ def test_roofline_without_profile_leaves_traffic_null(monkeypatch):
     r = bench.transport_roofline(per, 1e8, 20.0, None, None)
     assert r["traffic"] is None and r["traffic_source"] is None and r["peak_source"] == "fallback"
     assert "issue" not in r["ceilings"]
+
+
+def test_committed_transport_profile_describes_the_current_kernel():
+    """The ncu figures bench.py quotes (traffic, L2 sectors, instructions per
+    decay) are read from the committed transport summary only while it was
+    captured on the current kernel source; a kernel change must come with a
+    new capture, else the benchmark line loses those figures."""
+    import bench
+    prof = bench._profile_figures()
+    assert prof is not None, "profiles/transport_kernel_adult_phantom.md was captured on another kernel source"
+    for k in ("dram_bytes_per_decay", "lts_sectors_per_decay", "warp_inst_per_decay", "lane_efficiency_pct"):
+        assert prof[k] > 0, k
