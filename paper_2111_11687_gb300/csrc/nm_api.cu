@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "nm_internal.cuh"
+#include "nm_trace.h"
 
 using namespace nm;
 
@@ -718,6 +719,7 @@ static nm_status choose_shape(nm_dose* h) {
 
 nm_status nm_dose_create(nm_dose** out, const nm_grid* g, const nm_materials* mt,
                          const float* activity, const uint8_t* labels, const nm_options* opts) {
+  NvtxRange range("nm_dose_create");
   if (!out) return fail(NM_ERR_ARG, "out is NULL");
   *out = nullptr;
   nm_options o;
@@ -921,6 +923,7 @@ nm_status nm_dose_create(nm_dose** out, const nm_grid* g, const nm_materials* mt
 }
 
 nm_status nm_dose_run(nm_dose* h, uint64_t n, uint64_t seed) {
+  NvtxRange range("nm_dose_run");
   if (!h) return fail(NM_ERR_ARG, "handle is NULL");
   if (n == 0) return NM_OK;
   const uint64_t per = h->units_per_history();
@@ -952,6 +955,7 @@ nm_status nm_dose_run(nm_dose* h, uint64_t n, uint64_t seed) {
   NM_CUDA(cudaEventRecord(h->ev_fork, s), "cudaEventRecord");
   NM_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0), "cudaStreamWaitEvent");
   for (int b = 0; b < B; ++b) {
+    NvtxRange batch_range("batch");
     const uint64_t nb = n / B + ((uint64_t)b < n % B ? 1 : 0);
     const bool odd = (b & 1) != 0;
     cudaStream_t bs = odd ? h->side : s;
@@ -1034,6 +1038,7 @@ static std::map<BatchKey, Shape> g_batch_tune;
 
 extern "C" nm_status nm_dose_run_batch(nm_dose* const* hs, int32_t n, const uint64_t* n_decays,
                                        uint64_t seed) {
+  NvtxRange range("nm_dose_run_batch");
   if (!hs || !n_decays || n < 1 || n > kMaxBatchPatients)
     return fail(NM_ERR_ARG, "need 1..%d handles and their decay counts", kMaxBatchPatients);
   long long vox_sum = 0, vox_hash = 0;
@@ -1263,6 +1268,7 @@ static nm_status finalize(nm_dose* h, float* dose, float* sigma) {
 }
 
 nm_status nm_dose_get(nm_dose* h, float* dose, float* sigma, double* organ_dose) {
+  NvtxRange range("nm_dose_get");
   if (!h) return fail(NM_ERR_ARG, "handle is NULL");
   cudaStream_t s = h->stream;
   const bool dd = is_device_ptr(dose), ds = is_device_ptr(sigma);
@@ -1295,6 +1301,7 @@ nm_status nm_dose_get(nm_dose* h, float* dose, float* sigma, double* organ_dose)
 
 nm_status nm_dose_get_organs(nm_dose* h, double* mean, double* eps_rms, double* sigma_mean,
                              int64_t* voxels) {
+  NvtxRange range("nm_dose_get_organs");
   if (!h) return fail(NM_ERR_ARG, "handle is NULL");
   if (!eps_rms && h->labels) {
     // Eq. 2 and the batch sigma from the per-organ batch sums of the fold, no
@@ -1578,6 +1585,7 @@ nm_status nm_dose_restore(nm_dose* h, const void* buf, uint64_t bytes) {
 }
 
 nm_status nm_dose_merge(nm_dose* h, const void* buf, uint64_t bytes) {
+  NvtxRange range("nm_dose_merge");
   if (!h) return fail(NM_ERR_ARG, "handle is NULL");
   CkptHeader hd;
   nm_status st = ckpt_read_header(h, buf, bytes, &hd);

@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "nm_internal.cuh"
+#include "nm_trace.h"
 
 using namespace nm;
 
@@ -1090,6 +1091,7 @@ nm_status nm_denoise_captured(nm_denoiser* h, int32_t layer, int32_t kind, uint1
 
 nm_status nm_denoise_train_step(nm_denoiser* h, const uint16_t* x, const float* target, const float* weight,
                                 float lr, float* loss) {
+  NvtxRange range("nm_denoise_train_step");
   if (!h || !x || !target) return fail(NM_ERR_ARG, "bad arguments");
   if (!dev_ptr(x) || !dev_ptr(target) || (weight && !dev_ptr(weight)))
     return fail(NM_ERR_ARG, "x, target and weight must be device pointers");
@@ -1121,6 +1123,7 @@ nm_status nm_denoise_train_step(nm_denoiser* h, const uint16_t* x, const float* 
 }
 
 nm_status nm_denoise_forward(nm_denoiser* h, const uint16_t* x, float* y) {
+  NvtxRange range("nm_denoise_forward");
   if (!h || !x || !y || !dev_ptr(x) || !dev_ptr(y)) return fail(NM_ERR_ARG, "x and y must be device pointers");
   cudaStream_t s = h->s;
   const long long m = h->vox(0);
@@ -1173,6 +1176,7 @@ nm_status nm_denoise_apply(nm_denoiser* h, const float* dose, const float* densi
 
 nm_status nm_denoise_apply_roi(nm_denoiser* h, const float* dose, const float* density, const float* activity,
                                const uint8_t* roi, int32_t nx, int32_t ny, int32_t nz, float* dose_out) {
+  NvtxRange range("nm_denoise_apply_roi");
   if (!h || !dose || !density || !activity || !dose_out || nx <= 0 || ny <= 0 || nz <= 0)
     return fail(NM_ERR_ARG, "bad arguments");
   if (!dev_ptr(dose) || !dev_ptr(density) || !dev_ptr(activity) || !dev_ptr(dose_out) || (roi && !dev_ptr(roi)))
