@@ -179,10 +179,12 @@ def ptr(x):
     if x is None:
         return None
     if isinstance(x, np.ndarray):
-        assert x.flags.c_contiguous
+        if not x.flags.c_contiguous:
+            raise ValueError("array arguments must be C-contiguous")
         return x.ctypes.data
     if hasattr(x, "data_ptr"):
-        assert x.is_contiguous()
+        if not x.is_contiguous():
+            raise ValueError("tensor arguments must be contiguous")
         return x.data_ptr()
     raise TypeError(type(x))
 
@@ -282,6 +284,21 @@ def nm_ct_to_phantom(hu, density, material, stream=None):
     _check(load().nm_ct_to_phantom(ptr(hu), n, ptr(density), ptr(material), _stream_ptr(stream)))
 
 
+# Voxel and label counts of the handles nm_dose_create returned, so that the
+# raw wrappers below can check the buffers they hand over: the C side cannot
+# see the size of a device buffer.
+_HANDLE_GRID = {}
+
+
+def _handle_key(h):
+    return h.value if isinstance(h, C.c_void_p) else int(h)
+
+
+def _grid_of(h):
+    """(voxels, labels) of a handle made here, or None for one made elsewhere."""
+    return _HANDLE_GRID.get(_handle_key(h)) if h is not None else None
+
+
 def nm_dose_create(density, material, spacing, materials: Materials, activity=None, labels=None,
                    opts: nm_options | None = None):
     """density/material/activity/labels are [nz, ny, nx] (x fastest); spacing (dx, dy, dz) cm."""
@@ -296,6 +313,7 @@ def nm_dose_create(density, material, spacing, materials: Materials, activity=No
     h = C.c_void_p()
     _check(load().nm_dose_create(C.byref(h), C.byref(g), C.byref(m), ptr(activity), ptr(labels),
                                  C.byref(opts) if opts is not None else None))
+    _HANDLE_GRID[h.value] = (V, int(opts.n_labels) if opts is not None else 0)
     return h
 
 
@@ -312,7 +330,14 @@ def nm_dose_run_batch(handles, n_decays, seed: int):
 
 
 def nm_dose_get(h, dose=None, sigma=None, organ_dose=None):
-    _check(load().nm_dose_get(h, ptr(dose), ptr(sigma), ptr(organ_dose)))
+    grid = _grid_of(h)
+    if grid is not None:
+        V, n_labels = grid
+        _want("dose", dose, "float32", V)
+        _want("sigma", sigma, "float32", V)
+        _want("organ_dose", organ_dose, "float64", n_labels + 1)
+    pointers = ptr(dose), ptr(sigma), ptr(organ_dose)
+    _check(load().nm_dose_get(h, *pointers))
 
 
 def nm_dose_get_organs(h, n_labels: int, eps: bool = True, sigma: bool = True):
@@ -329,7 +354,11 @@ def nm_dose_get_organs(h, n_labels: int, eps: bool = True, sigma: bool = True):
 
 
 def nm_dose_get_tally(h, tally):
-    _check(load().nm_dose_get_tally(h, ptr(tally)))
+    grid = _grid_of(h)
+    if grid is not None:
+        _want("tally", tally, "int64", grid[0])
+    p = ptr(tally)
+    _check(load().nm_dose_get_tally(h, p))
 
 
 def nm_time_integrated_activity(maps, t_h, half_life_h: float, out, stream=None) -> float:
@@ -359,6 +388,8 @@ def nm_dose_reset(h):
 
 def nm_dose_destroy(h):
     load().nm_dose_destroy(h)
+    if h is not None:
+        _HANDLE_GRID.pop(_handle_key(h), None)
 
 
 def nm_release_cached_memory() -> None:

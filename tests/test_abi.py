@@ -107,3 +107,27 @@ def test_binding_rejects_mismatched_buffers_before_the_call(monkeypatch):
     for tally in (np.zeros(shape, np.int64), np.zeros(shape, np.int32), np.zeros(10, np.int64)):
         with pytest.raises(ValueError):
             nmdose.nm_dose_tally_noalloc(den, mat, (0.5, 0.5, 0.5), m, tally, 1000, 1, activity=act)
+
+
+def test_raw_getters_check_buffers_against_the_handle(monkeypatch):
+    """nm_dose_get and nm_dose_get_tally write V values (and n_labels + 1 organ
+    means) through raw pointers: for a handle made by the binding, buffers of
+    another size or type, or non-contiguous ones, are refused before the call."""
+    import numpy as np
+
+    from paper_2111_11687_gb300 import nmdose
+    monkeypatch.setattr(nmdose, "_lib", _NoCalls())
+    fake = 0x1234
+    monkeypatch.setitem(nmdose._HANDLE_GRID, fake, (120, 27))
+    good = np.empty(120, np.float32)
+    for kw in (dict(dose=np.empty(119, np.float32)), dict(dose=np.empty(120, np.float64)),
+               dict(sigma=np.empty(121, np.float32)), dict(organ_dose=np.empty(27))):
+        args = dict(dose=good, sigma=None, organ_dose=None)
+        args.update(kw)
+        with pytest.raises(ValueError):
+            nmdose.nm_dose_get(fake, **args)
+    for tally in (np.empty(120, np.int32), np.empty(100, np.int64)):
+        with pytest.raises(ValueError):
+            nmdose.nm_dose_get_tally(fake, tally)
+    with pytest.raises(ValueError):
+        nmdose.nm_dose_get(fake, np.empty((240,), np.float32)[::2], None, None)   # not contiguous
