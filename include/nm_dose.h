@@ -336,7 +336,10 @@ nm_status nm_check_kn_table(double e_mev, double cut_mev, double e0_mev, int64_t
  * created after one of the same grid maps no new memory.  This call returns
  * every kept buffer to the device (cudaFree); buffers of live handles are not
  * affected.  A failed allocation releases them by itself before it retries.
- * Safe to call at any time from any thread. */
+ * Safe to call at any time from any thread.  Kept buffers belong to the
+ * device's context: destroy the handles and call this before cudaDeviceReset
+ * or anything else that ends the primary context, whose memory (kept buffers
+ * included) does not outlive it. */
 void nm_release_cached_memory(void);
 
 /* Fault injection: the n-th device allocation made by the library from now
