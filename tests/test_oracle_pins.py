@@ -422,6 +422,31 @@ def test_eq4_reproduces_table1(orc):
     assert orc.rel_diff_percent(2.0, 1.0) == 100.0
 
 
+def test_oracle_dose_rate_scale_matches_table1(orc):
+    """The absolute scale of Eq. 1 (MeV -> J, g -> kg, voxel volume, A(t_s))
+    against the dose rates Table 1 prints (§3.2).  The stored FP64 oracle
+    organ means of the benchmark phantom carry the activity of the paper's
+    patient (8.0 mCi of 18F, 60 min after injection, §2.2) in the body of a
+    pelvis-to-head field of view, which weighs far less than that 79 kg
+    patient.  At equal activity a mean dose rate goes as 1 / mass, so the
+    median organ dose rate, times the phantom's body mass over 79 kg, must
+    land within a factor of two of Table 1's median (it lands within 5 %,
+    which the different anatomy and uptake make partly chance); a slip in any
+    unit of Eq. 1 moves it by orders of magnitude."""
+    from paper_2111_11687_gb300 import inputs
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "adult_phantom_organs_oracle.txt"))
+            if l.strip() and not l.startswith("#")]
+    organs = np.array([float(r[1]) for r in rows])[1:]
+    assert organs.size == 27 and np.all(organs > 0)
+    ph = inputs.adult_phantom()                 # the stored phantom: 256x256x300 x 2x2x3 mm, seed 1
+    den, _ = orc.hu_to_phantom(ph.hu)
+    body_kg = float(den[den >= 0.1].astype(np.float64).sum()) * 0.2 * 0.2 * 0.3 / 1000.0
+    assert 15.0 < body_kg < 60.0, body_kg
+    scaled = np.median(organs) * body_kg / 79.0
+    table = np.median([r[1] for r in _table1()])   # GATE column (the paper's reference)
+    assert 0.5 < scaled / table < 2.0, (scaled, table, body_kg)
+
+
 @pytest.mark.parametrize("absorb", [False, True])
 def test_history_sigma_bernoulli_closed_form(orc, absorb):
     # Every history deposits a fixed amount T in its decay voxel and nothing
